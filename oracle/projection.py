@@ -1,0 +1,127 @@
+"""Symmetry-adapted product basis of the oracle (Sec. III.C of the paper).
+
+Test infrastructure only (see the package docstring).
+
+  * Band rotations Gamma(s)_{kn}^{k'n'} = <phi_k'n' | s phi_kn>, k' = s k,
+    restricted to degenerate n' ~ n (Eq. Ts), with the action of Eq. sphi:
+    (s phi)(r) = phi(s^{-1} r), i.e. c'(R^{-T} p) = exp(-2 pi i R^{-T}p . t) c(p).
+  * Two-particle representation (Eq. Ttilde): s maps |k v c> to
+    sum Gamma(s)_{kc}^{k'c'} conj(Gamma(s)_{kv}^{k'v'}) |k' v' c'>.
+  * Projector P_mu = d_mu/|S| sum_s chi_mu(s)^* Gamma~(s) (Eq. projection).
+  * Basis: P_mu applied to the unit vectors of each orbit; the paper
+    orthonormalises by SVD, whose basis is not unique for equal singular
+    values, so the canonical basis used here is modified Gram-Schmidt (two
+    passes) over the orbit members in ascending order, keeping a vector when
+    its residual norm exceeds 1e-6.  The columns form U_mu and
+    H_mu = U_mu^dagger H U_mu (Eqs. transformationU, Hblock).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from .hamiltonian import Inputs
+from .tables import Group, MeshTables, multiplets, orbits
+
+KEEP_TOL = 1e-6
+
+
+def band_rotation(inp: Inputs, grp: Group, mt: MeshTables, s: int, k: int) -> np.ndarray:
+    """Gamma(s) at k as an Nb x Nb matrix G[n', n] = <phi_{sk,n'} | s phi_{kn}>,
+    zero between non-degenerate bands."""
+    k2 = int(mt.rotk[s, k])
+    nkc = int(inp.nkc[k])
+    y = inp.gk[k, :nkc] + mt.f(k)[None, :]                    # full vectors at k
+    yr = y @ grp.rk[s].T                                      # R^{-T} p
+    m2 = np.rint(yr - mt.f(k2)[None, :]).astype(np.int64)
+    if np.abs(yr - mt.f(k2) - m2).max() > 1e-9:
+        raise ValueError("rotated vector is off the mesh coset")
+    j = inp.index_in_sphere(k2, m2)
+    if np.any(j < 0):
+        raise ValueError("coset sphere is not closed under the operation")
+    phase = np.exp(-2j * math.pi * (yr @ grp.tau[s]))
+    c_k = inp.coef[k][:, :nkc]                                # [nb, nkc]
+    c_k2 = inp.coef[k2][:, j]                                 # value at R^{-T}p
+    g = np.conj(c_k2) @ (phase[:, None] * c_k.T)              # [n', n]
+    mask = np.zeros_like(g, dtype=bool)
+    for lo, hi in ((0, inp.nv), (inp.nv, inp.nb)):
+        for m in multiplets(inp.eps[k], lo, hi):
+            mask[np.ix_(m, m)] = True
+    return np.where(mask, g, 0.0)
+
+
+def two_particle_rep(inp: Inputs, grp: Group, mt: MeshTables, s: int) -> sp.csr_matrix:
+    """Gamma~(s) as a sparse N x N matrix M with M[J, I] = Gamma~(s)_I^J."""
+    nv, nc = inp.nv, inp.nc
+    rows, cols, vals = [], [], []
+    for k in range(inp.nk):
+        k2 = int(mt.rotk[s, k])
+        g = band_rotation(inp, grp, mt, s, k)
+        gv = g[:nv, :nv]
+        gc = g[nv:, nv:]
+        blk = np.einsum("dc,wv->wdvc", gc, np.conj(gv)).reshape(nv * nc, nv * nc)
+        r, c = np.nonzero(blk)
+        rows.append(k2 * nv * nc + r)
+        cols.append(k * nv * nc + c)
+        vals.append(blk[r, c])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(inp.N, inp.N))
+
+
+class Basis:
+    """Characters, projectors and the canonical symmetry-adapted basis."""
+
+    def __init__(self, inp: Inputs, grp: Group, mt: MeshTables):
+        self.inp, self.grp, self.mt = inp, grp, mt
+        self.chi, self.dims, self.class_of = grp.characters()
+        self.reps = [two_particle_rep(inp, grp, mt, s) for s in range(grp.n)]
+        self.orbits = orbits(mt, inp.eps, inp.nv, inp.nc)
+        self._u = {}
+
+    def projector(self, mu: int) -> sp.csr_matrix:
+        out = sp.csr_matrix((self.inp.N, self.inp.N), dtype=np.complex128)
+        for s in range(self.grp.n):
+            out = out + np.conj(self.chi[mu, s]) * self.reps[s]
+        return out * (self.dims[mu] / self.grp.n)
+
+    def bright(self):
+        """Irreps contained in the polar-vector representation (chi = Tr A)."""
+        vec = self.grp.vector_character()
+        mult = (self.chi.astype(np.float64) @ vec) / self.grp.n
+        return [mu for mu in range(len(self.dims)) if round(mult[mu]) > 0]
+
+    def basis(self, mu: int):
+        """(U_mu as a dense N x dim array, list of (orbit index, columns))."""
+        if mu in self._u:
+            return self._u[mu]
+        P = self.projector(mu).tocsc()
+        cols, owner = [], []
+        for o, mem in enumerate(self.orbits):
+            acc = []
+            for j in mem:
+                x = P[:, j].toarray()[mem, 0]
+                for _ in range(2):
+                    for u in acc:
+                        x = x - u * np.vdot(u, x)
+                nrm = np.linalg.norm(x)
+                if nrm > KEEP_TOL:
+                    acc.append(x / nrm)
+            for u in acc:
+                full = np.zeros(self.inp.N, dtype=np.complex128)
+                full[mem] = u
+                cols.append(full)
+                owner.append(o)
+        U = np.array(cols).T if cols else np.zeros((self.inp.N, 0), dtype=np.complex128)
+        self._u[mu] = (U, np.array(owner, dtype=np.int64))
+        return self._u[mu]
+
+    def block_dim_trace(self, mu: int) -> int:
+        """dim of the irrep subspace as Tr P_mu (an integer)."""
+        return int(round(self.projector(mu).diagonal().sum().real))
+
+
+def project(U: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """H_mu = U^dagger H U."""
+    return U.conj().T @ H @ U
