@@ -1,0 +1,210 @@
+/*
+ * bse.h - C ABI of the GB300 symmetry-reduced Bethe-Salpeter block builder.
+ *
+ * Computes, on one GPU, the symmetry-adapted block of the electron-hole
+ * Hamiltonian of Stöhler, Blügel and Friedrich, "Efficient all-electron
+ * Bethe-Salpeter implementation using crystal symmetries":
+ *
+ *   H = diag(eps_ck - eps_vk) + spin * K^x - K^d            (Eq. BSE-eigval)
+ *   H_mu = U_mu^dagger H U_mu                               (Eqs. projection,
+ *                                                            transformationU)
+ *
+ * in a plane-wave basis, and the optical spectrum of one block
+ * (Eqs. macro_diel, reducible_polar, oscillatorA, oscillator).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Atomic units (bohr, hartree).  Complex numbers are interleaved
+ *    (re, im) doubles.  Matrices are row-major unless stated otherwise.
+ *  - Lattice L: 3x3, row-major, columns are a1, a2, a3.  A symmetry
+ *    operation {R|t} maps fractional positions x -> R x + t (Eq. sk, sphi
+ *    with alpha = 0); it maps reciprocal fractional vectors y -> R^{-T} y.
+ *  - Gamma-centred mesh n1 x n2 x n3: f_k = (i/n1, j/n2, l/n3),
+ *    k = (i*n2 + j)*n3 + l.  The same mesh indexes q = k - k'.
+ *  - A plane wave of band coefficient c_kn(p) has the full wave vector
+ *    p = f_k + m (m integer, reciprocal fractional coordinates).
+ *  - Bands 0..nv-1 are occupied (v), nv..nv+nc-1 unoccupied (c).
+ *    Product index I = (k*nv + v)*nc + c  (Eq. 2p-product-basis).
+ *  - Irreps are numbered in the canonical order returned by bse_tables:
+ *    ascending (dimension, then character vector over operations).
+ *  - All device work runs on the CUDA stream given to bse_create, in stream
+ *    order; functions return once the work is enqueued unless stated.
+ *  - Every function returns BSE_OK (0) or a negative status; the message of
+ *    the last failure of the calling thread is bse_last_error().
+ */
+#ifndef BSE_GB300_H
+#define BSE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bse_ctx bse_ctx;   /* opaque, library-owned; not thread-safe */
+
+enum {
+    BSE_OK = 0,
+    BSE_EINVAL = -1,       /* invalid argument (sizes, pointers, indices) */
+    BSE_ENOMEM = -2,       /* device or host allocation failed */
+    BSE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    BSE_ESYMM = -4,        /* inputs break the symmetry (non-unitary band rotation,
+                              inconsistent orbits, block dims not summing to N) */
+    BSE_ETIMEOUT = -5,     /* a bounded device wait gave up */
+    BSE_EUNSUPPORTED = -6, /* a case outside what is implemented */
+    BSE_ESOLVER = -7       /* the dense eigensolver failed */
+};
+
+enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2 };
+
+/* terms of H to include (bit mask) */
+enum { BSE_TERM_DIAG = 1, BSE_TERM_EXCHANGE = 2, BSE_TERM_DIRECT = 4, BSE_TERM_ALL = 7 };
+
+/* band sets of bse_pairdens */
+enum { BSE_BANDS_CC = 0, BSE_BANDS_VV = 1, BSE_BANDS_CV = 2 };
+
+/*
+ * bse_system: one crystal, its symmetry, its band coefficients and W(q).
+ * Everything is copied at bse_create; the caller keeps ownership.
+ * Pointers marked [loc] are device pointers when device_inputs != 0, host
+ * pointers otherwise; all other pointers are host pointers.
+ */
+typedef struct {
+    double lattice[9];       /* L, row-major, columns a1 a2 a3 (bohr) */
+    int32_t n_ops;           /* number of space-group operations modulo lattice translations */
+    const int32_t* rot;      /* [n_ops][3][3] R (row-major) in lattice coordinates */
+    const double* tau;       /* [n_ops][3] fractional translation t */
+    int32_t mesh[3];         /* n1, n2, n3 */
+    int32_t nv, nc;          /* occupied / unoccupied bands per k */
+    int32_t npw_max;         /* capacity of the plane-wave axis of coef and gk */
+    const int32_t* npw;      /* [Nk] plane waves at k */
+    const int32_t* gk;       /* [Nk][npw_max][3] integer m of p = f_k + m; any order */
+    const double* coef;      /* [loc] [Nk][nv+nc][npw_max] complex c_kn(p), orthonormal bands */
+    const double* eps;       /* [loc] [Nk][nv+nc] band energies (Ha) entering H */
+    int32_t ng_max;          /* capacity of the G axis of W and gq */
+    const int32_t* ng;       /* [Nk] number of Q = f_q + G at q */
+    const int32_t* gq;       /* [Nk][ng_max][3] integer G of Q = f_q + G; sphere must contain G = 0 at q = 0 */
+    const double* w;         /* [loc] [Nk][ng_max][ng_max] complex W_{QQ'}(q), row Q, column Q'.
+                                At q = 0 the head and wings are ignored (Sec. III.B). */
+    double eps_inf[9];       /* dielectric tensor L of Eq. Wdiv, row-major */
+    double w_div;            /* head correction W^div (Ha); NaN: computed (Eqs. Wdiv,
+                                divergence_int, divergence_sum, b = 0.005) */
+    double qhat[3];          /* light polarisation (Cartesian, unit vector) */
+    double scissor;          /* eps0_c = eps_c - scissor in Eq. oscillator */
+    int32_t spin_factor;     /* 2 for a non-magnetic system without SOC */
+    int32_t device_inputs;   /* 0: [loc] pointers are host pointers; 1: device pointers */
+} bse_system;
+
+/*
+ * bse_create - validate the system, build the symmetry tables (stars,
+ * little groups, characters, orbits; Sec. III.C), the band rotations
+ * Gamma(s) (Eq. Ts) and the canonical orthonormal basis of every irrep
+ * (Eq. projection followed by two-pass modified Gram-Schmidt per orbit; the
+ * paper uses an SVD, whose basis is not unique), and compute W^div if
+ * requested.  stream: a cudaStream_t, or NULL for the default stream.
+ * On success *out owns device memory until bse_destroy.  Blocks until the
+ * set-up work has finished.
+ * Errors: EINVAL (sizes, non-unimodular R, mesh not invariant, G = 0 missing),
+ * ESYMM (operations not a group, sphere not closed under an operation,
+ * non-unitary Gamma, block dimensions not summing to N), EUNSUPPORTED
+ * (complex characters), ENOMEM, ECUDA.
+ */
+int bse_create(bse_ctx** out, const bse_system* sys, void* stream);
+
+/* bse_destroy - free everything owned by ctx (NULL is allowed). */
+int bse_destroy(bse_ctx* ctx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* bse_last_error(void);
+
+/*
+ * bse_tables_view: read-only host views into tables owned by ctx (valid
+ * until bse_destroy).  These are integer-exact and match the oracle's.
+ */
+typedef struct {
+    int32_t n_ops, nk, n_stars, n_irreps, n_orbits;
+    int64_t n_product;            /* N = Nk * nv * nc */
+    const int32_t* rotk;          /* [n_ops][nk] mesh index of s k */
+    const int32_t* star_of_k;     /* [nk] star of k; stars numbered by their lowest k */
+    const int32_t* star_rep;      /* [n_stars] lowest k of the star */
+    const int32_t* s_k;           /* [nk] lowest operation index s with s star_rep = k */
+    const int32_t* class_of_op;   /* [n_ops] conjugacy class (numbered by lowest op) */
+    const int32_t* chi;           /* [n_irreps][n_ops] characters (Eq. LOT holds) */
+    const int32_t* irrep_dim;     /* [n_irreps] d_mu */
+    const int32_t* bright;        /* [n_irreps] multiplicity in the polar-vector representation */
+    const int64_t* block_dim;     /* [n_irreps] dimension of H_mu */
+    const int32_t* orbit_of;      /* [N] orbit of each product index; orbits ordered by lowest member */
+    double w_div;                 /* head correction used on the diagonal (Ha) */
+} bse_tables_view;
+
+int bse_tables(const bse_ctx* ctx, bse_tables_view* out);
+
+/*
+ * bse_pairdens - pair densities (Eq. w_interaction in plane waves)
+ *   rho_nn'(k, k'; Q) = sum_{p' in S_k'} conj(c_kn(p' + Q)) c_k'n'(p'),
+ *   Q = f_q + G over the sphere of q = k - k'.
+ * bands: BSE_BANDS_CC (n, n' conduction), BSE_BANDS_VV, or BSE_BANDS_CV
+ * (n conduction, n' valence; with k = k' these are the exchange vectors
+ * m^k_cv(G) of Eq. v_scalar).
+ * k, kp: host arrays [npairs]; out_dev: device [npairs][n][n'][ng_max]
+ * complex128, entries with G index >= ng(q) set to zero; caller-owned.
+ */
+int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npairs,
+                 int32_t bands, void* out_dev);
+
+/*
+ * bse_build_block - H_mu = U_mu^dagger H U_mu for irrep mu, never forming
+ * the full H: direct-term tiles of each pair of k stars are projected at
+ * once (Sec. III.C.5), the exchange term is applied in the projected form
+ * (U_mu^dagger P) vbar (U_mu^dagger P)^dagger (Eq. v_scalar), the diagonal
+ * eps_c - eps_v - W^div in FP64.  terms: BSE_TERM_* mask.
+ * prec: BSE_FP64 (the only precision implemented so far; others return
+ * EUNSUPPORTED).  h_dev: device, complex128, column-major dim x dim with
+ * leading dimension ld >= dim; the full Hermitian matrix is written.
+ * Scratch is library-owned.
+ */
+int bse_build_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
+                    void* h_dev, int64_t ld);
+
+/*
+ * bse_build_full - the unprojected H (N x N, complex128, column-major, ld
+ * >= N, device) in FP64; meant for checks on small meshes.
+ */
+int bse_build_full(bse_ctx* ctx, uint32_t terms, void* h_dev, int64_t ld);
+
+/*
+ * bse_block_basis - the dense N x dim U_mu (complex128, column-major, ld >= N,
+ * device), columns in block order.
+ */
+int bse_block_basis(bse_ctx* ctx, int32_t irrep, void* u_dev, int64_t ld);
+
+/*
+ * bse_dipoles - B_kvc = <phi_kv| -i qhat.grad |phi_kc> / (sqrt(V_uc)
+ * (eps_c - scissor - eps_v)) (Eq. oscillator) for every product index;
+ * b_dev: device [N] complex128.
+ */
+int bse_dipoles(bse_ctx* ctx, void* b_dev);
+
+/*
+ * bse_block_spectrum - eigensolution of H_mu (dense Hermitian FP64 solver)
+ * and the spectrum of the block:
+ *   B_lambda = a_lambda^T (U_mu^T B)                (Eq. oscillatorA)
+ *   Im eps_M(w) = 4 pi spin / Nk sum_lambda |B_lambda|^2
+ *                 [eta/((w - Omega)^2 + eta^2) - eta/((w + Omega)^2 + eta^2)]
+ *                                                  (Eqs. macro_diel, reducible_polar)
+ * h_dev: H_mu as written by bse_build_block (read only); omega_dev: device
+ * [n_omega]; outputs (device, caller-owned): omega_out [dim] ascending
+ * eigenvalues, osc [dim] |B_lambda|^2, im_eps [n_omega].
+ * Errors: ESOLVER if the eigensolver reports failure.
+ */
+int bse_block_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t ld,
+                       const double* omega_dev, int64_t n_omega, double eta,
+                       double* omega_out, double* osc, double* im_eps);
+
+/* Wait for all work on the context's stream; returns ECUDA on a device error. */
+int bse_sync(bse_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

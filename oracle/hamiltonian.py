@@ -238,3 +238,36 @@ def full_hamiltonian(inp: Inputs, mt: MeshTables, w_div: float | None = None,
     if "w" in terms:
         H -= direct_matrix(inp, mt)
     return H
+
+
+def hamiltonian_block(inp: Inputs, mt: MeshTables, rows, cols, w_div: float) -> np.ndarray:
+    """Rows/columns of the full H restricted to product indices of the k
+    points in ``rows`` x ``cols`` (ordered as given, each k contributing its
+    Nv*Nc products in (v, c) order): the same entries as full_hamiltonian."""
+    nv, nc = inp.nv, inp.nc
+    b = nv * nc
+    H = -direct_matrix(inp, mt, rows, cols)
+    P, vbar = exchange_vectors_for(inp, mt, rows)
+    Pc, _ = exchange_vectors_for(inp, mt, cols)
+    H += inp.spin * (P * vbar[None, :]) @ Pc.conj().T / inp.volume
+    dg = diagonal(inp)
+    for i, k in enumerate(rows):
+        for j, kp in enumerate(cols):
+            if k == kp:
+                idx = np.arange(b)
+                H[i * b + idx, j * b + idx] += dg[k * b:(k + 1) * b] - w_div
+    return H
+
+
+def exchange_vectors_for(inp: Inputs, mt: MeshTables, ks):
+    """Rows of the exchange vectors P for the k points ks (see exchange_vectors)."""
+    nv, nc = inp.nv, inp.nc
+    ng0 = int(inp.ngc[0])
+    P = np.zeros((len(ks) * nv * nc, ng0), dtype=np.complex128)
+    for i, k in enumerate(ks):
+        rho, q = pair_density(inp, mt, k, k, range(nv, nv + nc), range(nv))
+        P[i * nv * nc:(i + 1) * nv * nc] = np.transpose(rho, (1, 0, 2)).reshape(nv * nc, ng0)
+    G = inp.cart(inp.gq[0, :ng0].astype(np.float64))
+    g2 = np.einsum("gi,gi->g", G, G)
+    vbar = np.where(g2 > 0, 4.0 * math.pi / np.where(g2 > 0, g2, 1.0), 0.0)
+    return P, vbar

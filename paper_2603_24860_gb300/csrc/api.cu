@@ -1,0 +1,672 @@
+// C ABI of the symmetry-reduced BSE block builder: context set-up, the
+// star-pair tiling of the fused build + projection, and the block spectrum.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace bse {
+const char* last_error();
+}
+
+using namespace bse;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+int ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.n >= bytes) return BSE_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BSE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    b.n = bytes;
+    return BSE_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+template <class T>
+int upload(DevBuf& b, const T* src, size_t count, cudaStream_t st) {
+    BSE_TRY(ensure(b, sizeof(T) * count));
+    if (count) BSE_CUDA(cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyDefault, st));
+    return BSE_OK;
+}
+
+struct IrrepDev {
+    bool ready = false;
+    Basis host;
+    DevBuf col_orbit, col_off, coef;
+};
+
+}  // namespace
+
+struct bse_ctx {
+    Tables t;
+    cudaStream_t stream = nullptr;
+    DevSys S{};
+    std::vector<int32_t> npw, ng, gk, gq;
+    DevBuf coef, eps, w, dgk, dgq, dnpw, dng, kidx, box, rk, tau, rotk, vbar;
+    DevBuf orbit_off, members, member_loc;
+    std::vector<IrrepDev> irr;
+    std::vector<int64_t> block_dim;
+    int ng0 = 0;
+    double w_div = 0.0;
+    double spin = 2.0;
+    DevBuf P;            // exchange vectors [N][ng0]
+    bool P_ready = false;
+    DevBuf B;            // dipoles [N]
+    bool B_ready = false;
+    // scratch (library-owned, grow-only)
+    DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum;
+    cusolverDnHandle_t solver = nullptr;
+};
+
+static DevBasis dev_basis(bse_ctx* c, int mu) {
+    IrrepDev& d = c->irr[mu];
+    DevBasis b;
+    b.dim = d.host.dim;
+    b.col_orbit = (const int*)d.col_orbit.p;
+    b.col_off = (const int64_t*)d.col_off.p;
+    b.coef = (const double2*)d.coef.p;
+    b.orbit_off = (const int64_t*)c->orbit_off.p;
+    b.members = (const int64_t*)c->members.p;
+    b.member_loc = (const int*)c->member_loc.p;
+    return b;
+}
+
+static int ensure_basis(bse_ctx* c, int mu) {
+    if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
+    IrrepDev& d = c->irr[mu];
+    if (d.ready) return BSE_OK;
+    BSE_TRY(build_basis(c->t, mu, d.host));
+    if (d.host.dim != c->block_dim[mu])
+        return fail(BSE_ESYMM, "irrep %d: orthonormal basis has %lld vectors but Tr P = %lld", mu,
+                    (long long)d.host.dim, (long long)c->block_dim[mu]);
+    BSE_TRY(upload(d.col_orbit, d.host.col_orbit.data(), d.host.col_orbit.size(), c->stream));
+    BSE_TRY(upload(d.col_off, d.host.col_off.data(), d.host.col_off.size(), c->stream));
+    BSE_TRY(upload(d.coef, reinterpret_cast<const double2*>(d.host.coef.data()), d.host.coef.size(), c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    d.ready = true;
+    return BSE_OK;
+}
+
+static int ensure_exchange_vectors(bse_ctx* c) {
+    if (c->P_ready) return BSE_OK;
+    const int nk = c->t.nk;
+    std::vector<int32_t> kk(nk);
+    for (int k = 0; k < nk; ++k) kk[k] = k;
+    BSE_TRY(upload(c->pairs, kk.data(), kk.size(), c->stream));
+    BSE_TRY(ensure(c->P, sizeof(double2) * (size_t)c->t.N * c->ng0));
+    BSE_TRY(launch_pairdens(c->S, (const int*)c->pairs.p, (const int*)c->pairs.p, nk, BSE_BANDS_CV, 1,
+                            (double2*)c->P.p, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    c->P_ready = true;
+    return BSE_OK;
+}
+
+static int ensure_dipoles(bse_ctx* c) {
+    if (c->B_ready) return BSE_OK;
+    BSE_TRY(ensure(c->B, sizeof(double2) * (size_t)c->t.N));
+    BSE_TRY(launch_dipoles(c->S, (double2*)c->B.p, c->stream));
+    c->B_ready = true;
+    return BSE_OK;
+}
+
+// H00 = (1/sqrt(4 pi)) int dOmega 1/(q^T L q): closed form when L is isotropic,
+// otherwise Gauss-Legendre in cos(theta) times a periodic trapezoid in phi.
+static double h00(const double* L) {
+    bool iso = true;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if ((i == j && L[3 * i + j] != L[0]) || (i != j && L[3 * i + j] != 0.0)) iso = false;
+    if (iso) return std::sqrt(4.0 * M_PI) / L[0];
+    const int nt = 96, np = 192;
+    std::vector<double> x(nt), wt(nt);
+    for (int i = 0; i < nt; ++i) {   // Newton iteration on P_nt
+        double z = std::cos(M_PI * (i + 0.75) / (nt + 0.5)), pp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= nt; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = nt * (z * p1 - p2) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+    double acc = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        double ct = x[i], st = std::sqrt(1.0 - ct * ct);
+        for (int j = 0; j < np; ++j) {
+            double ph = 2.0 * M_PI * j / np;
+            double n[3] = {st * std::cos(ph), st * std::sin(ph), ct};
+            double q = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) q += n[a] * L[3 * a + b] * n[b];
+            acc += wt[i] * (2.0 * M_PI / np) / q;
+        }
+    }
+    return acc / std::sqrt(4.0 * M_PI);
+}
+
+static int compute_wdiv(bse_ctx* c, const double* L) {
+    const double b = 0.005;
+    const double qmax = std::sqrt(-std::log(b) / b);
+    const double vbz = 8.0 * M_PI * M_PI * M_PI / c->t.v_uc;
+    const double delta = std::cbrt(vbz / c->t.nk);
+    int64_t np = wdiv_partials(c->t.lattice, c->t.n, qmax, delta);
+    BSE_TRY(ensure(c->wpart, sizeof(double) * (size_t)np));
+    BSE_TRY(ensure(c->wsum, sizeof(double)));
+    double rl[18];
+    std::memcpy(rl, c->t.recip, sizeof(double) * 9);
+    std::memcpy(rl + 9, c->t.lattice, sizeof(double) * 9);
+    BSE_TRY(launch_wdiv(rl, c->t.n, L, b, qmax, delta, (double*)c->wpart.p, np, (double*)c->wsum.p, c->stream));
+    double sum = 0.0;
+    BSE_CUDA(cudaMemcpyAsync(&sum, c->wsum.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    double integral = M_PI * h00(L) / std::sqrt(b) * std::erf(std::sqrt(b) * qmax);
+    c->w_div = integral / (2.0 * M_PI * M_PI) - 4.0 * M_PI / (c->t.nk * c->t.v_uc) * sum;
+    return BSE_OK;
+}
+
+static int create_impl(bse_ctx* c, const bse_system* sys) {
+    Tables& t = c->t;
+    if (sys->nv <= 0 || sys->nc <= 0) return fail(BSE_EINVAL, "nv and nc must be positive");
+    if (sys->npw_max <= 0 || sys->npw_max > 32767 || sys->ng_max <= 0)
+        return fail(BSE_EINVAL, "npw_max must be in 1..32767 and ng_max positive");
+    if (!sys->npw || !sys->gk || !sys->coef || !sys->eps || !sys->ng || !sys->gq || !sys->w)
+        return fail(BSE_EINVAL, "missing input array");
+    if (sys->spin_factor <= 0) return fail(BSE_EINVAL, "spin_factor must be positive");
+    t.nv = sys->nv;
+    t.nc = sys->nc;
+    t.nb = t.nv + t.nc;
+    t.B = t.nv * t.nc;
+    for (int i = 0; i < 3; ++i) t.n[i] = sys->mesh[i];
+    BSE_TRY(build_group(t, sys));
+    BSE_TRY(build_mesh(t));
+    t.N = (int64_t)t.nk * t.B;
+    c->spin = sys->spin_factor;
+    const int nk = t.nk, nb = t.nb;
+    c->npw.assign(sys->npw, sys->npw + nk);
+    c->ng.assign(sys->ng, sys->ng + nk);
+    c->gk.assign(sys->gk, sys->gk + (size_t)nk * sys->npw_max * 3);
+    c->gq.assign(sys->gq, sys->gq + (size_t)nk * sys->ng_max * 3);
+    for (int k = 0; k < nk; ++k) {
+        if (c->npw[k] <= 0 || c->npw[k] > sys->npw_max) return fail(BSE_EINVAL, "npw[%d] out of range", k);
+        if (c->ng[k] <= 0 || c->ng[k] > sys->ng_max) return fail(BSE_EINVAL, "ng[%d] out of range", k);
+    }
+    std::vector<double> eps_h((size_t)nk * nb);
+    BSE_CUDA(cudaMemcpy(eps_h.data(), sys->eps, sizeof(double) * eps_h.size(), cudaMemcpyDefault));
+    BSE_TRY(build_characters(t));
+    BSE_TRY(build_multiplets_and_orbits(t, eps_h.data()));
+    cudaStream_t st = c->stream;
+    // device copies of the inputs
+    BSE_TRY(upload(c->coef, reinterpret_cast<const double2*>(sys->coef), (size_t)nk * nb * sys->npw_max, st));
+    BSE_TRY(upload(c->eps, sys->eps, (size_t)nk * nb, st));
+    BSE_TRY(upload(c->w, reinterpret_cast<const double2*>(sys->w), (size_t)nk * sys->ng_max * sys->ng_max, st));
+    BSE_TRY(upload(c->dgk, c->gk.data(), c->gk.size(), st));
+    BSE_TRY(upload(c->dgq, c->gq.data(), c->gq.size(), st));
+    BSE_TRY(upload(c->dnpw, c->npw.data(), c->npw.size(), st));
+    BSE_TRY(upload(c->dng, c->ng.data(), c->ng.size(), st));
+    BSE_TRY(upload(c->kidx, t.kidx.data(), t.kidx.size(), st));
+    BSE_TRY(upload(c->rk, t.rk.data(), t.rk.size(), st));
+    BSE_TRY(upload(c->tau, t.tau.data(), t.tau.size(), st));
+    BSE_TRY(upload(c->rotk, t.rotk.data(), t.rotk.size(), st));
+    // look-up box of the coset spheres
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    for (int k = 0; k < nk; ++k)
+        for (int i = 0; i < c->npw[k]; ++i)
+            for (int a = 0; a < 3; ++a) {
+                int v = c->gk[((size_t)k * sys->npw_max + i) * 3 + a];
+                lo[a] = std::min(lo[a], v);
+                hi[a] = std::max(hi[a], v);
+            }
+    DevSys& S = c->S;
+    int64_t bvol = 1;
+    for (int a = 0; a < 3; ++a) {
+        S.blo[a] = lo[a];
+        S.bdim[a] = hi[a] - lo[a] + 1;
+        bvol *= S.bdim[a];
+    }
+    S.bvol = bvol;
+    std::vector<short> boxh((size_t)nk * bvol, (short)-1);
+    for (int k = 0; k < nk; ++k)
+        for (int i = 0; i < c->npw[k]; ++i) {
+            const int* m = &c->gk[((size_t)k * sys->npw_max + i) * 3];
+            int64_t pos = ((int64_t)(m[0] - lo[0]) * S.bdim[1] + (m[1] - lo[1])) * S.bdim[2] + (m[2] - lo[2]);
+            short& slot = boxh[(size_t)k * bvol + pos];
+            if (slot != -1) return fail(BSE_EINVAL, "plane wave repeated in the sphere of k=%d", k);
+            slot = (short)i;
+        }
+    BSE_TRY(upload(c->box, boxh.data(), boxh.size(), st));
+    // G = 0 in the sphere of q = 0 and the exchange Coulomb factors
+    c->ng0 = c->ng[0];
+    c->S.g0 = -1;
+    std::vector<double> vb(c->ng0);
+    for (int g = 0; g < c->ng0; ++g) {
+        const int* m = &c->gq[(size_t)g * 3];
+        if (m[0] == 0 && m[1] == 0 && m[2] == 0) c->S.g0 = g;
+        double G[3];
+        for (int a = 0; a < 3; ++a) G[a] = t.recip[3 * a] * m[0] + t.recip[3 * a + 1] * m[1] + t.recip[3 * a + 2] * m[2];
+        double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        vb[g] = g2 > 0 ? 4.0 * M_PI / g2 : 0.0;
+    }
+    if (c->S.g0 < 0) return fail(BSE_EINVAL, "the sphere of q = 0 lacks G = 0");
+    BSE_TRY(upload(c->vbar, vb.data(), vb.size(), st));
+    S.coef = (const double2*)c->coef.p;
+    S.eps = (const double*)c->eps.p;
+    S.w = (const double2*)c->w.p;
+    S.gk = (const int*)c->dgk.p;
+    S.gq = (const int*)c->dgq.p;
+    S.npw = (const int*)c->dnpw.p;
+    S.ng = (const int*)c->dng.p;
+    S.kidx = (const int*)c->kidx.p;
+    S.box = (const short*)c->box.p;
+    S.n1 = t.n[0];
+    S.n2 = t.n[1];
+    S.n3 = t.n[2];
+    S.nk = nk;
+    S.nv = t.nv;
+    S.nc = t.nc;
+    S.nb = nb;
+    S.npw_max = sys->npw_max;
+    S.ng_max = sys->ng_max;
+    S.inv_vol = 1.0 / (nk * t.v_uc);
+    std::memcpy(S.recip, t.recip, sizeof(S.recip));
+    double qn = std::sqrt(sys->qhat[0] * sys->qhat[0] + sys->qhat[1] * sys->qhat[1] + sys->qhat[2] * sys->qhat[2]);
+    if (!(qn > 0)) return fail(BSE_EINVAL, "qhat must be nonzero");
+    for (int a = 0; a < 3; ++a) S.qhat[a] = sys->qhat[a] / qn;
+    S.v_uc = t.v_uc;
+    S.scissor = sys->scissor;
+    // band rotations Gamma(s) on the device
+    std::vector<int32_t> ent;
+    ent.reserve((size_t)t.gam_per_s * 3);
+    for (int k = 0; k < nk; ++k) {
+        for (auto* ms : {&t.vmult[k], &t.cmult[k]})
+            for (auto& m : *ms)
+                for (int a = 0; a < m.second; ++a)
+                    for (int b = 0; b < m.second; ++b) {
+                        ent.push_back(k);
+                        ent.push_back(m.first + a);
+                        ent.push_back(m.first + b);
+                    }
+    }
+    DevBuf perm, phase, dent, dgam;
+    int rc = BSE_OK;
+    do {
+        size_t nmap = (size_t)t.nops * nk * sys->npw_max;
+        if ((rc = ensure(perm, sizeof(int) * nmap)) != BSE_OK) break;
+        if ((rc = ensure(phase, sizeof(double2) * nmap)) != BSE_OK) break;
+        if ((rc = upload(dent, ent.data(), ent.size(), st)) != BSE_OK) break;
+        if ((rc = ensure(dgam, sizeof(double2) * (size_t)t.nops * t.gam_per_s)) != BSE_OK) break;
+        if ((rc = launch_rotmap(S, (const int*)c->rk.p, (const double*)c->tau.p, (const int*)c->rotk.p, t.nops,
+                                (int*)perm.p, (double2*)phase.p, st)) != BSE_OK)
+            break;
+        if ((rc = launch_gamma(S, t.nops, (const int*)c->rotk.p, (const int*)perm.p, (const double2*)phase.p,
+                               (const int*)dent.p, t.gam_per_s, (double2*)dgam.p, st)) != BSE_OK)
+            break;
+        t.gamma.resize((size_t)t.nops * t.gam_per_s);
+        cudaError_t e = cudaMemcpyAsync(t.gamma.data(), dgam.p, sizeof(double2) * t.gamma.size(),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(BSE_ECUDA, "band rotations: %s", cudaGetErrorString(e));
+    } while (0);
+    release(perm);
+    release(phase);
+    release(dent);
+    release(dgam);
+    BSE_TRY(rc);
+    BSE_TRY(check_band_rotations(t));
+    // block dimensions from the trace formula dim_mu = d_mu/|S| sum_s chi_mu(s) Tr Gamma~(s)
+    std::vector<cplx> trace(t.nops, 0.0);
+    for (int s = 0; s < t.nops; ++s)
+        for (int k = 0; k < nk; ++k) {
+            if (t.rotk[(size_t)s * nk + k] != k) continue;
+            cplx tv = 0, tc = 0;
+            int64_t off = (int64_t)s * t.gam_per_s + t.gam_koff[k];
+            for (auto& m : t.vmult[k]) {
+                for (int a = 0; a < m.second; ++a) tv += t.gamma[off + a * m.second + a];
+                off += (int64_t)m.second * m.second;
+            }
+            for (auto& m : t.cmult[k]) {
+                for (int a = 0; a < m.second; ++a) tc += t.gamma[off + a * m.second + a];
+                off += (int64_t)m.second * m.second;
+            }
+            trace[s] += tc * std::conj(tv);
+        }
+    c->block_dim.assign(t.n_irreps, 0);
+    int64_t tot = 0;
+    for (int mu = 0; mu < t.n_irreps; ++mu) {
+        cplx a = 0;
+        for (int s = 0; s < t.nops; ++s) a += (double)t.chi[(size_t)mu * t.nops + s] * trace[s];
+        double d = a.real() * t.irrep_dim[mu] / t.nops;
+        long r = std::lround(d);
+        if (std::fabs(d - r) > 1e-6 || std::fabs(a.imag()) > 1e-6)
+            return fail(BSE_ESYMM, "Tr P_%d = %.9f is not an integer", mu, d);
+        c->block_dim[mu] = r;
+        tot += r;
+    }
+    if (tot != t.N) return fail(BSE_ESYMM, "block dimensions sum to %lld, not N = %lld", (long long)tot, (long long)t.N);
+    // orbit tables on the device
+    std::vector<int> loc(t.orbit_members.size());
+    for (size_t i = 0; i < loc.size(); ++i) {
+        int64_t I = t.orbit_members[i];
+        int k = (int)(I / t.B);
+        loc[i] = t.pos_in_star[k] * t.B + (int)(I % t.B);
+    }
+    BSE_TRY(upload(c->orbit_off, t.orbit_off.data(), t.orbit_off.size(), st));
+    BSE_TRY(upload(c->members, t.orbit_members.data(), t.orbit_members.size(), st));
+    BSE_TRY(upload(c->member_loc, loc.data(), loc.size(), st));
+    c->irr.resize(t.n_irreps);
+    if (std::isnan(sys->w_div)) {
+        BSE_TRY(compute_wdiv(c, sys->eps_inf));
+    } else {
+        c->w_div = sys->w_div;
+    }
+    BSE_CUDA(cudaStreamSynchronize(st));
+    return BSE_OK;
+}
+
+static void free_ctx(bse_ctx* c) {
+    for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
+                      &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
+                      &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum})
+        release(*b);
+    for (auto& d : c->irr) {
+        release(d.col_orbit);
+        release(d.col_off);
+        release(d.coef);
+    }
+    if (c->solver) cusolverDnDestroy(c->solver);
+    delete c;
+}
+
+extern "C" {
+
+const char* bse_last_error(void) { return bse::last_error(); }
+
+int bse_create(bse_ctx** out, const bse_system* sys, void* stream) {
+    clear_error();
+    if (!out || !sys) return fail(BSE_EINVAL, "null argument");
+    *out = nullptr;
+    bse_ctx* c = new (std::nothrow) bse_ctx();
+    if (!c) return fail(BSE_ENOMEM, "out of host memory");
+    c->stream = (cudaStream_t)stream;
+    int r = create_impl(c, sys);
+    if (r != BSE_OK) {
+        cudaStreamSynchronize(c->stream);
+        free_ctx(c);
+        return r;
+    }
+    *out = c;
+    return BSE_OK;
+}
+
+int bse_destroy(bse_ctx* ctx) {
+    if (!ctx) return BSE_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return BSE_OK;
+}
+
+int bse_tables(const bse_ctx* c, bse_tables_view* v) {
+    clear_error();
+    if (!c || !v) return fail(BSE_EINVAL, "null argument");
+    const Tables& t = c->t;
+    v->n_ops = t.nops;
+    v->nk = t.nk;
+    v->n_stars = (int32_t)t.star_rep.size();
+    v->n_irreps = t.n_irreps;
+    v->n_orbits = (int32_t)t.orbit_star.size();
+    v->n_product = t.N;
+    v->rotk = t.rotk.data();
+    v->star_of_k = t.star_of.data();
+    v->star_rep = t.star_rep.data();
+    v->s_k = t.s_k.data();
+    v->class_of_op = t.class_of.data();
+    v->chi = t.chi.data();
+    v->irrep_dim = t.irrep_dim.data();
+    v->bright = t.bright.data();
+    v->block_dim = c->block_dim.data();
+    v->orbit_of = t.orbit_of.data();
+    v->w_div = c->w_div;
+    return BSE_OK;
+}
+
+int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs, int32_t bands, void* out) {
+    clear_error();
+    if (!c || (npairs > 0 && (!k || !kp || !out))) return fail(BSE_EINVAL, "null argument");
+    if (bands < 0 || bands > 2) return fail(BSE_EINVAL, "bands must be CC, VV or CV");
+    if (npairs < 0 || npairs > (1ll << 31) - 1) return fail(BSE_EINVAL, "npairs out of range");
+    if (npairs == 0) return BSE_OK;
+    std::vector<int32_t> both((size_t)2 * npairs);
+    for (int64_t i = 0; i < npairs; ++i) {
+        if (k[i] < 0 || k[i] >= c->t.nk || kp[i] < 0 || kp[i] >= c->t.nk)
+            return fail(BSE_EINVAL, "k index out of range at pair %lld", (long long)i);
+        both[i] = k[i];
+        both[npairs + i] = kp[i];
+    }
+    BSE_TRY(upload(c->pairs, both.data(), both.size(), c->stream));
+    const int* d = (const int*)c->pairs.p;
+    return launch_pairdens(c->S, d, d + npairs, npairs, bands, 0, (double2*)out, c->stream);
+}
+
+int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
+    clear_error();
+    if (!c || !h) return fail(BSE_EINVAL, "null argument");
+    const Tables& t = c->t;
+    if (ld < t.N || ld > (1ll << 31) - 1) return fail(BSE_EINVAL, "ld must be in [N, 2^31)");
+    std::vector<PairTask> tasks;
+    tasks.reserve((size_t)t.nk * (t.nk + 1) / 2);
+    for (int k = 0; k < t.nk; ++k)
+        for (int kp = k; kp < t.nk; ++kp) {
+            PairTask p;
+            p.k = k;
+            p.kp = kp;
+            p.row0 = k * t.B;
+            p.col0 = kp * t.B;
+            p.xoff = 0;
+            p.ld = (int32_t)ld;
+            p.flags = kp > k ? 1 : 0;
+            tasks.push_back(p);
+        }
+    BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
+    BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), (double2*)h, terms, c->w_div,
+                          c->stream));
+    if (terms & BSE_TERM_EXCHANGE) {
+        BSE_TRY(ensure_exchange_vectors(c));
+        BSE_TRY(launch_exchange_full((const double2*)c->P.p, (const double*)c->vbar.p, c->ng0, t.N,
+                                     c->spin * c->S.inv_vol, (double2*)h, ld, c->stream));
+    }
+    return BSE_OK;
+}
+
+int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
+    clear_error();
+    if (!c || !h) return fail(BSE_EINVAL, "null argument");
+    if (prec != BSE_FP64) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    BSE_TRY(ensure_basis(c, mu));
+    const Tables& t = c->t;
+    const Basis& bh = c->irr[mu].host;
+    const int64_t dim = bh.dim;
+    if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
+    if (dim == 0) return BSE_OK;
+    DevBasis db = dev_basis(c, mu);
+    const double2* Pmu = nullptr;
+    if (terms & BSE_TERM_EXCHANGE) {
+        BSE_TRY(ensure_exchange_vectors(c));
+        BSE_TRY(ensure(c->Pmu, sizeof(double2) * (size_t)dim * c->ng0));
+        BSE_TRY(launch_exchange_project(db, (const double2*)c->P.p, c->ng0, (double2*)c->Pmu.p, c->stream));
+        Pmu = (const double2*)c->Pmu.p;
+    }
+    // star pairs (a <= b) whose stars carry basis vectors of this irrep
+    std::vector<int> act;
+    for (size_t a = 0; a < t.stars.size(); ++a)
+        if (bh.star_col[a + 1] > bh.star_col[a]) act.push_back((int)a);
+    const char* env = std::getenv("BSE_ARENA_MB");
+    const size_t budget = (size_t)(env ? std::atoll(env) : 2048) << 20;
+    const int B = t.B;
+    size_t iA = 0, iB = 0;
+    while (iA < act.size()) {
+        std::vector<TileTask> tiles;
+        std::vector<PairTask> tasks;
+        size_t xo = 0, yo = 0;
+        int64_t max_rows = 0, max_ca = 0, max_cb = 0;
+        while (iA < act.size()) {
+            int a = act[iA], b = act[iB];
+            int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
+            int64_t mb = bh.star_col[b + 1] - bh.star_col[b];
+            size_t xs = sizeof(double2) * rows * cols, ys = sizeof(double2) * rows * mb;
+            if (!tiles.empty() && (xo + xs > budget || yo + ys > budget)) break;
+            TileTask tt;
+            tt.xoff = (int64_t)(xo / sizeof(double2));
+            tt.yoff = (int64_t)(yo / sizeof(double2));
+            tt.rows = (int32_t)rows;
+            tt.cols = (int32_t)cols;
+            tt.star_a = a;
+            tt.star_b = b;
+            tt.ca0 = bh.star_col[a];
+            tt.ca1 = bh.star_col[a + 1];
+            tt.cb0 = bh.star_col[b];
+            tt.cb1 = bh.star_col[b + 1];
+            tiles.push_back(tt);
+            const auto& sa = t.stars[a];
+            const auto& sb = t.stars[b];
+            for (size_t i = 0; i < sa.size(); ++i)
+                for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
+                    PairTask p;
+                    p.k = sa[i];
+                    p.kp = sb[j];
+                    p.row0 = (int32_t)(i * B);
+                    p.col0 = (int32_t)(j * B);
+                    p.xoff = tt.xoff;
+                    p.ld = (int32_t)rows;
+                    p.flags = (a == b && j > i) ? 1 : 0;
+                    tasks.push_back(p);
+                }
+            xo += xs;
+            yo += ys;
+            max_rows = std::max(max_rows, rows);
+            max_ca = std::max(max_ca, tt.ca1 - tt.ca0);
+            max_cb = std::max(max_cb, mb);
+            if (++iB == act.size()) {
+                ++iA;
+                iB = iA;
+            }
+        }
+        BSE_TRY(ensure(c->arenaX, xo));
+        BSE_TRY(ensure(c->arenaY, yo));
+        BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
+        BSE_TRY(upload(c->tiles, tiles.data(), tiles.size(), c->stream));
+        BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), (double2*)c->arenaX.p, terms,
+                              c->w_div, c->stream));
+        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)tiles.size(), nullptr,
+                                     (const double2*)c->arenaX.p, (double2*)c->arenaY.p, max_rows, max_cb,
+                                     c->stream));
+        BSE_TRY(launch_project_left(db, (const TileTask*)c->tiles.p, (int)tiles.size(), (const double2*)c->arenaY.p,
+                                    Pmu, (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol, (double2*)h, ld,
+                                    max_ca, max_cb, c->stream));
+        // the next batch reuses the task buffers; host vectors go out of scope
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return BSE_OK;
+}
+
+int bse_block_basis(bse_ctx* c, int32_t mu, void* u, int64_t ld) {
+    clear_error();
+    if (!c || !u) return fail(BSE_EINVAL, "null argument");
+    BSE_TRY(ensure_basis(c, mu));
+    if (ld < c->t.N) return fail(BSE_EINVAL, "ld < N");
+    const int64_t dim = c->irr[mu].host.dim;
+    if (dim == 0) return BSE_OK;
+    BSE_CUDA(cudaMemsetAsync(u, 0, sizeof(double2) * (size_t)ld * dim, c->stream));
+    return launch_basis_dense(dev_basis(c, mu), (double2*)u, ld, c->stream);
+}
+
+int bse_dipoles(bse_ctx* c, void* b) {
+    clear_error();
+    if (!c || !b) return fail(BSE_EINVAL, "null argument");
+    return launch_dipoles(c->S, (double2*)b, c->stream);
+}
+
+int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
+                       double eta, double* omega_out, double* osc, double* im_eps) {
+    clear_error();
+    if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
+    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
+    BSE_TRY(ensure_basis(c, mu));
+    const int64_t dim = c->irr[mu].host.dim;
+    if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
+    if (dim == 0) {
+        if (n_omega) BSE_CUDA(cudaMemsetAsync(im_eps, 0, sizeof(double) * n_omega, c->stream));
+        return BSE_OK;
+    }
+    if (dim > (1ll << 31) - 1) return fail(BSE_EUNSUPPORTED, "block too large for the eigensolver");
+    BSE_TRY(ensure_dipoles(c));
+    BSE_TRY(ensure(c->Bmu, sizeof(double2) * (size_t)dim));
+    DevBasis db = dev_basis(c, mu);
+    BSE_TRY(launch_bmu(db, (const double2*)c->B.p, (double2*)c->Bmu.p, c->stream));
+    BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
+    BSE_CUDA(cudaMemcpy2DAsync(c->eigA.p, sizeof(double2) * dim, h, sizeof(double2) * ld, sizeof(double2) * dim, dim,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    if (!c->solver) {
+        if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS) return fail(BSE_ESOLVER, "cusolverDnCreate failed");
+    }
+    if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "cusolverDnSetStream failed");
+    int lwork = 0;
+    if (cusolverDnZheevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)dim,
+                                    (const cuDoubleComplex*)c->eigA.p, (int)dim, omega_out,
+                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "zheevd buffer size query failed");
+    BSE_TRY(ensure(c->eigWork, sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1)));
+    BSE_TRY(ensure(c->info, sizeof(int)));
+    if (cusolverDnZheevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)dim,
+                         (cuDoubleComplex*)c->eigA.p, (int)dim, omega_out, (cuDoubleComplex*)c->eigWork.p, lwork,
+                         (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "zheevd launch failed");
+    BSE_TRY(launch_oscillators((const double2*)c->eigA.p, dim, dim, (const double2*)c->Bmu.p, osc, c->stream));
+    BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, 4.0 * M_PI * c->spin / c->t.nk, im_eps,
+                            c->stream));
+    int info = 0;
+    BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    if (info != 0) return fail(BSE_ESOLVER, "zheevd info = %d", info);
+    return BSE_OK;
+}
+
+int bse_sync(bse_ctx* c) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null argument");
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,554 @@
+// Host-side symmetry tables (Sec. III.C of Stöhler, Blügel, Friedrich):
+// the point group S/S_T of the space group, the k mesh and its stars, the
+// character table (computed, not typed), multiplets, orbits of the product
+// basis and the canonical orthonormal basis of each irrep subspace.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "internal.h"
+
+namespace bse {
+
+static thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+void clear_error() { g_err.clear(); }
+const char* last_error() { return g_err.c_str(); }
+
+static void inv3(const double* a, double* out) {
+    double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                 a[2] * (a[3] * a[7] - a[4] * a[6]);
+    out[0] = (a[4] * a[8] - a[5] * a[7]) / det;
+    out[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+    out[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+    out[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+    out[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+    out[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+    out[6] = (a[3] * a[7] - a[4] * a[6]) / det;
+    out[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+    out[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+}
+
+// exact inverse of a unimodular integer matrix; returns false otherwise
+static bool inv_unimodular(const int32_t* r, int32_t* out) {
+    long det = (long)r[0] * (r[4] * r[8] - r[5] * r[7]) - (long)r[1] * (r[3] * r[8] - r[5] * r[6]) +
+               (long)r[2] * (r[3] * r[7] - r[4] * r[6]);
+    if (det != 1 && det != -1) return false;
+    int32_t adj[9] = {r[4] * r[8] - r[5] * r[7], r[2] * r[7] - r[1] * r[8], r[1] * r[5] - r[2] * r[4],
+                      r[5] * r[6] - r[3] * r[8], r[0] * r[8] - r[2] * r[6], r[2] * r[3] - r[0] * r[5],
+                      r[3] * r[7] - r[4] * r[6], r[1] * r[6] - r[0] * r[7], r[0] * r[4] - r[1] * r[3]};
+    for (int i = 0; i < 9; ++i) out[i] = adj[i] * (int32_t)det;
+    return true;
+}
+
+int build_group(Tables& t, const bse_system* sys) {
+    t.nops = sys->n_ops;
+    if (t.nops <= 0 || t.nops > 48 || !sys->rot || !sys->tau)
+        return fail(BSE_EINVAL, "n_ops must be in 1..48 with rot and tau given");
+    std::memcpy(t.lattice, sys->lattice, sizeof(t.lattice));
+    double linv[9];
+    inv3(t.lattice, linv);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t.recip[i * 3 + j] = 2.0 * M_PI * linv[j * 3 + i];
+    const double* L = t.lattice;
+    t.v_uc = std::fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                       L[2] * (L[3] * L[7] - L[4] * L[6]));
+    t.rot.assign(sys->rot, sys->rot + 9 * t.nops);
+    t.tau.assign(sys->tau, sys->tau + 3 * t.nops);
+    t.rk.resize(9 * t.nops);
+    t.cart.resize(9 * t.nops);
+    for (int s = 0; s < t.nops; ++s) {
+        int32_t inv[9];
+        if (!inv_unimodular(&t.rot[9 * s], inv))
+            return fail(BSE_EINVAL, "operation %d is not unimodular", s);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) t.rk[9 * s + 3 * i + j] = inv[3 * j + i];
+        // A = L R L^{-1}
+        double lr[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double a = 0;
+                for (int l = 0; l < 3; ++l) a += L[3 * i + l] * t.rot[9 * s + 3 * l + j];
+                lr[3 * i + j] = a;
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double a = 0;
+                for (int l = 0; l < 3; ++l) a += lr[3 * i + l] * linv[3 * l + j];
+                t.cart[9 * s + 3 * i + j] = a;
+            }
+        for (int i = 0; i < 3; ++i) {
+            double o = 0;
+            for (int j = 0; j < 3; ++j) o += t.cart[9 * s + 3 * i + j] * t.cart[9 * s + 3 * i + j];
+            if (std::fabs(o - 1.0) > 1e-9)
+                return fail(BSE_ESYMM, "operation %d is not orthogonal in Cartesian space", s);
+        }
+    }
+    std::map<std::vector<int32_t>, int> key;
+    for (int s = 0; s < t.nops; ++s) {
+        std::vector<int32_t> v(t.rot.begin() + 9 * s, t.rot.begin() + 9 * s + 9);
+        if (!key.emplace(v, s).second) return fail(BSE_ESYMM, "operation %d repeats a rotation", s);
+    }
+    t.mult.assign((size_t)t.nops * t.nops, -1);
+    for (int a = 0; a < t.nops; ++a)
+        for (int b = 0; b < t.nops; ++b) {
+            std::vector<int32_t> p(9);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    int32_t v = 0;
+                    for (int l = 0; l < 3; ++l) v += t.rot[9 * a + 3 * i + l] * t.rot[9 * b + 3 * l + j];
+                    p[3 * i + j] = v;
+                }
+            auto it = key.find(p);
+            if (it == key.end()) return fail(BSE_ESYMM, "operations do not close (%d*%d)", a, b);
+            int c = it->second;
+            t.mult[(size_t)a * t.nops + b] = c;
+            for (int i = 0; i < 3; ++i) {
+                double d = t.tau[3 * a + i] - t.tau[3 * c + i];
+                for (int j = 0; j < 3; ++j) d += t.rot[9 * a + 3 * i + j] * t.tau[3 * b + j];
+                if (std::fabs(d - std::nearbyint(d)) > 1e-9)
+                    return fail(BSE_ESYMM, "translations of %d*%d do not compose", a, b);
+            }
+        }
+    std::vector<int32_t> e = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    auto it = key.find(e);
+    if (it == key.end()) return fail(BSE_ESYMM, "identity operation missing");
+    t.identity = it->second;
+    return BSE_OK;
+}
+
+int build_mesh(Tables& t) {
+    int n1 = t.n[0], n2 = t.n[1], n3 = t.n[2];
+    if (n1 <= 0 || n2 <= 0 || n3 <= 0) return fail(BSE_EINVAL, "mesh dimensions must be positive");
+    t.nk = n1 * n2 * n3;
+    t.kidx.resize(3 * t.nk);
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j)
+            for (int l = 0; l < n3; ++l) {
+                int k = (i * n2 + j) * n3 + l;
+                t.kidx[3 * k] = i;
+                t.kidx[3 * k + 1] = j;
+                t.kidx[3 * k + 2] = l;
+            }
+    long Nl = std::lcm(std::lcm((long)n1, (long)n2), (long)n3);
+    long step[3] = {Nl / n1, Nl / n2, Nl / n3};
+    t.rotk.assign((size_t)t.nops * t.nk, -1);
+    for (int s = 0; s < t.nops; ++s)
+        for (int k = 0; k < t.nk; ++k) {
+            long X[3], Y[3];
+            for (int i = 0; i < 3; ++i) X[i] = t.kidx[3 * k + i] * step[i];
+            int id[3];
+            for (int i = 0; i < 3; ++i) {
+                Y[i] = 0;
+                for (int j = 0; j < 3; ++j) Y[i] += (long)t.rk[9 * s + 3 * i + j] * X[j];
+                if (Y[i] % step[i] != 0) return fail(BSE_EINVAL, "mesh not invariant under operation %d", s);
+                long v = Y[i] / step[i];
+                id[i] = (int)(((v % t.n[i]) + t.n[i]) % t.n[i]);
+            }
+            t.rotk[(size_t)s * t.nk + k] = (id[0] * n2 + id[1]) * n3 + id[2];
+        }
+    t.star_of.assign(t.nk, -1);
+    t.star_rep.clear();
+    t.stars.clear();
+    for (int k = 0; k < t.nk; ++k) {
+        if (t.star_of[k] >= 0) continue;
+        int a = (int)t.star_rep.size();
+        t.star_rep.push_back(k);
+        std::vector<int32_t> mem;
+        for (int s = 0; s < t.nops; ++s) {
+            int k2 = t.rotk[(size_t)s * t.nk + k];
+            if (t.star_of[k2] < 0) {
+                t.star_of[k2] = a;
+                mem.push_back(k2);
+            }
+        }
+        std::sort(mem.begin(), mem.end());
+        t.stars.push_back(mem);
+    }
+    t.s_k.assign(t.nk, -1);
+    t.pos_in_star.assign(t.nk, -1);
+    for (size_t a = 0; a < t.stars.size(); ++a) {
+        int p = t.star_rep[a];
+        for (size_t i = 0; i < t.stars[a].size(); ++i) t.pos_in_star[t.stars[a][i]] = (int)i;
+        for (int s = t.nops - 1; s >= 0; --s) t.s_k[t.rotk[(size_t)s * t.nk + p]] = s;
+    }
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// characters by the Burnside-Dixon method
+// ---------------------------------------------------------------------------
+
+// cyclic Jacobi eigensolver of a real symmetric n x n matrix (row-major).
+static void jacobi(std::vector<double>& a, int n, std::vector<double>& v, std::vector<double>& w) {
+    v.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0;
+    double nrm = 0;
+    for (double x : a) nrm += x * x;
+    nrm = std::sqrt(nrm);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a[(size_t)p * n + q] * a[(size_t)p * n + q];
+        if (std::sqrt(off) <= 1e-15 * nrm) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = a[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double tt = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(tt * tt + 1.0), s = tt * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = c * akp - s * akq;
+                    a[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = c * apk - s * aqk;
+                    a[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+                    v[(size_t)k * n + p] = c * vkp - s * vkq;
+                    v[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = a[(size_t)i * n + i];
+}
+
+int build_characters(Tables& t) {
+    const int G = t.nops;
+    std::vector<int32_t> inv(G);
+    for (int a = 0; a < G; ++a)
+        for (int b = 0; b < G; ++b)
+            if (t.mult[(size_t)a * G + b] == t.identity) inv[a] = b;
+    t.class_of.assign(G, -1);
+    std::vector<int> rep;
+    for (int g = 0; g < G; ++g) {
+        if (t.class_of[g] >= 0) continue;
+        int c = (int)rep.size();
+        rep.push_back(g);
+        for (int h = 0; h < G; ++h) {
+            int x = t.mult[(size_t)t.mult[(size_t)h * G + g] * G + inv[h]];
+            t.class_of[x] = c;
+        }
+    }
+    const int r = (int)rep.size();
+    std::vector<double> size(r, 0.0);
+    for (int g = 0; g < G; ++g) size[t.class_of[g]] += 1.0;
+    for (int g = 0; g < G; ++g)
+        if (t.class_of[inv[g]] != t.class_of[g])
+            return fail(BSE_EUNSUPPORTED, "group is not ambivalent (complex characters)");
+    // c[i][j][k] = #{x in C_i, y in C_j: x y = z} for a fixed z in C_k
+    std::vector<double> c((size_t)r * r * r, 0.0);
+    for (int x = 0; x < G; ++x)
+        for (int y = 0; y < G; ++y)
+            c[((size_t)t.class_of[x] * r + t.class_of[y]) * r + t.class_of[t.mult[(size_t)x * G + y]]] += 1.0;
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j)
+            for (int k = 0; k < r; ++k) c[((size_t)i * r + j) * r + k] /= size[k];
+    const int e = t.class_of[t.identity];
+    uint64_t state = 0x9E3779B97F4A7C15ull;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        // random combination A = sum_i x_i A_i, (A_i)_{jk} = c_ijk; A D is symmetric for
+        // ambivalent groups, so S = D^{-1/2} A D^{1/2} is symmetric with eigenvectors D^{-1/2} w.
+        std::vector<double> x(r);
+        for (int i = 0; i < r; ++i) {
+            state = state * 6364136223846793005ull + 1442695040888963407ull;
+            x[i] = (double)(state >> 11) / 9007199254740992.0 - 0.5;
+        }
+        std::vector<double> S((size_t)r * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int k = 0; k < r; ++k) {
+                double a = 0;
+                for (int i = 0; i < r; ++i) a += x[i] * c[((size_t)i * r + j) * r + k];
+                S[(size_t)j * r + k] = a * std::sqrt(size[k] / size[j]);
+            }
+        for (int j = 0; j < r; ++j)
+            for (int k = j + 1; k < r; ++k)
+                if (std::fabs(S[(size_t)j * r + k] - S[(size_t)k * r + j]) > 1e-10)
+                    return fail(BSE_EUNSUPPORTED, "class algebra is not symmetric");
+        std::vector<double> V, W;
+        jacobi(S, r, V, W);
+        std::vector<double> sw = W;
+        std::sort(sw.begin(), sw.end());
+        bool sep = true;
+        for (int i = 1; i < r; ++i)
+            if (sw[i] - sw[i - 1] < 1e-7) sep = false;
+        if (!sep) continue;
+        struct Irr { int d; std::vector<int32_t> chi; };
+        std::vector<Irr> irr;
+        bool ok = true;
+        for (int m = 0; m < r && ok; ++m) {
+            std::vector<double> w(r);
+            for (int j = 0; j < r; ++j) w[j] = V[(size_t)j * r + m] * std::sqrt(size[j]);
+            double we = w[e];
+            for (int j = 0; j < r; ++j) w[j] /= we;
+            double s2 = 0;
+            for (int j = 0; j < r; ++j) s2 += w[j] * w[j] / size[j];
+            double d = std::sqrt(G / s2);
+            Irr ir;
+            ir.d = (int)std::lround(d);
+            if (std::fabs(d - ir.d) > 1e-6) ok = false;
+            ir.chi.resize(G);
+            for (int g = 0; g < G; ++g) {
+                double ch = d * w[t.class_of[g]] / size[t.class_of[g]];
+                long rc = std::lround(ch);
+                if (std::fabs(ch - rc) > 1e-6) ok = false;
+                ir.chi[g] = (int32_t)rc;
+            }
+            irr.push_back(ir);
+        }
+        if (!ok) return fail(BSE_EUNSUPPORTED, "characters are not integers");
+        std::sort(irr.begin(), irr.end(), [](const Irr& a, const Irr& b) {
+            if (a.d != b.d) return a.d < b.d;
+            return a.chi < b.chi;
+        });
+        t.n_irreps = r;
+        t.chi.clear();
+        t.irrep_dim.clear();
+        for (auto& ir : irr) {
+            t.irrep_dim.push_back(ir.d);
+            t.chi.insert(t.chi.end(), ir.chi.begin(), ir.chi.end());
+        }
+        // first orthogonality check and multiplicity in the polar-vector rep
+        long sd2 = 0;
+        for (int m = 0; m < r; ++m) sd2 += (long)t.irrep_dim[m] * t.irrep_dim[m];
+        if (sd2 != G) return fail(BSE_ESYMM, "sum of squared irrep dimensions != |S|");
+        t.bright.assign(r, 0);
+        for (int m = 0; m < r; ++m) {
+            double acc = 0;
+            for (int g = 0; g < G; ++g) {
+                double tr = t.cart[9 * g] + t.cart[9 * g + 4] + t.cart[9 * g + 8];
+                acc += t.chi[(size_t)m * G + g] * tr;
+            }
+            t.bright[m] = (int32_t)std::lround(acc / G);
+        }
+        return BSE_OK;
+    }
+    return fail(BSE_EUNSUPPORTED, "could not separate the irreps");
+}
+
+// ---------------------------------------------------------------------------
+// multiplets and orbits
+// ---------------------------------------------------------------------------
+static const double kDegTol = 1e-9;
+
+static void runs(const double* e, int lo, int hi, std::vector<std::pair<int, int>>& out) {
+    out.clear();
+    int start = lo, last = lo;
+    for (int b = lo + 1; b < hi; ++b) {
+        if (std::fabs(e[b] - e[last]) <= kDegTol) {
+            last = b;
+        } else {
+            out.emplace_back(start, last - start + 1);
+            start = last = b;
+        }
+    }
+    out.emplace_back(start, last - start + 1);
+}
+
+int build_multiplets_and_orbits(Tables& t, const double* eps) {
+    const int nv = t.nv, nc = t.nc, nb = t.nb;
+    t.vmult.resize(t.nk);
+    t.cmult.resize(t.nk);
+    t.band_mult.assign((size_t)t.nk * nb, -1);
+    for (int k = 0; k < t.nk; ++k) {
+        runs(eps + (size_t)k * nb, 0, nv, t.vmult[k]);
+        runs(eps + (size_t)k * nb, nv, nb, t.cmult[k]);
+        int id = 0;
+        for (auto& m : t.vmult[k]) {
+            for (int b = m.first; b < m.first + m.second; ++b) t.band_mult[(size_t)k * nb + b] = id;
+            ++id;
+        }
+        for (auto& m : t.cmult[k]) {
+            for (int b = m.first; b < m.first + m.second; ++b) t.band_mult[(size_t)k * nb + b] = id;
+            ++id;
+        }
+    }
+    // energies must be equal across a star (bands map within their multiplet)
+    for (int k = 0; k < t.nk; ++k) {
+        int p = t.star_rep[t.star_of[k]];
+        for (int b = 0; b < nb; ++b)
+            if (std::fabs(eps[(size_t)k * nb + b] - eps[(size_t)p * nb + b]) > kDegTol)
+                return fail(BSE_ESYMM, "band energies differ within the star of k=%d", k);
+    }
+    const int64_t N = t.N;
+    t.orbit_of.assign(N, -1);
+    t.orbit_off.assign(1, 0);
+    t.orbit_members.clear();
+    t.orbit_star.clear();
+    t.orbit_vlo.clear(); t.orbit_vn.clear(); t.orbit_clo.clear(); t.orbit_cn.clear();
+    // visiting k in ascending order creates orbits in ascending order of their lowest member
+    for (int k = 0; k < t.nk; ++k) {
+        if (t.star_rep[t.star_of[k]] != k) continue;
+        const auto& st = t.stars[t.star_of[k]];
+        for (auto& V : t.vmult[k])
+            for (auto& C : t.cmult[k]) {
+                int o = (int)t.orbit_star.size();
+                t.orbit_star.push_back(t.star_of[k]);
+                t.orbit_vlo.push_back(V.first);
+                t.orbit_vn.push_back(V.second);
+                t.orbit_clo.push_back(C.first - nv);
+                t.orbit_cn.push_back(C.second);
+                for (int k2 : st)
+                    for (int v = V.first; v < V.first + V.second; ++v)
+                        for (int c = C.first - nv; c < C.first - nv + C.second; ++c) {
+                            int64_t I = ((int64_t)k2 * nv + v) * nc + c;
+                            t.orbit_members.push_back(I);
+                            t.orbit_of[I] = o;
+                        }
+                t.orbit_off.push_back((int64_t)t.orbit_members.size());
+            }
+    }
+    for (int64_t I = 0; I < N; ++I)
+        if (t.orbit_of[I] < 0) return fail(BSE_ESYMM, "product index %lld has no orbit", (long long)I);
+    // order orbits by lowest member: already ascending within a star (k ascending),
+    // and stars visited by ascending representative.  Verify.
+    for (size_t o = 1; o + 1 < t.orbit_off.size(); ++o)
+        if (t.orbit_members[t.orbit_off[o]] < t.orbit_members[t.orbit_off[o - 1]])
+            return fail(BSE_ESYMM, "orbit order violated");
+    // Gamma layout: per k, the multiplet blocks (valence, then conduction), d x d row-major
+    t.gam_koff.assign(t.nk + 1, 0);
+    for (int k = 0; k < t.nk; ++k) {
+        int64_t n = 0;
+        for (auto& m : t.vmult[k]) n += (int64_t)m.second * m.second;
+        for (auto& m : t.cmult[k]) n += (int64_t)m.second * m.second;
+        t.gam_koff[k + 1] = t.gam_koff[k] + n;
+    }
+    t.gam_per_s = t.gam_koff[t.nk];
+    return BSE_OK;
+}
+
+// Gamma(s) at k: entry of (n' <- n) inside the multiplet block of band n
+static inline int64_t gam_index(const Tables& t, int s, int k, int band_np, int band_n) {
+    // locate the block of band_n
+    int64_t off = t.gam_koff[k];
+    for (auto& m : t.vmult[k]) {
+        if (band_n >= m.first && band_n < m.first + m.second)
+            return (int64_t)s * t.gam_per_s + off + (int64_t)(band_np - m.first) * m.second + (band_n - m.first);
+        off += (int64_t)m.second * m.second;
+    }
+    for (auto& m : t.cmult[k]) {
+        if (band_n >= m.first && band_n < m.first + m.second)
+            return (int64_t)s * t.gam_per_s + off + (int64_t)(band_np - m.first) * m.second + (band_n - m.first);
+        off += (int64_t)m.second * m.second;
+    }
+    return -1;
+}
+
+int check_band_rotations(const Tables& t) {
+    // each multiplet block of Gamma(s) at k must be unitary
+    for (int s = 0; s < t.nops; ++s)
+        for (int k = 0; k < t.nk; ++k) {
+            int64_t off = (int64_t)s * t.gam_per_s + t.gam_koff[k];
+            auto chk = [&](const std::vector<std::pair<int, int>>& ms) -> bool {
+                for (auto& m : ms) {
+                    int d = m.second;
+                    const cplx* g = &t.gamma[off];
+                    for (int i = 0; i < d; ++i)
+                        for (int j = 0; j < d; ++j) {
+                            cplx a = 0;
+                            for (int l = 0; l < d; ++l) a += std::conj(g[l * d + i]) * g[l * d + j];
+                            if (std::abs(a - (i == j ? 1.0 : 0.0)) > 1e-9) return false;
+                        }
+                    off += (int64_t)d * d;
+                }
+                return true;
+            };
+            if (!chk(t.vmult[k]) || !chk(t.cmult[k]))
+                return fail(BSE_ESYMM, "band rotation of operation %d at k=%d is not unitary", s, k);
+        }
+    return BSE_OK;
+}
+
+// canonical orthonormal basis of irrep mu: P_mu e_j over each orbit, then two
+// passes of modified Gram-Schmidt, keeping residuals with norm > 1e-6.
+int build_basis(const Tables& t, int mu, Basis& out) {
+    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
+    const int G = t.nops, nv = t.nv, nc = t.nc;
+    const double pref = (double)t.irrep_dim[mu] / G;
+    const int32_t* chi = &t.chi[(size_t)mu * G];
+    out = Basis();
+    out.col_off.push_back(0);
+    const int nstars = (int)t.stars.size();
+    out.star_col.assign(nstars + 1, 0);
+    const int no = (int)t.orbit_star.size();
+    std::vector<cplx> x, acc;
+    for (int o = 0; o < no; ++o) {
+        const int64_t m0 = t.orbit_off[o], n_o = t.orbit_off[o + 1] - m0;
+        const int vn = t.orbit_vn[o], cn = t.orbit_cn[o], vlo = t.orbit_vlo[o], clo = t.orbit_clo[o];
+        const int blk = vn * cn;
+        const int st = t.orbit_star[o];
+        acc.clear();
+        int nacc = 0;
+        x.assign(n_o, 0.0);
+        for (int64_t jj = 0; jj < n_o; ++jj) {
+            const int64_t I = t.orbit_members[m0 + jj];
+            const int k = (int)(I / (nv * nc));
+            const int v = (int)((I / nc) % nv), c = (int)(I % nc);
+            std::fill(x.begin(), x.end(), cplx(0.0));
+            for (int s = 0; s < G; ++s) {
+                if (chi[s] == 0) continue;
+                const int k2 = t.rotk[(size_t)s * t.nk + k];
+                const int64_t base = (int64_t)t.pos_in_star[k2] * blk;
+                for (int vp = 0; vp < vn; ++vp) {
+                    cplx gv = t.gamma[gam_index(t, s, k, vlo + vp, v)];
+                    if (gv == 0.0) continue;
+                    for (int cp = 0; cp < cn; ++cp) {
+                        cplx gc = t.gamma[gam_index(t, s, k, nv + clo + cp, nv + c)];
+                        x[base + vp * cn + cp] += (double)chi[s] * gc * std::conj(gv);
+                    }
+                }
+            }
+            for (auto& z : x) z *= pref;
+            for (int pass = 0; pass < 2; ++pass)
+                for (int a = 0; a < nacc; ++a) {
+                    const cplx* u = &acc[(size_t)a * n_o];
+                    cplx d = 0;
+                    for (int64_t i = 0; i < n_o; ++i) d += std::conj(u[i]) * x[i];
+                    for (int64_t i = 0; i < n_o; ++i) x[i] -= u[i] * d;
+                }
+            double nrm = 0;
+            for (auto& z : x) nrm += std::norm(z);
+            nrm = std::sqrt(nrm);
+            if (nrm > 1e-6) {
+                for (auto& z : x) z /= nrm;
+                acc.insert(acc.end(), x.begin(), x.end());
+                ++nacc;
+            }
+        }
+        for (int a = 0; a < nacc; ++a) {
+            out.col_orbit.push_back(o);
+            out.coef.insert(out.coef.end(), acc.begin() + (size_t)a * n_o, acc.begin() + (size_t)(a + 1) * n_o);
+            out.col_off.push_back((int64_t)out.coef.size());
+        }
+        out.star_col[st + 1] += nacc;
+    }
+    out.dim = (int64_t)out.col_orbit.size();
+    for (int a = 0; a < nstars; ++a) out.star_col[a + 1] += out.star_col[a];
+    // columns must be grouped by star in star order
+    for (int64_t j = 1; j < out.dim; ++j)
+        if (t.orbit_star[out.col_orbit[j]] < t.orbit_star[out.col_orbit[j - 1]])
+            return fail(BSE_ESYMM, "basis columns not grouped by star");
+    return BSE_OK;
+}
+
+}  // namespace bse

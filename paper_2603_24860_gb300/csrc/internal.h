@@ -1,0 +1,172 @@
+// Internal declarations of the GB300 BSE block builder (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bse.h"
+
+namespace bse {
+
+using cplx = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);   // records the message, returns code
+void clear_error();
+
+#define BSE_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return ::bse::fail(BSE_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__,  \
+                               #call, cudaGetErrorString(e_));                 \
+    } while (0)
+
+#define BSE_TRY(call)                                                          \
+    do {                                                                       \
+        int r_ = (call);                                                       \
+        if (r_ != BSE_OK) return r_;                                           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// host symmetry tables (host_tables.cpp)
+// ---------------------------------------------------------------------------
+struct Tables {
+    int nops = 0, nk = 0, nv = 0, nc = 0, nb = 0, B = 0;  // B = nv * nc
+    int n[3] = {0, 0, 0};
+    int64_t N = 0;
+    double lattice[9];      // row-major, columns a_j
+    double recip[9];        // row-major, columns b_j = 2 pi L^{-T}
+    double v_uc = 0.0;
+    std::vector<int32_t> rot, rk;     // [nops*9] R and R^{-T}
+    std::vector<double> tau;          // [nops*3]
+    std::vector<double> cart;         // [nops*9] A = L R L^{-1}
+    std::vector<int32_t> mult;        // [nops*nops]
+    int identity = -1;
+    std::vector<int32_t> kidx;        // [nk*3] mesh indices i, j, l
+    std::vector<int32_t> rotk;        // [nops*nk]
+    std::vector<int32_t> star_of, star_rep, s_k, pos_in_star;
+    std::vector<std::vector<int32_t>> stars;
+    std::vector<int32_t> class_of;
+    int n_irreps = 0;
+    std::vector<int32_t> chi, irrep_dim, bright;   // chi [n_irreps*nops]
+    // multiplets at each k: (first band, size) for occupied and unoccupied
+    std::vector<std::vector<std::pair<int, int>>> vmult, cmult;
+    std::vector<int32_t> band_mult;   // [nk*nb] multiplet id of each band (per k)
+    // orbits of the product basis
+    std::vector<int64_t> orbit_off;     // [n_orbits+1] into orbit_members
+    std::vector<int64_t> orbit_members; // product indices, ascending per orbit
+    std::vector<int32_t> orbit_star;    // [n_orbits]
+    std::vector<int32_t> orbit_vlo, orbit_vn, orbit_clo, orbit_cn;
+    std::vector<int32_t> orbit_of;      // [N]
+    // band rotations Gamma(s): multiplet blocks, layout below
+    std::vector<int64_t> gam_koff;      // [nk+1] entry offset of k within one s
+    int64_t gam_per_s = 0;              // entries per operation
+    std::vector<cplx> gamma;            // [nops * gam_per_s]
+};
+
+int build_group(Tables& t, const bse_system* sys);
+int build_mesh(Tables& t);
+int build_characters(Tables& t);
+int build_multiplets_and_orbits(Tables& t, const double* eps_host);
+int check_band_rotations(const Tables& t);
+
+// canonical basis of one irrep (host_tables.cpp)
+struct Basis {
+    int64_t dim = 0;
+    std::vector<int32_t> col_orbit;       // [dim]
+    std::vector<int64_t> col_off;         // [dim+1] offset into coef (length = orbit size)
+    std::vector<cplx> coef;               // concatenated column vectors on their orbit
+    std::vector<int64_t> star_col;        // [n_stars+1] column range of each star
+};
+int build_basis(const Tables& t, int mu, Basis& out);
+
+// ---------------------------------------------------------------------------
+// device-side view of the system (passed by value to kernels)
+// ---------------------------------------------------------------------------
+struct DevSys {
+    const double2* coef;   // [nk][nb][npw_max]
+    const double* eps;     // [nk][nb]
+    const double2* w;      // [nk][ng_max][ng_max]
+    const int* gk;         // [nk][npw_max][3]
+    const int* gq;         // [nk][ng_max][3]
+    const int* npw;        // [nk]
+    const int* ng;         // [nk]
+    const int* kidx;       // [nk][3]
+    const short* box;      // [nk][bvol] index of m in S_k or -1
+    int blo[3], bdim[3];
+    int64_t bvol;
+    int n1, n2, n3, nk, nv, nc, nb, npw_max, ng_max;
+    int g0;                // index of G = 0 in the sphere of q = 0
+    double inv_vol;        // 1 / (Nk V_uc)
+    double recip[9];       // row-major reciprocal basis (columns b_j)
+    double qhat[3];
+    double v_uc, scissor;
+};
+
+// one k pair of the direct term and where its B x B block goes
+struct PairTask {
+    int32_t k, kp;
+    int32_t row0, col0;     // block origin inside the tile
+    int64_t xoff;           // tile origin in the arena (elements)
+    int32_t ld;             // tile leading dimension (column-major)
+    int32_t flags;          // 1: also write the mirrored (conjugate) block
+};
+
+// a star-pair tile for the projection kernels
+struct TileTask {
+    int64_t xoff, yoff;     // tile origins (elements) of X and Y
+    int32_t rows;           // |a| * B  (leading dimension of X and Y)
+    int32_t cols;           // |b| * B
+    int32_t star_a, star_b;
+    int64_t ca0, ca1;       // H_mu column range of star a
+    int64_t cb0, cb1;       // H_mu column range of star b
+};
+
+// device copy of one irrep basis
+struct DevBasis {
+    int64_t dim;
+    const int* col_orbit;       // [dim]
+    const int64_t* col_off;     // [dim+1]
+    const double2* coef;        // concatenated
+    const int64_t* orbit_off;   // [n_orbits+1]
+    const int64_t* members;     // product indices
+    const int* member_loc;      // local row of each member inside its star tile
+};
+
+// kernel launchers (kernels.cu); all on the given stream
+int launch_rotmap(const DevSys& s, const int* rk, const double* tau, const int* rotk, int nops,
+                  int* perm, double2* phase, cudaStream_t st);
+int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, const double2* phase,
+                 const int* ent, int64_t n_ent, double2* out, cudaStream_t st);
+int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands,
+                    int exchange_layout, double2* out, cudaStream_t st);
+int launch_direct(const DevSys& s, const PairTask* tasks, int64_t ntasks, double2* X,
+                  uint32_t terms, double w_div, cudaStream_t st);
+int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, const int* unused,
+                         const double2* X, double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
+int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y,
+                        const double2* Pmu, const double* vbar, int ng0, double xscale,
+                        double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
+int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
+int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
+                         double2* H, int64_t ld, cudaStream_t st);
+int launch_basis_dense(const DevBasis& b, double2* U, int64_t ld, cudaStream_t st);
+int launch_dipoles(const DevSys& s, double2* B, cudaStream_t st);
+int launch_bmu(const DevBasis& b, const double2* B, double2* Bmu, cudaStream_t st);
+int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, double* osc,
+                       cudaStream_t st);
+int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega,
+                    int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);
+// recip_and_lattice: reciprocal basis then lattice, both row-major 3x3
+int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax,
+                double delta, double* partial, int64_t npartial_max, double* out, cudaStream_t st);
+int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta);
+
+}  // namespace bse

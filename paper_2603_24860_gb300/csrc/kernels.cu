@@ -1,0 +1,718 @@
+// FP64 CUDA kernels of the symmetry-reduced BSE block builder (sm_103a).
+//
+// Paper references: Eq. w_interaction (pair densities in plane waves),
+// Eq. BSE-eigval (H = D + spin K^x - K^d), Eq. Wdiv with divergence_int and
+// divergence_sum (head correction), Eq. Ts (band rotations), Eqs. projection
+// and transformationU (projection onto an irrep), Eqs. oscillator,
+// oscillatorA, reducible_polar (spectrum).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "internal.h"
+
+namespace bse {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfma_conj(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+#define LAUNCH_CHECK()                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(BSE_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// mesh helpers
+// ---------------------------------------------------------------------------
+// q = k - k' on the mesh and the integer fold f_k' + f_q - f_k
+__device__ __forceinline__ int mesh_minus(const DevSys& S, int k, int kp, int fold[3]) {
+    const int n[3] = {S.n1, S.n2, S.n3};
+    int iq[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int ik = S.kidx[3 * k + a], ikp = S.kidx[3 * kp + a];
+        iq[a] = (ik - ikp + n[a]) % n[a];
+        fold[a] = (ikp + iq[a] - ik) / n[a];
+    }
+    return (iq[0] * S.n2 + iq[1]) * S.n3 + iq[2];
+}
+
+// position of integer vector m in the coset sphere of k, -1 if absent
+__device__ __forceinline__ int sphere_index(const DevSys& S, int k, int m0, int m1, int m2) {
+    int x0 = m0 - S.blo[0], x1 = m1 - S.blo[1], x2 = m2 - S.blo[2];
+    if ((unsigned)x0 >= (unsigned)S.bdim[0] || (unsigned)x1 >= (unsigned)S.bdim[1] ||
+        (unsigned)x2 >= (unsigned)S.bdim[2])
+        return -1;
+    return S.box[(int64_t)k * S.bvol + ((int64_t)x0 * S.bdim[1] + x1) * S.bdim[2] + x2];
+}
+
+// ---------------------------------------------------------------------------
+// band rotations (Eq. Ts): map p -> R^{-T} p and its phase exp(-2 pi i R^{-T}p . t)
+// ---------------------------------------------------------------------------
+__global__ void rotmap_kernel(DevSys S, const int* __restrict__ rk, const double* __restrict__ tau,
+                              const int* __restrict__ rotk, int nops, int* perm, double2* phase) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)nops * S.nk * S.npw_max;
+    if (id >= tot) return;
+    int i = (int)(id % S.npw_max);
+    int k = (int)((id / S.npw_max) % S.nk);
+    int s = (int)(id / ((int64_t)S.npw_max * S.nk));
+    if (i >= S.npw[k]) {
+        perm[id] = -1;
+        phase[id] = make_double2(0.0, 0.0);
+        return;
+    }
+    const int* R = rk + 9 * s;
+    const int k2 = rotk[(int64_t)s * S.nk + k];
+    const double n[3] = {(double)S.n1, (double)S.n2, (double)S.n3};
+    const int* m = S.gk + ((int64_t)k * S.npw_max + i) * 3;
+    int mr[3];
+    double th = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double fr = 0.0;
+        int mm = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            fr += R[3 * a + b] * (S.kidx[3 * k + b] / n[b]);
+            mm += R[3 * a + b] * m[b];
+        }
+        double f2 = S.kidx[3 * k2 + a] / n[a];
+        int fold = (int)rint(fr - f2);
+        mr[a] = mm + fold;
+        th += (f2 + mr[a]) * tau[3 * s + a];
+    }
+    th -= floor(th);
+    double sn, cs;
+    sincospi(-2.0 * th, &sn, &cs);
+    perm[id] = sphere_index(S, k2, mr[0], mr[1], mr[2]);
+    phase[id] = make_double2(cs, sn);
+}
+
+// Gamma(s)_{k n}^{sk n'} = sum_p conj(c_{sk n'}(R^{-T} p)) exp(..) c_{k n}(p)
+__global__ void gamma_kernel(DevSys S, int nops, const int* __restrict__ rotk, const int* __restrict__ perm,
+                             const double2* __restrict__ phase, const int* __restrict__ ent, int64_t n_ent,
+                             double2* out) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)nops * n_ent) return;
+    int64_t e = id % n_ent;
+    int s = (int)(id / n_ent);
+    int k = ent[3 * e], np_ = ent[3 * e + 1], nb_ = ent[3 * e + 2];
+    int k2 = rotk[(int64_t)s * S.nk + k];
+    const double2* ck = S.coef + ((int64_t)k * S.nb + nb_) * S.npw_max;
+    const double2* ck2 = S.coef + ((int64_t)k2 * S.nb + np_) * S.npw_max;
+    const int64_t base = ((int64_t)s * S.nk + k) * S.npw_max;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < S.npw[k]; ++i) {
+        int j = perm[base + i];
+        if (j < 0) continue;
+        cfma_conj(acc, ck2[j], cmul(phase[base + i], ck[i]));
+    }
+    out[id] = acc;
+}
+
+int launch_rotmap(const DevSys& s, const int* rk, const double* tau, const int* rotk, int nops, int* perm,
+                  double2* phase, cudaStream_t st) {
+    int64_t n = (int64_t)nops * s.nk * s.npw_max;
+    rotmap_kernel<<<ceil_div(n, 256), 256, 0, st>>>(s, rk, tau, rotk, nops, perm, phase);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, const double2* phase, const int* ent,
+                 int64_t n_ent, double2* out, cudaStream_t st) {
+    int64_t n = (int64_t)nops * n_ent;
+    if (n == 0) return BSE_OK;
+    gamma_kernel<<<ceil_div(n, 128), 128, 0, st>>>(s, nops, rotk, perm, phase, ent, n_ent, out);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pair densities (Eq. w_interaction in plane waves)
+// ---------------------------------------------------------------------------
+// shared-memory staging of one k pair: coefficients of both k and the
+// index table idx[g][j] = position of p'_j + Q_g in S_k (or -1).
+struct PairStage {
+    double2* ck;    // [nb][npw_max]
+    double2* ckp;   // [nb][npw_max]
+    short* idx;     // [ng][npkp]
+    int q, ng, npkp;
+};
+
+__device__ void stage_pair(const DevSys& S, int k, int kp, PairStage& P) {
+    int fold[3];
+    P.q = mesh_minus(S, k, kp, fold);
+    P.ng = S.ng[P.q];
+    P.npkp = S.npw[kp];
+    const int tot = S.nb * S.npw_max;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        P.ck[e] = S.coef[(int64_t)k * tot + e];
+        P.ckp[e] = S.coef[(int64_t)kp * tot + e];
+    }
+    const int* gq = S.gq + (int64_t)P.q * S.ng_max * 3;
+    const int* gk = S.gk + (int64_t)kp * S.npw_max * 3;
+    for (int e = threadIdx.x; e < P.ng * P.npkp; e += blockDim.x) {
+        int g = e / P.npkp, j = e % P.npkp;
+        P.idx[e] = (short)sphere_index(S, k, gk[3 * j] + gq[3 * g] + fold[0], gk[3 * j + 1] + gq[3 * g + 1] + fold[1],
+                                       gk[3 * j + 2] + gq[3 * g + 2] + fold[2]);
+    }
+}
+
+// rho[a][b][g] for bands n = n_lo + a (a < nn), n' = np_lo + b (b < nnp)
+__device__ __forceinline__ double2 rho_elem(const DevSys& S, const PairStage& P, int n, int np_, int g) {
+    const double2* cn = P.ck + n * S.npw_max;
+    const double2* cp = P.ckp + np_ * S.npw_max;
+    const short* row = P.idx + g * P.npkp;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < P.npkp; ++j) {
+        int i = row[j];
+        if (i >= 0) cfma_conj(acc, cn[i], cp[j]);
+    }
+    return acc;
+}
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t stage_bytes(int nb, int npw_max, int ng_max) {
+    return align16(sizeof(double2) * (size_t)nb * npw_max) * 2 + align16(sizeof(short) * (size_t)ng_max * npw_max);
+}
+
+__global__ void pairdens_kernel(DevSys S, const int* __restrict__ kk, const int* __restrict__ kpp, int bands,
+                                int exchange_layout, double2* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PairStage P;
+    P.ck = (double2*)smem;
+    P.ckp = (double2*)(smem + align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
+    P.idx = (short*)(smem + 2 * align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
+    const int64_t pr = blockIdx.x;
+    const int k = kk[pr], kp = kpp[pr];
+    stage_pair(S, k, kp, P);
+    __syncthreads();
+    int n_lo, nn, np_lo, nnp;
+    if (bands == BSE_BANDS_CC) { n_lo = S.nv; nn = S.nc; np_lo = S.nv; nnp = S.nc; }
+    else if (bands == BSE_BANDS_VV) { n_lo = 0; nn = S.nv; np_lo = 0; nnp = S.nv; }
+    else { n_lo = S.nv; nn = S.nc; np_lo = 0; nnp = S.nv; }
+    if (!exchange_layout) {
+        const int tot = nn * nnp * S.ng_max;
+        double2* o = out + pr * (int64_t)tot;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            int g = e % S.ng_max, ab = e / S.ng_max;
+            o[e] = g < P.ng ? rho_elem(S, P, n_lo + ab / nnp, np_lo + ab % nnp, g) : make_double2(0.0, 0.0);
+        }
+    } else {
+        // exchange vectors P[(k*nv + v)*nc + c][g] = m^k_cv(G_g), q = 0
+        const int ng0 = P.ng;
+        const int tot = nn * nnp * ng0;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            int g = e % ng0, ab = e / ng0;
+            int c = ab / nnp, v = ab % nnp;
+            out[(((int64_t)k * S.nv + v) * S.nc + c) * ng0 + g] = rho_elem(S, P, n_lo + c, np_lo + v, g);
+        }
+    }
+}
+
+int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands, int exchange_layout,
+                    double2* out, cudaStream_t st) {
+    if (npairs == 0) return BSE_OK;
+    size_t sm = stage_bytes(s.nb, s.npw_max, s.ng_max);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pairdens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return fail(BSE_ECUDA, "pairdens smem %zu: %s", sm, cudaGetErrorString(e));
+    }
+    pairdens_kernel<<<(unsigned)npairs, 256, sm, st>>>(s, k, kp, bands, exchange_layout, out);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// direct term of one k pair, written into a column-major tile:
+//   X[(v,c),(v',c')] = -K^d + delta_{kk'} delta (eps_c - eps_v - W^div)
+//   K^d = 1/V sum_{Q,Q'} rho_cc'(Q) W_QQ'(q) conj(rho_vv'(Q'))   (Eq. BSE-eigval)
+// At q = 0 the head and wings of W are dropped (Sec. III.B).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t direct_smem(int nb, int nv, int nc, int npw_max, int ng_max) {
+    size_t st = stage_bytes(nb, npw_max, ng_max);
+    size_t t = align16(sizeof(double2) * (size_t)nv * nv * ng_max);
+    size_t a = st > t ? st : t;
+    return a + align16(sizeof(double2) * (size_t)nc * nc * ng_max) + align16(sizeof(double2) * (size_t)nv * nv * ng_max);
+}
+
+__global__ void __launch_bounds__(256) direct_fp64_kernel(DevSys S, const PairTask* __restrict__ tasks, double2* X,
+                                                          uint32_t terms, double w_div) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PairTask t = tasks[blockIdx.x];
+    const int nv = S.nv, nc = S.nc, B = nv * nc;
+    size_t st = stage_bytes(S.nb, S.npw_max, S.ng_max);
+    size_t tb = align16(sizeof(double2) * (size_t)nv * nv * S.ng_max);
+    size_t region = st > tb ? st : tb;
+    PairStage P;
+    P.ck = (double2*)smem;
+    P.ckp = (double2*)(smem + align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
+    P.idx = (short*)(smem + 2 * align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
+    double2* T = (double2*)smem;   // reuses the staging region after rho is formed
+    double2* rc = (double2*)(smem + region);
+    double2* rv = (double2*)(smem + region + align16(sizeof(double2) * (size_t)nc * nc * S.ng_max));
+    double2* Xt = X + t.xoff;
+    const bool direct = (terms & BSE_TERM_DIRECT) != 0;
+    int ng = 0, q = 0;
+    if (direct) {
+        stage_pair(S, t.k, t.kp, P);
+        __syncthreads();
+        ng = P.ng;
+        q = P.q;
+        const int ncc = nc * nc, tot = (ncc + nv * nv) * ng;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            int g = e % ng, ab = e / ng;
+            if (ab < ncc) rc[ab * S.ng_max + g] = rho_elem(S, P, nv + ab / nc, nv + ab % nc, g);
+            else {
+                int vv = ab - ncc;
+                rv[vv * S.ng_max + g] = rho_elem(S, P, vv / nv, vv % nv, g);
+            }
+        }
+        __syncthreads();
+        // T[vv'][Q] = sum_Q' W_QQ'(q) conj(rho_vv'(Q'))
+        const double2* W = S.w + (int64_t)q * S.ng_max * S.ng_max;
+        const int skip = (q == 0) ? S.g0 : -1;
+        for (int e = threadIdx.x; e < nv * nv * ng; e += blockDim.x) {
+            int Q = e % ng, vv = e / ng;
+            double2 acc = make_double2(0.0, 0.0);
+            if (Q != skip) {
+                const double2* wr = W + (int64_t)Q * S.ng_max;
+                const double2* r = rv + vv * S.ng_max;
+                for (int Qp = 0; Qp < ng; ++Qp) {
+                    if (Qp == skip) continue;
+                    cfma(acc, wr[Qp], conjd(r[Qp]));
+                }
+            }
+            T[vv * S.ng_max + Q] = acc;
+        }
+        __syncthreads();
+    }
+    const bool diag = (t.k == t.kp) && (terms & BSE_TERM_DIAG);
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        int r = e % B, cidx = e / B;    // r: (v, c) row, cidx: (v', c') column
+        int v = r / nc, c = r % nc, vp = cidx / nc, cp = cidx % nc;
+        double2 acc = make_double2(0.0, 0.0);
+        if (direct) {
+            const double2* a = rc + (c * nc + cp) * S.ng_max;
+            const double2* b = T + (v * nv + vp) * S.ng_max;
+            for (int Q = 0; Q < ng; ++Q) cfma(acc, a[Q], b[Q]);
+        }
+        double2 val = make_double2(-acc.x * S.inv_vol, -acc.y * S.inv_vol);
+        if (diag && r == cidx) val.x += S.eps[t.k * S.nb + nv + c] - S.eps[t.k * S.nb + v] - w_div;
+        Xt[(int64_t)(t.col0 + cidx) * t.ld + t.row0 + r] = val;
+        if (t.flags & 1) Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + cidx] = conjd(val);
+    }
+}
+
+int launch_direct(const DevSys& s, const PairTask* tasks, int64_t ntasks, double2* X, uint32_t terms, double w_div,
+                  cudaStream_t st) {
+    if (ntasks == 0) return BSE_OK;
+    size_t sm = direct_smem(s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
+    if (sm > 227 * 1024) return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", sm);
+    cudaError_t e = cudaFuncSetAttribute(direct_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", sm, cudaGetErrorString(e));
+    for (int64_t off = 0; off < ntasks; off += 1 << 30) {
+        int64_t n = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
+        direct_fp64_kernel<<<(unsigned)n, 256, sm, st>>>(s, tasks + off, X, terms, w_div);
+        LAUNCH_CHECK();
+    }
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// projection (Eqs. projection, transformationU), orbit-sparse, two stages:
+//   Y = X U_b   (tile rows of star a, columns of star b's basis vectors)
+//   H_mu[cols a, cols b] = U_a^dagger Y (+ exchange, projected)
+// ---------------------------------------------------------------------------
+__global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ X,
+                                     double2* Y) {
+    const TileTask t = tiles[blockIdx.z];
+    const int r = blockIdx.x * 32 + threadIdx.x;
+    const int64_t ncol = t.cb1 - t.cb0;
+    if (r >= t.rows) return;
+    const double2* Xt = X + t.xoff;
+    for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
+        const int64_t j = t.cb0 + jj;
+        const int o = Bs.col_orbit[j];
+        const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+        const double2* u = Bs.coef + Bs.col_off[j];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int64_t tt = 0; tt < n_o; ++tt) cfma(acc, Xt[(int64_t)Bs.member_loc[m0 + tt] * t.rows + r], u[tt]);
+        Y[t.yoff + jj * t.rows + r] = acc;
+    }
+}
+
+__global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ Y,
+                                    const double2* __restrict__ Pmu, const double* __restrict__ vbar, int ng0,
+                                    double xscale, double2* H, int64_t ld) {
+    const TileTask t = tiles[blockIdx.z];
+    const int64_t ii = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t nrow = t.ca1 - t.ca0, ncol = t.cb1 - t.cb0;
+    if (ii >= nrow) return;
+    const int64_t i = t.ca0 + ii;
+    const int o = Bs.col_orbit[i];
+    const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+    const double2* u = Bs.coef + Bs.col_off[i];
+    for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
+        const int64_t j = t.cb0 + jj;
+        const double2* y = Y + t.yoff + jj * t.rows;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int64_t tt = 0; tt < n_o; ++tt) cfma_conj(acc, u[tt], y[Bs.member_loc[m0 + tt]]);
+        if (Pmu) {
+            const double2* pi = Pmu + i * ng0;
+            const double2* pj = Pmu + j * ng0;
+            double2 ex = make_double2(0.0, 0.0);
+            for (int g = 0; g < ng0; ++g) {
+                double2 z = cmul(pi[g], conjd(pj[g]));
+                ex.x = fma(vbar[g], z.x, ex.x);
+                ex.y = fma(vbar[g], z.y, ex.y);
+            }
+            acc.x = fma(xscale, ex.x, acc.x);
+            acc.y = fma(xscale, ex.y, acc.y);
+        }
+        H[j * ld + i] = acc;
+        if (t.star_a != t.star_b) H[i * ld + j] = conjd(acc);
+    }
+}
+
+int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, const int*, const double2* X,
+                         double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st) {
+    if (ntiles == 0) return BSE_OK;
+    dim3 blk(32, 8);
+    int gy = ceil_div(max_cols, 8);
+    if (gy > 64) gy = 64;
+    if (gy < 1) gy = 1;
+    for (int off = 0; off < ntiles; off += 65535) {
+        int n = ntiles - off < 65535 ? ntiles - off : 65535;
+        dim3 grd(ceil_div(max_rows, 32), gy, n);
+        project_right_kernel<<<grd, blk, 0, st>>>(b, tiles + off, X, Y);
+        LAUNCH_CHECK();
+    }
+    return BSE_OK;
+}
+
+int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y, const double2* Pmu,
+                        const double* vbar, int ng0, double xscale, double2* H, int64_t ld, int64_t max_ca,
+                        int64_t max_cb, cudaStream_t st) {
+    if (ntiles == 0) return BSE_OK;
+    dim3 blk(32, 8);
+    int gy = ceil_div(max_cb, 8);
+    if (gy > 64) gy = 64;
+    if (gy < 1) gy = 1;
+    for (int off = 0; off < ntiles; off += 65535) {
+        int n = ntiles - off < 65535 ? ntiles - off : 65535;
+        dim3 grd(ceil_div(max_ca, 32) > 0 ? ceil_div(max_ca, 32) : 1, gy, n);
+        project_left_kernel<<<grd, blk, 0, st>>>(b, tiles + off, Y, Pmu, vbar, ng0, xscale, H, ld);
+        LAUNCH_CHECK();
+    }
+    return BSE_OK;
+}
+
+// Pmu[i][g] = sum_t conj(U_i[t]) P[member_t][g]
+__global__ void exchange_project_kernel(DevBasis Bs, const double2* __restrict__ P, int ng0, double2* Pmu) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= Bs.dim * ng0) return;
+    int64_t i = id / ng0;
+    int g = (int)(id % ng0);
+    const int o = Bs.col_orbit[i];
+    const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+    const double2* u = Bs.coef + Bs.col_off[i];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t tt = 0; tt < n_o; ++tt) cfma_conj(acc, u[tt], P[Bs.members[m0 + tt] * ng0 + g]);
+    Pmu[id] = acc;
+}
+
+int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st) {
+    int64_t n = b.dim * ng0;
+    if (n == 0) return BSE_OK;
+    exchange_project_kernel<<<ceil_div(n, 256), 256, 0, st>>>(b, P, ng0, Pmu);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// H[I, J] += xscale sum_g vbar_g P[I][g] conj(P[J][g])  (column-major H)
+__global__ void exchange_full_kernel(const double2* __restrict__ P, const double* __restrict__ vbar, int ng0,
+                                     int64_t N, double xscale, double2* H, int64_t ld) {
+    int64_t I = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    int64_t J = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    if (I >= N || J >= N) return;
+    double2 ex = make_double2(0.0, 0.0);
+    for (int g = 0; g < ng0; ++g) {
+        double2 z = cmul(P[I * ng0 + g], conjd(P[J * ng0 + g]));
+        ex.x = fma(vbar[g], z.x, ex.x);
+        ex.y = fma(vbar[g], z.y, ex.y);
+    }
+    double2 h = H[J * ld + I];
+    h.x = fma(xscale, ex.x, h.x);
+    h.y = fma(xscale, ex.y, h.y);
+    H[J * ld + I] = h;
+}
+
+int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale, double2* H,
+                         int64_t ld, cudaStream_t st) {
+    dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+    exchange_full_kernel<<<grd, blk, 0, st>>>(P, vbar, ng0, N, xscale, H, ld);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+__global__ void basis_dense_kernel(DevBasis Bs, double2* U, int64_t ld) {
+    int64_t j = blockIdx.x;
+    if (j >= Bs.dim) return;
+    const int o = Bs.col_orbit[j];
+    const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+    for (int64_t tt = threadIdx.x; tt < n_o; tt += blockDim.x) U[j * ld + Bs.members[m0 + tt]] = Bs.coef[Bs.col_off[j] + tt];
+}
+
+int launch_basis_dense(const DevBasis& b, double2* U, int64_t ld, cudaStream_t st) {
+    if (b.dim == 0) return BSE_OK;
+    basis_dense_kernel<<<(unsigned)b.dim, 64, 0, st>>>(b, U, ld);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// spectrum (Eqs. oscillator, oscillatorA, reducible_polar)
+// ---------------------------------------------------------------------------
+__global__ void dipoles_kernel(DevSys S, double2* Bout) {
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nv = S.nv, nc = S.nc;
+    if (id >= (int64_t)S.nk * nv * nc) return;
+    int k = (int)(id / (nv * nc)), v = (int)((id / nc) % nv), c = (int)(id % nc);
+    const double2* cv = S.coef + ((int64_t)k * S.nb + v) * S.npw_max;
+    const double2* cc = S.coef + ((int64_t)k * S.nb + nv + c) * S.npw_max;
+    const double f[3] = {S.kidx[3 * k] / (double)S.n1, S.kidx[3 * k + 1] / (double)S.n2,
+                         S.kidx[3 * k + 2] / (double)S.n3};
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < S.npw[k]; ++i) {
+        const int* m = S.gk + ((int64_t)k * S.npw_max + i) * 3;
+        double qp = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double pa = 0.0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) pa += S.recip[3 * a + b] * (f[b] + m[b]);
+            qp += S.qhat[a] * pa;
+        }
+        double2 z = cc[i];
+        z.x *= qp;
+        z.y *= qp;
+        cfma_conj(acc, cv[i], z);
+    }
+    double de = S.eps[k * S.nb + nv + c] - S.scissor - S.eps[k * S.nb + v];
+    double sc = 1.0 / (sqrt(S.v_uc) * de);
+    Bout[id] = make_double2(acc.x * sc, acc.y * sc);
+}
+
+int launch_dipoles(const DevSys& s, double2* B, cudaStream_t st) {
+    int64_t n = (int64_t)s.nk * s.nv * s.nc;
+    dipoles_kernel<<<ceil_div(n, 128), 128, 0, st>>>(s, B);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+__global__ void bmu_kernel(DevBasis Bs, const double2* __restrict__ B, double2* Bmu) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Bs.dim) return;
+    const int o = Bs.col_orbit[j];
+    const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+    const double2* u = Bs.coef + Bs.col_off[j];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t tt = 0; tt < n_o; ++tt) cfma(acc, u[tt], B[Bs.members[m0 + tt]]);
+    Bmu[j] = acc;
+}
+
+int launch_bmu(const DevBasis& b, const double2* B, double2* Bmu, cudaStream_t st) {
+    if (b.dim == 0) return BSE_OK;
+    bmu_kernel<<<ceil_div(b.dim, 128), 128, 0, st>>>(b, B, Bmu);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// osc[l] = |sum_i a[i, l] Bmu[i]|^2, one warp per eigenvector
+__global__ void oscillator_kernel(const double2* __restrict__ a, int64_t lda, int64_t dim,
+                                  const double2* __restrict__ Bmu, double* osc) {
+    int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (l >= dim) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = lane; i < dim; i += 32) cfma(acc, a[l * lda + i], Bmu[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) osc[l] = acc.x * acc.x + acc.y * acc.y;
+}
+
+int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, double* osc, cudaStream_t st) {
+    if (dim == 0) return BSE_OK;
+    oscillator_kernel<<<ceil_div(dim * 32, 256), 256, 0, st>>>(a, lda, dim, Bmu, osc);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+__global__ void spectrum_kernel(const double* __restrict__ Om, const double* __restrict__ osc, int64_t dim,
+                                const double* __restrict__ omega, int64_t n_omega, double eta, double pref,
+                                double* im) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_omega) return;
+    const double x = omega[w], e2 = eta * eta;
+    double acc = 0.0;
+    for (int64_t l = 0; l < dim; ++l) {
+        double d1 = x - Om[l], d2 = x + Om[l];
+        acc = fma(osc[l], eta / (d1 * d1 + e2) - eta / (d2 * d2 + e2), acc);
+    }
+    im[w] = pref * acc;
+}
+
+int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega, int64_t n_omega, double eta,
+                    double pref, double* im, cudaStream_t st) {
+    if (n_omega == 0) return BSE_OK;
+    spectrum_kernel<<<ceil_div(n_omega, 128), 128, 0, st>>>(Om, osc, dim, omega, n_omega, eta, pref, im);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// head correction: smoothed double-counting sum of Eq. divergence_sum over
+// Q = sum_j X_j b_j / n_j (X integer, Q != 0), one thread per (X1, X2) column
+// ---------------------------------------------------------------------------
+struct WdivGeom {
+    double s[9];      // columns: b_j / n_j (row-major 3x3)
+    double L[9];
+    double b, qmax, delta, lim;
+    int e1, e2;
+};
+
+__global__ void wdiv_kernel(WdivGeom g, double* partial) {
+    __shared__ double red[256];
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t ncol = (int64_t)(2 * g.e1 + 1) * (2 * g.e2 + 1);
+    double acc = 0.0;
+    if (id < ncol) {
+        int x1 = (int)(id / (2 * g.e2 + 1)) - g.e1;
+        int x2 = (int)(id % (2 * g.e2 + 1)) - g.e2;
+        double p[3], s3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p[a] = g.s[3 * a] * x1 + g.s[3 * a + 1] * x2;
+            s3[a] = g.s[3 * a + 2];
+        }
+        // |p + x3 s3|^2 <= lim^2: quadratic in x3
+        double A = s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2];
+        double Bq = 2.0 * (p[0] * s3[0] + p[1] * s3[1] + p[2] * s3[2]);
+        double C = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - g.lim * g.lim;
+        double disc = Bq * Bq - 4.0 * A * C;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            int lo = (int)floor((-Bq - sq) / (2.0 * A)) - 1;
+            int hi = (int)ceil((-Bq + sq) / (2.0 * A)) + 1;
+            for (int x3 = lo; x3 <= hi; ++x3) {
+                double Q[3] = {p[0] + x3 * s3[0], p[1] + x3 * s3[1], p[2] + x3 * s3[2]};
+                double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+                if (q2 <= 0.0) continue;
+                double q = sqrt(q2);
+                if (q > g.lim) continue;
+                double w = 1.0;
+                if (q >= g.qmax - g.delta) {
+                    double x = (q - g.qmax) / g.delta;
+                    w = (x * x * x - 3.0 * x + 2.0) * 0.25;
+                }
+                double ql = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ql += Q[a] * g.L[3 * a + c] * Q[c];
+                acc += exp(-g.b * q2) * w / ql;
+            }
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// fixed-order reduction of the block partials (deterministic)
+__global__ void reduce_kernel(const double* __restrict__ partial, int64_t n, double* out) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+static void wdiv_extent(const double* lattice, const int* n, double lim, int e[3]) {
+    for (int j = 0; j < 3; ++j) {
+        double len = sqrt(lattice[j] * lattice[j] + lattice[3 + j] * lattice[3 + j] + lattice[6 + j] * lattice[6 + j]);
+        e[j] = (int)ceil(n[j] * lim * len / (2.0 * M_PI)) + 1;
+    }
+}
+
+int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta) {
+    int e[3];
+    wdiv_extent(lattice, n, qmax + delta, e);
+    int64_t ncol = (int64_t)(2 * e[0] + 1) * (2 * e[1] + 1);
+    return (ncol + 255) / 256;
+}
+
+int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax, double delta,
+                double* partial, int64_t npartial_max, double* out, cudaStream_t st) {
+    // recip_and_lattice: 18 doubles, reciprocal basis then lattice (row-major)
+    WdivGeom g;
+    const double* recip = recip_and_lattice;
+    const double* lattice = recip_and_lattice + 9;
+    for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < 3; ++j) g.s[3 * a + j] = recip[3 * a + j] / n[j];
+    for (int i = 0; i < 9; ++i) g.L[i] = L[i];
+    g.b = b;
+    g.qmax = qmax;
+    g.delta = delta;
+    g.lim = qmax + delta;
+    int e[3];
+    wdiv_extent(lattice, n, g.lim, e);
+    g.e1 = e[0];
+    g.e2 = e[1];
+    int64_t ncol = (int64_t)(2 * e[0] + 1) * (2 * e[1] + 1);
+    int64_t nblk = (ncol + 255) / 256;
+    if (nblk > npartial_max) return fail(BSE_EINVAL, "head-correction scratch too small (%lld > %lld)",
+                                         (long long)nblk, (long long)npartial_max);
+    wdiv_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, partial);
+    LAUNCH_CHECK();
+    reduce_kernel<<<1, 1024, 0, st>>>(partial, nblk, out);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+}  // namespace bse

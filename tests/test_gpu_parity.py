@@ -1,0 +1,205 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Tolerances: integer tables bit-exact; FP64 floating point within 1e-10
+relative to the largest element (H, H_mu, U_mu), eigenvalues within 1e-10 Ha,
+spectra within 1e-9 relative L2."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import oracle_case, oracle_h
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wdiv.json")))
+SMALL = ["si2", "si4", "lif4", "mos2_331"]
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    from paper_2603_24860_gb300 import bse
+    assert torch.cuda.is_available()
+    ctxs = {}
+
+    def get(name):
+        if name not in ctxs:
+            from synth import generate
+            ctxs[name] = bse.bse_create(generate(name), stream=torch.cuda.current_stream())
+        return ctxs[name]
+    yield bse, torch, get
+    for c in ctxs.values():
+        bse.bse_destroy(c)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_tables_bit_exact(gpu, name):
+    bse, torch, get = gpu
+    t = bse.bse_tables(get(name))
+    d, inp, grp, mt, b = oracle_case(name)
+    chi, dims, cls = grp.characters()
+    assert np.array_equal(t["rotk"], mt.rotk)
+    assert np.array_equal(t["star_of_k"], mt.star_of)
+    assert np.array_equal(t["star_rep"], mt.star_rep)
+    assert np.array_equal(t["s_k"], mt.s_k)
+    assert np.array_equal(t["class_of_op"], cls)
+    assert np.array_equal(t["chi"], chi)
+    assert np.array_equal(t["irrep_dim"], dims)
+    vec = grp.vector_character()
+    assert np.array_equal(t["bright"], np.rint(chi @ vec / grp.n).astype(int))
+    assert np.array_equal(t["block_dim"], [b.basis(mu)[0].shape[1] for mu in range(len(dims))])
+    orb = np.zeros(inp.N, dtype=np.int64)
+    for o, mem in enumerate(b.orbits):
+        orb[mem] = o
+    assert np.array_equal(t["orbit_of"], orb)
+    assert t["n_orbits"] == len(b.orbits)
+
+
+@pytest.mark.parametrize("name", ["si2", "si4", "lif4", "mos2_331", "si8", "lif10"])
+def test_head_correction(gpu, name):
+    bse, torch, get = gpu
+    w = bse.bse_tables(get(name))["w_div"]
+    assert abs(w - GOLD[name]) <= TOL * abs(GOLD[name])
+
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("bands", [0, 1, 2])
+def test_pair_densities(gpu, name, bands):
+    bse, torch, get = gpu
+    from oracle.hamiltonian import pair_density
+    d, inp, grp, mt, b = oracle_case(name)
+    rng = np.random.default_rng(11)
+    k = np.concatenate([[0, inp.nk - 1, 1], rng.integers(0, inp.nk, 13)]).astype(np.int32)
+    kp = np.concatenate([[0, 0, inp.nk - 1], rng.integers(0, inp.nk, 13)]).astype(np.int32)
+    nv, nc = inp.nv, inp.nc
+    sets = {0: (range(nv, nv + nc), range(nv, nv + nc)), 1: (range(nv), range(nv)), 2: (range(nv, nv + nc), range(nv))}
+    n, npr = (len(x) for x in sets[bands])
+    ngmax = inp.gq.shape[1]
+    out = torch.zeros((len(k), n, npr, ngmax), dtype=torch.complex128, device="cuda")
+    bse.bse_pairdens(get(name), k, kp, bands, out)
+    got = out.cpu().numpy()
+    for i in range(len(k)):
+        ref, q = pair_density(inp, mt, int(k[i]), int(kp[i]), *sets[bands])
+        ng = ref.shape[2]
+        assert np.abs(got[i, :, :, :ng] - ref).max() < 1e-13
+        assert np.all(got[i, :, :, ng:] == 0)
+
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("terms", [1, 2, 4, 7])
+def test_full_hamiltonian(gpu, name, terms):
+    bse, torch, get = gpu
+    code = "".join(c for bit, c in ((1, "d"), (2, "x"), (4, "w")) if terms & bit)
+    ref = oracle_h(name, code)
+    got = bse.full(get(name), terms).cpu().numpy()
+    assert _rel(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_basis(gpu, name):
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    mus = range(len(b.dims)) if name != "si4" else b.bright() + [0, 4]
+    for mu in mus:
+        U, _ = b.basis(mu)
+        if U.shape[1] == 0:
+            continue
+        got = bse.basis(get(name), mu).cpu().numpy()
+        assert got.shape == U.shape
+        assert _rel(got, U) <= TOL
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_blocks(gpu, name):
+    """H_mu = U_mu^dagger H U_mu for every irrep (si4: bright and two others)."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    H = oracle_h(name)
+    mus = range(len(b.dims)) if name != "si4" else b.bright() + [0, 4]
+    for mu in mus:
+        U, _ = b.basis(mu)
+        ref = project(U, H)
+        got = bse.block(get(name), mu).cpu().numpy()
+        assert got.shape == ref.shape
+        if ref.size:
+            assert _rel(got, ref) <= TOL, (name, mu)
+
+
+@pytest.mark.parametrize("terms", [1, 2, 4])
+def test_block_terms(gpu, terms):
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case("si4")
+    code = "".join(c for bit, c in ((1, "d"), (2, "x"), (4, "w")) if terms & bit)
+    mu = b.bright()[0]
+    ref = project(b.basis(mu)[0], oracle_h("si4", code))
+    got = bse.block(get("si4"), mu, terms=terms).cpu().numpy()
+    assert _rel(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_dipoles(gpu, name):
+    from oracle.spectrum import dipoles
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    out = torch.empty(inp.N, dtype=torch.complex128, device="cuda")
+    bse.bse_dipoles(get(name), out)
+    assert _rel(out.cpu().numpy(), dipoles(inp, mt)) <= 1e-12
+
+
+def _clusters(om, tol=1e-8):
+    """Group indices of (sorted) eigenvalues closer than tol."""
+    out, cur = [], [0]
+    for i in range(1, len(om)):
+        if om[i] - om[cur[-1]] <= tol:
+            cur.append(i)
+        else:
+            out.append(cur)
+            cur = [i]
+    out.append(cur)
+    return out
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_block_spectrum(gpu, name):
+    from oracle.projection import project
+    from oracle.spectrum import block_spectrum, dipoles
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    B = dipoles(inp, mt)
+    omega = torch.tensor(d["omega"], device="cuda")
+    for mu in b.bright():
+        U, _ = b.basis(mu)
+        if U.shape[1] == 0:
+            continue
+        ref_h = project(U, oracle_h(name))
+        rom, rosc, rim = block_spectrum(inp, ref_h, U, B, d["omega"], d["eta"])
+        h = bse.block(get(name), mu)
+        om, osc, im = (x.cpu().numpy() for x in bse.spectrum(get(name), mu, h, omega, d["eta"]))
+        assert np.abs(om - rom).max() <= TOL
+        # oscillator strengths are basis independent only summed over degenerate levels
+        scale = np.linalg.norm(B) ** 2
+        for cl in _clusters(rom):
+            assert abs(osc[cl].sum() - rosc[cl].sum()) <= 1e-9 * scale
+        assert np.linalg.norm(im - rim) <= 1e-9 * np.linalg.norm(rim)
+
+
+def test_empty_block(gpu):
+    """An irrep whose block is empty builds and solves to nothing."""
+    bse, torch, get = gpu
+    for name in SMALL:
+        t = bse.bse_tables(get(name))
+        empty = [mu for mu in range(t["n_irreps"]) if t["block_dim"][mu] == 0]
+        if empty:
+            h = bse.block(get(name), empty[0])
+            assert h.shape == (0, 0)
+            return
+    pytest.skip("no empty irrep block among the small cases")

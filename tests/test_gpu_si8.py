@@ -1,0 +1,82 @@
+"""Full-size parity for the Si-like 8x8x8 mesh (Nv = 4, Nc = 6, N = 12288) in
+the launch configuration the benchmark times: the whole T1u block is built
+by bse_build_block and sampled star-pair sub-blocks are compared with the
+oracle, which computes each one from its definition (U_a^dagger H_ab U_b)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import oracle_case
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wdiv.json")))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import torch
+    from paper_2603_24860_gb300 import bse
+    from synth import generate
+    d = generate("si8")
+    ctx = bse.bse_create(d, stream=torch.cuda.current_stream())
+    t = bse.bse_tables(ctx)
+    mu = int(np.nonzero(t["bright"])[0][0])
+    h = bse.block(ctx, mu).cpu().numpy()
+    yield bse, torch, ctx, t, mu, h
+    bse.bse_destroy(ctx)
+
+
+def test_block_dimension(built):
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    assert mu == b.bright()[0]
+    assert h.shape[0] == b.basis(mu)[0].shape[1] == t["block_dim"][mu]
+    assert np.abs(h - h.conj().T).max() <= 1e-14 * np.abs(h).max()
+
+
+def _star_cols(b, mt, mu):
+    U, owner = b.basis(mu)
+    star_of_orbit = np.array([mt.star_of[m[0] // (b.inp.nv * b.inp.nc)] for m in b.orbits])
+    return U, star_of_orbit[owner]
+
+
+@pytest.mark.parametrize("pair", ["gamma", "small-large", "large-large", "mid-mid"])
+def test_sampled_star_pair_blocks(built, pair):
+    from oracle.hamiltonian import hamiltonian_block
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    sizes = np.array([len(s) for s in mt.stars])
+    big = int(np.nonzero(sizes == 48)[0][0])
+    mid = int(np.nonzero(sizes == 12)[0][0])
+    small = int(np.nonzero(sizes == 6)[0][0])
+    a, c = {"gamma": (0, 0), "small-large": (small, big), "large-large": (big, big), "mid-mid": (mid, mid)}[pair]
+    U, col_star = _star_cols(b, mt, mu)
+    ca, cb = np.nonzero(col_star == a)[0], np.nonzero(col_star == c)[0]
+    if len(ca) == 0 or len(cb) == 0:
+        pytest.skip("star carries no T1u vectors")
+    B = inp.nv * inp.nc
+    rows = np.concatenate([np.arange(k * B, (k + 1) * B) for k in mt.stars[a]])
+    cols = np.concatenate([np.arange(k * B, (k + 1) * B) for k in mt.stars[c]])
+    Hab = hamiltonian_block(inp, mt, list(mt.stars[a]), list(mt.stars[c]), GOLD["si8"])
+    ref = U[np.ix_(rows, ca)].conj().T @ Hab @ U[np.ix_(cols, cb)]
+    got = h[np.ix_(ca, cb)]
+    assert np.abs(got - ref).max() <= TOL * np.abs(h).max()
+
+
+def test_spectrum_sum_rule(built):
+    """sum_lambda |B_lambda|^2 = |U_mu^T B|^2 and the spectrum is positive."""
+    from oracle.spectrum import dipoles
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    U, _ = b.basis(mu)
+    bmu = U.T @ dipoles(inp, mt)
+    hd = torch.tensor(h, device="cuda").T.contiguous().T
+    omega = torch.tensor(d["omega"], device="cuda")
+    om, osc, im = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, hd, omega, d["eta"]))
+    assert abs(osc.sum() - np.linalg.norm(bmu) ** 2) <= 1e-10 * np.linalg.norm(bmu) ** 2
+    assert np.all(np.diff(om) >= -1e-14)
+    assert np.all(im[d["omega"] > 0] > 0)
