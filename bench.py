@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the symmetry-reduced BSE block builder on GB300.
+
+One step = the whole path on one synthetic input set: symmetry tables, band
+rotations and the canonical basis (bse_create), the optically active block
+H_mu (bse_build_block) and its spectrum (bse_block_spectrum).  The default
+workload is the Si-like 8x8x8 mesh (Nv = 4, Nc = 6, N = 12288, T1u block) in
+FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is the algorithmic work of the
+block build (pair densities, direct contraction, projection, exchange; real
+flops, complex multiply-add = 8) of all ranks' steps divided by the slowest
+rank's time for its K steps, inputs resident in HBM.  With N > 1 every rank
+runs an independent replica (the path needs no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H-block build TFLOP/s vs peak; time-to-spectrum, mixed vs FP64 at 0.1 meV"
+# FP64 FMA peak of GB300 derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the direct-term kernel from the committed ncu capture
+# (profiles/), keyed by workload; None until a capture of the current kernel exists.
+DIRECT_TRAFFIC = {"si8": 44.935168e6 + 1211.345e6}   # profiles/direct_fp64_si8.md
+WORKLOADS = {
+    "si8": "Si-like diamond (Oh, a=10.26 bohr), Gamma-centred 8x8x8 mesh, Nv=4, Nc=6, |G|<=3.2 (2pi/a); "
+           "T1u block of the full dim 12288",
+    "si4": "Si-like diamond (Oh), 4x4x4 mesh, Nv=Nc=4, |G|<=3.2 (2pi/a); T1u block of the full dim 1024",
+    "si12": "Si-like diamond (Oh), 12x12x12 mesh, Nv=4, Nc=8, |G|<=4.0 (2pi/a); T1u block of the full dim 55296",
+    "lif10": "LiF-like rocksalt (Oh, a=7.6 bohr), 10x10x10 mesh, Nv=3, Nc=6; T1u block of the full dim 18000",
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", default="si8")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="approximate size of the oracle sample (CPU seconds)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="run exactly one step (no warm-up, no end-to-end leg) for profiler captures")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, uuid):
+        q = ("clocks.sm,clocks.max.sm,utilization.gpu," +
+             ",".join("clocks_event_reasons." + r for r in REASONS))
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", uuid, "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        out, _ = self.p.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 3 + len(REASONS):
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), float(f[2]), f[3:3 + len(REASONS)]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        busy = [r for r in rows if r[2] >= 50] or rows
+        reasons = sorted({REASONS[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_busy": len(busy)}
+
+
+# ---------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_plan(config: str, cpu_seconds: float):
+    """Seeded star pairs of the workload whose k-pair count fits the budget
+    (about 4 ms of oracle time per k pair on one core)."""
+    import numpy as np
+    from oracle.tables import Group, MeshTables
+    from synth import generate
+    d = generate(config)
+    mt = MeshTables(Group(d["rot"], d["tau"], d["lattice"]), d["mesh"])
+    rng = np.random.default_rng(2026)
+    ns = len(mt.stars)
+    pairs, npairs = [], 0
+    target = max(100, int(cpu_seconds / 4e-3))
+    for _ in range(10000):
+        a, b = sorted(int(x) for x in rng.integers(0, ns, 2))
+        if (a, b) in pairs:
+            continue
+        n = len(mt.stars[a]) * len(mt.stars[b])
+        if npairs + n > target and pairs:
+            continue
+        pairs.append((a, b))
+        npairs += n
+        if npairs >= 0.8 * target:
+            break
+    return pairs
+
+
+def oracle_sample_run(config: str, pairs, repeats: int = 1):
+    """Time the oracle on the sampled star-pair blocks of the bright irrep
+    (set-up of its tables and basis excluded); returns one (seconds,
+    algorithmic flops of the sample, k pairs) per repeat."""
+    import json as _json
+    import numpy as np
+    from oracle.hamiltonian import Inputs, hamiltonian_block, head_correction
+    from oracle.projection import Basis
+    from oracle.tables import Group, MeshTables
+    from synth import generate
+    d = generate(config)
+    inp = Inputs(d)
+    grp = Group(d["rot"], d["tau"], d["lattice"])
+    mt = MeshTables(grp, d["mesh"])
+    b = Basis(inp, grp, mt)
+    mu = b.bright()[0]
+    U, owner = b.basis(mu)
+    gold = _json.load(open(os.path.join(ROOT, "tests", "golden", "wdiv.json")))
+    wd = gold[config] if config in gold else head_correction(inp)
+    star_of_col = np.array([mt.star_of[b.orbits[o][0] // (inp.nv * inp.nc)] for o in owner])
+    B = inp.nv * inp.nc
+    nv, nc = inp.nv, inp.nc
+    # algorithmic work of the sample (same definition as the library's count)
+    flops, kpairs = 0.0, 0
+    for a, c in pairs:
+        for i, k in enumerate(mt.stars[a]):
+            for j, kp in enumerate(mt.stars[c]):
+                if a == c and j < i:
+                    continue
+                q, fold = mt.minus(int(k), int(kp))
+                ng, npk = int(inp.ngc[q]), int(inp.nkc[kp])
+                tgt = inp.gk[kp, None, :npk, :] + inp.gq[q, :ng, None, :] + fold
+                novl = int(np.sum(inp.index_in_sphere(int(k), tgt) >= 0))
+                flops += 8.0 * ((nc * nc + nv * nv) * novl + nv * nv * ng * ng + nc * nc * nv * nv * ng)
+                kpairs += 1
+        ca, cb = np.nonzero(star_of_col == a)[0], np.nonzero(star_of_col == c)[0]
+        no = np.array([len(b.orbits[o]) for o in owner])
+        flops += 8.0 * (len(mt.stars[a]) * B * no[cb].sum() + no[ca].sum() * len(cb))
+        flops += 8.0 * len(ca) * len(cb) * int(inp.ngc[0])
+    out = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        for a, c in pairs:
+            rows = np.concatenate([np.arange(k * B, (k + 1) * B) for k in mt.stars[a]])
+            cols = np.concatenate([np.arange(k * B, (k + 1) * B) for k in mt.stars[c]])
+            ca, cb = np.nonzero(star_of_col == a)[0], np.nonzero(star_of_col == c)[0]
+            Hab = hamiltonian_block(inp, mt, list(mt.stars[a]), list(mt.stars[c]), wd)
+            _ = U[np.ix_(rows, ca)].conj().T @ Hab @ U[np.ix_(cols, cb)]
+        out.append((time.perf_counter() - t0, flops, kpairs))
+    return out
+
+
+def _oracle_subprocess(config, cpu_seconds, repeats=1):
+    """Run the oracle sample in a fresh (spawned) interpreter pinned to one
+    BLAS thread; returns a list of (seconds, flops, k pairs)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "p = bench.oracle_sample_plan(%r, %r); "
+            "print(json.dumps(bench.oracle_sample_run(%r, p, %d) + [p]))"
+            % (ROOT, config, cpu_seconds, config, repeats))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out[:-1], out[-1]
+
+
+def cpu_baseline(config, cpu_seconds):
+    runs, plan = _oracle_subprocess(config, cpu_seconds)
+    sec, flops, kp = runs[0]
+    return {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "%d star-pair blocks of the T1u block (%d unordered k pairs: direct, exchange, "
+                      "projection), oracle tables and basis set-up excluded; %.1f s on one host core"
+                      % (len(plan), kp, sec)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2603_24860_gb300 import bse
+    from synth import generate
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    inp = generate(args.config)
+    devin = {k: torch.from_numpy(np.array(inp[k])).to(dev) for k in ("coef", "eps", "w")}
+    omega = torch.tensor(inp["omega"], device=dev)
+    eta = float(inp["eta"])
+
+    # untimed discovery: the bright irrep, its dimension and the algorithmic work
+    ctx = bse.bse_create(inp, stream=stream, device=devin)
+    tab = bse.bse_tables(ctx)
+    mu = int(np.nonzero(tab["bright"])[0][0])
+    dim = int(tab["block_dim"][mu])
+    work = bse.bse_build_work(ctx, mu)
+    launches_base = bse.bse_get_stats(ctx)["launches"]
+    bse.bse_destroy(ctx)
+    flops_build = work["rho"] + work["contract"] + work["project"] + work["exchange"]
+    flops_direct = work["rho"] + work["contract"]
+
+    H = torch.empty(dim * dim, dtype=torch.complex128, device=dev)
+    om = torch.empty(dim, dtype=torch.float64, device=dev)
+    osc = torch.empty(dim, dtype=torch.float64, device=dev)
+    im = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def step(host_inputs=None, d2h=None):
+        ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
+                             device=None if host_inputs is not None else devin)
+        bse.bse_set_timing(ctx, True)
+        bse.bse_build_block(ctx, mu, bse.BSE_FP64, bse.BSE_TERM_ALL, H, dim)
+        s1 = bse.bse_get_stats(ctx)
+        bse.bse_block_spectrum(ctx, mu, H, dim, omega, eta, om, osc, im)
+        s2 = bse.bse_get_stats(ctx)
+        if d2h is not None:
+            for src, dst in zip((om, osc, im), d2h):
+                dst.copy_(src, non_blocking=True)
+        return ctx, s1, s2
+
+    def timed(n, host_inputs=None, d2h=None):
+        per, stats = [], []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx, s1, s2 = step(host_inputs, d2h)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+            stats.append((s1, s2))
+            bse.bse_destroy(ctx)
+        return per, stats
+
+    if args.profile:
+        per, stats = timed(1)
+        return {"profile": args.config, "ms": per[0], "stage_ms": stats[0][0], "block_dim": dim}
+    _, warm = timed(args.warmup)
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid)
+    barrier(world)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    per, stats = timed(args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - w0
+    clocks = sampler.stop()
+    # the library's launch counter is process-wide; read at the end of each step
+    launches = stats[-1][1]["launches"] - (warm[-1][1]["launches"] if warm else launches_base)
+    total_ms = max_over_ranks(sum(per), world)
+
+    # end to end through host buffers: H2D of the inputs and D2H of the results each step
+    pin = {}
+    for k, v in inp.items():
+        if isinstance(v, np.ndarray) and k in ("coef", "eps", "w"):
+            t = torch.empty(v.shape, dtype=torch.from_numpy(v[:0].copy()).dtype, pin_memory=True)
+            t.numpy()[...] = v
+            pin[k] = t.numpy()
+    host_inputs = dict(inp)
+    host_inputs.update(pin)
+    outs = [torch.empty(x.numel(), dtype=x.dtype, pin_memory=True) for x in (om, osc, im)]
+    timed(1, host_inputs, outs)
+    barrier(world)
+    e2e_per, _ = timed(args.steps, host_inputs, outs)
+    barrier(world)
+    e2e_ms = max_over_ranks(sum(e2e_per), world)
+    h2d = sum(int(np.asarray(inp[k]).nbytes) for k in ("coef", "eps", "w", "gk", "gq", "nk_count",
+                                                         "ng_count", "rot", "tau"))
+    d2h = sum(x.numel() * x.element_size() for x in outs)
+
+    ms_direct = statistics.mean(s[0]["ms_direct"] for s in stats)
+    ms_project = statistics.mean(s[0]["ms_project"] for s in stats)
+    ms_exchange = statistics.mean(s[0]["ms_exchange"] for s in stats)
+    ms_eig = statistics.mean(s[1]["ms_eig"] for s in stats)
+    direct_launches = stats[0][0]["direct_launches"]
+    achieved = flops_direct / (ms_direct * 1e-3) / 1e12
+    value = flops_build * args.steps * world / (total_ms * 1e-3) / 1e12
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "TFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
+                   "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
+                   "block_dim": dim, "full_dim": int(tab["n_product"]), "precision": "fp64",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MiB buffer written between timed steps (outside the step events)",
+                   "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
+        "time_to_spectrum_ms": total_ms / args.steps,
+        "stage_ms": {"direct": ms_direct, "project": ms_project, "exchange": ms_exchange, "eigensolve": ms_eig},
+        "build_flops": flops_build,
+        "work": {k: work[k] for k in ("rho", "contract", "project", "exchange", "overlap")},
+        "build_tflops_kernels": flops_build / ((ms_direct + ms_project + ms_exchange) * 1e-3) / 1e12,
+        "roofline": {"bound": "alu", "kernel": "direct_fp64_kernel", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure "
+                                    "in MEASURED_PEAKS.json)",
+                     "flops_per_launch": flops_direct / max(direct_launches, 1),
+                     "launches_per_step": direct_launches,
+                     "traffic": DIRECT_TRAFFIC.get(args.config)},
+        "e2e": {"value": flops_build * args.steps * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.config, args.cpu_seconds)
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the machine's host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sec_per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    runs, plan = _oracle_subprocess(args.config, sec_per_step, repeats=args.warmup + args.steps)
+    timed = runs[args.warmup:]
+    tot = sum(r[0] for r in timed)
+    flops = sum(r[1] for r in timed)
+    value = flops / tot / 1e12
+    kp = timed[0][2]
+    return {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: %d star-pair blocks (%d unordered k pairs) of the T1u block "
+                                   "by the FP64 oracle on one host core" % (len(plan), kp)},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

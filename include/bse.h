@@ -204,6 +204,47 @@ int bse_block_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t l
 /* Wait for all work on the context's stream; returns ECUDA on a device error. */
 int bse_sync(bse_ctx* ctx);
 
+/*
+ * Measurement support (not part of the paper's method).
+ *
+ * bse_work: algorithmic work of one bse_build_block, in real flops with a
+ * complex multiply-add counted as 8, over the unordered pairs of k stars the
+ * build visits (a <= b, and k <= k' inside a star):
+ *   rho      = 8 (Nc^2 + Nv^2) sum_pairs n_ovl(k,k'),  n_ovl = #{(p', Q):
+ *              p' in S_k', Q in S_q, p' + Q in S_k}
+ *   contract = 8 sum_pairs (Nv^2 NG(q)^2 + Nc^2 Nv^2 NG(q))
+ *   project  = 8 sum_tiles (|a| B sum_{j in b} n_o(j) + sum_{i in a} n_o(i) m_b)
+ *   exchange = 8 (sum_i n_o(i) NG0 + sum_tiles m_a m_b NG0)
+ * bse_build_work runs a counting kernel and blocks until it has finished.
+ */
+typedef struct {
+    double rho, contract, project, exchange;
+    int64_t k_pairs;       /* unordered k pairs of the direct term */
+    int64_t overlap;       /* sum over those pairs of n_ovl */
+    int64_t tiles;         /* star-pair tiles */
+} bse_work;
+
+int bse_build_work(bse_ctx* ctx, int32_t irrep, bse_work* out);
+
+/*
+ * bse_stats: kernel launches of this library in the process so far, and,
+ * when timing is on (bse_set_timing), the device time of the stages of the
+ * last bse_build_block / bse_block_spectrum measured with CUDA events on the
+ * context's stream.  bse_get_stats synchronises that stream.
+ */
+typedef struct {
+    int64_t launches;           /* process-wide count of this library's kernel launches */
+    int64_t direct_launches;    /* direct-term kernel launches of the last build */
+    float ms_direct;            /* direct-term kernel(s) of the last build */
+    float ms_project;           /* both projection stages of the last build */
+    float ms_exchange;          /* exchange projection of the last build */
+    float ms_eig;               /* dense eigensolver of the last spectrum */
+    float ms_spectrum;          /* oscillator strengths and Im eps of the last spectrum */
+} bse_stats;
+
+int bse_set_timing(bse_ctx* ctx, int32_t on);
+int bse_get_stats(bse_ctx* ctx, bse_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,17 @@ class BseTablesView(C.Structure):
     ]
 
 
+class BseWork(C.Structure):
+    _fields_ = [("rho", C.c_double), ("contract", C.c_double), ("project", C.c_double),
+                ("exchange", C.c_double), ("k_pairs", C.c_int64), ("overlap", C.c_int64), ("tiles", C.c_int64)]
+
+
+class BseStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("direct_launches", C.c_int64), ("ms_direct", C.c_float),
+                ("ms_project", C.c_float), ("ms_exchange", C.c_float), ("ms_eig", C.c_float),
+                ("ms_spectrum", C.c_float)]
+
+
 EXPORTS = {
     "bse_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(BseSystem), C.c_void_p]),
     "bse_destroy": (C.c_int, [C.c_void_p]),
@@ -64,6 +75,9 @@ EXPORTS = {
     "bse_block_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_sync": (C.c_int, [C.c_void_p]),
+    "bse_build_work": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(BseWork)]),
+    "bse_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_get_stats": (C.c_int, [C.c_void_p, C.POINTER(BseStats)]),
 }
 
 _lib = None
@@ -242,6 +256,22 @@ def bse_block_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float, 
 
 def bse_sync(ctx: Context):
     _check(lib().bse_sync(ctx.handle))
+
+
+def bse_build_work(ctx: Context, irrep: int) -> dict:
+    w = BseWork()
+    _check(lib().bse_build_work(ctx.handle, irrep, C.byref(w)))
+    return {f: getattr(w, f) for f, _ in BseWork._fields_}
+
+
+def bse_set_timing(ctx: Context, on: bool):
+    _check(lib().bse_set_timing(ctx.handle, 1 if on else 0))
+
+
+def bse_get_stats(ctx: Context) -> dict:
+    s = BseStats()
+    _check(lib().bse_get_stats(ctx.handle, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in BseStats._fields_}
 
 
 # ---------------------------------------------------------------------------

@@ -77,9 +77,82 @@ struct bse_ctx {
     DevBuf B;            // dipoles [N]
     bool B_ready = false;
     // scratch (library-owned, grow-only)
-    DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum;
+    DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum, counter;
     cusolverDnHandle_t solver = nullptr;
+    // measurement
+    bool timing = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bse_stats stats{};
 };
+
+namespace {
+
+// star-pair tiles of one irrep, grouped into batches whose X and Y arenas fit a budget
+struct Batch {
+    std::vector<TileTask> tiles;
+    std::vector<PairTask> tasks;
+    size_t xbytes = 0, ybytes = 0;
+    int64_t max_rows = 0, max_ca = 0, max_cb = 0;
+};
+
+size_t arena_budget() {
+    const char* env = std::getenv("BSE_ARENA_MB");
+    return (size_t)(env ? std::atoll(env) : 2048) << 20;
+}
+
+void plan_batches(const Tables& t, const Basis& bh, size_t budget, std::vector<Batch>& out) {
+    out.clear();
+    std::vector<int> act;
+    for (size_t a = 0; a < t.stars.size(); ++a)
+        if (bh.star_col[a + 1] > bh.star_col[a]) act.push_back((int)a);
+    const int B = t.B;
+    Batch cur;
+    for (size_t iA = 0; iA < act.size(); ++iA)
+        for (size_t iB = iA; iB < act.size(); ++iB) {
+            int a = act[iA], b = act[iB];
+            int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
+            int64_t mb = bh.star_col[b + 1] - bh.star_col[b];
+            size_t xs = sizeof(double2) * rows * cols, ys = sizeof(double2) * rows * mb;
+            if (!cur.tiles.empty() && (cur.xbytes + xs > budget || cur.ybytes + ys > budget)) {
+                out.push_back(std::move(cur));
+                cur = Batch();
+            }
+            TileTask tt;
+            tt.xoff = (int64_t)(cur.xbytes / sizeof(double2));
+            tt.yoff = (int64_t)(cur.ybytes / sizeof(double2));
+            tt.rows = (int32_t)rows;
+            tt.cols = (int32_t)cols;
+            tt.star_a = a;
+            tt.star_b = b;
+            tt.ca0 = bh.star_col[a];
+            tt.ca1 = bh.star_col[a + 1];
+            tt.cb0 = bh.star_col[b];
+            tt.cb1 = bh.star_col[b + 1];
+            cur.tiles.push_back(tt);
+            const auto& sa = t.stars[a];
+            const auto& sb = t.stars[b];
+            for (size_t i = 0; i < sa.size(); ++i)
+                for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
+                    PairTask p;
+                    p.k = sa[i];
+                    p.kp = sb[j];
+                    p.row0 = (int32_t)(i * B);
+                    p.col0 = (int32_t)(j * B);
+                    p.xoff = tt.xoff;
+                    p.ld = (int32_t)rows;
+                    p.flags = (a == b && j > i) ? 1 : 0;
+                    cur.tasks.push_back(p);
+                }
+            cur.xbytes += xs;
+            cur.ybytes += ys;
+            cur.max_rows = std::max(cur.max_rows, rows);
+            cur.max_ca = std::max(cur.max_ca, tt.ca1 - tt.ca0);
+            cur.max_cb = std::max(cur.max_cb, mb);
+        }
+    if (!cur.tiles.empty()) out.push_back(std::move(cur));
+}
+
+}  // namespace
 
 static DevBasis dev_basis(bse_ctx* c, int mu) {
     IrrepDev& d = c->irr[mu];
@@ -404,6 +477,9 @@ static void free_ctx(bse_ctx* c) {
         release(d.coef);
     }
     if (c->solver) cusolverDnDestroy(c->solver);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    release(c->counter);
     delete c;
 }
 
@@ -519,81 +595,50 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
     if (dim == 0) return BSE_OK;
     DevBasis db = dev_basis(c, mu);
     const double2* Pmu = nullptr;
+    if (c->timing) c->stats.ms_exchange = 0.f;
     if (terms & BSE_TERM_EXCHANGE) {
         BSE_TRY(ensure_exchange_vectors(c));
         BSE_TRY(ensure(c->Pmu, sizeof(double2) * (size_t)dim * c->ng0));
+        if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
         BSE_TRY(launch_exchange_project(db, (const double2*)c->P.p, c->ng0, (double2*)c->Pmu.p, c->stream));
+        if (c->timing) {
+            BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
+            BSE_CUDA(cudaEventSynchronize(c->ev[4]));
+            BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_exchange, c->ev[3], c->ev[4]));
+        }
         Pmu = (const double2*)c->Pmu.p;
     }
-    // star pairs (a <= b) whose stars carry basis vectors of this irrep
-    std::vector<int> act;
-    for (size_t a = 0; a < t.stars.size(); ++a)
-        if (bh.star_col[a + 1] > bh.star_col[a]) act.push_back((int)a);
-    const char* env = std::getenv("BSE_ARENA_MB");
-    const size_t budget = (size_t)(env ? std::atoll(env) : 2048) << 20;
-    const int B = t.B;
-    size_t iA = 0, iB = 0;
-    while (iA < act.size()) {
-        std::vector<TileTask> tiles;
-        std::vector<PairTask> tasks;
-        size_t xo = 0, yo = 0;
-        int64_t max_rows = 0, max_ca = 0, max_cb = 0;
-        while (iA < act.size()) {
-            int a = act[iA], b = act[iB];
-            int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
-            int64_t mb = bh.star_col[b + 1] - bh.star_col[b];
-            size_t xs = sizeof(double2) * rows * cols, ys = sizeof(double2) * rows * mb;
-            if (!tiles.empty() && (xo + xs > budget || yo + ys > budget)) break;
-            TileTask tt;
-            tt.xoff = (int64_t)(xo / sizeof(double2));
-            tt.yoff = (int64_t)(yo / sizeof(double2));
-            tt.rows = (int32_t)rows;
-            tt.cols = (int32_t)cols;
-            tt.star_a = a;
-            tt.star_b = b;
-            tt.ca0 = bh.star_col[a];
-            tt.ca1 = bh.star_col[a + 1];
-            tt.cb0 = bh.star_col[b];
-            tt.cb1 = bh.star_col[b + 1];
-            tiles.push_back(tt);
-            const auto& sa = t.stars[a];
-            const auto& sb = t.stars[b];
-            for (size_t i = 0; i < sa.size(); ++i)
-                for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
-                    PairTask p;
-                    p.k = sa[i];
-                    p.kp = sb[j];
-                    p.row0 = (int32_t)(i * B);
-                    p.col0 = (int32_t)(j * B);
-                    p.xoff = tt.xoff;
-                    p.ld = (int32_t)rows;
-                    p.flags = (a == b && j > i) ? 1 : 0;
-                    tasks.push_back(p);
-                }
-            xo += xs;
-            yo += ys;
-            max_rows = std::max(max_rows, rows);
-            max_ca = std::max(max_ca, tt.ca1 - tt.ca0);
-            max_cb = std::max(max_cb, mb);
-            if (++iB == act.size()) {
-                ++iA;
-                iB = iA;
-            }
-        }
-        BSE_TRY(ensure(c->arenaX, xo));
-        BSE_TRY(ensure(c->arenaY, yo));
-        BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
-        BSE_TRY(upload(c->tiles, tiles.data(), tiles.size(), c->stream));
-        BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), (double2*)c->arenaX.p, terms,
-                              c->w_div, c->stream));
-        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)tiles.size(), nullptr,
-                                     (const double2*)c->arenaX.p, (double2*)c->arenaY.p, max_rows, max_cb,
+    std::vector<Batch> batches;
+    plan_batches(t, bh, arena_budget(), batches);
+    if (c->timing) {
+        c->stats.ms_direct = c->stats.ms_project = 0.f;
+        c->stats.direct_launches = 0;
+    }
+    for (const Batch& bt : batches) {
+        BSE_TRY(ensure(c->arenaX, bt.xbytes));
+        BSE_TRY(ensure(c->arenaY, bt.ybytes));
+        BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
+        BSE_TRY(upload(c->tiles, bt.tiles.data(), bt.tiles.size(), c->stream));
+        if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
+        BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(), (double2*)c->arenaX.p,
+                              terms, c->w_div, c->stream));
+        if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[1], c->stream));
+        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), nullptr,
+                                     (const double2*)c->arenaX.p, (double2*)c->arenaY.p, bt.max_rows, bt.max_cb,
                                      c->stream));
-        BSE_TRY(launch_project_left(db, (const TileTask*)c->tiles.p, (int)tiles.size(), (const double2*)c->arenaY.p,
+        BSE_TRY(launch_project_left(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), (const double2*)c->arenaY.p,
                                     Pmu, (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol, (double2*)h, ld,
-                                    max_ca, max_cb, c->stream));
-        // the next batch reuses the task buffers; host vectors go out of scope
-        BSE_CUDA(cudaStreamSynchronize(c->stream));
+                                    bt.max_ca, bt.max_cb, c->stream));
+        if (c->timing) {
+            BSE_CUDA(cudaEventRecord(c->ev[2], c->stream));
+            BSE_CUDA(cudaEventSynchronize(c->ev[2]));
+            float a = 0.f, b = 0.f;
+            BSE_CUDA(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+            BSE_CUDA(cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+            c->stats.ms_direct += a;
+            c->stats.ms_project += b;
+            c->stats.direct_launches += 1;
+        }
     }
     return BSE_OK;
 }
@@ -647,17 +692,96 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
         return fail(BSE_ESOLVER, "zheevd buffer size query failed");
     BSE_TRY(ensure(c->eigWork, sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1)));
     BSE_TRY(ensure(c->info, sizeof(int)));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
     if (cusolverDnZheevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)dim,
                          (cuDoubleComplex*)c->eigA.p, (int)dim, omega_out, (cuDoubleComplex*)c->eigWork.p, lwork,
                          (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
         return fail(BSE_ESOLVER, "zheevd launch failed");
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     BSE_TRY(launch_oscillators((const double2*)c->eigA.p, dim, dim, (const double2*)c->Bmu.p, osc, c->stream));
     BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, 4.0 * M_PI * c->spin / c->t.nk, im_eps,
                             c->stream));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[5], c->stream));
     int info = 0;
     BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BSE_CUDA(cudaStreamSynchronize(c->stream));
     if (info != 0) return fail(BSE_ESOLVER, "zheevd info = %d", info);
+    if (c->timing) {
+        BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
+        BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
+    }
+    return BSE_OK;
+}
+
+int bse_set_timing(bse_ctx* c, int32_t on) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null argument");
+    if (on && !c->ev[0])
+        for (auto& e : c->ev) BSE_CUDA(cudaEventCreate(&e));
+    c->timing = on != 0;
+    return BSE_OK;
+}
+
+int bse_get_stats(bse_ctx* c, bse_stats* out) {
+    clear_error();
+    if (!c || !out) return fail(BSE_EINVAL, "null argument");
+    if (c->timing) BSE_CUDA(cudaStreamSynchronize(c->stream));
+    *out = c->stats;
+    out->launches = launches_total();
+    return BSE_OK;
+}
+
+int bse_build_work(bse_ctx* c, int32_t mu, bse_work* out) {
+    clear_error();
+    if (!c || !out) return fail(BSE_EINVAL, "null argument");
+    BSE_TRY(ensure_basis(c, mu));
+    const Tables& t = c->t;
+    const Basis& bh = c->irr[mu].host;
+    *out = bse_work{};
+    if (bh.dim == 0) return BSE_OK;
+    std::vector<Batch> batches;
+    plan_batches(t, bh, arena_budget(), batches);
+    auto n_o = [&](int64_t j) -> double {
+        int o = bh.col_orbit[j];
+        return (double)(t.orbit_off[o + 1] - t.orbit_off[o]);
+    };
+    const double nv = t.nv, nc = t.nc;
+    double sum_ng = 0, sum_ng2 = 0, proj = 0, exch_tiles = 0;
+    BSE_TRY(ensure(c->counter, sizeof(unsigned long long)));
+    BSE_CUDA(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned long long), c->stream));
+    for (const Batch& bt : batches) {
+        for (const PairTask& p : bt.tasks) {
+            int iq[3];
+            for (int a = 0; a < 3; ++a) iq[a] = (t.kidx[3 * p.k + a] - t.kidx[3 * p.kp + a] + t.n[a]) % t.n[a];
+            int q = (iq[0] * t.n[1] + iq[1]) * t.n[2] + iq[2];
+            double ng = c->ng[q];
+            sum_ng += ng;
+            sum_ng2 += ng * ng;
+        }
+        for (const TileTask& tt : bt.tiles) {
+            double sb = 0, sa = 0;
+            for (int64_t j = tt.cb0; j < tt.cb1; ++j) sb += n_o(j);
+            for (int64_t i = tt.ca0; i < tt.ca1; ++i) sa += n_o(i);
+            double mb = (double)(tt.cb1 - tt.cb0), ma = (double)(tt.ca1 - tt.ca0);
+            proj += tt.rows * sb + sa * mb;
+            exch_tiles += ma * mb;
+        }
+        out->k_pairs += (int64_t)bt.tasks.size();
+        out->tiles += (int64_t)bt.tiles.size();
+        BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
+        BSE_TRY(launch_count_overlap(c->S, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(),
+                                     (unsigned long long*)c->counter.p, c->stream));
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    unsigned long long ov = 0;
+    BSE_CUDA(cudaMemcpy(&ov, c->counter.p, sizeof(ov), cudaMemcpyDeviceToHost));
+    double pmu = 0;
+    for (int64_t i = 0; i < bh.dim; ++i) pmu += n_o(i);
+    out->overlap = (int64_t)ov;
+    out->rho = 8.0 * (nc * nc + nv * nv) * (double)ov;
+    out->contract = 8.0 * (nv * nv * sum_ng2 + nc * nc * nv * nv * sum_ng);
+    out->project = 8.0 * proj;
+    out->exchange = 8.0 * (pmu + exch_tiles) * c->ng0;
     return BSE_OK;
 }
 

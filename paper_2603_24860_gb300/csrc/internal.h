@@ -168,5 +168,8 @@ int launch_spectrum(const double* Om, const double* osc, int64_t dim, const doub
 int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax,
                 double delta, double* partial, int64_t npartial_max, double* out, cudaStream_t st);
 int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta);
+int launch_count_overlap(const DevSys& s, const PairTask* tasks, int64_t ntasks, unsigned long long* out,
+                         cudaStream_t st);
+int64_t launches_total();
 
 }  // namespace bse

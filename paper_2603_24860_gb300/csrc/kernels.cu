@@ -7,12 +7,17 @@
 // oscillatorA, reducible_polar (spectrum).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 
 #include "internal.h"
 
 namespace bse {
+
+// process-wide count of kernel launches made by this library
+static std::atomic<long long> g_launches{0};
+int64_t launches_total() { return g_launches.load(); }
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -37,6 +42,7 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 
 #define LAUNCH_CHECK()                                                                  \
     do {                                                                                \
+        g_launches.fetch_add(1);                                                        \
         cudaError_t e_ = cudaGetLastError();                                            \
         if (e_ != cudaSuccess)                                                          \
             return fail(BSE_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
@@ -712,6 +718,42 @@ int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, 
     LAUNCH_CHECK();
     reduce_kernel<<<1, 1024, 0, st>>>(partial, nblk, out);
     LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// algorithmic work: n_ovl(k,k') = #{(p', Q): p' in S_k', Q in S_q, p' + Q in S_k}
+// ---------------------------------------------------------------------------
+__global__ void count_overlap_kernel(DevSys S, const PairTask* __restrict__ tasks, unsigned long long* out) {
+    __shared__ unsigned long long red[256];
+    const PairTask t = tasks[blockIdx.x];
+    int fold[3];
+    const int q = mesh_minus(S, t.k, t.kp, fold);
+    const int ng = S.ng[q], npkp = S.npw[t.kp];
+    const int* gq = S.gq + (int64_t)q * S.ng_max * 3;
+    const int* gk = S.gk + (int64_t)t.kp * S.npw_max * 3;
+    unsigned long long c = 0;
+    for (int e = threadIdx.x; e < ng * npkp; e += blockDim.x) {
+        int g = e / npkp, j = e % npkp;
+        c += sphere_index(S, t.k, gk[3 * j] + gq[3 * g] + fold[0], gk[3 * j + 1] + gq[3 * g + 1] + fold[1],
+                          gk[3 * j + 2] + gq[3 * g + 2] + fold[2]) >= 0;
+    }
+    red[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+int launch_count_overlap(const DevSys& s, const PairTask* tasks, int64_t ntasks, unsigned long long* out,
+                         cudaStream_t st) {
+    for (int64_t off = 0; off < ntasks; off += 1 << 30) {
+        int64_t n = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
+        count_overlap_kernel<<<(unsigned)n, 256, 0, st>>>(s, tasks + off, out);
+        LAUNCH_CHECK();
+    }
     return BSE_OK;
 }
 
