@@ -245,6 +245,29 @@ typedef struct {
 int bse_set_timing(bse_ctx* ctx, int32_t on);
 int bse_get_stats(bse_ctx* ctx, bse_stats* out);
 
+/*
+ * bse_head_correction_noalloc - the head correction W^div of bse_create
+ * (b = 0.005) for a lattice (host [9], row-major, columns a1 a2 a3), a
+ * Gamma-centred mesh (host [3]) and a dielectric tensor (host [9]), written
+ * to w_div_dev (device, one double) on the given stream, without allocating
+ * any memory.  The paper has no counterpart; it exists for callers that
+ * cannot allocate device memory where they need the value (a framework that
+ * owns the device memory budget through its own pool, a latency-critical loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree, a
+ * plug-in handed only pre-allocated buffers).
+ * The partial sums live in a fixed device array of 65536 doubles (512 KiB)
+ * inside the library, held on every device that loads the library until the
+ * process exits; meshes whose lattice sum needs more partial sums are
+ * rejected with EINVAL.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents; nothing in it has to start at zero.  Calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it.
+ * Returns once the work is enqueued.
+ */
+int bse_head_correction_noalloc(const double* lattice, const int32_t* mesh, const double* eps_inf,
+                                double* w_div_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

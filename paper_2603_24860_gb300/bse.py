@@ -78,6 +78,7 @@ EXPORTS = {
     "bse_build_work": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(BseWork)]),
     "bse_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "bse_get_stats": (C.c_int, [C.c_void_p, C.POINTER(BseStats)]),
+    "bse_head_correction_noalloc": (C.c_int, [_PD, _P32, _PD, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -272,6 +273,17 @@ def bse_get_stats(ctx: Context) -> dict:
     s = BseStats()
     _check(lib().bse_get_stats(ctx.handle, C.byref(s)))
     return {f: getattr(s, f) for f, _ in BseStats._fields_}
+
+
+def bse_head_correction_noalloc(lattice, mesh, eps_inf, out, stream=None):
+    """W^div into the one-element float64 CUDA tensor ``out`` using the
+    library's fixed scratch (no device memory is allocated)."""
+    lat = np.ascontiguousarray(lattice, dtype=np.float64).ravel()
+    msh = np.ascontiguousarray(mesh, dtype=np.int32).ravel()
+    ein = np.ascontiguousarray(eps_inf, dtype=np.float64).ravel()
+    _check(lib().bse_head_correction_noalloc(lat.ctypes.data_as(_PD), msh.ctypes.data_as(_P32),
+                                             ein.ctypes.data_as(_PD), _ptr(out), _stream_handle(stream)))
+    return out
 
 
 # ---------------------------------------------------------------------------

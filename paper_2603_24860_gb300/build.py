@@ -1,6 +1,6 @@
 """Compile the CUDA library in-tree for sm_103a (nvcc, no CMake).
 
-The three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``libbse_gb300.so`` next to this file.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbse_gb300.so")
-SOURCES = ["host_tables.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["host_tables.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -247,6 +247,11 @@ static double h00(const double* L) {
     return acc / std::sqrt(4.0 * M_PI);
 }
 
+namespace bse {
+// H00 for callers outside this file
+double head_h00(const double* L) { return h00(L); }
+}  // namespace bse
+
 static int compute_wdiv(bse_ctx* c, const double* L) {
     const double b = 0.005;
     const double qmax = std::sqrt(-std::log(b) / b);
