@@ -31,11 +31,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "H-block build TFLOP/s vs peak; time-to-spectrum, mixed vs FP64 at 0.1 meV"
-# FP64 FMA peak of GB300 derived from the unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# ALU peaks of GB300 derived from the unit counts at the 2.07 GHz maximum SM clock:
+# 152 SMs x 2 DFMA/clk (FP64) or 128 FFMA/clk (FP32) x 2 flop
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+HA_MEV = 27211.386245988
 # DRAM bytes per launch of the direct-term kernel from the committed ncu capture
 # (profiles/), keyed by workload; None until a capture of the current kernel exists.
-DIRECT_TRAFFIC = {"si8": 44.935168e6 + 1211.345e6}   # profiles/direct_fp64_si8.md
+DIRECT_TRAFFIC = {("si8", "fp64"): 41.711872e6 + 1210.309e6,    # profiles/direct_kernel_si8.md
+                  ("si8", "fp32"): 13.125632e6 + 576.739072e6}
 WORKLOADS = {
     "si8": "Si-like diamond (Oh, a=10.26 bohr), Gamma-centred 8x8x8 mesh, Nv=4, Nc=6, |G|<=3.2 (2pi/a); "
            "T1u block of the full dim 12288",
@@ -52,6 +56,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--config", default="si8")
+    p.add_argument("--prec", choices=["fp32", "fp64"], default="fp32",
+                   help="precision of the direct term; the FP64 build is also timed for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="approximate size of the oracle sample (CPU seconds)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,11 +284,13 @@ def run_ours(args, rank, world, local):
     im = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    def step(host_inputs=None, d2h=None):
+    prec = bse.BSE_FP32 if args.prec == "fp32" else bse.BSE_FP64
+
+    def step(host_inputs=None, d2h=None, p=None):
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
                              device=None if host_inputs is not None else devin)
         bse.bse_set_timing(ctx, True)
-        bse.bse_build_block(ctx, mu, bse.BSE_FP64, bse.BSE_TERM_ALL, H, dim)
+        bse.bse_build_block(ctx, mu, prec if p is None else p, bse.BSE_TERM_ALL, H, dim)
         s1 = bse.bse_get_stats(ctx)
         bse.bse_block_spectrum(ctx, mu, H, dim, omega, eta, om, osc, im)
         s2 = bse.bse_get_stats(ctx)
@@ -291,14 +299,14 @@ def run_ours(args, rank, world, local):
                 dst.copy_(src, non_blocking=True)
         return ctx, s1, s2
 
-    def timed(n, host_inputs=None, d2h=None):
+    def timed(n, host_inputs=None, d2h=None, p=None):
         per, stats = [], []
         for _ in range(n):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx, s1, s2 = step(host_inputs, d2h)
+            ctx, s1, s2 = step(host_inputs, d2h, p)
             e1.record(stream)
             e1.synchronize()
             per.append(e0.elapsed_time(e1))
@@ -320,6 +328,7 @@ def run_ours(args, rank, world, local):
     barrier(world)
     wall = time.perf_counter() - w0
     clocks = sampler.stop()
+    om_main, im_main = om.cpu().numpy().copy(), im.cpu().numpy().copy()
     # the library's launch counter is process-wide; read at the end of each step
     launches = stats[-1][1]["launches"] - (warm[-1][1]["launches"] if warm else launches_base)
     total_ms = max_over_ranks(sum(per), world)
@@ -343,12 +352,24 @@ def run_ours(args, rank, world, local):
                                                          "ng_count", "rot", "tau"))
     d2h = sum(x.numel() * x.element_size() for x in outs)
 
+    # FP64 build of the same block for comparison (time to spectrum and accuracy)
+    cmp = None
+    if prec != bse.BSE_FP64:
+        timed(1, p=bse.BSE_FP64)
+        per64, stats64 = timed(max(1, min(args.steps, 3)), p=bse.BSE_FP64)
+        om64, im64 = om.cpu().numpy(), im.cpu().numpy()
+        cmp = {"ms_per_step": max_over_ranks(statistics.mean(per64), world),
+               "stage_ms": {"direct": statistics.mean(x[0]["ms_direct"] for x in stats64),
+                            "eigensolve": statistics.mean(x[1]["ms_eig"] for x in stats64)},
+               "max_dOmega_meV": float(np.abs(om_main - om64).max() * HA_MEV),
+               "spectrum_rel_l2": float(np.linalg.norm(im_main - im64) / np.linalg.norm(im64))}
     ms_direct = statistics.mean(s[0]["ms_direct"] for s in stats)
     ms_project = statistics.mean(s[0]["ms_project"] for s in stats)
     ms_exchange = statistics.mean(s[0]["ms_exchange"] for s in stats)
     ms_eig = statistics.mean(s[1]["ms_eig"] for s in stats)
     direct_launches = stats[0][0]["direct_launches"]
     achieved = flops_direct / (ms_direct * 1e-3) / 1e12
+    peak = FP32_PEAK_TFLOPS if prec == bse.BSE_FP32 else FP64_PEAK_TFLOPS
     value = flops_build * args.steps * world / (total_ms * 1e-3) / 1e12
     out = {
         "metric": METRIC,
@@ -361,11 +382,13 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32" if prec == bse.BSE_FP32 else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
                    "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
-                   "block_dim": dim, "full_dim": int(tab["n_product"]), "precision": "fp64",
+                   "block_dim": dim, "full_dim": int(tab["n_product"]),
+                   "precision": ("direct term FP32 on CUDA cores; diagonal, projection, exchange and "
+                                 "eigensolver FP64") if prec == bse.BSE_FP32 else "FP64 throughout",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
@@ -374,13 +397,14 @@ def run_ours(args, rank, world, local):
         "build_flops": flops_build,
         "work": {k: work[k] for k in ("rho", "contract", "project", "exchange", "overlap")},
         "build_tflops_kernels": flops_build / ((ms_direct + ms_project + ms_exchange) * 1e-3) / 1e12,
-        "roofline": {"bound": "alu", "kernel": "direct_fp64_kernel", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure "
-                                    "in MEASURED_PEAKS.json)",
+        "roofline": {"bound": "alu", "kernel": "direct_kernel<%s>" % ("float" if prec == bse.BSE_FP32 else "double"),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": ("derived: 152 SMs x %s x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
+                                     "CUDA-core figure)" % ("128 FFMA/clk" if prec == bse.BSE_FP32 else "2 DFMA/clk")),
                      "flops_per_launch": flops_direct / max(direct_launches, 1),
                      "launches_per_step": direct_launches,
-                     "traffic": DIRECT_TRAFFIC.get(args.config)},
+                     "traffic": DIRECT_TRAFFIC.get((args.config, args.prec))},
+        "fp64_build": cmp,
         "e2e": {"value": flops_build * args.steps * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},

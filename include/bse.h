@@ -55,7 +55,10 @@ enum {
     BSE_ESOLVER = -7       /* the dense eigensolver failed */
 };
 
-enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2 };
+/* precision of the direct term: FP64 throughout, or FP32 CUDA-core arithmetic
+   (pair densities and contractions; the diagonal, the projection and the
+   exchange stay FP64); the split BF16/FP16 tensor-core modes are reserved */
+enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2, BSE_FP32 = 3 };
 
 /* terms of H to include (bit mask) */
 enum { BSE_TERM_DIAG = 1, BSE_TERM_EXCHANGE = 2, BSE_TERM_DIRECT = 4, BSE_TERM_ALL = 7 };
@@ -158,8 +161,8 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  * once (Sec. III.C.5), the exchange term is applied in the projected form
  * (U_mu^dagger P) vbar (U_mu^dagger P)^dagger (Eq. v_scalar), the diagonal
  * eps_c - eps_v - W^div in FP64.  terms: BSE_TERM_* mask.
- * prec: BSE_FP64 (the only precision implemented so far; others return
- * EUNSUPPORTED).  h_dev: device, complex128, column-major dim x dim with
+ * prec: BSE_FP64 or BSE_FP32 (direct term on CUDA cores in FP32; the other
+ * stages stay FP64); the split modes return EUNSUPPORTED for now.  h_dev: device, complex128, column-major dim x dim with
  * leading dimension ld >= dim; the full Hermitian matrix is written.
  * Scratch is library-owned.
  */

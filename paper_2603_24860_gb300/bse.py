@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libbse_gb300.so")
 
 BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ECUDA, BSE_ESYMM, BSE_ETIMEOUT, BSE_EUNSUPPORTED, BSE_ESOLVER = (
     0, -1, -2, -3, -4, -5, -6, -7)
-BSE_FP64, BSE_BF16_SPLIT, BSE_FP16_SPLIT = 0, 1, 2
+BSE_FP64, BSE_BF16_SPLIT, BSE_FP16_SPLIT, BSE_FP32 = 0, 1, 2, 3
 BSE_TERM_DIAG, BSE_TERM_EXCHANGE, BSE_TERM_DIRECT, BSE_TERM_ALL = 1, 2, 4, 7
 BSE_BANDS_CC, BSE_BANDS_VV, BSE_BANDS_CV = 0, 1, 2
 

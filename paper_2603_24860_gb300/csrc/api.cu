@@ -76,6 +76,9 @@ struct bse_ctx {
     bool P_ready = false;
     DevBuf B;            // dipoles [N]
     bool B_ready = false;
+    DevBuf de;           // eps_c - eps_v per product index (FP64)
+    DevBuf coef32, w32;  // FP32 copies for the FP32 build, made on first use
+    bool narrow_ready = false;
     // scratch (library-owned, grow-only)
     DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum, counter;
     cusolverDnHandle_t solver = nullptr;
@@ -205,6 +208,18 @@ static int ensure_dipoles(bse_ctx* c) {
     return BSE_OK;
 }
 
+static int ensure_narrow(bse_ctx* c) {
+    if (c->narrow_ready) return BSE_OK;
+    const int64_t nc = (int64_t)c->t.nk * c->t.nb * c->S.npw_max;
+    const int64_t nw = (int64_t)c->t.nk * c->S.ng_max * c->S.ng_max;
+    BSE_TRY(ensure(c->coef32, sizeof(float2) * (size_t)nc));
+    BSE_TRY(ensure(c->w32, sizeof(float2) * (size_t)nw));
+    BSE_TRY(launch_narrow(c->S.coef, (float2*)c->coef32.p, nc, c->stream));
+    BSE_TRY(launch_narrow(c->S.w, (float2*)c->w32.p, nw, c->stream));
+    c->narrow_ready = true;
+    return BSE_OK;
+}
+
 // H00 = (1/sqrt(4 pi)) int dOmega 1/(q^T L q): closed form when L is isotropic,
 // otherwise Gauss-Legendre in cos(theta) times a periodic trapezoid in phi.
 static double h00(const double* L) {
@@ -302,6 +317,15 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     BSE_CUDA(cudaMemcpy(eps_h.data(), sys->eps, sizeof(double) * eps_h.size(), cudaMemcpyDefault));
     BSE_TRY(build_characters(t));
     BSE_TRY(build_multiplets_and_orbits(t, eps_h.data()));
+    {
+        std::vector<double> de((size_t)t.N);
+        for (int k = 0; k < nk; ++k)
+            for (int v = 0; v < t.nv; ++v)
+                for (int cc = 0; cc < t.nc; ++cc)
+                    de[((size_t)k * t.nv + v) * t.nc + cc] = eps_h[(size_t)k * nb + t.nv + cc] - eps_h[(size_t)k * nb + v];
+        BSE_TRY(upload(c->de, de.data(), de.size(), c->stream));
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+    }
     cudaStream_t st = c->stream;
     // device copies of the inputs
     BSE_TRY(upload(c->coef, reinterpret_cast<const double2*>(sys->coef), (size_t)nk * nb * sys->npw_max, st));
@@ -474,7 +498,7 @@ static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
-                      &c->info, &c->Bmu, &c->wpart, &c->wsum})
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -577,9 +601,15 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
             p.flags = kp > k ? 1 : 0;
             tasks.push_back(p);
         }
-    BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
-    BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), (double2*)h, terms, c->w_div,
-                          c->stream));
+    if (terms & BSE_TERM_DIRECT) {
+        BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
+        BSE_TRY(launch_direct(c->S, 0, c->S.coef, c->S.w, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), h,
+                              c->stream));
+    } else {
+        BSE_CUDA(cudaMemset2DAsync(h, sizeof(double2) * ld, 0, sizeof(double2) * t.N, t.N, c->stream));
+    }
+    if (terms & BSE_TERM_DIAG)
+        BSE_TRY(launch_diag_full((const double*)c->de.p, t.N, c->w_div, (double2*)h, ld, c->stream));
     if (terms & BSE_TERM_EXCHANGE) {
         BSE_TRY(ensure_exchange_vectors(c));
         BSE_TRY(launch_exchange_full((const double2*)c->P.p, (const double*)c->vbar.p, c->ng0, t.N,
@@ -591,7 +621,8 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
 int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    const int p32 = prec == BSE_FP32;
     BSE_TRY(ensure_basis(c, mu));
     const Tables& t = c->t;
     const Basis& bh = c->irr[mu].host;
@@ -613,6 +644,8 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
         }
         Pmu = (const double2*)c->Pmu.p;
     }
+    if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
+    const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
     std::vector<Batch> batches;
     plan_batches(t, bh, arena_budget(), batches);
     if (c->timing) {
@@ -620,20 +653,25 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
         c->stats.direct_launches = 0;
     }
     for (const Batch& bt : batches) {
-        BSE_TRY(ensure(c->arenaX, bt.xbytes));
+        BSE_TRY(ensure(c->arenaX, bt.xbytes / sizeof(double2) * xel));
         BSE_TRY(ensure(c->arenaY, bt.ybytes));
         BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
         BSE_TRY(upload(c->tiles, bt.tiles.data(), bt.tiles.size(), c->stream));
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
-        BSE_TRY(launch_direct(c->S, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(), (double2*)c->arenaX.p,
-                              terms, c->w_div, c->stream));
+        if (terms & BSE_TERM_DIRECT) {
+            BSE_TRY(launch_direct(c->S, p32, p32 ? c->coef32.p : (const void*)c->S.coef,
+                                  p32 ? c->w32.p : (const void*)c->S.w, (const PairTask*)c->tasks.p,
+                                  (int64_t)bt.tasks.size(), c->arenaX.p, c->stream));
+        } else {
+            BSE_CUDA(cudaMemsetAsync(c->arenaX.p, 0, bt.xbytes / sizeof(double2) * xel, c->stream));
+        }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[1], c->stream));
-        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), nullptr,
-                                     (const double2*)c->arenaX.p, (double2*)c->arenaY.p, bt.max_rows, bt.max_cb,
-                                     c->stream));
+        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), p32, c->arenaX.p,
+                                     (double2*)c->arenaY.p, bt.max_rows, bt.max_cb, c->stream));
         BSE_TRY(launch_project_left(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), (const double2*)c->arenaY.p,
-                                    Pmu, (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol, (double2*)h, ld,
-                                    bt.max_ca, bt.max_cb, c->stream));
+                                    Pmu, (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
+                                    (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
+                                    (double2*)h, ld, bt.max_ca, bt.max_cb, c->stream));
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[2], c->stream));
             BSE_CUDA(cudaEventSynchronize(c->ev[2]));

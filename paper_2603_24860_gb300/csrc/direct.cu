@@ -1,0 +1,243 @@
+// Direct term of the electron-hole Hamiltonian, one k pair per CTA, on CUDA
+// cores, in FP64 or FP32 (template over the real type R):
+//
+//   rho_nn'(k,k';Q) = sum_{p' in S_k'} conj(c_kn(p' + Q)) c_k'n'(p')     (Eq. w_interaction)
+//   T_vv'(Q)        = sum_Q' W_QQ'(q) conj(rho_vv'(Q'))
+//   K^d[(v,c),(v',c')] = 1/V sum_Q rho_cc'(Q) T_vv'(Q)                    (Eq. BSE-eigval)
+//
+// written as -K^d into a column-major tile (the diagonal eps_c - eps_v - W^div
+// is added in FP64 by the projection).  At q = 0 the head and wings of W are
+// dropped (Sec. III.B).
+//
+// The pair densities use compacted overlap lists: for each Q the plane waves
+// p' with p' + Q in S_k are gathered once (warp ballot), and a warp sweeps a
+// list with its lanes spread over band pairs, so every issued FMA is useful.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bse {
+
+template <typename R>
+struct C2;
+template <>
+struct C2<double> {
+    using T = double2;
+};
+template <>
+struct C2<float> {
+    using T = float2;
+};
+
+template <typename V>
+__device__ __forceinline__ void cmac(V& acc, V a, V b) {   // acc += a * b
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+template <typename V>
+__device__ __forceinline__ void cmacc(V& acc, V a, V b) {  // acc += conj(a) * b
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// shared-memory plan of one CTA
+struct DirectPlan {
+    size_t coef, cnt, list, stage, rho, T, total;
+};
+
+__host__ __device__ inline DirectPlan direct_plan(int cplx_bytes, int nb, int nv, int nc, int npw_max, int ng_max) {
+    DirectPlan p;
+    p.coef = al16((size_t)cplx_bytes * npw_max * nb);                 // one k
+    p.cnt = al16(sizeof(int) * (size_t)ng_max);
+    p.list = al16(sizeof(int) * (size_t)ng_max * npw_max);
+    p.stage = 2 * p.coef + p.cnt + p.list;
+    p.T = al16((size_t)cplx_bytes * ng_max * nv * nv);
+    p.rho = al16((size_t)cplx_bytes * ng_max * (nc * nc + nv * nv));
+    size_t region = p.stage > p.T ? p.stage : p.T;                     // T reuses the staging region
+    p.total = region + p.rho;
+    return p;
+}
+
+constexpr int kMaxSlots = 4;   // band pairs per lane: nc^2 + nv^2 <= 128
+
+template <typename R>
+__global__ void __launch_bounds__(256) direct_kernel(DevSys S, const typename C2<R>::T* __restrict__ coef,
+                                                     const typename C2<R>::T* __restrict__ wq,
+                                                     const PairTask* __restrict__ tasks, typename C2<R>::T* X) {
+    using V = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PairTask t = tasks[blockIdx.x];
+    const int nv = S.nv, nc = S.nc, nb = S.nb, B = nv * nc, P = nc * nc + nv * nv;
+    const DirectPlan pl = direct_plan((int)sizeof(V), nb, nv, nc, S.npw_max, S.ng_max);
+    V* ckT = (V*)smem;                                      // [npw][nb] at k
+    V* ckpT = (V*)(smem + pl.coef);                         // [npw][nb] at k'
+    int* cnt = (int*)(smem + 2 * pl.coef);                  // [ng]
+    int* list = (int*)(smem + 2 * pl.coef + pl.cnt);        // [ng][npw_max]: i | j << 16
+    V* T = (V*)smem;                                        // [ng][nv*nv], after rho
+    size_t region = pl.stage > pl.T ? pl.stage : pl.T;
+    V* rho = (V*)(smem + region);                           // [ng][P]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+
+    // q = k - k' and the fold f_k' + f_q - f_k
+    int fold[3], iq[3];
+    const int n[3] = {S.n1, S.n2, S.n3};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int ik = S.kidx[3 * t.k + a], ikp = S.kidx[3 * t.kp + a];
+        iq[a] = (ik - ikp + n[a]) % n[a];
+        fold[a] = (ikp + iq[a] - ik) / n[a];
+    }
+    const int q = (iq[0] * S.n2 + iq[1]) * S.n3 + iq[2];
+    const int ng = S.ng[q], npk = S.npw[t.k], npkp = S.npw[t.kp];
+
+    // stage both coefficient sets, band fastest
+    for (int e = threadIdx.x; e < nb * S.npw_max; e += blockDim.x) {
+        int b = e / S.npw_max, i = e % S.npw_max;
+        ckT[i * nb + b] = coef[((int64_t)t.k * nb + b) * S.npw_max + i];
+        ckpT[i * nb + b] = coef[((int64_t)t.kp * nb + b) * S.npw_max + i];
+    }
+    // compacted overlap list of each Q: (i in S_k, j in S_k') with p'_j + Q = p_i
+    const int* gq = S.gq + (int64_t)q * S.ng_max * 3;
+    const int* gk = S.gk + (int64_t)t.kp * S.npw_max * 3;
+    for (int g = warp; g < ng; g += nwarp) {
+        int c = 0;
+        for (int j0 = 0; j0 < npkp; j0 += 32) {
+            int j = j0 + lane, idx = -1;
+            if (j < npkp) {
+                int x0 = gk[3 * j] + gq[3 * g] + fold[0] - S.blo[0];
+                int x1 = gk[3 * j + 1] + gq[3 * g + 1] + fold[1] - S.blo[1];
+                int x2 = gk[3 * j + 2] + gq[3 * g + 2] + fold[2] - S.blo[2];
+                if ((unsigned)x0 < (unsigned)S.bdim[0] && (unsigned)x1 < (unsigned)S.bdim[1] &&
+                    (unsigned)x2 < (unsigned)S.bdim[2])
+                    idx = S.box[(int64_t)t.k * S.bvol + ((int64_t)x0 * S.bdim[1] + x1) * S.bdim[2] + x2];
+            }
+            unsigned m = __ballot_sync(0xffffffffu, idx >= 0);
+            if (idx >= 0) list[g * S.npw_max + c + __popc(m & ((1u << lane) - 1u))] = idx | (j << 16);
+            c += __popc(m);
+        }
+        if (lane == 0) cnt[g] = c;
+    }
+    (void)npk;
+    __syncthreads();
+
+    // rho: one warp per Q, lanes over band pairs (cc' first, then vv')
+    int na[kMaxSlots], nbp[kMaxSlots];
+#pragma unroll
+    for (int s = 0; s < kMaxSlots; ++s) {
+        int p = lane + 32 * s;
+        if (p < nc * nc) {
+            na[s] = nv + p / nc;
+            nbp[s] = nv + p % nc;
+        } else if (p < P) {
+            na[s] = (p - nc * nc) / nv;
+            nbp[s] = (p - nc * nc) % nv;
+        } else {
+            na[s] = nbp[s] = -1;
+        }
+    }
+    for (int g = warp; g < ng; g += nwarp) {
+        V acc[kMaxSlots];
+#pragma unroll
+        for (int s = 0; s < kMaxSlots; ++s) acc[s].x = acc[s].y = R(0);
+        const int* L = list + g * S.npw_max;
+        const int len = cnt[g];
+        for (int e = 0; e < len; ++e) {
+            const int ij = L[e];
+            const V* a = ckT + (ij & 0xffff) * nb;
+            const V* b = ckpT + (ij >> 16) * nb;
+#pragma unroll
+            for (int s = 0; s < kMaxSlots; ++s)
+                if (na[s] >= 0) cmacc(acc[s], a[na[s]], b[nbp[s]]);
+        }
+#pragma unroll
+        for (int s = 0; s < kMaxSlots; ++s)
+            if (na[s] >= 0) rho[g * P + lane + 32 * s] = acc[s];
+    }
+    __syncthreads();
+
+    // T[Q][vv'] = sum_Q' W_QQ'(q) conj(rho_vv'(Q')), head and wings dropped at q = 0
+    const int nvv = nv * nv, skip = (q == 0) ? S.g0 : -1;
+    const V* W = wq + (int64_t)q * S.ng_max * S.ng_max;
+    for (int e = threadIdx.x; e < ng * nvv; e += blockDim.x) {
+        const int Q = e / nvv, vv = e % nvv;
+        V acc;
+        acc.x = acc.y = R(0);
+        if (Q != skip) {
+            const V* wr = W + (int64_t)Q * S.ng_max;
+            for (int Qp = 0; Qp < ng; ++Qp) {
+                if (Qp == skip) continue;
+                V r = rho[Qp * P + nc * nc + vv];
+                r.y = -r.y;
+                cmac(acc, wr[Qp], r);
+            }
+        }
+        T[Q * nvv + vv] = acc;
+    }
+    __syncthreads();
+
+    // -K^d block, rows (v, c) fastest for coalesced column-major stores
+    V* Xt = X + t.xoff;
+    const R scale = R(-S.inv_vol);
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int r = e % B, col = e / B;
+        const int v = r / nc, c = r % nc, vp = col / nc, cp = col % nc;
+        V acc;
+        acc.x = acc.y = R(0);
+        for (int Q = 0; Q < ng; ++Q) cmac(acc, rho[Q * P + c * nc + cp], T[Q * nvv + v * nv + vp]);
+        acc.x *= scale;
+        acc.y *= scale;
+        Xt[(int64_t)(t.col0 + col) * t.ld + t.row0 + r] = acc;
+        if (t.flags & 1) {
+            V m = acc;
+            m.y = -m.y;
+            Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + col] = m;
+        }
+    }
+}
+
+template <typename R>
+static int launch_direct_t(const DevSys& s, const void* coef, const void* w, const PairTask* tasks, int64_t ntasks,
+                           void* X, cudaStream_t st) {
+    using V = typename C2<R>::T;
+    if (ntasks == 0) return BSE_OK;
+    if (s.nc * s.nc + s.nv * s.nv > 32 * kMaxSlots)
+        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", 32 * kMaxSlots);
+    if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
+    DirectPlan pl = direct_plan((int)sizeof(V), s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
+    if (pl.total > 227 * 1024) return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", pl.total);
+    cudaError_t e = cudaFuncSetAttribute(direct_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.total);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", pl.total, cudaGetErrorString(e));
+    for (int64_t off = 0; off < ntasks; off += 1 << 30) {
+        int64_t nt = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
+        direct_kernel<R><<<(unsigned)nt, 256, pl.total, st>>>(s, (const V*)coef, (const V*)w, tasks + off, (V*)X);
+        note_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(BSE_ECUDA, "direct launch: %s", cudaGetErrorString(e));
+    }
+    return BSE_OK;
+}
+
+int launch_direct(const DevSys& s, int prec32, const void* coef, const void* w, const PairTask* tasks, int64_t ntasks,
+                  void* X, cudaStream_t st) {
+    return prec32 ? launch_direct_t<float>(s, coef, w, tasks, ntasks, X, st)
+                  : launch_direct_t<double>(s, coef, w, tasks, ntasks, X, st);
+}
+
+// FP32 copies of the coefficients and of W (made once per context)
+__global__ void narrow_kernel(const double2* __restrict__ in, float2* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st) {
+    if (n == 0) return BSE_OK;
+    narrow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "narrow launch: %s", cudaGetErrorString(e));
+    return BSE_OK;
+}
+
+}  // namespace bse

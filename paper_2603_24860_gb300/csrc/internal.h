@@ -147,13 +147,18 @@ int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, co
                  const int* ent, int64_t n_ent, double2* out, cudaStream_t st);
 int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands,
                     int exchange_layout, double2* out, cudaStream_t st);
-int launch_direct(const DevSys& s, const PairTask* tasks, int64_t ntasks, double2* X,
-                  uint32_t terms, double w_div, cudaStream_t st);
-int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, const int* unused,
-                         const double2* X, double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
+// direct term (direct.cu): prec32 = 0 -> FP64 (coef/w double2, X double2), 1 -> FP32 (float2)
+int launch_direct(const DevSys& s, int prec32, const void* coef, const void* w, const PairTask* tasks,
+                  int64_t ntasks, void* X, cudaStream_t st);
+int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st);
+int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X,
+                         double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
+// de: eps_c - eps_v per product index (or null to skip the diagonal)
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y,
-                        const double2* Pmu, const double* vbar, int ng0, double xscale,
-                        double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
+                        const double2* Pmu, const double* vbar, int ng0, double xscale, const double* de,
+                        double w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
+int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st);
+void note_launch();
 int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
 int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
                          double2* H, int64_t ld, cudaStream_t st);

@@ -18,6 +18,7 @@ namespace bse {
 // process-wide count of kernel launches made by this library
 static std::atomic<long long> g_launches{0};
 int64_t launches_total() { return g_launches.load(); }
+void note_launch() { g_launches.fetch_add(1); }
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -253,127 +254,36 @@ int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs
 }
 
 // ---------------------------------------------------------------------------
-// direct term of one k pair, written into a column-major tile:
-//   X[(v,c),(v',c')] = -K^d + delta_{kk'} delta (eps_c - eps_v - W^div)
-//   K^d = 1/V sum_{Q,Q'} rho_cc'(Q) W_QQ'(q) conj(rho_vv'(Q'))   (Eq. BSE-eigval)
-// At q = 0 the head and wings of W are dropped (Sec. III.B).
-// ---------------------------------------------------------------------------
-__host__ __device__ inline size_t direct_smem(int nb, int nv, int nc, int npw_max, int ng_max) {
-    size_t st = stage_bytes(nb, npw_max, ng_max);
-    size_t t = align16(sizeof(double2) * (size_t)nv * nv * ng_max);
-    size_t a = st > t ? st : t;
-    return a + align16(sizeof(double2) * (size_t)nc * nc * ng_max) + align16(sizeof(double2) * (size_t)nv * nv * ng_max);
-}
-
-__global__ void __launch_bounds__(256) direct_fp64_kernel(DevSys S, const PairTask* __restrict__ tasks, double2* X,
-                                                          uint32_t terms, double w_div) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const PairTask t = tasks[blockIdx.x];
-    const int nv = S.nv, nc = S.nc, B = nv * nc;
-    size_t st = stage_bytes(S.nb, S.npw_max, S.ng_max);
-    size_t tb = align16(sizeof(double2) * (size_t)nv * nv * S.ng_max);
-    size_t region = st > tb ? st : tb;
-    PairStage P;
-    P.ck = (double2*)smem;
-    P.ckp = (double2*)(smem + align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
-    P.idx = (short*)(smem + 2 * align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
-    double2* T = (double2*)smem;   // reuses the staging region after rho is formed
-    double2* rc = (double2*)(smem + region);
-    double2* rv = (double2*)(smem + region + align16(sizeof(double2) * (size_t)nc * nc * S.ng_max));
-    double2* Xt = X + t.xoff;
-    const bool direct = (terms & BSE_TERM_DIRECT) != 0;
-    int ng = 0, q = 0;
-    if (direct) {
-        stage_pair(S, t.k, t.kp, P);
-        __syncthreads();
-        ng = P.ng;
-        q = P.q;
-        const int ncc = nc * nc, tot = (ncc + nv * nv) * ng;
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            int g = e % ng, ab = e / ng;
-            if (ab < ncc) rc[ab * S.ng_max + g] = rho_elem(S, P, nv + ab / nc, nv + ab % nc, g);
-            else {
-                int vv = ab - ncc;
-                rv[vv * S.ng_max + g] = rho_elem(S, P, vv / nv, vv % nv, g);
-            }
-        }
-        __syncthreads();
-        // T[vv'][Q] = sum_Q' W_QQ'(q) conj(rho_vv'(Q'))
-        const double2* W = S.w + (int64_t)q * S.ng_max * S.ng_max;
-        const int skip = (q == 0) ? S.g0 : -1;
-        for (int e = threadIdx.x; e < nv * nv * ng; e += blockDim.x) {
-            int Q = e % ng, vv = e / ng;
-            double2 acc = make_double2(0.0, 0.0);
-            if (Q != skip) {
-                const double2* wr = W + (int64_t)Q * S.ng_max;
-                const double2* r = rv + vv * S.ng_max;
-                for (int Qp = 0; Qp < ng; ++Qp) {
-                    if (Qp == skip) continue;
-                    cfma(acc, wr[Qp], conjd(r[Qp]));
-                }
-            }
-            T[vv * S.ng_max + Q] = acc;
-        }
-        __syncthreads();
-    }
-    const bool diag = (t.k == t.kp) && (terms & BSE_TERM_DIAG);
-    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-        int r = e % B, cidx = e / B;    // r: (v, c) row, cidx: (v', c') column
-        int v = r / nc, c = r % nc, vp = cidx / nc, cp = cidx % nc;
-        double2 acc = make_double2(0.0, 0.0);
-        if (direct) {
-            const double2* a = rc + (c * nc + cp) * S.ng_max;
-            const double2* b = T + (v * nv + vp) * S.ng_max;
-            for (int Q = 0; Q < ng; ++Q) cfma(acc, a[Q], b[Q]);
-        }
-        double2 val = make_double2(-acc.x * S.inv_vol, -acc.y * S.inv_vol);
-        if (diag && r == cidx) val.x += S.eps[t.k * S.nb + nv + c] - S.eps[t.k * S.nb + v] - w_div;
-        Xt[(int64_t)(t.col0 + cidx) * t.ld + t.row0 + r] = val;
-        if (t.flags & 1) Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + cidx] = conjd(val);
-    }
-}
-
-int launch_direct(const DevSys& s, const PairTask* tasks, int64_t ntasks, double2* X, uint32_t terms, double w_div,
-                  cudaStream_t st) {
-    if (ntasks == 0) return BSE_OK;
-    size_t sm = direct_smem(s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
-    if (sm > 227 * 1024) return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", sm);
-    cudaError_t e = cudaFuncSetAttribute(direct_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", sm, cudaGetErrorString(e));
-    for (int64_t off = 0; off < ntasks; off += 1 << 30) {
-        int64_t n = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
-        direct_fp64_kernel<<<(unsigned)n, 256, sm, st>>>(s, tasks + off, X, terms, w_div);
-        LAUNCH_CHECK();
-    }
-    return BSE_OK;
-}
-
-// ---------------------------------------------------------------------------
 // projection (Eqs. projection, transformationU), orbit-sparse, two stages:
 //   Y = X U_b   (tile rows of star a, columns of star b's basis vectors)
 //   H_mu[cols a, cols b] = U_a^dagger Y (+ exchange, projected)
 // ---------------------------------------------------------------------------
-__global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ X,
+template <typename VX>
+__global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const VX* __restrict__ X,
                                      double2* Y) {
     const TileTask t = tiles[blockIdx.z];
     const int r = blockIdx.x * 32 + threadIdx.x;
     const int64_t ncol = t.cb1 - t.cb0;
     if (r >= t.rows) return;
-    const double2* Xt = X + t.xoff;
+    const VX* Xt = X + t.xoff;
     for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
         const int64_t j = t.cb0 + jj;
         const int o = Bs.col_orbit[j];
         const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
         const double2* u = Bs.coef + Bs.col_off[j];
         double2 acc = make_double2(0.0, 0.0);
-        for (int64_t tt = 0; tt < n_o; ++tt) cfma(acc, Xt[(int64_t)Bs.member_loc[m0 + tt] * t.rows + r], u[tt]);
+        for (int64_t tt = 0; tt < n_o; ++tt) {
+            VX x = Xt[(int64_t)Bs.member_loc[m0 + tt] * t.rows + r];
+            cfma(acc, make_double2((double)x.x, (double)x.y), u[tt]);
+        }
         Y[t.yoff + jj * t.rows + r] = acc;
     }
 }
 
 __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ Y,
                                     const double2* __restrict__ Pmu, const double* __restrict__ vbar, int ng0,
-                                    double xscale, double2* H, int64_t ld) {
+                                    double xscale, const double* __restrict__ de, double w_div, double2* H,
+                                    int64_t ld) {
     const TileTask t = tiles[blockIdx.z];
     const int64_t ii = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t nrow = t.ca1 - t.ca0, ncol = t.cb1 - t.cb0;
@@ -387,6 +297,19 @@ __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ ti
         const double2* y = Y + t.yoff + jj * t.rows;
         double2 acc = make_double2(0.0, 0.0);
         for (int64_t tt = 0; tt < n_o; ++tt) cfma_conj(acc, u[tt], y[Bs.member_loc[m0 + tt]]);
+        if (de && Bs.col_orbit[j] == o) {
+            // U_i^dagger diag(eps_c - eps_v) U_j on the shared orbit, minus W^div delta_ij (FP64)
+            const double2* uj = Bs.coef + Bs.col_off[j];
+            double2 d = make_double2(0.0, 0.0);
+            for (int64_t tt = 0; tt < n_o; ++tt) {
+                double2 z = cmul(conjd(u[tt]), uj[tt]);
+                const double e = de[Bs.members[m0 + tt]];
+                d.x = fma(e, z.x, d.x);
+                d.y = fma(e, z.y, d.y);
+            }
+            acc.x += d.x - (i == j ? w_div : 0.0);
+            acc.y += d.y;
+        }
         if (Pmu) {
             const double2* pi = Pmu + i * ng0;
             const double2* pj = Pmu + j * ng0;
@@ -404,8 +327,8 @@ __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ ti
     }
 }
 
-int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, const int*, const double2* X,
-                         double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st) {
+int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X, double2* Y,
+                         int64_t max_rows, int64_t max_cols, cudaStream_t st) {
     if (ntiles == 0) return BSE_OK;
     dim3 blk(32, 8);
     int gy = ceil_div(max_cols, 8);
@@ -414,15 +337,18 @@ int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, c
     for (int off = 0; off < ntiles; off += 65535) {
         int n = ntiles - off < 65535 ? ntiles - off : 65535;
         dim3 grd(ceil_div(max_rows, 32), gy, n);
-        project_right_kernel<<<grd, blk, 0, st>>>(b, tiles + off, X, Y);
+        if (x32)
+            project_right_kernel<float2><<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, Y);
+        else
+            project_right_kernel<double2><<<grd, blk, 0, st>>>(b, tiles + off, (const double2*)X, Y);
         LAUNCH_CHECK();
     }
     return BSE_OK;
 }
 
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y, const double2* Pmu,
-                        const double* vbar, int ng0, double xscale, double2* H, int64_t ld, int64_t max_ca,
-                        int64_t max_cb, cudaStream_t st) {
+                        const double* vbar, int ng0, double xscale, const double* de, double w_div, double2* H,
+                        int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st) {
     if (ntiles == 0) return BSE_OK;
     dim3 blk(32, 8);
     int gy = ceil_div(max_cb, 8);
@@ -431,7 +357,7 @@ int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, co
     for (int off = 0; off < ntiles; off += 65535) {
         int n = ntiles - off < 65535 ? ntiles - off : 65535;
         dim3 grd(ceil_div(max_ca, 32) > 0 ? ceil_div(max_ca, 32) : 1, gy, n);
-        project_left_kernel<<<grd, blk, 0, st>>>(b, tiles + off, Y, Pmu, vbar, ng0, xscale, H, ld);
+        project_left_kernel<<<grd, blk, 0, st>>>(b, tiles + off, Y, Pmu, vbar, ng0, xscale, de, w_div, H, ld);
         LAUNCH_CHECK();
     }
     return BSE_OK;
@@ -481,6 +407,18 @@ int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t 
                          int64_t ld, cudaStream_t st) {
     dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
     exchange_full_kernel<<<grd, blk, 0, st>>>(P, vbar, ng0, N, xscale, H, ld);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
+// H[I, I] += eps_c - eps_v - W^div (column-major H)
+__global__ void diag_full_kernel(const double* __restrict__ de, int64_t N, double w_div, double2* H, int64_t ld) {
+    int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I < N) H[I * ld + I].x += de[I] - w_div;
+}
+
+int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st) {
+    diag_full_kernel<<<ceil_div(N, 256), 256, 0, st>>>(de, N, w_div, H, ld);
     LAUNCH_CHECK();
     return BSE_OK;
 }

@@ -206,3 +206,38 @@ def test_empty_block(gpu):
             assert h.shape == (0, 0)
             return
     pytest.skip("no empty irrep block among the small cases")
+
+
+# --- FP32 direct term (CUDA cores); diagonal, projection, exchange stay FP64 ---
+HA_MEV = 27211.386245988
+TOL32 = 2e-6          # H_mu elements relative to the largest element
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_blocks_fp32(gpu, name):
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    H = oracle_h(name)
+    for mu in b.bright():
+        U, _ = b.basis(mu)
+        if U.shape[1] == 0:
+            continue
+        ref = project(U, H)
+        got = bse.block(get(name), mu, prec=bse.BSE_FP32).cpu().numpy()
+        assert _rel(got, ref) <= TOL32, (name, mu, _rel(got, ref))
+        # exciton energies within 0.1 meV of the oracle
+        assert np.abs(np.linalg.eigvalsh(got) - np.linalg.eigvalsh(ref)).max() * HA_MEV <= 0.1
+
+
+@pytest.mark.parametrize("terms", [2, 4])
+def test_block_terms_fp32(gpu, terms):
+    """The FP32 mode only changes the direct term; the exchange is FP64."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case("si4")
+    code = {2: "x", 4: "w"}[terms]
+    mu = b.bright()[0]
+    ref = project(b.basis(mu)[0], oracle_h("si4", code))
+    got = bse.block(get("si4"), mu, prec=bse.BSE_FP32, terms=terms).cpu().numpy()
+    assert _rel(got, ref) <= (TOL * 10 if terms == 2 else 1e-5)

@@ -80,3 +80,18 @@ def test_spectrum_sum_rule(built):
     assert abs(osc.sum() - np.linalg.norm(bmu) ** 2) <= 1e-10 * np.linalg.norm(bmu) ** 2
     assert np.all(np.diff(om) >= -1e-14)
     assert np.all(im[d["omega"] > 0] > 0)
+
+
+def test_fp32_build_within_0p1_mev(built):
+    """FP32 direct term vs the FP64 build (itself pinned to the oracle above):
+    exciton energies within 0.1 meV, spectra within 1e-3 relative L2."""
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    h32 = bse.block(ctx, mu, prec=bse.BSE_FP32)
+    h64 = torch.tensor(h, device="cuda").T.contiguous().T
+    omega = torch.tensor(d["omega"], device="cuda")
+    om64, osc64, im64 = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, h64, omega, d["eta"]))
+    om32, osc32, im32 = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, h32, omega, d["eta"]))
+    assert np.abs(om32 - om64).max() * 27211.386245988 <= 0.1
+    assert np.linalg.norm(im32 - im64) <= 1e-3 * np.linalg.norm(im64)
+    assert np.abs(h32.cpu().numpy() - h).max() <= 2e-6 * np.abs(h).max()
