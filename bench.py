@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--config", default="si8")
+    p.add_argument("--block", choices=["partner", "full"], default="partner",
+                   help="solve the partner block (dim/d, same levels and spectrum) or the whole irrep block")
     p.add_argument("--prec", choices=["fp32", "fp64"], default="fp32",
                    help="precision of the direct term; the FP64 build is also timed for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -271,8 +273,9 @@ def run_ours(args, rank, world, local):
     ctx = bse.bse_create(inp, stream=stream, device=devin)
     tab = bse.bse_tables(ctx)
     mu = int(np.nonzero(tab["bright"])[0][0])
-    dim = int(tab["block_dim"][mu])
-    work = bse.bse_build_work(ctx, mu)
+    partner = args.block == "partner"
+    dim = int(tab["partner_dim"][mu] if partner else tab["block_dim"][mu])
+    work = bse.bse_build_work(ctx, mu, partner)
     launches_base = bse.bse_get_stats(ctx)["launches"]
     bse.bse_destroy(ctx)
     flops_build = work["rho"] + work["contract"] + work["project"] + work["exchange"]
@@ -290,9 +293,11 @@ def run_ours(args, rank, world, local):
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
                              device=None if host_inputs is not None else devin)
         bse.bse_set_timing(ctx, True)
-        bse.bse_build_block(ctx, mu, prec if p is None else p, bse.BSE_TERM_ALL, H, dim)
+        build = bse.bse_build_partner_block if partner else bse.bse_build_block
+        solve = bse.bse_partner_spectrum if partner else bse.bse_block_spectrum
+        build(ctx, mu, prec if p is None else p, bse.BSE_TERM_ALL, H, dim)
         s1 = bse.bse_get_stats(ctx)
-        bse.bse_block_spectrum(ctx, mu, H, dim, omega, eta, om, osc, im)
+        solve(ctx, mu, H, dim, omega, eta, om, osc, im)
         s2 = bse.bse_get_stats(ctx)
         if d2h is not None:
             for src, dst in zip((om, osc, im), d2h):
@@ -386,14 +391,21 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
                    "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
-                   "block_dim": dim, "full_dim": int(tab["n_product"]),
+                   "block": ("partner block of the irrep (dim %d = %d/%d): same levels and spectrum as the "
+                             "whole block" % (dim, int(tab["block_dim"][mu]), int(tab["irrep_dim"][mu])))
+                            if partner else "whole irrep block",
+                   "block_dim": int(tab["block_dim"][mu]), "solved_dim": dim, "full_dim": int(tab["n_product"]),
                    "precision": ("direct term FP32 on CUDA cores; diagonal, projection, exchange and "
                                  "eigensolver FP64") if prec == bse.BSE_FP32 else "FP64 throughout",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
         "time_to_spectrum_ms": total_ms / args.steps,
-        "stage_ms": {"direct": ms_direct, "project": ms_project, "exchange": ms_exchange, "eigensolve": ms_eig},
+        "stage_ms": {"direct": ms_direct, "project": ms_project, "exchange": ms_exchange, "eigensolve": ms_eig,
+                     "create": statistics.mean(x[1]["ms_create"] for x in stats),
+                     "create_parts": {k: statistics.mean(x[1][k] for x in stats)
+                                      for k in ("ms_create_tables", "ms_create_upload", "ms_create_gamma",
+                                                "ms_create_wdiv", "ms_basis")}},
         "build_flops": flops_build,
         "work": {k: work[k] for k in ("rho", "contract", "project", "exchange", "overlap")},
         "build_tflops_kernels": flops_build / ((ms_direct + ms_project + ms_exchange) * 1e-3) / 1e12,

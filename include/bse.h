@@ -138,6 +138,7 @@ typedef struct {
     const int64_t* block_dim;     /* [n_irreps] dimension of H_mu */
     const int32_t* orbit_of;      /* [N] orbit of each product index; orbits ordered by lowest member */
     double w_div;                 /* head correction used on the diagonal (Ha) */
+    const int64_t* partner_dim;   /* [n_irreps] dim_mu / d_mu where a partner block exists, else 0 */
 } bse_tables_view;
 
 int bse_tables(const bse_ctx* ctx, bse_tables_view* out);
@@ -168,6 +169,24 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  */
 int bse_build_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
                     void* h_dev, int64_t ld);
+
+/*
+ * bse_build_partner_block - for an irrep contained once in the polar-vector
+ * representation (the optically active ones: T1u of Oh, E1u and A2u of
+ * D6h), the block of its first partner, H_mu^(1) = U_1^dagger H U_1, where
+ * U_1 spans the range of the row projector
+ *   P_11 = d_mu/|S| sum_s Gamma_mu(s)_11 Gamma~(s)
+ * and Gamma_mu(s) are the Cartesian rotations restricted to the irrep's
+ * Cartesian subspace.  Sec. III.C.3 (the blocks H^{mu i}_{mu j} are
+ * multiples of the identity) makes H_mu unitarily equivalent to d_mu copies
+ * of H_mu^(1): its eigenvalues are those of H_mu, each once instead of d_mu
+ * times, and the eigensolver works on a matrix d_mu times smaller.
+ * Dimension partner_dim[irrep] of bse_tables; arguments as bse_build_block.
+ * Errors: EUNSUPPORTED for an irrep that is not contained once in the
+ * polar-vector representation.
+ */
+int bse_build_partner_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
+                            void* h_dev, int64_t ld);
 
 /*
  * bse_build_full - the unprojected H (N x N, complex128, column-major, ld
@@ -204,6 +223,17 @@ int bse_block_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t l
                        const double* omega_dev, int64_t n_omega, double eta,
                        double* omega_out, double* osc, double* im_eps);
 
+/*
+ * bse_partner_spectrum - as bse_block_spectrum for the partner block of
+ * bse_build_partner_block: omega_out [partner_dim] are the distinct levels of
+ * H_mu (each d_mu-fold in H_mu), osc [partner_dim] the oscillator strength of
+ * each level summed over the d_mu partners, sum_i |a^T (U_i^T B)|^2 with
+ * U_i = P_i1 U_1, and im_eps the spectrum of the whole block H_mu.
+ */
+int bse_partner_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t ld,
+                         const double* omega_dev, int64_t n_omega, double eta,
+                         double* omega_out, double* osc, double* im_eps);
+
 /* Wait for all work on the context's stream; returns ECUDA on a device error. */
 int bse_sync(bse_ctx* ctx);
 
@@ -227,7 +257,7 @@ typedef struct {
     int64_t tiles;         /* star-pair tiles */
 } bse_work;
 
-int bse_build_work(bse_ctx* ctx, int32_t irrep, bse_work* out);
+int bse_build_work(bse_ctx* ctx, int32_t irrep, int32_t partner, bse_work* out);   /* partner: 0 block, 1 partner block */
 
 /*
  * bse_stats: kernel launches of this library in the process so far, and,
@@ -243,6 +273,12 @@ typedef struct {
     float ms_exchange;          /* exchange projection of the last build */
     float ms_eig;               /* dense eigensolver of the last spectrum */
     float ms_spectrum;          /* oscillator strengths and Im eps of the last spectrum */
+    float ms_create;            /* wall time of bse_create */
+    float ms_create_tables;     /* ... host tables (group, mesh, stars, characters, orbits) */
+    float ms_create_upload;     /* ... device copies of the inputs and the look-up box */
+    float ms_create_gamma;      /* ... band rotations (kernels, copy back, unitarity check) */
+    float ms_create_wdiv;       /* ... head correction */
+    float ms_basis;             /* wall time of the last basis construction (host, incl. upload) */
 } bse_stats;
 
 int bse_set_timing(bse_ctx* ctx, int32_t on);

@@ -125,3 +125,72 @@ class Basis:
 def project(U: np.ndarray, H: np.ndarray) -> np.ndarray:
     """H_mu = U^dagger H U."""
     return U.conj().T @ H @ U
+
+
+# ---------------------------------------------------------------------------
+# partner (row) blocks of an irrep contained once in the polar-vector
+# representation.  Its matrices are the Cartesian rotations restricted to
+# the irrep's Cartesian subspace, so the row projectors
+#   P_ij = d/|S| sum_s conj(Gamma_mu(s)_ij) Gamma~(s)
+# are available without tables.  Great orthogonality (Sec. III.C.3: the
+# blocks H^{mu i}_{mu j} are multiples of the identity) makes
+# U_i^dagger H U_i the same matrix for every partner i, with U_i = P_i1 U_1:
+# the block H_mu is d_mu copies of it.
+# ---------------------------------------------------------------------------
+
+def partner_irrep_matrices(grp, chi_mu, d):
+    """Gamma_mu(s) = E^T A(s) E (d x d) with E an orthonormal basis of the
+    range of the vector-representation projector d/|S| sum chi A(s), chosen by
+    Gram-Schmidt over the Cartesian axes x, y, z in that order."""
+    pv = d / grp.n * np.einsum("s,sij->ij", chi_mu.astype(float), grp.cart)
+    cols = []
+    for a in range(3):
+        x = pv[:, a].copy()
+        for e in cols:
+            x -= e * (e @ x)
+        if np.linalg.norm(x) > 1e-8:
+            cols.append(x / np.linalg.norm(x))
+    if len(cols) != d:
+        raise ValueError("irrep is not contained once in the polar-vector representation")
+    E = np.array(cols).T
+    return np.einsum("ai,sab,bj->sij", E, grp.cart, E)
+
+
+class PartnerBasis:
+    """Canonical basis of partner 1 of a bright irrep and its transfers."""
+
+    def __init__(self, basis: Basis, mu: int):
+        self.b = basis
+        grp = basis.grp
+        self.d = int(basis.dims[mu])
+        self.gam = partner_irrep_matrices(grp, basis.chi[mu], self.d)
+        n = basis.inp.N
+        self.P = [[sum(self.d / grp.n * np.conj(self.gam[s, i, j]) * basis.reps[s] for s in range(grp.n))
+                   for j in range(self.d)] for i in range(self.d)]
+        P11 = self.P[0][0].tocsc()
+        cols = []
+        for mem in basis.orbits:
+            acc = []
+            for j in mem:
+                x = P11[:, j].toarray()[mem, 0]
+                for _ in range(2):
+                    for u in acc:
+                        x = x - u * np.vdot(u, x)
+                nrm = np.linalg.norm(x)
+                if nrm > KEEP_TOL:
+                    acc.append(x / nrm)
+            for u in acc:
+                full = np.zeros(n, dtype=np.complex128)
+                full[mem] = u
+                cols.append(full)
+        U1 = np.array(cols).T if cols else np.zeros((n, 0), dtype=np.complex128)
+        self.U = [U1] + [self.P[i][0] @ U1 for i in range(1, self.d)]
+
+
+def partner_spectrum(inp, H1, Us, B, omega, eta):
+    """Levels of the partner block, oscillator strengths summed over the
+    partners, and Im eps_M (equal to the spectrum of the whole block)."""
+    from .spectrum import lorentz_sum
+    Om, a = np.linalg.eigh(H1)
+    osc = sum(np.abs(a.T @ (U.T @ B)) ** 2 for U in Us)
+    return Om, osc, lorentz_sum(inp, Om, osc, omega, eta)

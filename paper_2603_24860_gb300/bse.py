@@ -47,7 +47,7 @@ class BseTablesView(C.Structure):
         ("n_orbits", C.c_int32), ("n_product", C.c_int64),
         ("rotk", _P32), ("star_of_k", _P32), ("star_rep", _P32), ("s_k", _P32),
         ("class_of_op", _P32), ("chi", _P32), ("irrep_dim", _P32), ("bright", _P32),
-        ("block_dim", _P64), ("orbit_of", _P32), ("w_div", C.c_double),
+        ("block_dim", _P64), ("orbit_of", _P32), ("w_div", C.c_double), ("partner_dim", _P64),
     ]
 
 
@@ -59,7 +59,9 @@ class BseWork(C.Structure):
 class BseStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("direct_launches", C.c_int64), ("ms_direct", C.c_float),
                 ("ms_project", C.c_float), ("ms_exchange", C.c_float), ("ms_eig", C.c_float),
-                ("ms_spectrum", C.c_float)]
+                ("ms_spectrum", C.c_float), ("ms_create", C.c_float), ("ms_create_tables", C.c_float),
+                ("ms_create_upload", C.c_float), ("ms_create_gamma", C.c_float), ("ms_create_wdiv", C.c_float),
+                ("ms_basis", C.c_float)]
 
 
 EXPORTS = {
@@ -75,7 +77,10 @@ EXPORTS = {
     "bse_block_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_sync": (C.c_int, [C.c_void_p]),
-    "bse_build_work": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(BseWork)]),
+    "bse_build_work": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(BseWork)]),
+    "bse_build_partner_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_uint32, C.c_void_p, C.c_int64]),
+    "bse_partner_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                       C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "bse_get_stats": (C.c_int, [C.c_void_p, C.POINTER(BseStats)]),
     "bse_head_correction_noalloc": (C.c_int, [_PD, _P32, _PD, C.c_void_p, C.c_void_p]),
@@ -214,7 +219,7 @@ def bse_tables(ctx: Context) -> dict:
         rotk=get(v.rotk, no * nk, (no, nk)), star_of_k=get(v.star_of_k, nk), star_rep=get(v.star_rep, v.n_stars),
         s_k=get(v.s_k, nk), class_of_op=get(v.class_of_op, no), chi=get(v.chi, ni * no, (ni, no)),
         irrep_dim=get(v.irrep_dim, ni), bright=get(v.bright, ni), block_dim=get(v.block_dim, ni),
-        orbit_of=get(v.orbit_of, v.n_product), w_div=v.w_div)
+        orbit_of=get(v.orbit_of, v.n_product), w_div=v.w_div, partner_dim=get(v.partner_dim, ni))
 
 
 def bse_pairdens(ctx: Context, k, kp, bands: int, out):
@@ -233,6 +238,17 @@ def bse_build_block(ctx: Context, irrep: int, prec: int, terms: int, out, ld: in
     column-major with leading dimension ld)."""
     _check(lib().bse_build_block(ctx.handle, irrep, prec, terms, _ptr(out), ld))
     return out
+
+
+def bse_build_partner_block(ctx: Context, irrep: int, prec: int, terms: int, out, ld: int):
+    """H_mu^(1) (partner block) into ``out``, column-major with leading dimension ld."""
+    _check(lib().bse_build_partner_block(ctx.handle, irrep, prec, terms, _ptr(out), ld))
+    return out
+
+
+def bse_partner_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float, omega_out, osc, im_eps):
+    _check(lib().bse_partner_spectrum(ctx.handle, irrep, _ptr(h), ld, _ptr(omega), omega.numel(), eta,
+                                      _ptr(omega_out), _ptr(osc), _ptr(im_eps)))
 
 
 def bse_build_full(ctx: Context, terms: int, out, ld: int):
@@ -259,9 +275,9 @@ def bse_sync(ctx: Context):
     _check(lib().bse_sync(ctx.handle))
 
 
-def bse_build_work(ctx: Context, irrep: int) -> dict:
+def bse_build_work(ctx: Context, irrep: int, partner: bool = False) -> dict:
     w = BseWork()
-    _check(lib().bse_build_work(ctx.handle, irrep, C.byref(w)))
+    _check(lib().bse_build_work(ctx.handle, irrep, 1 if partner else 0, C.byref(w)))
     return {f: getattr(w, f) for f, _ in BseWork._fields_}
 
 
@@ -303,6 +319,27 @@ def block(ctx: Context, irrep: int, prec: int = BSE_FP64, terms: int = BSE_TERM_
     buf = torch.empty(max(dim * dim, 1), dtype=torch.complex128, device="cuda")
     bse_build_block(ctx, irrep, prec, terms, buf, max(dim, 1))
     return colmajor(buf, dim, dim, max(dim, 1))
+
+
+def partner_block(ctx: Context, irrep: int, prec: int = BSE_FP64, terms: int = BSE_TERM_ALL):
+    """Build the partner block and return it as a [n, n] complex128 CUDA view."""
+    import torch
+    n = int(bse_tables(ctx)["partner_dim"][irrep])
+    buf = torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda")
+    bse_build_partner_block(ctx, irrep, prec, terms, buf, max(n, 1))
+    return colmajor(buf, n, n, max(n, 1))
+
+
+def partner_spectrum(ctx: Context, irrep: int, h, omega, eta: float):
+    """(levels, oscillator strengths summed over partners, Im eps_M)."""
+    import torch
+    n = h.shape[0]
+    ld = h.stride(1) if n else 1
+    om = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    osc = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    im = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+    bse_partner_spectrum(ctx, irrep, h, ld, omega, eta, om, osc, im)
+    return om[:n], osc[:n], im
 
 
 def full(ctx: Context, terms: int = BSE_TERM_ALL):

@@ -4,6 +4,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -13,6 +14,10 @@
 
 namespace bse {
 const char* last_error();
+}
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 using namespace bse;
@@ -69,6 +74,13 @@ struct bse_ctx {
     DevBuf orbit_off, members, member_loc;
     std::vector<IrrepDev> irr;
     std::vector<int64_t> block_dim;
+    struct PartnerDev {
+        bool ready = false;
+        int d = 0;
+        IrrepDev part[3];   // partner 1 basis and its transfers P_i1 U_1
+    };
+    std::vector<PartnerDev> partner;
+    std::vector<int64_t> partner_dim;   // dim_mu / d_mu for partner-capable irreps, else 0
     int ng0 = 0;
     double w_div = 0.0;
     double spin = 2.0;
@@ -157,8 +169,7 @@ void plan_batches(const Tables& t, const Basis& bh, size_t budget, std::vector<B
 
 }  // namespace
 
-static DevBasis dev_basis(bse_ctx* c, int mu) {
-    IrrepDev& d = c->irr[mu];
+static DevBasis dev_basis_of(bse_ctx* c, IrrepDev& d) {
     DevBasis b;
     b.dim = d.host.dim;
     b.col_orbit = (const int*)d.col_orbit.p;
@@ -170,19 +181,56 @@ static DevBasis dev_basis(bse_ctx* c, int mu) {
     return b;
 }
 
-static int ensure_basis(bse_ctx* c, int mu) {
-    if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
-    IrrepDev& d = c->irr[mu];
-    if (d.ready) return BSE_OK;
-    BSE_TRY(build_basis(c->t, mu, d.host));
-    if (d.host.dim != c->block_dim[mu])
-        return fail(BSE_ESYMM, "irrep %d: orthonormal basis has %lld vectors but Tr P = %lld", mu,
-                    (long long)d.host.dim, (long long)c->block_dim[mu]);
+static DevBasis dev_basis(bse_ctx* c, int mu) { return dev_basis_of(c, c->irr[mu]); }
+
+static int upload_basis(bse_ctx* c, IrrepDev& d) {
     BSE_TRY(upload(d.col_orbit, d.host.col_orbit.data(), d.host.col_orbit.size(), c->stream));
     BSE_TRY(upload(d.col_off, d.host.col_off.data(), d.host.col_off.size(), c->stream));
     BSE_TRY(upload(d.coef, reinterpret_cast<const double2*>(d.host.coef.data()), d.host.coef.size(), c->stream));
     BSE_CUDA(cudaStreamSynchronize(c->stream));
     d.ready = true;
+    return BSE_OK;
+}
+
+// partner 1 of an irrep contained once in the polar-vector representation:
+// canonical basis of the range of P_11 and its transfers U_i = P_i1 U_1
+static int ensure_partner(bse_ctx* c, int mu) {
+    if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
+    auto& pd = c->partner[mu];
+    if (pd.ready) return BSE_OK;
+    const double t0 = now_ms();
+    int d = 0;
+    std::vector<double> gam;
+    BSE_TRY(partner_matrices(c->t, mu, d, gam));
+    const int G = c->t.nops;
+    auto weights = [&](int i, int j) {
+        std::vector<double> w(G);
+        for (int s = 0; s < G; ++s) w[s] = (double)d / G * gam[((size_t)s * d + i) * d + j];
+        return w;
+    };
+    BSE_TRY(build_basis_weighted(c->t, weights(0, 0), pd.part[0].host));
+    if (pd.part[0].host.dim != c->partner_dim[mu])
+        return fail(BSE_ESYMM, "irrep %d: partner basis has %lld vectors but Tr P_11 = %lld", mu,
+                    (long long)pd.part[0].host.dim, (long long)c->partner_dim[mu]);
+    for (int i = 1; i < d; ++i) BSE_TRY(transfer_basis(c->t, pd.part[0].host, weights(i, 0), pd.part[i].host));
+    for (int i = 0; i < d; ++i) BSE_TRY(upload_basis(c, pd.part[i]));
+    pd.d = d;
+    pd.ready = true;
+    c->stats.ms_basis = (float)(now_ms() - t0);
+    return BSE_OK;
+}
+
+static int ensure_basis(bse_ctx* c, int mu) {
+    if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
+    IrrepDev& d = c->irr[mu];
+    if (d.ready) return BSE_OK;
+    const double t0 = now_ms();
+    BSE_TRY(build_basis(c->t, mu, d.host));
+    if (d.host.dim != c->block_dim[mu])
+        return fail(BSE_ESYMM, "irrep %d: orthonormal basis has %lld vectors but Tr P = %lld", mu,
+                    (long long)d.host.dim, (long long)c->block_dim[mu]);
+    BSE_TRY(upload_basis(c, d));
+    c->stats.ms_basis = (float)(now_ms() - t0);
     return BSE_OK;
 }
 
@@ -289,6 +337,7 @@ static int compute_wdiv(bse_ctx* c, const double* L) {
 
 static int create_impl(bse_ctx* c, const bse_system* sys) {
     Tables& t = c->t;
+    const double t0 = now_ms();
     if (sys->nv <= 0 || sys->nc <= 0) return fail(BSE_EINVAL, "nv and nc must be positive");
     if (sys->npw_max <= 0 || sys->npw_max > 32767 || sys->ng_max <= 0)
         return fail(BSE_EINVAL, "npw_max must be in 1..32767 and ng_max positive");
@@ -326,6 +375,7 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
         BSE_TRY(upload(c->de, de.data(), de.size(), c->stream));
         BSE_CUDA(cudaStreamSynchronize(c->stream));
     }
+    const double t1 = now_ms();
     cudaStream_t st = c->stream;
     // device copies of the inputs
     BSE_TRY(upload(c->coef, reinterpret_cast<const double2*>(sys->coef), (size_t)nk * nb * sys->npw_max, st));
@@ -405,6 +455,8 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     for (int a = 0; a < 3; ++a) S.qhat[a] = sys->qhat[a] / qn;
     S.v_uc = t.v_uc;
     S.scissor = sys->scissor;
+    BSE_CUDA(cudaStreamSynchronize(st));
+    const double t2 = now_ms();
     // band rotations Gamma(s) on the device
     std::vector<int32_t> ent;
     ent.reserve((size_t)t.gam_per_s * 3);
@@ -444,6 +496,7 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     release(dgam);
     BSE_TRY(rc);
     BSE_TRY(check_band_rotations(t));
+    const double t3 = now_ms();
     // block dimensions from the trace formula dim_mu = d_mu/|S| sum_s chi_mu(s) Tr Gamma~(s)
     std::vector<cplx> trace(t.nops, 0.0);
     for (int s = 0; s < t.nops; ++s)
@@ -474,6 +527,23 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
         tot += r;
     }
     if (tot != t.N) return fail(BSE_ESYMM, "block dimensions sum to %lld, not N = %lld", (long long)tot, (long long)t.N);
+    c->partner_dim.assign(t.n_irreps, 0);
+    for (int mu = 0; mu < t.n_irreps; ++mu) {
+        int d = 0;
+        std::vector<double> gam;
+        if (t.bright[mu] != 1 || partner_matrices(t, mu, d, gam) != BSE_OK) {
+            clear_error();
+            continue;
+        }
+        cplx a = 0;
+        for (int s = 0; s < t.nops; ++s) a += gam[(size_t)s * d * d] * trace[s];
+        double dd = a.real() * d / t.nops;
+        long r = std::lround(dd);
+        if (std::fabs(dd - r) > 1e-6 || r * d != c->block_dim[mu])
+            return fail(BSE_ESYMM, "Tr P_11 of irrep %d = %.9f is not dim/d", mu, dd);
+        c->partner_dim[mu] = r;
+    }
+    c->partner.resize(t.n_irreps);
     // orbit tables on the device
     std::vector<int> loc(t.orbit_members.size());
     for (size_t i = 0; i < loc.size(); ++i) {
@@ -485,12 +555,19 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     BSE_TRY(upload(c->members, t.orbit_members.data(), t.orbit_members.size(), st));
     BSE_TRY(upload(c->member_loc, loc.data(), loc.size(), st));
     c->irr.resize(t.n_irreps);
+    const double t4 = now_ms();
     if (std::isnan(sys->w_div)) {
         BSE_TRY(compute_wdiv(c, sys->eps_inf));
     } else {
         c->w_div = sys->w_div;
     }
     BSE_CUDA(cudaStreamSynchronize(st));
+    const double t5 = now_ms();
+    c->stats.ms_create_tables = (float)(t1 - t0);
+    c->stats.ms_create_upload = (float)(t2 - t1);
+    c->stats.ms_create_gamma = (float)(t3 - t2);
+    c->stats.ms_create_wdiv = (float)(t5 - t4);
+    c->stats.ms_create = (float)(t5 - t0);
     return BSE_OK;
 }
 
@@ -505,6 +582,12 @@ static void free_ctx(bse_ctx* c) {
         release(d.col_off);
         release(d.coef);
     }
+    for (auto& p : c->partner)
+        for (auto& d : p.part) {
+            release(d.col_orbit);
+            release(d.col_off);
+            release(d.coef);
+        }
     if (c->solver) cusolverDnDestroy(c->solver);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -561,6 +644,7 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
     v->block_dim = c->block_dim.data();
     v->orbit_of = t.orbit_of.data();
     v->w_div = c->w_div;
+    v->partner_dim = c->partner_dim.data();
     return BSE_OK;
 }
 
@@ -618,18 +702,15 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
     return BSE_OK;
 }
 
-int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
-    clear_error();
-    if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+// U^dagger H U for an orbit-sparse basis U (an irrep block or a partner block)
+static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     const int p32 = prec == BSE_FP32;
-    BSE_TRY(ensure_basis(c, mu));
     const Tables& t = c->t;
-    const Basis& bh = c->irr[mu].host;
+    const Basis& bh = bd.host;
     const int64_t dim = bh.dim;
     if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
     if (dim == 0) return BSE_OK;
-    DevBasis db = dev_basis(c, mu);
+    DevBasis db = dev_basis_of(c, bd);
     const double2* Pmu = nullptr;
     if (c->timing) c->stats.ms_exchange = 0.f;
     if (terms & BSE_TERM_EXCHANGE) {
@@ -686,6 +767,22 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
     return BSE_OK;
 }
 
+int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
+    clear_error();
+    if (!c || !h) return fail(BSE_EINVAL, "null argument");
+    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    BSE_TRY(ensure_basis(c, mu));
+    return build_generic(c, c->irr[mu], prec, terms, h, ld);
+}
+
+int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
+    clear_error();
+    if (!c || !h) return fail(BSE_EINVAL, "null argument");
+    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    BSE_TRY(ensure_partner(c, mu));
+    return build_generic(c, c->partner[mu].part[0], prec, terms, h, ld);
+}
+
 int bse_block_basis(bse_ctx* c, int32_t mu, void* u, int64_t ld) {
     clear_error();
     if (!c || !u) return fail(BSE_EINVAL, "null argument");
@@ -703,13 +800,12 @@ int bse_dipoles(bse_ctx* c, void* b) {
     return launch_dipoles(c->S, (double2*)b, c->stream);
 }
 
-int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
-                       double eta, double* omega_out, double* osc, double* im_eps) {
-    clear_error();
-    if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
-    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
-    BSE_TRY(ensure_basis(c, mu));
-    const int64_t dim = c->irr[mu].host.dim;
+// eigensolution of U^dagger H U and the spectrum; the oscillator strength of
+// each level sums |a^T (U_p^T B)|^2 over the given bases U_p (one for an
+// irrep block, the d transfers for a partner block)
+static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, const void* h, int64_t ld, const double* omega,
+                            int64_t n_omega, double eta, double* omega_out, double* osc, double* im_eps) {
+    const int64_t dim = parts[0].host.dim;
     if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
     if (dim == 0) {
         if (n_omega) BSE_CUDA(cudaMemsetAsync(im_eps, 0, sizeof(double) * n_omega, c->stream));
@@ -717,9 +813,10 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
     }
     if (dim > (1ll << 31) - 1) return fail(BSE_EUNSUPPORTED, "block too large for the eigensolver");
     BSE_TRY(ensure_dipoles(c));
-    BSE_TRY(ensure(c->Bmu, sizeof(double2) * (size_t)dim));
-    DevBasis db = dev_basis(c, mu);
-    BSE_TRY(launch_bmu(db, (const double2*)c->B.p, (double2*)c->Bmu.p, c->stream));
+    BSE_TRY(ensure(c->Bmu, sizeof(double2) * (size_t)dim * nparts));
+    for (int p = 0; p < nparts; ++p)
+        BSE_TRY(launch_bmu(dev_basis_of(c, parts[p]), (const double2*)c->B.p, (double2*)c->Bmu.p + (size_t)p * dim,
+                           c->stream));
     BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
     BSE_CUDA(cudaMemcpy2DAsync(c->eigA.p, sizeof(double2) * dim, h, sizeof(double2) * ld, sizeof(double2) * dim, dim,
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -741,7 +838,8 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
                          (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
         return fail(BSE_ESOLVER, "zheevd launch failed");
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
-    BSE_TRY(launch_oscillators((const double2*)c->eigA.p, dim, dim, (const double2*)c->Bmu.p, osc, c->stream));
+    BSE_TRY(launch_oscillators((const double2*)c->eigA.p, dim, dim, (const double2*)c->Bmu.p, nparts, osc,
+                               c->stream));
     BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, 4.0 * M_PI * c->spin / c->t.nk, im_eps,
                             c->stream));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[5], c->stream));
@@ -754,6 +852,25 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
         BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
     }
     return BSE_OK;
+}
+
+int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
+                       double eta, double* omega_out, double* osc, double* im_eps) {
+    clear_error();
+    if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
+    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
+    BSE_TRY(ensure_basis(c, mu));
+    return spectrum_generic(c, &c->irr[mu], 1, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+}
+
+int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
+                         double eta, double* omega_out, double* osc, double* im_eps) {
+    clear_error();
+    if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
+    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
+    BSE_TRY(ensure_partner(c, mu));
+    auto& pd = c->partner[mu];
+    return spectrum_generic(c, pd.part, pd.d, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
 }
 
 int bse_set_timing(bse_ctx* c, int32_t on) {
@@ -774,12 +891,13 @@ int bse_get_stats(bse_ctx* c, bse_stats* out) {
     return BSE_OK;
 }
 
-int bse_build_work(bse_ctx* c, int32_t mu, bse_work* out) {
+int bse_build_work(bse_ctx* c, int32_t mu, int32_t partner, bse_work* out) {
     clear_error();
     if (!c || !out) return fail(BSE_EINVAL, "null argument");
-    BSE_TRY(ensure_basis(c, mu));
+    if (partner) BSE_TRY(ensure_partner(c, mu));
+    else BSE_TRY(ensure_basis(c, mu));
     const Tables& t = c->t;
-    const Basis& bh = c->irr[mu].host;
+    const Basis& bh = partner ? c->partner[mu].part[0].host : c->irr[mu].host;
     *out = bse_work{};
     if (bh.dim == 0) return BSE_OK;
     std::vector<Batch> batches;

@@ -3,6 +3,10 @@
 // character table (computed, not typed), multiplets, orbits of the product
 // basis and the canonical orthonormal basis of each irrep subspace.
 #include <algorithm>
+#include <array>
+#include <atomic>
+#include <cstdlib>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -434,24 +438,17 @@ int build_multiplets_and_orbits(Tables& t, const double* eps) {
         t.gam_koff[k + 1] = t.gam_koff[k] + n;
     }
     t.gam_per_s = t.gam_koff[t.nk];
+    // position of each band's multiplet block inside Gamma(s) at k
+    t.gam_boff.assign((size_t)t.nk * nb, 0);
+    for (int k = 0; k < t.nk; ++k) {
+        int64_t off = 0;
+        for (auto* ms : {&t.vmult[k], &t.cmult[k]})
+            for (auto& m : *ms) {
+                for (int b = m.first; b < m.first + m.second; ++b) t.gam_boff[(size_t)k * nb + b] = off;
+                off += (int64_t)m.second * m.second;
+            }
+    }
     return BSE_OK;
-}
-
-// Gamma(s) at k: entry of (n' <- n) inside the multiplet block of band n
-static inline int64_t gam_index(const Tables& t, int s, int k, int band_np, int band_n) {
-    // locate the block of band_n
-    int64_t off = t.gam_koff[k];
-    for (auto& m : t.vmult[k]) {
-        if (band_n >= m.first && band_n < m.first + m.second)
-            return (int64_t)s * t.gam_per_s + off + (int64_t)(band_np - m.first) * m.second + (band_n - m.first);
-        off += (int64_t)m.second * m.second;
-    }
-    for (auto& m : t.cmult[k]) {
-        if (band_n >= m.first && band_n < m.first + m.second)
-            return (int64_t)s * t.gam_per_s + off + (int64_t)(band_np - m.first) * m.second + (band_n - m.first);
-        off += (int64_t)m.second * m.second;
-    }
-    return -1;
 }
 
 int check_band_rotations(const Tables& t) {
@@ -479,46 +476,76 @@ int check_band_rotations(const Tables& t) {
     return BSE_OK;
 }
 
-// canonical orthonormal basis of irrep mu: P_mu e_j over each orbit, then two
-// passes of modified Gram-Schmidt, keeping residuals with norm > 1e-6.
-int build_basis(const Tables& t, int mu, Basis& out) {
-    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
-    const int G = t.nops, nv = t.nv, nc = t.nc;
-    const double pref = (double)t.irrep_dim[mu] / G;
-    const int32_t* chi = &t.chi[(size_t)mu * G];
+// Dense restriction to orbit o of P = sum_s w[s] Gamma~(s), column-major
+// (column jj = P e_I for the orbit's member jj).  Gamma~(s) maps |k v c> to
+// sum Gamma(s)_{kc}^{sk c'} conj(Gamma(s)_{kv}^{sk v'}) |sk v' c'> (Eq. Ttilde).
+static void orbit_matrix(const Tables& t, int o, const double* w, std::vector<cplx>& M) {
+    const int nv = t.nv, nc = t.nc, nb = t.nb;
+    const int vn = t.orbit_vn[o], cn = t.orbit_cn[o], vlo = t.orbit_vlo[o], clo = t.orbit_clo[o];
+    const int blk = vn * cn;
+    const int64_t m0 = t.orbit_off[o], n_o = t.orbit_off[o + 1] - m0;
+    M.assign((size_t)n_o * n_o, cplx(0.0));
+    for (int64_t jj = 0; jj < n_o; ++jj) {
+        const int64_t I = t.orbit_members[m0 + jj];
+        const int k = (int)(I / (nv * nc));
+        const int v = (int)((I / nc) % nv), c = (int)(I % nc);
+        cplx* col = &M[(size_t)jj * n_o];
+        const int64_t ov = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + v];
+        const int64_t oc = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + nv + c];
+        for (int s = 0; s < t.nops; ++s) {
+            if (w[s] == 0.0) continue;
+            const int k2 = t.rotk[(size_t)s * t.nk + k];
+            const int64_t base = (int64_t)t.pos_in_star[k2] * blk;
+            const cplx* gvb = &t.gamma[(size_t)s * t.gam_per_s + ov];   // vn x vn, [v'][v]
+            const cplx* gcb = &t.gamma[(size_t)s * t.gam_per_s + oc];   // cn x cn, [c'][c]
+            for (int vp = 0; vp < vn; ++vp) {
+                const cplx gv = gvb[vp * vn + (v - vlo)];
+                if (gv == 0.0) continue;
+                const cplx wg = w[s] * std::conj(gv);
+                for (int cp = 0; cp < cn; ++cp) col[base + vp * cn + cp] += wg * gcb[cp * cn + (c - clo)];
+            }
+        }
+    }
+}
+
+// run f(o) for every orbit on a small pool of host threads
+template <class F>
+static void for_each_orbit(int no, F f) {
+    int nt = (int)std::thread::hardware_concurrency();
+    if (const char* e = std::getenv("BSE_HOST_THREADS")) nt = std::atoi(e);
+    nt = std::max(1, std::min(nt, 32));
+    if (nt == 1 || no < 64) {
+        for (int o = 0; o < no; ++o) f(o);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int i = 0; i < nt; ++i)
+        pool.emplace_back([&] {
+            for (int o = next.fetch_add(1); o < no; o = next.fetch_add(1)) f(o);
+        });
+    for (auto& th : pool) th.join();
+}
+
+// canonical orthonormal basis of the range of P = sum_s w[s] Gamma~(s): P e_j
+// over each orbit, then two passes of modified Gram-Schmidt, keeping residuals
+// with norm > 1e-6 (the irrep projector of Eq. projection has w = d/|S| chi*).
+int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& out) {
     out = Basis();
     out.col_off.push_back(0);
     const int nstars = (int)t.stars.size();
     out.star_col.assign(nstars + 1, 0);
     const int no = (int)t.orbit_star.size();
-    std::vector<cplx> x, acc;
-    for (int o = 0; o < no; ++o) {
-        const int64_t m0 = t.orbit_off[o], n_o = t.orbit_off[o + 1] - m0;
-        const int vn = t.orbit_vn[o], cn = t.orbit_cn[o], vlo = t.orbit_vlo[o], clo = t.orbit_clo[o];
-        const int blk = vn * cn;
-        const int st = t.orbit_star[o];
-        acc.clear();
+    std::vector<std::vector<cplx>> acc_o(no);
+    std::vector<int> nacc_o(no, 0);
+    for_each_orbit(no, [&](int o) {
+        const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
+        std::vector<cplx> M, x(n_o);
+        orbit_matrix(t, o, w.data(), M);
+        std::vector<cplx>& acc = acc_o[o];
         int nacc = 0;
-        x.assign(n_o, 0.0);
         for (int64_t jj = 0; jj < n_o; ++jj) {
-            const int64_t I = t.orbit_members[m0 + jj];
-            const int k = (int)(I / (nv * nc));
-            const int v = (int)((I / nc) % nv), c = (int)(I % nc);
-            std::fill(x.begin(), x.end(), cplx(0.0));
-            for (int s = 0; s < G; ++s) {
-                if (chi[s] == 0) continue;
-                const int k2 = t.rotk[(size_t)s * t.nk + k];
-                const int64_t base = (int64_t)t.pos_in_star[k2] * blk;
-                for (int vp = 0; vp < vn; ++vp) {
-                    cplx gv = t.gamma[gam_index(t, s, k, vlo + vp, v)];
-                    if (gv == 0.0) continue;
-                    for (int cp = 0; cp < cn; ++cp) {
-                        cplx gc = t.gamma[gam_index(t, s, k, nv + clo + cp, nv + c)];
-                        x[base + vp * cn + cp] += (double)chi[s] * gc * std::conj(gv);
-                    }
-                }
-            }
-            for (auto& z : x) z *= pref;
+            std::copy(M.begin() + (size_t)jj * n_o, M.begin() + (size_t)(jj + 1) * n_o, x.begin());
             for (int pass = 0; pass < 2; ++pass)
                 for (int a = 0; a < nacc; ++a) {
                     const cplx* u = &acc[(size_t)a * n_o];
@@ -535,19 +562,89 @@ int build_basis(const Tables& t, int mu, Basis& out) {
                 ++nacc;
             }
         }
-        for (int a = 0; a < nacc; ++a) {
+        nacc_o[o] = nacc;
+    });
+    for (int o = 0; o < no; ++o) {
+        const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
+        for (int a = 0; a < nacc_o[o]; ++a) {
             out.col_orbit.push_back(o);
-            out.coef.insert(out.coef.end(), acc.begin() + (size_t)a * n_o, acc.begin() + (size_t)(a + 1) * n_o);
+            out.coef.insert(out.coef.end(), acc_o[o].begin() + (size_t)a * n_o, acc_o[o].begin() + (size_t)(a + 1) * n_o);
             out.col_off.push_back((int64_t)out.coef.size());
         }
-        out.star_col[st + 1] += nacc;
+        out.star_col[t.orbit_star[o] + 1] += nacc_o[o];
     }
     out.dim = (int64_t)out.col_orbit.size();
     for (int a = 0; a < nstars; ++a) out.star_col[a + 1] += out.star_col[a];
-    // columns must be grouped by star in star order
     for (int64_t j = 1; j < out.dim; ++j)
         if (t.orbit_star[out.col_orbit[j]] < t.orbit_star[out.col_orbit[j - 1]])
             return fail(BSE_ESYMM, "basis columns not grouped by star");
+    return BSE_OK;
+}
+
+int build_basis(const Tables& t, int mu, Basis& out) {
+    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
+    std::vector<double> w(t.nops);
+    for (int s = 0; s < t.nops; ++s) w[s] = (double)t.irrep_dim[mu] / t.nops * t.chi[(size_t)mu * t.nops + s];
+    return build_basis_weighted(t, w, out);
+}
+
+// Matrices Gamma_mu(s) = E^T A(s) E of an irrep contained once in the
+// polar-vector representation, E an orthonormal basis of the range of
+// d/|S| sum chi(s) A(s) chosen by Gram-Schmidt over the axes x, y, z.
+int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam) {
+    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
+    if (t.bright[mu] != 1)
+        return fail(BSE_EUNSUPPORTED, "irrep %d is not contained once in the polar-vector representation", mu);
+    d = t.irrep_dim[mu];
+    double pv[9] = {0};
+    for (int s = 0; s < t.nops; ++s)
+        for (int i = 0; i < 9; ++i) pv[i] += (double)d / t.nops * t.chi[(size_t)mu * t.nops + s] * t.cart[9 * s + i];
+    std::vector<std::array<double, 3>> E;
+    for (int a = 0; a < 3; ++a) {
+        std::array<double, 3> x = {pv[a], pv[3 + a], pv[6 + a]};
+        for (auto& e : E) {
+            double dt = e[0] * x[0] + e[1] * x[1] + e[2] * x[2];
+            for (int i = 0; i < 3; ++i) x[i] -= e[i] * dt;
+        }
+        double nr = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (nr > 1e-8) E.push_back({x[0] / nr, x[1] / nr, x[2] / nr});
+    }
+    if ((int)E.size() != d) return fail(BSE_ESYMM, "irrep %d: Cartesian subspace has dim %d, not %d", mu, (int)E.size(), d);
+    gam.assign((size_t)t.nops * d * d, 0.0);
+    for (int s = 0; s < t.nops; ++s)
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double acc = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) acc += E[i][a] * t.cart[9 * s + 3 * a + b] * E[j][b];
+                gam[((size_t)s * d + i) * d + j] = acc;
+            }
+    return BSE_OK;
+}
+
+// out columns = (sum_s w[s] Gamma~(s)) u, column by column (orbit-local)
+int transfer_basis(const Tables& t, const Basis& u, const std::vector<double>& w, Basis& out) {
+    out = u;
+    const int no = (int)t.orbit_star.size();
+    // first column of each orbit in u (columns are grouped by orbit)
+    std::vector<int64_t> first(no + 1, -1);
+    for (int64_t j = u.dim - 1; j >= 0; --j) first[u.col_orbit[j]] = j;
+    for_each_orbit(no, [&](int o) {
+        if (first[o] < 0) return;
+        const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
+        std::vector<cplx> M;
+        orbit_matrix(t, o, w.data(), M);
+        for (int64_t j = first[o]; j < u.dim && u.col_orbit[j] == o; ++j) {
+            const cplx* x = &u.coef[u.col_off[j]];
+            cplx* y = &out.coef[u.col_off[j]];
+            for (int64_t i = 0; i < n_o; ++i) y[i] = 0.0;
+            for (int64_t jj = 0; jj < n_o; ++jj) {
+                if (x[jj] == 0.0) continue;
+                const cplx* col = &M[(size_t)jj * n_o];
+                for (int64_t i = 0; i < n_o; ++i) y[i] += col[i] * x[jj];
+            }
+        }
+    });
     return BSE_OK;
 }
 

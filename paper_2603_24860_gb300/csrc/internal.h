@@ -67,6 +67,7 @@ struct Tables {
     std::vector<int32_t> orbit_of;      // [N]
     // band rotations Gamma(s): multiplet blocks, layout below
     std::vector<int64_t> gam_koff;      // [nk+1] entry offset of k within one s
+    std::vector<int64_t> gam_boff;      // [nk*nb] offset of the band's multiplet block from gam_koff[k]
     int64_t gam_per_s = 0;              // entries per operation
     std::vector<cplx> gamma;            // [nops * gam_per_s]
 };
@@ -86,6 +87,9 @@ struct Basis {
     std::vector<int64_t> star_col;        // [n_stars+1] column range of each star
 };
 int build_basis(const Tables& t, int mu, Basis& out);
+int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& out);
+int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam);
+int transfer_basis(const Tables& t, const Basis& u, const std::vector<double>& w, Basis& out);
 
 // ---------------------------------------------------------------------------
 // device-side view of the system (passed by value to kernels)
@@ -165,7 +169,7 @@ int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t 
 int launch_basis_dense(const DevBasis& b, double2* U, int64_t ld, cudaStream_t st);
 int launch_dipoles(const DevSys& s, double2* B, cudaStream_t st);
 int launch_bmu(const DevBasis& b, const double2* B, double2* Bmu, cudaStream_t st);
-int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, double* osc,
+int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, int nparts, double* osc,
                        cudaStream_t st);
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega,
                     int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);

@@ -496,24 +496,29 @@ int launch_bmu(const DevBasis& b, const double2* B, double2* Bmu, cudaStream_t s
     return BSE_OK;
 }
 
-// osc[l] = |sum_i a[i, l] Bmu[i]|^2, one warp per eigenvector
+// osc[l] = sum_p |sum_i a[i, l] Bmu[p][i]|^2, one warp per eigenvector
 __global__ void oscillator_kernel(const double2* __restrict__ a, int64_t lda, int64_t dim,
-                                  const double2* __restrict__ Bmu, double* osc) {
+                                  const double2* __restrict__ Bmu, int nparts, double* osc) {
     int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (l >= dim) return;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t i = lane; i < dim; i += 32) cfma(acc, a[l * lda + i], Bmu[i]);
-    for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    double tot = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int64_t i = lane; i < dim; i += 32) cfma(acc, a[l * lda + i], Bmu[(int64_t)p * dim + i]);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        tot += acc.x * acc.x + acc.y * acc.y;
     }
-    if (lane == 0) osc[l] = acc.x * acc.x + acc.y * acc.y;
+    if (lane == 0) osc[l] = tot;
 }
 
-int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, double* osc, cudaStream_t st) {
+int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, int nparts, double* osc,
+                       cudaStream_t st) {
     if (dim == 0) return BSE_OK;
-    oscillator_kernel<<<ceil_div(dim * 32, 256), 256, 0, st>>>(a, lda, dim, Bmu, osc);
+    oscillator_kernel<<<ceil_div(dim * 32, 256), 256, 0, st>>>(a, lda, dim, Bmu, nparts, osc);
     LAUNCH_CHECK();
     return BSE_OK;
 }
@@ -574,15 +579,27 @@ __global__ void wdiv_kernel(WdivGeom g, double* partial) {
             double sq = sqrt(disc);
             int lo = (int)floor((-Bq - sq) / (2.0 * A)) - 1;
             int hi = (int)ceil((-Bq + sq) / (2.0 * A)) + 1;
+            // exp(-b q^2) along the line by the exact recurrence
+            //   E(x3 + 1) = E(x3) R(x3),  R(x3 + 1) = R(x3) C,  C = exp(-2 b |s3|^2),
+            // restarted from exp every 64 points to bound the rounding growth
+            const double C2 = exp(-2.0 * g.b * A);
+            const double lim2 = g.lim * g.lim, in2 = (g.qmax - g.delta) * (g.qmax - g.delta);
+            double E = 0.0, Rr = 0.0;
             for (int x3 = lo; x3 <= hi; ++x3) {
                 double Q[3] = {p[0] + x3 * s3[0], p[1] + x3 * s3[1], p[2] + x3 * s3[2]};
                 double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
-                if (q2 <= 0.0) continue;
-                double q = sqrt(q2);
-                if (q > g.lim) continue;
+                if (((x3 - lo) & 63) == 0) {
+                    E = exp(-g.b * q2);
+                    Rr = exp(-g.b * (2.0 * (Q[0] * s3[0] + Q[1] * s3[1] + Q[2] * s3[2]) + A));
+                } else {
+                    E *= Rr;
+                    Rr *= C2;
+                }
+                if (q2 <= 0.0 || q2 > lim2) continue;
                 double w = 1.0;
-                if (q >= g.qmax - g.delta) {
-                    double x = (q - g.qmax) / g.delta;
+                if (q2 >= in2) {
+                    double x = (sqrt(q2) - g.qmax) / g.delta;
+                    if (x > 1.0) continue;
                     w = (x * x * x - 3.0 * x + 2.0) * 0.25;
                 }
                 double ql = 0.0;
@@ -590,7 +607,7 @@ __global__ void wdiv_kernel(WdivGeom g, double* partial) {
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) ql += Q[a] * g.L[3 * a + c] * Q[c];
-                acc += exp(-g.b * q2) * w / ql;
+                acc += E * w / ql;
             }
         }
     }

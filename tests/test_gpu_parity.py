@@ -241,3 +241,49 @@ def test_block_terms_fp32(gpu, terms):
     ref = project(b.basis(mu)[0], oracle_h("si4", code))
     got = bse.block(get("si4"), mu, prec=bse.BSE_FP32, terms=terms).cpu().numpy()
     assert _rel(got, ref) <= (TOL * 10 if terms == 2 else 1e-5)
+
+
+# --- partner (row) blocks of the optically active irreps ---
+
+@pytest.mark.parametrize("name", SMALL)
+def test_partner_blocks(gpu, name):
+    from oracle.projection import PartnerBasis, partner_spectrum
+    from oracle.spectrum import dipoles
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    t = bse.bse_tables(get(name))
+    H = oracle_h(name)
+    B = dipoles(inp, mt)
+    omega = torch.tensor(d["omega"], device="cuda")
+    for mu in b.bright():
+        pb = PartnerBasis(b, mu)
+        assert t["partner_dim"][mu] == pb.U[0].shape[1]
+        if pb.U[0].shape[1] == 0:
+            continue
+        ref = pb.U[0].conj().T @ H @ pb.U[0]
+        for prec, tol in ((bse.BSE_FP64, TOL), (bse.BSE_FP32, TOL32)):
+            got = bse.partner_block(get(name), mu, prec=prec).cpu().numpy()
+            assert _rel(got, ref) <= tol, (name, mu, prec)
+        h1 = bse.partner_block(get(name), mu)
+        om, osc, im = (x.cpu().numpy() for x in bse.partner_spectrum(get(name), mu, h1, omega, d["eta"]))
+        rom, rosc, rim = partner_spectrum(inp, ref, pb.U, B, d["omega"], d["eta"])
+        assert np.abs(om - rom).max() <= TOL
+        for cl in _clusters(rom):
+            assert abs(osc[cl].sum() - rosc[cl].sum()) <= 1e-9 * np.linalg.norm(B) ** 2
+        # the same spectrum as the whole irrep block
+        hb = bse.block(get(name), mu)
+        bom, bosc, bim = (x.cpu().numpy() for x in bse.spectrum(get(name), mu, hb, omega, d["eta"]))
+        assert np.abs(np.repeat(om, pb.d) - bom).max() <= TOL
+        scale = max(np.linalg.norm(bim), np.linalg.norm(B) ** 2 * 1e-3)
+        assert np.linalg.norm(im - bim) <= 1e-9 * scale
+
+
+def test_partner_unsupported_irrep(gpu):
+    bse, torch, get = gpu
+    t = bse.bse_tables(get("si2"))
+    mu = int(np.nonzero(t["bright"] == 0)[0][0])
+    assert t["partner_dim"][mu] == 0
+    buf = torch.empty(1, dtype=torch.complex128, device="cuda")
+    with pytest.raises(bse.BseError) as e:
+        bse.bse_build_partner_block(get("si2"), mu, bse.BSE_FP64, bse.BSE_TERM_ALL, buf, 1)
+    assert e.value.code == bse.BSE_EUNSUPPORTED

@@ -95,3 +95,19 @@ def test_fp32_build_within_0p1_mev(built):
     assert np.abs(om32 - om64).max() * 27211.386245988 <= 0.1
     assert np.linalg.norm(im32 - im64) <= 1e-3 * np.linalg.norm(im64)
     assert np.abs(h32.cpu().numpy() - h).max() <= 2e-6 * np.abs(h).max()
+
+
+def test_partner_block_levels(built):
+    """The T1u block is three copies of the partner block: levels and the
+    spectrum agree with the whole block (built above in FP64)."""
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    assert t["partner_dim"][mu] * 3 == t["block_dim"][mu]
+    h1 = bse.partner_block(ctx, mu)
+    omega = torch.tensor(d["omega"], device="cuda")
+    om1, osc1, im1 = (x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"]))
+    hd = torch.tensor(h, device="cuda").T.contiguous().T
+    om, osc, im = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, hd, omega, d["eta"]))
+    assert np.abs(np.repeat(om1, 3) - om).max() <= TOL
+    assert abs(osc1.sum() - osc.sum()) <= 1e-10 * osc.sum()
+    assert np.linalg.norm(im1 - im) <= 1e-9 * np.linalg.norm(im)
