@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--config", default="si8")
     p.add_argument("--block", choices=["partner", "full"], default="partner",
                    help="solve the partner block (dim/d, same levels and spectrum) or the whole irrep block")
-    p.add_argument("--prec", choices=["fp32", "fp64"], default="fp32",
+    p.add_argument("--prec", choices=["fp32", "fp64", "bf16"], default="fp32",
                    help="precision of the direct term; the FP64 build is also timed for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="approximate size of the oracle sample (CPU seconds)")
@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local):
     im = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    prec = bse.BSE_FP32 if args.prec == "fp32" else bse.BSE_FP64
+    prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64, "bf16": bse.BSE_BF16_SPLIT}[args.prec]
 
     def step(host_inputs=None, d2h=None, p=None):
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
@@ -374,7 +374,7 @@ def run_ours(args, rank, world, local):
     ms_eig = statistics.mean(s[1]["ms_eig"] for s in stats)
     direct_launches = stats[0][0]["direct_launches"]
     achieved = flops_direct / (ms_direct * 1e-3) / 1e12
-    peak = FP32_PEAK_TFLOPS if prec == bse.BSE_FP32 else FP64_PEAK_TFLOPS
+    peak = FP64_PEAK_TFLOPS if prec == bse.BSE_FP64 else FP32_PEAK_TFLOPS
     value = flops_build * args.steps * world / (total_ms * 1e-3) / 1e12
     out = {
         "metric": METRIC,
@@ -387,7 +387,7 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == bse.BSE_FP32 else "f64",
+        "dtype": {bse.BSE_FP32: "f32", bse.BSE_FP64: "f64", bse.BSE_BF16_SPLIT: "bf16x3"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
                    "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
@@ -395,8 +395,13 @@ def run_ours(args, rank, world, local):
                              "whole block" % (dim, int(tab["block_dim"][mu]), int(tab["irrep_dim"][mu])))
                             if partner else "whole irrep block",
                    "block_dim": int(tab["block_dim"][mu]), "solved_dim": dim, "full_dim": int(tab["n_product"]),
-                   "precision": ("direct term FP32 on CUDA cores; diagonal, projection, exchange and "
-                                 "eigensolver FP64") if prec == bse.BSE_FP32 else "FP64 throughout",
+                   "precision": {bse.BSE_FP32: "direct term FP32 on CUDA cores; diagonal, projection, exchange "
+                                               "and eigensolver FP64",
+                                 bse.BSE_FP64: "FP64 throughout",
+                                 bse.BSE_BF16_SPLIT: "pair densities FP32 on CUDA cores, dense contractions on "
+                                                     "tcgen05 tensor cores with bf16 hi+lo operands (3 products) "
+                                                     "and FP32 accumulation; diagonal, projection, exchange and "
+                                                     "eigensolver FP64"}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
@@ -409,10 +414,14 @@ def run_ours(args, rank, world, local):
         "build_flops": flops_build,
         "work": {k: work[k] for k in ("rho", "contract", "project", "exchange", "overlap")},
         "build_tflops_kernels": flops_build / ((ms_direct + ms_project + ms_exchange) * 1e-3) / 1e12,
-        "roofline": {"bound": "alu", "kernel": "direct_kernel<%s>" % ("float" if prec == bse.BSE_FP32 else "double"),
+        "roofline": {"bound": "alu", "kernel": {bse.BSE_FP32: "direct_kernel<float>", bse.BSE_FP64: "direct_kernel<double>",
+                                                bse.BSE_BF16_SPLIT: "direct_tc_kernel"}[prec],
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": ("derived: 152 SMs x %s x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
-                                     "CUDA-core figure)" % ("128 FFMA/clk" if prec == bse.BSE_FP32 else "2 DFMA/clk")),
+                                     "CUDA-core figure)%s" % ("2 DFMA/clk" if prec == bse.BSE_FP64 else "128 FFMA/clk",
+                                                               "; the split kernel is bounded by its FP32 pair "
+                                                               "densities, its tensor share is reported separately"
+                                                               if prec == bse.BSE_BF16_SPLIT else "")),
                      "flops_per_launch": flops_direct / max(direct_launches, 1),
                      "launches_per_step": direct_launches,
                      "traffic": DIRECT_TRAFFIC.get((args.config, args.prec))},

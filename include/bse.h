@@ -55,9 +55,12 @@ enum {
     BSE_ESOLVER = -7       /* the dense eigensolver failed */
 };
 
-/* precision of the direct term: FP64 throughout, or FP32 CUDA-core arithmetic
-   (pair densities and contractions; the diagonal, the projection and the
-   exchange stay FP64); the split BF16/FP16 tensor-core modes are reserved */
+/* precision of the direct term: FP64 throughout; FP32 CUDA-core arithmetic;
+   or BF16_SPLIT: pair densities in FP32 on CUDA cores and both dense
+   contractions (W(q) conj(rho_vv') and rho_cc'^T T) on the tensor cores with
+   every operand split into bf16 hi + lo and three products accumulated in
+   FP32.  The diagonal, the projection and the exchange stay FP64.
+   FP16_SPLIT is reserved. */
 enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2, BSE_FP32 = 3 };
 
 /* terms of H to include (bit mask) */
@@ -162,8 +165,10 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  * once (Sec. III.C.5), the exchange term is applied in the projected form
  * (U_mu^dagger P) vbar (U_mu^dagger P)^dagger (Eq. v_scalar), the diagonal
  * eps_c - eps_v - W^div in FP64.  terms: BSE_TERM_* mask.
- * prec: BSE_FP64 or BSE_FP32 (direct term on CUDA cores in FP32; the other
- * stages stay FP64); the split modes return EUNSUPPORTED for now.  h_dev: device, complex128, column-major dim x dim with
+ * prec: BSE_FP64, BSE_FP32 or BSE_BF16_SPLIT (see the precision enum); the
+ * split mode needs NG_max <= 64, nv <= 4 and nc <= 8 and returns
+ * EUNSUPPORTED otherwise; FP16_SPLIT returns EUNSUPPORTED.  ETIMEOUT if a
+ * bounded wait of the tensor-core kernel gave up (the context stays usable).  h_dev: device, complex128, column-major dim x dim with
  * leading dimension ld >= dim; the full Hermitian matrix is written.
  * Scratch is library-owned.
  */

@@ -91,6 +91,9 @@ struct bse_ctx {
     DevBuf de;           // eps_c - eps_v per product index (FP64)
     DevBuf coef32, w32;  // FP32 copies for the FP32 build, made on first use
     bool narrow_ready = false;
+    DevBuf wemb;         // split-precision W(q) embeddings for the tensor-core build
+    int wemb_ngp = 0;
+    DevBuf groups, status;
     // scratch (library-owned, grow-only)
     DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum, counter;
     cusolverDnHandle_t solver = nullptr;
@@ -253,6 +256,14 @@ static int ensure_dipoles(bse_ctx* c) {
     BSE_TRY(ensure(c->B, sizeof(double2) * (size_t)c->t.N));
     BSE_TRY(launch_dipoles(c->S, (double2*)c->B.p, c->stream));
     c->B_ready = true;
+    return BSE_OK;
+}
+
+static int ensure_wemb(bse_ctx* c, int ngp) {
+    if (c->wemb_ngp == ngp) return BSE_OK;
+    BSE_TRY(ensure(c->wemb, sizeof(uint16_t) * (size_t)c->t.nk * 2 * 128 * 2 * ngp));
+    BSE_TRY(launch_wemb(c->S, ngp, c->wemb.p, c->stream));
+    c->wemb_ngp = ngp;
     return BSE_OK;
 }
 
@@ -575,7 +586,7 @@ static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
-                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32})
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -704,7 +715,13 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
 
 // U^dagger H U for an orbit-sparse basis U (an irrep block or a partner block)
 static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms, void* h, int64_t ld) {
-    const int p32 = prec == BSE_FP32;
+    const int tcp = prec == BSE_BF16_SPLIT;
+    const int p32 = prec == BSE_FP32 || tcp;   // the tile arena is FP32 for both
+    int ngp = 0;
+    if (tcp && (terms & BSE_TERM_DIRECT)) {
+        size_t sm = 0;
+        BSE_TRY(tc_supported(c->S, ngp, sm));
+    }
     const Tables& t = c->t;
     const Basis& bh = bd.host;
     const int64_t dim = bh.dim;
@@ -726,6 +743,11 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
         Pmu = (const double2*)c->Pmu.p;
     }
     if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
+    if (tcp && (terms & BSE_TERM_DIRECT)) {
+        BSE_TRY(ensure_wemb(c, ngp));
+        BSE_TRY(ensure(c->status, sizeof(int)));
+        BSE_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+    }
     const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
     std::vector<Batch> batches;
     plan_batches(t, bh, arena_budget(), batches);
@@ -736,10 +758,44 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
     for (const Batch& bt : batches) {
         BSE_TRY(ensure(c->arenaX, bt.xbytes / sizeof(double2) * xel));
         BSE_TRY(ensure(c->arenaY, bt.ybytes));
-        BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
+        std::vector<TcGroup> groups;
+        if (tcp && (terms & BSE_TERM_DIRECT)) {
+            // the tensor-core kernel takes groups of pairs with the same q
+            std::vector<PairTask> sorted(bt.tasks);
+            std::vector<int> qof(sorted.size());
+            for (size_t i = 0; i < sorted.size(); ++i) {
+                int iq[3];
+                for (int a = 0; a < 3; ++a)
+                    iq[a] = (t.kidx[3 * sorted[i].k + a] - t.kidx[3 * sorted[i].kp + a] + t.n[a]) % t.n[a];
+                qof[i] = (iq[0] * t.n[1] + iq[1]) * t.n[2] + iq[2];
+            }
+            std::vector<size_t> order(sorted.size());
+            for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return qof[a] < qof[b]; });
+            for (size_t i = 0; i < order.size(); ++i) sorted[i] = bt.tasks[order[i]];
+            for (size_t i = 0; i < order.size();) {
+                TcGroup gp;
+                gp.first = (int32_t)i;
+                gp.q = qof[order[i]];
+                gp.count = 0;
+                while (i < order.size() && qof[order[i]] == gp.q && gp.count < 4) {
+                    ++gp.count;
+                    ++i;
+                }
+                groups.push_back(gp);
+            }
+            BSE_TRY(upload(c->tasks, sorted.data(), sorted.size(), c->stream));
+            BSE_TRY(upload(c->groups, groups.data(), groups.size(), c->stream));
+        } else {
+            BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
+        }
         BSE_TRY(upload(c->tiles, bt.tiles.data(), bt.tiles.size(), c->stream));
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
-        if (terms & BSE_TERM_DIRECT) {
+        if ((terms & BSE_TERM_DIRECT) && tcp) {
+            BSE_TRY(launch_direct_tc(c->S, c->coef32.p, c->wemb.p, ngp, (const PairTask*)c->tasks.p,
+                                     (const TcGroup*)c->groups.p, (int64_t)groups.size(), c->arenaX.p,
+                                     (int*)c->status.p, c->stream));
+        } else if (terms & BSE_TERM_DIRECT) {
             BSE_TRY(launch_direct(c->S, p32, p32 ? c->coef32.p : (const void*)c->S.coef,
                                   p32 ? c->w32.p : (const void*)c->S.w, (const PairTask*)c->tasks.p,
                                   (int64_t)bt.tasks.size(), c->arenaX.p, c->stream));
@@ -764,13 +820,20 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
             c->stats.direct_launches += 1;
         }
     }
+    if (tcp && (terms & BSE_TERM_DIRECT)) {
+        int st = 0;
+        BSE_CUDA(cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+        if (st) return fail(BSE_ETIMEOUT, "a bounded wait of the tensor-core direct kernel gave up");
+    }
     return BSE_OK;
 }
 
 int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+        return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     BSE_TRY(ensure_basis(c, mu));
     return build_generic(c, c->irr[mu], prec, terms, h, ld);
 }
@@ -778,7 +841,8 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
 int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32) return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+        return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     BSE_TRY(ensure_partner(c, mu));
     return build_generic(c, c->partner[mu].part[0], prec, terms, h, ld);
 }

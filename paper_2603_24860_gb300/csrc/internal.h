@@ -123,6 +123,11 @@ struct PairTask {
     int32_t flags;          // 1: also write the mirrored (conjugate) block
 };
 
+// a group of k pairs with the same q = k - k' (tensor-core direct term)
+struct TcGroup {
+    int32_t first, count, q;   // range in the q-sorted task list
+};
+
 // a star-pair tile for the projection kernels
 struct TileTask {
     int64_t xoff, yoff;     // tile origins (elements) of X and Y
@@ -163,6 +168,11 @@ int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, co
                         double w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
 int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st);
 void note_launch();
+// split-precision tensor-core direct term (direct_tc.cu)
+int tc_supported(const DevSys& s, int& ngp, size_t& smem);
+int launch_wemb(const DevSys& s, int ngp, void* out, cudaStream_t st);
+int launch_direct_tc(const DevSys& s, const void* coef32, const void* wemb, int ngp, const PairTask* tasks,
+                     const TcGroup* groups, int64_t ngroups, void* X, int* status, cudaStream_t st);
 int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
 int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
                          double2* H, int64_t ld, cudaStream_t st);

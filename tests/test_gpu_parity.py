@@ -287,3 +287,49 @@ def test_partner_unsupported_irrep(gpu):
     with pytest.raises(bse.BseError) as e:
         bse.bse_build_partner_block(get("si2"), mu, bse.BSE_FP64, bse.BSE_TERM_ALL, buf, 1)
     assert e.value.code == bse.BSE_EUNSUPPORTED
+
+
+# --- BF16-split tensor-core direct term (tcgen05), FP32 accumulation ---
+TOLBF = 2e-5          # H_mu elements relative to the largest element
+
+
+@pytest.mark.parametrize("name", ["si2", "si4", "lif4"])
+def test_blocks_bf16_split(gpu, name):
+    from oracle.projection import PartnerBasis, project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    H = oracle_h(name)
+    for mu in b.bright():
+        U, _ = b.basis(mu)
+        if U.shape[1] == 0:
+            continue
+        ref = project(U, H)
+        got = bse.block(get(name), mu, prec=bse.BSE_BF16_SPLIT).cpu().numpy()
+        assert _rel(got, ref) <= TOLBF, (name, mu, _rel(got, ref))
+        assert np.abs(np.linalg.eigvalsh(got) - np.linalg.eigvalsh(ref)).max() * HA_MEV <= 0.1
+        pb = PartnerBasis(b, mu)
+        ref1 = pb.U[0].conj().T @ H @ pb.U[0]
+        got1 = bse.partner_block(get(name), mu, prec=bse.BSE_BF16_SPLIT).cpu().numpy()
+        assert _rel(got1, ref1) <= TOLBF
+
+
+def test_bf16_split_direct_term_only(gpu):
+    """The split mode changes only the direct term."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case("si4")
+    mu = b.bright()[0]
+    ref = project(b.basis(mu)[0], oracle_h("si4", "w"))
+    got = bse.block(get("si4"), mu, prec=bse.BSE_BF16_SPLIT, terms=4).cpu().numpy()
+    assert _rel(got, ref) <= 2e-4      # relative to the largest element of K^d alone
+
+
+def test_bf16_split_rejects_large_spheres(gpu):
+    bse, torch, get = gpu
+    t = bse.bse_tables(get("mos2_331"))
+    mu = int(np.nonzero(t["bright"])[0][0])
+    buf = torch.empty(max(int(t["block_dim"][mu]) ** 2, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(bse.BseError) as e:
+        bse.bse_build_block(get("mos2_331"), mu, bse.BSE_BF16_SPLIT, bse.BSE_TERM_ALL, buf,
+                            max(int(t["block_dim"][mu]), 1))
+    assert e.value.code == bse.BSE_EUNSUPPORTED

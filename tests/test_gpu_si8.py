@@ -111,3 +111,16 @@ def test_partner_block_levels(built):
     assert np.abs(np.repeat(om1, 3) - om).max() <= TOL
     assert abs(osc1.sum() - osc.sum()) <= 1e-10 * osc.sum()
     assert np.linalg.norm(im1 - im) <= 1e-9 * np.linalg.norm(im)
+
+
+def test_bf16_split_build_within_0p1_mev(built):
+    """Tensor-core split-precision direct term vs the FP64 build."""
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    hb = bse.block(ctx, mu, prec=bse.BSE_BF16_SPLIT)
+    h64 = torch.tensor(h, device="cuda").T.contiguous().T
+    omega = torch.tensor(d["omega"], device="cuda")
+    om64, osc64, im64 = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, h64, omega, d["eta"]))
+    omb, oscb, imb = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, hb, omega, d["eta"]))
+    assert np.abs(omb - om64).max() * 27211.386245988 <= 0.1
+    assert np.linalg.norm(imb - im64) <= 1e-3 * np.linalg.norm(im64)
