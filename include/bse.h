@@ -194,6 +194,14 @@ int bse_build_partner_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t 
                             void* h_dev, int64_t ld);
 
 /*
+ * bse_block_star_columns - column ranges of the k stars in the block of an
+ * irrep (partner = 0) or in its partner block (partner = 1): the basis
+ * vectors of star a are columns [out[a], out[a+1]); out is a host array of
+ * n_stars + 1 entries.  Builds the basis if needed.
+ */
+int bse_block_star_columns(bse_ctx* ctx, int32_t irrep, int32_t partner, int64_t* out);
+
+/*
  * bse_build_full - the unprojected H (N x N, complex128, column-major, ld
  * >= N, device) in FP64; meant for checks on small meshes.
  */

@@ -194,3 +194,54 @@ def partner_spectrum(inp, H1, Us, B, omega, eta):
     Om, a = np.linalg.eigh(H1)
     osc = sum(np.abs(a.T @ (U.T @ B)) ** 2 for U in Us)
     return Om, osc, lorentz_sum(inp, Om, osc, omega, eta)
+
+
+def star_basis(inp: Inputs, grp: Group, mt: MeshTables, orbit_list, star: int, weights):
+    """The canonical basis columns that live on the orbits of one k star, for
+    the operator sum_s weights[s] Gamma~(s) (an irrep projector: d/|S| chi*;
+    a row projector: d/|S| conj(Gamma_mu(s)_11)).  Same construction as
+    Basis.basis restricted to one star, for sampled checks on large meshes.
+    Returns (product indices of the star's rows, [n_rows x n_cols] array)."""
+    nv, nc = inp.nv, inp.nc
+    ks = [int(k) for k in mt.stars[star]]
+    rows = np.concatenate([np.arange(k * nv * nc, (k + 1) * nv * nc) for k in ks])
+    pos = {int(I): i for i, I in enumerate(rows)}
+    rot = {}
+    cols = []
+    for mem in orbit_list:
+        if int(mem[0]) // (nv * nc) not in ks:
+            continue
+        loc = {int(I): i for i, I in enumerate(mem)}
+        n_o = len(mem)
+        P = np.zeros((n_o, n_o), dtype=np.complex128)
+        for jj, I in enumerate(mem):
+            k, v, c = int(I) // (nv * nc), (int(I) // nc) % nv, int(I) % nc
+            vm = [m for m in multiplets(inp.eps[k], 0, nv) if v in m][0]
+            cm = [m for m in multiplets(inp.eps[k], nv, nv + nc) if nv + c in m][0]
+            for s in range(grp.n):
+                if weights[s] == 0:
+                    continue
+                if (s, k) not in rot:
+                    rot[(s, k)] = band_rotation(inp, grp, mt, s, k)
+                g = rot[(s, k)]
+                k2 = int(mt.rotk[s, k])
+                for vp in vm:
+                    for cp in cm:
+                        J = (k2 * nv + vp) * nc + (cp - nv)
+                        P[loc[J], jj] += weights[s] * g[cp, nv + c] * np.conj(g[vp, v])
+        acc = []
+        for jj in range(n_o):
+            x = P[:, jj].copy()
+            for _ in range(2):
+                for u in acc:
+                    x = x - u * np.vdot(u, x)
+            nrm = np.linalg.norm(x)
+            if nrm > KEEP_TOL:
+                acc.append(x / nrm)
+        for u in acc:
+            full = np.zeros(len(rows), dtype=np.complex128)
+            for i, I in enumerate(mem):
+                full[pos[int(I)]] = u[i]
+            cols.append(full)
+    U = np.array(cols).T if cols else np.zeros((len(rows), 0), dtype=np.complex128)
+    return rows, U

@@ -84,6 +84,7 @@ EXPORTS = {
     "bse_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "bse_get_stats": (C.c_int, [C.c_void_p, C.POINTER(BseStats)]),
     "bse_head_correction_noalloc": (C.c_int, [_PD, _P32, _PD, C.c_void_p, C.c_void_p]),
+    "bse_block_star_columns": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _P64]),
 }
 
 _lib = None
@@ -249,6 +250,14 @@ def bse_build_partner_block(ctx: Context, irrep: int, prec: int, terms: int, out
 def bse_partner_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float, omega_out, osc, im_eps):
     _check(lib().bse_partner_spectrum(ctx.handle, irrep, _ptr(h), ld, _ptr(omega), omega.numel(), eta,
                                       _ptr(omega_out), _ptr(osc), _ptr(im_eps)))
+
+
+def bse_block_star_columns(ctx: Context, irrep: int, partner: bool = False):
+    """Column range [out[a], out[a+1]) of each k star in the (partner) block."""
+    n = int(bse_tables(ctx)["n_stars"])
+    out = np.zeros(n + 1, dtype=np.int64)
+    _check(lib().bse_block_star_columns(ctx.handle, irrep, 1 if partner else 0, out.ctypes.data_as(_P64)))
+    return out
 
 
 def bse_build_full(ctx: Context, terms: int, out, ld: int):

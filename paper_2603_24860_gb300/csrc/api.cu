@@ -847,6 +847,16 @@ int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms
     return build_generic(c, c->partner[mu].part[0], prec, terms, h, ld);
 }
 
+int bse_block_star_columns(bse_ctx* c, int32_t mu, int32_t partner, int64_t* out) {
+    clear_error();
+    if (!c || !out) return fail(BSE_EINVAL, "null argument");
+    if (partner) BSE_TRY(ensure_partner(c, mu));
+    else BSE_TRY(ensure_basis(c, mu));
+    const Basis& bh = partner ? c->partner[mu].part[0].host : c->irr[mu].host;
+    std::copy(bh.star_col.begin(), bh.star_col.end(), out);
+    return BSE_OK;
+}
+
 int bse_block_basis(bse_ctx* c, int32_t mu, void* u, int64_t ld) {
     clear_error();
     if (!c || !u) return fail(BSE_EINVAL, "null argument");

@@ -1,0 +1,76 @@
+"""Full-size checks for the Si-like 12x12x12 mesh (Nv = 4, Nc = 8,
+|G| <= 4.0 (2 pi / a), N = 55296): the T1u partner block is built in FP64
+and FP32 in the launch configuration of the benchmark; sampled star-pair
+sub-blocks are compared with the oracle (its canonical basis restricted to
+the two stars, U_a^dagger H_ab U_b), and the FP32 levels with the FP64
+ones (0.1 meV)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wdiv.json")))
+HA_MEV = 27211.386245988
+
+
+@pytest.fixture(scope="module")
+def si12():
+    import torch
+    from paper_2603_24860_gb300 import bse
+    from synth import generate
+    from oracle.hamiltonian import Inputs
+    from oracle.tables import Group, MeshTables, orbits
+    d = generate("si12")
+    ctx = bse.bse_create(d, stream=torch.cuda.current_stream())
+    t = bse.bse_tables(ctx)
+    mu = int(np.nonzero(t["bright"])[0][0])
+    h64 = bse.partner_block(ctx, mu, prec=bse.BSE_FP64)
+    h32 = bse.partner_block(ctx, mu, prec=bse.BSE_FP32)
+    cols = bse.bse_block_star_columns(ctx, mu, partner=True)
+    inp = Inputs(d)
+    grp = Group(d["rot"], d["tau"], d["lattice"])
+    mt = MeshTables(grp, d["mesh"])
+    orb = orbits(mt, inp.eps, inp.nv, inp.nc)
+    yield bse, torch, ctx, t, mu, h64, h32, cols, d, inp, grp, mt, orb
+    bse.bse_destroy(ctx)
+
+
+def test_head_correction(si12):
+    bse, torch, ctx, t, *_ = si12
+    assert abs(t["w_div"] - GOLD["si12"]) <= 1e-10 * GOLD["si12"]
+
+
+@pytest.mark.parametrize("pair", ["gamma-large", "small-mid", "mid-mid"])
+def test_sampled_partner_sub_blocks(si12, pair):
+    from oracle.hamiltonian import hamiltonian_block
+    from oracle.projection import partner_irrep_matrices, star_basis
+    bse, torch, ctx, t, mu, h64, h32, cols, d, inp, grp, mt, orb = si12
+    chi, dims, cls = grp.characters()
+    gam = partner_irrep_matrices(grp, chi[mu], int(dims[mu]))
+    w = int(dims[mu]) / grp.n * gam[:, 0, 0]
+    sizes = np.array([len(s) for s in mt.stars])
+    big, mid, small = (int(np.nonzero(sizes == n)[0][0]) for n in (48, 12, 6))
+    a, b = {"gamma-large": (0, big), "small-mid": (small, mid), "mid-mid": (mid, mid)}[pair]
+    ra, Ua = star_basis(inp, grp, mt, orb, a, w)
+    rb, Ub = star_basis(inp, grp, mt, orb, b, w)
+    assert Ua.shape[1] == cols[a + 1] - cols[a] and Ub.shape[1] == cols[b + 1] - cols[b]
+    if Ua.shape[1] == 0 or Ub.shape[1] == 0:
+        pytest.skip("star carries no partner vectors")
+    Hab = hamiltonian_block(inp, mt, [int(k) for k in mt.stars[a]], [int(k) for k in mt.stars[b]], GOLD["si12"])
+    ref = Ua.conj().T @ Hab @ Ub
+    scale = float(torch.max(torch.abs(h64)).item())
+    sub = lambda h: h[cols[a]:cols[a + 1], cols[b]:cols[b + 1]].cpu().numpy()
+    assert np.abs(sub(h64) - ref).max() <= 1e-10 * scale
+    assert np.abs(sub(h32) - ref).max() <= 2e-6 * scale
+
+
+def test_fp32_levels_within_0p1_mev(si12):
+    bse, torch, ctx, t, mu, h64, h32, cols, d, *_ = si12
+    omega = torch.tensor(d["omega"], device="cuda")
+    om64, osc64, im64 = (x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h64, omega, d["eta"]))
+    om32, osc32, im32 = (x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h32, omega, d["eta"]))
+    assert np.abs(om32 - om64).max() * HA_MEV <= 0.1
+    assert np.linalg.norm(im32 - im64) <= 1e-3 * np.linalg.norm(im64)

@@ -63,3 +63,20 @@ def test_partner_spectrum_equals_block_spectrum(name):
         Om, osc, im = spc.block_spectrum(inp, pj.project(U, H), U, B, d["omega"], d["eta"])
         assert abs(osc1.sum() - osc.sum()) <= 1e-12 * np.linalg.norm(B) ** 2
         assert np.linalg.norm(im1 - im) <= 1e-10 * max(np.linalg.norm(im), 1e-300) + 1e-30
+
+
+def test_star_basis_matches_global_basis():
+    """The star-restricted construction used for sampled checks on large
+    meshes reproduces the global canonical bases column by column."""
+    d, inp, grp, mt, b = oracle_case("si4")
+    mu = b.bright()[0]
+    U, _ = b.basis(mu)
+    pb = pj.PartnerBasis(b, mu)
+    for W, w in ((U, b.dims[mu] / grp.n * b.chi[mu].astype(float)),
+                 (pb.U[0], pb.d / grp.n * pb.gam[:, 0, 0])):
+        col = 0
+        for a in range(len(mt.stars)):
+            rows, Ua = pj.star_basis(inp, grp, mt, b.orbits, a, w)
+            assert np.abs(W[np.ix_(rows, np.arange(col, col + Ua.shape[1]))] - Ua).max() < 1e-12
+            col += Ua.shape[1]
+        assert col == W.shape[1]
