@@ -45,7 +45,7 @@ WORKLOADS = {
            "T1u block of the full dim 12288",
     "si4": "Si-like diamond (Oh), 4x4x4 mesh, Nv=Nc=4, |G|<=3.2 (2pi/a); T1u block of the full dim 1024",
     "si12": "Si-like diamond (Oh), 12x12x12 mesh, Nv=4, Nc=8, |G|<=4.0 (2pi/a); T1u block of the full dim 55296",
-    "lif10": "LiF-like rocksalt (Oh, a=7.6 bohr), 10x10x10 mesh, Nv=3, Nc=6; T1u block of the full dim 18000",
+    "lif10": "LiF-like rocksalt (Oh, a=7.6 bohr, gap 14 eV, eps_inf 1.9), 10x10x10 mesh, Nv=3, Nc=6, full dim 18000",
 }
 
 
@@ -56,8 +56,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--config", default="si8")
-    p.add_argument("--block", choices=["partner", "full"], default="partner",
-                   help="solve the partner block (dim/d, same levels and spectrum) or the whole irrep block")
+    p.add_argument("--block", choices=["partner", "full", "all"], default="partner",
+                   help="solve the partner block (dim/d, same levels and spectrum), the whole irrep block, or "
+                        "build every irrep block in one pass and solve each")
     p.add_argument("--prec", choices=["fp32", "fp64", "bf16"], default="fp32",
                    help="precision of the direct term; the FP64 build is also timed for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -269,22 +270,33 @@ def run_ours(args, rank, world, local):
     omega = torch.tensor(inp["omega"], device=dev)
     eta = float(inp["eta"])
 
-    # untimed discovery: the bright irrep, its dimension and the algorithmic work
+    # untimed discovery: the bright irrep, the blocks solved, their dimensions and the algorithmic work
     ctx = bse.bse_create(inp, stream=stream, device=devin)
     tab = bse.bse_tables(ctx)
     mu = int(np.nonzero(tab["bright"])[0][0])
     partner = args.block == "partner"
-    dim = int(tab["partner_dim"][mu] if partner else tab["block_dim"][mu])
-    work = bse.bse_build_work(ctx, mu, partner)
+    if args.block == "all":
+        # every irrep; an irrep contained once in the polar-vector representation through its
+        # partner block (same levels, each once, and the same spectrum)
+        targets = [m for m in range(int(tab["n_irreps"])) if tab["block_dim"][m] > 0]
+        pflags = [int(tab["partner_dim"][m] > 0) for m in targets]
+    else:
+        targets = [mu]
+        pflags = [int(partner)]
+    dims = [int(tab["partner_dim"][m] if p else tab["block_dim"][m]) for m, p in zip(targets, pflags)]
+    dim = dims[targets.index(mu)]
+    work = bse.bse_build_blocks_work(ctx, targets, pflags)
     launches_base = bse.bse_get_stats(ctx)["launches"]
     bse.bse_destroy(ctx)
     flops_build = work["rho"] + work["contract"] + work["project"] + work["exchange"]
     flops_direct = work["rho"] + work["contract"]
 
-    H = torch.empty(dim * dim, dtype=torch.complex128, device=dev)
-    om = torch.empty(dim, dtype=torch.float64, device=dev)
-    osc = torch.empty(dim, dtype=torch.float64, device=dev)
-    im = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
+    Hs = [torch.empty(n * n, dtype=torch.complex128, device=dev) for n in dims]
+    oms = [torch.empty(n, dtype=torch.float64, device=dev) for n in dims]
+    oscs = [torch.empty(n, dtype=torch.float64, device=dev) for n in dims]
+    ims = [torch.empty(omega.numel(), dtype=torch.float64, device=dev) for _ in dims]
+    ib = targets.index(mu)
+    om, im = oms[ib], ims[ib]
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64, "bf16": bse.BSE_BF16_SPLIT}[args.prec]
@@ -293,14 +305,20 @@ def run_ours(args, rank, world, local):
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
                              device=None if host_inputs is not None else devin)
         bse.bse_set_timing(ctx, True)
-        build = bse.bse_build_partner_block if partner else bse.bse_build_block
-        solve = bse.bse_partner_spectrum if partner else bse.bse_block_spectrum
-        build(ctx, mu, prec if p is None else p, bse.BSE_TERM_ALL, H, dim)
+        bse.bse_build_blocks(ctx, targets, pflags, prec if p is None else p, bse.BSE_TERM_ALL, Hs, dims)
         s1 = bse.bse_get_stats(ctx)
-        solve(ctx, mu, H, dim, omega, eta, om, osc, im)
+        eig = 0.0
+        solvers = []
+        for m, pf, n, H, o, s, i in zip(targets, pflags, dims, Hs, oms, oscs, ims):
+            (bse.bse_partner_spectrum if pf else bse.bse_block_spectrum)(ctx, m, H, n, omega, eta, o, s, i)
+            st = bse.bse_get_stats(ctx)
+            eig += st["ms_eig"]
+            solvers.append(st["solver"])
         s2 = bse.bse_get_stats(ctx)
+        s2["ms_eig"] = eig
+        s2["solvers"] = solvers
         if d2h is not None:
-            for src, dst in zip((om, osc, im), d2h):
+            for src, dst in zip([x for t in zip(oms, oscs, ims) for x in t], d2h):
                 dst.copy_(src, non_blocking=True)
         return ctx, s1, s2
 
@@ -334,6 +352,7 @@ def run_ours(args, rank, world, local):
     wall = time.perf_counter() - w0
     clocks = sampler.stop()
     om_main, im_main = om.cpu().numpy().copy(), im.cpu().numpy().copy()
+    om_all = [o.cpu().numpy().copy() for o in oms]
     # the library's launch counter is process-wide; read at the end of each step
     launches = stats[-1][1]["launches"] - (warm[-1][1]["launches"] if warm else launches_base)
     total_ms = max_over_ranks(sum(per), world)
@@ -347,7 +366,7 @@ def run_ours(args, rank, world, local):
             pin[k] = t.numpy()
     host_inputs = dict(inp)
     host_inputs.update(pin)
-    outs = [torch.empty(x.numel(), dtype=x.dtype, pin_memory=True) for x in (om, osc, im)]
+    outs = [torch.empty(x.numel(), dtype=x.dtype, pin_memory=True) for t in zip(oms, oscs, ims) for x in t]
     timed(1, host_inputs, outs)
     barrier(world)
     e2e_per, _ = timed(args.steps, host_inputs, outs)
@@ -363,10 +382,12 @@ def run_ours(args, rank, world, local):
         timed(1, p=bse.BSE_FP64)
         per64, stats64 = timed(max(1, min(args.steps, 3)), p=bse.BSE_FP64)
         om64, im64 = om.cpu().numpy(), im.cpu().numpy()
+        dall = max(float(np.abs(a - b.cpu().numpy()).max()) for a, b in zip(om_all, oms) if len(a))
         cmp = {"ms_per_step": max_over_ranks(statistics.mean(per64), world),
                "stage_ms": {"direct": statistics.mean(x[0]["ms_direct"] for x in stats64),
                             "eigensolve": statistics.mean(x[1]["ms_eig"] for x in stats64)},
                "max_dOmega_meV": float(np.abs(om_main - om64).max() * HA_MEV),
+               "max_dOmega_meV_all_blocks": dall * HA_MEV,
                "spectrum_rel_l2": float(np.linalg.norm(im_main - im64) / np.linalg.norm(im64))}
     ms_direct = statistics.mean(s[0]["ms_direct"] for s in stats)
     ms_project = statistics.mean(s[0]["ms_project"] for s in stats)
@@ -393,7 +414,11 @@ def run_ours(args, rank, world, local):
                    "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
                    "block": ("partner block of the irrep (dim %d = %d/%d): same levels and spectrum as the "
                              "whole block" % (dim, int(tab["block_dim"][mu]), int(tab["irrep_dim"][mu])))
-                            if partner else "whole irrep block",
+                            if partner else ("all %d irreps in one build (one direct pass): %d whole blocks and "
+                                             "%d partner blocks, each solved" % (len(targets), len(targets) - sum(pflags),
+                                                                                sum(pflags))
+                                             if args.block == "all" else "whole irrep block"),
+                   "block_dims": dims,
                    "block_dim": int(tab["block_dim"][mu]), "solved_dim": dim, "full_dim": int(tab["n_product"]),
                    "precision": {bse.BSE_FP32: "direct term FP32 on CUDA cores; diagonal, projection, exchange "
                                                "and eigensolver FP64",
@@ -406,6 +431,8 @@ def run_ours(args, rank, world, local):
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
         "time_to_spectrum_ms": total_ms / args.steps,
+        "eigensolver": sorted({{1: "dense zheevd", 2: "tridiagonal reduction (no eigenvectors)"}[s]
+                               for s in stats[-1][1]["solvers"]}),
         "stage_ms": {"direct": ms_direct, "project": ms_project, "exchange": ms_exchange, "eigensolve": ms_eig,
                      "create": statistics.mean(x[1]["ms_create"] for x in stats),
                      "create_parts": {k: statistics.mean(x[1][k] for x in stats)

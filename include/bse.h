@@ -194,6 +194,22 @@ int bse_build_partner_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t 
                             void* h_dev, int64_t ld);
 
 /*
+ * bse_build_blocks - several blocks in one build: target i is the block of
+ * irrep[i] (partner == NULL or partner[i] == 0) or its partner block
+ * (partner[i] != 0), written to h_dev[i] (device, complex128 column-major,
+ * leading dimension ld[i]; may be NULL when the block is empty).  Sec. III.C
+ * decomposes H into the blocks of all irreps; their direct terms share the
+ * same k-pair matrix elements, so the direct kernel runs once per star pair
+ * and every target projects the same tiles (Eqs. transformationU, Hblock).
+ * irrep, partner, h_dev and ld are host arrays of n entries, borrowed for the
+ * call.  The result of each target equals that of bse_build_block or
+ * bse_build_partner_block with the same arguments.  Errors as
+ * bse_build_block, reported for the first target that fails.
+ */
+int bse_build_blocks(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
+                     uint32_t terms, void* const* h_dev, const int64_t* ld);
+
+/*
  * bse_block_star_columns - column ranges of the k stars in the block of an
  * irrep (partner = 0) or in its partner block (partner = 1): the basis
  * vectors of star a are columns [out[a], out[a+1]); out is a host array of
@@ -247,6 +263,35 @@ int bse_partner_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t
                          const double* omega_dev, int64_t n_omega, double eta,
                          double* omega_out, double* osc, double* im_eps);
 
+/*
+ * bse_set_solver - how bse_block_spectrum / bse_partner_spectrum obtain the
+ * levels Omega_l and the oscillator strengths of Eqs. oscillator and
+ * oscillatorA:
+ *   BSE_SOLVER_DENSE   cuSOLVER zheevd (all eigenvectors), then |a_l^T b|^2.
+ *   BSE_SOLVER_TRIDIAG a reflector maps c = conj(b) to a multiple of e_0,
+ *                      a Householder reduction that keeps e_0 fixed turns
+ *                      the block into a real tridiagonal T, and the strengths
+ *                      are ||c||^2 times the squared first components of T's
+ *                      eigenvectors (bisection for the levels, a twisted
+ *                      factorisation per level for the components); no
+ *                      eigenvector matrix is formed.  Needs the partners'
+ *                      projections b_i to be parallel (true for the partner
+ *                      blocks of bse_partner_spectrum) and n <= 8192; the
+ *                      sum of the weights must come out as 1 within 1e-8.
+ *                      Otherwise the spectrum call fails (EUNSUPPORTED or
+ *                      ESOLVER).  Exactly degenerate levels (the d_mu
+ *                      copies in a whole block of a d_mu-dimensional irrep)
+ *                      break the last condition.
+ *   BSE_SOLVER_AUTO    (default) TRIDIAG for partner blocks, for blocks
+ *                      of one-dimensional irreps and for blocks of irreps
+ *                      outside the polar-vector representation (B_mu = 0
+ *                      by symmetry: levels only, strengths 0), DENSE
+ *                      otherwise and whenever a TRIDIAG condition fails.
+ * bse_stats.solver reports the solver the last spectrum used.
+ */
+enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2 };
+int bse_set_solver(bse_ctx* ctx, int32_t solver);
+
 /* Wait for all work on the context's stream; returns ECUDA on a device error. */
 int bse_sync(bse_ctx* ctx);
 
@@ -271,6 +316,9 @@ typedef struct {
 } bse_work;
 
 int bse_build_work(bse_ctx* ctx, int32_t irrep, int32_t partner, bse_work* out);   /* partner: 0 block, 1 partner block */
+/* the same for one bse_build_blocks call (arguments as there); the direct
+ * term's pairs are counted once, the projections once per target */
+int bse_build_blocks_work(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_t* partner, bse_work* out);
 
 /*
  * bse_stats: kernel launches of this library in the process so far, and,
@@ -292,6 +340,8 @@ typedef struct {
     float ms_create_gamma;      /* ... band rotations (kernels, copy back, unitarity check) */
     float ms_create_wdiv;       /* ... head correction */
     float ms_basis;             /* wall time of the last basis construction (host, incl. upload) */
+    int32_t solver;             /* eigensolver of the last spectrum: BSE_SOLVER_DENSE or BSE_SOLVER_TRIDIAG */
+    int32_t reserved;
 } bse_stats;
 
 int bse_set_timing(bse_ctx* ctx, int32_t on);

@@ -24,6 +24,7 @@ BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ECUDA, BSE_ESYMM, BSE_ETIMEOUT, BSE_EUNSUPPO
 BSE_FP64, BSE_BF16_SPLIT, BSE_FP16_SPLIT, BSE_FP32 = 0, 1, 2, 3
 BSE_TERM_DIAG, BSE_TERM_EXCHANGE, BSE_TERM_DIRECT, BSE_TERM_ALL = 1, 2, 4, 7
 BSE_BANDS_CC, BSE_BANDS_VV, BSE_BANDS_CV = 0, 1, 2
+BSE_SOLVER_AUTO, BSE_SOLVER_DENSE, BSE_SOLVER_TRIDIAG = 0, 1, 2
 
 _P32 = C.POINTER(C.c_int32)
 _P64 = C.POINTER(C.c_int64)
@@ -61,7 +62,7 @@ class BseStats(C.Structure):
                 ("ms_project", C.c_float), ("ms_exchange", C.c_float), ("ms_eig", C.c_float),
                 ("ms_spectrum", C.c_float), ("ms_create", C.c_float), ("ms_create_tables", C.c_float),
                 ("ms_create_upload", C.c_float), ("ms_create_gamma", C.c_float), ("ms_create_wdiv", C.c_float),
-                ("ms_basis", C.c_float)]
+                ("ms_basis", C.c_float), ("solver", C.c_int32), ("reserved", C.c_int32)]
 
 
 EXPORTS = {
@@ -85,6 +86,10 @@ EXPORTS = {
     "bse_get_stats": (C.c_int, [C.c_void_p, C.POINTER(BseStats)]),
     "bse_head_correction_noalloc": (C.c_int, [_PD, _P32, _PD, C.c_void_p, C.c_void_p]),
     "bse_block_star_columns": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _P64]),
+    "bse_set_solver": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_build_blocks_work": (C.c_int, [C.c_void_p, C.c_int32, _P32, _P32, C.POINTER(BseWork)]),
+    "bse_build_blocks": (C.c_int, [C.c_void_p, C.c_int32, _P32, _P32, C.c_int32, C.c_uint32,
+                                   C.POINTER(C.c_void_p), _P64]),
 }
 
 _lib = None
@@ -247,6 +252,20 @@ def bse_build_partner_block(ctx: Context, irrep: int, prec: int, terms: int, out
     return out
 
 
+def bse_build_blocks(ctx: Context, irreps, partners, prec: int, terms: int, outs, lds):
+    """Several blocks in one build (one direct pass shared by all targets);
+    ``outs`` are device buffers (or None for an empty block)."""
+    n = len(irreps)
+    ir = np.ascontiguousarray(irreps, dtype=np.int32)
+    pa = None if partners is None else np.ascontiguousarray(partners, dtype=np.int32)
+    ptrs = (C.c_void_p * max(n, 1))(*[_ptr(o) if o is not None else None for o in outs])
+    ld = np.ascontiguousarray(lds, dtype=np.int64)
+    _check(lib().bse_build_blocks(ctx.handle, n, ir.ctypes.data_as(_P32),
+                                  None if pa is None else pa.ctypes.data_as(_P32), prec, terms, ptrs,
+                                  ld.ctypes.data_as(_P64)))
+    return outs
+
+
 def bse_partner_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float, omega_out, osc, im_eps):
     _check(lib().bse_partner_spectrum(ctx.handle, irrep, _ptr(h), ld, _ptr(omega), omega.numel(), eta,
                                       _ptr(omega_out), _ptr(osc), _ptr(im_eps)))
@@ -288,6 +307,19 @@ def bse_build_work(ctx: Context, irrep: int, partner: bool = False) -> dict:
     w = BseWork()
     _check(lib().bse_build_work(ctx.handle, irrep, 1 if partner else 0, C.byref(w)))
     return {f: getattr(w, f) for f, _ in BseWork._fields_}
+
+
+def bse_build_blocks_work(ctx: Context, irreps, partners=None) -> dict:
+    ir = np.ascontiguousarray(irreps, dtype=np.int32)
+    pa = None if partners is None else np.ascontiguousarray(partners, dtype=np.int32)
+    w = BseWork()
+    _check(lib().bse_build_blocks_work(ctx.handle, len(ir), ir.ctypes.data_as(_P32),
+                                       None if pa is None else pa.ctypes.data_as(_P32), C.byref(w)))
+    return {f: getattr(w, f) for f, _ in BseWork._fields_}
+
+
+def bse_set_solver(ctx: Context, solver: int):
+    _check(lib().bse_set_solver(ctx.handle, solver))
 
 
 def bse_set_timing(ctx: Context, on: bool):
@@ -337,6 +369,19 @@ def partner_block(ctx: Context, irrep: int, prec: int = BSE_FP64, terms: int = B
     buf = torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda")
     bse_build_partner_block(ctx, irrep, prec, terms, buf, max(n, 1))
     return colmajor(buf, n, n, max(n, 1))
+
+
+def blocks(ctx: Context, irreps=None, partner: bool = False, prec: int = BSE_FP64, terms: int = BSE_TERM_ALL):
+    """Build the blocks of several irreps (default: all) in one pass; returns
+    a list of [dim, dim] complex128 CUDA views in the order of ``irreps``."""
+    import torch
+    t = bse_tables(ctx)
+    if irreps is None:
+        irreps = list(range(int(t["n_irreps"])))
+    dims = [int(t["partner_dim" if partner else "block_dim"][mu]) for mu in irreps]
+    bufs = [torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda") for n in dims]
+    bse_build_blocks(ctx, irreps, [int(partner)] * len(irreps), prec, terms, bufs, [max(n, 1) for n in dims])
+    return [colmajor(b, n, n, max(n, 1)) for b, n in zip(bufs, dims)]
 
 
 def partner_spectrum(ctx: Context, irrep: int, h, omega, eta: float):

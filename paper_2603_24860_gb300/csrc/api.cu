@@ -94,6 +94,8 @@ struct bse_ctx {
     DevBuf wemb;         // split-precision W(q) embeddings for the tensor-core build
     int wemb_ngp = 0;
     DevBuf groups, status;
+    int32_t solver_mode = BSE_SOLVER_AUTO;
+    DevBuf triScratch, triSmall;   // tridiagonal path: scratch; gram [9], weight sum, error flag
     // scratch (library-owned, grow-only)
     DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum, counter;
     cusolverDnHandle_t solver = nullptr;
@@ -105,12 +107,17 @@ struct bse_ctx {
 
 namespace {
 
-// star-pair tiles of one irrep, grouped into batches whose X and Y arenas fit a budget
+// star-pair tiles shared by one or more target bases (irrep blocks or partner
+// blocks), grouped into batches whose X and Y arenas fit a budget.  X (the
+// direct term on the product basis of a star pair) does not depend on the
+// target, so every target of a batch projects the same X tiles.
 struct Batch {
-    std::vector<TileTask> tiles;
     std::vector<PairTask> tasks;
-    size_t xbytes = 0, ybytes = 0;
-    int64_t max_rows = 0, max_ca = 0, max_cb = 0;
+    std::vector<TileTask> tiles;          // all targets' tiles, concatenated
+    std::vector<int> tile_off;            // [targets + 1] range of each target in tiles
+    size_t xbytes = 0;
+    std::vector<size_t> ybytes;           // per target
+    std::vector<int64_t> max_rows, max_ca, max_cb;   // per target
 };
 
 size_t arena_budget() {
@@ -118,35 +125,73 @@ size_t arena_budget() {
     return (size_t)(env ? std::atoll(env) : 2048) << 20;
 }
 
-void plan_batches(const Tables& t, const Basis& bh, size_t budget, std::vector<Batch>& out) {
+void plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t budget, std::vector<Batch>& out) {
     out.clear();
+    const size_t nt = bases.size();
+    auto ncols = [&](size_t i, int a) { return bases[i]->star_col[a + 1] - bases[i]->star_col[a]; };
     std::vector<int> act;
     for (size_t a = 0; a < t.stars.size(); ++a)
-        if (bh.star_col[a + 1] > bh.star_col[a]) act.push_back((int)a);
+        for (size_t i = 0; i < nt; ++i)
+            if (ncols(i, (int)a) > 0) {
+                act.push_back((int)a);
+                break;
+            }
     const int B = t.B;
+    std::vector<std::vector<TileTask>> per(nt);
     Batch cur;
+    auto reset = [&]() {
+        cur = Batch();
+        cur.ybytes.assign(nt, 0);
+        cur.max_rows.assign(nt, 0);
+        cur.max_ca.assign(nt, 0);
+        cur.max_cb.assign(nt, 0);
+        for (auto& v : per) v.clear();
+    };
+    auto flush = [&]() {
+        cur.tile_off.assign(1, 0);
+        for (size_t i = 0; i < nt; ++i) {
+            cur.tiles.insert(cur.tiles.end(), per[i].begin(), per[i].end());
+            cur.tile_off.push_back((int)cur.tiles.size());
+        }
+        out.push_back(std::move(cur));
+    };
+    reset();
     for (size_t iA = 0; iA < act.size(); ++iA)
         for (size_t iB = iA; iB < act.size(); ++iB) {
-            int a = act[iA], b = act[iB];
-            int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
-            int64_t mb = bh.star_col[b + 1] - bh.star_col[b];
-            size_t xs = sizeof(double2) * rows * cols, ys = sizeof(double2) * rows * mb;
-            if (!cur.tiles.empty() && (cur.xbytes + xs > budget || cur.ybytes + ys > budget)) {
-                out.push_back(std::move(cur));
-                cur = Batch();
+            const int a = act[iA], b = act[iB];
+            bool used = false;
+            for (size_t i = 0; i < nt; ++i) used = used || (ncols(i, a) > 0 && ncols(i, b) > 0);
+            if (!used) continue;
+            const int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
+            const size_t xs = sizeof(double2) * rows * cols;
+            bool full = !cur.tasks.empty() && cur.xbytes + xs > budget;
+            for (size_t i = 0; i < nt && !full; ++i)
+                full = !cur.tasks.empty() && ncols(i, a) > 0 && cur.ybytes[i] + sizeof(double2) * rows * ncols(i, b) > budget;
+            if (full) {
+                flush();
+                reset();
             }
-            TileTask tt;
-            tt.xoff = (int64_t)(cur.xbytes / sizeof(double2));
-            tt.yoff = (int64_t)(cur.ybytes / sizeof(double2));
-            tt.rows = (int32_t)rows;
-            tt.cols = (int32_t)cols;
-            tt.star_a = a;
-            tt.star_b = b;
-            tt.ca0 = bh.star_col[a];
-            tt.ca1 = bh.star_col[a + 1];
-            tt.cb0 = bh.star_col[b];
-            tt.cb1 = bh.star_col[b + 1];
-            cur.tiles.push_back(tt);
+            const int64_t xoff = (int64_t)(cur.xbytes / sizeof(double2));
+            for (size_t i = 0; i < nt; ++i) {
+                const int64_t ma = ncols(i, a), mb = ncols(i, b);
+                if (ma == 0 || mb == 0) continue;
+                TileTask tt;
+                tt.xoff = xoff;
+                tt.yoff = (int64_t)(cur.ybytes[i] / sizeof(double2));
+                tt.rows = (int32_t)rows;
+                tt.cols = (int32_t)cols;
+                tt.star_a = a;
+                tt.star_b = b;
+                tt.ca0 = bases[i]->star_col[a];
+                tt.ca1 = bases[i]->star_col[a + 1];
+                tt.cb0 = bases[i]->star_col[b];
+                tt.cb1 = bases[i]->star_col[b + 1];
+                per[i].push_back(tt);
+                cur.ybytes[i] += sizeof(double2) * rows * mb;
+                cur.max_rows[i] = std::max(cur.max_rows[i], rows);
+                cur.max_ca[i] = std::max(cur.max_ca[i], ma);
+                cur.max_cb[i] = std::max(cur.max_cb[i], mb);
+            }
             const auto& sa = t.stars[a];
             const auto& sb = t.stars[b];
             for (size_t i = 0; i < sa.size(); ++i)
@@ -156,18 +201,14 @@ void plan_batches(const Tables& t, const Basis& bh, size_t budget, std::vector<B
                     p.kp = sb[j];
                     p.row0 = (int32_t)(i * B);
                     p.col0 = (int32_t)(j * B);
-                    p.xoff = tt.xoff;
+                    p.xoff = xoff;
                     p.ld = (int32_t)rows;
                     p.flags = (a == b && j > i) ? 1 : 0;
                     cur.tasks.push_back(p);
                 }
             cur.xbytes += xs;
-            cur.ybytes += ys;
-            cur.max_rows = std::max(cur.max_rows, rows);
-            cur.max_ca = std::max(cur.max_ca, tt.ca1 - tt.ca0);
-            cur.max_cb = std::max(cur.max_cb, mb);
         }
-    if (!cur.tiles.empty()) out.push_back(std::move(cur));
+    if (!cur.tasks.empty()) flush();
 }
 
 }  // namespace
@@ -714,7 +755,11 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
 }
 
 // U^dagger H U for an orbit-sparse basis U (an irrep block or a partner block)
-static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms, void* h, int64_t ld) {
+// One build of several blocks (whole irrep blocks or partner blocks): the
+// direct term of every star pair runs once per batch and each target projects
+// the same X tiles with its own basis (Eqs. transformationU, Hblock).
+static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t prec, uint32_t terms,
+                       void* const* h, const int64_t* ld) {
     const int tcp = prec == BSE_BF16_SPLIT;
     const int p32 = prec == BSE_FP32 || tcp;   // the tile arena is FP32 for both
     int ngp = 0;
@@ -723,24 +768,34 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
         BSE_TRY(tc_supported(c->S, ngp, sm));
     }
     const Tables& t = c->t;
-    const Basis& bh = bd.host;
-    const int64_t dim = bh.dim;
-    if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
-    if (dim == 0) return BSE_OK;
-    DevBasis db = dev_basis_of(c, bd);
-    const double2* Pmu = nullptr;
+    const size_t nt = tg.size();
+    std::vector<const Basis*> bases;
+    std::vector<DevBasis> db;
+    std::vector<int64_t> pmu_off(nt + 1, 0);
+    int64_t total = 0;
+    for (size_t i = 0; i < nt; ++i) {
+        if (ld[i] < tg[i]->host.dim) return fail(BSE_EINVAL, "target %zu: ld < block dimension", i);
+        if (tg[i]->host.dim > 0 && !h[i]) return fail(BSE_EINVAL, "target %zu: null output", i);
+        bases.push_back(&tg[i]->host);
+        db.push_back(dev_basis_of(c, *tg[i]));
+        pmu_off[i + 1] = pmu_off[i] + tg[i]->host.dim * c->ng0;
+        total += tg[i]->host.dim;
+    }
+    if (total == 0) return BSE_OK;
     if (c->timing) c->stats.ms_exchange = 0.f;
     if (terms & BSE_TERM_EXCHANGE) {
         BSE_TRY(ensure_exchange_vectors(c));
-        BSE_TRY(ensure(c->Pmu, sizeof(double2) * (size_t)dim * c->ng0));
+        BSE_TRY(ensure(c->Pmu, sizeof(double2) * (size_t)pmu_off[nt]));
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
-        BSE_TRY(launch_exchange_project(db, (const double2*)c->P.p, c->ng0, (double2*)c->Pmu.p, c->stream));
+        for (size_t i = 0; i < nt; ++i)
+            if (db[i].dim > 0)
+                BSE_TRY(launch_exchange_project(db[i], (const double2*)c->P.p, c->ng0,
+                                                (double2*)c->Pmu.p + pmu_off[i], c->stream));
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
             BSE_CUDA(cudaEventSynchronize(c->ev[4]));
             BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_exchange, c->ev[3], c->ev[4]));
         }
-        Pmu = (const double2*)c->Pmu.p;
     }
     if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
     if (tcp && (terms & BSE_TERM_DIRECT)) {
@@ -750,14 +805,16 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
     }
     const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
     std::vector<Batch> batches;
-    plan_batches(t, bh, arena_budget(), batches);
+    plan_batches(t, bases, arena_budget(), batches);
     if (c->timing) {
         c->stats.ms_direct = c->stats.ms_project = 0.f;
         c->stats.direct_launches = 0;
     }
     for (const Batch& bt : batches) {
+        size_t ymax = 0;
+        for (size_t y : bt.ybytes) ymax = std::max(ymax, y);
         BSE_TRY(ensure(c->arenaX, bt.xbytes / sizeof(double2) * xel));
-        BSE_TRY(ensure(c->arenaY, bt.ybytes));
+        BSE_TRY(ensure(c->arenaY, ymax));
         std::vector<TcGroup> groups;
         if (tcp && (terms & BSE_TERM_DIRECT)) {
             // the tensor-core kernel takes groups of pairs with the same q
@@ -803,12 +860,18 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
             BSE_CUDA(cudaMemsetAsync(c->arenaX.p, 0, bt.xbytes / sizeof(double2) * xel, c->stream));
         }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[1], c->stream));
-        BSE_TRY(launch_project_right(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), p32, c->arenaX.p,
-                                     (double2*)c->arenaY.p, bt.max_rows, bt.max_cb, c->stream));
-        BSE_TRY(launch_project_left(db, (const TileTask*)c->tiles.p, (int)bt.tiles.size(), (const double2*)c->arenaY.p,
-                                    Pmu, (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
-                                    (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
-                                    (double2*)h, ld, bt.max_ca, bt.max_cb, c->stream));
+        for (size_t i = 0; i < nt; ++i) {
+            const int n = bt.tile_off[i + 1] - bt.tile_off[i];
+            if (n == 0) continue;
+            const TileTask* tl = (const TileTask*)c->tiles.p + bt.tile_off[i];
+            BSE_TRY(launch_project_right(db[i], tl, n, p32, c->arenaX.p, (double2*)c->arenaY.p, bt.max_rows[i],
+                                         bt.max_cb[i], c->stream));
+            BSE_TRY(launch_project_left(db[i], tl, n, (const double2*)c->arenaY.p,
+                                        (terms & BSE_TERM_EXCHANGE) ? (const double2*)c->Pmu.p + pmu_off[i] : nullptr,
+                                        (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
+                                        (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
+                                        (double2*)h[i], ld[i], bt.max_ca[i], bt.max_cb[i], c->stream));
+        }
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[2], c->stream));
             BSE_CUDA(cudaEventSynchronize(c->ev[2]));
@@ -829,6 +892,11 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
     return BSE_OK;
 }
 
+static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms, void* h, int64_t ld) {
+    std::vector<IrrepDev*> tg{&bd};
+    return build_multi(c, tg, prec, terms, &h, &ld);
+}
+
 int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
@@ -845,6 +913,26 @@ int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     BSE_TRY(ensure_partner(c, mu));
     return build_generic(c, c->partner[mu].part[0], prec, terms, h, ld);
+}
+
+int bse_build_blocks(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
+                     uint32_t terms, void* const* h, const int64_t* ld) {
+    clear_error();
+    if (!c || n < 0 || (n > 0 && (!irrep || !h || !ld))) return fail(BSE_EINVAL, "null argument");
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+        return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    std::vector<IrrepDev*> tg;
+    for (int32_t i = 0; i < n; ++i) {
+        if (partner && partner[i]) {
+            BSE_TRY(ensure_partner(c, irrep[i]));
+            tg.push_back(&c->partner[irrep[i]].part[0]);
+        } else {
+            BSE_TRY(ensure_basis(c, irrep[i]));
+            tg.push_back(&c->irr[irrep[i]]);
+        }
+    }
+    if (n == 0) return BSE_OK;
+    return build_multi(c, tg, prec, terms, h, ld);
 }
 
 int bse_block_star_columns(bse_ctx* c, int32_t mu, int32_t partner, int64_t* out) {
@@ -877,8 +965,61 @@ int bse_dipoles(bse_ctx* c, void* b) {
 // eigensolution of U^dagger H U and the spectrum; the oscillator strength of
 // each level sums |a^T (U_p^T B)|^2 over the given bases U_p (one for an
 // irrep block, the d transfers for a partner block)
-static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, const void* h, int64_t ld, const double* omega,
-                            int64_t n_omega, double eta, double* omega_out, double* osc, double* im_eps) {
+// Levels and strengths without eigenvectors (see bse_set_solver).  Returns
+// BSE_OK when done; EUNSUPPORTED / ESOLVER when a condition of the path fails
+// (the caller may fall back to the dense solver).
+static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, const void* h, int64_t ld,
+                            double* omega_out, double* osc) {
+    if (dim > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: block dimension %lld > %d",
+                                             (long long)dim, tridiag_max_dim());
+    BSE_TRY(ensure(c->triSmall, 256));
+    double2* gram = (double2*)c->triSmall.p;
+    double* wsum = (double*)((char*)c->triSmall.p + 160);
+    int* err = (int*)((char*)c->triSmall.p + 176);
+    BSE_TRY(launch_gram((const double2*)c->Bmu.p, dim, nparts, gram, c->stream));
+    double2 g[9];
+    BSE_CUDA(cudaMemcpyAsync(g, gram, sizeof(g), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    // the projections must be parallel: |G_pj|^2 = G_pp G_jj for the largest G_pp
+    int pmax = 0;
+    double scale = 0.0;
+    for (int i = 0; i < nparts; ++i) {
+        scale += g[i * 3 + i].x;
+        if (g[i * 3 + i].x > g[pmax * 3 + pmax].x) pmax = i;
+    }
+    const double gpp = g[pmax * 3 + pmax].x;
+    // an irrep outside the polar-vector representation has B_mu = 0 by symmetry: levels only
+    if (dark) scale = 0.0;
+    for (int j = 0; j < nparts && !dark; ++j) {
+        const double gjj = g[j * 3 + j].x, a2 = g[pmax * 3 + j].x * g[pmax * 3 + j].x + g[pmax * 3 + j].y * g[pmax * 3 + j].y;
+        if (gjj > 1e-20 * gpp && a2 < (1.0 - 1e-10) * gpp * gjj)
+            return fail(BSE_EUNSUPPORTED, "tridiagonal path: the partners' dipole projections are not parallel");
+    }
+    BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
+    BSE_CUDA(cudaMemcpy2DAsync(c->eigA.p, sizeof(double2) * dim, h, sizeof(double2) * ld, sizeof(double2) * dim, dim,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    BSE_TRY(ensure(c->triScratch, tridiag_scratch_bytes(dim)));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
+    BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
+                                    c->triScratch.p, omega_out, osc, wsum, err, c->stream));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
+    struct {
+        double s;
+        int e;
+    } chk{0.0, 0};
+    BSE_CUDA(cudaMemcpyAsync(&chk.s, wsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaMemcpyAsync(&chk.e, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    if (chk.e) return fail(BSE_ETIMEOUT, "a grid barrier of the tridiagonal reduction gave up");
+    if (scale > 0.0 && !(std::fabs(chk.s - 1.0) <= 1e-8))
+        return fail(BSE_ESOLVER, "tridiagonal path: weights sum to %.17g instead of 1", chk.s);
+    return BSE_OK;
+}
+
+static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_dim, bool dark, const void* h,
+                            int64_t ld,
+                            const double* omega, int64_t n_omega, double eta, double* omega_out, double* osc,
+                            double* im_eps) {
     const int64_t dim = parts[0].host.dim;
     if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
     if (dim == 0) {
@@ -891,6 +1032,27 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, const void*
     for (int p = 0; p < nparts; ++p)
         BSE_TRY(launch_bmu(dev_basis_of(c, parts[p]), (const double2*)c->B.p, (double2*)c->Bmu.p + (size_t)p * dim,
                            c->stream));
+    const double pref = 4.0 * M_PI * c->spin / c->t.nk;
+    const bool try_tri = c->solver_mode == BSE_SOLVER_TRIDIAG ||
+                         (c->solver_mode == BSE_SOLVER_AUTO && (nparts > 1 || irrep_dim == 1 || dark) &&
+                          dim <= tridiag_max_dim());
+    if (try_tri) {
+        const int rc = spectrum_tridiag(c, nparts, dark, dim, h, ld, omega_out, osc);
+        if (rc == BSE_OK) {
+            if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
+            BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, pref, im_eps, c->stream));
+            if (c->timing) {
+                BSE_CUDA(cudaEventRecord(c->ev[5], c->stream));
+                BSE_CUDA(cudaEventSynchronize(c->ev[5]));
+                BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
+                BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
+            }
+            c->stats.solver = BSE_SOLVER_TRIDIAG;
+            return BSE_OK;
+        }
+        if (c->solver_mode == BSE_SOLVER_TRIDIAG || rc == BSE_ETIMEOUT || rc == BSE_ECUDA) return rc;
+        clear_error();
+    }
     BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
     BSE_CUDA(cudaMemcpy2DAsync(c->eigA.p, sizeof(double2) * dim, h, sizeof(double2) * ld, sizeof(double2) * dim, dim,
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -914,8 +1076,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, const void*
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     BSE_TRY(launch_oscillators((const double2*)c->eigA.p, dim, dim, (const double2*)c->Bmu.p, nparts, osc,
                                c->stream));
-    BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, 4.0 * M_PI * c->spin / c->t.nk, im_eps,
-                            c->stream));
+    BSE_TRY(launch_spectrum(omega_out, osc, dim, omega, n_omega, eta, pref, im_eps, c->stream));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[5], c->stream));
     int info = 0;
     BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -925,6 +1086,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, const void*
         BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
         BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
     }
+    c->stats.solver = BSE_SOLVER_DENSE;
     return BSE_OK;
 }
 
@@ -934,7 +1096,8 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
     if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     BSE_TRY(ensure_basis(c, mu));
-    return spectrum_generic(c, &c->irr[mu], 1, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+    return spectrum_generic(c, &c->irr[mu], 1, c->t.irrep_dim[mu], !c->t.bright[mu], h, ld, omega, n_omega, eta,
+                            omega_out, osc, im_eps);
 }
 
 int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
@@ -944,7 +1107,16 @@ int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, cons
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     BSE_TRY(ensure_partner(c, mu));
     auto& pd = c->partner[mu];
-    return spectrum_generic(c, pd.part, pd.d, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+    return spectrum_generic(c, pd.part, pd.d, pd.d, false, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+}
+
+int bse_set_solver(bse_ctx* c, int32_t solver) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null argument");
+    if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG)
+        return fail(BSE_EINVAL, "unknown solver %d", solver);
+    c->solver_mode = solver;
+    return BSE_OK;
 }
 
 int bse_set_timing(bse_ctx* c, int32_t on) {
@@ -965,18 +1137,27 @@ int bse_get_stats(bse_ctx* c, bse_stats* out) {
     return BSE_OK;
 }
 
-int bse_build_work(bse_ctx* c, int32_t mu, int32_t partner, bse_work* out) {
+int bse_build_blocks_work(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t* partner, bse_work* out) {
     clear_error();
-    if (!c || !out) return fail(BSE_EINVAL, "null argument");
-    if (partner) BSE_TRY(ensure_partner(c, mu));
-    else BSE_TRY(ensure_basis(c, mu));
+    if (!c || !out || n < 0 || (n > 0 && !irrep)) return fail(BSE_EINVAL, "null argument");
+    std::vector<const Basis*> bases;
+    for (int32_t i = 0; i < n; ++i) {
+        if (partner && partner[i]) {
+            BSE_TRY(ensure_partner(c, irrep[i]));
+            bases.push_back(&c->partner[irrep[i]].part[0].host);
+        } else {
+            BSE_TRY(ensure_basis(c, irrep[i]));
+            bases.push_back(&c->irr[irrep[i]].host);
+        }
+    }
     const Tables& t = c->t;
-    const Basis& bh = partner ? c->partner[mu].part[0].host : c->irr[mu].host;
     *out = bse_work{};
-    if (bh.dim == 0) return BSE_OK;
+    int64_t total = 0;
+    for (const Basis* bh : bases) total += bh->dim;
+    if (total == 0) return BSE_OK;
     std::vector<Batch> batches;
-    plan_batches(t, bh, arena_budget(), batches);
-    auto n_o = [&](int64_t j) -> double {
+    plan_batches(t, bases, arena_budget(), batches);
+    auto n_o = [&](const Basis& bh, int64_t j) -> double {
         int o = bh.col_orbit[j];
         return (double)(t.orbit_off[o + 1] - t.orbit_off[o]);
     };
@@ -993,14 +1174,16 @@ int bse_build_work(bse_ctx* c, int32_t mu, int32_t partner, bse_work* out) {
             sum_ng += ng;
             sum_ng2 += ng * ng;
         }
-        for (const TileTask& tt : bt.tiles) {
-            double sb = 0, sa = 0;
-            for (int64_t j = tt.cb0; j < tt.cb1; ++j) sb += n_o(j);
-            for (int64_t i = tt.ca0; i < tt.ca1; ++i) sa += n_o(i);
-            double mb = (double)(tt.cb1 - tt.cb0), ma = (double)(tt.ca1 - tt.ca0);
-            proj += tt.rows * sb + sa * mb;
-            exch_tiles += ma * mb;
-        }
+        for (size_t i = 0; i < bases.size(); ++i)
+            for (int j = bt.tile_off[i]; j < bt.tile_off[i + 1]; ++j) {
+                const TileTask& tt = bt.tiles[j];
+                double sb = 0, sa = 0;
+                for (int64_t x = tt.cb0; x < tt.cb1; ++x) sb += n_o(*bases[i], x);
+                for (int64_t x = tt.ca0; x < tt.ca1; ++x) sa += n_o(*bases[i], x);
+                double mb = (double)(tt.cb1 - tt.cb0), ma = (double)(tt.ca1 - tt.ca0);
+                proj += tt.rows * sb + sa * mb;
+                exch_tiles += ma * mb;
+            }
         out->k_pairs += (int64_t)bt.tasks.size();
         out->tiles += (int64_t)bt.tiles.size();
         BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
@@ -1011,13 +1194,18 @@ int bse_build_work(bse_ctx* c, int32_t mu, int32_t partner, bse_work* out) {
     unsigned long long ov = 0;
     BSE_CUDA(cudaMemcpy(&ov, c->counter.p, sizeof(ov), cudaMemcpyDeviceToHost));
     double pmu = 0;
-    for (int64_t i = 0; i < bh.dim; ++i) pmu += n_o(i);
+    for (const Basis* bh : bases)
+        for (int64_t i = 0; i < bh->dim; ++i) pmu += n_o(*bh, i);
     out->overlap = (int64_t)ov;
     out->rho = 8.0 * (nc * nc + nv * nv) * (double)ov;
     out->contract = 8.0 * (nv * nv * sum_ng2 + nc * nc * nv * nv * sum_ng);
     out->project = 8.0 * proj;
     out->exchange = 8.0 * (pmu + exch_tiles) * c->ng0;
     return BSE_OK;
+}
+
+int bse_build_work(bse_ctx* c, int32_t mu, int32_t partner, bse_work* out) {
+    return bse_build_blocks_work(c, 1, &mu, &partner, out);
 }
 
 int bse_sync(bse_ctx* c) {

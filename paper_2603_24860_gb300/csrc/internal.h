@@ -181,6 +181,12 @@ int launch_dipoles(const DevSys& s, double2* B, cudaStream_t st);
 int launch_bmu(const DevBasis& b, const double2* B, double2* Bmu, cudaStream_t st);
 int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2* Bmu, int nparts, double* osc,
                        cudaStream_t st);
+// tridiag.cu: levels and strengths through a tridiagonal reduction from the dipole direction
+size_t tridiag_scratch_bytes(int64_t n);
+int tridiag_max_dim();
+int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st);
+int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
+                            double* osc, double* wsum, int* err, cudaStream_t st);
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega,
                     int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);
 // recip_and_lattice: reciprocal basis then lattice, both row-major 3x3

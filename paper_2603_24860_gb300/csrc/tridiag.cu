@@ -1,0 +1,619 @@
+// Levels and oscillator strengths of a Hermitian block without eigenvectors
+// (sm_103a).
+//
+// Eqs. oscillator and oscillatorA need, for every eigenpair (Omega_l, a_l) of
+// a block H, the weight |a_l^T b|^2 with b = U^T B.  With c = conj(b) this is
+// |<c, a_l>|^2: the weights of the spectral measure of H seen from c.  A
+// reflector H0 maps c to a multiple of e_0; the Householder reduction
+// Q^H (H0 H H0) Q = T, whose reflectors act on rows 1..n-1 only, keeps e_0
+// fixed, so the weights are ||c||^2 z_0(l)^2 with z(l) the eigenvectors of the
+// real symmetric tridiagonal T (the Gauss quadrature of that measure).  The
+// levels come from Sturm-count bisection of T, the first components from a
+// twisted factorisation of T - Omega_l, O(n) per level; no eigenvector matrix
+// is formed or back-transformed.
+//
+// GB300 layout: the reduction is one persistent cooperative kernel with one
+// CTA per SM.  Column j of the block belongs to CTA j mod G; for n up to
+// about 1400 every CTA keeps its columns in shared memory for the whole
+// reduction (152 x 227 KB hold a 1400 x 1400 complex matrix), otherwise they
+// stay in global memory.  Because the block is Hermitian, (A v)_j is a dot
+// product with column j, so each step needs no cross-CTA reduction except one
+// scalar, and two grid barriers per step order the reflector and x = tau A v.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+
+#include "internal.h"
+
+namespace bse {
+
+namespace {
+
+constexpr int kTriThreads = 256;
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr int kChunk = 8;                 // columns reduced together
+constexpr long kSpinLimit = 1l << 22;     // x >= 64 ns per poll: a few seconds
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of a cooperative launch (all CTAs co-resident).  Bounded: on
+// timeout, or when another CTA has raised the error flag, returns false.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        bool ok = false;
+        for (long it = 0; it < kSpinLimit; ++it) {
+            if (ld_acquire(bar) >= target) {
+                ok = true;
+                break;
+            }
+            if (*(volatile int*)err) break;
+            __nanosleep(64);
+        }
+        if (!ok) atomicExch(err, 1);
+        __threadfence();
+        *s_flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+struct TriArgs {
+    double2* A;           // n x n column-major, leading dimension n (updated in place in the global variant)
+    int64_t n;
+    const double2* v0;    // initial reflector
+    const double* beta0;  // its (real) scalar
+    double2* vbuf;        // [2][n] reflectors, by step parity
+    double2* xbuf;        // [n] x = tau A v
+    double2* spart;       // [G] per-CTA parts of x^H v
+    double* d;            // [n] diagonal of T
+    double* e;            // [n] off-diagonal of T (e[n-1] unused)
+    unsigned* bar;        // barrier counter, zero on entry
+    int* err;             // error flag, zero on entry
+};
+
+template <bool kSmem>
+__global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
+    extern __shared__ __align__(16) double2 s_cols[];
+    __shared__ double2 s_red[kTriWarps][kChunk];
+    __shared__ double2 s_s[kChunk];
+    __shared__ double2 s_scal[2];
+    __shared__ double s_sig[kTriWarps];
+    __shared__ int s_flag;
+
+    const int n = (int)a.n;
+    const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;
+    auto col = [&](int l) -> double2* {
+        return kSmem ? s_cols + (size_t)l * n : a.A + (size_t)(blk + l * G) * n;
+    };
+    if (kSmem) {
+        for (int l = 0; l < ncl; ++l) {
+            const double2* src = a.A + (size_t)(blk + l * G) * n;
+            for (int r = tid; r < n; r += kTriThreads) s_cols[(size_t)l * n + r] = src[r];
+        }
+        __syncthreads();
+    }
+    unsigned nbar = 0;
+
+    // reflector of column k (owner CTA): rows k+1..n-1, v_{k+1} = 1 (LAPACK zlarfg convention)
+    auto make_reflector = [&](int k) {
+        double2* ck = col(k / G);
+        double sg = 0.0;
+        for (int r = k + 2 + tid; r < n; r += kTriThreads) sg += ck[r].x * ck[r].x + ck[r].y * ck[r].y;
+        sg = warp_sum(sg);
+        if (lane == 0) s_sig[wid] = sg;
+        __syncthreads();
+        if (tid == 0) {
+            double sigma = 0.0;
+            for (int w = 0; w < kTriWarps; ++w) sigma += s_sig[w];
+            const double2 al = ck[k + 1];
+            double2 tau, inv;
+            double beta;
+            if (sigma == 0.0 && al.y == 0.0) {
+                tau = make_double2(0.0, 0.0);
+                beta = al.x;
+                inv = make_double2(0.0, 0.0);
+            } else {
+                beta = -copysign(sqrt(al.x * al.x + al.y * al.y + sigma), al.x);
+                tau = make_double2((beta - al.x) / beta, -al.y / beta);
+                const double2 den = make_double2(al.x - beta, al.y);
+                const double m2 = den.x * den.x + den.y * den.y;
+                inv = make_double2(den.x / m2, -den.y / m2);
+            }
+            s_scal[0] = inv;
+            a.d[k] = ck[k].x;
+            a.e[k] = beta;
+            a.vbuf[(size_t)(k & 1) * n + k + 1] = make_double2(1.0, 0.0);
+            // tau rides in the slot below the reflector's first row (row k is outside its support)
+            a.vbuf[(size_t)(k & 1) * n + k] = tau;
+        }
+        __syncthreads();
+        const double2 inv = s_scal[0];
+        double2* vb = a.vbuf + (size_t)(k & 1) * n;
+        for (int r = k + 2 + tid; r < n; r += kTriThreads) vb[r] = cmul(ck[r], inv);
+    };
+
+    for (int i = -1; i <= n - 2; ++i) {
+        const int r0 = i + 1;
+        const double2* vb = i < 0 ? a.v0 : a.vbuf + (size_t)(i & 1) * n;
+        if (i >= 0 && !grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+        const double2 tau = i < 0 ? make_double2(__ldcg(a.beta0), 0.0) : __ldcg(vb + i);
+        // (b) x_j = tau sum_r conj(A_rj) v_r for own columns j >= r0, and this CTA's part of x^H v
+        const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;   // first own slot with j >= r0
+        double2 spart = make_double2(0.0, 0.0);
+        for (int c0 = l0; c0 < ncl; c0 += kChunk) {
+            const int nc = min(kChunk, ncl - c0);
+            double2 acc[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) acc[c] = make_double2(0.0, 0.0);
+            for (int r = r0 + tid; r < n; r += kTriThreads) {
+                const double2 v = __ldcg(vb + r);
+#pragma unroll
+                for (int c = 0; c < kChunk; ++c)
+                    if (c < nc) {
+                        const double2 x = cmulc(col(c0 + c)[r], v);
+                        acc[c].x += x.x;
+                        acc[c].y += x.y;
+                    }
+            }
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                const double sx = warp_sum(acc[c].x), sy = warp_sum(acc[c].y);
+                if (lane == 0) s_red[wid][c] = make_double2(sx, sy);
+            }
+            __syncthreads();
+            if (tid < nc) {
+                double2 s = make_double2(0.0, 0.0);
+                for (int w = 0; w < kTriWarps; ++w) {
+                    s.x += s_red[w][tid].x;
+                    s.y += s_red[w][tid].y;
+                }
+                const int j = blk + (c0 + tid) * G;
+                const double2 x = cmul(tau, s);
+                a.xbuf[j] = x;
+                const double2 sv = cmulc(x, __ldcg(vb + j));
+                s_s[tid] = sv;
+            }
+            __syncthreads();
+            if (tid == 0)
+                for (int c = 0; c < nc; ++c) {
+                    spart.x += s_s[c].x;
+                    spart.y += s_s[c].y;
+                }
+            __syncthreads();
+        }
+        if (tid == 0) a.spart[blk] = spart;
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+        // (c) alpha = -tau (x^H v) / 2, w = x + alpha v, A -= v w^H + w v^H on own columns j >= r0
+        if (wid == 0) {
+            double sx = 0.0, sy = 0.0;
+            for (int b = lane; b < G; b += 32) {
+                const double2 p = __ldcg(a.spart + b);
+                sx += p.x;
+                sy += p.y;
+            }
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) {
+                const double2 al = cmul(tau, make_double2(sx, sy));
+                s_scal[1] = make_double2(-0.5 * al.x, -0.5 * al.y);
+            }
+        }
+        __syncthreads();
+        const double2 alpha = s_scal[1];
+        const int next = i + 1;
+        const bool lookahead = next <= n - 2 && next % G == blk;
+        auto update = [&](int c0, int nc, int skip) {
+            double2 vj[kChunk], wj[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c)
+                if (c < nc) {
+                    const int j = blk + (c0 + c) * G;
+                    vj[c] = __ldcg(vb + j);
+                    const double2 xj = __ldcg(a.xbuf + j);
+                    const double2 av = cmul(alpha, vj[c]);
+                    wj[c] = make_double2(xj.x + av.x, xj.y + av.y);
+                }
+            for (int r = r0 + tid; r < n; r += kTriThreads) {
+                const double2 v = __ldcg(vb + r), x = __ldcg(a.xbuf + r);
+                const double2 av = cmul(alpha, v);
+                const double2 w = make_double2(x.x + av.x, x.y + av.y);
+#pragma unroll
+                for (int c = 0; c < kChunk; ++c)
+                    if (c < nc && c0 + c != skip) {
+                        double2* p = col(c0 + c) + r;
+                        const double2 t1 = cmulc(wj[c], v), t2 = cmulc(vj[c], w);
+                        // v_r conj(w_j) + w_r conj(v_j)
+                        double2 q = *p;
+                        q.x -= t1.x + t2.x;
+                        q.y -= t1.y + t2.y;
+                        *p = q;
+                    }
+            }
+        };
+        int skip = -1;
+        if (lookahead) {
+            skip = next / G;
+            update(skip, 1, -1);
+            __syncthreads();
+            make_reflector(next);
+        }
+        for (int c0 = l0; c0 < ncl; c0 += kChunk) update(c0, min(kChunk, ncl - c0), skip);
+    }
+    __syncthreads();
+    if ((n - 1) % G == blk && tid == 0) a.d[n - 1] = col((n - 1) / G)[n - 1].x;
+}
+
+// Gram matrix of the conjugated projections: G_ij = sum_r b_i[r] conj(b_j[r]) (one block)
+__global__ void gram_kernel(const double2* __restrict__ b, int64_t n, int np, double2* G) {
+    __shared__ double s[kTriWarps][18];
+    double acc[18];
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x)
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                const double2 bi = b[(size_t)i * n + r], bj = b[(size_t)j * n + r];
+                acc[2 * (i * 3 + j)] += bi.x * bj.x + bi.y * bj.y;
+                acc[2 * (i * 3 + j) + 1] += bi.y * bj.x - bi.x * bj.y;
+            }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 18; ++q) {
+        const double v = warp_sum(acc[q]);
+        if (lane == 0) s[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            x += s[w][2 * threadIdx.x];
+            y += s[w][2 * threadIdx.x + 1];
+        }
+        G[threadIdx.x] = make_double2(x, y);
+    }
+}
+
+// H0 = I - beta v v^H with H0 conj(b) = -phase ||b|| e_0 (one block)
+__global__ void reflect0_kernel(const double2* __restrict__ b, int64_t n, double2* v, double* beta) {
+    __shared__ double s[kTriWarps];
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) acc += b[r].x * b[r].x + b[r].y * b[r].y;
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double nrm2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) nrm2 += s[w];
+    const double nrm = sqrt(nrm2);
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const double2 c = make_double2(b[r].x, -b[r].y);
+        if (nrm2 == 0.0) {
+            v[r] = make_double2(0.0, 0.0);
+        } else if (r == 0) {
+            const double ac = sqrt(c.x * c.x + c.y * c.y);
+            const double2 ph = ac > 0.0 ? make_double2(c.x / ac, c.y / ac) : make_double2(1.0, 0.0);
+            v[0] = make_double2(c.x + ph.x * nrm, c.y + ph.y * nrm);
+        } else {
+            v[r] = c;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const double2 c0 = make_double2(b[0].x, -b[0].y);
+        const double ac = sqrt(c0.x * c0.x + c0.y * c0.y);
+        *beta = nrm2 == 0.0 ? 0.0 : 2.0 / (2.0 * nrm2 + 2.0 * nrm * ac);
+    }
+}
+
+struct TriBounds {
+    double gl, gu, tnorm, pivmin, tol;
+    int m;   // T splits after row m-1 (first |e| <= tol), m = n when it does not
+};
+
+// Gershgorin interval, deflation of negligible off-diagonals, e^2 (one block)
+__global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __restrict__ e, int64_t n, double* e2,
+                                  TriBounds* out) {
+    __shared__ double s_lo[kTriWarps], s_hi[kTriWarps], s_nm[kTriWarps], s_e[kTriWarps];
+    __shared__ int s_m[kTriWarps];
+    double lo = DBL_MAX, hi = -DBL_MAX, nm = 0.0, emax = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+        nm = fmax(nm, fabs(d[i]) + r);
+        if (i + 1 < n) emax = fmax(emax, e[i] * e[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        nm = fmax(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+        emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        s_lo[wid] = lo;
+        s_hi[wid] = hi;
+        s_nm[wid] = nm;
+        s_e[wid] = emax;
+    }
+    __syncthreads();
+    lo = DBL_MAX;
+    hi = -DBL_MAX;
+    nm = 0.0;
+    emax = 0.0;
+    for (int w = 0; w < nw; ++w) {
+        lo = fmin(lo, s_lo[w]);
+        hi = fmax(hi, s_hi[w]);
+        nm = fmax(nm, s_nm[w]);
+        emax = fmax(emax, s_e[w]);
+    }
+    const double tol = 64.0 * DBL_EPSILON * nm;
+    int m = (int)n;
+    for (int64_t i = threadIdx.x; i + 1 < n; i += blockDim.x) {
+        const bool small = fabs(e[i]) <= tol;
+        e2[i] = small ? 0.0 : e[i] * e[i];
+        if (small && (int)i + 1 < m) m = (int)i + 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_m[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < nw; ++w) m = min(m, s_m[w]);
+        TriBounds b;
+        b.tnorm = nm;
+        b.pivmin = DBL_MIN * fmax(1.0, emax);
+        b.gl = lo - 2.0 * DBL_EPSILON * nm * (double)n - 2.0 * b.pivmin;
+        b.gu = hi + 2.0 * DBL_EPSILON * nm * (double)n + 2.0 * b.pivmin;
+        b.tol = tol;
+        b.m = m;
+        *out = b;
+    }
+}
+
+// number of eigenvalues below x of the tridiagonal rows [i0, i1)
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int i0, int i1,
+                                           double x, double pivmin) {
+    double q = __ldg(d + i0) - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    int c = q < 0.0;
+    for (int i = i0 + 1; i < i1; ++i) {
+        q = (__ldg(d + i) - x) - __ldg(e2 + i - 1) / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// one warp per level: 33-section of the Gershgorin interval with Sturm counts.
+// Levels k < m belong to rows [0, m), the others to rows [m, n).
+__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e2, int64_t n,
+                              const TriBounds* __restrict__ bnd, double* lam) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const TriBounds b = *bnd;
+    const int i0 = k < b.m ? 0 : b.m, i1 = k < b.m ? b.m : (int)n;
+    const int kk = (int)(k - i0);
+    double lo = b.gl, hi = b.gu;
+    for (int it = 0; it < 24; ++it) {
+        const double wdt = hi - lo;
+        if (wdt <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + b.pivmin) break;
+        const double x = lo + wdt * (double)(lane + 1) / 33.0;
+        const int c = sturm_count(d, e2, i0, i1, x, b.pivmin);
+        const unsigned mask = __ballot_sync(0xffffffffu, c > kk);
+        const int ls = mask ? __ffs(mask) - 1 : 32;
+        const double xl = __shfl_sync(0xffffffffu, x, ls > 0 ? ls - 1 : 0);
+        const double xh = __shfl_sync(0xffffffffu, x, ls < 32 ? ls : 31);
+        if (ls > 0) lo = xl;
+        if (ls < 32) hi = xh;
+    }
+    if (lane == 0) lam[k] = 0.5 * (lo + hi);
+}
+
+// squared first component of the eigenvector of rows [0, m) for level k < m,
+// from the twisted factorisation T - lam = N_r Delta_r N_r^T at the twist index
+// r with the smallest |gamma_r|; zero for levels of rows [m, n).
+// dp: scratch [m][n] (level index fastest) for the top-down pivots.
+__global__ void twisted_weights_kernel(const double* __restrict__ d, const double* __restrict__ e, int64_t n,
+                                       const TriBounds* __restrict__ bnd, const double* __restrict__ lam, double* dp,
+                                       double* w) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const TriBounds b = *bnd;
+    if (k >= b.m) {
+        w[k] = 0.0;
+        return;
+    }
+    const int m = b.m;
+    const double l = lam[k], piv = b.pivmin;
+    // top-down: T - l = L+ D+ L+^T
+    double p = __ldg(d) - l;
+    for (int i = 0; i + 1 < m; ++i) {
+        if (fabs(p) < piv) p = -piv;
+        dp[(size_t)i * n + k] = p;
+        const double ei = __ldg(e + i);
+        p = (__ldg(d + i + 1) - l) - ei * (ei / p);
+    }
+    if (fabs(p) < piv) p = -piv;
+    dp[(size_t)(m - 1) * n + k] = p;
+    // bottom-up: T - l = U- D- U-^T, twist element gamma_i = D+_i + D-_i - (d_i - l),
+    // t_i = sum_{j>i} z_j^2 / z_i^2
+    double q = __ldg(d + m - 1) - l, t = 0.0;
+    double gbest = fabs(p), tbest = 0.0;
+    int rbest = m - 1;
+    for (int i = m - 2; i >= 0; --i) {
+        if (fabs(q) < piv) q = -piv;
+        const double ei = __ldg(e + i);
+        const double u = ei / q;
+        const double di = __ldg(d + i) - l;
+        q = di - u * ei;
+        t = u * u * (1.0 + t);
+        const double g = fabs(dp[(size_t)i * n + k] + q - di);
+        if (g < gbest) {
+            gbest = g;
+            rbest = i;
+            tbest = t;
+        }
+    }
+    // head: z_0^2 / z_r^2 and sum_{j<r} z_j^2 / z_r^2
+    double P = 1.0, h = 0.0;
+    for (int i = 0; i < rbest; ++i) {
+        const double L = __ldg(e + i) / dp[(size_t)i * n + k];
+        const double L2 = L * L;
+        P *= L2;
+        h = L2 * (1.0 + h);
+    }
+    w[k] = P / (1.0 + h + tbest);   // P = 1 when r = 0 (z_0 = z_r)
+}
+
+// ascending order of all levels (ties by index): a permutation even where the
+// independently bisected levels of the two parts interleave; osc = scale * w
+__global__ void rank_levels_kernel(const double* __restrict__ lam, const double* __restrict__ w, int64_t n,
+                                   double scale, double* omega_out, double* osc) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double x = lam[k];
+    int64_t pos = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        const double y = __ldg(lam + j);
+        pos += (y < x) || (y == x && j < k);
+    }
+    omega_out[pos] = x;
+    osc[pos] = scale * w[k];
+}
+
+__global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out) {
+    __shared__ double s[kTriWarps];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += w[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
+        *out = t;
+    }
+}
+
+}  // namespace
+
+size_t tridiag_scratch_bytes(int64_t n) {
+    // v0 n, vbuf 2n, xbuf n, spart 1024 (double2); d, e, e2, lam, w (n doubles); dp n*n doubles; small items
+    return sizeof(double2) * (size_t)(4 * n + 1024) + sizeof(double) * (size_t)(5 * n + n * n) + 8192;
+}
+
+int tridiag_max_dim() { return 8192; }
+
+int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st) {
+    if (np < 1 || np > 3) return fail(BSE_EINVAL, "gram of %d vectors", np);
+    gram_kernel<<<1, kTriThreads, 0, st>>>(b, n, np, G);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
+// Reduce the block h (n x n, ld n, device; overwritten in the global-memory
+// variant) to T after the start reflector of b, then levels and weights.
+int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
+                            double* osc, double* wsum, int* err, cudaStream_t st) {
+    if (n < 1 || n > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld", (long long)n);
+    char* p = (char*)scratch;
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return (void*)q;
+    };
+    double2* v0 = (double2*)take(sizeof(double2) * n);
+    double2* vbuf = (double2*)take(sizeof(double2) * 2 * n);
+    double2* xbuf = (double2*)take(sizeof(double2) * n);
+    double2* spart = (double2*)take(sizeof(double2) * 1024);
+    double* d = (double*)take(sizeof(double) * n);
+    double* e = (double*)take(sizeof(double) * n);
+    double* e2 = (double*)take(sizeof(double) * n);
+    double* lam = (double*)take(sizeof(double) * n);
+    double* w = (double*)take(sizeof(double) * n);
+    double* beta0 = (double*)take(sizeof(double));
+    TriBounds* bnd = (TriBounds*)take(sizeof(TriBounds));
+    unsigned* bar = (unsigned*)take(sizeof(unsigned));
+    double* dp = (double*)take(sizeof(double) * n * n);
+
+    int dev = 0, sms = 0, maxsm = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 3) / 4));
+    const size_t static_smem = sizeof(double2) * (kTriWarps * kChunk + kChunk + 2) + sizeof(double) * kTriWarps + 64;
+    const size_t cols_bytes = sizeof(double2) * (size_t)((n - 1) / G + 1) * n;
+    const bool smem = cols_bytes + static_smem <= (size_t)maxsm;
+    if (!smem) G = sms;
+
+    BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+    BSE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    BSE_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, st));
+    reflect0_kernel<<<1, kTriThreads, 0, st>>>(b, n, v0, beta0);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+
+    TriArgs a;
+    a.A = h;
+    a.n = n;
+    a.v0 = v0;
+    a.beta0 = beta0;
+    a.vbuf = vbuf;
+    a.xbuf = xbuf;
+    a.spart = spart;
+    a.d = d;
+    a.e = e;
+    a.bar = bar;
+    a.err = err;
+    void* args[] = {&a};
+    const size_t dyn = smem ? cols_bytes : 0;
+    const void* fn = smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
+    if (smem) BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
+    if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
+    BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
+    note_launch();
+
+    tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, bnd);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    const int64_t warps_per_blk = 8;
+    bisect_kernel<<<(unsigned)((n + warps_per_blk - 1) / warps_per_blk), 32 * warps_per_blk, 0, st>>>(d, e2, n, bnd,
+                                                                                                   lam);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    twisted_weights_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d, e, n, bnd, lam, dp, w);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    rank_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam, w, n, scale, omega_out, osc);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    sum_kernel<<<1, kTriThreads, 0, st>>>(w, n, wsum);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
+}  // namespace bse

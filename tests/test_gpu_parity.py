@@ -333,3 +333,107 @@ def test_bf16_split_rejects_large_spheres(gpu):
         bse.bse_build_block(get("mos2_331"), mu, bse.BSE_BF16_SPLIT, bse.BSE_TERM_ALL, buf,
                             max(int(t["block_dim"][mu]), 1))
     assert e.value.code == bse.BSE_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("name", ["si4", "lif4", "mos2_331"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_all_blocks_one_build(gpu, name, prec):
+    """Every irrep block, plus the partner blocks of the optically active
+    irreps, from one bse_build_blocks call: each equals the oracle's
+    U^dagger H U and the single-target build of the same block."""
+    from oracle.projection import PartnerBasis, project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    H = oracle_h(name)
+    p = bse.BSE_FP64 if prec == "fp64" else bse.BSE_FP32
+    tol = TOL if prec == "fp64" else TOL32
+    ctx = get(name)
+    t = bse.bse_tables(ctx)
+    n_ir = len(b.dims)
+    bright = [mu for mu in b.bright() if t["partner_dim"][mu] > 0]
+    targets = [(mu, 0) for mu in range(n_ir)] + [(mu, 1) for mu in bright]
+    dims = [int(t["partner_dim" if pt else "block_dim"][mu]) for mu, pt in targets]
+    bufs = [torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda") for n in dims]
+    bse.bse_build_blocks(ctx, [mu for mu, _ in targets], [pt for _, pt in targets], p, bse.BSE_TERM_ALL,
+                         bufs, [max(n, 1) for n in dims])
+    for (mu, pt), buf, n in zip(targets, bufs, dims):
+        got = bse.colmajor(buf, n, n, max(n, 1)).cpu().numpy()
+        U = PartnerBasis(b, mu).U[0] if pt else b.basis(mu)[0]
+        assert got.shape == (U.shape[1],) * 2
+        if n == 0:
+            continue
+        ref = project(U, H)
+        assert _rel(got, ref) <= tol, (name, mu, pt, _rel(got, ref))
+        single = (bse.partner_block if pt else bse.block)(ctx, mu, prec=p).cpu().numpy()
+        assert np.abs(got - single).max() <= 1e-13 * np.abs(single).max(), (name, mu, pt)
+
+
+def test_build_blocks_arguments(gpu):
+    bse, torch, get = gpu
+    ctx = get("si4")
+    bse.bse_build_blocks(ctx, [], None, bse.BSE_FP64, bse.BSE_TERM_ALL, [], [])
+    with pytest.raises(RuntimeError):
+        bse.bse_build_blocks(ctx, [99], None, bse.BSE_FP64, bse.BSE_TERM_ALL, [None], [1])
+    mu = int(np.nonzero(bse.bse_tables(ctx)["bright"])[0][0])
+    n = int(bse.bse_tables(ctx)["block_dim"][mu])
+    buf = torch.empty(n * n, dtype=torch.complex128, device="cuda")
+    with pytest.raises(RuntimeError):
+        bse.bse_build_blocks(ctx, [mu], None, bse.BSE_FP64, bse.BSE_TERM_ALL, [buf], [n - 1])
+    with pytest.raises(RuntimeError):
+        bse.bse_build_blocks(ctx, [mu], None, bse.BSE_FP64, bse.BSE_TERM_ALL, [None], [n])
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_solver_choice_and_agreement(gpu, name):
+    """AUTO solves partner blocks without eigenvectors (tridiagonal
+    reduction from the dipole direction) and whole blocks of bright
+    multi-dimensional irreps with the dense solver; forcing either solver
+    on a partner block gives the same levels, strengths and spectrum."""
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    ctx = get(name)
+    t = bse.bse_tables(ctx)
+    omega = torch.tensor(d["omega"], device="cuda")
+    for mu in b.bright():
+        if t["partner_dim"][mu] == 0:
+            continue
+        h1 = bse.partner_block(ctx, mu)
+        out = {}
+        for solver in (bse.BSE_SOLVER_AUTO, bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG):
+            bse.bse_set_solver(ctx, solver)
+            out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
+            used = bse.bse_get_stats(ctx)["solver"]
+            assert used == (bse.BSE_SOLVER_DENSE if solver == bse.BSE_SOLVER_DENSE else bse.BSE_SOLVER_TRIDIAG)
+        bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
+        (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[bse.BSE_SOLVER_TRIDIAG]
+        assert np.abs(om - om2).max() <= TOL
+        for cl in _clusters(om):
+            assert abs(osc[cl].sum() - osc2[cl].sum()) <= 1e-10 * max(osc.sum(), 1e-300)
+        assert np.linalg.norm(im - im2) <= 1e-9 * max(np.linalg.norm(im), 1e-300)
+        if t["irrep_dim"][mu] > 1:
+            hb = bse.block(ctx, mu)
+            bse.spectrum(ctx, mu, hb, omega, d["eta"])
+            assert bse.bse_get_stats(ctx)["solver"] == bse.BSE_SOLVER_DENSE
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_dark_blocks_levels_only(gpu, name):
+    """Irreps outside the polar-vector representation: levels from the
+    tridiagonal path equal the oracle's eigenvalues, strengths are 0."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    ctx = get(name)
+    H = oracle_h(name)
+    omega = torch.tensor(d["omega"], device="cuda")
+    bright = set(b.bright())
+    for mu in range(len(b.dims)):
+        U, _ = b.basis(mu)
+        if mu in bright or U.shape[1] == 0:
+            continue
+        ref = np.linalg.eigvalsh(project(U, H))
+        h = bse.block(ctx, mu)
+        om, osc, im = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, h, omega, d["eta"]))
+        assert bse.bse_get_stats(ctx)["solver"] == bse.BSE_SOLVER_TRIDIAG
+        assert np.abs(om - ref).max() <= TOL * max(np.abs(ref).max(), 1.0), (name, mu)
+        assert np.all(osc == 0.0) and np.all(im == 0.0)

@@ -124,3 +124,22 @@ def test_bf16_split_build_within_0p1_mev(built):
     omb, oscb, imb = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, hb, omega, d["eta"]))
     assert np.abs(omb - om64).max() * 27211.386245988 <= 0.1
     assert np.linalg.norm(imb - im64) <= 1e-3 * np.linalg.norm(im64)
+
+
+def test_partner_solvers_agree(built):
+    """Levels and strengths of the partner block without eigenvectors
+    (tridiagonal reduction held in shared memory across all SMs) against the
+    dense eigensolver."""
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    h1 = bse.partner_block(ctx, mu)
+    omega = torch.tensor(d["omega"], device="cuda")
+    out = {}
+    for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG):
+        bse.bse_set_solver(ctx, solver)
+        out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
+    bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
+    (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[bse.BSE_SOLVER_TRIDIAG]
+    assert np.abs(om - om2).max() <= TOL * np.abs(om).max()
+    assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()
+    assert np.linalg.norm(im - im2) <= 1e-9 * np.linalg.norm(im)
