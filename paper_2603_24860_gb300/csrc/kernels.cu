@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "fp64_fast.h"
 #include "internal.h"
 
 namespace bse {
@@ -579,35 +580,53 @@ __global__ void wdiv_kernel(WdivGeom g, double* partial) {
             double sq = sqrt(disc);
             int lo = (int)floor((-Bq - sq) / (2.0 * A)) - 1;
             int hi = (int)ceil((-Bq + sq) / (2.0 * A)) + 1;
-            // exp(-b q^2) along the line by the exact recurrence
+            // Along the line x3 the quadratics q^2 = |p + x3 s3|^2 and Q^T L Q advance
+            // by forward differences and exp(-b q^2) by the exact recurrence
             //   E(x3 + 1) = E(x3) R(x3),  R(x3 + 1) = R(x3) C,  C = exp(-2 b |s3|^2),
-            // restarted from exp every 64 points to bound the rounding growth
+            // all restarted from their definitions every 64 points to bound the
+            // rounding growth; 1/(Q^T L Q) by a Newton reciprocal (no FP64 divide).
             const double C2 = exp(-2.0 * g.b * A);
             const double lim2 = g.lim * g.lim, in2 = (g.qmax - g.delta) * (g.qmax - g.delta);
-            double E = 0.0, Rr = 0.0;
+            double Ls[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Ls[a] = g.L[3 * a] * s3[0] + g.L[3 * a + 1] * s3[1] + g.L[3 * a + 2] * s3[2];
+            const double sLs = s3[0] * Ls[0] + s3[1] * Ls[1] + s3[2] * Ls[2];
+            double E = 0.0, Rr = 0.0, q2 = 0.0, dq2 = 0.0, ql = 0.0, dql = 0.0;
             for (int x3 = lo; x3 <= hi; ++x3) {
-                double Q[3] = {p[0] + x3 * s3[0], p[1] + x3 * s3[1], p[2] + x3 * s3[2]};
-                double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
                 if (((x3 - lo) & 63) == 0) {
+                    const double Q[3] = {p[0] + x3 * s3[0], p[1] + x3 * s3[1], p[2] + x3 * s3[2]};
+                    q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+                    dq2 = 2.0 * (Q[0] * s3[0] + Q[1] * s3[1] + Q[2] * s3[2]) + A;
+                    ql = 0.0;
+                    double QLs = 0.0, sLQ = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            ql += Q[a] * g.L[3 * a + c] * Q[c];
+                            sLQ += s3[a] * g.L[3 * a + c] * Q[c];
+                        }
+                        QLs += Q[a] * Ls[a];
+                    }
+                    dql = QLs + sLQ + sLs;
                     E = exp(-g.b * q2);
-                    Rr = exp(-g.b * (2.0 * (Q[0] * s3[0] + Q[1] * s3[1] + Q[2] * s3[2]) + A));
+                    Rr = exp(-g.b * dq2);
                 } else {
+                    q2 += dq2;
+                    dq2 += 2.0 * A;
+                    ql += dql;
+                    dql += 2.0 * sLs;
                     E *= Rr;
                     Rr *= C2;
                 }
-                if (q2 <= 0.0 || q2 > lim2) continue;
+                if ((x1 == 0 && x2 == 0 && x3 == 0) || q2 > lim2) continue;
                 double w = 1.0;
                 if (q2 >= in2) {
                     double x = (sqrt(q2) - g.qmax) / g.delta;
                     if (x > 1.0) continue;
                     w = (x * x * x - 3.0 * x + 2.0) * 0.25;
                 }
-                double ql = 0.0;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) ql += Q[a] * g.L[3 * a + c] * Q[c];
-                acc += E * w / ql;
+                acc = fma(E * w, rcp_nr(ql), acc);
             }
         }
     }

@@ -24,6 +24,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "fp64_fast.h"
 #include "internal.h"
 
 namespace bse {
@@ -33,7 +34,7 @@ namespace {
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kChunk = 8;                 // columns reduced together
-constexpr long kSpinLimit = 1l << 22;     // x >= 64 ns per poll: a few seconds
+constexpr long kSpinLimit = 1l << 23;     // >= 32 ns + an L2 round trip per poll: seconds
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -55,13 +56,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// Grid barrier of a cooperative launch (all CTAs co-resident).  Bounded: on
+// Grid barrier of a cooperative launch (all CTAs co-resident): one
+// release-add per CTA and acquire-polling of the counter.  Bounded: on
 // timeout, or when another CTA has raised the error flag, returns false.
 __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         bool ok = false;
         for (long it = 0; it < kSpinLimit; ++it) {
             if (ld_acquire(bar) >= target) {
@@ -69,66 +70,231 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, int* s_fl
                 break;
             }
             if (*(volatile int*)err) break;
-            __nanosleep(64);
+            if (it > 64) __nanosleep(32);
         }
         if (!ok) atomicExch(err, 1);
-        __threadfence();
         *s_flag = ok ? 1 : 0;
     }
     __syncthreads();
     return *s_flag != 0;
 }
 
+// Rank-2 update  A_rc -= v_r conj(w_c) + w_r conj(v_c)  of a chunk, eight FMAs per element
+template <int NC>
+__device__ __forceinline__ void chunk_update(double2* cb, size_t cs, const double2* V, const double2* W,
+                                             const int* jcol, int r0, int n) {
+    double2 vj[NC], wj[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        vj[c] = V[jcol[c]];
+        wj[c] = W[jcol[c]];
+    }
+    for (int r = r0 + (int)threadIdx.x; r < n; r += kTriThreads) {
+        const double2 v = V[r], w = W[r];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double2 q = cb[c * cs + r];
+            q.x = fma(-v.x, wj[c].x, q.x);
+            q.x = fma(-v.y, wj[c].y, q.x);
+            q.x = fma(-w.x, vj[c].x, q.x);
+            q.x = fma(-w.y, vj[c].y, q.x);
+            q.y = fma(-v.y, wj[c].x, q.y);
+            q.y = fma(v.x, wj[c].y, q.y);
+            q.y = fma(-w.y, vj[c].x, q.y);
+            q.y = fma(w.x, vj[c].y, q.y);
+            cb[c * cs + r] = q;
+        }
+    }
+}
+
+#define BSE_NC_DISPATCH(nc, F, ...)         \
+    switch (nc) {                            \
+        case 1: F<1>(__VA_ARGS__); break;    \
+        case 2: F<2>(__VA_ARGS__); break;    \
+        case 3: F<3>(__VA_ARGS__); break;    \
+        case 4: F<4>(__VA_ARGS__); break;    \
+        case 5: F<5>(__VA_ARGS__); break;    \
+        case 6: F<6>(__VA_ARGS__); break;    \
+        case 7: F<7>(__VA_ARGS__); break;    \
+        default: F<8>(__VA_ARGS__); break;   \
+    }
+
 struct TriArgs {
     double2* A;           // n x n column-major, leading dimension n (updated in place in the global variant)
     int64_t n;
     const double2* v0;    // initial reflector
     const double* beta0;  // its (real) scalar
-    double2* vbuf;        // [2][n] reflectors, by step parity
-    double2* xbuf;        // [n] x = tau A v
-    double2* spart;       // [G] per-CTA parts of x^H v
+    double2* ncol;        // [2][n] the next column to be reflected, published by its owner, by parity
+    double2* xbuf;        // [2][n] x = tau A v, by step parity
+    double2* spart;       // [2][G] per-CTA parts of x^H v, by step parity
     double* d;            // [n] diagonal of T
     double* e;            // [n] off-diagonal of T (e[n-1] unused)
     unsigned* bar;        // barrier counter, zero on entry
     int* err;             // error flag, zero on entry
 };
 
+// One grid barrier per reflection step s (H(s) = I - tau v v^H on rows >= s+1,
+// s = -1 being the start reflector H0 on all rows):
+//   P1  x(s) and the parts of x^H v from all CTAs: alpha = -tau (x^H v)/2,
+//       w = x + alpha v (shared memory)
+//   P2  own columns j > s:  A_rj -= v_r conj(w_j) + w_r conj(v_j),  r > s
+//   P3  every CTA applies the same update to the published copy of column
+//       k = s+1 and forms reflector k from it (zlarfg convention, v_{k+1} = 1)
+//   P4  the owner of column k+1 publishes it (its state before step k)
+//   P5  x(k)_j = tau(k) sum_r conj(A_rj) v_r for own columns j > k (Hermitian:
+//       (A v)_j is a column dot product) and this CTA's part of x^H v
+//   grid barrier
 template <bool kSmem>
 __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
-    extern __shared__ __align__(16) double2 s_cols[];
-    __shared__ double2 s_red[kTriWarps][kChunk];
-    __shared__ double2 s_s[kChunk];
-    __shared__ double2 s_scal[2];
+    extern __shared__ __align__(16) double2 s_dyn[];
+    __shared__ double2 s_s[kTriWarps];
+    __shared__ double2 s_scal[2];   // [0] inv(alpha - beta) of the new reflector, [1] alpha of P1
+    __shared__ double2 s_tau;
     __shared__ double s_sig[kTriWarps];
     __shared__ int s_flag;
 
     const int n = (int)a.n;
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;
+    double2* V = s_dyn;
+    double2* W = s_dyn + n;
+    double2* C = s_dyn + 2 * (size_t)n;
+    double2* s_cols = s_dyn + 3 * (size_t)n;
     auto col = [&](int l) -> double2* {
         return kSmem ? s_cols + (size_t)l * n : a.A + (size_t)(blk + l * G) * n;
     };
-    if (kSmem) {
+    const size_t cstride = kSmem ? (size_t)n : (size_t)G * n;
+    if (kSmem)
         for (int l = 0; l < ncl; ++l) {
             const double2* src = a.A + (size_t)(blk + l * G) * n;
             for (int r = tid; r < n; r += kTriThreads) s_cols[(size_t)l * n + r] = src[r];
         }
-        __syncthreads();
-    }
+    for (int r = tid; r < n; r += kTriThreads) V[r] = __ldcg(a.v0 + r);
+    if (tid == 0) s_tau = make_double2(__ldcg(a.beta0), 0.0);
+    __syncthreads();
+    // column 0 as it is before the start reflector
+    if (blk == 0)
+        for (int r = tid; r < n; r += kTriThreads) a.ncol[r] = col(0)[r];
     unsigned nbar = 0;
 
-    // reflector of column k (owner CTA): rows k+1..n-1, v_{k+1} = 1 (LAPACK zlarfg convention)
-    auto make_reflector = [&](int k) {
-        double2* ck = col(k / G);
+    // P5 for reflector k (rows > k; k = -1: all rows): one warp per column, so
+    // the only cross-lane FP64 work is one shuffle reduction per column
+    auto dots = [&](int k) {
+        const int r0 = k + 1;
+        const double2 tau = s_tau;
+        const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;
+        double2* xb = a.xbuf + (size_t)(k & 1) * n;
+        double2 sw = make_double2(0.0, 0.0);
+        for (int l = l0 + wid; l < ncl; l += kTriWarps) {
+            const double2* cl = col(l);
+            double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+            int r = r0 + lane;
+            for (; r + 32 < n; r += 64) {
+                const double2 a0 = cl[r], v0 = V[r], a1 = cl[r + 32], v1 = V[r + 32];
+                acc.x = fma(a0.x, v0.x, acc.x);
+                acc.x = fma(a0.y, v0.y, acc.x);
+                acc.y = fma(a0.x, v0.y, acc.y);
+                acc.y = fma(-a0.y, v0.x, acc.y);
+                acc2.x = fma(a1.x, v1.x, acc2.x);
+                acc2.x = fma(a1.y, v1.y, acc2.x);
+                acc2.y = fma(a1.x, v1.y, acc2.y);
+                acc2.y = fma(-a1.y, v1.x, acc2.y);
+            }
+            if (r < n) {
+                const double2 a0 = cl[r], v0 = V[r];
+                acc.x = fma(a0.x, v0.x, acc.x);
+                acc.x = fma(a0.y, v0.y, acc.x);
+                acc.y = fma(a0.x, v0.y, acc.y);
+                acc.y = fma(-a0.y, v0.x, acc.y);
+            }
+            const double sx = warp_sum(acc.x + acc2.x), sy = warp_sum(acc.y + acc2.y);
+            if (lane == 0) {
+                const int j = blk + l * G;
+                const double2 x = cmul(tau, make_double2(sx, sy));
+                xb[j] = x;
+                const double2 t = cmulc(x, V[j]);
+                sw.x += t.x;
+                sw.y += t.y;
+            }
+        }
+        if (lane == 0) s_s[wid] = sw;
+        __syncthreads();
+        if (tid == 0) {
+            double2 sp = make_double2(0.0, 0.0);
+            for (int w = 0; w < kTriWarps; ++w) {
+                sp.x += s_s[w].x;
+                sp.y += s_s[w].y;
+            }
+            a.spart[(size_t)(k & 1) * G + blk] = sp;
+        }
+    };
+
+    dots(-1);
+    if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+
+    for (int s = -1; s <= n - 2; ++s) {
+        const int r0 = s + 1;
+        const int k = s + 1;   // column reflected next
+        const bool more = s < n - 2;
+        // P1: gather x(s), the parts of x^H v and the published column k in one round trip
+        const double2* xb = a.xbuf + (size_t)(s & 1) * n;
+        const double2* nc_src = a.ncol + (size_t)(k & 1) * n;
+        for (int r = r0 + tid; r < n; r += kTriThreads) {
+            W[r] = __ldcg(xb + r);
+            if (more) C[r] = __ldcg(nc_src + r);
+        }
+        if (wid == 0) {
+            double sx = 0.0, sy = 0.0;
+            const double2* sp = a.spart + (size_t)(s & 1) * G;
+#pragma unroll 4
+            for (int b = lane; b < G; b += 32) {
+                const double2 p = __ldcg(sp + b);
+                sx += p.x;
+                sy += p.y;
+            }
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) {
+                const double2 al = cmul(s_tau, make_double2(sx, sy));
+                s_scal[1] = make_double2(-0.5 * al.x, -0.5 * al.y);
+            }
+        }
+        __syncthreads();
+        const double2 alpha = s_scal[1];
+        for (int r = r0 + tid; r < n; r += kTriThreads) {
+            const double2 av = cmul(alpha, V[r]);
+            W[r].x += av.x;
+            W[r].y += av.y;
+        }
+        __syncthreads();
+        // P2: rank-2 update of own columns j >= r0
+        const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;
+        for (int c0 = l0; c0 < ncl; c0 += kChunk) {
+            const int nc = min(kChunk, ncl - c0);
+            int jcol[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) jcol[c] = blk + (c0 + c) * G;
+            BSE_NC_DISPATCH(nc, chunk_update, col(c0), cstride, V, W, jcol, r0, n)
+        }
+        if (!more) break;
+        // P3: column k after this step's update, then its reflector
+        const double2 vk = V[k], wk = W[k];
+        __syncthreads();
         double sg = 0.0;
-        for (int r = k + 2 + tid; r < n; r += kTriThreads) sg += ck[r].x * ck[r].x + ck[r].y * ck[r].y;
+        for (int r = k + tid; r < n; r += kTriThreads) {
+            const double2 c = C[r], v = V[r], w = W[r];
+            const double2 t1 = cmulc(wk, v), t2 = cmulc(vk, w);
+            const double2 cr = make_double2(c.x - t1.x - t2.x, c.y - t1.y - t2.y);
+            W[r] = cr;
+            if (r >= k + 2) sg += cr.x * cr.x + cr.y * cr.y;
+        }
         sg = warp_sum(sg);
         if (lane == 0) s_sig[wid] = sg;
         __syncthreads();
         if (tid == 0) {
             double sigma = 0.0;
             for (int w = 0; w < kTriWarps; ++w) sigma += s_sig[w];
-            const double2 al = ck[k + 1];
+            const double2 al = W[k + 1];
             double2 tau, inv;
             double beta;
             if (sigma == 0.0 && al.y == 0.0) {
@@ -137,130 +303,34 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
                 inv = make_double2(0.0, 0.0);
             } else {
                 beta = -copysign(sqrt(al.x * al.x + al.y * al.y + sigma), al.x);
-                tau = make_double2((beta - al.x) / beta, -al.y / beta);
+                const double rb = 1.0 / beta;
+                tau = make_double2((beta - al.x) * rb, -al.y * rb);
                 const double2 den = make_double2(al.x - beta, al.y);
-                const double m2 = den.x * den.x + den.y * den.y;
-                inv = make_double2(den.x / m2, -den.y / m2);
+                const double rm = 1.0 / (den.x * den.x + den.y * den.y);
+                inv = make_double2(den.x * rm, -den.y * rm);
             }
             s_scal[0] = inv;
-            a.d[k] = ck[k].x;
-            a.e[k] = beta;
-            a.vbuf[(size_t)(k & 1) * n + k + 1] = make_double2(1.0, 0.0);
-            // tau rides in the slot below the reflector's first row (row k is outside its support)
-            a.vbuf[(size_t)(k & 1) * n + k] = tau;
+            s_tau = tau;
+            if (blk == 0) {
+                a.d[k] = W[k].x;
+                a.e[k] = beta;
+            }
         }
         __syncthreads();
-        const double2 inv = s_scal[0];
-        double2* vb = a.vbuf + (size_t)(k & 1) * n;
-        for (int r = k + 2 + tid; r < n; r += kTriThreads) vb[r] = cmul(ck[r], inv);
-    };
-
-    for (int i = -1; i <= n - 2; ++i) {
-        const int r0 = i + 1;
-        const double2* vb = i < 0 ? a.v0 : a.vbuf + (size_t)(i & 1) * n;
-        if (i >= 0 && !grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
-        const double2 tau = i < 0 ? make_double2(__ldcg(a.beta0), 0.0) : __ldcg(vb + i);
-        // (b) x_j = tau sum_r conj(A_rj) v_r for own columns j >= r0, and this CTA's part of x^H v
-        const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;   // first own slot with j >= r0
-        double2 spart = make_double2(0.0, 0.0);
-        for (int c0 = l0; c0 < ncl; c0 += kChunk) {
-            const int nc = min(kChunk, ncl - c0);
-            double2 acc[kChunk];
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) acc[c] = make_double2(0.0, 0.0);
-            for (int r = r0 + tid; r < n; r += kTriThreads) {
-                const double2 v = __ldcg(vb + r);
-#pragma unroll
-                for (int c = 0; c < kChunk; ++c)
-                    if (c < nc) {
-                        const double2 x = cmulc(col(c0 + c)[r], v);
-                        acc[c].x += x.x;
-                        acc[c].y += x.y;
-                    }
-            }
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) {
-                const double sx = warp_sum(acc[c].x), sy = warp_sum(acc[c].y);
-                if (lane == 0) s_red[wid][c] = make_double2(sx, sy);
-            }
-            __syncthreads();
-            if (tid < nc) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int w = 0; w < kTriWarps; ++w) {
-                    s.x += s_red[w][tid].x;
-                    s.y += s_red[w][tid].y;
-                }
-                const int j = blk + (c0 + tid) * G;
-                const double2 x = cmul(tau, s);
-                a.xbuf[j] = x;
-                const double2 sv = cmulc(x, __ldcg(vb + j));
-                s_s[tid] = sv;
-            }
-            __syncthreads();
-            if (tid == 0)
-                for (int c = 0; c < nc; ++c) {
-                    spart.x += s_s[c].x;
-                    spart.y += s_s[c].y;
-                }
-            __syncthreads();
+        {
+            const double2 inv = s_scal[0];
+            for (int r = k + 1 + tid; r < n; r += kTriThreads) V[r] = r == k + 1 ? make_double2(1.0, 0.0) : cmul(W[r], inv);
         }
-        if (tid == 0) a.spart[blk] = spart;
+        __syncthreads();
+        // P4: publish column k+1 (state before step k)
+        if (k + 1 <= n - 2 && (k + 1) % G == blk) {
+            const double2* ck = col((k + 1) / G);
+            double2* dst = a.ncol + (size_t)((k + 1) & 1) * n;
+            for (int r = k + 1 + tid; r < n; r += kTriThreads) dst[r] = ck[r];
+        }
+        // P5
+        dots(k);
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
-        // (c) alpha = -tau (x^H v) / 2, w = x + alpha v, A -= v w^H + w v^H on own columns j >= r0
-        if (wid == 0) {
-            double sx = 0.0, sy = 0.0;
-            for (int b = lane; b < G; b += 32) {
-                const double2 p = __ldcg(a.spart + b);
-                sx += p.x;
-                sy += p.y;
-            }
-            sx = warp_sum(sx);
-            sy = warp_sum(sy);
-            if (lane == 0) {
-                const double2 al = cmul(tau, make_double2(sx, sy));
-                s_scal[1] = make_double2(-0.5 * al.x, -0.5 * al.y);
-            }
-        }
-        __syncthreads();
-        const double2 alpha = s_scal[1];
-        const int next = i + 1;
-        const bool lookahead = next <= n - 2 && next % G == blk;
-        auto update = [&](int c0, int nc, int skip) {
-            double2 vj[kChunk], wj[kChunk];
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c)
-                if (c < nc) {
-                    const int j = blk + (c0 + c) * G;
-                    vj[c] = __ldcg(vb + j);
-                    const double2 xj = __ldcg(a.xbuf + j);
-                    const double2 av = cmul(alpha, vj[c]);
-                    wj[c] = make_double2(xj.x + av.x, xj.y + av.y);
-                }
-            for (int r = r0 + tid; r < n; r += kTriThreads) {
-                const double2 v = __ldcg(vb + r), x = __ldcg(a.xbuf + r);
-                const double2 av = cmul(alpha, v);
-                const double2 w = make_double2(x.x + av.x, x.y + av.y);
-#pragma unroll
-                for (int c = 0; c < kChunk; ++c)
-                    if (c < nc && c0 + c != skip) {
-                        double2* p = col(c0 + c) + r;
-                        const double2 t1 = cmulc(wj[c], v), t2 = cmulc(vj[c], w);
-                        // v_r conj(w_j) + w_r conj(v_j)
-                        double2 q = *p;
-                        q.x -= t1.x + t2.x;
-                        q.y -= t1.y + t2.y;
-                        *p = q;
-                    }
-            }
-        };
-        int skip = -1;
-        if (lookahead) {
-            skip = next / G;
-            update(skip, 1, -1);
-            __syncthreads();
-            make_reflector(next);
-        }
-        for (int c0 = l0; c0 < ncl; c0 += kChunk) update(c0, min(kChunk, ncl - c0), skip);
     }
     __syncthreads();
     if ((n - 1) % G == blk && tid == 0) a.d[n - 1] = col((n - 1) / G)[n - 1].x;
@@ -389,44 +459,66 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
     }
 }
 
-// number of eigenvalues below x of the tridiagonal rows [i0, i1)
+// Number of eigenvalues below x of the tridiagonal rows [i0, i1): sign
+// changes of the leading principal minors p_i = det(T[i0..i] - x), from the
+// three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm).
+// No division (an FP64 divide costs about a thousand cycles of latency on
+// this GPU); p_{i-1}, p_i are rescaled by an exact power of two every eight
+// rows.  An exact zero p_i is replaced by -2^-200 p_{i-1}, as a zero pivot is
+// replaced by a tiny negative one in the ratio form.
 __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int i0, int i1,
-                                           double x, double pivmin) {
-    double q = __ldg(d + i0) - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    int c = q < 0.0;
+                                           double x) {
+    double pm = 1.0, p = __ldg(d + i0) - x;
+    if (p == 0.0) p = -0x1p-200;
+    bool sp = p < 0.0;
+    int c = sp;
     for (int i = i0 + 1; i < i1; ++i) {
-        q = (__ldg(d + i) - x) - __ldg(e2 + i - 1) / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+        double pn = fma(__ldg(d + i) - x, p, -__ldg(e2 + i - 1) * pm);
+        if (pn == 0.0) pn = -p * 0x1p-200;   // the zero pivot becomes -tiny (ratio p_i / p_{i-1})
+        const bool sn = pn < 0.0;
+        c += sn != sp;
+        sp = sn;
+        pm = p;
+        p = pn;
+        if (((i - i0) & 7) == 0) {
+            const int ex = (int)((__double_as_longlong(p) >> 52) & 0x7ff) - 1023;
+            if (ex > 256 || ex < -256) {
+                const double s = exp2i(-ex);
+                p *= s;
+                pm *= s;
+            }
+        }
     }
     return c;
 }
 
-// one warp per level: 33-section of the Gershgorin interval with Sturm counts.
-// Levels k < m belong to rows [0, m), the others to rows [m, n).
+// Sixteen lanes per level: 17-section of the Gershgorin interval with Sturm
+// counts, 14 rounds from 2 ||T|| below eps ||T||.  GB300 runs two FP64 lanes
+// per clock per SM, so the cost is the chain of FP64 warp instructions each
+// warp issues: fewer, wider rounds and one warp per SM sub-partition beat
+// narrow bisection.  Every lane runs all rounds (uniform ballots).  Levels
+// k < m belong to rows [0, m), the others to rows [m, n).
+constexpr int kSect = 16;
 __global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e2, int64_t n,
                               const TriBounds* __restrict__ bnd, double* lam) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, sub = lane % kSect, base = lane - sub;
+    const int64_t k = min(t / kSect, n - 1);
     const TriBounds b = *bnd;
     const int i0 = k < b.m ? 0 : b.m, i1 = k < b.m ? b.m : (int)n;
     const int kk = (int)(k - i0);
     double lo = b.gl, hi = b.gu;
-    for (int it = 0; it < 24; ++it) {
-        const double wdt = hi - lo;
-        if (wdt <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + b.pivmin) break;
-        const double x = lo + wdt * (double)(lane + 1) / 33.0;
-        const int c = sturm_count(d, e2, i0, i1, x, b.pivmin);
-        const unsigned mask = __ballot_sync(0xffffffffu, c > kk);
-        const int ls = mask ? __ffs(mask) - 1 : 32;
-        const double xl = __shfl_sync(0xffffffffu, x, ls > 0 ? ls - 1 : 0);
-        const double xh = __shfl_sync(0xffffffffu, x, ls < 32 ? ls : 31);
+    for (int it = 0; it < 14; ++it) {
+        const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (kSect + 1));
+        const int c = sturm_count(d, e2, i0, i1, x);
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
+        const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
+        const double xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
+        const double xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
         if (ls > 0) lo = xl;
-        if (ls < 32) hi = xh;
+        if (ls < kSect) hi = xh;
     }
-    if (lane == 0) lam[k] = 0.5 * (lo + hi);
+    if (sub == 0 && t / kSect < n) lam[k] = 0.5 * (lo + hi);
 }
 
 // squared first component of the eigenvector of rows [0, m) for level k < m,
@@ -451,7 +543,7 @@ __global__ void twisted_weights_kernel(const double* __restrict__ d, const doubl
         if (fabs(p) < piv) p = -piv;
         dp[(size_t)i * n + k] = p;
         const double ei = __ldg(e + i);
-        p = (__ldg(d + i + 1) - l) - ei * (ei / p);
+        p = (__ldg(d + i + 1) - l) - ei * ei * rcp_nr(p);
     }
     if (fabs(p) < piv) p = -piv;
     dp[(size_t)(m - 1) * n + k] = p;
@@ -460,10 +552,11 @@ __global__ void twisted_weights_kernel(const double* __restrict__ d, const doubl
     double q = __ldg(d + m - 1) - l, t = 0.0;
     double gbest = fabs(p), tbest = 0.0;
     int rbest = m - 1;
+#pragma unroll 4
     for (int i = m - 2; i >= 0; --i) {
         if (fabs(q) < piv) q = -piv;
         const double ei = __ldg(e + i);
-        const double u = ei / q;
+        const double u = ei * rcp_nr(q);
         const double di = __ldg(d + i) - l;
         q = di - u * ei;
         t = u * u * (1.0 + t);
@@ -476,8 +569,9 @@ __global__ void twisted_weights_kernel(const double* __restrict__ d, const doubl
     }
     // head: z_0^2 / z_r^2 and sum_{j<r} z_j^2 / z_r^2
     double P = 1.0, h = 0.0;
+#pragma unroll 4
     for (int i = 0; i < rbest; ++i) {
-        const double L = __ldg(e + i) / dp[(size_t)i * n + k];
+        const double L = __ldg(e + i) * rcp_nr(dp[(size_t)i * n + k]);
         const double L2 = L * L;
         P *= L2;
         h = L2 * (1.0 + h);
@@ -518,11 +612,11 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 }  // namespace
 
 size_t tridiag_scratch_bytes(int64_t n) {
-    // v0 n, vbuf 2n, xbuf n, spart 1024 (double2); d, e, e2, lam, w (n doubles); dp n*n doubles; small items
-    return sizeof(double2) * (size_t)(4 * n + 1024) + sizeof(double) * (size_t)(5 * n + n * n) + 8192;
+    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); dp n*n doubles; small items
+    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + n * n) + 8192;
 }
 
-int tridiag_max_dim() { return 8192; }
+int tridiag_max_dim() { return 4736; }   // v, w and the next column of a step in 227 KB of shared memory
 
 int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st) {
     if (np < 1 || np > 3) return fail(BSE_EINVAL, "gram of %d vectors", np);
@@ -544,9 +638,9 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
         return (void*)q;
     };
     double2* v0 = (double2*)take(sizeof(double2) * n);
-    double2* vbuf = (double2*)take(sizeof(double2) * 2 * n);
-    double2* xbuf = (double2*)take(sizeof(double2) * n);
-    double2* spart = (double2*)take(sizeof(double2) * 1024);
+    double2* ncol = (double2*)take(sizeof(double2) * 2 * n);
+    double2* xbuf = (double2*)take(sizeof(double2) * 2 * n);
+    double2* spart = (double2*)take(sizeof(double2) * 2048);
     double* d = (double*)take(sizeof(double) * n);
     double* e = (double*)take(sizeof(double) * n);
     double* e2 = (double*)take(sizeof(double) * n);
@@ -562,10 +656,13 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     BSE_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 3) / 4));
-    const size_t static_smem = sizeof(double2) * (kTriWarps * kChunk + kChunk + 2) + sizeof(double) * kTriWarps + 64;
+    const size_t static_smem = sizeof(double2) * (kTriWarps + 3) + sizeof(double) * kTriWarps + 64;
+    const size_t vec_bytes = sizeof(double2) * 3 * (size_t)n;   // v, w and the next column of a step
     const size_t cols_bytes = sizeof(double2) * (size_t)((n - 1) / G + 1) * n;
-    const bool smem = cols_bytes + static_smem <= (size_t)maxsm;
+    const bool smem = vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
     if (!smem) G = sms;
+    if (vec_bytes + static_smem > (size_t)maxsm)
+        return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld exceeds shared memory", (long long)n);
 
     BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     BSE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -579,7 +676,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     a.n = n;
     a.v0 = v0;
     a.beta0 = beta0;
-    a.vbuf = vbuf;
+    a.ncol = ncol;
     a.xbuf = xbuf;
     a.spart = spart;
     a.d = d;
@@ -587,9 +684,9 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     a.bar = bar;
     a.err = err;
     void* args[] = {&a};
-    const size_t dyn = smem ? cols_bytes : 0;
+    const size_t dyn = vec_bytes + (smem ? cols_bytes : 0);
     const void* fn = smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
-    if (smem) BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
     if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
@@ -599,12 +696,10 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, bnd);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    const int64_t warps_per_blk = 8;
-    bisect_kernel<<<(unsigned)((n + warps_per_blk - 1) / warps_per_blk), 32 * warps_per_blk, 0, st>>>(d, e2, n, bnd,
-                                                                                                   lam);
+    bisect_kernel<<<(unsigned)((kSect * n + 31) / 32), 32, 0, st>>>(d, e2, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    twisted_weights_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d, e, n, bnd, lam, dp, w);
+    twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(d, e, n, bnd, lam, dp, w);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     rank_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam, w, n, scale, omega_out, osc);
