@@ -109,7 +109,11 @@ typedef struct {
  * paper uses an SVD, whose basis is not unique), and compute W^div if
  * requested.  stream: a cudaStream_t, or NULL for the default stream.
  * On success *out owns device memory until bse_destroy.  Blocks until the
- * set-up work has finished.
+ * set-up work has finished.  Device memory of contexts comes from the
+ * device's stream-ordered memory pool (cudaMallocAsync on the context's
+ * stream); bse_create raises that pool's release threshold to 16 GiB, so
+ * memory freed by one context is reused by the next without a driver
+ * allocation.
  * Errors: EINVAL (sizes, non-unimodular R, mesh not invariant, G = 0 missing),
  * ESYMM (operations not a group, sphere not closed under an operation,
  * non-unitary Gamma, block dimensions not summing to N), EUNSUPPORTED
@@ -117,7 +121,9 @@ typedef struct {
  */
 int bse_create(bse_ctx** out, const bse_system* sys, void* stream);
 
-/* bse_destroy - free everything owned by ctx (NULL is allowed). */
+/* bse_destroy - wait for the context's stream, then free everything owned
+ * by ctx (device memory returns to the device's memory pool; NULL is
+ * allowed). */
 int bse_destroy(bse_ctx* ctx);
 
 /* Message of the last failure on the calling thread ("" if none). */

@@ -24,30 +24,56 @@ using namespace bse;
 
 namespace {
 
+// Device memory of a context comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the context's stream).  The pool keeps
+// up to kPoolKeep bytes that contexts free for the next one, so creating a
+// context per workload costs no driver allocation once the pool is warm.
+constexpr uint64_t kPoolKeep = 16ull << 30;
+thread_local cudaStream_t t_alloc_stream = nullptr;
+
+struct AllocStream {   // stream the allocations of one API call are ordered on
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+    ~AllocStream() { t_alloc_stream = prev; }
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t n = 0;
+    cudaStream_t st = nullptr;   // stream of the allocation (its free is ordered there)
 };
 
 int ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.n >= bytes) return BSE_OK;
-    if (b.p) cudaFree(b.p);
+    if (b.p) cudaFreeAsync(b.p, b.st);
     b.p = nullptr;
     b.n = 0;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = cudaMallocAsync(&b.p, bytes, t_alloc_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(BSE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        b.p = nullptr;
+        return fail(BSE_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     }
     b.n = bytes;
+    b.st = t_alloc_stream;
     return BSE_OK;
 }
 
 void release(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) cudaFreeAsync(b.p, b.st);
     b.p = nullptr;
     b.n = 0;
+}
+
+int keep_pool_memory() {
+    int dev = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    BSE_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t keep = kPoolKeep;
+    BSE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    return BSE_OK;
 }
 
 template <class T>
@@ -627,7 +653,8 @@ static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
-                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status})
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status,
+                      &c->triScratch, &c->triSmall})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -658,7 +685,9 @@ int bse_create(bse_ctx** out, const bse_system* sys, void* stream) {
     bse_ctx* c = new (std::nothrow) bse_ctx();
     if (!c) return fail(BSE_ENOMEM, "out of host memory");
     c->stream = (cudaStream_t)stream;
-    int r = create_impl(c, sys);
+    AllocStream alloc_on_(c->stream);
+    int r = keep_pool_memory();
+    if (r == BSE_OK) r = create_impl(c, sys);
     if (r != BSE_OK) {
         cudaStreamSynchronize(c->stream);
         free_ctx(c);
@@ -702,6 +731,8 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
 
 int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs, int32_t bands, void* out) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || (npairs > 0 && (!k || !kp || !out))) return fail(BSE_EINVAL, "null argument");
     if (bands < 0 || bands > 2) return fail(BSE_EINVAL, "bands must be CC, VV or CV");
     if (npairs < 0 || npairs > (1ll << 31) - 1) return fail(BSE_EINVAL, "npairs out of range");
@@ -720,6 +751,8 @@ int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs
 
 int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
     const Tables& t = c->t;
     if (ld < t.N || ld > (1ll << 31) - 1) return fail(BSE_EINVAL, "ld must be in [N, 2^31)");
@@ -899,6 +932,8 @@ static int build_generic(bse_ctx* c, IrrepDev& bd, int32_t prec, uint32_t terms,
 
 int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
     if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
@@ -908,6 +943,8 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
 
 int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* h, int64_t ld) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
     if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
@@ -918,6 +955,8 @@ int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms
 int bse_build_blocks(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
                      uint32_t terms, void* const* h, const int64_t* ld) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || n < 0 || (n > 0 && (!irrep || !h || !ld))) return fail(BSE_EINVAL, "null argument");
     if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
@@ -937,6 +976,8 @@ int bse_build_blocks(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t*
 
 int bse_block_star_columns(bse_ctx* c, int32_t mu, int32_t partner, int64_t* out) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !out) return fail(BSE_EINVAL, "null argument");
     if (partner) BSE_TRY(ensure_partner(c, mu));
     else BSE_TRY(ensure_basis(c, mu));
@@ -947,6 +988,8 @@ int bse_block_star_columns(bse_ctx* c, int32_t mu, int32_t partner, int64_t* out
 
 int bse_block_basis(bse_ctx* c, int32_t mu, void* u, int64_t ld) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !u) return fail(BSE_EINVAL, "null argument");
     BSE_TRY(ensure_basis(c, mu));
     if (ld < c->t.N) return fail(BSE_EINVAL, "ld < N");
@@ -958,6 +1001,8 @@ int bse_block_basis(bse_ctx* c, int32_t mu, void* u, int64_t ld) {
 
 int bse_dipoles(bse_ctx* c, void* b) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !b) return fail(BSE_EINVAL, "null argument");
     return launch_dipoles(c->S, (double2*)b, c->stream);
 }
@@ -1093,6 +1138,8 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
 int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
                        double eta, double* omega_out, double* osc, double* im_eps) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     BSE_TRY(ensure_basis(c, mu));
@@ -1103,6 +1150,8 @@ int bse_block_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const 
 int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, const double* omega, int64_t n_omega,
                          double eta, double* omega_out, double* osc, double* im_eps) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !h || !omega_out || !osc || (n_omega > 0 && (!omega || !im_eps))) return fail(BSE_EINVAL, "null argument");
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     BSE_TRY(ensure_partner(c, mu));
@@ -1139,6 +1188,8 @@ int bse_get_stats(bse_ctx* c, bse_stats* out) {
 
 int bse_build_blocks_work(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t* partner, bse_work* out) {
     clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
     if (!c || !out || n < 0 || (n > 0 && !irrep)) return fail(BSE_EINVAL, "null argument");
     std::vector<const Basis*> bases;
     for (int32_t i = 0; i < n; ++i) {

@@ -27,4 +27,23 @@ __device__ __forceinline__ double rcp_nr(double a) {
     return y;
 }
 
+// 1/sqrt(a) by Newton-Raphson (y <- y (3 - a y^2) / 2, quadratic convergence)
+// from a single-precision seed of a scaled into [1, 4): three steps take 23
+// bits past 53 with margin.  For normal, finite a > 0; within a few ulp.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+    const long long bits = __double_as_longlong(a);
+    const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
+    const int h = ex >> 1;                                       // a = m 2^(2h), m in [1, 4)
+    const double m = __longlong_as_double((bits & 0x000fffffffffffffll) |
+                                          ((long long)(1023 + (ex - 2 * h)) << 52));
+    double y = (double)rsqrtf((float)m);
+    const double hm = 0.5 * m;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y = y * fma(-hm, y * y, 1.5);
+    return y * exp2i(-h);
+}
+
+// sign bit of x (no FP64 compare: the FP64 pipe is the scarce unit)
+__device__ __forceinline__ bool neg_bit(double x) { return __double_as_longlong(x) < 0; }
+
 }  // namespace bse

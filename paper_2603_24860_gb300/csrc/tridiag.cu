@@ -262,9 +262,11 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
         __syncthreads();
         const double2 alpha = s_scal[1];
         for (int r = r0 + tid; r < n; r += kTriThreads) {
-            const double2 av = cmul(alpha, V[r]);
-            W[r].x += av.x;
-            W[r].y += av.y;
+            const double2 v = V[r];
+            double2 x = W[r];
+            x.x = fma(alpha.x, v.x, fma(-alpha.y, v.y, x.x));
+            x.y = fma(alpha.x, v.y, fma(alpha.y, v.x, x.y));
+            W[r] = x;
         }
         __syncthreads();
         // P2: rank-2 update of own columns j >= r0
@@ -283,10 +285,11 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
         double sg = 0.0;
         for (int r = k + tid; r < n; r += kTriThreads) {
             const double2 c = C[r], v = V[r], w = W[r];
-            const double2 t1 = cmulc(wk, v), t2 = cmulc(vk, w);
-            const double2 cr = make_double2(c.x - t1.x - t2.x, c.y - t1.y - t2.y);
+            double2 cr;   // c - v conj(w_k) - w conj(v_k)
+            cr.x = fma(-v.x, wk.x, fma(-v.y, wk.y, fma(-w.x, vk.x, fma(-w.y, vk.y, c.x))));
+            cr.y = fma(-v.y, wk.x, fma(v.x, wk.y, fma(-w.y, vk.x, fma(w.x, vk.y, c.y))));
             W[r] = cr;
-            if (r >= k + 2) sg += cr.x * cr.x + cr.y * cr.y;
+            if (r >= k + 2) sg = fma(cr.x, cr.x, fma(cr.y, cr.y, sg));
         }
         sg = warp_sum(sg);
         if (lane == 0) s_sig[wid] = sg;
@@ -302,11 +305,12 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
                 beta = al.x;
                 inv = make_double2(0.0, 0.0);
             } else {
-                beta = -copysign(sqrt(al.x * al.x + al.y * al.y + sigma), al.x);
-                const double rb = 1.0 / beta;
-                tau = make_double2((beta - al.x) * rb, -al.y * rb);
+                const double nrm2 = fma(al.x, al.x, fma(al.y, al.y, sigma));
+                const double y = copysign(rsqrt_nr(nrm2), al.x);   // -1/beta
+                beta = -nrm2 * y;
+                tau = make_double2(fma(al.x, y, 1.0), al.y * y);     // (beta - alpha) / beta
                 const double2 den = make_double2(al.x - beta, al.y);
-                const double rm = 1.0 / (den.x * den.x + den.y * den.y);
+                const double rm = rcp_nr(fma(den.x, den.x, den.y * den.y));
                 inv = make_double2(den.x * rm, -den.y * rm);
             }
             s_scal[0] = inv;
@@ -469,13 +473,13 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
 __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int i0, int i1,
                                            double x) {
     double pm = 1.0, p = __ldg(d + i0) - x;
-    if (p == 0.0) p = -0x1p-200;
-    bool sp = p < 0.0;
+    if ((__double_as_longlong(p) << 1) == 0) p = -0x1p-200;
+    bool sp = neg_bit(p);
     int c = sp;
     for (int i = i0 + 1; i < i1; ++i) {
         double pn = fma(__ldg(d + i) - x, p, -__ldg(e2 + i - 1) * pm);
-        if (pn == 0.0) pn = -p * 0x1p-200;   // the zero pivot becomes -tiny (ratio p_i / p_{i-1})
-        const bool sn = pn < 0.0;
+        if ((__double_as_longlong(pn) << 1) == 0) pn = -p * 0x1p-200;   // zero pivot -> -tiny (ratio p_i / p_{i-1})
+        const bool sn = neg_bit(pn);
         c += sn != sp;
         sp = sn;
         pm = p;
@@ -521,62 +525,92 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
     if (sub == 0 && t / kSect < n) lam[k] = 0.5 * (lo + hi);
 }
 
-// squared first component of the eigenvector of rows [0, m) for level k < m,
-// from the twisted factorisation T - lam = N_r Delta_r N_r^T at the twist index
-// r with the smallest |gamma_r|; zero for levels of rows [m, n).
-// dp: scratch [m][n] (level index fastest) for the top-down pivots.
-__global__ void twisted_weights_kernel(const double* __restrict__ d, const double* __restrict__ e, int64_t n,
-                                       const TriBounds* __restrict__ bnd, const double* __restrict__ lam, double* dp,
-                                       double* w) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+// Squared first component of the eigenvector of rows [0, m) for level k < m,
+// from the twisted factorisation T - lam = N_r Delta_r N_r^T at the twist
+// index r with the smallest |gamma_r| (gamma_r = D+_r + D-_r - (d_r - lam));
+// zero for levels of rows [m, n).  With z_r = 1, z_i = -L+_i z_{i+1} above r
+// and z_{i+1} = -U-_i z_i below it, so
+//   z_0^2 = prod_{i<r} L+_i^2,  sum_{i<r} z_i^2 = h_r,  sum_{i>r} z_i^2 = t_r
+// with h_{i+1} = L+_i^2 (1 + h_i) and t_i = U-_i^2 (1 + t_{i+1}).
+// A block of two warps takes 32 levels: warp 0 runs the top-down pass, warp
+// 1 the bottom-up pass at the same time (each FP64 instruction of a warp
+// costs the same whatever its active lanes, so the passes are split across
+// warps, not lanes); both then scan half of the twist indices.
+// st: scratch of 5 [m][n] arrays (level index fastest).
+__global__ void __launch_bounds__(64) twisted_weights_kernel(const double* __restrict__ d, const double* __restrict__ e,
+                                                             int64_t n, const TriBounds* __restrict__ bnd,
+                                                             const double* __restrict__ lam, double* st, double* w) {
+    __shared__ unsigned long long s_best[2][32];
+    __shared__ int s_r[2][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * 32 + lane;
     const TriBounds b = *bnd;
-    if (k >= b.m) {
-        w[k] = 0.0;
-        return;
-    }
     const int m = b.m;
+    const bool act = k0 < m;
+    const int64_t k = act ? k0 : 0;
     const double l = lam[k], piv = b.pivmin;
-    // top-down: T - l = L+ D+ L+^T
-    double p = __ldg(d) - l;
-    for (int i = 0; i + 1 < m; ++i) {
-        if (fabs(p) < piv) p = -piv;
-        dp[(size_t)i * n + k] = p;
-        const double ei = __ldg(e + i);
-        p = (__ldg(d + i + 1) - l) - ei * ei * rcp_nr(p);
-    }
-    if (fabs(p) < piv) p = -piv;
-    dp[(size_t)(m - 1) * n + k] = p;
-    // bottom-up: T - l = U- D- U-^T, twist element gamma_i = D+_i + D-_i - (d_i - l),
-    // t_i = sum_{j>i} z_j^2 / z_i^2
-    double q = __ldg(d + m - 1) - l, t = 0.0;
-    double gbest = fabs(p), tbest = 0.0;
-    int rbest = m - 1;
-#pragma unroll 4
-    for (int i = m - 2; i >= 0; --i) {
-        if (fabs(q) < piv) q = -piv;
-        const double ei = __ldg(e + i);
-        const double u = ei * rcp_nr(q);
-        const double di = __ldg(d + i) - l;
-        q = di - u * ei;
-        t = u * u * (1.0 + t);
-        const double g = fabs(dp[(size_t)i * n + k] + q - di);
-        if (g < gbest) {
-            gbest = g;
-            rbest = i;
-            tbest = t;
+    double* Dp = st;
+    double* Ph = st + (size_t)n * n;
+    double* Hh = st + 2 * (size_t)n * n;
+    double* Dm = st + 3 * (size_t)n * n;
+    double* Tt = st + 4 * (size_t)n * n;
+    if (act) {
+        if (wid == 0) {   // top-down: D+_i, and P_i, h_i before row i
+            double p = __ldg(d) - l, P = 1.0, h = 0.0;
+            for (int i = 0; i + 1 < m; ++i) {
+                if (fabs(p) < piv) p = -piv;
+                Dp[(size_t)i * n + k] = p;
+                Ph[(size_t)i * n + k] = P;
+                Hh[(size_t)i * n + k] = h;
+                const double L = __ldg(e + i) * rcp_nr(p);
+                const double L2 = L * L;
+                p = fma(-__ldg(e + i), L, __ldg(d + i + 1) - l);
+                P *= L2;
+                h = fma(L2, h, L2);
+            }
+            if (fabs(p) < piv) p = -piv;
+            Dp[(size_t)(m - 1) * n + k] = p;
+            Ph[(size_t)(m - 1) * n + k] = P;
+            Hh[(size_t)(m - 1) * n + k] = h;
+        } else {          // bottom-up: D-_i and t_i
+            double q = __ldg(d + m - 1) - l, t = 0.0;
+            Dm[(size_t)(m - 1) * n + k] = q;
+            Tt[(size_t)(m - 1) * n + k] = 0.0;
+            for (int i = m - 2; i >= 0; --i) {
+                if (fabs(q) < piv) q = -piv;
+                const double u = __ldg(e + i) * rcp_nr(q);
+                q = fma(-u, __ldg(e + i), __ldg(d + i) - l);
+                t = u * u * (1.0 + t);
+                Dm[(size_t)i * n + k] = q;
+                Tt[(size_t)i * n + k] = t;
+            }
         }
     }
-    // head: z_0^2 / z_r^2 and sum_{j<r} z_j^2 / z_r^2
-    double P = 1.0, h = 0.0;
-#pragma unroll 4
-    for (int i = 0; i < rbest; ++i) {
-        const double L = __ldg(e + i) * rcp_nr(dp[(size_t)i * n + k]);
-        const double L2 = L * L;
-        P *= L2;
-        h = L2 * (1.0 + h);
+    __syncthreads();
+    // twist index: smallest |gamma_i| over this warp's half (ties: lowest i)
+    unsigned long long best = ~0ull;
+    int rb = 0;
+    if (act) {
+        const int h0 = wid == 0 ? 0 : m / 2, h1 = wid == 0 ? m / 2 : m;
+        for (int i = h0; i < h1; ++i) {
+            const double g = Dp[(size_t)i * n + k] + Dm[(size_t)i * n + k] - (__ldg(d + i) - l);
+            const unsigned long long ga = (unsigned long long)__double_as_longlong(g) & 0x7fffffffffffffffull;
+            if (ga < best) {
+                best = ga;
+                rb = i;
+            }
+        }
     }
-    w[k] = P / (1.0 + h + tbest);   // P = 1 when r = 0 (z_0 = z_r)
+    s_best[wid][lane] = best;
+    s_r[wid][lane] = rb;
+    __syncthreads();
+    if (wid == 0 && act) {
+        const int r = s_best[1][lane] < s_best[0][lane] ? s_r[1][lane] : s_r[0][lane];
+        const double P = Ph[(size_t)r * n + k], h = Hh[(size_t)r * n + k], t = Tt[(size_t)r * n + k];
+        w[k] = P * rcp_nr(1.0 + h + t);
+    } else if (wid == 0 && k0 < n) {
+        w[k0] = 0.0;
+    }
 }
 
 // ascending order of all levels (ties by index): a permutation even where the
@@ -612,8 +646,8 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 }  // namespace
 
 size_t tridiag_scratch_bytes(int64_t n) {
-    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); dp n*n doubles; small items
-    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + n * n) + 8192;
+    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); twisted passes 5 n*n doubles
+    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) + 8192;
 }
 
 int tridiag_max_dim() { return 4736; }   // v, w and the next column of a step in 227 KB of shared memory
@@ -649,7 +683,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     double* beta0 = (double*)take(sizeof(double));
     TriBounds* bnd = (TriBounds*)take(sizeof(TriBounds));
     unsigned* bar = (unsigned*)take(sizeof(unsigned));
-    double* dp = (double*)take(sizeof(double) * n * n);
+    double* dp = (double*)take(sizeof(double) * 5 * n * n);
 
     int dev = 0, sms = 0, maxsm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
@@ -699,7 +733,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     bisect_kernel<<<(unsigned)((kSect * n + 31) / 32), 32, 0, st>>>(d, e2, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(d, e, n, bnd, lam, dp, w);
+    twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d, e, n, bnd, lam, dp, w);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     rank_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam, w, n, scale, omega_out, osc);
