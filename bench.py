@@ -40,6 +40,10 @@ HA_MEV = 27211.386245988
 # (profiles/), keyed by workload; None until a capture of the current kernel exists.
 DIRECT_TRAFFIC = {("si8", "fp64"): 41.711872e6 + 1210.309e6,    # profiles/direct_kernel_si8.md
                   ("si8", "fp32"): 13.125632e6 + 576.739072e6}
+# DRAM bytes per launch of the tridiagonal reduction kernel (profiles/), keyed by
+# (workload, block): the block is read once and the reduction then works from
+# shared memory.
+REDUCE_TRAFFIC = {("si8", "partner"): 10.499584e6 + 0.002048e6}    # profiles/tridiag_kernel_si8_partner.md
 WORKLOADS = {
     "si8": "Si-like diamond (Oh, a=10.26 bohr), Gamma-centred 8x8x8 mesh, Nv=4, Nc=6, |G|<=3.2 (2pi/a); "
            "T1u block of the full dim 12288",
@@ -308,14 +312,17 @@ def run_ours(args, rank, world, local):
         bse.bse_build_blocks(ctx, targets, pflags, prec if p is None else p, bse.BSE_TERM_ALL, Hs, dims)
         s1 = bse.bse_get_stats(ctx)
         eig = 0.0
+        red = 0.0
         solvers = []
         for m, pf, n, H, o, s, i in zip(targets, pflags, dims, Hs, oms, oscs, ims):
             (bse.bse_partner_spectrum if pf else bse.bse_block_spectrum)(ctx, m, H, n, omega, eta, o, s, i)
             st = bse.bse_get_stats(ctx)
             eig += st["ms_eig"]
+            red += st["ms_reduce"]
             solvers.append(st["solver"])
         s2 = bse.bse_get_stats(ctx)
         s2["ms_eig"] = eig
+        s2["ms_reduce"] = red
         s2["solvers"] = solvers
         if d2h is not None:
             for src, dst in zip([x for t in zip(oms, oscs, ims) for x in t], d2h):
@@ -396,6 +403,31 @@ def run_ours(args, rank, world, local):
     direct_launches = stats[0][0]["direct_launches"]
     achieved = flops_direct / (ms_direct * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if prec == bse.BSE_FP64 else FP32_PEAK_TFLOPS
+    ms_reduce = statistics.mean(s[1]["ms_reduce"] for s in stats)
+    roofs = [{"bound": "alu", "kernel": {bse.BSE_FP32: "direct_kernel<float>", bse.BSE_FP64: "direct_kernel<double>",
+                                         bse.BSE_BF16_SPLIT: "direct_tc_kernel"}[prec],
+              "ms_per_step": ms_direct,
+              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+              "peak_source": ("derived: 152 SMs x %s x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
+                              "CUDA-core figure)%s" % ("2 DFMA/clk" if prec == bse.BSE_FP64 else "128 FFMA/clk",
+                                                        "; the split kernel is bounded by its FP32 pair "
+                                                        "densities, its tensor share is reported separately"
+                                                        if prec == bse.BSE_BF16_SPLIT else "")),
+              "flops_per_launch": flops_direct / max(direct_launches, 1),
+              "launches_per_step": direct_launches,
+              "traffic": DIRECT_TRAFFIC.get((args.config, args.prec))}]
+    if ms_reduce > 0:
+        # LAPACK's count for a Hermitian tridiagonal reduction, (16/3) n^3 real flops per block
+        rflops = sum(16.0 / 3.0 * n ** 3 for n, s in zip(dims, stats[-1][1]["solvers"]) if s == bse.BSE_SOLVER_TRIDIAG)
+        ra = rflops / (ms_reduce * 1e-3) / 1e12
+        roofs.append({"bound": "alu", "kernel": "tridiag_kernel", "ms_per_step": ms_reduce, "achieved": ra,
+                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ra / FP64_PEAK_TFLOPS,
+                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
+                      "flops_per_launch": rflops / max(1, sum(1 for s in stats[-1][1]["solvers"]
+                                                              if s == bse.BSE_SOLVER_TRIDIAG)),
+                      "launches_per_step": sum(1 for s in stats[-1][1]["solvers"] if s == bse.BSE_SOLVER_TRIDIAG),
+                      "traffic": REDUCE_TRAFFIC.get((args.config, args.block))})
+    roof_main = max(roofs, key=lambda r: r["ms_per_step"])   # the kernel with the largest share of the step
     value = flops_build * args.steps * world / (total_ms * 1e-3) / 1e12
     out = {
         "metric": METRIC,
@@ -441,17 +473,8 @@ def run_ours(args, rank, world, local):
         "build_flops": flops_build,
         "work": {k: work[k] for k in ("rho", "contract", "project", "exchange", "overlap")},
         "build_tflops_kernels": flops_build / ((ms_direct + ms_project + ms_exchange) * 1e-3) / 1e12,
-        "roofline": {"bound": "alu", "kernel": {bse.BSE_FP32: "direct_kernel<float>", bse.BSE_FP64: "direct_kernel<double>",
-                                                bse.BSE_BF16_SPLIT: "direct_tc_kernel"}[prec],
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": ("derived: 152 SMs x %s x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
-                                     "CUDA-core figure)%s" % ("2 DFMA/clk" if prec == bse.BSE_FP64 else "128 FFMA/clk",
-                                                               "; the split kernel is bounded by its FP32 pair "
-                                                               "densities, its tensor share is reported separately"
-                                                               if prec == bse.BSE_BF16_SPLIT else "")),
-                     "flops_per_launch": flops_direct / max(direct_launches, 1),
-                     "launches_per_step": direct_launches,
-                     "traffic": DIRECT_TRAFFIC.get((args.config, args.prec))},
+        "roofline": roof_main,
+        "roofline_kernels": roofs,
         "fp64_build": cmp,
         "e2e": {"value": flops_build * args.steps * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

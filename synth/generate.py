@@ -76,6 +76,44 @@ CONFIGS = {
 }
 
 
+# Meshes of the mixed batch: MoS2-like hexagonal cells from 9x9x1 to 18x18x3 and
+# Si-like cells from 4^3 to 8^3.
+BATCH_MOS2_MESHES = [(9, 9, 1), (12, 12, 1), (9, 9, 3), (12, 12, 2), (15, 15, 1), (18, 18, 1), (18, 18, 2),
+                     (18, 18, 3)]
+BATCH_SI_MESHES = [(4, 4, 4), (5, 5, 5), (6, 6, 6), (7, 7, 7), (8, 8, 8)]
+
+
+def batch_configs(count: int = 32, seed: int = SEED_BASE + 5, n_si: int = 10) -> list:
+    """A seeded batch of independent instances: count - n_si MoS2-like D6h cells
+    (a = 5.97 bohr, c/a = 39/10) and n_si Si-like Oh cells, meshes from the
+    lists above, N_v and N_c drawn from {2..6} (Si valence from {2, 4}).  A
+    draw whose band counts would split a degenerate multiplet is replaced by
+    the next draw, so the list generates (each instance is generated once to
+    check; generate() caches it)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        si = i >= count - n_si
+        while True:
+            if si:
+                mesh = BATCH_SI_MESHES[int(rng.integers(len(BATCH_SI_MESHES)))]
+                nv, nc = int(rng.choice([2, 4])), int(rng.integers(2, 7))
+                cfg = Config("b%02d_si_%d%d%d_%d%d" % (i, *mesh, nv, nc), "Si", mesh, nv, nc, Fr(16, 5), 1.1, 12.0,
+                             seed + 1000 + i)
+            else:
+                mesh = BATCH_MOS2_MESHES[int(rng.integers(len(BATCH_MOS2_MESHES)))]
+                nv, nc = int(rng.integers(2, 7)), int(rng.integers(2, 7))
+                cfg = Config("b%02d_mos2_%d%d%d_%d%d" % (i, *mesh, nv, nc), "MoS2", mesh, nv, nc, Fr(93, 50), 1.9,
+                             15.0, seed + 1000 + i, eta_ev=0.05)
+            try:
+                generate(cfg)
+            except RuntimeError:
+                continue
+            out.append(cfg)
+            break
+    return out
+
+
 def crystal_of(cfg: Config) -> Crystal:
     if cfg.material == "Si":
         return si_diamond(cfg.a or 10.26)
@@ -126,7 +164,7 @@ def generate(cfg: Config | str) -> dict:
     return _generate(cfg)
 
 
-@lru_cache(maxsize=8)
+@lru_cache(maxsize=40)
 def _generate(cfg: Config) -> dict:
     rng = np.random.default_rng(cfg.seed)
     crys = crystal_of(cfg)
