@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 typedef struct bse_ctx bse_ctx;   /* opaque, library-owned; not thread-safe */
+typedef struct bse_batch bse_batch;   /* opaque: a batched build of several contexts */
 
 enum {
     BSE_OK = 0,
@@ -174,10 +175,19 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  * prec: BSE_FP64, BSE_FP32 or BSE_BF16_SPLIT (see the precision enum); the
  * split mode needs NG_max <= 64, nv <= 4 and nc <= 8 and returns
  * EUNSUPPORTED otherwise; FP16_SPLIT returns EUNSUPPORTED.  ETIMEOUT if a
- * bounded wait of the tensor-core kernel gave up (the context stays usable).  h_dev: device, complex128, column-major dim x dim with
- * leading dimension ld >= dim; the full Hermitian matrix is written.
- * Scratch is library-owned.
+ * bounded wait of the tensor-core kernel gave up (the context stays usable).
+ * h_dev: device, complex128, column-major dim x dim with leading dimension
+ * ld >= dim; the full Hermitian matrix is written.  irrep = BSE_IRREP_ALL
+ * writes the blocks of all irreps from one direct pass (as bse_build_blocks),
+ * packed one after another in irrep order: block mu is dim_mu x dim_mu,
+ * column-major with leading dimension dim_mu, at element offset
+ * sum_{nu < mu} dim_nu^2 (ld is ignored).  Scratch is library-owned.
  */
+enum { BSE_IRREP_ALL = -1 };
+
+/* bse_block_dim - dim_mu = Tr P_mu of an irrep (N for BSE_IRREP_ALL). */
+int bse_block_dim(const bse_ctx* ctx, int32_t irrep, int64_t* dim);
+
 int bse_build_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
                     void* h_dev, int64_t ld);
 
@@ -214,6 +224,38 @@ int bse_build_partner_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t 
  */
 int bse_build_blocks(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
                      uint32_t terms, void* const* h_dev, const int64_t* ld);
+
+/*
+ * Batched builds (no counterpart in the paper, which treats one crystal at a
+ * time): one block for each of n independent contexts on the same device
+ * and stream.  The direct terms of all contexts run in one launch of the
+ * direct kernel (every k-pair task carries the index of its context's
+ * system); the exchange and projections follow per context.  The sequence
+ * is captured once into a CUDA graph, so a build of the whole batch is one
+ * graph launch.
+ *
+ * bse_batch_create - plan the batch: target i is the block of irrep[i] of
+ *   ctxs[i] (partner == NULL or partner[i] == 0) or its partner block
+ *   (partner[i] != 0), written to h_dev[i] with leading dimension ld[i];
+ *   prec BSE_FP64 or BSE_FP32.  All arrays are host arrays of n entries,
+ *   borrowed for the call; the contexts and the output buffers must outlive
+ *   the batch.  Builds the bases, uploads the plan, allocates one X arena
+ *   for all contexts (the sum of their direct-term tiles) and captures the
+ *   graph; blocks until done.  Errors: as bse_build_blocks; EINVAL if the
+ *   contexts do not share one stream; EUNSUPPORTED for other precisions.
+ * bse_batch_run - launch the graph on the contexts' stream (asynchronous).
+ *   The result of target i equals that of bse_build_blocks on ctxs[i] alone.
+ * bse_batch_kernels - number of kernel launches one run performs.
+ * bse_batch_destroy - wait for the stream and free the batch (NULL allowed).
+ * bse_build_blocks_batched - create, run once, destroy.
+ */
+int bse_batch_create(bse_batch** out, bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
+                     int32_t prec, uint32_t terms, void* const* h_dev, const int64_t* ld);
+int bse_batch_run(bse_batch* batch);
+int bse_batch_kernels(const bse_batch* batch, int64_t* out);
+int bse_batch_destroy(bse_batch* batch);
+int bse_build_blocks_batched(bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
+                             int32_t prec, uint32_t terms, void* const* h_dev, const int64_t* ld);
 
 /*
  * bse_block_star_columns - column ranges of the k stars in the block of an
@@ -296,6 +338,18 @@ int bse_partner_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t
  * bse_stats.solver reports the solver the last spectrum used.
  */
 enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2 };
+
+/*
+ * bse_set_seeds - direct term by seeds (on, the default) or pair by pair.
+ * On: in each pair of k stars (a, b) the direct kernel computes only one k
+ * pair per symmetry orbit, (k0, k'_r) with k0 the representative of star a
+ * and k'_r the lowest k of each orbit of star b under the little group of
+ * k0; every other pair (k, k') = (s^-1 k0, s^-1 k'_r) follows by Eq. Wtrafo,
+ * K^d(k, k') = G(s,k)^dagger K^d(k0, k'_r) G(s,k'), with the two-particle
+ * band rotations G of Eq. Ttilde (sums over degenerate multiplets only).
+ * Off: every pair is computed.  Both give the same blocks to rounding.
+ */
+int bse_set_seeds(bse_ctx* ctx, int32_t on);
 int bse_set_solver(bse_ctx* ctx, int32_t solver);
 
 /* Wait for all work on the context's stream; returns ECUDA on a device error. */
@@ -306,7 +360,8 @@ int bse_sync(bse_ctx* ctx);
  *
  * bse_work: algorithmic work of one bse_build_block, in real flops with a
  * complex multiply-add counted as 8, over the unordered pairs of k stars the
- * build visits (a <= b, and k <= k' inside a star):
+ * build visits (a <= b, and k <= k' inside a star); rho and contract count
+ * the k pairs the direct kernel computes (the seeds when bse_set_seeds is on):
  *   rho      = 8 (Nc^2 + Nv^2) sum_pairs n_ovl(k,k'),  n_ovl = #{(p', Q):
  *              p' in S_k', Q in S_q, p' + Q in S_k}
  *   contract = 8 sum_pairs (Nv^2 NG(q)^2 + Nc^2 Nv^2 NG(q))
@@ -317,8 +372,11 @@ int bse_sync(bse_ctx* ctx);
 typedef struct {
     double rho, contract, project, exchange;
     int64_t k_pairs;       /* unordered k pairs of the direct term */
-    int64_t overlap;       /* sum over those pairs of n_ovl */
+    int64_t overlap;       /* sum over the computed pairs of n_ovl */
     int64_t tiles;         /* star-pair tiles */
+    int64_t seeds;         /* k pairs the direct kernel computes (all of them without seeds) */
+    int64_t rotated;       /* k pairs rotated from their seeds (Eq. Wtrafo) */
+    double rotate;         /* flops of the rotations: 16 B sum over both sides of the multiplet terms */
 } bse_work;
 
 int bse_build_work(bse_ctx* ctx, int32_t irrep, int32_t partner, bse_work* out);   /* partner: 0 block, 1 partner block */
@@ -347,6 +405,8 @@ typedef struct {
     float ms_create_wdiv;       /* ... head correction */
     float ms_basis;             /* wall time of the last basis construction (host, incl. upload) */
     int32_t solver;             /* eigensolver of the last spectrum: BSE_SOLVER_DENSE or BSE_SOLVER_TRIDIAG */
+    float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */
+    float ms_rotate;            /* rotated direct-term blocks of the last build (part of ms_direct) */
     int32_t reserved;
 } bse_stats;
 

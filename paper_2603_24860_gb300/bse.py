@@ -25,6 +25,7 @@ BSE_FP64, BSE_BF16_SPLIT, BSE_FP16_SPLIT, BSE_FP32 = 0, 1, 2, 3
 BSE_TERM_DIAG, BSE_TERM_EXCHANGE, BSE_TERM_DIRECT, BSE_TERM_ALL = 1, 2, 4, 7
 BSE_BANDS_CC, BSE_BANDS_VV, BSE_BANDS_CV = 0, 1, 2
 BSE_SOLVER_AUTO, BSE_SOLVER_DENSE, BSE_SOLVER_TRIDIAG = 0, 1, 2
+BSE_IRREP_ALL = -1
 
 _P32 = C.POINTER(C.c_int32)
 _P64 = C.POINTER(C.c_int64)
@@ -54,7 +55,8 @@ class BseTablesView(C.Structure):
 
 class BseWork(C.Structure):
     _fields_ = [("rho", C.c_double), ("contract", C.c_double), ("project", C.c_double),
-                ("exchange", C.c_double), ("k_pairs", C.c_int64), ("overlap", C.c_int64), ("tiles", C.c_int64)]
+                ("exchange", C.c_double), ("k_pairs", C.c_int64), ("overlap", C.c_int64), ("tiles", C.c_int64),
+                ("seeds", C.c_int64), ("rotated", C.c_int64), ("rotate", C.c_double)]
 
 
 class BseStats(C.Structure):
@@ -62,7 +64,8 @@ class BseStats(C.Structure):
                 ("ms_project", C.c_float), ("ms_exchange", C.c_float), ("ms_eig", C.c_float),
                 ("ms_spectrum", C.c_float), ("ms_create", C.c_float), ("ms_create_tables", C.c_float),
                 ("ms_create_upload", C.c_float), ("ms_create_gamma", C.c_float), ("ms_create_wdiv", C.c_float),
-                ("ms_basis", C.c_float), ("solver", C.c_int32), ("reserved", C.c_int32)]
+                ("ms_basis", C.c_float), ("solver", C.c_int32), ("ms_reduce", C.c_float),
+                ("ms_rotate", C.c_float), ("reserved", C.c_int32)]
 
 
 EXPORTS = {
@@ -87,6 +90,15 @@ EXPORTS = {
     "bse_head_correction_noalloc": (C.c_int, [_PD, _P32, _PD, C.c_void_p, C.c_void_p]),
     "bse_block_star_columns": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _P64]),
     "bse_set_solver": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_set_seeds": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_block_dim": (C.c_int, [C.c_void_p, C.c_int32, _P64]),
+    "bse_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32, _P32, _P32, C.c_int32,
+                                   C.c_uint32, C.POINTER(C.c_void_p), _P64]),
+    "bse_batch_run": (C.c_int, [C.c_void_p]),
+    "bse_batch_kernels": (C.c_int, [C.c_void_p, _P64]),
+    "bse_batch_destroy": (C.c_int, [C.c_void_p]),
+    "bse_build_blocks_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _P32, _P32, C.c_int32, C.c_uint32,
+                                           C.POINTER(C.c_void_p), _P64]),
     "bse_build_blocks_work": (C.c_int, [C.c_void_p, C.c_int32, _P32, _P32, C.POINTER(BseWork)]),
     "bse_build_blocks": (C.c_int, [C.c_void_p, C.c_int32, _P32, _P32, C.c_int32, C.c_uint32,
                                    C.POINTER(C.c_void_p), _P64]),
@@ -266,6 +278,57 @@ def bse_build_blocks(ctx: Context, irreps, partners, prec: int, terms: int, outs
     return outs
 
 
+class Batch:
+    """A planned batched build (bse_batch_create); keeps its contexts and
+    outputs referenced."""
+
+    def __init__(self, handle, ctxs, outs):
+        self.handle, self.ctxs, self.outs = handle, ctxs, outs
+
+
+def _batch_args(ctxs, irreps, partners, outs, lds):
+    n = len(ctxs)
+    hs = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    ir = np.ascontiguousarray(irreps, dtype=np.int32)
+    pa = None if partners is None else np.ascontiguousarray(partners, dtype=np.int32)
+    ptrs = (C.c_void_p * n)(*[_ptr(o) if o is not None else None for o in outs])
+    ld = np.ascontiguousarray(lds, dtype=np.int64)
+    return n, hs, ir, pa, ptrs, ld
+
+
+def bse_batch_create(ctxs, irreps, partners, prec: int, terms: int, outs, lds) -> Batch:
+    n, hs, ir, pa, ptrs, ld = _batch_args(ctxs, irreps, partners, outs, lds)
+    h = C.c_void_p()
+    _check(lib().bse_batch_create(C.byref(h), hs, n, ir.ctypes.data_as(_P32),
+                                  None if pa is None else pa.ctypes.data_as(_P32), prec, terms, ptrs,
+                                  ld.ctypes.data_as(_P64)))
+    return Batch(h, list(ctxs), list(outs))
+
+
+def bse_batch_run(batch: Batch):
+    _check(lib().bse_batch_run(batch.handle))
+
+
+def bse_batch_kernels(batch: Batch) -> int:
+    v = C.c_int64()
+    _check(lib().bse_batch_kernels(batch.handle, C.byref(v)))
+    return v.value
+
+
+def bse_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(lib().bse_batch_destroy(batch.handle))
+        batch.handle = None
+
+
+def bse_build_blocks_batched(ctxs, irreps, partners, prec: int, terms: int, outs, lds):
+    n, hs, ir, pa, ptrs, ld = _batch_args(ctxs, irreps, partners, outs, lds)
+    _check(lib().bse_build_blocks_batched(hs, n, ir.ctypes.data_as(_P32),
+                                          None if pa is None else pa.ctypes.data_as(_P32), prec, terms, ptrs,
+                                          ld.ctypes.data_as(_P64)))
+    return outs
+
+
 def bse_partner_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float, omega_out, osc, im_eps):
     _check(lib().bse_partner_spectrum(ctx.handle, irrep, _ptr(h), ld, _ptr(omega), omega.numel(), eta,
                                       _ptr(omega_out), _ptr(osc), _ptr(im_eps)))
@@ -316,6 +379,16 @@ def bse_build_blocks_work(ctx: Context, irreps, partners=None) -> dict:
     _check(lib().bse_build_blocks_work(ctx.handle, len(ir), ir.ctypes.data_as(_P32),
                                        None if pa is None else pa.ctypes.data_as(_P32), C.byref(w)))
     return {f: getattr(w, f) for f, _ in BseWork._fields_}
+
+
+def bse_block_dim(ctx: Context, irrep: int) -> int:
+    v = C.c_int64()
+    _check(lib().bse_block_dim(ctx.handle, irrep, C.byref(v)))
+    return v.value
+
+
+def bse_set_seeds(ctx: Context, on: bool):
+    _check(lib().bse_set_seeds(ctx.handle, 1 if on else 0))
 
 
 def bse_set_solver(ctx: Context, solver: int):

@@ -120,6 +120,11 @@ struct bse_ctx {
     DevBuf wemb;         // split-precision W(q) embeddings for the tensor-core build
     int wemb_ngp = 0;
     DevBuf groups, status;
+    DevBuf dinst;        // the context's system as a direct-kernel instance
+    // band rotations kept on the device for the rotated direct-term blocks (Eq. Wtrafo)
+    DevBuf gam, gam32, gkoff, gboff, mfirst, msize;
+    bool seeds = true;   // compute one k pair per symmetry orbit and rotate the rest
+    DevBuf rots;
     int32_t solver_mode = BSE_SOLVER_AUTO;
     DevBuf triScratch, triSmall;   // tridiagonal path: scratch; gram [9], weight sum, error flag
     // scratch (library-owned, grow-only)
@@ -127,7 +132,7 @@ struct bse_ctx {
     cusolverDnHandle_t solver = nullptr;
     // measurement
     bool timing = false;
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[10] = {};
     bse_stats stats{};
 };
 
@@ -138,7 +143,8 @@ namespace {
 // direct term on the product basis of a star pair) does not depend on the
 // target, so every target of a batch projects the same X tiles.
 struct Batch {
-    std::vector<PairTask> tasks;
+    std::vector<PairTask> tasks;          // k pairs the direct kernel computes (seeds when symmetry is used)
+    std::vector<RotTask> rots;            // k pairs rotated from their seed (Eq. Wtrafo)
     std::vector<TileTask> tiles;          // all targets' tiles, concatenated
     std::vector<int> tile_off;            // [targets + 1] range of each target in tiles
     size_t xbytes = 0;
@@ -151,8 +157,37 @@ size_t arena_budget() {
     return (size_t)(env ? std::atoll(env) : 2048) << 20;
 }
 
-void plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t budget, std::vector<Batch>& out) {
+// Seeds of a star-pair tile (a, b) (Eq. Wtrafo): every k pair (k, k') is
+// (s k0, s k'_r)-equivalent to a pair with k0 = star a's representative and
+// k'_r the representative (lowest k) of the orbit of k' under the little
+// group of k0.  rep[j], gop[j] for the members j of star b: that
+// representative and an operation of the little group taking k'_j to it.
+static void little_orbits(const Tables& t, int a, int b, std::vector<int>& rep, std::vector<int>& gop) {
+    const int k0 = t.stars[a][0];
+    const auto& sb = t.stars[b];
+    rep.assign(sb.size(), -1);
+    gop.assign(sb.size(), -1);
+    for (size_t j = 0; j < sb.size(); ++j) {
+        const int kp = sb[j];
+        for (int g = 0; g < t.nops; ++g) {
+            if (t.rotk[(size_t)g * t.nk + k0] != k0) continue;
+            const int x = t.rotk[(size_t)g * t.nk + kp];
+            if (rep[j] < 0 || x < rep[j]) {
+                rep[j] = x;
+                gop[j] = g;
+            }
+        }
+    }
+}
+
+int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t budget, std::vector<Batch>& out,
+                 bool seeds = false) {
     out.clear();
+    std::vector<int> inv(t.nops, -1);
+    for (int a = 0; a < t.nops; ++a)
+        for (int b = 0; b < t.nops; ++b)
+            if (t.mult[(size_t)a * t.nops + b] == t.identity) inv[a] = b;
+    std::vector<int> rep, gop;
     const size_t nt = bases.size();
     auto ncols = [&](size_t i, int a) { return bases[i]->star_col[a + 1] - bases[i]->star_col[a]; };
     std::vector<int> act;
@@ -220,8 +255,34 @@ void plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_
             }
             const auto& sa = t.stars[a];
             const auto& sb = t.stars[b];
+            if (seeds) little_orbits(t, a, b, rep, gop);
+            const int k0 = sa[0];
             for (size_t i = 0; i < sa.size(); ++i)
                 for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
+                    if (seeds) {
+                        const int k = sa[i], kp = sb[j];
+                        const int s1 = inv[t.s_k[k]];   // takes k to k0
+                        const int jpp = t.pos_in_star[t.rotk[(size_t)s1 * t.nk + kp]];
+                        const int r = rep[jpp];
+                        const int s = t.mult[(size_t)gop[jpp] * t.nops + s1];
+                        if (t.rotk[(size_t)s * t.nk + k] != k0 || t.rotk[(size_t)s * t.nk + kp] != r)
+                            return fail(BSE_ESYMM, "seed of the k pair (%d, %d) not found", k, kp);
+                        const int jr = t.pos_in_star[r];
+                        if (!(i == 0 && (int)j == jr)) {
+                            RotTask rt;
+                            rt.src = xoff + (int64_t)jr * B * rows;
+                            rt.dst = xoff + (int64_t)j * B * rows + (int64_t)i * B;
+                            rt.dstm = xoff + (int64_t)i * B * rows + (int64_t)j * B;
+                            rt.k = k;
+                            rt.kp = kp;
+                            rt.s = s;
+                            rt.ld = (int32_t)rows;
+                            rt.flags = (a == b && j > i) ? 1 : 0;
+                            rt.pad = 0;
+                            cur.rots.push_back(rt);
+                            continue;
+                        }
+                    }
                     PairTask p;
                     p.k = sa[i];
                     p.kp = sb[j];
@@ -235,6 +296,7 @@ void plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_
             cur.xbytes += xs;
         }
     if (!cur.tasks.empty()) flush();
+    return BSE_OK;
 }
 
 }  // namespace
@@ -342,6 +404,9 @@ static int ensure_narrow(bse_ctx* c) {
     BSE_TRY(ensure(c->w32, sizeof(float2) * (size_t)nw));
     BSE_TRY(launch_narrow(c->S.coef, (float2*)c->coef32.p, nc, c->stream));
     BSE_TRY(launch_narrow(c->S.w, (float2*)c->w32.p, nw, c->stream));
+    const int64_t ng = (int64_t)c->t.nops * c->t.gam_per_s;
+    BSE_TRY(ensure(c->gam32, sizeof(float2) * (size_t)std::max<int64_t>(ng, 1)));
+    BSE_TRY(launch_narrow((const double2*)c->gam.p, (float2*)c->gam32.p, ng, c->stream));
     c->narrow_ready = true;
     return BSE_OK;
 }
@@ -571,8 +636,24 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     release(perm);
     release(phase);
     release(dent);
-    release(dgam);
+    if (rc != BSE_OK) release(dgam);
     BSE_TRY(rc);
+    c->gam = dgam;   // kept for the rotated direct-term blocks
+    {
+        std::vector<int32_t> mf((size_t)nk * t.nb), ms((size_t)nk * t.nb);
+        for (int k = 0; k < nk; ++k)
+            for (auto* mm : {&t.vmult[k], &t.cmult[k]})
+                for (auto& m : *mm)
+                    for (int b = m.first; b < m.first + m.second; ++b) {
+                        mf[(size_t)k * t.nb + b] = m.first;
+                        ms[(size_t)k * t.nb + b] = m.second;
+                    }
+        BSE_TRY(upload(c->gkoff, t.gam_koff.data(), t.gam_koff.size(), st));
+        BSE_TRY(upload(c->gboff, t.gam_boff.data(), t.gam_boff.size(), st));
+        BSE_TRY(upload(c->mfirst, mf.data(), mf.size(), st));
+        BSE_TRY(upload(c->msize, ms.data(), ms.size(), st));
+        BSE_CUDA(cudaStreamSynchronize(st));
+    }
     BSE_TRY(check_band_rotations(t));
     const double t3 = now_ms();
     // block dimensions from the trace formula dim_mu = d_mu/|S| sum_s chi_mu(s) Tr Gamma~(s)
@@ -654,7 +735,8 @@ static void free_ctx(bse_ctx* c) {
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status,
-                      &c->triScratch, &c->triSmall})
+                      &c->triScratch, &c->triSmall, &c->dinst,
+                      &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -672,6 +754,31 @@ static void free_ctx(bse_ctx* c) {
         if (e) cudaEventDestroy(e);
     release(c->counter);
     delete c;
+}
+
+// the context's band rotations as a rotation-kernel system
+static RotSys rot_sys(bse_ctx* c, int p32) {
+    RotSys r;
+    r.gam = p32 ? c->gam32.p : c->gam.p;
+    r.koff = (const int64_t*)c->gkoff.p;
+    r.boff = (const int64_t*)c->gboff.p;
+    r.mfirst = (const int*)c->mfirst.p;
+    r.msize = (const int*)c->msize.p;
+    r.gps = c->t.gam_per_s;
+    r.nk = c->t.nk;
+    r.nb = c->t.nb;
+    r.nv = c->t.nv;
+    r.nc = c->t.nc;
+    return r;
+}
+
+// the direct kernel on the context's own tasks (its system as a kernel parameter)
+static int direct_single(bse_ctx* c, int p32, const PairTask* tasks, int64_t n, void* X) {
+    DirectInst di;
+    di.S = c->S;
+    di.coef = p32 ? c->coef32.p : (const void*)c->S.coef;
+    di.w = p32 ? c->w32.p : (const void*)c->S.w;
+    return launch_direct(di, p32, tasks, n, X, c->stream);
 }
 
 extern "C" {
@@ -772,8 +879,7 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
         }
     if (terms & BSE_TERM_DIRECT) {
         BSE_TRY(upload(c->tasks, tasks.data(), tasks.size(), c->stream));
-        BSE_TRY(launch_direct(c->S, 0, c->S.coef, c->S.w, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), h,
-                              c->stream));
+        BSE_TRY(direct_single(c, 0, (const PairTask*)c->tasks.p, (int64_t)tasks.size(), h));
     } else {
         BSE_CUDA(cudaMemset2DAsync(h, sizeof(double2) * ld, 0, sizeof(double2) * t.N, t.N, c->stream));
     }
@@ -838,9 +944,9 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
     }
     const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
     std::vector<Batch> batches;
-    plan_batches(t, bases, arena_budget(), batches);
+    BSE_TRY(plan_batches(t, bases, arena_budget(), batches, c->seeds && (terms & BSE_TERM_DIRECT)));
     if (c->timing) {
-        c->stats.ms_direct = c->stats.ms_project = 0.f;
+        c->stats.ms_direct = c->stats.ms_project = c->stats.ms_rotate = 0.f;
         c->stats.direct_launches = 0;
     }
     for (const Batch& bt : batches) {
@@ -886,11 +992,15 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
                                      (const TcGroup*)c->groups.p, (int64_t)groups.size(), c->arenaX.p,
                                      (int*)c->status.p, c->stream));
         } else if (terms & BSE_TERM_DIRECT) {
-            BSE_TRY(launch_direct(c->S, p32, p32 ? c->coef32.p : (const void*)c->S.coef,
-                                  p32 ? c->w32.p : (const void*)c->S.w, (const PairTask*)c->tasks.p,
-                                  (int64_t)bt.tasks.size(), c->arenaX.p, c->stream));
+            BSE_TRY(direct_single(c, p32, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(), c->arenaX.p));
         } else {
             BSE_CUDA(cudaMemsetAsync(c->arenaX.p, 0, bt.xbytes / sizeof(double2) * xel, c->stream));
+        }
+        if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[8], c->stream));
+        if ((terms & BSE_TERM_DIRECT) && !bt.rots.empty()) {   // the other pairs from their seeds (Eq. Wtrafo)
+            BSE_TRY(upload(c->rots, bt.rots.data(), bt.rots.size(), c->stream));
+            BSE_TRY(launch_rotate(rot_sys(c, p32), p32, (const RotTask*)c->rots.p, (int64_t)bt.rots.size(),
+                                  c->arenaX.p, c->stream));
         }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[1], c->stream));
         for (size_t i = 0; i < nt; ++i) {
@@ -908,9 +1018,11 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[2], c->stream));
             BSE_CUDA(cudaEventSynchronize(c->ev[2]));
-            float a = 0.f, b = 0.f;
+            float a = 0.f, b = 0.f, r = 0.f;
             BSE_CUDA(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
             BSE_CUDA(cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+            BSE_CUDA(cudaEventElapsedTime(&r, c->ev[8], c->ev[1]));
+            c->stats.ms_rotate += r;
             c->stats.ms_direct += a;
             c->stats.ms_project += b;
             c->stats.direct_launches += 1;
@@ -937,6 +1049,21 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
     if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
+    if (mu == BSE_IRREP_ALL) {   // every block, packed one after another in irrep order
+        std::vector<IrrepDev*> tg;
+        std::vector<void*> hs;
+        std::vector<int64_t> lds;
+        size_t off = 0;
+        for (int m = 0; m < c->t.n_irreps; ++m) {
+            BSE_TRY(ensure_basis(c, m));
+            const int64_t d = c->irr[m].host.dim;
+            tg.push_back(&c->irr[m]);
+            hs.push_back(d > 0 ? (void*)((double2*)h + off) : nullptr);
+            lds.push_back(std::max<int64_t>(d, 1));
+            off += (size_t)d * d;
+        }
+        return build_multi(c, tg, prec, terms, hs.data(), lds.data());
+    }
     BSE_TRY(ensure_basis(c, mu));
     return build_generic(c, c->irr[mu], prec, terms, h, ld);
 }
@@ -972,6 +1099,307 @@ int bse_build_blocks(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t*
     }
     if (n == 0) return BSE_OK;
     return build_multi(c, tg, prec, terms, h, ld);
+}
+
+// ---------------------------------------------------------------------------
+// batched build: one block per context, the direct terms of all contexts in
+// one launch, the projections per context, captured once as a CUDA graph
+// ---------------------------------------------------------------------------
+struct bse_batch {
+    std::vector<bse_ctx*> ctx;
+    std::vector<IrrepDev*> tg;
+    std::vector<void*> h;
+    std::vector<int64_t> ld;
+    cudaStream_t stream = nullptr;
+    DevBuf insts, tasks, tiles, arenaX, pmu, rsys, rots;
+    int64_t nrots = 0;
+    int bmax = 0;
+    static constexpr int kBranches = 4;   // concurrent projection branches of the graph
+    DevBuf arenaY[kBranches];
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;          // kernel nodes in the graph
+};
+
+static void free_batch(bse_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (DevBuf* d : {&b->insts, &b->tasks, &b->tiles, &b->arenaX, &b->pmu, &b->rsys, &b->rots}) release(*d);
+    for (auto& y : b->arenaY) release(y);
+    delete b;
+}
+
+// a group of instances whose direct-term tasks share one launch (and its
+// dynamic shared memory, the maximum of the group)
+struct DirectClass {
+    int64_t first = 0, count = 0;
+    DevSys smax{};
+};
+
+// the launches of one batched build, captured into the graph on stream st:
+// the direct term per shared-memory class, then the exchange and the
+// projections of the instances on kBranches concurrent branches (fork/join
+// through events), each branch with its own Y arena
+static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaEvent_t* ev, int p32, uint32_t terms,
+                          const std::vector<Batch>& plans, const std::vector<int64_t>& pmu_off,
+                          const std::vector<int>& tile_off, const std::vector<DirectClass>& classes,
+                          const std::vector<int>& order) {
+    const int nb = bse_batch::kBranches;
+    if (terms & BSE_TERM_DIRECT) {
+        for (const DirectClass& dc : classes)
+            BSE_TRY(launch_direct_multi((const DirectInst*)b->insts.p, dc.smax, p32,
+                                        (const PairTask*)b->tasks.p + dc.first, dc.count, b->arenaX.p, st));
+        if (b->nrots > 0)   // pairs rotated from their seeds (Eq. Wtrafo)
+            BSE_TRY(launch_rotate_multi((const RotSys*)b->rsys.p, b->bmax, p32, (const RotTask*)b->rots.p, b->nrots,
+                                        b->arenaX.p, st));
+    } else {
+        BSE_CUDA(cudaMemsetAsync(b->arenaX.p, 0, b->arenaX.n, st));
+    }
+    BSE_CUDA(cudaEventRecord(ev[0], st));
+    for (int j = 0; j < nb; ++j) BSE_CUDA(cudaStreamWaitEvent(br[j], ev[0], 0));
+    for (size_t q = 0; q < order.size(); ++q) {
+        const int i = order[q];
+        const int j = (int)(q % nb);
+        bse_ctx* c = b->ctx[i];
+        if (b->tg[i]->host.dim == 0) continue;
+        DevBasis db = dev_basis_of(c, *b->tg[i]);
+        if (terms & BSE_TERM_EXCHANGE)
+            BSE_TRY(launch_exchange_project(db, (const double2*)c->P.p, c->ng0, (double2*)b->pmu.p + pmu_off[i], br[j]));
+        const Batch& bt = plans[i];
+        const int nt = (int)bt.tiles.size();
+        if (nt == 0) continue;
+        const TileTask* tl = (const TileTask*)b->tiles.p + tile_off[i];   // xoff already global in the arena
+        BSE_TRY(launch_project_right(db, tl, nt, p32, b->arenaX.p, (double2*)b->arenaY[j].p, bt.max_rows[0],
+                                     bt.max_cb[0], br[j]));
+        BSE_TRY(launch_project_left(db, tl, nt, (const double2*)b->arenaY[j].p,
+                                    (terms & BSE_TERM_EXCHANGE) ? (const double2*)b->pmu.p + pmu_off[i] : nullptr,
+                                    (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
+                                    (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
+                                    (double2*)b->h[i], b->ld[i], bt.max_ca[0], bt.max_cb[0], br[j]));
+    }
+    for (int j = 0; j < nb; ++j) {
+        BSE_CUDA(cudaEventRecord(ev[1 + j], br[j]));
+        BSE_CUDA(cudaStreamWaitEvent(st, ev[1 + j], 0));
+    }
+    return BSE_OK;
+}
+
+static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
+                             uint32_t terms, void* const* h, const int64_t* ld) {
+    const int p32 = prec == BSE_FP32;
+    for (int32_t i = 0; i < n; ++i) {
+        bse_ctx* c = b->ctx[i];
+        if (partner && partner[i]) {
+            BSE_TRY(ensure_partner(c, irrep[i]));
+            b->tg.push_back(&c->partner[irrep[i]].part[0]);
+        } else {
+            BSE_TRY(ensure_basis(c, irrep[i]));
+            b->tg.push_back(&c->irr[irrep[i]]);
+        }
+        if (ld[i] < b->tg[i]->host.dim) return fail(BSE_EINVAL, "instance %d: ld < block dimension", i);
+        if (b->tg[i]->host.dim > 0 && !h[i]) return fail(BSE_EINVAL, "instance %d: null output", i);
+        if (terms & BSE_TERM_EXCHANGE) BSE_TRY(ensure_exchange_vectors(c));
+        if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
+        b->h.push_back(h[i]);
+        b->ld.push_back(ld[i]);
+    }
+    // one plan (one arena batch) per instance; tasks and tiles concatenated
+    std::vector<Batch> plans(n);
+    std::vector<int64_t> xbase(n + 1, 0), pmu_off(n + 1, 0);
+    std::vector<int> tile_off(n + 1, 0);
+    std::vector<PairTask> tasks;
+    std::vector<TileTask> tiles;
+    std::vector<DirectInst> insts(n);
+    std::vector<RotSys> rsys(n);
+    std::vector<RotTask> rots;
+    std::vector<size_t> ysz(n, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        bse_ctx* c = b->ctx[i];
+        std::vector<Batch> bb;
+        BSE_TRY(plan_batches(c->t, std::vector<const Basis*>{&b->tg[i]->host}, (size_t)1 << 62, bb,
+                             c->seeds && (terms & BSE_TERM_DIRECT)));
+        if (bb.size() > 1) return fail(BSE_EUNSUPPORTED, "instance %d: tiles do not fit one arena", i);
+        if (!bb.empty()) plans[i] = std::move(bb[0]);
+        else {
+            plans[i].max_rows.assign(1, 0);
+            plans[i].max_ca.assign(1, 0);
+            plans[i].max_cb.assign(1, 0);
+            plans[i].ybytes.assign(1, 0);
+        }
+        const int64_t xel_count = (int64_t)(plans[i].xbytes / sizeof(double2));
+        xbase[i + 1] = xbase[i] + xel_count;
+        tile_off[i] = (int)tiles.size();
+        for (TileTask t : plans[i].tiles) {
+            t.xoff += xbase[i];
+            tiles.push_back(t);
+        }
+        tile_off[i + 1] = (int)tiles.size();
+        ysz[i] = plans[i].ybytes.empty() ? (size_t)0 : plans[i].ybytes[0];
+        pmu_off[i + 1] = pmu_off[i] + b->tg[i]->host.dim * c->ng0;
+        insts[i].S = c->S;
+        insts[i].coef = p32 ? c->coef32.p : (const void*)c->S.coef;
+        insts[i].w = p32 ? c->w32.p : (const void*)c->S.w;
+        rsys[i] = rot_sys(c, p32);
+        b->bmax = std::max(b->bmax, c->t.nv * c->t.nc);
+        for (RotTask r : plans[i].rots) {
+            r.src += xbase[i];
+            r.dst += xbase[i];
+            r.dstm += xbase[i];
+            r.flags |= i << 1;
+            rots.push_back(r);
+        }
+    }
+    b->nrots = (int64_t)rots.size();
+    // direct-term tasks grouped by shared-memory class (rounded to 8 KB), so a
+    // small system does not run at the occupancy of the largest one
+    std::vector<int> byclass(n);
+    for (int32_t i = 0; i < n; ++i) byclass[i] = i;
+    auto cls = [&](int i) { return (direct_smem(b->ctx[i]->S, p32) + 8191) / 8192; };
+    std::stable_sort(byclass.begin(), byclass.end(), [&](int x, int y) { return cls(x) < cls(y); });
+    std::vector<DirectClass> classes;
+    for (int q = 0; q < n; ++q) {
+        const int i = byclass[q];
+        if (classes.empty() || cls(byclass[q - 1]) != cls(i)) {
+            DirectClass dc;
+            dc.first = (int64_t)tasks.size();
+            dc.smax = b->ctx[i]->S;
+            classes.push_back(dc);
+        }
+        DirectClass& dc = classes.back();
+        const DevSys& s = b->ctx[i]->S;
+        dc.smax.nb = std::max(dc.smax.nb, s.nb);
+        dc.smax.nv = std::max(dc.smax.nv, s.nv);
+        dc.smax.nc = std::max(dc.smax.nc, s.nc);
+        dc.smax.npw_max = std::max(dc.smax.npw_max, s.npw_max);
+        dc.smax.ng_max = std::max(dc.smax.ng_max, s.ng_max);
+        for (PairTask t : plans[i].tasks) {
+            t.xoff += xbase[i];
+            t.flags |= i << 1;
+            tasks.push_back(t);
+        }
+        dc.count = (int64_t)tasks.size() - dc.first;
+    }
+    // projection order: largest first, dealt round-robin to the branches
+    std::vector<int> order(n);
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ysz[x] > ysz[y]; });
+    size_t ybr[bse_batch::kBranches] = {0, 0, 0, 0};
+    for (size_t q = 0; q < order.size(); ++q)
+        ybr[q % bse_batch::kBranches] = std::max(ybr[q % bse_batch::kBranches], ysz[order[q]]);
+    const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
+    BSE_TRY(upload(b->insts, insts.data(), insts.size(), b->stream));
+    BSE_TRY(upload(b->tasks, tasks.data(), tasks.size(), b->stream));
+    BSE_TRY(upload(b->tiles, tiles.data(), tiles.size(), b->stream));
+    BSE_TRY(upload(b->rsys, rsys.data(), rsys.size(), b->stream));
+    BSE_TRY(upload(b->rots, rots.data(), rots.size(), b->stream));
+    BSE_TRY(ensure(b->arenaX, (size_t)xbase[n] * xel));
+    for (int j = 0; j < bse_batch::kBranches; ++j) BSE_TRY(ensure(b->arenaY[j], ybr[j]));
+    BSE_TRY(ensure(b->pmu, sizeof(double2) * (size_t)std::max<int64_t>(pmu_off[n], 1)));
+    BSE_CUDA(cudaStreamSynchronize(b->stream));
+    // capture on a stream of our own (the context's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the context's
+    const int64_t l0 = launches_total();
+    cudaStream_t cs = nullptr, br[bse_batch::kBranches] = {};
+    cudaEvent_t ev[1 + bse_batch::kBranches] = {};
+    auto cleanup = [&]() {
+        for (auto& s : br)
+            if (s) cudaStreamDestroy(s);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    cudaError_t be = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (auto& s : br)
+        if (be == cudaSuccess) be = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (auto& e : ev)
+        if (be == cudaSuccess) be = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (be == cudaSuccess) be = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+        cleanup();
+        return fail(BSE_ECUDA, "graph capture: %s", cudaGetErrorString(be));
+    }
+    const int rc = batch_launches(b, cs, br, ev, p32, terms, plans, pmu_off, tile_off, classes, order);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cleanup();
+    if (rc != BSE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(BSE_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    b->graph = g;
+    b->kernels = launches_total() - l0;
+    BSE_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return BSE_OK;
+}
+
+int bse_batch_create(bse_batch** out, bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
+                     int32_t prec, uint32_t terms, void* const* h, const int64_t* ld) {
+    clear_error();
+    if (!out || !ctxs || n < 1 || !irrep || !h || !ld) return fail(BSE_EINVAL, "null argument");
+    *out = nullptr;
+    if (prec != BSE_FP64 && prec != BSE_FP32)
+        return fail(BSE_EUNSUPPORTED, "batched builds take BSE_FP64 or BSE_FP32 (got %d)", prec);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(BSE_EINVAL, "null context %d", i);
+        if (ctxs[i]->stream != ctxs[0]->stream) return fail(BSE_EINVAL, "contexts of a batch share one stream");
+    }
+    bse_batch* b = new (std::nothrow) bse_batch();
+    if (!b) return fail(BSE_ENOMEM, "out of host memory");
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = ctxs[0]->stream;
+    AllocStream alloc_on_(b->stream);
+    const int rc = batch_create_impl(b, n, irrep, partner, prec, terms, h, ld);
+    if (rc != BSE_OK) {
+        cudaStreamSynchronize(b->stream);
+        free_batch(b);
+        return rc;
+    }
+    *out = b;
+    return BSE_OK;
+}
+
+int bse_batch_run(bse_batch* b) {
+    clear_error();
+    if (!b) return fail(BSE_EINVAL, "null batch");
+    BSE_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    for (int64_t i = 0; i < b->kernels; ++i) note_launch();
+    return BSE_OK;
+}
+
+int bse_batch_kernels(const bse_batch* b, int64_t* out) {
+    clear_error();
+    if (!b || !out) return fail(BSE_EINVAL, "null argument");
+    *out = b->kernels;
+    return BSE_OK;
+}
+
+int bse_batch_destroy(bse_batch* b) {
+    if (!b) return BSE_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return BSE_OK;
+}
+
+int bse_build_blocks_batched(bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
+                             int32_t prec, uint32_t terms, void* const* h, const int64_t* ld) {
+    bse_batch* b = nullptr;
+    BSE_TRY(bse_batch_create(&b, ctxs, n, irrep, partner, prec, terms, h, ld));
+    const int rc = bse_batch_run(b);
+    bse_batch_destroy(b);
+    return rc;
+}
+
+int bse_block_dim(const bse_ctx* c, int32_t mu, int64_t* dim) {
+    clear_error();
+    if (!c || !dim) return fail(BSE_EINVAL, "null argument");
+    if (mu == BSE_IRREP_ALL) {
+        *dim = c->t.N;
+        return BSE_OK;
+    }
+    if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
+    *dim = c->block_dim[mu];
+    return BSE_OK;
 }
 
 int bse_block_star_columns(bse_ctx* c, int32_t mu, int32_t partner, int64_t* out) {
@@ -1046,7 +1474,8 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     BSE_TRY(ensure(c->triScratch, tridiag_scratch_bytes(dim)));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
     BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
-                                    c->triScratch.p, omega_out, osc, wsum, err, c->stream));
+                                    c->triScratch.p, omega_out, osc, wsum, err, c->stream,
+                                    c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     struct {
         double s;
@@ -1092,6 +1521,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
                 BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
                 BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
             }
+            if (c->timing) BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_reduce, c->ev[6], c->ev[7]));
             c->stats.solver = BSE_SOLVER_TRIDIAG;
             return BSE_OK;
         }
@@ -1132,6 +1562,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
         BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_spectrum, c->ev[4], c->ev[5]));
     }
     c->stats.solver = BSE_SOLVER_DENSE;
+    c->stats.ms_reduce = 0.f;
     return BSE_OK;
 }
 
@@ -1165,6 +1596,13 @@ int bse_set_solver(bse_ctx* c, int32_t solver) {
     if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG)
         return fail(BSE_EINVAL, "unknown solver %d", solver);
     c->solver_mode = solver;
+    return BSE_OK;
+}
+
+int bse_set_seeds(bse_ctx* c, int32_t on) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null argument");
+    c->seeds = on != 0;
     return BSE_OK;
 }
 
@@ -1207,13 +1645,13 @@ int bse_build_blocks_work(bse_ctx* c, int32_t n, const int32_t* irrep, const int
     for (const Basis* bh : bases) total += bh->dim;
     if (total == 0) return BSE_OK;
     std::vector<Batch> batches;
-    plan_batches(t, bases, arena_budget(), batches);
+    BSE_TRY(plan_batches(t, bases, arena_budget(), batches, c->seeds));
     auto n_o = [&](const Basis& bh, int64_t j) -> double {
         int o = bh.col_orbit[j];
         return (double)(t.orbit_off[o + 1] - t.orbit_off[o]);
     };
     const double nv = t.nv, nc = t.nc;
-    double sum_ng = 0, sum_ng2 = 0, proj = 0, exch_tiles = 0;
+    double sum_ng = 0, sum_ng2 = 0, proj = 0, exch_tiles = 0, rot_flops = 0;
     BSE_TRY(ensure(c->counter, sizeof(unsigned long long)));
     BSE_CUDA(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned long long), c->stream));
     for (const Batch& bt : batches) {
@@ -1235,8 +1673,20 @@ int bse_build_blocks_work(bse_ctx* c, int32_t n, const int32_t* irrep, const int
                 proj += tt.rows * sb + sa * mb;
                 exch_tiles += ma * mb;
             }
-        out->k_pairs += (int64_t)bt.tasks.size();
+        out->k_pairs += (int64_t)(bt.tasks.size() + bt.rots.size());
+        out->seeds += (int64_t)bt.tasks.size();
+        out->rotated += (int64_t)bt.rots.size();
         out->tiles += (int64_t)bt.tiles.size();
+        // rotation: per output element the multiplet terms of both sides, two complex products each
+        for (const RotTask& r : bt.rots) {
+            double right = 0, left = 0;
+            for (int v = 0; v < t.nv; ++v)
+                for (int cc = 0; cc < t.nc; ++cc) {
+                    right += (double)t.band_mult_size(r.kp, v) * t.band_mult_size(r.kp, t.nv + cc);
+                    left += (double)t.band_mult_size(r.k, v) * t.band_mult_size(r.k, t.nv + cc);
+                }
+            rot_flops += 2.0 * 8.0 * t.B * (right + left);
+        }
         BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
         BSE_TRY(launch_count_overlap(c->S, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(),
                                      (unsigned long long*)c->counter.p, c->stream));
@@ -1252,6 +1702,7 @@ int bse_build_blocks_work(bse_ctx* c, int32_t n, const int32_t* irrep, const int
     out->contract = 8.0 * (nv * nv * sum_ng2 + nc * nc * nv * nv * sum_ng);
     out->project = 8.0 * proj;
     out->exchange = 8.0 * (pmu + exch_tiles) * c->ng0;
+    out->rotate = rot_flops;
     return BSE_OK;
 }
 

@@ -62,13 +62,26 @@ __host__ __device__ inline DirectPlan direct_plan(int cplx_bytes, int nb, int nv
 
 constexpr int kMaxSlots = 4;   // band pairs per lane: nc^2 + nv^2 <= 128
 
-template <typename R>
-__global__ void __launch_bounds__(256) direct_kernel(DevSys S, const typename C2<R>::T* __restrict__ coef,
-                                                     const typename C2<R>::T* __restrict__ wq,
+// kBatch: the task's system comes from insts[flags >> 1] (copied into shared
+// memory); otherwise every task uses the kernel parameter `one`.
+template <typename R, bool kBatch>
+__global__ void __launch_bounds__(256) direct_kernel(const DirectInst* __restrict__ insts,
+                                                     const __grid_constant__ DirectInst one,
                                                      const PairTask* __restrict__ tasks, typename C2<R>::T* X) {
     using V = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DirectInst sI;
     const PairTask t = tasks[blockIdx.x];
+    if (kBatch) {   // the task's system, copied cooperatively (one round trip)
+        const unsigned long long* src = (const unsigned long long*)(insts + (t.flags >> 1));
+        unsigned long long* dst = (unsigned long long*)&sI;
+        for (int i = threadIdx.x; i < (int)(sizeof(DirectInst) / 8); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const DirectInst& I = kBatch ? sI : one;
+    const DevSys& S = I.S;
+    const V* __restrict__ coef = (const V*)I.coef;
+    const V* __restrict__ wq = (const V*)I.w;
     const int nv = S.nv, nc = S.nc, nb = S.nb, B = nv * nc, P = nc * nc + nv * nv;
     const DirectPlan pl = direct_plan((int)sizeof(V), nb, nv, nc, S.npw_max, S.ng_max);
     V* ckT = (V*)smem;                                      // [npw][nb] at k
@@ -197,21 +210,23 @@ __global__ void __launch_bounds__(256) direct_kernel(DevSys S, const typename C2
     }
 }
 
-template <typename R>
-static int launch_direct_t(const DevSys& s, const void* coef, const void* w, const PairTask* tasks, int64_t ntasks,
-                           void* X, cudaStream_t st) {
+template <typename R, bool kBatch>
+static int launch_direct_t(const DirectInst* insts, const DirectInst& one, const DevSys& s, const PairTask* tasks,
+                           int64_t ntasks, void* X, cudaStream_t st) {
     using V = typename C2<R>::T;
     if (ntasks == 0) return BSE_OK;
     if (s.nc * s.nc + s.nv * s.nv > 32 * kMaxSlots)
         return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", 32 * kMaxSlots);
     if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
     DirectPlan pl = direct_plan((int)sizeof(V), s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
-    if (pl.total > 227 * 1024) return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", pl.total);
-    cudaError_t e = cudaFuncSetAttribute(direct_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.total);
+    if (pl.total + sizeof(DirectInst) > 227 * 1024)
+        return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", pl.total);
+    cudaError_t e = cudaFuncSetAttribute(direct_kernel<R, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pl.total);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", pl.total, cudaGetErrorString(e));
     for (int64_t off = 0; off < ntasks; off += 1 << 30) {
         int64_t nt = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
-        direct_kernel<R><<<(unsigned)nt, 256, pl.total, st>>>(s, (const V*)coef, (const V*)w, tasks + off, (V*)X);
+        direct_kernel<R, kBatch><<<(unsigned)nt, 256, pl.total, st>>>(insts, one, tasks + off, (V*)X);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "direct launch: %s", cudaGetErrorString(e));
@@ -219,10 +234,20 @@ static int launch_direct_t(const DevSys& s, const void* coef, const void* w, con
     return BSE_OK;
 }
 
-int launch_direct(const DevSys& s, int prec32, const void* coef, const void* w, const PairTask* tasks, int64_t ntasks,
-                  void* X, cudaStream_t st) {
-    return prec32 ? launch_direct_t<float>(s, coef, w, tasks, ntasks, X, st)
-                  : launch_direct_t<double>(s, coef, w, tasks, ntasks, X, st);
+int launch_direct_multi(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks, int64_t ntasks,
+                        void* X, cudaStream_t st) {
+    DirectInst none{};
+    return prec32 ? launch_direct_t<float, true>(insts, none, smax, tasks, ntasks, X, st)
+                  : launch_direct_t<double, true>(insts, none, smax, tasks, ntasks, X, st);
+}
+
+int launch_direct(const DirectInst& one, int prec32, const PairTask* tasks, int64_t ntasks, void* X, cudaStream_t st) {
+    return prec32 ? launch_direct_t<float, false>(nullptr, one, one.S, tasks, ntasks, X, st)
+                  : launch_direct_t<double, false>(nullptr, one, one.S, tasks, ntasks, X, st);
+}
+
+size_t direct_smem(const DevSys& s, int prec32) {
+    return direct_plan(prec32 ? 8 : 16, s.nb, s.nv, s.nc, s.npw_max, s.ng_max).total;
 }
 
 // FP32 copies of the coefficients and of W (made once per context)

@@ -59,6 +59,12 @@ struct Tables {
     // multiplets at each k: (first band, size) for occupied and unoccupied
     std::vector<std::vector<std::pair<int, int>>> vmult, cmult;
     std::vector<int32_t> band_mult;   // [nk*nb] multiplet id of each band (per k)
+    int band_mult_size(int k, int band) const {   // size of the band's multiplet at k
+        for (auto* ms : {&vmult[k], &cmult[k]})
+            for (auto& m : *ms)
+                if (band >= m.first && band < m.first + m.second) return m.second;
+        return 1;
+    }
     // orbits of the product basis
     std::vector<int64_t> orbit_off;     // [n_orbits+1] into orbit_members
     std::vector<int64_t> orbit_members; // product indices, ascending per orbit
@@ -120,7 +126,14 @@ struct PairTask {
     int32_t row0, col0;     // block origin inside the tile
     int64_t xoff;           // tile origin in the arena (elements)
     int32_t ld;             // tile leading dimension (column-major)
-    int32_t flags;          // 1: also write the mirrored (conjugate) block
+    int32_t flags;          // bit 0: also write the mirrored (conjugate) block; bits 1..: instance index
+};
+
+// one system of a direct-kernel launch (several in a batched launch)
+struct __align__(16) DirectInst {
+    DevSys S;
+    const void* coef;       // coefficients in the launch precision (FP64 or FP32 complex)
+    const void* w;          // W(q) in the launch precision
 };
 
 // a group of k pairs with the same q = k - k' (tensor-core direct term)
@@ -157,8 +170,39 @@ int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, co
 int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands,
                     int exchange_layout, double2* out, cudaStream_t st);
 // direct term (direct.cu): prec32 = 0 -> FP64 (coef/w double2, X double2), 1 -> FP32 (float2)
-int launch_direct(const DevSys& s, int prec32, const void* coef, const void* w, const PairTask* tasks,
-                  int64_t ntasks, void* X, cudaStream_t st);
+// direct term of the tasks of one or more systems: insts (device) holds the
+// systems, task.flags >> 1 indexes them; smax: any system's (nb, nv, nc,
+// npw_max, ng_max) maxima, for the shared-memory size
+int launch_direct_multi(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks, int64_t ntasks,
+                        void* X, cudaStream_t st);
+// one system, passed as a kernel parameter
+int launch_direct(const DirectInst& one, int prec32, const PairTask* tasks, int64_t ntasks, void* X, cudaStream_t st);
+
+// rotated direct-term blocks (rotate.cu, Eq. Wtrafo)
+struct RotSys {
+    const void* gam;        // Gamma(s) multiplet blocks [nops][gps] in the launch precision
+    const int64_t* koff;    // [nk+1] offset of k's blocks within one operation
+    const int64_t* boff;    // [nk*nb] offset of a band's multiplet block from koff[k]
+    const int* mfirst;      // [nk*nb] first band of the band's multiplet at k
+    const int* msize;       // [nk*nb] size of that multiplet
+    int64_t gps;            // entries per operation
+    int nk, nb, nv, nc;
+};
+struct RotTask {
+    int64_t src;            // seed block origin in the arena (elements)
+    int64_t dst;            // target block origin
+    int64_t dstm;           // origin of its mirror (conjugate transpose), if flags & 1
+    int32_t k, kp;          // target pair
+    int32_t s;              // operation with s k = seed k, s k' = seed k'
+    int32_t ld;             // tile leading dimension
+    int32_t flags;          // bit 0: write the mirror; bits 1..: instance index
+    int32_t pad;
+};
+int launch_rotate(const RotSys& one, int prec32, const RotTask* tasks, int64_t n, void* X, cudaStream_t st);
+int launch_rotate_multi(const RotSys* systems, int bmax, int prec32, const RotTask* tasks, int64_t n, void* X,
+                        cudaStream_t st);
+// dynamic shared memory of the direct kernel for a system
+size_t direct_smem(const DevSys& s, int prec32);
 int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st);
 int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X,
                          double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
@@ -185,8 +229,9 @@ int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2
 size_t tridiag_scratch_bytes(int64_t n);
 int tridiag_max_dim();
 int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st);
+// ev0 / ev1 (may be null) are recorded around the reduction kernel
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
-                            double* osc, double* wsum, int* err, cudaStream_t st);
+                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega,
                     int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);
 // recip_and_lattice: reciprocal basis then lattice, both row-major 3x3

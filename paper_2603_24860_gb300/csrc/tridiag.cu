@@ -663,7 +663,7 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // Reduce the block h (n x n, ld n, device; overwritten in the global-memory
 // variant) to T after the start reflector of b, then levels and weights.
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
-                            double* osc, double* wsum, int* err, cudaStream_t st) {
+                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
     if (n < 1 || n > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld", (long long)n);
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) {
@@ -724,8 +724,10 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     int per_sm = 0;
     BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
     if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
+    if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
     BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
     note_launch();
+    if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
 
     tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, bnd);
     note_launch();

@@ -1,0 +1,111 @@
+"""The mixed batch of 32 independent instances (MoS2-like D6h cells on
+9x9x1 to 18x18x3 meshes and Si-like Oh cells on 4^3 to 7^3 meshes, N_v and
+N_c from 2 to 6, seeded): the partner block of each instance's optically
+active irrep (E1u for q along x in D6h, T1u in Oh) from one graph launch in
+FP32 and FP64.  Every block equals the single-context build; the FP32
+levels agree with the FP64 ones within 0.1 meV for every instance; sampled
+star-pair sub-blocks of the smallest MoS2-like instance match the oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+HA_MEV = 27211.386245988
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import torch
+    from paper_2603_24860_gb300 import bse
+    from synth.generate import batch_configs, generate
+    cfgs = batch_configs()
+    stream = torch.cuda.current_stream()
+    ctxs = [bse.bse_create(generate(c), stream=stream) for c in cfgs]
+    mus, dims = [], []
+    for c in ctxs:
+        t = bse.bse_tables(c)
+        mu = int(np.nonzero(t["bright"] & (t["partner_dim"] > 0))[0][0])
+        mus.append(mu)
+        dims.append(int(t["partner_dim"][mu]))
+    out = {}
+    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64)):
+        bufs = [torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda") for n in dims]
+        b = bse.bse_batch_create(ctxs, mus, [1] * len(ctxs), prec, bse.BSE_TERM_ALL, bufs, [max(n, 1) for n in dims])
+        bse.bse_batch_run(b)
+        torch.cuda.synchronize()
+        bse.bse_batch_destroy(b)
+        out[name] = [bse.colmajor(x, n, n, max(n, 1)) for x, n in zip(bufs, dims)]
+    yield bse, torch, cfgs, ctxs, mus, dims, out
+    for c in ctxs:
+        bse.bse_destroy(c)
+
+
+def test_batch_shape(batch):
+    bse, torch, cfgs, ctxs, mus, dims, out = batch
+    assert len(cfgs) == 32
+    assert sum(c.material == "MoS2" for c in cfgs) == 22
+    meshes = {c.mesh for c in cfgs if c.material == "MoS2"}
+    assert (18, 18, 3) in meshes and (9, 9, 1) in meshes
+    assert all(2 <= c.nv <= 6 and 2 <= c.nc <= 6 for c in cfgs)
+
+
+@pytest.mark.parametrize("i", list(range(0, 32, 3)))
+def test_batch_equals_single_builds(batch, i):
+    bse, torch, cfgs, ctxs, mus, dims, out = batch
+    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64)):
+        single = bse.partner_block(ctxs[i], mus[i], prec=prec)
+        got = out[name][i]
+        scale = float(torch.max(torch.abs(single)).item())
+        assert float(torch.max(torch.abs(got - single)).item()) <= 1e-13 * scale, (cfgs[i].name, name)
+
+
+def test_batch_fp32_levels_within_0p1_mev(batch):
+    bse, torch, cfgs, ctxs, mus, dims, out = batch
+    from synth.generate import generate
+    worst = 0.0
+    for i, c in enumerate(ctxs):
+        if dims[i] == 0:
+            continue
+        d = generate(cfgs[i])
+        omega = torch.tensor(d["omega"], device="cuda")
+        om64 = bse.partner_spectrum(c, mus[i], out["fp64"][i], omega, d["eta"])[0].cpu().numpy()
+        om32 = bse.partner_spectrum(c, mus[i], out["fp32"][i], omega, d["eta"])[0].cpu().numpy()
+        worst = max(worst, float(np.abs(om32 - om64).max()) * HA_MEV)
+    assert worst <= 0.1
+
+
+def test_batch_against_oracle(batch):
+    """Sub-blocks of three star pairs of the smallest MoS2-like instance."""
+    from oracle.hamiltonian import Inputs, hamiltonian_block, head_correction
+    from oracle.projection import partner_irrep_matrices, star_basis
+    from oracle.tables import Group, MeshTables, orbits
+    from synth.generate import generate
+    bse, torch, cfgs, ctxs, mus, dims, out = batch
+    i = min((j for j, c in enumerate(cfgs) if c.material == "MoS2"), key=lambda j: dims[j])
+    d = generate(cfgs[i])
+    inp = Inputs(d)
+    grp = Group(d["rot"], d["tau"], d["lattice"])
+    mt = MeshTables(grp, d["mesh"])
+    orb = orbits(mt, inp.eps, inp.nv, inp.nc)
+    chi, dm, cls = grp.characters()
+    mu = mus[i]
+    gam = partner_irrep_matrices(grp, chi[mu], int(dm[mu]))
+    w = int(dm[mu]) / grp.n * gam[:, 0, 0]
+    wdiv = head_correction(inp)
+    cols = bse.bse_block_star_columns(ctxs[i], mu, partner=True)
+    sizes = np.array([len(s) for s in mt.stars])
+    order = np.argsort(-sizes, kind="stable")
+    pairs = [(0, int(order[0])), (int(order[0]), int(order[0])), (int(order[1]), int(order[2]))]
+    h64 = out["fp64"][i]
+    scale = float(torch.max(torch.abs(h64)).item())
+    checked = 0
+    for a, b in pairs:
+        ra, Ua = star_basis(inp, grp, mt, orb, a, w)
+        rb, Ub = star_basis(inp, grp, mt, orb, b, w)
+        if Ua.shape[1] == 0 or Ub.shape[1] == 0:
+            continue
+        Hab = hamiltonian_block(inp, mt, [int(k) for k in mt.stars[a]], [int(k) for k in mt.stars[b]], wdiv)
+        ref = Ua.conj().T @ Hab @ Ub
+        got = h64[cols[a]:cols[a + 1], cols[b]:cols[b + 1]].cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-10 * scale, (a, b)
+        checked += 1
+    assert checked >= 2

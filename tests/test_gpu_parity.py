@@ -437,3 +437,112 @@ def test_dark_blocks_levels_only(gpu, name):
         assert bse.bse_get_stats(ctx)["solver"] == bse.BSE_SOLVER_TRIDIAG
         assert np.abs(om - ref).max() <= TOL * max(np.abs(ref).max(), 1.0), (name, mu)
         assert np.all(osc == 0.0) and np.all(im == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_build_small(gpu, prec):
+    """Blocks of several contexts (Oh and D6h cells, whole and partner
+    blocks) from one graph launch equal the single-context builds, and in
+    FP64 the oracle; a second launch of the same graph gives the same."""
+    from oracle.projection import PartnerBasis, project
+    bse, torch, get = gpu
+    p = bse.BSE_FP64 if prec == "fp64" else bse.BSE_FP32
+    names = ["si2", "si4", "lif4", "mos2_331", "si4"]
+    ctxs = [get(nm) for nm in names]
+    targets = []
+    for i, (nm, c) in enumerate(zip(names, ctxs)):
+        t = bse.bse_tables(c)
+        mu = int(np.nonzero(t["bright"])[0][0])
+        pt = int(i % 2 == 1 and t["partner_dim"][mu] > 0)
+        targets.append((mu, pt, int(t["partner_dim" if pt else "block_dim"][mu])))
+    bufs = [torch.full((max(n * n, 1),), float("nan"), dtype=torch.complex128, device="cuda") for _, _, n in targets]
+    lds = [max(n, 1) for _, _, n in targets]
+    batch = bse.bse_batch_create(ctxs, [m for m, _, _ in targets], [pt for _, pt, _ in targets], p,
+                                 bse.BSE_TERM_ALL, bufs, lds)
+    try:
+        assert bse.bse_batch_kernels(batch) >= 1 + 2 * len(names)
+        bse.bse_batch_run(batch)
+        torch.cuda.synchronize()
+        first = [b.clone() for b in bufs]
+        bse.bse_batch_run(batch)
+        torch.cuda.synchronize()
+    finally:
+        bse.bse_batch_destroy(batch)
+    for (mu, pt, n), b, f, nm, c in zip(targets, bufs, first, names, ctxs):
+        got = bse.colmajor(b, n, n, max(n, 1)).cpu().numpy()
+        assert torch.equal(b, f)
+        single = (bse.partner_block if pt else bse.block)(c, mu, prec=p).cpu().numpy()
+        assert np.abs(got - single).max() <= 1e-13 * np.abs(single).max(), (nm, mu, pt)
+        if prec == "fp64":
+            d, inp, grp, mt, bb = oracle_case(nm)
+            U = PartnerBasis(bb, mu).U[0] if pt else bb.basis(mu)[0]
+            assert _rel(got, project(U, oracle_h(nm))) <= TOL, (nm, mu, pt)
+
+
+def test_batched_build_arguments(gpu):
+    bse, torch, get = gpu
+    ctxs = [get("si2"), get("si4")]
+    mus = [int(np.nonzero(bse.bse_tables(c)["bright"])[0][0]) for c in ctxs]
+    dims = [int(bse.bse_tables(c)["block_dim"][m]) for c, m in zip(ctxs, mus)]
+    bufs = [torch.empty(n * n, dtype=torch.complex128, device="cuda") for n in dims]
+    with pytest.raises(bse.BseError) as e:
+        bse.bse_build_blocks_batched(ctxs, mus, None, bse.BSE_BF16_SPLIT, bse.BSE_TERM_ALL, bufs, dims)
+    assert e.value.code == bse.BSE_EUNSUPPORTED
+    with pytest.raises(bse.BseError) as e:
+        bse.bse_build_blocks_batched(ctxs, mus, None, bse.BSE_FP64, bse.BSE_TERM_ALL, bufs, [dims[0] - 1, dims[1]])
+    assert e.value.code == bse.BSE_EINVAL
+    # the one-shot form equals the single builds
+    bse.bse_build_blocks_batched(ctxs, mus, None, bse.BSE_FP64, bse.BSE_TERM_ALL, bufs, dims)
+    for c, m, b, n in zip(ctxs, mus, bufs, dims):
+        single = bse.block(c, m).cpu().numpy()
+        assert np.abs(bse.colmajor(b, n, n, n).cpu().numpy() - single).max() <= 1e-13 * np.abs(single).max()
+
+
+@pytest.mark.parametrize("name", ["si4", "lif4", "mos2_331"])
+def test_all_blocks_packed(gpu, name):
+    """bse_build_block(BSE_IRREP_ALL) packs every block in irrep order; each
+    equals the oracle's projection."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    ctx = get(name)
+    assert bse.bse_block_dim(ctx, bse.BSE_IRREP_ALL) == inp.N
+    dims = [bse.bse_block_dim(ctx, mu) for mu in range(len(b.dims))]
+    assert sum(dims) == inp.N
+    buf = torch.empty(sum(n * n for n in dims), dtype=torch.complex128, device="cuda")
+    bse.bse_build_block(ctx, bse.BSE_IRREP_ALL, bse.BSE_FP64, bse.BSE_TERM_ALL, buf, 0)
+    H = oracle_h(name)
+    off = 0
+    for mu, n in enumerate(dims):
+        if n:
+            got = buf[off:off + n * n].view(n, n).transpose(0, 1).cpu().numpy()
+            assert _rel(got, project(b.basis(mu)[0], H)) <= TOL, (name, mu)
+        off += n * n
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_seeds_match_all_pairs(gpu, name):
+    """Eq. Wtrafo: blocks from one k pair per symmetry orbit plus rotated
+    blocks equal the pair-by-pair build (FP64 and FP32), and the seeds are a
+    fraction of the pairs."""
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    ctx = get(name)
+    t = bse.bse_tables(ctx)
+    for mu in b.bright():
+        if t["block_dim"][mu] == 0:
+            continue
+        w_on = bse.bse_build_work(ctx, mu)
+        bse.bse_set_seeds(ctx, False)
+        try:
+            w_off = bse.bse_build_work(ctx, mu)
+            off = {p: bse.block(ctx, mu, prec=p).cpu().numpy() for p in (bse.BSE_FP64, bse.BSE_FP32)}
+        finally:
+            bse.bse_set_seeds(ctx, True)
+        on = {p: bse.block(ctx, mu, prec=p).cpu().numpy() for p in (bse.BSE_FP64, bse.BSE_FP32)}
+        assert w_on["k_pairs"] == w_off["k_pairs"] == w_on["seeds"] + w_on["rotated"]
+        assert w_off["rotated"] == 0 and w_off["seeds"] == w_off["k_pairs"]
+        if grp.n > 1 and inp.nk > 1:
+            assert w_on["seeds"] < w_on["k_pairs"]
+        assert _rel(on[bse.BSE_FP64], off[bse.BSE_FP64]) <= 1e-12, (name, mu)
+        assert _rel(on[bse.BSE_FP32], off[bse.BSE_FP32]) <= 2e-6, (name, mu)
