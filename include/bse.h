@@ -352,6 +352,27 @@ enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2 };
 int bse_set_seeds(bse_ctx* ctx, int32_t on);
 int bse_set_solver(bse_ctx* ctx, int32_t solver);
 
+/*
+ * bse_loss_spectrum - longitudinal excitons and the loss spectrum of a block
+ * (Sec. III.D, "Excitonic energies and loss spectrum").  With the
+ * unmodified Coulomb interaction H gains alpha B* B^T (Eq. epsinv_div),
+ * alpha = 4 pi spin / N_k (B of Eq. oscillator carries 1/sqrt(V_uc)).  From
+ * the levels Omega_l and strengths w_l = |B_l|^2 of bse_block_spectrum or
+ * bse_partner_spectrum (omega_levels, osc: device, n entries, levels
+ * ascending) the new levels are the roots of the secular equation
+ * 1 - alpha sum_l w_l / (x - Omega_l) = 0 (Eq. secular): one in each gap
+ * between consecutive levels with w_l > 1e-14 max w and one above the
+ * highest; the other levels stay, with strength 0.  The strength of a
+ * longitudinal exciton follows from its closed-form eigenvector
+ * (Eq. eigenvec_xi): |B'_x|^2 = 1 / (alpha^2 sum_l w_l / (x - Omega_l)^2).
+ * Outputs (device, caller-owned): omega_long [n] ascending, osc_long [n],
+ * loss [n_omega] = -Im eps_M^-1(omega) = alpha sum_x |B'_x|^2
+ * [eta/((omega-x)^2+eta^2) - eta/((omega+x)^2+eta^2)].  Asynchronous on the
+ * context's stream.  Errors: EINVAL, EUNSUPPORTED (n > 2^20), ECUDA.
+ */
+int bse_loss_spectrum(bse_ctx* ctx, int64_t n, const double* omega_levels, const double* osc, const double* omega,
+                      int64_t n_omega, double eta, double* omega_long, double* osc_long, double* loss);
+
 /* Wait for all work on the context's stream; returns ECUDA on a device error. */
 int bse_sync(bse_ctx* ctx);
 

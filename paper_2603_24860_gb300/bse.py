@@ -91,6 +91,8 @@ EXPORTS = {
     "bse_block_star_columns": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _P64]),
     "bse_set_solver": (C.c_int, [C.c_void_p, C.c_int32]),
     "bse_set_seeds": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_loss_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_block_dim": (C.c_int, [C.c_void_p, C.c_int32, _P64]),
     "bse_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32, _P32, _P32, C.c_int32,
                                    C.c_uint32, C.POINTER(C.c_void_p), _P64]),
@@ -385,6 +387,23 @@ def bse_block_dim(ctx: Context, irrep: int) -> int:
     v = C.c_int64()
     _check(lib().bse_block_dim(ctx.handle, irrep, C.byref(v)))
     return v.value
+
+
+def bse_loss_spectrum(ctx: Context, omega_levels, osc, omega, eta: float, omega_long, osc_long, loss):
+    _check(lib().bse_loss_spectrum(ctx.handle, omega_levels.numel(), _ptr(omega_levels), _ptr(osc), _ptr(omega),
+                                   omega.numel(), eta, _ptr(omega_long), _ptr(osc_long), _ptr(loss)))
+
+
+def loss_spectrum(ctx: Context, omega_levels, osc, omega, eta: float):
+    """(longitudinal levels, their strengths, -Im eps_M^-1(omega)) from the
+    output of spectrum / partner_spectrum."""
+    import torch
+    n = omega_levels.numel()
+    ol = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    ow = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    ls = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+    bse_loss_spectrum(ctx, omega_levels.contiguous(), osc.contiguous(), omega, eta, ol, ow, ls)
+    return ol[:n], ow[:n], ls
 
 
 def bse_set_seeds(ctx: Context, on: bool):

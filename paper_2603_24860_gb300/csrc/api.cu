@@ -125,6 +125,8 @@ struct bse_ctx {
     DevBuf gam, gam32, gkoff, gboff, mfirst, msize;
     bool seeds = true;   // compute one k pair per symmetry orbit and rotate the rest
     DevBuf rots;
+    DevBuf lossScratch;
+    DevBuf wsym, wcand;  // orbit sum of W^div: per-column arrays and the flat candidate list
     int32_t solver_mode = BSE_SOLVER_AUTO;
     DevBuf triScratch, triSmall;   // tridiagonal path: scratch; gram [9], weight sum, error flag
     // scratch (library-owned, grow-only)
@@ -469,7 +471,44 @@ static int compute_wdiv(bse_ctx* c, const double* L) {
     double rl[18];
     std::memcpy(rl, c->t.recip, sizeof(double) * 9);
     std::memcpy(rl + 9, c->t.lattice, sizeof(double) * 9);
-    BSE_TRY(launch_wdiv(rl, c->t.n, L, b, qmax, delta, (double*)c->wpart.p, np, (double*)c->wsum.p, c->stream));
+    // the point group on the integer coordinates X of Q = sum_j X_j b_j / n_j:
+    // M = D rk D^-1 (rk = R^-T on fractional reciprocal coordinates, D = diag(n));
+    // the sum runs over orbits when every M is integral and L is invariant
+    std::vector<int> Mx((size_t)9 * c->t.nops);
+    bool sym = c->t.nops <= 48;
+    for (int s = 0; s < c->t.nops && sym; ++s)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                const long num = (long)c->t.rk[9 * s + 3 * i + j] * c->t.n[i];
+                if (num % c->t.n[j] != 0) sym = false;
+                Mx[9 * s + 3 * i + j] = (int)(num / c->t.n[j]);
+            }
+    double lnorm = 0.0;
+    for (int i = 0; i < 9; ++i) lnorm = std::max(lnorm, std::fabs(L[i]));
+    for (int s = 0; s < c->t.nops && sym; ++s) {
+        const double* R = &c->t.cart[9 * s];
+        for (int i = 0; i < 3 && sym; ++i)
+            for (int j = 0; j < 3 && sym; ++j) {
+                double v = 0.0;   // (R L R^T)_ij
+                for (int a = 0; a < 3; ++a)
+                    for (int d = 0; d < 3; ++d) v += R[3 * i + a] * L[3 * a + d] * R[3 * j + d];
+                if (std::fabs(v - L[3 * i + j]) > 1e-12 * lnorm) sym = false;
+            }
+    }
+    WdivScratch ws;
+    if (sym) {
+        BSE_TRY(ensure(c->wsym, wdiv_sym_bytes(c->t.lattice, c->t.n, qmax, delta)));
+        ws.base = c->wsym.p;
+        ws.owner = c;
+        ws.grow = [](WdivScratch* self, size_t bytes) -> int {
+            bse_ctx* cc = (bse_ctx*)self->owner;
+            BSE_TRY(ensure(cc->wcand, bytes));
+            self->cand = cc->wcand.p;
+            return BSE_OK;
+        };
+    }
+    BSE_TRY(launch_wdiv(rl, c->t.n, L, b, qmax, delta, (double*)c->wpart.p, np, (double*)c->wsum.p, c->stream,
+                        sym ? c->t.nops : 0, sym ? Mx.data() : nullptr, sym ? &ws : nullptr));
     double sum = 0.0;
     BSE_CUDA(cudaMemcpyAsync(&sum, c->wsum.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BSE_CUDA(cudaStreamSynchronize(c->stream));
@@ -736,7 +775,8 @@ static void free_ctx(bse_ctx* c) {
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
-                      &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots})
+                      &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots,
+                      &c->lossScratch, &c->wsym, &c->wcand})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -1588,6 +1628,27 @@ int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, cons
     BSE_TRY(ensure_partner(c, mu));
     auto& pd = c->partner[mu];
     return spectrum_generic(c, pd.part, pd.d, pd.d, false, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+}
+
+int bse_loss_spectrum(bse_ctx* c, int64_t n, const double* omega_levels, const double* osc, const double* omega,
+                      int64_t n_omega, double eta, double* omega_long, double* osc_long, double* loss) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
+    if (n < 0 || (n > 0 && (!omega_levels || !osc || !omega_long || !osc_long)) || (n_omega > 0 && (!omega || !loss)))
+        return fail(BSE_EINVAL, "null argument");
+    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
+    if (n > (1 << 20)) return fail(BSE_EUNSUPPORTED, "loss spectrum of more than 2^20 levels");
+    const double alpha = 4.0 * M_PI * c->spin / c->t.nk;
+    if (n > 0) {
+        BSE_TRY(ensure(c->lossScratch, loss_scratch_bytes(n)));
+        BSE_TRY(launch_loss_levels(omega_levels, osc, n, alpha, c->lossScratch.p, omega_long, osc_long, c->stream));
+    }
+    if (n_omega > 0) {
+        if (n > 0) BSE_TRY(launch_spectrum(omega_long, osc_long, n, omega, n_omega, eta, alpha, loss, c->stream));
+        else BSE_CUDA(cudaMemsetAsync(loss, 0, sizeof(double) * n_omega, c->stream));
+    }
+    return BSE_OK;
 }
 
 int bse_set_solver(bse_ctx* c, int32_t solver) {

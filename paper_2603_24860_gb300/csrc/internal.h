@@ -232,11 +232,28 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // ev0 / ev1 (may be null) are recorded around the reduction kernel
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+// loss.cu: longitudinal levels (Eq. secular) and strengths (Eq. eigenvec_xi)
+size_t loss_scratch_bytes(int64_t n);
+int launch_loss_levels(const double* Om, const double* osc, int64_t n, double alpha, void* scratch, double* out_l,
+                       double* out_w, cudaStream_t st);
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega,
                     int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);
-// recip_and_lattice: reciprocal basis then lattice, both row-major 3x3
+// recip_and_lattice: reciprocal basis then lattice, both row-major 3x3.  With
+// nops > 0, Mx [nops][9] is the point group acting on the integer coordinates
+// of Q = sum X_j b_j / n_j (row-major) and the sum runs over one point per
+// orbit (the caller has checked that L is invariant); nops = 0: every point.
+// scratch of the orbit sum: base holds the per-column arrays (wdiv_sym_bytes),
+// grow(self, bytes) makes cand hold the flat candidate list
+struct WdivScratch {
+    void* base = nullptr;
+    void* cand = nullptr;
+    int (*grow)(WdivScratch* self, size_t bytes) = nullptr;
+    void* owner = nullptr;
+};
+size_t wdiv_sym_bytes(const double* lattice, const int* n, double qmax, double delta);
 int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax,
-                double delta, double* partial, int64_t npartial_max, double* out, cudaStream_t st);
+                double delta, double* partial, int64_t npartial_max, double* out, cudaStream_t st, int nops = 0,
+                const int* Mx = nullptr, WdivScratch* sym_scratch = nullptr);
 int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta);
 int launch_count_overlap(const DevSys& s, const PairTask* tasks, int64_t ntasks, unsigned long long* out,
                          cudaStream_t st);

@@ -524,24 +524,32 @@ int launch_oscillators(const double2* a, int64_t lda, int64_t dim, const double2
     return BSE_OK;
 }
 
+// Im eps_M on the frequency grid: 8 lanes per frequency share the sum over
+// the levels (one warp per frequency would leave the FP64 pipes of most SM
+// sub-partitions idle at a few thousand frequencies); Newton reciprocals.
+constexpr int kSpecLanes = 8;
 __global__ void spectrum_kernel(const double* __restrict__ Om, const double* __restrict__ osc, int64_t dim,
                                 const double* __restrict__ omega, int64_t n_omega, double eta, double pref,
                                 double* im) {
-    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_omega) return;
-    const double x = omega[w], e2 = eta * eta;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t w = g / kSpecLanes;
+    const int part = (int)(g % kSpecLanes);
+    const double x = w < n_omega ? omega[w] : 0.0, e2 = eta * eta;
     double acc = 0.0;
-    for (int64_t l = 0; l < dim; ++l) {
-        double d1 = x - Om[l], d2 = x + Om[l];
-        acc = fma(osc[l], eta / (d1 * d1 + e2) - eta / (d2 * d2 + e2), acc);
-    }
-    im[w] = pref * acc;
+    if (w < n_omega)
+        for (int64_t l = part; l < dim; l += kSpecLanes) {
+            const double d1 = x - Om[l], d2 = x + Om[l];
+            acc = fma(osc[l], eta * (rcp_nr(fma(d1, d1, e2)) - rcp_nr(fma(d2, d2, e2))), acc);
+        }
+#pragma unroll
+    for (int o = kSpecLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (part == 0 && w < n_omega) im[w] = pref * acc;
 }
 
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega, int64_t n_omega, double eta,
                     double pref, double* im, cudaStream_t st) {
     if (n_omega == 0) return BSE_OK;
-    spectrum_kernel<<<ceil_div(n_omega, 128), 128, 0, st>>>(Om, osc, dim, omega, n_omega, eta, pref, im);
+    spectrum_kernel<<<ceil_div(n_omega * kSpecLanes, 256), 256, 0, st>>>(Om, osc, dim, omega, n_omega, eta, pref, im);
     LAUNCH_CHECK();
     return BSE_OK;
 }
@@ -550,6 +558,15 @@ int launch_spectrum(const double* Om, const double* osc, int64_t dim, const doub
 // head correction: smoothed double-counting sum of Eq. divergence_sum over
 // Q = sum_j X_j b_j / n_j (X integer, Q != 0), one thread per (X1, X2) column
 // ---------------------------------------------------------------------------
+constexpr int kWdivMaxOps = 48;
+struct WdivSym {
+    int nops;
+    int M[kWdivMaxOps][9];      // action on the integer coordinates X, row-major
+    float u[kWdivMaxOps][3];    // p - M_g^T p (the identity's row is zero)
+    float inv3[kWdivMaxOps];    // 1 / u[g][2], or 0 when |u[g][2]| is negligible
+    double p[3];                // generic projection vector
+};
+
 struct WdivGeom {
     double s[9];      // columns: b_j / n_j (row-major 3x3)
     double L[9];
@@ -639,6 +656,198 @@ __global__ void wdiv_kernel(WdivGeom g, double* partial) {
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// The same sum over one representative per orbit of the point group: the
+// summand depends on Q only through |Q| and Q^T L Q, both invariant when L
+// is, so sum_Q f(Q) = sum_{representatives} |orbit| f(Q).  Q = sum_j X_j b_j /
+// n_j with X integer; the group acts on X by integer matrices M_g.  X is the
+// representative of its orbit when its projection X.p on a generic vector p
+// is the largest over the orbit (ties, possible only for distinct points with
+// equal projections, by the lexicographic order of the integer vectors); its
+// orbit has |G| / |stab(X)| points.  The necessary conditions (p - M_g^T p).X
+// >= 0 are linear in X_3, so each column (X_1, X_2) is clipped to the
+// interval of its cone (wdiv_clip_kernel); the candidates of all columns are
+// then laid out flat (wdiv_fill_kernel, after a scan of the counts) and
+// evaluated one per thread (wdiv_point_kernel), which keeps the FP64 work of
+// the ~1/|G| remaining points free of the columns' very uneven lengths.
+struct WdivCols {
+    int* lo;            // [ncol] first X_3 of the column's interval
+    int* cnt;           // [ncol] candidates of the column
+    int64_t* blocksum;  // [nblk] candidates per block of 256 columns, then their exclusive scan
+    int64_t* total;     // [1]
+    int* cand;          // [total] column index of each candidate
+    int* x3;            // [total] its X_3
+};
+
+__device__ __forceinline__ void wdiv_column(const WdivGeom& g, const WdivSym& sy, int64_t id, int& lo, int& hi) {
+    const int x1 = (int)(id / (2 * g.e2 + 1)) - g.e1;
+    const int x2 = (int)(id % (2 * g.e2 + 1)) - g.e2;
+    double p[3], s3[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = g.s[3 * a] * x1 + g.s[3 * a + 1] * x2;
+        s3[a] = g.s[3 * a + 2];
+    }
+    const double A = s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2];
+    const double Bq = 2.0 * (p[0] * s3[0] + p[1] * s3[1] + p[2] * s3[2]);
+    const double C = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - g.lim * g.lim;
+    const double disc = Bq * Bq - 4.0 * A * C;
+    lo = 0;
+    hi = -1;
+    if (disc < 0.0) return;
+    const double sq = sqrt(disc);
+    lo = (int)floor((-Bq - sq) / (2.0 * A)) - 1;
+    hi = (int)ceil((-Bq + sq) / (2.0 * A)) + 1;
+    // clip to the cone u_g . X >= 0 (FP32 with two points of slack; exact checks follow)
+    for (int o = 0; o < sy.nops && lo <= hi; ++o) {
+        const float b0 = sy.u[o][0] * (float)x1 + sy.u[o][1] * (float)x2;
+        const float ia = sy.inv3[o];
+        if (ia == 0.0f) {
+            if (b0 < -1e-2f) hi = lo - 1;
+        } else {
+            const float t = -b0 * ia;
+            if (sy.u[o][2] > 0.0f) lo = max(lo, (int)floorf(t) - 2);
+            else hi = min(hi, (int)ceilf(t) + 2);
+        }
+    }
+}
+
+__global__ void wdiv_clip_kernel(WdivGeom g, const __grid_constant__ WdivSym sy, WdivCols c) {
+    __shared__ int64_t red[256];
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ncol = (int64_t)(2 * g.e1 + 1) * (2 * g.e2 + 1);
+    int n = 0;
+    if (id < ncol) {
+        int lo, hi;
+        wdiv_column(g, sy, id, lo, hi);
+        n = hi >= lo ? hi - lo + 1 : 0;
+        c.lo[id] = lo;
+        c.cnt[id] = n;
+    }
+    red[threadIdx.x] = n;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) c.blocksum[blockIdx.x] = red[0];
+}
+
+// exclusive scan of the block sums (one block)
+__global__ void wdiv_scan_kernel(WdivCols c, int64_t nblk) {
+    __shared__ int64_t s[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (nblk + 1023) / 1024;
+    const int64_t i0 = t * per, i1 = min(nblk, i0 + per);
+    int64_t loc = 0;
+    for (int64_t i = i0; i < i1; ++i) loc += c.blocksum[i];
+    s[t] = loc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    int64_t run = s[t] - loc;
+    for (int64_t i = i0; i < i1; ++i) {
+        const int64_t x = c.blocksum[i];
+        c.blocksum[i] = run;
+        run += x;
+    }
+    if (t == 1023) *c.total = s[1023];
+}
+
+__global__ void wdiv_fill_kernel(WdivGeom g, WdivCols c) {
+    __shared__ int s[256];
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ncol = (int64_t)(2 * g.e1 + 1) * (2 * g.e2 + 1);
+    const int n = id < ncol ? c.cnt[id] : 0;
+    s[threadIdx.x] = n;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const int v = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int64_t base = c.blocksum[blockIdx.x] + s[threadIdx.x] - n;
+    const int lo = id < ncol ? c.lo[id] : 0;
+    for (int i = 0; i < n; ++i) {
+        c.cand[base + i] = (int)id;
+        c.x3[base + i] = lo + i;
+    }
+}
+
+// one candidate per thread, grid-stride over the total; partial sums per block
+__global__ void wdiv_point_kernel(WdivGeom g, const __grid_constant__ WdivSym sy, WdivCols c, double* partial) {
+    __shared__ double red[256];
+    const int64_t total = *c.total;
+    const double lim2 = g.lim * g.lim, in2 = (g.qmax - g.delta) * (g.qmax - g.delta);
+    double acc = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t id = c.cand[q];
+        const int x1 = (int)(id / (2 * g.e2 + 1)) - g.e1;
+        const int x2 = (int)(id % (2 * g.e2 + 1)) - g.e2;
+        const int x3 = c.x3[q];
+        if (x1 == 0 && x2 == 0 && x3 == 0) continue;
+        double Q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Q[a] = g.s[3 * a] * x1 + g.s[3 * a + 1] * x2 + g.s[3 * a + 2] * x3;
+        const double q2 = Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2];
+        if (q2 > lim2) continue;
+        // cone values in FP32: all clearly positive means an interior point, whose
+        // stabiliser is trivial (orbit of |G| points); any clearly negative one rejects
+        float vmin = 1e30f;
+        for (int o = 0; o < sy.nops; ++o) {
+            if (sy.u[o][0] == 0.0f && sy.u[o][1] == 0.0f && sy.u[o][2] == 0.0f) continue;   // the identity
+            vmin = fminf(vmin, sy.u[o][0] * (float)x1 + sy.u[o][1] * (float)x2 + sy.u[o][2] * (float)x3);
+        }
+        if (vmin < -1e-2f) continue;
+        int mult = sy.nops;
+        if (vmin <= 1e-2f) {   // near a face: exact test on the integer coordinates
+            const double pX = sy.p[0] * x1 + sy.p[1] * x2 + sy.p[2] * x3;
+            int stab = 0;
+            bool rep = true;
+            for (int o = 0; o < sy.nops; ++o) {
+                const int* M = sy.M[o];
+                const int y0 = M[0] * x1 + M[1] * x2 + M[2] * x3;
+                const int y1 = M[3] * x1 + M[4] * x2 + M[5] * x3;
+                const int y2 = M[6] * x1 + M[7] * x2 + M[8] * x3;
+                if (y0 == x1 && y1 == x2 && y2 == x3) {
+                    ++stab;
+                    continue;
+                }
+                const double pY = sy.p[0] * y0 + sy.p[1] * y1 + sy.p[2] * y2;
+                if (pY > pX || (pY == pX && (y0 > x1 || (y0 == x1 && (y1 > x2 || (y1 == x2 && y2 > x3)))))) {
+                    rep = false;
+                    break;
+                }
+            }
+            if (!rep) continue;
+            mult = sy.nops / stab;
+        }
+        double w = (double)mult;
+        if (q2 >= in2) {
+            const double x = (sqrt(q2) - g.qmax) / g.delta;
+            if (x > 1.0) continue;
+            w *= (x * x * x - 3.0 * x + 2.0) * 0.25;
+        }
+        double ql = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) ql += Q[a] * g.L[3 * a + cc] * Q[cc];
+        acc = fma(exp(-g.b * q2) * w, rcp_nr(ql), acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 // fixed-order reduction of the block partials (deterministic)
 __global__ void reduce_kernel(const double* __restrict__ partial, int64_t n, double* out) {
     __shared__ double red[1024];
@@ -660,6 +869,14 @@ static void wdiv_extent(const double* lattice, const int* n, double lim, int e[3
     }
 }
 
+size_t wdiv_sym_bytes(const double* lattice, const int* n, double qmax, double delta) {
+    int e[3];
+    wdiv_extent(lattice, n, qmax + delta, e);
+    const int64_t ncol = (int64_t)(2 * e[0] + 1) * (2 * e[1] + 1);
+    const int64_t nblk = (ncol + 255) / 256;
+    return sizeof(int) * 2 * (size_t)ncol + 16 + sizeof(int64_t) * (size_t)(nblk + 1);
+}
+
 int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta) {
     int e[3];
     wdiv_extent(lattice, n, qmax + delta, e);
@@ -668,7 +885,8 @@ int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double d
 }
 
 int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax, double delta,
-                double* partial, int64_t npartial_max, double* out, cudaStream_t st) {
+                double* partial, int64_t npartial_max, double* out, cudaStream_t st, int nops, const int* Mx,
+                WdivScratch* sym_scratch) {
     // recip_and_lattice: 18 doubles, reciprocal basis then lattice (row-major)
     WdivGeom g;
     const double* recip = recip_and_lattice;
@@ -688,7 +906,52 @@ int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, 
     int64_t nblk = (ncol + 255) / 256;
     if (nblk > npartial_max) return fail(BSE_EINVAL, "head-correction scratch too small (%lld > %lld)",
                                          (long long)nblk, (long long)npartial_max);
-    wdiv_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, partial);
+    if (nops > 0 && nops <= kWdivMaxOps && Mx && sym_scratch) {
+        WdivSym sy;
+        sy.nops = nops;
+        // a generic direction (no small-integer relation among the components)
+        sy.p[0] = 1.0;
+        sy.p[1] = 0.7548776662466927;   // plastic-number ratios
+        sy.p[2] = 0.5698402909980532;
+        for (int o = 0; o < nops; ++o) {
+            for (int i = 0; i < 9; ++i) sy.M[o][i] = Mx[9 * o + i];
+            for (int j = 0; j < 3; ++j) {
+                double mtp = 0.0;   // (M^T p)_j
+                for (int i = 0; i < 3; ++i) mtp += Mx[9 * o + 3 * i + j] * sy.p[i];
+                const double u = sy.p[j] - mtp;
+                sy.u[o][j] = std::fabs(u) < 1e-12 ? 0.0f : (float)u;
+            }
+            sy.inv3[o] = std::fabs(sy.u[o][2]) < 1e-6f ? 0.0f : 1.0f / sy.u[o][2];
+        }
+        WdivCols c;
+        char* ptr = (char*)sym_scratch->base;
+        c.lo = (int*)ptr;
+        c.cnt = c.lo + ncol;
+        c.blocksum = (int64_t*)(((uintptr_t)(c.cnt + ncol) + 15) & ~(uintptr_t)15);
+        c.total = c.blocksum + nblk;
+        c.cand = nullptr;
+        c.x3 = nullptr;
+        wdiv_clip_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, sy, c);
+        LAUNCH_CHECK();
+        wdiv_scan_kernel<<<1, 1024, 0, st>>>(c, nblk);
+        LAUNCH_CHECK();
+        int64_t total = 0;
+        BSE_CUDA(cudaMemcpyAsync(&total, c.total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        BSE_CUDA(cudaStreamSynchronize(st));
+        BSE_TRY(sym_scratch->grow(sym_scratch, (size_t)std::max<int64_t>(total, 1) * 2 * sizeof(int)));
+        c.cand = (int*)sym_scratch->cand;
+        c.x3 = c.cand + std::max<int64_t>(total, 1);
+        wdiv_fill_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, c);
+        LAUNCH_CHECK();
+        const int64_t pb = std::min<int64_t>(nblk, 152 * 8);
+        wdiv_point_kernel<<<(unsigned)pb, 256, 0, st>>>(g, sy, c, partial);
+        LAUNCH_CHECK();
+        reduce_kernel<<<1, 1024, 0, st>>>(partial, pb, out);
+        LAUNCH_CHECK();
+        return BSE_OK;
+    } else {
+        wdiv_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, partial);
+    }
     LAUNCH_CHECK();
     reduce_kernel<<<1, 1024, 0, st>>>(partial, nblk, out);
     LAUNCH_CHECK();

@@ -45,61 +45,70 @@ __device__ __forceinline__ V cmc(V a, V b) {  // a conj(b)
     return r;
 }
 
-// One thread per element of a rotated block (slots of bsq = B_max^2 per
-// task): out[(v c),(v' c')] = sum over the multiplets of v, c at k and of
-// v', c' at k' of conj(Gamma_c(k)[c1][c]) Gamma_v(k)[v1][v] S[(v1 c1),(v2 c2)]
-// Gamma_c(k')[c2][c'] conj(Gamma_v(k')[v2][v']) -- one term when the four
-// multiplets are single bands (every k of a general star), at most 81.
+// One CTA per rotated pair.  Phase 1: for every row (v c) at k the factors
+// L = Gamma_v(k)[v1][v] conj(Gamma_c(k)[c1][c]) with the seed rows (v1 c1)
+// of its multiplets, and for every column (v' c') at k' the factors
+// R = Gamma_c(k')[c2][c'] conj(Gamma_v(k')[v2][v']) with the seed columns,
+// into shared memory (at most 9 terms each; one at a general k).  Phase 2:
+// out[(v c), (v' c')] = sum L S[(v1 c1), (v2 c2)] R, the seed element read
+// from the tile arena, written to the block and to its mirror.
+constexpr int kMaxTerms = 9;
+constexpr int kRotThreads = 128;
+
 template <typename R, bool kBatch>
-__global__ void __launch_bounds__(256) rotate_kernel(const RotSys* __restrict__ systems,
-                                                     const __grid_constant__ RotSys one,
-                                                     const RotTask* __restrict__ tasks, int64_t ntasks, int bsq,
-                                                     typename C2r<R>::T* X) {
+__global__ void __launch_bounds__(kRotThreads) rotate_kernel(const RotSys* __restrict__ systems,
+                                                             const __grid_constant__ RotSys one,
+                                                             const RotTask* __restrict__ tasks,
+                                                             typename C2r<R>::T* X) {
     using V = typename C2r<R>::T;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t ti = g / bsq;
-    if (ti >= ntasks) return;
-    const int e = (int)(g - ti * bsq);
-    const RotTask& t = tasks[ti];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RotTask t = tasks[blockIdx.x];
     const RotSys& Y = kBatch ? systems[t.flags >> 1] : one;
     const int nv = Y.nv, nc = Y.nc, nb = Y.nb, B = nv * nc;
-    if (e >= B * B) return;
-    const int r = e % B, col = e / B;
-    const int v = r / nc, c = r % nc, vp = col / nc, cp = col % nc;
-    const int k = t.k, kp = t.kp;
+    V* fac = (V*)smem_raw;                               // [2][B][kMaxTerms]
+    int* idx = (int*)(fac + 2 * B * kMaxTerms);          // [2][B][kMaxTerms]
+    int* cnt = idx + 2 * B * kMaxTerms;                  // [2][B]
     const V* gam = (const V*)Y.gam + (size_t)t.s * Y.gps;
-    const int ik = k * nb, ikp = kp * nb;
-    const int fv = __ldg(Y.mfirst + ik + v), mv = __ldg(Y.msize + ik + v);
-    const int fc = __ldg(Y.mfirst + ik + nv + c) - nv, mc = __ldg(Y.msize + ik + nv + c);
-    const int fvp = __ldg(Y.mfirst + ikp + vp), mvp = __ldg(Y.msize + ikp + vp);
-    const int fcp = __ldg(Y.mfirst + ikp + nv + cp) - nv, mcp = __ldg(Y.msize + ikp + nv + cp);
-    const V* gvk = gam + __ldg(Y.koff + k) + __ldg(Y.boff + ik + v);
-    const V* gck = gam + __ldg(Y.koff + k) + __ldg(Y.boff + ik + nv + c);
-    const V* gvp = gam + __ldg(Y.koff + kp) + __ldg(Y.boff + ikp + vp);
-    const V* gcp = gam + __ldg(Y.koff + kp) + __ldg(Y.boff + ikp + nv + cp);
-    V acc;
-    acc.x = acc.y = R(0);
-    for (int a = 0; a < mv; ++a) {
-        const V g2 = gvk[a * mv + (v - fv)];
-        for (int b = 0; b < mc; ++b) {
-            const V L = cmc(g2, gck[b * mc + (c - fc)]);          // Gamma_v(k)[v1][v] conj(Gamma_c(k)[c1][c])
-            const int row = (fv + a) * nc + fc + b;
-            for (int a2 = 0; a2 < mvp; ++a2) {
-                const V h2 = gvp[a2 * mvp + (vp - fvp)];
-                for (int b2 = 0; b2 < mcp; ++b2) {
-                    const V Rt = cmc(gcp[b2 * mcp + (cp - fcp)], h2);   // Gamma_c(k')[c2][c'] conj(Gamma_v(k')[v2][v'])
-                    const V sv = X[t.src + (int64_t)((fvp + a2) * nc + fcp + b2) * t.ld + row];
-                    const V p = cm(cm(L, sv), Rt);
-                    acc.x += p.x;
-                    acc.y += p.y;
-                }
+    for (int q = threadIdx.x; q < 2 * B; q += blockDim.x) {
+        const int side = q / B, rc = q % B;              // side 0: rows at k, side 1: columns at k'
+        const int kk = side == 0 ? t.k : t.kp;
+        const int v = rc / nc, c = rc % nc, ik = kk * nb;
+        const int fv = __ldg(Y.mfirst + ik + v), mv = __ldg(Y.msize + ik + v);
+        const int fc = __ldg(Y.mfirst + ik + nv + c) - nv, mc = __ldg(Y.msize + ik + nv + c);
+        const int64_t ko = __ldg(Y.koff + kk);
+        const V* gv = gam + ko + __ldg(Y.boff + ik + v);
+        const V* gc = gam + ko + __ldg(Y.boff + ik + nv + c);
+        int n = 0;
+        for (int a = 0; a < mv; ++a)
+            for (int b = 0; b < mc; ++b) {
+                const V hv = gv[a * mv + (v - fv)], hc = gc[b * mc + (c - fc)];
+                fac[(side * B + rc) * kMaxTerms + n] = side == 0 ? cmc(hv, hc) : cmc(hc, hv);
+                idx[(side * B + rc) * kMaxTerms + n] = (fv + a) * nc + fc + b;
+                ++n;
+            }
+        cnt[side * B + rc] = n;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int r = e % B, col = e / B;
+        const int nr = cnt[r], ncl = cnt[B + col];
+        V acc;
+        acc.x = acc.y = R(0);
+        for (int i = 0; i < nr; ++i) {
+            const V Lf = fac[r * kMaxTerms + i];
+            const int srow = idx[r * kMaxTerms + i];
+            for (int j = 0; j < ncl; ++j) {
+                const int scol = idx[(B + col) * kMaxTerms + j];
+                const V p = cm(cm(Lf, X[t.src + (int64_t)scol * t.ld + srow]), fac[(B + col) * kMaxTerms + j]);
+                acc.x += p.x;
+                acc.y += p.y;
             }
         }
-    }
-    X[t.dst + (int64_t)col * t.ld + r] = acc;
-    if (t.flags & 1) {
-        acc.y = -acc.y;
-        X[t.dstm + (int64_t)r * t.ld + col] = acc;
+        X[t.dst + (int64_t)col * t.ld + r] = acc;
+        if (t.flags & 1) {
+            acc.y = -acc.y;
+            X[t.dstm + (int64_t)r * t.ld + col] = acc;
+        }
     }
 }
 
@@ -108,15 +117,15 @@ int launch_rotate_t(const RotSys* systems, const RotSys& one, int B, const RotTa
                     cudaStream_t st) {
     using V = typename C2r<R>::T;
     if (n == 0) return BSE_OK;
-    const int bsq = B * B;
-    const int64_t per = ((int64_t)1 << 31) / bsq;   // tasks per launch: at most 2^31 threads
-    for (int64_t off = 0; off < n; off += per) {
-        const int64_t nt = n - off < per ? n - off : per;
-        const int64_t threads = nt * bsq;
-        rotate_kernel<R, kBatch><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(systems, one, tasks + off, nt,
-                                                                                 bsq, (V*)X);
+    const size_t sm = (size_t)2 * B * kMaxTerms * (sizeof(V) + sizeof(int)) + sizeof(int) * 2 * B;
+    if (sm > 227 * 1024) return fail(BSE_EUNSUPPORTED, "rotation of %d x %d blocks exceeds shared memory", B, B);
+    cudaError_t e = cudaFuncSetAttribute(rotate_kernel<R, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "rotate smem: %s", cudaGetErrorString(e));
+    for (int64_t off = 0; off < n; off += 1 << 30) {
+        const int64_t nt = n - off < (1 << 30) ? n - off : (1 << 30);
+        rotate_kernel<R, kBatch><<<(unsigned)nt, kRotThreads, sm, st>>>(systems, one, tasks + off, (V*)X);
         note_launch();
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "rotate launch: %s", cudaGetErrorString(e));
     }
     return BSE_OK;

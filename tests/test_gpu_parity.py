@@ -546,3 +546,39 @@ def test_seeds_match_all_pairs(gpu, name):
             assert w_on["seeds"] < w_on["k_pairs"]
         assert _rel(on[bse.BSE_FP64], off[bse.BSE_FP64]) <= 1e-12, (name, mu)
         assert _rel(on[bse.BSE_FP32], off[bse.BSE_FP32]) <= 2e-6, (name, mu)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_loss_spectrum(gpu, name):
+    """Longitudinal levels (Eq. secular), strengths (Eq. eigenvec_xi) and the
+    loss spectrum from the partner-block levels against the oracle."""
+    from oracle import loss
+    from oracle.projection import PartnerBasis, project
+    from oracle.spectrum import dipoles
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case(name)
+    ctx = get(name)
+    t = bse.bse_tables(ctx)
+    H = oracle_h(name)
+    B = dipoles(inp, mt)
+    scale = np.linalg.norm(B) ** 2
+    omega = torch.tensor(d["omega"], device="cuda")
+    checked = 0
+    for mu in b.bright():
+        if t["partner_dim"][mu] == 0:
+            continue
+        pb = PartnerBasis(b, mu)
+        Hm = project(pb.U[0], H)
+        Om, a = np.linalg.eigh(Hm)
+        osc = sum(np.abs(a.T @ (U.T @ B)) ** 2 for U in pb.U)
+        ref_l, ref_w = loss.secular_levels(Om, osc, loss.loss_alpha(inp))
+        ref_s = loss.loss_spectrum(inp, ref_l, ref_w, d["omega"], d["eta"])
+        h1 = bse.partner_block(ctx, mu)
+        om, os_, _ = bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])
+        gl, gw, gs = (x.cpu().numpy() for x in bse.loss_spectrum(ctx, om, os_, omega, d["eta"]))
+        assert np.abs(gl - ref_l).max() <= TOL * max(np.abs(ref_l).max(), 1.0), (name, mu)
+        assert np.abs(gw - ref_w).max() <= 1e-9 * scale, (name, mu)
+        assert np.linalg.norm(gs - ref_s) <= 1e-9 * max(np.linalg.norm(ref_s), scale * 1e-3), (name, mu)
+        assert abs(gw.sum() - os_.cpu().numpy().sum()) <= 1e-9 * scale
+        checked += 1
+    assert checked >= 1

@@ -143,3 +143,23 @@ def test_partner_solvers_agree(built):
     assert np.abs(om - om2).max() <= TOL * np.abs(om).max()
     assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()
     assert np.linalg.norm(im - im2) <= 1e-9 * np.linalg.norm(im)
+
+
+def test_loss_levels_against_dense(built):
+    """The secular-equation levels of H + alpha B* B^T on the 806-dim partner
+    block against a dense eigensolution of that matrix (torch, FP64)."""
+    import math
+    bse, torch, ctx, t, mu, h = built
+    d, inp, grp, mt, b = oracle_case("si8")
+    h1 = bse.partner_block(ctx, mu)
+    omega = torch.tensor(d["omega"], device="cuda")
+    om, osc, _ = bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])
+    lv, lw, ls = bse.loss_spectrum(ctx, om, osc, omega, d["eta"])
+    alpha = 4.0 * math.pi * 2 / inp.nk
+    # the partner block's dipole projections are parallel: c = conj(U_1^T B) carries all the strength
+    ev, vec = torch.linalg.eigh(h1)
+    w = osc                                    # |a_l^T b|^2 in the eigenbasis (levels ascending)
+    hp = torch.diag(ev) + alpha * torch.sqrt(w)[:, None] * torch.sqrt(w)[None, :]
+    ref = torch.linalg.eigvalsh(hp).cpu().numpy()
+    assert np.abs(lv.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert abs(lw.sum().item() - osc.sum().item()) <= 1e-9 * osc.sum().item()
