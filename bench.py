@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--block", choices=["partner", "full", "all"], default="partner",
                    help="solve the partner block (dim/d, same levels and spectrum), the whole irrep block, or "
                         "build every irrep block in one pass and solve each")
-    p.add_argument("--prec", choices=["fp32", "fp64", "bf16"], default="fp32",
+    p.add_argument("--prec", choices=["fp32", "fp64", "bf16", "fp16"], default="fp32",
                    help="precision of the direct term; the FP64 build is also timed for comparison")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="approximate size of the oracle sample (CPU seconds)")
@@ -317,7 +317,8 @@ def run_ours(args, rank, world, local):
     om, im = oms[ib], ims[ib]
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64, "bf16": bse.BSE_BF16_SPLIT}[args.prec]
+    prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64, "bf16": bse.BSE_BF16_SPLIT,
+            "fp16": bse.BSE_FP16_SPLIT}[args.prec]
 
     def step(host_inputs=None, d2h=None, p=None):
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
@@ -421,14 +422,15 @@ def run_ours(args, rank, world, local):
     peak = FP64_PEAK_TFLOPS if prec == bse.BSE_FP64 else FP32_PEAK_TFLOPS
     ms_reduce = statistics.mean(s[1]["ms_reduce"] for s in stats)
     roofs = [{"bound": "alu", "kernel": {bse.BSE_FP32: "direct_kernel<float>", bse.BSE_FP64: "direct_kernel<double>",
-                                         bse.BSE_BF16_SPLIT: "direct_tc_kernel"}[prec],
+                                         bse.BSE_BF16_SPLIT: "direct_tc_kernel<bf16>",
+                                         bse.BSE_FP16_SPLIT: "direct_tc_kernel<fp16>"}[prec],
               "ms_per_step": ms_seed,
               "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
               "peak_source": ("derived: 152 SMs x %s x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
                               "CUDA-core figure)%s" % ("2 DFMA/clk" if prec == bse.BSE_FP64 else "128 FFMA/clk",
                                                         "; the split kernel is bounded by its FP32 pair "
                                                         "densities, its tensor share is reported separately"
-                                                        if prec == bse.BSE_BF16_SPLIT else "")),
+                                                        if prec in (bse.BSE_BF16_SPLIT, bse.BSE_FP16_SPLIT) else "")),
               "flops_per_launch": flops_direct / max(direct_launches, 1),
               "launches_per_step": direct_launches,
               "traffic": DIRECT_TRAFFIC.get((args.config, args.prec))}]
@@ -469,7 +471,8 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {bse.BSE_FP32: "f32", bse.BSE_FP64: "f64", bse.BSE_BF16_SPLIT: "bf16x3"}[prec],
+        "dtype": {bse.BSE_FP32: "f32", bse.BSE_FP64: "f64", bse.BSE_BF16_SPLIT: "bf16x3",
+                  bse.BSE_FP16_SPLIT: "f16x3"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "name": args.config,
                    "irrep": "T1u" if tab["irrep_dim"][mu] == 3 else "bright mu=%d" % mu,
@@ -487,7 +490,11 @@ def run_ours(args, rank, world, local):
                                  bse.BSE_BF16_SPLIT: "pair densities FP32 on CUDA cores, dense contractions on "
                                                      "tcgen05 tensor cores with bf16 hi+lo operands (3 products) "
                                                      "and FP32 accumulation; diagonal, projection, exchange and "
-                                                     "eigensolver FP64"}[prec],
+                                                     "eigensolver FP64",
+                                 bse.BSE_FP16_SPLIT: "pair densities FP32 on CUDA cores, dense contractions on "
+                                                     "tcgen05 tensor cores with fp16 hi+lo operands scaled by "
+                                                     "powers of two (3 products) and FP32 accumulation; diagonal, "
+                                                     "projection, exchange and eigensolver FP64"}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},

@@ -57,11 +57,12 @@ enum {
 };
 
 /* precision of the direct term: FP64 throughout; FP32 CUDA-core arithmetic;
-   or BF16_SPLIT: pair densities in FP32 on CUDA cores and both dense
-   contractions (W(q) conj(rho_vv') and rho_cc'^T T) on the tensor cores with
-   every operand split into bf16 hi + lo and three products accumulated in
-   FP32.  The diagonal, the projection and the exchange stay FP64.
-   FP16_SPLIT is reserved. */
+   or BF16_SPLIT / FP16_SPLIT: pair densities in FP32 on CUDA cores and both
+   dense contractions (W(q) conj(rho_vv') and rho_cc'^T T) on the tensor cores
+   with every operand split into a 16-bit hi + lo pair (bf16: 2 x 8
+   significant bits; fp16: 2 x 11 bits, each operand scaled by an exact power
+   of two into fp16's range) and three products accumulated in FP32.  The
+   diagonal, the projection and the exchange stay FP64. */
 enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2, BSE_FP32 = 3 };
 
 /* terms of H to include (bit mask) */
@@ -172,9 +173,9 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  * once (Sec. III.C.5), the exchange term is applied in the projected form
  * (U_mu^dagger P) vbar (U_mu^dagger P)^dagger (Eq. v_scalar), the diagonal
  * eps_c - eps_v - W^div in FP64.  terms: BSE_TERM_* mask.
- * prec: BSE_FP64, BSE_FP32 or BSE_BF16_SPLIT (see the precision enum); the
- * split mode needs NG_max <= 64, nv <= 4 and nc <= 8 and returns
- * EUNSUPPORTED otherwise; FP16_SPLIT returns EUNSUPPORTED.  ETIMEOUT if a
+ * prec: BSE_FP64, BSE_FP32, BSE_BF16_SPLIT or BSE_FP16_SPLIT (see the
+ * precision enum); the split modes need NG_max <= 64, nv <= 4 and nc <= 8
+ * and return EUNSUPPORTED otherwise.  ETIMEOUT if a
  * bounded wait of the tensor-core kernel gave up (the context stays usable).
  * h_dev: device, complex128, column-major dim x dim with leading dimension
  * ld >= dim; the full Hermitian matrix is written.  irrep = BSE_IRREP_ALL

@@ -118,7 +118,9 @@ struct bse_ctx {
     DevBuf coef32, w32;  // FP32 copies for the FP32 build, made on first use
     bool narrow_ready = false;
     DevBuf wemb;         // split-precision W(q) embeddings for the tensor-core build
+    DevBuf wexp;         // their per-q scale exponents
     int wemb_ngp = 0;
+    int wemb_fp16 = -1;  // element type of wemb (1 fp16, 0 bf16)
     DevBuf groups, status;
     DevBuf dinst;        // the context's system as a direct-kernel instance
     // band rotations kept on the device for the rotated direct-term blocks (Eq. Wtrafo)
@@ -390,11 +392,13 @@ static int ensure_dipoles(bse_ctx* c) {
     return BSE_OK;
 }
 
-static int ensure_wemb(bse_ctx* c, int ngp) {
-    if (c->wemb_ngp == ngp) return BSE_OK;
+static int ensure_wemb(bse_ctx* c, int ngp, int fp16) {
+    if (c->wemb_ngp == ngp && c->wemb_fp16 == fp16) return BSE_OK;
     BSE_TRY(ensure(c->wemb, sizeof(uint16_t) * (size_t)c->t.nk * 2 * 128 * 2 * ngp));
-    BSE_TRY(launch_wemb(c->S, ngp, c->wemb.p, c->stream));
+    BSE_TRY(ensure(c->wexp, sizeof(int) * (size_t)c->t.nk));
+    BSE_TRY(launch_wemb(c->S, ngp, fp16, c->wemb.p, (int*)c->wexp.p, c->stream));
     c->wemb_ngp = ngp;
+    c->wemb_fp16 = fp16;
     return BSE_OK;
 }
 
@@ -773,7 +777,7 @@ static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
-                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->groups, &c->status,
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
                       &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots,
                       &c->lossScratch, &c->wsym, &c->wcand})
@@ -939,8 +943,9 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
 // the same X tiles with its own basis (Eqs. transformationU, Hblock).
 static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t prec, uint32_t terms,
                        void* const* h, const int64_t* ld) {
-    const int tcp = prec == BSE_BF16_SPLIT;
-    const int p32 = prec == BSE_FP32 || tcp;   // the tile arena is FP32 for both
+    const int tcp = prec == BSE_BF16_SPLIT || prec == BSE_FP16_SPLIT;
+    const int fp16 = prec == BSE_FP16_SPLIT;
+    const int p32 = prec == BSE_FP32 || tcp;   // the tile arena is FP32 for all three
     int ngp = 0;
     if (tcp && (terms & BSE_TERM_DIRECT)) {
         size_t sm = 0;
@@ -978,7 +983,7 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
     }
     if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
     if (tcp && (terms & BSE_TERM_DIRECT)) {
-        BSE_TRY(ensure_wemb(c, ngp));
+        BSE_TRY(ensure_wemb(c, ngp, fp16));
         BSE_TRY(ensure(c->status, sizeof(int)));
         BSE_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
     }
@@ -1028,7 +1033,8 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         BSE_TRY(upload(c->tiles, bt.tiles.data(), bt.tiles.size(), c->stream));
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
         if ((terms & BSE_TERM_DIRECT) && tcp) {
-            BSE_TRY(launch_direct_tc(c->S, c->coef32.p, c->wemb.p, ngp, (const PairTask*)c->tasks.p,
+            BSE_TRY(launch_direct_tc(c->S, fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ngp,
+                                     (const PairTask*)c->tasks.p,
                                      (const TcGroup*)c->groups.p, (int64_t)groups.size(), c->arenaX.p,
                                      (int*)c->status.p, c->stream));
         } else if (terms & BSE_TERM_DIRECT) {
@@ -1087,7 +1093,7 @@ int bse_build_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms, void* 
     if (!c) return fail(BSE_EINVAL, "null context");
     AllocStream alloc_on_(c->stream);
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT && prec != BSE_FP16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     if (mu == BSE_IRREP_ALL) {   // every block, packed one after another in irrep order
         std::vector<IrrepDev*> tg;
@@ -1113,7 +1119,7 @@ int bse_build_partner_block(bse_ctx* c, int32_t mu, int32_t prec, uint32_t terms
     if (!c) return fail(BSE_EINVAL, "null context");
     AllocStream alloc_on_(c->stream);
     if (!c || !h) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT && prec != BSE_FP16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     BSE_TRY(ensure_partner(c, mu));
     return build_generic(c, c->partner[mu].part[0], prec, terms, h, ld);
@@ -1125,7 +1131,7 @@ int bse_build_blocks(bse_ctx* c, int32_t n, const int32_t* irrep, const int32_t*
     if (!c) return fail(BSE_EINVAL, "null context");
     AllocStream alloc_on_(c->stream);
     if (!c || n < 0 || (n > 0 && (!irrep || !h || !ld))) return fail(BSE_EINVAL, "null argument");
-    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT)
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT && prec != BSE_FP16_SPLIT)
         return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     std::vector<IrrepDev*> tg;
     for (int32_t i = 0; i < n; ++i) {

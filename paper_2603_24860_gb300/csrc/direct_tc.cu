@@ -1,7 +1,12 @@
 // Direct term with the dense contractions on the 5th-generation tensor
 // cores (tcgen05), in split precision: every operand x is stored as
-// hi = bf16(x), lo = bf16(x - hi), and a product A B is formed as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in TMEM.
+// hi = e(x), lo = e(x - hi) in a 16-bit type e (bf16 or fp16), and a product
+// A B is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in
+// TMEM.  bf16 keeps FP32's exponent range with 2 x 8 significant bits; fp16
+// keeps 2 x 11 bits but overflows above 65504 and loses bits below 2^-14, so
+// every operand is scaled by a power of two that brings its largest element
+// to [2^13, 2^14): W(q) per q, the pair densities per k pair, T per CTA.  The
+// scales are exact and are divided out in the epilogue; both types use them.
 //
 //   rho_nn'(k,k';Q) = sum_{p'} conj(c_kn(p' + Q)) c_k'n'(p')   (CUDA cores, FP32; Eq. w_interaction)
 //   T = W(q) conj(rho_vv')         MMA1, all pairs of a group share W(q)
@@ -14,6 +19,7 @@
 // W(q) (hi and lo) is prepared once per q in the core-matrix layout and
 // brought in by one bulk copy that overlaps the pair densities.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -49,9 +55,45 @@ __host__ __device__ inline TcPlan tc_plan(int ngp, int nb, int nv, int nc, int n
     return p;
 }
 
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+// the 16-bit operand types: conversions and the instruction descriptor's type flag
+template <typename E>
+struct Elem;
+template <>
+struct Elem<__nv_bfloat16> {
+    static constexpr int kBf16 = 1;
+    static __device__ __forceinline__ __nv_bfloat16 from(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float to(__nv_bfloat16 x) { return __bfloat162float(x); }
+};
+template <>
+struct Elem<__half> {
+    static constexpr int kBf16 = 0;
+    static __device__ __forceinline__ __half from(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float to(__half x) { return __half2float(x); }
+};
+
+template <typename E>
+__device__ __forceinline__ void split16(float x, E& hi, E& lo) {
+    hi = Elem<E>::from(x);
+    lo = Elem<E>::from(x - Elem<E>::to(hi));
+}
+
+// exponent e with max_abs * 2^e in [2^13, 2^14) (0 for an all-zero operand), clamped to keep 2^e a normal float
+__device__ __forceinline__ int scale_exp(float max_abs) {
+    if (!(max_abs > 0.f)) return 0;
+    int e = 13 - ilogbf(max_abs);
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// 2^e for |e| <= 126, built from the exponent field (exact)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// block-wide maximum of a non-negative float (bit patterns of non-negative floats order like integers)
+__device__ __forceinline__ float block_max(float m, unsigned* s_slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(s_slot, __float_as_uint(m));
+    __syncthreads();
+    return __uint_as_float(*s_slot);
 }
 
 __device__ __forceinline__ void cmacc32(float2& acc, float2 a, float2 b) {   // acc += conj(a) * b
@@ -59,8 +101,9 @@ __device__ __forceinline__ void cmacc32(float2& acc, float2 a, float2 b) {   // 
     acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
 }
 
+template <typename E>
 __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float2* __restrict__ coef,
-                                                           const __nv_bfloat16* __restrict__ wemb,
+                                                           const E* __restrict__ wemb, const int* __restrict__ wexp,
                                                            const PairTask* __restrict__ tasks,
                                                            const TcGroup* __restrict__ groups, int ngp, float2* X,
                                                            int* status) {
@@ -84,6 +127,8 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
     const TcGroup grp = groups[blockIdx.x];
     const int q = grp.q, ng = S.ng[q];
+    __shared__ unsigned s_max;      // block maximum of an operand (float bits)
+    __shared__ int s_erho[kG];      // scale exponent of each pair's densities
     constexpr uint32_t kCols = 128;   // TMEM: MMA1 accumulator cols [0, 64), MMA2 [64, 128)
     constexpr long kSpin = 1l << 24;
 
@@ -108,6 +153,7 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     // ---- pair densities (CUDA cores, FP32) for every pair of the group ----
     for (int p = 0; p < grp.count; ++p) {
         const PairTask t = tasks[grp.first + p];
+        if (tid == 0) s_max = 0u;
         int fold[3];
         const int n3[3] = {S.n1, S.n2, S.n3};
 #pragma unroll
@@ -166,19 +212,25 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
             }
         }
         __syncthreads();
+        // one scale for all densities of the pair
+        float mx = 0.f;
+        for (int e = tid; e < ng * P; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(rho[e].x), fabsf(rho[e].y)));
+        const int erho = scale_exp(block_max(mx, &s_max));
+        const float srho = pow2f(erho);
+        if (tid == 0) s_erho[p] = erho;
         // B1 rows p*16 + vv' = [rho_r | rho_i] of rho_vv', and rho_cc' kept for MMA2
         unsigned char* B1h = Bm;
         unsigned char* B1l = Bm + b_half;
         for (int e = tid; e < nvv * ngp; e += blockDim.x) {
             const int vv = e / ngp, Q = e % ngp;
             float2 r = Q < ng ? rho[Q * P + ncc + vv] : make_float2(0.f, 0.f);
-            __nv_bfloat16 h, l;
-            split_bf16(r.x, h, l);
-            *(__nv_bfloat16*)(B1h + core_off(p * kNVV + vv, Q, K)) = h;
-            *(__nv_bfloat16*)(B1l + core_off(p * kNVV + vv, Q, K)) = l;
-            split_bf16(r.y, h, l);
-            *(__nv_bfloat16*)(B1h + core_off(p * kNVV + vv, ngp + Q, K)) = h;
-            *(__nv_bfloat16*)(B1l + core_off(p * kNVV + vv, ngp + Q, K)) = l;
+            E h, l;
+            split16(r.x * srho, h, l);
+            *(E*)(B1h + core_off(p * kNVV + vv, Q, K)) = h;
+            *(E*)(B1l + core_off(p * kNVV + vv, Q, K)) = l;
+            split16(r.y * srho, h, l);
+            *(E*)(B1h + core_off(p * kNVV + vv, ngp + Q, K)) = h;
+            *(E*)(B1l + core_off(p * kNVV + vv, ngp + Q, K)) = l;
         }
         for (int e = tid; e < ncc * ngp; e += blockDim.x) {
             const int cc = e / ngp, Q = e % ngp;
@@ -187,13 +239,14 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         __syncthreads();
     }
 
+    if (tid == 0) s_max = 0u;   // read only after the barriers below
     // ---- MMA1: T = W(q) conj(rho_vv') for all pairs (N = 16 * kG) ----
     bool ok = __syncthreads_and(tc::mbar_wait(&mbar[0], 0, kSpin)) != 0;
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t idesc1 = tc::idesc_f16(128, kNVV * kG, 1);
+    const uint32_t idesc1 = tc::idesc_f16(128, kNVV * kG, Elem<E>::kBf16);
     const uint32_t lbo = 128, sbo = (uint32_t)(K / 8) * 128;
     if (tid == 0 && ok) {
         const uint32_t a0 = tc::smem_u32(A1), b0 = tc::smem_u32(Bm);
@@ -208,28 +261,37 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     }
     ok = __syncthreads_and(ok && tc::mbar_wait(&mbar[1], 0, kSpin)) != 0;
     tc::fence_after();
-    // ---- T: TMEM -> split -> B2 (rows p*16 + vv', K index = row of T) ----
+    // ---- T: TMEM -> scale -> split -> B2 (rows p*16 + vv', K index = row of T) ----
+    int eT = 0;
     if (ok) {
+        constexpr int kHalf = kNVV * kG / 2;
         const int row = 32 * (warp & 3) + lane;                 // row of T = K index of B2
-        const int c0 = (warp >> 2) * (kNVV * kG / 2);           // warps 4..7 take the upper columns
-        for (int cb = c0; cb < c0 + kNVV * kG / 2; cb += 8) {
-            float v[8];
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
-            if (row < K) {
+        const int c0 = (warp >> 2) * kHalf;                     // warps 4..7 take the upper columns
+        float v[kHalf];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    __nv_bfloat16 h, l;
-                    split_bf16(v[j], h, l);
-                    *(__nv_bfloat16*)(Bm + core_off(cb + j, row, K)) = h;
-                    *(__nv_bfloat16*)(Bm + b_half + core_off(cb + j, row, K)) = l;
-                }
+        for (int cb = 0; cb < kHalf; cb += 8)
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cb), v + cb);
+        float mx = 0.f;
+        if (row < K)
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j) mx = fmaxf(mx, fabsf(v[j]));
+        eT = scale_exp(block_max(mx, &s_max));
+        const float sT = pow2f(eT);
+        if (row < K) {
+#pragma unroll
+            for (int j = 0; j < kHalf; ++j) {
+                E h, l;
+                split16(v[j] * sT, h, l);
+                *(E*)(Bm + core_off(c0 + j, row, K)) = h;
+                *(E*)(Bm + b_half + core_off(c0 + j, row, K)) = l;
             }
         }
     }
     // ---- MMA2 per pair: K^d = rho_cc'^T T ----
-    const uint32_t idesc2 = tc::idesc_f16(128, kNVV, 1);
+    const uint32_t idesc2 = tc::idesc_f16(128, kNVV, Elem<E>::kBf16);
     for (int p = 0; p < grp.count && ok; ++p) {
         const float2* rc = RC + (size_t)p * ncc * ngp;
+        const float srho = pow2f(s_erho[p]);
         for (int e = tid; e < 128 * ngp; e += blockDim.x) {
             const int m = e / ngp, Q = e % ngp;
             float re = 0.f, re2 = 0.f;   // values at k = Q and k = ngp + Q
@@ -242,13 +304,13 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
                 re = r.y;
                 re2 = r.x;
             }
-            __nv_bfloat16 h, l;
-            split_bf16(re, h, l);
-            *(__nv_bfloat16*)(A2 + core_off(m, Q, K)) = h;
-            *(__nv_bfloat16*)(A2 + a_half + core_off(m, Q, K)) = l;
-            split_bf16(re2, h, l);
-            *(__nv_bfloat16*)(A2 + core_off(m, ngp + Q, K)) = h;
-            *(__nv_bfloat16*)(A2 + a_half + core_off(m, ngp + Q, K)) = l;
+            E h, l;
+            split16(re * srho, h, l);
+            *(E*)(A2 + core_off(m, Q, K)) = h;
+            *(E*)(A2 + a_half + core_off(m, Q, K)) = l;
+            split16(re2 * srho, h, l);
+            *(E*)(A2 + core_off(m, ngp + Q, K)) = h;
+            *(E*)(A2 + a_half + core_off(m, ngp + Q, K)) = l;
         }
         tc::fence_proxy_async();
         tc::fence_before();
@@ -284,9 +346,10 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     __syncthreads();
     if (ok) {
         const int B = nv * nc;
-        const float scale = (float)(-S.inv_vol);
         for (int p = 0; p < grp.count; ++p) {
             const PairTask t = tasks[grp.first + p];
+            // K^d = acc / (2^eW 2^(2 erho) 2^eT) and the factor -1/V
+            const float scale = ldexpf((float)(-S.inv_vol), -(wexp[q] + 2 * s_erho[p] + eT));
             float2* Xt = X + t.xoff;
             for (int e = tid; e < B * B; e += blockDim.x) {
                 const int r = e % B, col = e / B;
@@ -304,9 +367,27 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
-// W(q) real embedding in the core-matrix layout, hi then lo, zero padded;
-// at q = 0 the head and wings are dropped.
-__global__ void wemb_kernel(DevSys S, int ngp, __nv_bfloat16* out) {
+// per q: the exponent that brings max |Re W|, |Im W| (head and wings dropped at q = 0) to [2^13, 2^14)
+__global__ void wexp_kernel(DevSys S, int* wexp) {
+    __shared__ unsigned s_max;
+    const int q = blockIdx.x, ng = S.ng[q];
+    if (threadIdx.x == 0) s_max = 0u;
+    __syncthreads();
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < ng * ng; e += blockDim.x) {
+        const int Q = e / ng, Qp = e % ng;
+        if (q == 0 && (Q == S.g0 || Qp == S.g0)) continue;
+        const double2 w = S.w[((int64_t)q * S.ng_max + Q) * S.ng_max + Qp];
+        mx = fmaxf(mx, (float)fmax(fabs(w.x), fabs(w.y)));
+    }
+    const int e = scale_exp(block_max(mx, &s_max));
+    if (threadIdx.x == 0) wexp[q] = e;
+}
+
+// W(q) 2^wexp[q] as a real embedding in the core-matrix layout, hi then lo,
+// zero padded; at q = 0 the head and wings are dropped.
+template <typename E>
+__global__ void wemb_kernel(DevSys S, int ngp, const int* __restrict__ wexp, E* out) {
     const int K = 2 * ngp;
     const int64_t per = (int64_t)128 * K;
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,13 +401,13 @@ __global__ void wemb_kernel(DevSys S, int ngp, __nv_bfloat16* out) {
         double2 w = S.w[((int64_t)q * S.ng_max + Q) * S.ng_max + Qp];
         // [[Wr, Wi], [Wi, -Wr]]
         double x = (m < ngp) ? (k < ngp ? w.x : w.y) : (k < ngp ? w.y : -w.x);
-        v = (float)x;
+        v = (float)ldexp(x, wexp[q]);
     }
-    __nv_bfloat16 h, l;
-    split_bf16(v, h, l);
-    __nv_bfloat16* base = out + (int64_t)q * 2 * per;
-    *(__nv_bfloat16*)((unsigned char*)base + core_off(m, k, K)) = h;
-    *(__nv_bfloat16*)((unsigned char*)(base + per) + core_off(m, k, K)) = l;
+    E h, l;
+    split16(v, h, l);
+    E* base = out + (int64_t)q * 2 * per;
+    *(E*)((unsigned char*)base + core_off(m, k, K)) = h;
+    *(E*)((unsigned char*)(base + per) + core_off(m, k, K)) = l;
 }
 
 int tc_supported(const DevSys& s, int& ngp, size_t& smem) {
@@ -340,32 +421,48 @@ int tc_supported(const DevSys& s, int& ngp, size_t& smem) {
     return BSE_OK;
 }
 
-int launch_wemb(const DevSys& s, int ngp, void* out, cudaStream_t st) {
-    int64_t n = (int64_t)s.nk * 128 * 2 * ngp;
-    wemb_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, ngp, (__nv_bfloat16*)out);
+int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st) {
+    wexp_kernel<<<(unsigned)s.nk, 256, 0, st>>>(s, wexp);
     note_launch();
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "wexp launch: %s", cudaGetErrorString(e));
+    int64_t n = (int64_t)s.nk * 128 * 2 * ngp;
+    if (fp16)
+        wemb_kernel<__half><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, ngp, wexp, (__half*)out);
+    else
+        wemb_kernel<__nv_bfloat16><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, ngp, wexp, (__nv_bfloat16*)out);
+    note_launch();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail(BSE_ECUDA, "wemb launch: %s", cudaGetErrorString(e));
     return BSE_OK;
 }
 
-int launch_direct_tc(const DevSys& s, const void* coef32, const void* wemb, int ngp, const PairTask* tasks,
-                     const TcGroup* groups, int64_t ngroups, void* X, int* status, cudaStream_t st) {
-    if (ngroups == 0) return BSE_OK;
+template <typename E>
+static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* wemb, const int* wexp, int ngp,
+                              const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
+                              cudaStream_t st) {
     int ngp2;
     size_t sm;
     BSE_TRY(tc_supported(s, ngp2, sm));
-    cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc smem %zu: %s", sm, cudaGetErrorString(e));
     for (int64_t off = 0; off < ngroups; off += 1 << 30) {
         int64_t n = ngroups - off < (1 << 30) ? ngroups - off : (1 << 30);
-        direct_tc_kernel<<<(unsigned)n, 256, sm, st>>>(s, (const float2*)coef32, (const __nv_bfloat16*)wemb, tasks,
-                                                      groups + off, ngp, (float2*)X, status);
+        direct_tc_kernel<E><<<(unsigned)n, 256, sm, st>>>(s, (const float2*)coef32, (const E*)wemb, wexp, tasks,
+                                                          groups + off, ngp, (float2*)X, status);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc launch: %s", cudaGetErrorString(e));
     }
     return BSE_OK;
+}
+
+int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
+                     const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
+                     cudaStream_t st) {
+    if (ngroups == 0) return BSE_OK;
+    return fp16 ? launch_direct_tc_t<__half>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st)
+                : launch_direct_tc_t<__nv_bfloat16>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st);
 }
 
 }  // namespace bse

@@ -214,9 +214,11 @@ int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int6
 void note_launch();
 // split-precision tensor-core direct term (direct_tc.cu)
 int tc_supported(const DevSys& s, int& ngp, size_t& smem);
-int launch_wemb(const DevSys& s, int ngp, void* out, cudaStream_t st);
-int launch_direct_tc(const DevSys& s, const void* coef32, const void* wemb, int ngp, const PairTask* tasks,
-                     const TcGroup* groups, int64_t ngroups, void* X, int* status, cudaStream_t st);
+// split-precision W(q) embeddings (fp16 != 0: fp16 hi + lo, else bf16) and their per-q scale exponents
+int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st);
+int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
+                     const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
+                     cudaStream_t st);
 int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
 int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
                          double2* H, int64_t ld, cudaStream_t st);

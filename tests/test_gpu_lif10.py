@@ -1,6 +1,6 @@
 """Full-size checks for the LiF-like rocksalt 10x10x10 mesh (Nv = 3, Nc = 6,
 N = 18000): the blocks of all ten irreps of Oh from one build (one direct
-pass shared by every block), in FP64 and FP32.  Their dimensions add up to
+pass shared by every block), in FP64, FP32 and both split precisions.  Their dimensions add up to
 N; sampled star-pair sub-blocks of every irrep are compared with the oracle
 (its canonical basis restricted to the two stars, U_a^dagger H_ab U_b); the
 FP32 exciton energies of every block agree with the FP64 ones within
@@ -94,6 +94,25 @@ def test_fp32_levels_within_0p1_mev(lif10):
         e64 = torch.linalg.eigvalsh(h64[mu]).cpu().numpy()
         e32 = torch.linalg.eigvalsh(h32[mu]).cpu().numpy()
         assert np.abs(e32 - e64).max() * HA_MEV <= 0.1, mu
+
+
+@pytest.mark.parametrize("split", ["BSE_FP16_SPLIT", "BSE_BF16_SPLIT"])
+def test_split_blocks_within_0p1_mev(lif10, split):
+    """All ten blocks from one split-precision build (tensor-core direct
+    term): elements within the split mode's tolerance of the FP64 blocks and
+    exciton energies within 0.1 meV."""
+    bse, torch, ctx, t, h64, *_ = lif10
+    tol = {"BSE_FP16_SPLIT": 4e-6, "BSE_BF16_SPLIT": 2e-5}[split]
+    hs = bse.blocks(ctx, prec=getattr(bse, split))
+    for mu in range(len(h64)):
+        if h64[mu].shape[0] == 0:
+            continue
+        err = (hs[mu] - h64[mu]).abs().max().item() / h64[mu].abs().max().item()
+        assert err <= tol, (mu, err)
+        e64 = torch.linalg.eigvalsh(h64[mu]).cpu().numpy()
+        es = torch.linalg.eigvalsh(hs[mu]).cpu().numpy()
+        assert np.abs(es - e64).max() * HA_MEV <= 0.1, mu
+    del hs
 
 
 def test_levels_of_every_block(lif10):

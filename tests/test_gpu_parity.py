@@ -289,14 +289,20 @@ def test_partner_unsupported_irrep(gpu):
     assert e.value.code == bse.BSE_EUNSUPPORTED
 
 
-# --- BF16-split tensor-core direct term (tcgen05), FP32 accumulation ---
-TOLBF = 2e-5          # H_mu elements relative to the largest element
+# --- split-precision tensor-core direct term (tcgen05), FP32 accumulation ---
+# H_mu elements relative to the largest element: bf16 hi + lo keeps about 16
+# significant bits of every operand, fp16 hi + lo about 22 (the pair densities
+# themselves are FP32), so fp16 split sits near the FP32 path.
+SPLIT = {"bf16": ("BSE_BF16_SPLIT", 2e-5, 2e-4), "fp16": ("BSE_FP16_SPLIT", 4e-6, 2e-5)}
 
 
+@pytest.mark.parametrize("split", ["bf16", "fp16"])
 @pytest.mark.parametrize("name", ["si2", "si4", "lif4"])
-def test_blocks_bf16_split(gpu, name):
+def test_blocks_split(gpu, name, split):
     from oracle.projection import PartnerBasis, project
     bse, torch, get = gpu
+    prec, tol, _ = SPLIT[split]
+    prec = getattr(bse, prec)
     d, inp, grp, mt, b = oracle_case(name)
     H = oracle_h(name)
     for mu in b.bright():
@@ -304,33 +310,69 @@ def test_blocks_bf16_split(gpu, name):
         if U.shape[1] == 0:
             continue
         ref = project(U, H)
-        got = bse.block(get(name), mu, prec=bse.BSE_BF16_SPLIT).cpu().numpy()
-        assert _rel(got, ref) <= TOLBF, (name, mu, _rel(got, ref))
+        got = bse.block(get(name), mu, prec=prec).cpu().numpy()
+        assert _rel(got, ref) <= tol, (name, mu, _rel(got, ref))
         assert np.abs(np.linalg.eigvalsh(got) - np.linalg.eigvalsh(ref)).max() * HA_MEV <= 0.1
         pb = PartnerBasis(b, mu)
         ref1 = pb.U[0].conj().T @ H @ pb.U[0]
-        got1 = bse.partner_block(get(name), mu, prec=bse.BSE_BF16_SPLIT).cpu().numpy()
-        assert _rel(got1, ref1) <= TOLBF
+        got1 = bse.partner_block(get(name), mu, prec=prec).cpu().numpy()
+        assert _rel(got1, ref1) <= tol
 
 
-def test_bf16_split_direct_term_only(gpu):
-    """The split mode changes only the direct term."""
+@pytest.mark.parametrize("split", ["bf16", "fp16"])
+def test_split_direct_term_only(gpu, split):
+    """The split modes change only the direct term."""
     from oracle.projection import project
     bse, torch, get = gpu
+    prec, _, tol = SPLIT[split]
     d, inp, grp, mt, b = oracle_case("si4")
     mu = b.bright()[0]
     ref = project(b.basis(mu)[0], oracle_h("si4", "w"))
-    got = bse.block(get("si4"), mu, prec=bse.BSE_BF16_SPLIT, terms=4).cpu().numpy()
-    assert _rel(got, ref) <= 2e-4      # relative to the largest element of K^d alone
+    got = bse.block(get("si4"), mu, prec=getattr(bse, prec), terms=4).cpu().numpy()
+    assert _rel(got, ref) <= tol      # relative to the largest element of K^d alone
 
 
-def test_bf16_split_rejects_large_spheres(gpu):
+def test_fp16_split_more_accurate_than_bf16(gpu):
+    """fp16 hi + lo carries 22 significant bits against bf16's 16, so its
+    K^d is closer to the oracle's."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case("lif4")
+    mu = b.bright()[0]
+    ref = project(b.basis(mu)[0], oracle_h("lif4", "w"))
+    e16 = _rel(bse.block(get("lif4"), mu, prec=bse.BSE_FP16_SPLIT, terms=4).cpu().numpy(), ref)
+    ebf = _rel(bse.block(get("lif4"), mu, prec=bse.BSE_BF16_SPLIT, terms=4).cpu().numpy(), ref)
+    assert e16 < 0.25 * ebf, (e16, ebf)
+
+
+def test_split_scales_are_exact(gpu):
+    """The fp16 operands are scaled by powers of two: W(q) multiplied by 2^20
+    (far outside fp16's range before scaling) gives K^d multiplied by 2^20
+    to rounding, and the build stays finite."""
+    from synth import generate
+    bse, torch, get = gpu
+    d = dict(generate("si2"))
+    t = bse.bse_tables(get("si2"))
+    mu = int(np.nonzero(t["bright"])[0][0])
+    ref = bse.block(get("si2"), mu, prec=bse.BSE_FP64, terms=4).cpu().numpy()
+    d["w"] = np.asarray(d["w"]) * 2.0 ** 20
+    ctx = bse.bse_create(d, stream=torch.cuda.current_stream())
+    try:
+        got = bse.block(ctx, mu, prec=bse.BSE_FP16_SPLIT, terms=4).cpu().numpy()
+    finally:
+        bse.bse_destroy(ctx)
+    assert np.all(np.isfinite(got))
+    assert _rel(got * 2.0 ** -20, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("split", ["BSE_BF16_SPLIT", "BSE_FP16_SPLIT"])
+def test_split_rejects_large_spheres(gpu, split):
     bse, torch, get = gpu
     t = bse.bse_tables(get("mos2_331"))
     mu = int(np.nonzero(t["bright"])[0][0])
     buf = torch.empty(max(int(t["block_dim"][mu]) ** 2, 1), dtype=torch.complex128, device="cuda")
     with pytest.raises(bse.BseError) as e:
-        bse.bse_build_block(get("mos2_331"), mu, bse.BSE_BF16_SPLIT, bse.BSE_TERM_ALL, buf,
+        bse.bse_build_block(get("mos2_331"), mu, getattr(bse, split), bse.BSE_TERM_ALL, buf,
                             max(int(t["block_dim"][mu]), 1))
     assert e.value.code == bse.BSE_EUNSUPPORTED
 

@@ -113,11 +113,12 @@ def test_partner_block_levels(built):
     assert np.linalg.norm(im1 - im) <= 1e-9 * np.linalg.norm(im)
 
 
-def test_bf16_split_build_within_0p1_mev(built):
+@pytest.mark.parametrize("split", ["BSE_BF16_SPLIT", "BSE_FP16_SPLIT"])
+def test_split_build_within_0p1_mev(built, split):
     """Tensor-core split-precision direct term vs the FP64 build."""
     bse, torch, ctx, t, mu, h = built
     d, inp, grp, mt, b = oracle_case("si8")
-    hb = bse.block(ctx, mu, prec=bse.BSE_BF16_SPLIT)
+    hb = bse.block(ctx, mu, prec=getattr(bse, split))
     h64 = torch.tensor(h, device="cuda").T.contiguous().T
     omega = torch.tensor(d["omega"], device="cuda")
     om64, osc64, im64 = (x.cpu().numpy() for x in bse.spectrum(ctx, mu, h64, omega, d["eta"]))
