@@ -156,14 +156,94 @@ def partner_irrep_matrices(grp, chi_mu, d):
     return np.einsum("ai,sab,bj->sij", E, grp.cart, E)
 
 
+def commutant_seed(n: int) -> np.ndarray:
+    """A fixed symmetric n x n matrix with generic entries from the
+    two-dimensional Kronecker sequence with the generalised golden ratios
+    (g1, g2) = (0.7548776662466927, 0.5698402909980532):
+    X_ab = frac(g1 (a+1) + g2 (b+1)) + frac(g1 (b+1) + g2 (a+1)) - 1.
+    Any generic symmetric matrix serves; this one is reproducible."""
+    g1, g2 = 0.7548776662466927, 0.5698402909980532
+    a = np.arange(1, n + 1, dtype=np.float64)
+    x = g1 * a[:, None] + g2 * a[None, :]
+    y = x - np.floor(x)
+    return y + y.T - 1.0
+
+
+def _gram_schmidt(cols, keep, tol):
+    """Modified Gram-Schmidt (two passes) over the given columns in order,
+    keeping a vector when its residual norm exceeds tol, at most `keep`."""
+    acc = []
+    for x in cols:
+        x = np.array(x, dtype=np.float64)
+        for _ in range(2):
+            for u in acc:
+                x = x - u * (u @ x)
+        nrm = np.linalg.norm(x)
+        if nrm > tol:
+            acc.append(x / nrm)
+        if len(acc) == keep:
+            break
+    return np.array(acc).T
+
+
+def regular_irrep_matrices(grp, chi_mu, d):
+    """Real orthogonal matrices of a d-dimensional irrep with real characters
+    from the left regular representation R(s) e_b = e_{sb} (|S| x |S|):
+      1. P = d/|S| sum_s chi(s) R(s), i.e. P_ab = d/|S| chi(a b^-1), projects
+         onto the d copies of the irrep; B = Gram-Schmidt over its columns
+         (d^2 of them survive);
+      2. C = sum_s R(s) X R(s)^T with X = commutant_seed commutes with every
+         R(s), so on range(P) it acts on the multiplicity space only; its
+         eigenspaces there are single copies of the irrep, d-fold each;
+      3. the lowest one, E = B Y, is made canonical through its projector
+         Q = E E^T: Gram-Schmidt over Q e_0, Q e_1, ... gives E';
+      4. Gamma(s) = E'^T R(s) E'.
+    Raises ValueError when the lowest eigenspace is not separated."""
+    G = grp.n
+    chi = np.asarray(chi_mu, dtype=np.float64)
+    P = d / G * chi[grp.mult[np.arange(G)[:, None], grp.inverse[None, :]]]
+    B = _gram_schmidt(P.T, d * d, 1e-6)
+    if B.shape[1] != d * d:
+        raise ValueError("projector rank is not d^2")
+    X = commutant_seed(G)
+    C = np.zeros((G, G))
+    for s in range(G):
+        pinv = grp.mult[grp.inverse[s]]            # a -> s^-1 a
+        C += X[np.ix_(pinv, pinv)]
+    w, Y = np.linalg.eigh(B.T @ C @ B)
+    if not w[d] - w[d - 1] > 1e-8 * max(abs(w).max(), 1.0):
+        raise ValueError("degenerate commutant spectrum")
+    E = B @ Y[:, :d]
+    Q = E @ E.T
+    Ec = _gram_schmidt(Q.T, d, 1e-6)
+    gam = np.empty((G, d, d))
+    for s in range(G):
+        gam[s] = Ec[grp.mult[s]].T @ Ec                 # sum_b E'(sb, i) E'(b, j)
+    return gam
+
+
+def irrep_matrices(grp, chi_mu, d):
+    """Real orthogonal matrices Gamma_mu(s) of an irrep: by the Cartesian
+    route (partner_irrep_matrices) when the irrep is contained once in the
+    polar-vector representation, chi itself when d = 1, otherwise from the
+    regular representation (regular_irrep_matrices)."""
+    try:
+        return partner_irrep_matrices(grp, chi_mu, d)
+    except ValueError:
+        pass
+    if d == 1:
+        return np.asarray(chi_mu, dtype=np.float64).reshape(-1, 1, 1)
+    return regular_irrep_matrices(grp, chi_mu, d)
+
+
 class PartnerBasis:
-    """Canonical basis of partner 1 of a bright irrep and its transfers."""
+    """Canonical basis of partner 1 of an irrep and its transfers."""
 
     def __init__(self, basis: Basis, mu: int):
         self.b = basis
         grp = basis.grp
         self.d = int(basis.dims[mu])
-        self.gam = partner_irrep_matrices(grp, basis.chi[mu], self.d)
+        self.gam = irrep_matrices(grp, basis.chi[mu], self.d)
         n = basis.inp.N
         self.P = [[sum(self.d / grp.n * np.conj(self.gam[s, i, j]) * basis.reps[s] for s in range(grp.n))
                    for j in range(self.d)] for i in range(self.d)]

@@ -10,14 +10,45 @@ from oracle import spectrum as spc
 
 @pytest.mark.parametrize("name", ["si2", "mos2_331"])
 def test_irrep_matrices_are_a_representation(name):
+    """Every irrep's matrices: a representation with trace chi, and Schur's
+    orthogonality relations across all irreps,
+    sum_s Gamma^mu_ij(s) Gamma^nu_kl(s) = |S|/d delta_mu,nu delta_ik delta_jl
+    (which also makes each one irreducible and orthogonal)."""
     d, inp, grp, mt, b = oracle_case(name)
-    for mu in b.bright():
-        dm = int(b.dims[mu])
-        g = pj.partner_irrep_matrices(grp, b.chi[mu], dm)
+    gams = [pj.irrep_matrices(grp, b.chi[mu], int(b.dims[mu])) for mu in range(len(b.dims))]
+    for mu, g in enumerate(gams):
         assert np.allclose(np.trace(g, axis1=1, axis2=2), b.chi[mu], atol=1e-12)
         for s1 in range(grp.n):
             for s2 in range(grp.n):
                 assert np.allclose(g[s1] @ g[s2], g[grp.mult[s1, s2]], atol=1e-12)
+    for mu, g in enumerate(gams):
+        for nu, h in enumerate(gams):
+            got = np.einsum("sij,skl->ijkl", g, h)
+            want = 0.0
+            if mu == nu:
+                dm = g.shape[1]
+                want = grp.n / dm * np.einsum("ik,jl->ijkl", np.eye(dm), np.eye(dm))
+            assert np.abs(got - want).max() < 1e-11, (mu, nu)
+
+
+@pytest.mark.parametrize("name", ["si2", "mos2_331"])
+def test_regular_route_equivalent_to_cartesian(name):
+    """For the polar-vector irreps both routes give equivalent real
+    representations: M = sum_s Gamma_reg(s) Gamma_cart(s)^T intertwines them
+    and is a multiple of an orthogonal matrix (Schur's lemma)."""
+    d, inp, grp, mt, b = oracle_case(name)
+    for mu in b.bright():
+        dm = int(b.dims[mu])
+        if dm == 1:
+            continue
+        gc = pj.partner_irrep_matrices(grp, b.chi[mu], dm)
+        gr = pj.regular_irrep_matrices(grp, b.chi[mu], dm)
+        M = np.einsum("sij,skj->ik", gr, gc)
+        c = np.trace(M @ M.T) / dm
+        assert c > 1e-6
+        assert np.abs(M @ M.T - c * np.eye(dm)).max() < 1e-11 * c
+        for s in range(grp.n):
+            assert np.allclose(gr[s] @ M, M @ gc[s], atol=1e-11)
 
 
 @pytest.mark.parametrize("name", ["si2", "si4", "mos2_331"])
@@ -25,7 +56,7 @@ def test_partner_blocks(name):
     d, inp, grp, mt, b = oracle_case(name)
     H = oracle_h(name) if name != "si2" else __import__("oracle.hamiltonian", fromlist=["x"]).full_hamiltonian(
         inp, mt, w_div=0.01)
-    for mu in b.bright():
+    for mu in range(len(b.dims)):   # every irrep: Cartesian, one-dimensional and regular-route matrices
         pb = pj.PartnerBasis(b, mu)
         U, _ = b.basis(mu)
         n1 = pb.U[0].shape[1]
