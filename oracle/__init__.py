@@ -16,6 +16,10 @@ all-electron Bethe-Salpeter implementation using crystal symmetries":
                     projection, transformationU)
   * spectrum      - block eigensolution, oscillator strengths, Im eps_M
                     (Eqs. macro_diel, reducible_polar, oscillatorA, oscillator)
+  * loss          - longitudinal excitons and the loss spectrum (Eqs. secular,
+                    eigenvec_xi, epsinv_div)
+  * haydock       - Lanczos-Haydock spectrum of a block (Sec. IV): Lanczos
+                    recurrence and continued fraction
 
 Functions whose result has no independent pin say "parity unpinned" in their
 docstring.  At present every function has at least one pin in tests/.
