@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="approximate size of the oracle sample (CPU seconds)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--haydock-steps", type=int, default=150,
+                   help="Lanczos-Haydock steps of the side measurement on the bright block (0: skip)")
     p.add_argument("--profile", action="store_true",
                    help="run exactly one step (no warm-up, no end-to-end leg) for profiler captures")
     return p.parse_args()
@@ -288,10 +290,10 @@ def run_ours(args, rank, world, local):
     mu = int(np.nonzero(tab["bright"])[0][0])
     partner = args.block == "partner"
     if args.block == "all":
-        # every irrep; an irrep contained once in the polar-vector representation through its
-        # partner block (same levels, each once, and the same spectrum)
+        # every irrep; a multi-dimensional irrep through its partner block (its distinct levels,
+        # each once, and the same spectrum), a one-dimensional one whole
         targets = [m for m in range(int(tab["n_irreps"])) if tab["block_dim"][m] > 0]
-        pflags = [int(tab["partner_dim"][m] > 0) for m in targets]
+        pflags = [int(tab["partner_dim"][m] > 0 and tab["irrep_dim"][m] > 1) for m in targets]
     else:
         targets = [mu]
         pflags = [int(partner)]
@@ -359,9 +361,41 @@ def run_ours(args, rank, world, local):
             bse.bse_destroy(ctx)
         return per, stats
 
-    if args.profile:
+    # Lanczos-Haydock spectrum of the bright block (side measurement, Sec. IV): its time on the
+    # launching stream and its distance to the exact spectrum of the same block
+    def haydock_measure(reps, exact_ms):
+        if dims[ib] == 0:
+            return None
+        ctx = bse.bse_create(inp, stream=stream, device=devin)
+        bse.bse_build_blocks(ctx, targets, pflags, prec, bse.BSE_TERM_ALL, Hs, dims)
+        pf, n = pflags[ib], dims[ib]
+        (bse.bse_partner_spectrum if pf else bse.bse_block_spectrum)(ctx, mu, Hs[ib], n, omega, eta, oms[ib],
+                                                                      oscs[ib], ims[ib])
+        exact = ims[ib].cpu().numpy().copy()
+        hs = min(args.haydock_steps, n)
+        rz = torch.empty(hs, dtype=torch.float64, device=dev)
+        wt = torch.empty(hs, dtype=torch.float64, device=dev)
+        imh = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
+        k = bse.bse_block_spectrum_lanczos(ctx, mu, pf, Hs[ib], n, hs, omega, eta, rz, wt, imh)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            k = bse.bse_block_spectrum_lanczos(ctx, mu, pf, Hs[ib], n, hs, omega, eta, rz, wt, imh)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        bse.bse_destroy(ctx)
+        return {"steps": k, "block_dim": n, "ms": statistics.median(ts) if ts else None,
+                "spectrum_rel_l2_vs_exact": float(np.linalg.norm(imh.cpu().numpy() - exact) / np.linalg.norm(exact)),
+                "exact_eigensolve_ms": exact_ms}
+
+    if args.profile:   # one step, then one Lanczos-Haydock spectrum of the bright block
         per, stats = timed(1)
-        return {"profile": args.config, "ms": per[0], "stage_ms": stats[0][0], "block_dim": dim}
+        hay = haydock_measure(0, stats[0][1]["ms_eig"]) if args.haydock_steps > 0 else None
+        return {"profile": args.config, "ms": per[0], "stage_ms": stats[0][0], "block_dim": dim, "haydock": hay}
     _, warm = timed(args.warmup)
     uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     sampler = ClockSampler(uuid)
@@ -411,6 +445,7 @@ def run_ours(args, rank, world, local):
                "max_dOmega_meV": float(np.abs(om_main - om64).max() * HA_MEV),
                "max_dOmega_meV_all_blocks": dall * HA_MEV,
                "spectrum_rel_l2": float(np.linalg.norm(im_main - im64) / np.linalg.norm(im64))}
+    hay = haydock_measure(3, statistics.mean(s[1]["ms_eig"] for s in stats)) if args.haydock_steps > 0 else None
     ms_direct = statistics.mean(s[0]["ms_direct"] for s in stats)
     ms_rotate = statistics.mean(s[0]["ms_rotate"] for s in stats)
     ms_project = statistics.mean(s[0]["ms_project"] for s in stats)
@@ -517,6 +552,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof_main,
         "roofline_kernels": roofs,
         "fp64_build": cmp,
+        "haydock": hay,
         "e2e": {"value": flops_build_all * args.steps * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
@@ -578,7 +614,8 @@ def run_batch(args, rank, world, local):
     stream = torch.cuda.current_stream()
     cfgs = batch_configs()
     inputs = [generate(c) for c in cfgs]
-    prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64}[args.prec]
+    prec = {"fp32": bse.BSE_FP32, "fp64": bse.BSE_FP64, "bf16": bse.BSE_BF16_SPLIT,
+            "fp16": bse.BSE_FP16_SPLIT}[args.prec]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctxs = [bse.bse_create(d, stream=stream) for d in inputs]
@@ -638,7 +675,8 @@ def run_batch(args, rank, world, local):
         "value": flops * args.steps * world / (total_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {bse.BSE_FP32: "f32", bse.BSE_FP64: "f64"}[prec], "data": "synthetic",
+        "dtype": {bse.BSE_FP32: "f32", bse.BSE_FP64: "f64", bse.BSE_BF16_SPLIT: "bf16x3",
+                  bse.BSE_FP16_SPLIT: "f16x3"}[prec], "data": "synthetic",
         "config": {"workload": "32 seeded instances: 22 MoS2-like D6h cells (9x9x1 to 18x18x3, Nv, Nc in 2..6, "
                                "|G| <= 1.86 (2pi/a)) and 10 Si-like Oh cells (4^3 to 7^3); the partner block of "
                                "each instance's optically active irrep",

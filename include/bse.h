@@ -174,8 +174,9 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  * (U_mu^dagger P) vbar (U_mu^dagger P)^dagger (Eq. v_scalar), the diagonal
  * eps_c - eps_v - W^div in FP64.  terms: BSE_TERM_* mask.
  * prec: BSE_FP64, BSE_FP32, BSE_BF16_SPLIT or BSE_FP16_SPLIT (see the
- * precision enum); the split modes need NG_max <= 64, nv <= 4 and nc <= 8
- * and return EUNSUPPORTED otherwise.  ETIMEOUT if a
+ * precision enum); the split modes need NG_max <= 128, nv <= 8, nc <= 8 and
+ * their operands within 227 KB of shared memory per CTA, and return
+ * EUNSUPPORTED otherwise.  ETIMEOUT if a
  * bounded wait of the tensor-core kernel gave up (the context stays usable).
  * h_dev: device, complex128, column-major dim x dim with leading dimension
  * ld >= dim; the full Hermitian matrix is written.  irrep = BSE_IRREP_ALL
@@ -193,19 +194,22 @@ int bse_build_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
                     void* h_dev, int64_t ld);
 
 /*
- * bse_build_partner_block - for an irrep contained once in the polar-vector
- * representation (the optically active ones: T1u of Oh, E1u and A2u of
- * D6h), the block of its first partner, H_mu^(1) = U_1^dagger H U_1, where
- * U_1 spans the range of the row projector
+ * bse_build_partner_block - the block of the first partner of an irrep,
+ * H_mu^(1) = U_1^dagger H U_1, where U_1 spans the range of the row projector
  *   P_11 = d_mu/|S| sum_s Gamma_mu(s)_11 Gamma~(s)
- * and Gamma_mu(s) are the Cartesian rotations restricted to the irrep's
- * Cartesian subspace.  Sec. III.C.3 (the blocks H^{mu i}_{mu j} are
- * multiples of the identity) makes H_mu unitarily equivalent to d_mu copies
- * of H_mu^(1): its eigenvalues are those of H_mu, each once instead of d_mu
- * times, and the eigensolver works on a matrix d_mu times smaller.
- * Dimension partner_dim[irrep] of bse_tables; arguments as bse_build_block.
- * Errors: EUNSUPPORTED for an irrep that is not contained once in the
- * polar-vector representation.
+ * with real orthogonal irrep matrices Gamma_mu(s): for an irrep contained
+ * once in the polar-vector representation (the optically active ones: T1u
+ * of Oh, E1u and A2u of D6h) the Cartesian rotations restricted to its
+ * Cartesian subspace; for a one-dimensional irrep its character; for any
+ * other irrep a canonical copy inside the left regular representation (the
+ * lowest eigenspace of a fixed generic element of its commutant, its basis
+ * fixed by Gram-Schmidt over the projected unit vectors).  Sec. III.C.3 (the
+ * blocks H^{mu i}_{mu j} are multiples of the identity) makes H_mu unitarily
+ * equivalent to d_mu copies of H_mu^(1): its eigenvalues are those of H_mu,
+ * each once instead of d_mu times, and the eigensolver works on a matrix
+ * d_mu times smaller.  Dimension partner_dim[irrep] of bse_tables; arguments
+ * as bse_build_block.  Errors: ESYMM if the irrep matrices cannot be formed
+ * (partner_dim is 0 then).
  */
 int bse_build_partner_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
                             void* h_dev, int64_t ld);
@@ -238,16 +242,20 @@ int bse_build_blocks(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_
  * bse_batch_create - plan the batch: target i is the block of irrep[i] of
  *   ctxs[i] (partner == NULL or partner[i] == 0) or its partner block
  *   (partner[i] != 0), written to h_dev[i] with leading dimension ld[i];
- *   prec BSE_FP64 or BSE_FP32.  All arrays are host arrays of n entries,
+ *   prec any of the precision enum (the split modes launch the tensor-core
+ *   kernel once per instance inside the graph, each over its own q-sorted
+ *   k pairs).  All arrays are host arrays of n entries,
  *   borrowed for the call; the contexts and the output buffers must outlive
  *   the batch.  Builds the bases, uploads the plan, allocates one X arena
  *   for all contexts (the sum of their direct-term tiles) and captures the
  *   graph; blocks until done.  Errors: as bse_build_blocks; EINVAL if the
- *   contexts do not share one stream; EUNSUPPORTED for other precisions.
+ *   contexts do not share one stream; EUNSUPPORTED where a split mode does
+ *   not support an instance's sizes.
  * bse_batch_run - launch the graph on the contexts' stream (asynchronous).
  *   The result of target i equals that of bse_build_blocks on ctxs[i] alone.
  * bse_batch_kernels - number of kernel launches one run performs.
- * bse_batch_destroy - wait for the stream and free the batch (NULL allowed).
+ * bse_batch_destroy - wait for the stream and free the batch (NULL allowed);
+ *   ETIMEOUT if a bounded wait of the tensor-core kernel gave up in any run.
  * bse_build_blocks_batched - create, run once, destroy.
  */
 int bse_batch_create(bse_batch** out, bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
@@ -306,11 +314,38 @@ int bse_block_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t l
  * bse_build_partner_block: omega_out [partner_dim] are the distinct levels of
  * H_mu (each d_mu-fold in H_mu), osc [partner_dim] the oscillator strength of
  * each level summed over the d_mu partners, sum_i |a^T (U_i^T B)|^2 with
- * U_i = P_i1 U_1, and im_eps the spectrum of the whole block H_mu.
+ * U_i = P_i1 U_1 (zero for an irrep outside the polar-vector
+ * representation), and im_eps the spectrum of the whole block H_mu.
  */
 int bse_partner_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t ld,
                          const double* omega_dev, int64_t n_omega, double eta,
                          double* omega_out, double* osc, double* im_eps);
+
+/*
+ * bse_block_spectrum_lanczos - the Lanczos-Haydock spectrum of a block
+ * (Sec. IV: the spectrum without diagonalising, summed over the contributing
+ * blocks), for blocks too large to reduce or when only Im eps is wanted.
+ * steps of the Hermitian Lanczos recurrence on h_dev (the block of irrep, or
+ * its partner block when partner != 0; device, complex128 column-major,
+ * leading dimension ld, read only) from the dipole direction conj(U^T B),
+ * without reorthogonalisation; the tridiagonal T_m it builds gives the Ritz
+ * values ritz[k] (ascending) and Gauss weights weights[k] = sum_i |U_i^T B|^2
+ * z_0(k)^2 (z_0 the first components of T_m's eigenvectors, from cuSOLVER's
+ * dense symmetric eigensolver on the small T_m), and im_eps the Lorentzian
+ * sum over them, which equals the continued fraction of the Haydock method.
+ * The first 2 m moments of the spectral measure are reproduced; an
+ * invariant subspace ends the recurrence early and the spectrum is then
+ * exact.  ritz, weights: device, [steps], zero beyond *steps_done (host: the
+ * steps performed).  A dark irrep (no dipole weight) gives an empty spectrum
+ * and *steps_done = 0.
+ * Errors: EINVAL for steps outside [1, dim]; EUNSUPPORTED for dim above the
+ * shared-memory capacity (about 14 000) or non-parallel partner projections;
+ * ETIMEOUT if a bounded grid barrier gave up; ESOLVER if the dense
+ * eigensolver of the small T_m fails.
+ */
+int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, const void* h_dev, int64_t ld,
+                               int32_t steps, const double* omega_dev, int64_t n_omega, double eta,
+                               double* ritz_dev, double* weights_dev, double* im_eps_dev, int32_t* steps_done);
 
 /*
  * bse_set_solver - how bse_block_spectrum / bse_partner_spectrum obtain the

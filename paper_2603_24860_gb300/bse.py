@@ -94,6 +94,9 @@ EXPORTS = {
     "bse_loss_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_block_dim": (C.c_int, [C.c_void_p, C.c_int32, _P64]),
+    "bse_block_spectrum_lanczos": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_int32,
+                                             C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             _P32]),
     "bse_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32, _P32, _P32, C.c_int32,
                                    C.c_uint32, C.POINTER(C.c_void_p), _P64]),
     "bse_batch_run": (C.c_int, [C.c_void_p]),
@@ -336,6 +339,16 @@ def bse_partner_spectrum(ctx: Context, irrep: int, h, ld: int, omega, eta: float
                                       _ptr(omega_out), _ptr(osc), _ptr(im_eps)))
 
 
+def bse_block_spectrum_lanczos(ctx: Context, irrep: int, partner: bool, h, ld: int, steps: int, omega, eta: float,
+                               ritz, weights, im_eps) -> int:
+    """Returns the number of Lanczos steps performed."""
+    done = np.zeros(1, dtype=np.int32)
+    _check(lib().bse_block_spectrum_lanczos(ctx.handle, irrep, 1 if partner else 0, _ptr(h), ld, steps, _ptr(omega),
+                                            omega.numel(), eta, _ptr(ritz), _ptr(weights), _ptr(im_eps),
+                                            done.ctypes.data_as(_P32)))
+    return int(done[0])
+
+
 def bse_block_star_columns(ctx: Context, irrep: int, partner: bool = False):
     """Column range [out[a], out[a+1]) of each k star in the (partner) block."""
     n = int(bse_tables(ctx)["n_stars"])
@@ -486,6 +499,19 @@ def partner_spectrum(ctx: Context, irrep: int, h, omega, eta: float):
     im = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
     bse_partner_spectrum(ctx, irrep, h, ld, omega, eta, om, osc, im)
     return om[:n], osc[:n], im
+
+
+def lanczos_spectrum(ctx: Context, irrep: int, h, omega, eta: float, steps: int, partner: bool = False):
+    """(Ritz values, Gauss weights, Im eps_M) of the Lanczos-Haydock spectrum
+    of a block (or partner block) after at most `steps` steps."""
+    import torch
+    n = h.shape[0]
+    ld = h.stride(1) if n else 1
+    rz = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda")
+    wt = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda")
+    im = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+    k = bse_block_spectrum_lanczos(ctx, irrep, partner, h, ld, steps, omega, eta, rz, wt, im)
+    return rz[:k], wt[:k], im
 
 
 def full(ctx: Context, terms: int = BSE_TERM_ALL):

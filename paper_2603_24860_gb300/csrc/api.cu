@@ -119,6 +119,7 @@ struct bse_ctx {
     bool narrow_ready = false;
     DevBuf wemb;         // split-precision W(q) embeddings for the tensor-core build
     DevBuf wexp;         // their per-q scale exponents
+    DevBuf lzScratch;    // Lanczos vectors, T_m and its eigenvectors
     int wemb_ngp = 0;
     int wemb_fp16 = -1;  // element type of wemb (1 fp16, 0 bf16)
     DevBuf groups, status;
@@ -328,8 +329,8 @@ static int upload_basis(bse_ctx* c, IrrepDev& d) {
     return BSE_OK;
 }
 
-// partner 1 of an irrep contained once in the polar-vector representation:
-// canonical basis of the range of P_11 and its transfers U_i = P_i1 U_1
+// partner 1 of an irrep: canonical basis of the range of P_11 and its
+// transfers U_i = P_i1 U_1
 static int ensure_partner(bse_ctx* c, int mu) {
     if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
     auto& pd = c->partner[mu];
@@ -733,7 +734,7 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     for (int mu = 0; mu < t.n_irreps; ++mu) {
         int d = 0;
         std::vector<double> gam;
-        if (t.bright[mu] != 1 || partner_matrices(t, mu, d, gam) != BSE_OK) {
+        if (partner_matrices(t, mu, d, gam) != BSE_OK) {   // no irrep matrices: no partner block
             clear_error();
             continue;
         }
@@ -780,7 +781,7 @@ static void free_ctx(bse_ctx* c) {
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
                       &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots,
-                      &c->lossScratch, &c->wsym, &c->wcand})
+                      &c->lossScratch, &c->wsym, &c->wcand, &c->lzScratch})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -937,6 +938,35 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
     return BSE_OK;
 }
 
+// The tensor-core kernel takes groups of up to kg pairs with the same
+// q = k - k' (they share W(q)): the tasks sorted by q (stable) and their groups.
+static void tc_group_tasks(const Tables& t, const std::vector<PairTask>& in, int kg, std::vector<PairTask>& sorted,
+                           std::vector<TcGroup>& groups) {
+    std::vector<int> qof(in.size());
+    for (size_t i = 0; i < in.size(); ++i) {
+        int iq[3];
+        for (int a = 0; a < 3; ++a) iq[a] = (t.kidx[3 * in[i].k + a] - t.kidx[3 * in[i].kp + a] + t.n[a]) % t.n[a];
+        qof[i] = (iq[0] * t.n[1] + iq[1]) * t.n[2] + iq[2];
+    }
+    std::vector<size_t> order(in.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return qof[a] < qof[b]; });
+    sorted.resize(in.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = in[order[i]];
+    groups.clear();
+    for (size_t i = 0; i < order.size();) {
+        TcGroup gp;
+        gp.first = (int32_t)i;
+        gp.q = qof[order[i]];
+        gp.count = 0;
+        while (i < order.size() && qof[order[i]] == gp.q && gp.count < kg) {
+            ++gp.count;
+            ++i;
+        }
+        groups.push_back(gp);
+    }
+}
+
 // U^dagger H U for an orbit-sparse basis U (an irrep block or a partner block)
 // One build of several blocks (whole irrep blocks or partner blocks): the
 // direct term of every star pair runs once per batch and each target projects
@@ -946,10 +976,10 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
     const int tcp = prec == BSE_BF16_SPLIT || prec == BSE_FP16_SPLIT;
     const int fp16 = prec == BSE_FP16_SPLIT;
     const int p32 = prec == BSE_FP32 || tcp;   // the tile arena is FP32 for all three
-    int ngp = 0;
+    int ngp = 0, tc_group = 1;
     if (tcp && (terms & BSE_TERM_DIRECT)) {
         size_t sm = 0;
-        BSE_TRY(tc_supported(c->S, ngp, sm));
+        BSE_TRY(tc_supported(c->S, ngp, sm, &tc_group));
     }
     const Tables& t = c->t;
     const size_t nt = tg.size();
@@ -1001,30 +1031,8 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         BSE_TRY(ensure(c->arenaY, ymax));
         std::vector<TcGroup> groups;
         if (tcp && (terms & BSE_TERM_DIRECT)) {
-            // the tensor-core kernel takes groups of pairs with the same q
-            std::vector<PairTask> sorted(bt.tasks);
-            std::vector<int> qof(sorted.size());
-            for (size_t i = 0; i < sorted.size(); ++i) {
-                int iq[3];
-                for (int a = 0; a < 3; ++a)
-                    iq[a] = (t.kidx[3 * sorted[i].k + a] - t.kidx[3 * sorted[i].kp + a] + t.n[a]) % t.n[a];
-                qof[i] = (iq[0] * t.n[1] + iq[1]) * t.n[2] + iq[2];
-            }
-            std::vector<size_t> order(sorted.size());
-            for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return qof[a] < qof[b]; });
-            for (size_t i = 0; i < order.size(); ++i) sorted[i] = bt.tasks[order[i]];
-            for (size_t i = 0; i < order.size();) {
-                TcGroup gp;
-                gp.first = (int32_t)i;
-                gp.q = qof[order[i]];
-                gp.count = 0;
-                while (i < order.size() && qof[order[i]] == gp.q && gp.count < 4) {
-                    ++gp.count;
-                    ++i;
-                }
-                groups.push_back(gp);
-            }
+            std::vector<PairTask> sorted;
+            tc_group_tasks(t, bt.tasks, tc_group, sorted, groups);
             BSE_TRY(upload(c->tasks, sorted.data(), sorted.size(), c->stream));
             BSE_TRY(upload(c->groups, groups.data(), groups.size(), c->stream));
         } else {
@@ -1160,6 +1168,14 @@ struct bse_batch {
     DevBuf insts, tasks, tiles, arenaX, pmu, rsys, rots;
     int64_t nrots = 0;
     int bmax = 0;
+    // split precisions: one tensor-core launch per instance over its q-sorted tasks
+    struct TcInst {
+        int64_t task_off = 0, group_off = 0, ngroups = 0;
+        int ngp = 0;
+    };
+    std::vector<TcInst> tci;
+    int tcp = 0, fp16 = 0;
+    DevBuf tctasks, tcgroups, status;
     static constexpr int kBranches = 4;   // concurrent projection branches of the graph
     DevBuf arenaY[kBranches];
     cudaGraph_t graph = nullptr;
@@ -1170,7 +1186,9 @@ struct bse_batch {
 static void free_batch(bse_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (DevBuf* d : {&b->insts, &b->tasks, &b->tiles, &b->arenaX, &b->pmu, &b->rsys, &b->rots}) release(*d);
+    for (DevBuf* d : {&b->insts, &b->tasks, &b->tiles, &b->arenaX, &b->pmu, &b->rsys, &b->rots, &b->tctasks,
+                      &b->tcgroups, &b->status})
+        release(*d);
     for (auto& y : b->arenaY) release(y);
     delete b;
 }
@@ -1191,10 +1209,23 @@ static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaE
                           const std::vector<int>& tile_off, const std::vector<DirectClass>& classes,
                           const std::vector<int>& order) {
     const int nb = bse_batch::kBranches;
+    if ((terms & BSE_TERM_DIRECT) && b->tcp) {
+        BSE_CUDA(cudaMemsetAsync(b->status.p, 0, sizeof(int), st));
+        for (size_t i = 0; i < b->tci.size(); ++i) {
+            const bse_batch::TcInst& ti = b->tci[i];
+            if (ti.ngroups == 0) continue;
+            bse_ctx* c = b->ctx[i];
+            BSE_TRY(launch_direct_tc(c->S, b->fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ti.ngp,
+                                     (const PairTask*)b->tctasks.p + ti.task_off,
+                                     (const TcGroup*)b->tcgroups.p + ti.group_off, ti.ngroups, b->arenaX.p,
+                                     (int*)b->status.p, st));
+        }
+    }
     if (terms & BSE_TERM_DIRECT) {
         for (const DirectClass& dc : classes)
-            BSE_TRY(launch_direct_multi((const DirectInst*)b->insts.p, dc.smax, p32,
-                                        (const PairTask*)b->tasks.p + dc.first, dc.count, b->arenaX.p, st));
+            if (!b->tcp)
+                BSE_TRY(launch_direct_multi((const DirectInst*)b->insts.p, dc.smax, p32,
+                                            (const PairTask*)b->tasks.p + dc.first, dc.count, b->arenaX.p, st));
         if (b->nrots > 0)   // pairs rotated from their seeds (Eq. Wtrafo)
             BSE_TRY(launch_rotate_multi((const RotSys*)b->rsys.p, b->bmax, p32, (const RotTask*)b->rots.p, b->nrots,
                                         b->arenaX.p, st));
@@ -1232,7 +1263,9 @@ static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaE
 
 static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, const int32_t* partner, int32_t prec,
                              uint32_t terms, void* const* h, const int64_t* ld) {
-    const int p32 = prec == BSE_FP32;
+    b->tcp = (prec == BSE_BF16_SPLIT || prec == BSE_FP16_SPLIT) && (terms & BSE_TERM_DIRECT);
+    b->fp16 = prec == BSE_FP16_SPLIT;
+    const int p32 = prec == BSE_FP32 || prec == BSE_BF16_SPLIT || prec == BSE_FP16_SPLIT;   // FP32 tile arena
     for (int32_t i = 0; i < n; ++i) {
         bse_ctx* c = b->ctx[i];
         if (partner && partner[i]) {
@@ -1246,6 +1279,13 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
         if (b->tg[i]->host.dim > 0 && !h[i]) return fail(BSE_EINVAL, "instance %d: null output", i);
         if (terms & BSE_TERM_EXCHANGE) BSE_TRY(ensure_exchange_vectors(c));
         if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
+        if (b->tcp) {
+            bse_batch::TcInst ti;
+            size_t sm = 0;
+            BSE_TRY(tc_supported(c->S, ti.ngp, sm));
+            BSE_TRY(ensure_wemb(c, ti.ngp, b->fp16));
+            b->tci.push_back(ti);
+        }
         b->h.push_back(h[i]);
         b->ld.push_back(ld[i]);
     }
@@ -1296,6 +1336,24 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
         }
     }
     b->nrots = (int64_t)rots.size();
+    std::vector<PairTask> tctasks;
+    std::vector<TcGroup> tcgroups;
+    if (b->tcp)
+        for (int32_t i = 0; i < n; ++i) {
+            bse_ctx* c = b->ctx[i];
+            int ngp = 0, kg = 1;
+            size_t sm = 0;
+            BSE_TRY(tc_supported(c->S, ngp, sm, &kg));
+            std::vector<PairTask> in(plans[i].tasks), sorted;
+            std::vector<TcGroup> gr;
+            for (PairTask& t : in) t.xoff += xbase[i];
+            tc_group_tasks(c->t, in, kg, sorted, gr);
+            b->tci[i].task_off = (int64_t)tctasks.size();
+            b->tci[i].group_off = (int64_t)tcgroups.size();
+            b->tci[i].ngroups = (int64_t)gr.size();
+            tctasks.insert(tctasks.end(), sorted.begin(), sorted.end());
+            tcgroups.insert(tcgroups.end(), gr.begin(), gr.end());
+        }
     // direct-term tasks grouped by shared-memory class (rounded to 8 KB), so a
     // small system does not run at the occupancy of the largest one
     std::vector<int> byclass(n);
@@ -1338,6 +1396,11 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
     BSE_TRY(upload(b->tiles, tiles.data(), tiles.size(), b->stream));
     BSE_TRY(upload(b->rsys, rsys.data(), rsys.size(), b->stream));
     BSE_TRY(upload(b->rots, rots.data(), rots.size(), b->stream));
+    if (b->tcp) {
+        BSE_TRY(upload(b->tctasks, tctasks.data(), tctasks.size(), b->stream));
+        BSE_TRY(upload(b->tcgroups, tcgroups.data(), tcgroups.size(), b->stream));
+        BSE_TRY(ensure(b->status, sizeof(int)));
+    }
     BSE_TRY(ensure(b->arenaX, (size_t)xbase[n] * xel));
     for (int j = 0; j < bse_batch::kBranches; ++j) BSE_TRY(ensure(b->arenaY[j], ybr[j]));
     BSE_TRY(ensure(b->pmu, sizeof(double2) * (size_t)std::max<int64_t>(pmu_off[n], 1)));
@@ -1384,8 +1447,8 @@ int bse_batch_create(bse_batch** out, bse_ctx* const* ctxs, int32_t n, const int
     clear_error();
     if (!out || !ctxs || n < 1 || !irrep || !h || !ld) return fail(BSE_EINVAL, "null argument");
     *out = nullptr;
-    if (prec != BSE_FP64 && prec != BSE_FP32)
-        return fail(BSE_EUNSUPPORTED, "batched builds take BSE_FP64 or BSE_FP32 (got %d)", prec);
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT && prec != BSE_FP16_SPLIT)
+        return fail(BSE_EUNSUPPORTED, "precision %d is not implemented", prec);
     for (int32_t i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(BSE_EINVAL, "null context %d", i);
         if (ctxs[i]->stream != ctxs[0]->stream) return fail(BSE_EINVAL, "contexts of a batch share one stream");
@@ -1421,9 +1484,13 @@ int bse_batch_kernels(const bse_batch* b, int64_t* out) {
 }
 
 int bse_batch_destroy(bse_batch* b) {
+    clear_error();
     if (!b) return BSE_OK;
     cudaStreamSynchronize(b->stream);
+    int st = 0;
+    if (b->tcp && b->status.p) cudaMemcpy(&st, b->status.p, sizeof(int), cudaMemcpyDeviceToHost);
     free_batch(b);
+    if (st) return fail(BSE_ETIMEOUT, "a bounded wait of the tensor-core direct kernel gave up");
     return BSE_OK;
 }
 
@@ -1432,8 +1499,8 @@ int bse_build_blocks_batched(bse_ctx* const* ctxs, int32_t n, const int32_t* irr
     bse_batch* b = nullptr;
     BSE_TRY(bse_batch_create(&b, ctxs, n, irrep, partner, prec, terms, h, ld));
     const int rc = bse_batch_run(b);
-    bse_batch_destroy(b);
-    return rc;
+    const int rd = bse_batch_destroy(b);   // waits; ETIMEOUT from a bounded wait of the run
+    return rc != BSE_OK ? rc : rd;
 }
 
 int bse_block_dim(const bse_ctx* c, int32_t mu, int64_t* dim) {
@@ -1487,19 +1554,18 @@ int bse_dipoles(bse_ctx* c, void* b) {
 // Levels and strengths without eigenvectors (see bse_set_solver).  Returns
 // BSE_OK when done; EUNSUPPORTED / ESOLVER when a condition of the path fails
 // (the caller may fall back to the dense solver).
-static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, const void* h, int64_t ld,
-                            double* omega_out, double* osc) {
-    if (dim > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: block dimension %lld > %d",
-                                             (long long)dim, tridiag_max_dim());
+// The start direction of an eigenvector-free spectrum: the partner whose
+// projection b_p = U_p^T B has the largest norm, and the total weight
+// sum_p |b_p|^2 (0 for a dark irrep).  The partners' projections must be
+// parallel (|G_pj|^2 = G_pp G_jj with G the Gram matrix), as they are for the
+// partner blocks, so that one direction carries the whole measure.
+static int start_direction(bse_ctx* c, int nparts, bool dark, int64_t dim, int* pmax_out, double* scale_out) {
     BSE_TRY(ensure(c->triSmall, 256));
     double2* gram = (double2*)c->triSmall.p;
-    double* wsum = (double*)((char*)c->triSmall.p + 160);
-    int* err = (int*)((char*)c->triSmall.p + 176);
     BSE_TRY(launch_gram((const double2*)c->Bmu.p, dim, nparts, gram, c->stream));
     double2 g[9];
     BSE_CUDA(cudaMemcpyAsync(g, gram, sizeof(g), cudaMemcpyDeviceToHost, c->stream));
     BSE_CUDA(cudaStreamSynchronize(c->stream));
-    // the projections must be parallel: |G_pj|^2 = G_pp G_jj for the largest G_pp
     int pmax = 0;
     double scale = 0.0;
     for (int i = 0; i < nparts; ++i) {
@@ -1512,8 +1578,22 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     for (int j = 0; j < nparts && !dark; ++j) {
         const double gjj = g[j * 3 + j].x, a2 = g[pmax * 3 + j].x * g[pmax * 3 + j].x + g[pmax * 3 + j].y * g[pmax * 3 + j].y;
         if (gjj > 1e-20 * gpp && a2 < (1.0 - 1e-10) * gpp * gjj)
-            return fail(BSE_EUNSUPPORTED, "tridiagonal path: the partners' dipole projections are not parallel");
+            return fail(BSE_EUNSUPPORTED, "the partners' dipole projections are not parallel");
     }
+    *pmax_out = pmax;
+    *scale_out = scale;
+    return BSE_OK;
+}
+
+static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, const void* h, int64_t ld,
+                            double* omega_out, double* osc) {
+    if (dim > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: block dimension %lld > %d",
+                                             (long long)dim, tridiag_max_dim());
+    int pmax = 0;
+    double scale = 0.0;
+    BSE_TRY(start_direction(c, nparts, dark, dim, &pmax, &scale));
+    double* wsum = (double*)((char*)c->triSmall.p + 160);
+    int* err = (int*)((char*)c->triSmall.p + 176);
     BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
     BSE_CUDA(cudaMemcpy2DAsync(c->eigA.p, sizeof(double2) * dim, h, sizeof(double2) * ld, sizeof(double2) * dim, dim,
                                cudaMemcpyDeviceToDevice, c->stream));
@@ -1633,7 +1713,86 @@ int bse_partner_spectrum(bse_ctx* c, int32_t mu, const void* h, int64_t ld, cons
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     BSE_TRY(ensure_partner(c, mu));
     auto& pd = c->partner[mu];
-    return spectrum_generic(c, pd.part, pd.d, pd.d, false, h, ld, omega, n_omega, eta, omega_out, osc, im_eps);
+    return spectrum_generic(c, pd.part, pd.d, pd.d, !c->t.bright[mu], h, ld, omega, n_omega, eta, omega_out, osc,
+                            im_eps);
+}
+
+int bse_block_spectrum_lanczos(bse_ctx* c, int32_t mu, int32_t partner, const void* h, int64_t ld, int32_t steps,
+                               const double* omega, int64_t n_omega, double eta, double* ritz, double* weights,
+                               double* im_eps, int32_t* steps_done) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null context");
+    AllocStream alloc_on_(c->stream);
+    if (!h || !ritz || !weights || !steps_done || (n_omega > 0 && (!omega || !im_eps)))
+        return fail(BSE_EINVAL, "null argument");
+    if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
+    *steps_done = 0;
+    IrrepDev* parts = nullptr;
+    int nparts = 1;
+    if (partner) {
+        BSE_TRY(ensure_partner(c, mu));
+        parts = c->partner[mu].part;
+        nparts = c->partner[mu].d;
+    } else {
+        BSE_TRY(ensure_basis(c, mu));
+        parts = &c->irr[mu];
+    }
+    const int64_t dim = parts[0].host.dim;
+    if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
+    if (steps < 1 || steps > std::max<int64_t>(dim, 1))
+        return fail(BSE_EINVAL, "steps must be in [1, %lld]", (long long)dim);
+    BSE_CUDA(cudaMemsetAsync(ritz, 0, sizeof(double) * steps, c->stream));
+    BSE_CUDA(cudaMemsetAsync(weights, 0, sizeof(double) * steps, c->stream));
+    if (dim == 0 || !c->t.bright[mu]) {   // no dipole weight: an empty spectrum
+        if (n_omega) BSE_CUDA(cudaMemsetAsync(im_eps, 0, sizeof(double) * n_omega, c->stream));
+        return BSE_OK;
+    }
+    BSE_TRY(ensure_dipoles(c));
+    BSE_TRY(ensure(c->Bmu, sizeof(double2) * (size_t)dim * nparts));
+    for (int p = 0; p < nparts; ++p)
+        BSE_TRY(launch_bmu(dev_basis_of(c, parts[p]), (const double2*)c->B.p, (double2*)c->Bmu.p + (size_t)p * dim,
+                           c->stream));
+    int pmax = 0;
+    double scale = 0.0;
+    BSE_TRY(start_direction(c, nparts, false, dim, &pmax, &scale));
+    if (!(scale > 0.0)) {
+        if (n_omega) BSE_CUDA(cudaMemsetAsync(im_eps, 0, sizeof(double) * n_omega, c->stream));
+        return BSE_OK;
+    }
+    const size_t lzb = (lanczos_scratch_bytes(dim, steps) + 255) & ~(size_t)255;
+    BSE_TRY(ensure(c->lzScratch, lzb + sizeof(double) * (size_t)steps * steps));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
+    double *alpha = nullptr, *beta = nullptr;
+    int done = 0;
+    BSE_TRY(launch_lanczos((const double2*)h, ld, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, steps,
+                           c->lzScratch.p, &alpha, &beta, &done, c->stream));
+    // eigenpairs of T_done (dense symmetric eigensolver; clusters of Ritz values are harmless there)
+    double* T = (double*)((char*)c->lzScratch.p + lzb);
+    BSE_TRY(launch_tm_dense(alpha, beta + 1, done, T, c->stream));
+    if (!c->solver && cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "cusolverDnCreate failed");
+    if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "cusolverDnSetStream failed");
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done, ritz,
+                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "dsyevd buffer size query failed");
+    BSE_TRY(ensure(c->eigWork, sizeof(double) * (size_t)std::max(lwork, 1)));
+    BSE_TRY(ensure(c->info, sizeof(int)));
+    if (cusolverDnDsyevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done, ritz,
+                         (double*)c->eigWork.p, lwork, (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
+        return fail(BSE_ESOLVER, "dsyevd launch failed");
+    BSE_TRY(launch_tm_weights(T, done, scale, weights, c->stream));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
+    const double pref = 4.0 * M_PI * c->spin / c->t.nk;
+    if (n_omega > 0) BSE_TRY(launch_spectrum(ritz, weights, done, omega, n_omega, eta, pref, im_eps, c->stream));
+    int info = 0;
+    BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BSE_CUDA(cudaStreamSynchronize(c->stream));
+    if (info != 0) return fail(BSE_ESOLVER, "dsyevd info = %d", info);
+    if (c->timing) BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
+    *steps_done = done;
+    return BSE_OK;
 }
 
 int bse_loss_spectrum(bse_ctx* c, int64_t n, const double* omega_levels, const double* osc, const double* omega,

@@ -12,12 +12,15 @@
 //   T = W(q) conj(rho_vv')         MMA1, all pairs of a group share W(q)
 //   K^d = 1/V rho_cc'^T T          MMA2, one pair at a time           (Eq. BSE-eigval)
 //
-// One CTA per group of up to kG k pairs with the same q = k - k'.  Complex
-// products use real embeddings:
-//   A1 = [[Wr, Wi], [Wi, -Wr]] (rows: Re T | Im T), B1 = [rho_r | rho_i]  ->  T = W conj(rho_vv')
-//   A2 = [[rho_r, -rho_i], [rho_i, rho_r]] (rows: Re K | Im K), B2 = [T_r | T_i]
-// W(q) (hi and lo) is prepared once per q in the core-matrix layout and
-// brought in by one bulk copy that overlaps the pair densities.
+// One CTA per group of up to 4 k pairs with the same q = k - k' (fewer when
+// the operands of larger spheres fill shared memory or TMEM).  Complex
+// products use real operands:
+//   MMA1  T_r = Wr rho_r + Wi rho_i,  T_i = Wi rho_r + Wr (-rho_i)   (M = 128 rows Q, K = NGp)
+//   MMA2  A2 = [[rho_r, -rho_i], [rho_i, rho_r]] (rows: Re K | Im K), B2 = [T_r | T_i]  (K = 2 NGp)
+// so NG <= 128.  W(q) (Wr and Wi, hi and lo) is prepared once per q in the
+// core-matrix layout and brought in by one bulk copy (from L2 as a rule) into
+// the shared memory the pair densities were staged in; A2 and the epilogue
+// staging reuse it after MMA1.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -29,29 +32,38 @@ namespace bse {
 
 using tc::core_off;
 
-constexpr int kG = 4;        // pairs per group
-constexpr int kNVV = 16;     // rows of B1/B2 per pair (nv^2 padded)
+constexpr int kMaxG = 4;                            // pairs per group at most
+constexpr int kTmemCols = 256;                      // T_r, T_i and K^d of every pair: 3 nr kg columns
+constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic shared memory per CTA
+constexpr size_t kSmemFloor = 82 * 1024;            // at most two CTAs (2 x 256 TMEM columns) per SM
 
 struct TcPlan {
-    int K;                   // 2 * NGp
-    size_t a1, b, a2, rc, st_coef, st_cnt, st_list, st_rho, total;
+    size_t a, b, rc, st_coef, st_cnt, st_list, st_rho, total;   // a: W / A2 / epilogue and, before them, the staging
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 1023) & ~(size_t)1023; }
+__host__ __device__ inline size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+// rows of B1 and B2 per k pair: the nv^2 valence pairs padded to a multiple of 16 (N of MMA2)
+__host__ __device__ inline int tc_rows(int nv) { return (nv * nv + 15) / 16 * 16; }
 
-__host__ __device__ inline TcPlan tc_plan(int ngp, int nb, int nv, int nc, int npw_max, int ng_max) {
+// ngp: NG padded to a multiple of 16 (K of MMA1); kg: pairs per group
+__host__ __device__ inline TcPlan tc_plan(int kg, int ngp, int nb, int nv, int nc, int npw_max, int ng_max) {
     TcPlan p;
-    p.K = 2 * ngp;
-    p.a1 = a16((size_t)2 * 128 * p.K * 2);
-    p.b = a16((size_t)2 * kG * kNVV * p.K * 2);
-    size_t a2 = (size_t)2 * 128 * p.K * 2, epi = (size_t)kG * kNVV * 128 * sizeof(float);
-    p.a2 = a16(a2 > epi ? a2 : epi);   // also holds the epilogue staging
-    p.rc = a16((size_t)kG * nc * nc * ngp * sizeof(float2));
+    const int nr = tc_rows(nv);
+    const size_t a1 = (size_t)4 * 128 * ngp * 2;              // Wr hi, Wr lo, Wi hi, Wi lo: 128 x ngp each
+    const size_t a2 = (size_t)2 * 128 * (2 * ngp) * 2;        // A2 hi, lo: 128 x 2 ngp each
+    const size_t epi = (size_t)kg * nr * 128 * sizeof(float);
     p.st_coef = a16((size_t)npw_max * nb * sizeof(float2));
     p.st_cnt = a16((size_t)ng_max * sizeof(int));
     p.st_list = a16((size_t)ng_max * npw_max * sizeof(int));
     p.st_rho = a16((size_t)ng_max * (nc * nc + nv * nv) * sizeof(float2));
-    p.total = p.a1 + p.b + p.a2 + p.rc + 2 * p.st_coef + p.st_cnt + p.st_list + p.st_rho + 1024 + 64;
+    const size_t staging = 2 * p.st_coef + p.st_cnt + p.st_list + p.st_rho;
+    p.a = a16(zmax(zmax(zmax(a1, a2), epi), staging));
+    const size_t b1 = (size_t)6 * kg * nr * ngp * 2;         // rho_r, rho_i, -rho_i (hi, lo): (nr kg) x ngp each
+    const size_t b2 = (size_t)2 * kg * nr * (2 * ngp) * 2;   // [T_r | T_i] hi, lo: (nr kg) x 2 ngp each
+    p.b = a16(zmax(b1, b2));
+    p.rc = a16((size_t)kg * nc * nc * ngp * sizeof(float2));
+    p.total = p.a + p.b + p.rc + 1024 + 64;
     return p;
 }
 
@@ -105,31 +117,36 @@ template <typename E>
 __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float2* __restrict__ coef,
                                                            const E* __restrict__ wemb, const int* __restrict__ wexp,
                                                            const PairTask* __restrict__ tasks,
-                                                           const TcGroup* __restrict__ groups, int ngp, float2* X,
-                                                           int* status) {
+                                                           const TcGroup* __restrict__ groups, int ngp, int kg,
+                                                           float2* X, int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nv = S.nv, nc = S.nc, nb = S.nb, P = nc * nc + nv * nv, ncc = nc * nc, nvv = nv * nv;
-    const TcPlan pl = tc_plan(ngp, nb, nv, nc, S.npw_max, S.ng_max);
-    const int K = pl.K;
-    unsigned char* A1 = smem;                           // [hi | lo] 128 x K
-    unsigned char* Bm = A1 + pl.a1;                     // [hi | lo] (kG*16) x K : B1, then B2
-    unsigned char* A2 = Bm + pl.b;                      // [hi | lo] 128 x K
-    float2* RC = (float2*)(A2 + pl.a2);                 // [kG][ncc][ngp] rho_cc'
-    float2* ckT = (float2*)((unsigned char*)RC + pl.rc);
+    const TcPlan pl = tc_plan(kg, ngp, nb, nv, nc, S.npw_max, S.ng_max);
+    const int K2 = 2 * ngp;                             // K of MMA2
+    const int NR = tc_rows(nv);                         // rows per pair (N of MMA2)
+    const int NB = NR * kg;                             // N of MMA1 (rows of B1 and B2)
+    unsigned char* Am = smem;   // the pair-density staging, then W planes, A2 (hi | lo) and the epilogue staging
+    unsigned char* Bm = Am + pl.a;                      // B1 planes, then B2 (hi | lo)
+    float2* RC = (float2*)(Bm + pl.b);                  // [kg][ncc][ngp] rho_cc'
+    float2* ckT = (float2*)Am;
     float2* ckpT = (float2*)((unsigned char*)ckT + pl.st_coef);
     int* cnt = (int*)((unsigned char*)ckpT + pl.st_coef);
     int* list = (int*)((unsigned char*)cnt + pl.st_cnt);
     float2* rho = (float2*)((unsigned char*)list + pl.st_list);   // [ng][P]
-    uint64_t* mbar = (uint64_t*)((unsigned char*)rho + pl.st_rho);
+    uint64_t* mbar = (uint64_t*)((unsigned char*)RC + pl.rc);
     uint32_t* slot = (uint32_t*)(mbar + 4);
-    const size_t a_half = (size_t)128 * K * 2, b_half = (size_t)kG * kNVV * K * 2;
+    const size_t wpl = (size_t)128 * ngp * 2;           // one W plane (bytes)
+    const size_t bpl = (size_t)NB * ngp * 2;            // one B1 plane
+    const size_t a2h = (size_t)128 * K2 * 2;            // A2 hi (lo follows)
+    const size_t b2h = (size_t)NB * K2 * 2;             // B2 hi (lo follows)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
     const TcGroup grp = groups[blockIdx.x];
     const int q = grp.q, ng = S.ng[q];
     __shared__ unsigned s_max;      // block maximum of an operand (float bits)
-    __shared__ int s_erho[kG];      // scale exponent of each pair's densities
-    constexpr uint32_t kCols = 128;   // TMEM: MMA1 accumulator cols [0, 64), MMA2 [64, 128)
+    __shared__ int s_erho[kMaxG];   // scale exponent of each pair's densities
+    // TMEM: T_r in columns [0, NB), T_i in [NB, 2 NB), K^d of pair p in [2 NB + NR p, 2 NB + NR (p + 1))
+    constexpr uint32_t kCols = kTmemCols;
     constexpr long kSpin = 1l << 24;
 
     if (tid == 0) {
@@ -138,17 +155,12 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         tc::mbar_init(&mbar[2], 1);
     }
     if (warp == 0) tc::tmem_alloc(slot, kCols);
-    // zero B1 (its padding must be finite: A1 is zero there)
-    for (size_t e = tid * 16; e < 2 * b_half; e += blockDim.x * 16) *(uint4*)(Bm + e) = make_uint4(0, 0, 0, 0);
+    // zero the B1 planes (rows of absent pairs and of vv' >= nv^2 must be finite: they feed the scale of T)
+    for (size_t e = tid * 16; e < pl.b; e += blockDim.x * 16) *(uint4*)(Bm + e) = make_uint4(0, 0, 0, 0);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *slot;
-    if (tid == 0) {
-        const uint32_t bytes = (uint32_t)(2 * a_half);
-        tc::mbar_expect_tx(&mbar[0], bytes);
-        tc::bulk_g2s(A1, wemb + (size_t)q * 2 * 128 * K, bytes, &mbar[0]);
-    }
 
     // ---- pair densities (CUDA cores, FP32) for every pair of the group ----
     for (int p = 0; p < grp.count; ++p) {
@@ -218,19 +230,21 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         const int erho = scale_exp(block_max(mx, &s_max));
         const float srho = pow2f(erho);
         if (tid == 0) s_erho[p] = erho;
-        // B1 rows p*16 + vv' = [rho_r | rho_i] of rho_vv', and rho_cc' kept for MMA2
-        unsigned char* B1h = Bm;
-        unsigned char* B1l = Bm + b_half;
+        // B1 rows p*NR + vv': planes rho_r, rho_i, -rho_i of rho_vv' (hi, lo), K index Q; rho_cc' kept for MMA2
         for (int e = tid; e < nvv * ngp; e += blockDim.x) {
             const int vv = e / ngp, Q = e % ngp;
-            float2 r = Q < ng ? rho[Q * P + ncc + vv] : make_float2(0.f, 0.f);
+            const float2 r = Q < ng ? rho[Q * P + ncc + vv] : make_float2(0.f, 0.f);
+            const uint32_t o = core_off(p * NR + vv, Q, ngp);
             E h, l;
             split16(r.x * srho, h, l);
-            *(E*)(B1h + core_off(p * kNVV + vv, Q, K)) = h;
-            *(E*)(B1l + core_off(p * kNVV + vv, Q, K)) = l;
+            *(E*)(Bm + o) = h;
+            *(E*)(Bm + bpl + o) = l;
             split16(r.y * srho, h, l);
-            *(E*)(B1h + core_off(p * kNVV + vv, ngp + Q, K)) = h;
-            *(E*)(B1l + core_off(p * kNVV + vv, ngp + Q, K)) = l;
+            *(E*)(Bm + 2 * bpl + o) = h;
+            *(E*)(Bm + 3 * bpl + o) = l;
+            split16(-r.y * srho, h, l);
+            *(E*)(Bm + 4 * bpl + o) = h;
+            *(E*)(Bm + 5 * bpl + o) = l;
         }
         for (int e = tid; e < ncc * ngp; e += blockDim.x) {
             const int cc = e / ngp, Q = e % ngp;
@@ -239,56 +253,78 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         __syncthreads();
     }
 
-    if (tid == 0) s_max = 0u;   // read only after the barriers below
-    // ---- MMA1: T = W(q) conj(rho_vv') for all pairs (N = 16 * kG) ----
+    // ---- W(q) into the region of the staging, now dead (generic-proxy accesses ordered before the bulk copy) ----
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(4 * wpl);
+        tc::mbar_expect_tx(&mbar[0], bytes);
+        tc::bulk_g2s(Am, wemb + (size_t)q * 4 * 128 * ngp, bytes, &mbar[0]);
+        s_max = 0u;   // read only after the barriers below
+    }
+    // ---- MMA1: T_r and T_i for all pairs (M = 128, N = NR kg, K = ngp) ----
     bool ok = __syncthreads_and(tc::mbar_wait(&mbar[0], 0, kSpin)) != 0;
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t idesc1 = tc::idesc_f16(128, kNVV * kG, Elem<E>::kBf16);
-    const uint32_t lbo = 128, sbo = (uint32_t)(K / 8) * 128;
+    const uint32_t idesc1 = tc::idesc_f16(128, NB, Elem<E>::kBf16);
     if (tid == 0 && ok) {
-        const uint32_t a0 = tc::smem_u32(A1), b0 = tc::smem_u32(Bm);
-        for (int prod = 0; prod < 3; ++prod) {
-            const uint32_t ab = a0 + (prod == 2 ? (uint32_t)a_half : 0u);
-            const uint32_t bb = b0 + (prod == 1 ? (uint32_t)b_half : 0u);
-            for (int ks = 0; ks < K / 16; ++ks)
-                tc::mma_f16(tmem, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo), idesc1,
-                            (prod | ks) != 0);
-        }
+        const uint32_t lbo = 128, sbo = (uint32_t)(ngp / 8) * 128;
+        const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm);
+        const uint32_t Wr = a0, Wi = a0 + 2 * (uint32_t)wpl;
+        const uint32_t Rr = b0, Ri = b0 + 2 * (uint32_t)bpl, Rn = b0 + 4 * (uint32_t)bpl;
+        // d += A B over the three split products (A_hi B_hi, A_hi B_lo, A_lo B_hi)
+        auto chain = [&](uint32_t d, uint32_t A, uint32_t B, bool first) {
+            for (int prod = 0; prod < 3; ++prod) {
+                const uint32_t ab = A + (prod == 2 ? (uint32_t)wpl : 0u);
+                const uint32_t bb = B + (prod == 1 ? (uint32_t)bpl : 0u);
+                for (int ks = 0; ks < ngp / 16; ++ks)
+                    tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
+                                idesc1, !(first && prod == 0 && ks == 0));
+            }
+        };
+        chain(tmem, Wr, Rr, true);                    // T_r = Wr rho_r + Wi rho_i
+        chain(tmem, Wi, Ri, false);
+        chain(tmem + (uint32_t)NB, Wi, Rr, true);     // T_i = Wi rho_r - Wr rho_i
+        chain(tmem + (uint32_t)NB, Wr, Rn, false);
         tc::mma_commit(&mbar[1]);
     }
     ok = __syncthreads_and(ok && tc::mbar_wait(&mbar[1], 0, kSpin)) != 0;
     tc::fence_after();
-    // ---- T: TMEM -> scale -> split -> B2 (rows p*16 + vv', K index = row of T) ----
+    // ---- T: TMEM -> scale -> split -> B2 (rows p*NR + vv'; K index Q for T_r, ngp + Q for T_i) ----
     int eT = 0;
     if (ok) {
-        constexpr int kHalf = kNVV * kG / 2;
-        const int row = 32 * (warp & 3) + lane;                 // row of T = K index of B2
-        const int c0 = (warp >> 2) * kHalf;                     // warps 4..7 take the upper columns
-        float v[kHalf];
-#pragma unroll
-        for (int cb = 0; cb < kHalf; cb += 8)
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cb), v + cb);
+        const int row = 32 * (warp & 3) + lane;                 // lane of TMEM = Q
+        const int half = warp >> 2;                             // warps 0..3: T_r, 4..7: T_i
+        const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * NB);
         float mx = 0.f;
-        if (row < K)
+        for (int cb = 0; cb < NB; cb += 8) {
+            float v[8];
+            tc::tmem_ld8(tbase + (uint32_t)cb, v);
+            if (row < ngp)
 #pragma unroll
-            for (int j = 0; j < kHalf; ++j) mx = fmaxf(mx, fabsf(v[j]));
+                for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fabsf(v[j]));
+        }
         eT = scale_exp(block_max(mx, &s_max));
         const float sT = pow2f(eT);
-        if (row < K) {
+        for (int cb = 0; cb < NB; cb += 8) {
+            float v[8];
+            tc::tmem_ld8(tbase + (uint32_t)cb, v);
+            if (row < ngp) {
 #pragma unroll
-            for (int j = 0; j < kHalf; ++j) {
-                E h, l;
-                split16(v[j] * sT, h, l);
-                *(E*)(Bm + core_off(c0 + j, row, K)) = h;
-                *(E*)(Bm + b_half + core_off(c0 + j, row, K)) = l;
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t o = core_off(cb + j, half * ngp + row, K2);
+                    E h, l;
+                    split16(v[j] * sT, h, l);
+                    *(E*)(Bm + o) = h;
+                    *(E*)(Bm + b2h + o) = l;
+                }
             }
         }
     }
-    // ---- MMA2 per pair: K^d = rho_cc'^T T ----
-    const uint32_t idesc2 = tc::idesc_f16(128, kNVV, Elem<E>::kBf16);
+    // ---- MMA2 per pair: K^d = rho_cc'^T T (M = 128, N = NR, K = 2 ngp) ----
+    const uint32_t idesc2 = tc::idesc_f16(128, NR, Elem<E>::kBf16);
     for (int p = 0; p < grp.count && ok; ++p) {
         const float2* rc = RC + (size_t)p * ncc * ngp;
         const float srho = pow2f(s_erho[p]);
@@ -306,23 +342,24 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
             }
             E h, l;
             split16(re * srho, h, l);
-            *(E*)(A2 + core_off(m, Q, K)) = h;
-            *(E*)(A2 + a_half + core_off(m, Q, K)) = l;
+            *(E*)(Am + core_off(m, Q, K2)) = h;
+            *(E*)(Am + a2h + core_off(m, Q, K2)) = l;
             split16(re2 * srho, h, l);
-            *(E*)(A2 + core_off(m, ngp + Q, K)) = h;
-            *(E*)(A2 + a_half + core_off(m, ngp + Q, K)) = l;
+            *(E*)(Am + core_off(m, ngp + Q, K2)) = h;
+            *(E*)(Am + a2h + core_off(m, ngp + Q, K2)) = l;
         }
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
         if (tid == 0) {
-            const uint32_t a0 = tc::smem_u32(A2), b0 = tc::smem_u32(Bm) + (uint32_t)core_off(p * kNVV, 0, K);
-            const uint32_t d = tmem + 64 + 16 * p;
+            const uint32_t lbo = 128, sbo = (uint32_t)(K2 / 8) * 128;
+            const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm) + (uint32_t)core_off(p * NR, 0, K2);
+            const uint32_t d = tmem + 2 * (uint32_t)NB + (uint32_t)(NR * p);
             for (int prod = 0; prod < 3; ++prod) {
-                const uint32_t ab = a0 + (prod == 2 ? (uint32_t)a_half : 0u);
-                const uint32_t bb = b0 + (prod == 1 ? (uint32_t)b_half : 0u);
-                for (int ks = 0; ks < K / 16; ++ks)
+                const uint32_t ab = a0 + (prod == 2 ? (uint32_t)a2h : 0u);
+                const uint32_t bb = b0 + (prod == 1 ? (uint32_t)b2h : 0u);
+                for (int ks = 0; ks < K2 / 16; ++ks)
                     tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
                                 idesc2, (prod | ks) != 0);
             }
@@ -331,16 +368,16 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         ok = __syncthreads_and(tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), kSpin)) != 0;
         tc::fence_after();
     }
-    // ---- epilogue: TMEM -> staging (A2 region) -> -K^d / V into the tile ----
-    float* EPI = (float*)A2;   // [kG][16][128]
+    // ---- epilogue: TMEM -> staging (A region) -> -K^d / V into the tile ----
+    float* EPI = (float*)Am;   // [kg][NR][128]
     if (ok && warp < 4) {
         const int row = 32 * warp + lane;
         for (int p = 0; p < grp.count; ++p)
-            for (int cb = 0; cb < 16; cb += 8) {
+            for (int cb = 0; cb < NR; cb += 8) {
                 float v[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(64 + 16 * p + cb), v);
+                tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(2 * NB + NR * p + cb), v);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) EPI[((size_t)p * 16 + cb + j) * 128 + row] = v[j];
+                for (int j = 0; j < 8; ++j) EPI[((size_t)p * NR + cb + j) * 128 + row] = v[j];
             }
     }
     __syncthreads();
@@ -354,7 +391,7 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
             for (int e = tid; e < B * B; e += blockDim.x) {
                 const int r = e % B, col = e / B;
                 const int v = r / nc, c = r % nc, vp = col / nc, cp = col % nc;
-                const float* ep = EPI + ((size_t)p * 16 + v * nv + vp) * 128;
+                const float* ep = EPI + ((size_t)p * NR + v * nv + vp) * 128;
                 float2 val = make_float2(scale * ep[c * nc + cp], scale * ep[ncc + c * nc + cp]);
                 Xt[(int64_t)(t.col0 + col) * t.ld + t.row0 + r] = val;
                 if (t.flags & 1) Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + col] = make_float2(val.x, -val.y);
@@ -384,41 +421,47 @@ __global__ void wexp_kernel(DevSys S, int* wexp) {
     if (threadIdx.x == 0) wexp[q] = e;
 }
 
-// W(q) 2^wexp[q] as a real embedding in the core-matrix layout, hi then lo,
-// zero padded; at q = 0 the head and wings are dropped.
+// W(q) 2^wexp[q] as four planes in the core-matrix layout (128 rows Q x ngp
+// columns Q' each): Wr hi, Wr lo, Wi hi, Wi lo; zero padded; at q = 0 the
+// head and wings are dropped.
 template <typename E>
 __global__ void wemb_kernel(DevSys S, int ngp, const int* __restrict__ wexp, E* out) {
-    const int K = 2 * ngp;
-    const int64_t per = (int64_t)128 * K;
+    const int64_t per = (int64_t)128 * ngp;
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)S.nk * per) return;
-    const int q = (int)(id / per);
-    const int m = (int)((id % per) / K), k = (int)(id % K);
+    if (id >= (int64_t)S.nk * 2 * per) return;
+    const int q = (int)(id / (2 * per));
+    const int part = (int)((id / per) % 2);   // 0: Re W, 1: Im W
+    const int m = (int)((id % per) / ngp), k = (int)(id % ngp);
     const int ng = S.ng[q];
     float v = 0.f;
-    const int Q = m < ngp ? m : m - ngp, Qp = k < ngp ? k : k - ngp;
-    if (m < 2 * ngp && Q < ng && Qp < ng && !(q == 0 && (Q == S.g0 || Qp == S.g0))) {
-        double2 w = S.w[((int64_t)q * S.ng_max + Q) * S.ng_max + Qp];
-        // [[Wr, Wi], [Wi, -Wr]]
-        double x = (m < ngp) ? (k < ngp ? w.x : w.y) : (k < ngp ? w.y : -w.x);
-        v = (float)ldexp(x, wexp[q]);
+    if (m < ng && k < ng && !(q == 0 && (m == S.g0 || k == S.g0))) {
+        const double2 w = S.w[((int64_t)q * S.ng_max + m) * S.ng_max + k];
+        v = (float)ldexp(part == 0 ? w.x : w.y, wexp[q]);
     }
     E h, l;
     split16(v, h, l);
-    E* base = out + (int64_t)q * 2 * per;
-    *(E*)((unsigned char*)base + core_off(m, k, K)) = h;
-    *(E*)((unsigned char*)(base + per) + core_off(m, k, K)) = l;
+    unsigned char* base = (unsigned char*)(out + (int64_t)q * 4 * per + (int64_t)(2 * part) * per);
+    *(E*)(base + core_off(m, k, ngp)) = h;
+    *(E*)(base + per * sizeof(E) + core_off(m, k, ngp)) = l;
 }
 
-int tc_supported(const DevSys& s, int& ngp, size_t& smem) {
-    ngp = (s.ng_max + 7) / 8 * 8;
-    smem = tc_plan(ngp, s.nb, s.nv, s.nc, s.npw_max, s.ng_max).total;
-    if (ngp > 64) return fail(BSE_EUNSUPPORTED, "split precision needs NG <= 64 (have %d)", s.ng_max);
-    if (s.nv * s.nv > kNVV) return fail(BSE_EUNSUPPORTED, "split precision needs nv <= 4");
+int tc_supported(const DevSys& s, int& ngp, size_t& smem, int* kg_out) {
+    ngp = (s.ng_max + 15) / 16 * 16;
+    if (ngp > 128) return fail(BSE_EUNSUPPORTED, "split precision needs NG <= 128 (have %d)", s.ng_max);
+    if (3 * tc_rows(s.nv) > kTmemCols) return fail(BSE_EUNSUPPORTED, "split precision needs nv <= 8");
     if (2 * s.nc * s.nc > 128) return fail(BSE_EUNSUPPORTED, "split precision needs nc <= 8");
     if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
-    if (smem > 227 * 1024) return fail(BSE_EUNSUPPORTED, "split precision needs %zu bytes of shared memory", smem);
-    return BSE_OK;
+    smem = 0;
+    for (int kg = kMaxG; kg >= 1; kg /= 2) {
+        if (3 * tc_rows(s.nv) * kg > kTmemCols) continue;
+        smem = tc_plan(kg, ngp, s.nb, s.nv, s.nc, s.npw_max, s.ng_max).total;
+        if (smem <= kSmemBudget) {
+            smem = zmax(smem, kSmemFloor);
+            if (kg_out) *kg_out = kg;
+            return BSE_OK;
+        }
+    }
+    return fail(BSE_EUNSUPPORTED, "split precision needs %zu bytes of shared memory", smem);
 }
 
 int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st) {
@@ -426,7 +469,7 @@ int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaSt
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(BSE_ECUDA, "wexp launch: %s", cudaGetErrorString(e));
-    int64_t n = (int64_t)s.nk * 128 * 2 * ngp;
+    int64_t n = (int64_t)s.nk * 2 * 128 * ngp;   // one thread per (q, Re/Im, row, column)
     if (fp16)
         wemb_kernel<__half><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, ngp, wexp, (__half*)out);
     else
@@ -441,15 +484,16 @@ template <typename E>
 static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* wemb, const int* wexp, int ngp,
                               const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
                               cudaStream_t st) {
-    int ngp2;
+    int ngp2, kg = 1;
     size_t sm;
-    BSE_TRY(tc_supported(s, ngp2, sm));
+    BSE_TRY(tc_supported(s, ngp2, sm, &kg));
+    if (ngp2 != ngp) return fail(BSE_EINVAL, "split precision: W embedding for NGp %d, system needs %d", ngp, ngp2);
     cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc smem %zu: %s", sm, cudaGetErrorString(e));
     for (int64_t off = 0; off < ngroups; off += 1 << 30) {
         int64_t n = ngroups - off < (1 << 30) ? ngroups - off : (1 << 30);
         direct_tc_kernel<E><<<(unsigned)n, 256, sm, st>>>(s, (const float2*)coef32, (const E*)wemb, wexp, tasks,
-                                                          groups + off, ngp, (float2*)X, status);
+                                                          groups + off, ngp, kg, (float2*)X, status);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc launch: %s", cudaGetErrorString(e));

@@ -508,6 +508,56 @@ static void orbit_matrix(const Tables& t, int o, const double* w, std::vector<cp
     }
 }
 
+// Column jj of that restriction alone (P e_I for the orbit's member jj), into col[0, n_o).
+static void orbit_column(const Tables& t, int o, const double* w, int64_t jj, cplx* col) {
+    const int nv = t.nv, nc = t.nc, nb = t.nb;
+    const int vn = t.orbit_vn[o], cn = t.orbit_cn[o], vlo = t.orbit_vlo[o], clo = t.orbit_clo[o];
+    const int blk = vn * cn;
+    const int64_t m0 = t.orbit_off[o], n_o = t.orbit_off[o + 1] - m0;
+    for (int64_t i = 0; i < n_o; ++i) col[i] = 0.0;
+    const int64_t I = t.orbit_members[m0 + jj];
+    const int k = (int)(I / (nv * nc));
+    const int v = (int)((I / nc) % nv), c = (int)(I % nc);
+    const int64_t ov = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + v];
+    const int64_t oc = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + nv + c];
+    for (int s = 0; s < t.nops; ++s) {
+        if (w[s] == 0.0) continue;
+        const int k2 = t.rotk[(size_t)s * t.nk + k];
+        const int64_t base = (int64_t)t.pos_in_star[k2] * blk;
+        const cplx* gvb = &t.gamma[(size_t)s * t.gam_per_s + ov];
+        const cplx* gcb = &t.gamma[(size_t)s * t.gam_per_s + oc];
+        for (int vp = 0; vp < vn; ++vp) {
+            const cplx gv = gvb[vp * vn + (v - vlo)];
+            if (gv == 0.0) continue;
+            const cplx wg = w[s] * std::conj(gv);
+            for (int cp = 0; cp < cn; ++cp) col[base + vp * cn + cp] += wg * gcb[cp * cn + (c - clo)];
+        }
+    }
+}
+
+// Tr P on orbit o (its rank, P being a projector that leaves the orbit invariant):
+// only the operations fixing the member's k contribute to a diagonal element.
+static double orbit_trace(const Tables& t, int o, const double* w) {
+    const int nv = t.nv, nc = t.nc, nb = t.nb;
+    const int vn = t.orbit_vn[o], cn = t.orbit_cn[o], vlo = t.orbit_vlo[o], clo = t.orbit_clo[o];
+    const int64_t m0 = t.orbit_off[o], n_o = t.orbit_off[o + 1] - m0;
+    double tr = 0.0;
+    for (int64_t jj = 0; jj < n_o; ++jj) {
+        const int64_t I = t.orbit_members[m0 + jj];
+        const int k = (int)(I / (nv * nc));
+        const int v = (int)((I / nc) % nv), c = (int)(I % nc);
+        const int64_t ov = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + v];
+        const int64_t oc = t.gam_koff[k] + t.gam_boff[(size_t)k * nb + nv + c];
+        for (int s = 0; s < t.nops; ++s) {
+            if (w[s] == 0.0 || t.rotk[(size_t)s * t.nk + k] != k) continue;
+            const cplx gv = t.gamma[(size_t)s * t.gam_per_s + ov + (v - vlo) * vn + (v - vlo)];
+            const cplx gc = t.gamma[(size_t)s * t.gam_per_s + oc + (c - clo) * cn + (c - clo)];
+            tr += (w[s] * std::conj(gv) * gc).real();
+        }
+    }
+    return tr;
+}
+
 // run f(o) for every orbit on a small pool of host threads
 template <class F>
 static void for_each_orbit(int no, F f) {
@@ -540,12 +590,14 @@ int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& o
     std::vector<int> nacc_o(no, 0);
     for_each_orbit(no, [&](int o) {
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
-        std::vector<cplx> M, x(n_o);
-        orbit_matrix(t, o, w.data(), M);
+        std::vector<cplx> x(n_o);
+        // the orbit contributes rank = Tr P vectors; the columns after the one that
+        // completes them have zero residual, so they are neither formed nor projected
+        const long rank = std::lround(orbit_trace(t, o, w.data()));
         std::vector<cplx>& acc = acc_o[o];
         int nacc = 0;
-        for (int64_t jj = 0; jj < n_o; ++jj) {
-            std::copy(M.begin() + (size_t)jj * n_o, M.begin() + (size_t)(jj + 1) * n_o, x.begin());
+        for (int64_t jj = 0; jj < n_o && nacc < rank; ++jj) {
+            orbit_column(t, o, w.data(), jj, x.data());
             for (int pass = 0; pass < 2; ++pass)
                 for (int a = 0; a < nacc; ++a) {
                     const cplx* u = &acc[(size_t)a * n_o];
@@ -588,14 +640,38 @@ int build_basis(const Tables& t, int mu, Basis& out) {
     return build_basis_weighted(t, w, out);
 }
 
-// Matrices Gamma_mu(s) = E^T A(s) E of an irrep contained once in the
-// polar-vector representation, E an orthonormal basis of the range of
-// d/|S| sum chi(s) A(s) chosen by Gram-Schmidt over the axes x, y, z.
-int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam) {
-    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
-    if (t.bright[mu] != 1)
-        return fail(BSE_EUNSUPPORTED, "irrep %d is not contained once in the polar-vector representation", mu);
-    d = t.irrep_dim[mu];
+// Modified Gram-Schmidt (two passes) over the n-vectors cols[j*n .. j*n+n),
+// j = 0..m-1 in order, keeping a vector when its residual norm exceeds tol,
+// at most `keep` of them; out: the kept vectors, column j at out[j*n].
+static int gram_schmidt_real(const std::vector<double>& cols, int n, int m, int keep, double tol,
+                             std::vector<double>& out) {
+    out.clear();
+    int r = 0;
+    std::vector<double> x(n);
+    for (int j = 0; j < m && r < keep; ++j) {
+        for (int i = 0; i < n; ++i) x[i] = cols[(size_t)j * n + i];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int u = 0; u < r; ++u) {
+                const double* e = &out[(size_t)u * n];
+                double dt = 0;
+                for (int i = 0; i < n; ++i) dt += e[i] * x[i];
+                for (int i = 0; i < n; ++i) x[i] -= e[i] * dt;
+            }
+        double nr = 0;
+        for (int i = 0; i < n; ++i) nr += x[i] * x[i];
+        nr = std::sqrt(nr);
+        if (nr > tol) {
+            for (int i = 0; i < n; ++i) out.push_back(x[i] / nr);
+            ++r;
+        }
+    }
+    return r;
+}
+
+// Gamma_mu(s) = E^T A(s) E for an irrep contained once in the polar-vector
+// representation, E an orthonormal basis of the range of d/|S| sum chi(s) A(s)
+// chosen by Gram-Schmidt over the axes x, y, z.
+static int cartesian_irrep_matrices(const Tables& t, int mu, int d, std::vector<double>& gam) {
     double pv[9] = {0};
     for (int s = 0; s < t.nops; ++s)
         for (int i = 0; i < 9; ++i) pv[i] += (double)d / t.nops * t.chi[(size_t)mu * t.nops + s] * t.cart[9 * s + i];
@@ -619,6 +695,117 @@ int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam) 
                     for (int b = 0; b < 3; ++b) acc += E[i][a] * t.cart[9 * s + 3 * a + b] * E[j][b];
                 gam[((size_t)s * d + i) * d + j] = acc;
             }
+    return BSE_OK;
+}
+
+// Real orthogonal matrices of a d-dimensional irrep (real characters) from
+// the left regular representation R(s) e_b = e_{sb}:
+//   P_ab = d/|S| chi(a b^-1) projects onto the d copies of the irrep; B is
+//   Gram-Schmidt over its columns (d^2 vectors).  C = sum_s R(s) X R(s)^T,
+//   X a fixed generic symmetric matrix (two-dimensional Kronecker sequence),
+//   commutes with the group, so B^T C B has d eigenvalues, d-fold each, whose
+//   eigenspaces are single copies of the irrep.  The lowest one, E, is made
+//   canonical through its projector: Gram-Schmidt over (E E^T) e_0, e_1, ...
+//   gives E', and Gamma(s) = E'^T R(s) E'.
+static int regular_irrep_matrices(const Tables& t, int mu, int d, std::vector<double>& gam) {
+    const int G = t.nops, d2 = d * d;
+    std::vector<int> inv(G, -1);
+    for (int a = 0; a < G; ++a)
+        for (int b = 0; b < G; ++b)
+            if (t.mult[(size_t)a * G + b] == t.identity) inv[a] = b;
+    const int32_t* chi = &t.chi[(size_t)mu * G];
+    std::vector<double> P((size_t)G * G), B;
+    for (int b = 0; b < G; ++b)
+        for (int a = 0; a < G; ++a) P[(size_t)b * G + a] = (double)d / G * chi[t.mult[(size_t)a * G + inv[b]]];
+    if (gram_schmidt_real(P, G, G, d2, 1e-6, B) != d2) return fail(BSE_ESYMM, "irrep %d: projector rank is not d^2", mu);
+    const double g1 = 0.7548776662466927, g2 = 0.5698402909980532;
+    auto frac = [](double x) { return x - std::floor(x); };
+    std::vector<double> X((size_t)G * G), C((size_t)G * G, 0.0);
+    for (int a = 0; a < G; ++a)
+        for (int b = 0; b < G; ++b)
+            X[(size_t)a * G + b] = frac(g1 * (a + 1) + g2 * (b + 1)) + frac(g1 * (b + 1) + g2 * (a + 1)) - 1.0;
+    for (int s = 0; s < G; ++s) {
+        const int32_t* row = &t.mult[(size_t)inv[s] * G];   // a -> s^-1 a
+        for (int a = 0; a < G; ++a)
+            for (int b = 0; b < G; ++b) C[(size_t)a * G + b] += X[(size_t)row[a] * G + row[b]];
+    }
+    std::vector<double> CB((size_t)G * d2, 0.0), M((size_t)d2 * d2, 0.0), V, W;
+    for (int j = 0; j < d2; ++j)
+        for (int a = 0; a < G; ++a) {
+            double acc = 0;
+            for (int b = 0; b < G; ++b) acc += C[(size_t)a * G + b] * B[(size_t)j * G + b];
+            CB[(size_t)j * G + a] = acc;
+        }
+    for (int i = 0; i < d2; ++i)
+        for (int j = 0; j < d2; ++j) {
+            double acc = 0;
+            for (int a = 0; a < G; ++a) acc += B[(size_t)i * G + a] * CB[(size_t)j * G + a];
+            M[(size_t)i * d2 + j] = acc;
+        }
+    jacobi(M, d2, V, W);
+    std::vector<int> order(d2);
+    for (int i = 0; i < d2; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return W[x] < W[y]; });
+    double wmax = 1.0;
+    for (double w : W) wmax = std::max(wmax, std::fabs(w));
+    if (!(W[order[d]] - W[order[d - 1]] > 1e-8 * wmax))
+        return fail(BSE_ESYMM, "irrep %d: degenerate commutant spectrum", mu);
+    std::vector<double> E((size_t)G * d, 0.0), Q((size_t)G * G, 0.0), Ec;
+    for (int c = 0; c < d; ++c)
+        for (int j = 0; j < d2; ++j) {
+            const double y = V[(size_t)j * d2 + order[c]];   // eigenvector order[c], component j
+            for (int a = 0; a < G; ++a) E[(size_t)c * G + a] += B[(size_t)j * G + a] * y;
+        }
+    for (int b = 0; b < G; ++b)
+        for (int a = 0; a < G; ++a) {
+            double acc = 0;
+            for (int c = 0; c < d; ++c) acc += E[(size_t)c * G + a] * E[(size_t)c * G + b];
+            Q[(size_t)b * G + a] = acc;
+        }
+    if (gram_schmidt_real(Q, G, G, d, 1e-6, Ec) != d) return fail(BSE_ESYMM, "irrep %d: eigenspace rank is not d", mu);
+    gam.assign((size_t)G * d * d, 0.0);
+    for (int s = 0; s < G; ++s)
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double acc = 0;
+                for (int b = 0; b < G; ++b) acc += Ec[(size_t)i * G + t.mult[(size_t)s * G + b]] * Ec[(size_t)j * G + b];
+                gam[((size_t)s * d + i) * d + j] = acc;
+            }
+    return BSE_OK;
+}
+
+// Real orthogonal matrices Gamma_mu(s) of irrep mu: the Cartesian route for
+// an irrep contained once in the polar-vector representation, chi itself for
+// a one-dimensional irrep, the regular-representation route otherwise.  The
+// result is checked: a representation with trace chi.
+int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam) {
+    if (mu < 0 || mu >= t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range", mu);
+    d = t.irrep_dim[mu];
+    const int G = t.nops;
+    if (t.bright[mu] == 1) {
+        BSE_TRY(cartesian_irrep_matrices(t, mu, d, gam));
+    } else if (d == 1) {
+        gam.resize(G);
+        for (int s = 0; s < G; ++s) gam[s] = t.chi[(size_t)mu * G + s];
+    } else {
+        BSE_TRY(regular_irrep_matrices(t, mu, d, gam));
+    }
+    for (int s1 = 0; s1 < G; ++s1) {
+        double tr = 0;
+        for (int i = 0; i < d; ++i) tr += gam[((size_t)s1 * d + i) * d + i];
+        if (std::fabs(tr - t.chi[(size_t)mu * G + s1]) > 1e-9) return fail(BSE_ESYMM, "irrep %d: trace is not chi", mu);
+        for (int s2 = 0; s2 < G; ++s2) {
+            const double* g12 = &gam[(size_t)t.mult[(size_t)s1 * G + s2] * d * d];
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    double acc = 0;
+                    for (int k = 0; k < d; ++k)
+                        acc += gam[((size_t)s1 * d + i) * d + k] * gam[((size_t)s2 * d + k) * d + j];
+                    if (std::fabs(acc - g12[i * d + j]) > 1e-9)
+                        return fail(BSE_ESYMM, "irrep %d: matrices are not a representation", mu);
+                }
+        }
+    }
     return BSE_OK;
 }
 

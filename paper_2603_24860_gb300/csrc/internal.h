@@ -213,7 +213,9 @@ int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, co
 int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st);
 void note_launch();
 // split-precision tensor-core direct term (direct_tc.cu)
-int tc_supported(const DevSys& s, int& ngp, size_t& smem);
+// split-precision support for a system: NG padded to 16 (ngp), the shared memory of a CTA and the
+// number of k pairs per group (kg, at most 4); EUNSUPPORTED when the sizes do not fit
+int tc_supported(const DevSys& s, int& ngp, size_t& smem, int* kg = nullptr);
 // split-precision W(q) embeddings (fp16 != 0: fp16 hi + lo, else bf16) and their per-q scale exponents
 int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st);
 int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
@@ -234,6 +236,16 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // ev0 / ev1 (may be null) are recorded around the reduction kernel
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+// lanczos.cu: the Lanczos recurrence on a Hermitian block from conj(b) (Lanczos-Haydock, Sec. IV)
+size_t lanczos_scratch_bytes(int64_t n, int m);
+int lanczos_max_dim();
+// steps: requested; on return *done (host) = steps performed, alpha [done], beta [done] (beta[j] couples j-1, j)
+int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, int steps, void* scratch,
+                   double** alpha, double** beta, int* done, cudaStream_t st);
+// T_m dense (k x k column-major) from alpha and beta1 (beta1[j] couples j, j + 1); Gauss weights
+// scale V[0][j]^2 from its eigenvector matrix V
+int launch_tm_dense(const double* alpha, const double* beta1, int k, double* T, cudaStream_t st);
+int launch_tm_weights(const double* V, int k, double scale, double* w, cudaStream_t st);
 // loss.cu: longitudinal levels (Eq. secular) and strengths (Eq. eigenvec_xi)
 size_t loss_scratch_bytes(int64_t n);
 int launch_loss_levels(const double* Om, const double* osc, int64_t n, double alpha, void* scratch, double* out_l,

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "fp64_fast.h"
+#include "grid_sync.h"
 #include "internal.h"
 
 namespace bse {
@@ -34,7 +35,6 @@ namespace {
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kChunk = 8;                 // columns reduced together
-constexpr long kSpinLimit = 1l << 23;     // >= 32 ns + an L2 round trip per poll: seconds
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -48,35 +48,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid barrier of a cooperative launch (all CTAs co-resident): one
-// release-add per CTA and acquire-polling of the counter.  Bounded: on
-// timeout, or when another CTA has raised the error flag, returns false.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, int* s_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-        bool ok = false;
-        for (long it = 0; it < kSpinLimit; ++it) {
-            if (ld_acquire(bar) >= target) {
-                ok = true;
-                break;
-            }
-            if (*(volatile int*)err) break;
-            if (it > 64) __nanosleep(32);
-        }
-        if (!ok) atomicExch(err, 1);
-        *s_flag = ok ? 1 : 0;
-    }
-    __syncthreads();
-    return *s_flag != 0;
 }
 
 // Rank-2 update  A_rc -= v_r conj(w_c) + w_r conj(v_c)  of a chunk, eight FMAs per element

@@ -2,9 +2,11 @@
 9x9x1 to 18x18x3 meshes and Si-like Oh cells on 4^3 to 7^3 meshes, N_v and
 N_c from 2 to 6, seeded): the partner block of each instance's optically
 active irrep (E1u for q along x in D6h, T1u in Oh) from one graph launch in
-FP32 and FP64.  Every block equals the single-context build; the FP32
-levels agree with the FP64 ones within 0.1 meV for every instance; sampled
-star-pair sub-blocks of the smallest MoS2-like instance match the oracle."""
+FP32, FP64 and both split precisions (tensor-core direct term, one launch per
+instance in the graph).  Every block equals the single-context build; the
+FP32 and split levels agree with the FP64 ones within 0.1 meV for every
+instance; sampled star-pair sub-blocks of the smallest MoS2-like instance
+match the oracle."""
 import numpy as np
 import pytest
 
@@ -27,7 +29,8 @@ def batch():
         mus.append(mu)
         dims.append(int(t["partner_dim"][mu]))
     out = {}
-    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64)):
+    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64), ("bf16", bse.BSE_BF16_SPLIT),
+                       ("fp16", bse.BSE_FP16_SPLIT)):
         bufs = [torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda") for n in dims]
         b = bse.bse_batch_create(ctxs, mus, [1] * len(ctxs), prec, bse.BSE_TERM_ALL, bufs, [max(n, 1) for n in dims])
         bse.bse_batch_run(b)
@@ -51,14 +54,15 @@ def test_batch_shape(batch):
 @pytest.mark.parametrize("i", list(range(0, 32, 3)))
 def test_batch_equals_single_builds(batch, i):
     bse, torch, cfgs, ctxs, mus, dims, out = batch
-    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64)):
+    for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64), ("fp16", bse.BSE_FP16_SPLIT)):
         single = bse.partner_block(ctxs[i], mus[i], prec=prec)
         got = out[name][i]
         scale = float(torch.max(torch.abs(single)).item())
         assert float(torch.max(torch.abs(got - single)).item()) <= 1e-13 * scale, (cfgs[i].name, name)
 
 
-def test_batch_fp32_levels_within_0p1_mev(batch):
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_batch_levels_within_0p1_mev(batch, prec):
     bse, torch, cfgs, ctxs, mus, dims, out = batch
     from synth.generate import generate
     worst = 0.0
@@ -68,8 +72,8 @@ def test_batch_fp32_levels_within_0p1_mev(batch):
         d = generate(cfgs[i])
         omega = torch.tensor(d["omega"], device="cuda")
         om64 = bse.partner_spectrum(c, mus[i], out["fp64"][i], omega, d["eta"])[0].cpu().numpy()
-        om32 = bse.partner_spectrum(c, mus[i], out["fp32"][i], omega, d["eta"])[0].cpu().numpy()
-        worst = max(worst, float(np.abs(om32 - om64).max()) * HA_MEV)
+        oml = bse.partner_spectrum(c, mus[i], out[prec][i], omega, d["eta"])[0].cpu().numpy()
+        worst = max(worst, float(np.abs(oml - om64).max()) * HA_MEV)
     assert worst <= 0.1
 
 

@@ -1,9 +1,10 @@
 """Full-size checks for the Si-like 12x12x12 mesh (Nv = 4, Nc = 8,
 |G| <= 4.0 (2 pi / a), N = 55296): the T1u partner block is built in FP64
-and FP32 in the launch configuration of the benchmark; sampled star-pair
+and FP32 in the launch configuration of the benchmark, and in both split
+precisions (tensor-core direct term, NG up to 73); sampled star-pair
 sub-blocks are compared with the oracle (its canonical basis restricted to
-the two stars, U_a^dagger H_ab U_b), and the FP32 levels with the FP64
-ones (0.1 meV)."""
+the two stars, U_a^dagger H_ab U_b), and the FP32 and split levels with the
+FP64 ones (0.1 meV)."""
 import json
 import os
 
@@ -65,6 +66,37 @@ def test_sampled_partner_sub_blocks(si12, pair):
     sub = lambda h: h[cols[a]:cols[a + 1], cols[b]:cols[b + 1]].cpu().numpy()
     assert np.abs(sub(h64) - ref).max() <= 1e-10 * scale
     assert np.abs(sub(h32) - ref).max() <= 2e-6 * scale
+
+
+SPLIT_TOL = {"BSE_BF16_SPLIT": 2e-5, "BSE_FP16_SPLIT": 4e-6}
+
+
+@pytest.mark.parametrize("split", ["BSE_FP16_SPLIT", "BSE_BF16_SPLIT"])
+def test_split_partner_block(si12, split):
+    """Split-precision partner block: a sampled star-pair sub-block against
+    the oracle, the levels within 0.1 meV and the spectrum within 1e-3
+    relative L2 of the FP64 build."""
+    from oracle.hamiltonian import hamiltonian_block
+    from oracle.projection import partner_irrep_matrices, star_basis
+    bse, torch, ctx, t, mu, h64, h32, cols, d, inp, grp, mt, orb = si12
+    hs = bse.partner_block(ctx, mu, prec=getattr(bse, split))
+    scale = float(torch.max(torch.abs(h64)).item())
+    assert float(torch.max(torch.abs(hs - h64)).item()) <= SPLIT_TOL[split] * scale
+    chi, dims, cls = grp.characters()
+    gam = partner_irrep_matrices(grp, chi[mu], int(dims[mu]))
+    w = int(dims[mu]) / grp.n * gam[:, 0, 0]
+    sizes = np.array([len(s) for s in mt.stars])
+    a = b = int(np.nonzero(sizes == 12)[0][0])
+    ra, Ua = star_basis(inp, grp, mt, orb, a, w)
+    Hab = hamiltonian_block(inp, mt, [int(k) for k in mt.stars[a]], [int(k) for k in mt.stars[b]], GOLD["si12"])
+    ref = Ua.conj().T @ Hab @ Ua
+    sub = hs[cols[a]:cols[a + 1], cols[b]:cols[b + 1]].cpu().numpy()
+    assert np.abs(sub - ref).max() <= SPLIT_TOL[split] * scale
+    omega = torch.tensor(d["omega"], device="cuda")
+    om64, osc64, im64 = (x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h64, omega, d["eta"]))
+    oms, oscs, ims = (x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, hs, omega, d["eta"]))
+    assert np.abs(oms - om64).max() * HA_MEV <= 0.1
+    assert np.linalg.norm(ims - im64) <= 1e-3 * np.linalg.norm(im64)
 
 
 def test_fp32_levels_within_0p1_mev(si12):
