@@ -328,20 +328,20 @@ int bse_partner_spectrum(bse_ctx* ctx, int32_t irrep, const void* h_dev, int64_t
  * steps of the Hermitian Lanczos recurrence on h_dev (the block of irrep, or
  * its partner block when partner != 0; device, complex128 column-major,
  * leading dimension ld, read only) from the dipole direction conj(U^T B),
- * without reorthogonalisation; the tridiagonal T_m it builds gives the Ritz
- * values ritz[k] (ascending) and Gauss weights weights[k] = sum_i |U_i^T B|^2
- * z_0(k)^2 (z_0 the first components of T_m's eigenvectors, from cuSOLVER's
- * dense symmetric eigensolver on the small T_m), and im_eps the Lorentzian
- * sum over them, which equals the continued fraction of the Haydock method.
- * The first 2 m moments of the spectral measure are reproduced; an
- * invariant subspace ends the recurrence early and the spectrum is then
- * exact.  ritz, weights: device, [steps], zero beyond *steps_done (host: the
- * steps performed).  A dark irrep (no dipole weight) gives an empty spectrum
- * and *steps_done = 0.
- * Errors: EINVAL for steps outside [1, dim]; EUNSUPPORTED for dim above the
- * shared-memory capacity (about 14 000) or non-parallel partner projections;
- * ETIMEOUT if a bounded grid barrier gave up; ESOLVER if the dense
- * eigensolver of the small T_m fails.
+ * without reorthogonalisation, build the tridiagonal T_m; im_eps is the
+ * continued fraction of T_m (the Haydock spectrum), which reproduces the
+ * first 2 m moments of the spectral measure; an invariant subspace ends the
+ * recurrence early and the spectrum is then exact.  ritz_dev and weights_dev
+ * are optional (both NULL or both device arrays of [steps]): the Ritz values
+ * of T_m (ascending) and its Gauss weights sum_i |U_i^T B|^2 z_0(k)^2 (z_0
+ * the first components of T_m's eigenvectors, from cuSOLVER's dense
+ * symmetric eigensolver on the small T_m), zero beyond *steps_done, whose
+ * Lorentzian sum equals im_eps.  *steps_done (host): the steps performed.  A
+ * dark irrep (no dipole weight) gives an empty spectrum and *steps_done = 0.
+ * Errors: EINVAL for steps outside [1, dim] or only one of ritz_dev and
+ * weights_dev; EUNSUPPORTED for dim above 12 000 or non-parallel partner
+ * projections; ETIMEOUT if a bounded grid barrier gave up; ESOLVER if the
+ * dense eigensolver of T_m fails.
  */
 int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, const void* h_dev, int64_t ld,
                                int32_t steps, const double* omega_dev, int64_t n_omega, double eta,

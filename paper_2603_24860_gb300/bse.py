@@ -501,17 +501,19 @@ def partner_spectrum(ctx: Context, irrep: int, h, omega, eta: float):
     return om[:n], osc[:n], im
 
 
-def lanczos_spectrum(ctx: Context, irrep: int, h, omega, eta: float, steps: int, partner: bool = False):
+def lanczos_spectrum(ctx: Context, irrep: int, h, omega, eta: float, steps: int, partner: bool = False,
+                     ritz: bool = True):
     """(Ritz values, Gauss weights, Im eps_M) of the Lanczos-Haydock spectrum
-    of a block (or partner block) after at most `steps` steps."""
+    of a block (or partner block) after at most `steps` steps; with
+    ritz=False only Im eps_M (the first two are None)."""
     import torch
     n = h.shape[0]
     ld = h.stride(1) if n else 1
-    rz = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda")
-    wt = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda")
+    rz = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda") if ritz else None
+    wt = torch.empty(max(steps, 1), dtype=torch.float64, device="cuda") if ritz else None
     im = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
     k = bse_block_spectrum_lanczos(ctx, irrep, partner, h, ld, steps, omega, eta, rz, wt, im)
-    return rz[:k], wt[:k], im
+    return (rz[:k], wt[:k], im) if ritz else (None, None, im)
 
 
 def full(ctx: Context, terms: int = BSE_TERM_ALL):

@@ -1723,7 +1723,7 @@ int bse_block_spectrum_lanczos(bse_ctx* c, int32_t mu, int32_t partner, const vo
     clear_error();
     if (!c) return fail(BSE_EINVAL, "null context");
     AllocStream alloc_on_(c->stream);
-    if (!h || !ritz || !weights || !steps_done || (n_omega > 0 && (!omega || !im_eps)))
+    if (!h || !steps_done || (!ritz) != (!weights) || (n_omega > 0 && (!omega || !im_eps)))
         return fail(BSE_EINVAL, "null argument");
     if (!(eta > 0)) return fail(BSE_EINVAL, "eta must be positive");
     *steps_done = 0;
@@ -1741,8 +1741,10 @@ int bse_block_spectrum_lanczos(bse_ctx* c, int32_t mu, int32_t partner, const vo
     if (ld < dim) return fail(BSE_EINVAL, "ld < block dimension");
     if (steps < 1 || steps > std::max<int64_t>(dim, 1))
         return fail(BSE_EINVAL, "steps must be in [1, %lld]", (long long)dim);
-    BSE_CUDA(cudaMemsetAsync(ritz, 0, sizeof(double) * steps, c->stream));
-    BSE_CUDA(cudaMemsetAsync(weights, 0, sizeof(double) * steps, c->stream));
+    if (ritz) {
+        BSE_CUDA(cudaMemsetAsync(ritz, 0, sizeof(double) * steps, c->stream));
+        BSE_CUDA(cudaMemsetAsync(weights, 0, sizeof(double) * steps, c->stream));
+    }
     if (dim == 0 || !c->t.bright[mu]) {   // no dipole weight: an empty spectrum
         if (n_omega) BSE_CUDA(cudaMemsetAsync(im_eps, 0, sizeof(double) * n_omega, c->stream));
         return BSE_OK;
@@ -1766,31 +1768,35 @@ int bse_block_spectrum_lanczos(bse_ctx* c, int32_t mu, int32_t partner, const vo
     int done = 0;
     BSE_TRY(launch_lanczos((const double2*)h, ld, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, steps,
                            c->lzScratch.p, &alpha, &beta, &done, c->stream));
-    // eigenpairs of T_done (dense symmetric eigensolver; clusters of Ritz values are harmless there)
-    double* T = (double*)((char*)c->lzScratch.p + lzb);
-    BSE_TRY(launch_tm_dense(alpha, beta + 1, done, T, c->stream));
-    if (!c->solver && cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS)
-        return fail(BSE_ESOLVER, "cusolverDnCreate failed");
-    if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS)
-        return fail(BSE_ESOLVER, "cusolverDnSetStream failed");
-    int lwork = 0;
-    if (cusolverDnDsyevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done, ritz,
-                                    &lwork) != CUSOLVER_STATUS_SUCCESS)
-        return fail(BSE_ESOLVER, "dsyevd buffer size query failed");
-    BSE_TRY(ensure(c->eigWork, sizeof(double) * (size_t)std::max(lwork, 1)));
-    BSE_TRY(ensure(c->info, sizeof(int)));
-    if (cusolverDnDsyevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done, ritz,
-                         (double*)c->eigWork.p, lwork, (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
-        return fail(BSE_ESOLVER, "dsyevd launch failed");
-    BSE_TRY(launch_tm_weights(T, done, scale, weights, c->stream));
-    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     const double pref = 4.0 * M_PI * c->spin / c->t.nk;
-    if (n_omega > 0) BSE_TRY(launch_spectrum(ritz, weights, done, omega, n_omega, eta, pref, im_eps, c->stream));
-    int info = 0;
-    BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    BSE_CUDA(cudaStreamSynchronize(c->stream));
-    if (info != 0) return fail(BSE_ESOLVER, "dsyevd info = %d", info);
-    if (c->timing) BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
+    BSE_TRY(launch_cf_spectrum(alpha, beta + 1, done, scale, omega, n_omega, eta, pref, im_eps, c->stream));
+    if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
+    if (ritz) {   // eigenpairs of T_done (dense symmetric eigensolver; clusters of Ritz values are harmless there)
+        double* T = (double*)((char*)c->lzScratch.p + lzb);
+        BSE_TRY(launch_tm_dense(alpha, beta + 1, done, T, c->stream));
+        if (!c->solver && cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS)
+            return fail(BSE_ESOLVER, "cusolverDnCreate failed");
+        if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS)
+            return fail(BSE_ESOLVER, "cusolverDnSetStream failed");
+        int lwork = 0;
+        if (cusolverDnDsyevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done,
+                                        ritz, &lwork) != CUSOLVER_STATUS_SUCCESS)
+            return fail(BSE_ESOLVER, "dsyevd buffer size query failed");
+        BSE_TRY(ensure(c->eigWork, sizeof(double) * (size_t)std::max(lwork, 1)));
+        BSE_TRY(ensure(c->info, sizeof(int)));
+        if (cusolverDnDsyevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, done, T, done, ritz,
+                             (double*)c->eigWork.p, lwork, (int*)c->info.p) != CUSOLVER_STATUS_SUCCESS)
+            return fail(BSE_ESOLVER, "dsyevd launch failed");
+        BSE_TRY(launch_tm_weights(T, done, scale, weights, c->stream));
+        int info = 0;
+        BSE_CUDA(cudaMemcpyAsync(&info, c->info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+        if (info != 0) return fail(BSE_ESOLVER, "dsyevd info = %d", info);
+    }
+    if (c->timing) {
+        BSE_CUDA(cudaEventSynchronize(c->ev[4]));
+        BSE_CUDA(cudaEventElapsedTime(&c->stats.ms_eig, c->ev[3], c->ev[4]));
+    }
     *steps_done = done;
     return BSE_OK;
 }

@@ -246,6 +246,9 @@ int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, in
 // scale V[0][j]^2 from its eigenvector matrix V
 int launch_tm_dense(const double* alpha, const double* beta1, int k, double* T, cudaStream_t st);
 int launch_tm_weights(const double* V, int k, double scale, double* w, cudaStream_t st);
+// Im eps from the continued fraction of (alpha, beta1) with weight norm2 and prefactor pref
+int launch_cf_spectrum(const double* alpha, const double* beta1, int k, double norm2, const double* omega,
+                       int64_t n_omega, double eta, double pref, double* im, cudaStream_t st);
 // loss.cu: longitudinal levels (Eq. secular) and strengths (Eq. eigenvec_xi)
 size_t loss_scratch_bytes(int64_t n);
 int launch_loss_levels(const double* Om, const double* osc, int64_t n, double alpha, void* scratch, double* out_l,

@@ -10,21 +10,26 @@
 // buffers), so a step needs two grid-wide sums and two grid barriers.  The
 // tridiagonal T_m = (alpha, beta) then gives the Ritz values and Gauss
 // weights (levels of T_m and |c|^2 times the squared first components) whose
-// Lorentzian sum is the continued fraction of the Haydock method; T_m is
-// small and, without reorthogonalisation, has near-coincident Ritz values
-// (copies of converged ones), so its eigenpairs come from a dense symmetric
-// eigensolver, for which such clusters are harmless.
+// Lorentzian sum is the continued fraction of the Haydock method.  Im eps is
+// evaluated from the fraction itself (one thread per frequency); when the
+// Ritz pairs are asked for, T_m (small, and without reorthogonalisation with
+// near-coincident Ritz values, copies of converged ones) goes to a dense
+// symmetric eigensolver, for which such clusters are harmless.
 //
 // GB300 layout: one persistent cooperative kernel, one CTA per SM.  Every CTA
 // holds v_j in shared memory; (H v)_r is the dot product of column r with v
-// (H is Hermitian: (H v)_r = sum_i conj(H_ir) v_i), one warp per column, so
-// the block is read once per step with coalesced loads and no cross-CTA
-// reduction except the two scalars.  The FP64 pipe bounds a step: 4 n^2 DFMA.
+// (H is Hermitian: (H v)_r = sum_i conj(H_ir) v_i).  Column r belongs to CTA
+// r mod G and each of its 8 warps takes one eighth of the rows of every own
+// column (so all SMs work even when n < 8 G), the eight partial dots summed in
+// shared memory: the block is read once per step with coalesced loads and
+// no cross-CTA reduction except the two scalars.  The FP64 pipe bounds a
+// step: 4 n^2 DFMA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 
+#include "fp64_fast.h"
 #include "grid_sync.h"
 #include "internal.h"
 
@@ -75,12 +80,15 @@ struct LzArgs {
 };
 
 __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
-    extern __shared__ __align__(16) double2 s_v[];   // v_j
+    extern __shared__ __align__(16) double2 s_v[];   // v_j [n], then the partial dots [ncl][kLzWarps]
     __shared__ double s_red[kLzWarps];
     __shared__ double s_tot;
     __shared__ int s_flag;
     const int n = (int)a.n, G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int gw = blk * kLzWarps + wid, nw = G * kLzWarps;
+    const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;   // own columns r = blk + G l
+    double2* s_part = s_v + n;
+    const int seg = (n + kLzWarps - 1) / kLzWarps;       // rows of a warp's segment
+    const int i0 = wid * seg, i1 = min(n, i0 + seg);
     unsigned nbar = 0;
     double bj = __ldcg(a.beta), bjm1 = 1.0;
     int steps = a.m;
@@ -120,52 +128,62 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
             s_v[i] = make_double2(u.x * inv, u.y * inv);
         }
         __syncthreads();
-        // y = H v_j - beta_j v_{j-1} on own columns (v_{j-1} = u_{j-1} / beta_{j-1})
-        const double cprev = j > 0 ? bj / bjm1 : 0.0;
-        double p1 = 0.0;
-        for (int r = gw; r < n; r += nw) {
-            const double2* col = a.H + (size_t)r * a.ld;
+        // (H v_j)_r over this warp's rows for every own column, then y = H v_j - beta_j v_{j-1}
+        // (v_{j-1} = u_{j-1} / beta_{j-1}) by the thread that owns column l = tid
+        for (int l = 0; l < ncl; ++l) {
+            const double2* col = a.H + (size_t)(blk + (size_t)l * G) * a.ld;
             double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
-            int i = lane;
-            for (; i + 32 < n; i += 64) {
+            int i = i0 + lane;
+            for (; i + 32 < i1; i += 64) {
                 const double2 h0 = __ldg(col + i), v0 = s_v[i], h1 = __ldg(col + i + 32), v1 = s_v[i + 32];
                 ax = fma(h0.x, v0.x, fma(h0.y, v0.y, ax));
                 ay = fma(h0.x, v0.y, fma(-h0.y, v0.x, ay));
                 bx = fma(h1.x, v1.x, fma(h1.y, v1.y, bx));
                 by = fma(h1.x, v1.y, fma(-h1.y, v1.x, by));
             }
-            if (i < n) {
+            if (i < i1) {
                 const double2 h0 = __ldg(col + i), v0 = s_v[i];
                 ax = fma(h0.x, v0.x, fma(h0.y, v0.y, ax));
                 ay = fma(h0.x, v0.y, fma(-h0.y, v0.x, ay));
             }
             const double sx = lz_warp_sum(ax + bx), sy = lz_warp_sum(ay + by);
-            if (lane == 0) {
-                double2 y = make_double2(sx, sy);
-                if (j > 0) {
-                    const double2 q = __ldcg(ujm1 + r);
-                    y.x = fma(-cprev, q.x, y.x);
-                    y.y = fma(-cprev, q.y, y.y);
-                }
-                ujp1[r] = y;
-                const double2 v = s_v[r];
-                p1 = fma(v.x, y.x, fma(v.y, y.y, p1));   // Re(conj(v) y)
+            if (lane == 0) s_part[l * kLzWarps + wid] = make_double2(sx, sy);
+        }
+        __syncthreads();
+        const double cprev = j > 0 ? bj / bjm1 : 0.0;
+        double p1 = 0.0;
+        for (int l = tid; l < ncl; l += kLzThreads) {
+            const int r = blk + l * G;
+            double2 y = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int w = 0; w < kLzWarps; ++w) {
+                const double2 q = s_part[l * kLzWarps + w];
+                y.x += q.x;
+                y.y += q.y;
             }
+            if (j > 0) {
+                const double2 q = __ldcg(ujm1 + r);
+                y.x = fma(-cprev, q.x, y.x);
+                y.y = fma(-cprev, q.y, y.y);
+            }
+            ujp1[r] = y;
+            const double2 v = s_v[r];
+            p1 = fma(v.x, y.x, fma(v.y, y.y, p1));   // Re(conj(v) y)
         }
         block_part(p1, a.part1);
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
         const double al = grid_total(a.part1);
         // u_{j+1} = y - alpha_j v_j on own columns (the thread that wrote y)
         double p2 = 0.0;
-        if (lane == 0)
-            for (int r = gw; r < n; r += nw) {
-                double2 y = __ldcg(ujp1 + r);
-                const double2 v = s_v[r];
-                y.x = fma(-al, v.x, y.x);
-                y.y = fma(-al, v.y, y.y);
-                ujp1[r] = y;
-                p2 = fma(y.x, y.x, fma(y.y, y.y, p2));
-            }
+        for (int l = tid; l < ncl; l += kLzThreads) {
+            const int r = blk + l * G;
+            double2 y = __ldcg(ujp1 + r);
+            const double2 v = s_v[r];
+            y.x = fma(-al, v.x, y.x);
+            y.y = fma(-al, v.y, y.y);
+            ujp1[r] = y;
+            p2 = fma(y.x, y.x, fma(y.y, y.y, p2));
+        }
         block_part(p2, a.part2);
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
         const double bn = sqrt(grid_total(a.part2));
@@ -199,7 +217,39 @@ __global__ void tm_weights_kernel(const double* __restrict__ V, int k, double sc
     w[j] = scale * z * z;
 }
 
+// Im eps_M(omega) = pref (-Im g(omega + i eta) + Im g(-omega + i eta)) with the continued fraction
+// g(z) = norm2 / (z - a_0 - b_1^2 / (z - a_1 - ... / (z - a_{k-1}))) evaluated from the bottom up;
+// beta1[j] couples j and j + 1.  Every denominator has imaginary part >= eta > 0.
+__global__ void cf_spectrum_kernel(const double* __restrict__ alpha, const double* __restrict__ beta1, int k,
+                                   double norm2, const double* __restrict__ omega, int64_t n_omega, double eta,
+                                   double pref, double* im) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_omega) return;
+    auto im_g = [&](double x) -> double {
+        double tr = x - alpha[k - 1], ti = eta;
+        for (int j = k - 2; j >= 0; --j) {
+            const double b = beta1[j];
+            const double r = b * b * rcp_nr(fma(tr, tr, ti * ti));   // b^2 / t = r conj(t)
+            tr = fma(-r, tr, x - alpha[j]);
+            ti = fma(r, ti, eta);
+        }
+        return -norm2 * ti * rcp_nr(fma(tr, tr, ti * ti));
+    };
+    const double w = omega[i];
+    im[i] = pref * (im_g(-w) - im_g(w));
+}
+
 }  // namespace
+
+int launch_cf_spectrum(const double* alpha, const double* beta1, int k, double norm2, const double* omega,
+                       int64_t n_omega, double eta, double pref, double* im, cudaStream_t st) {
+    if (n_omega < 1) return BSE_OK;
+    cf_spectrum_kernel<<<(unsigned)((n_omega + 127) / 128), 128, 0, st>>>(alpha, beta1, k, norm2, omega, n_omega,
+                                                                            eta, pref, im);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
 
 int launch_tm_dense(const double* alpha, const double* beta1, int k, double* T, cudaStream_t st) {
     tm_dense_kernel<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, st>>>(alpha, beta1, k, T);
@@ -215,7 +265,8 @@ int launch_tm_weights(const double* V, int k, double scale, double* w, cudaStrea
     return BSE_OK;
 }
 
-int lanczos_max_dim() { return (227 * 1024 - 4096) / (int)sizeof(double2); }   // v_j in shared memory
+// v_j and the partial dots of the own columns (at most n / 152 + 1 of them, 8 each) in shared memory
+int lanczos_max_dim() { return 12000; }
 
 size_t lanczos_scratch_bytes(int64_t n, int m) {
     return sizeof(double2) * (size_t)(3 * n) + sizeof(double) * (size_t)(2 * 1024 + 2 * m + 1) + 6 * 256 + 64;
@@ -244,8 +295,10 @@ int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, in
     int dev = 0, sms = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int G = (int)std::min<int64_t>(std::min(sms, 1024), std::max<int64_t>(1, (n + kLzWarps - 1) / kLzWarps));
-    const size_t dyn = sizeof(double2) * (size_t)n;
+    const int G = (int)std::min<int64_t>(std::min(sms, 1024), n);
+    const int ncl_max = (int)((n - 1) / G + 1);
+    const size_t dyn = sizeof(double2) * ((size_t)n + (size_t)ncl_max * kLzWarps);
+    if (dyn > 227 * 1024 - 1024) return fail(BSE_EUNSUPPORTED, "Lanczos path: n = %lld exceeds shared memory", (long long)n);
     BSE_CUDA(cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kLzThreads, dyn));
