@@ -371,12 +371,14 @@ __global__ void reflect0_kernel(const double2* __restrict__ b, int64_t n, double
 
 struct TriBounds {
     double gl, gu, tnorm, pivmin, tol;
-    int m;   // T splits after row m-1 (first |e| <= tol), m = n when it does not
+    int m;           // T splits after row m-1 (first |e| <= tol), m = n when it does not
+    float pivmin32;  // smallest pivot magnitude of the FP32 Sturm counts
 };
 
-// Gershgorin interval, deflation of negligible off-diagonals, e^2 (one block)
+// Gershgorin interval, deflation of negligible off-diagonals, e^2, and FP32
+// copies of d and e^2 for the first rounds of the bisection (one block)
 __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __restrict__ e, int64_t n, double* e2,
-                                  TriBounds* out) {
+                                  float* d32, float* e2_32, TriBounds* out) {
     __shared__ double s_lo[kTriWarps], s_hi[kTriWarps], s_nm[kTriWarps], s_e[kTriWarps];
     __shared__ int s_m[kTriWarps];
     double lo = DBL_MAX, hi = -DBL_MAX, nm = 0.0, emax = 0.0;
@@ -416,8 +418,10 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
     for (int64_t i = threadIdx.x; i + 1 < n; i += blockDim.x) {
         const bool small = fabs(e[i]) <= tol;
         e2[i] = small ? 0.0 : e[i] * e[i];
+        e2_32[i] = (float)e2[i];
         if (small && (int)i + 1 < m) m = (int)i + 1;
     }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) d32[i] = (float)d[i];
     for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) s_m[wid] = m;
     __syncthreads();
@@ -430,6 +434,7 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
         b.gu = hi + 2.0 * DBL_EPSILON * nm * (double)n + 2.0 * b.pivmin;
         b.tol = tol;
         b.m = m;
+        b.pivmin32 = FLT_MIN * (float)fmin(fmax(1.0, emax), 1e30);
         *out = b;
     }
 }
@@ -467,14 +472,36 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const d
     return c;
 }
 
+// Number of eigenvalues below x of rows [i0, i1) in FP32, ratio form
+// q_i = (d_i - x) - e_{i-1}^2 / q_{i-1} with pivots kept away from zero by
+// pivmin (negative q counted).  The count is exact for a matrix within a few
+// FP32 roundings of T (Kahan's backward analysis of the ratio recurrence), so
+// a level bracketed by FP32 counts lies within 16 eps_32 (||T|| + |x|) of the
+// bracket; the FP32 pipe is 64 times the FP64 one on this GPU.
+__device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const float* __restrict__ e2, int i0, int i1,
+                                             float x, float pivmin) {
+    float q = __ldg(d + i0) - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    int c = q < 0.f;
+    for (int i = i0 + 1; i < i1; ++i) {
+        q = (__ldg(d + i) - x) - __ldg(e2 + i - 1) / q;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        c += q < 0.f;
+    }
+    return c;
+}
+
 // Sixteen lanes per level: 17-section of the Gershgorin interval with Sturm
-// counts, 14 rounds from 2 ||T|| below eps ||T||.  GB300 runs two FP64 lanes
+// counts: 6 rounds in FP32 (from 2 ||T|| to about eps_32 ||T||), the bracket
+// widened by the FP32 counts' backward error, then 9 rounds in FP64 to below
+// eps ||T|| (17^9 > 1e11).  GB300 runs two FP64 lanes
 // per clock per SM, so the cost is the chain of FP64 warp instructions each
 // warp issues: fewer, wider rounds and one warp per SM sub-partition beat
 // narrow bisection.  Every lane runs all rounds (uniform ballots).  Levels
 // k < m belong to rows [0, m), the others to rows [m, n).
 constexpr int kSect = 16;
-__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e2, int64_t n,
+__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e2,
+                              const float* __restrict__ d32, const float* __restrict__ e2_32, int64_t n,
                               const TriBounds* __restrict__ bnd, double* lam) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, sub = lane % kSect, base = lane - sub;
@@ -482,8 +509,20 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
     const TriBounds b = *bnd;
     const int i0 = k < b.m ? 0 : b.m, i1 = k < b.m ? b.m : (int)n;
     const int kk = (int)(k - i0);
-    double lo = b.gl, hi = b.gu;
-    for (int it = 0; it < 14; ++it) {
+    float lof = (float)b.gl, hif = (float)b.gu;
+    for (int it = 0; it < 6; ++it) {
+        const float x = lof + (hif - lof) * (float)(sub + 1) * (1.0f / (kSect + 1));
+        const int c = sturm_count32(d32, e2_32, i0, i1, x, b.pivmin32);
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
+        const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
+        const float xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
+        const float xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
+        if (ls > 0) lof = xl;
+        if (ls < kSect) hif = xh;
+    }
+    const double del = 16.0 * FLT_EPSILON * (b.tnorm + fmax(fabs((double)lof), fabs((double)hif)));
+    double lo = fmax(b.gl, (double)lof - del), hi = fmin(b.gu, (double)hif + del);
+    for (int it = 0; it < 9; ++it) {
         const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (kSect + 1));
         const int c = sturm_count(d, e2, i0, i1, x);
         const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
@@ -617,8 +656,10 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 }  // namespace
 
 size_t tridiag_scratch_bytes(int64_t n) {
-    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); twisted passes 5 n*n doubles
-    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) + 8192;
+    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
+    // twisted passes 5 n*n doubles; 256-byte alignment of each piece
+    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) +
+           sizeof(float) * (size_t)(2 * n) + 8192;
 }
 
 int tridiag_max_dim() { return 4736; }   // v, w and the next column of a step in 227 KB of shared memory
@@ -649,6 +690,8 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     double* d = (double*)take(sizeof(double) * n);
     double* e = (double*)take(sizeof(double) * n);
     double* e2 = (double*)take(sizeof(double) * n);
+    float* d32 = (float*)take(sizeof(float) * n);
+    float* e2_32 = (float*)take(sizeof(float) * n);
     double* lam = (double*)take(sizeof(double) * n);
     double* w = (double*)take(sizeof(double) * n);
     double* beta0 = (double*)take(sizeof(double));
@@ -700,10 +743,10 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     note_launch();
     if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
 
-    tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, bnd);
+    tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, d32, e2_32, bnd);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    bisect_kernel<<<(unsigned)((kSect * n + 31) / 32), 32, 0, st>>>(d, e2, n, bnd, lam);
+    bisect_kernel<<<(unsigned)((kSect * n + 31) / 32), 32, 0, st>>>(d, e2, d32, e2_32, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d, e, n, bnd, lam, dp, w);
