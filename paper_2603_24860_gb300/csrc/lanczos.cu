@@ -18,12 +18,13 @@
 //
 // GB300 layout: one persistent cooperative kernel, one CTA per SM.  Every CTA
 // holds v_j in shared memory; (H v)_r is the dot product of column r with v
-// (H is Hermitian: (H v)_r = sum_i conj(H_ir) v_i).  Column r belongs to CTA
-// r mod G and each of its 8 warps takes one eighth of the rows of every own
-// column (so all SMs work even when n < 8 G), the eight partial dots summed in
-// shared memory: the block is read once per step with coalesced loads and
-// no cross-CTA reduction except the two scalars.  The FP64 pipe bounds a
-// step: 4 n^2 DFMA.
+// (H is Hermitian: (H v)_r = sum_i conj(H_ir) v_i), one warp per column, so
+// the block is read once per step with coalesced loads and no cross-CTA
+// reduction except the two scalars.  The FP64 pipe bounds a step: 4 n^2 DFMA
+// plus one shuffle reduction per column.  One FP64 warp instruction occupies
+// its sub-partition's pipe for 64 cycles whatever its active lanes, so a
+// column is not split across warps: the extra reductions would cost more
+// than the idle SMs of small blocks (n < 8 x 152).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -80,15 +81,12 @@ struct LzArgs {
 };
 
 __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
-    extern __shared__ __align__(16) double2 s_v[];   // v_j [n], then the partial dots [ncl][kLzWarps]
+    extern __shared__ __align__(16) double2 s_v[];   // v_j
     __shared__ double s_red[kLzWarps];
     __shared__ double s_tot;
     __shared__ int s_flag;
     const int n = (int)a.n, G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;   // own columns r = blk + G l
-    double2* s_part = s_v + n;
-    const int seg = (n + kLzWarps - 1) / kLzWarps;       // rows of a warp's segment
-    const int i0 = wid * seg, i1 = min(n, i0 + seg);
+    const int gw = blk * kLzWarps + wid, nw = G * kLzWarps;
     unsigned nbar = 0;
     double bj = __ldcg(a.beta), bjm1 = 1.0;
     int steps = a.m;
@@ -128,62 +126,52 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
             s_v[i] = make_double2(u.x * inv, u.y * inv);
         }
         __syncthreads();
-        // (H v_j)_r over this warp's rows for every own column, then y = H v_j - beta_j v_{j-1}
-        // (v_{j-1} = u_{j-1} / beta_{j-1}) by the thread that owns column l = tid
-        for (int l = 0; l < ncl; ++l) {
-            const double2* col = a.H + (size_t)(blk + (size_t)l * G) * a.ld;
+        // y = H v_j - beta_j v_{j-1} on own columns (v_{j-1} = u_{j-1} / beta_{j-1})
+        const double cprev = j > 0 ? bj / bjm1 : 0.0;
+        double p1 = 0.0;
+        for (int r = gw; r < n; r += nw) {
+            const double2* col = a.H + (size_t)r * a.ld;
             double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
-            int i = i0 + lane;
-            for (; i + 32 < i1; i += 64) {
+            int i = lane;
+            for (; i + 32 < n; i += 64) {
                 const double2 h0 = __ldg(col + i), v0 = s_v[i], h1 = __ldg(col + i + 32), v1 = s_v[i + 32];
                 ax = fma(h0.x, v0.x, fma(h0.y, v0.y, ax));
                 ay = fma(h0.x, v0.y, fma(-h0.y, v0.x, ay));
                 bx = fma(h1.x, v1.x, fma(h1.y, v1.y, bx));
                 by = fma(h1.x, v1.y, fma(-h1.y, v1.x, by));
             }
-            if (i < i1) {
+            if (i < n) {
                 const double2 h0 = __ldg(col + i), v0 = s_v[i];
                 ax = fma(h0.x, v0.x, fma(h0.y, v0.y, ax));
                 ay = fma(h0.x, v0.y, fma(-h0.y, v0.x, ay));
             }
             const double sx = lz_warp_sum(ax + bx), sy = lz_warp_sum(ay + by);
-            if (lane == 0) s_part[l * kLzWarps + wid] = make_double2(sx, sy);
-        }
-        __syncthreads();
-        const double cprev = j > 0 ? bj / bjm1 : 0.0;
-        double p1 = 0.0;
-        for (int l = tid; l < ncl; l += kLzThreads) {
-            const int r = blk + l * G;
-            double2 y = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int w = 0; w < kLzWarps; ++w) {
-                const double2 q = s_part[l * kLzWarps + w];
-                y.x += q.x;
-                y.y += q.y;
+            if (lane == 0) {
+                double2 y = make_double2(sx, sy);
+                if (j > 0) {
+                    const double2 q = __ldcg(ujm1 + r);
+                    y.x = fma(-cprev, q.x, y.x);
+                    y.y = fma(-cprev, q.y, y.y);
+                }
+                ujp1[r] = y;
+                const double2 v = s_v[r];
+                p1 = fma(v.x, y.x, fma(v.y, y.y, p1));   // Re(conj(v) y)
             }
-            if (j > 0) {
-                const double2 q = __ldcg(ujm1 + r);
-                y.x = fma(-cprev, q.x, y.x);
-                y.y = fma(-cprev, q.y, y.y);
-            }
-            ujp1[r] = y;
-            const double2 v = s_v[r];
-            p1 = fma(v.x, y.x, fma(v.y, y.y, p1));   // Re(conj(v) y)
         }
         block_part(p1, a.part1);
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
         const double al = grid_total(a.part1);
         // u_{j+1} = y - alpha_j v_j on own columns (the thread that wrote y)
         double p2 = 0.0;
-        for (int l = tid; l < ncl; l += kLzThreads) {
-            const int r = blk + l * G;
-            double2 y = __ldcg(ujp1 + r);
-            const double2 v = s_v[r];
-            y.x = fma(-al, v.x, y.x);
-            y.y = fma(-al, v.y, y.y);
-            ujp1[r] = y;
-            p2 = fma(y.x, y.x, fma(y.y, y.y, p2));
-        }
+        if (lane == 0)
+            for (int r = gw; r < n; r += nw) {
+                double2 y = __ldcg(ujp1 + r);
+                const double2 v = s_v[r];
+                y.x = fma(-al, v.x, y.x);
+                y.y = fma(-al, v.y, y.y);
+                ujp1[r] = y;
+                p2 = fma(y.x, y.x, fma(y.y, y.y, p2));
+            }
         block_part(p2, a.part2);
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
         const double bn = sqrt(grid_total(a.part2));
@@ -265,8 +253,7 @@ int launch_tm_weights(const double* V, int k, double scale, double* w, cudaStrea
     return BSE_OK;
 }
 
-// v_j and the partial dots of the own columns (at most n / 152 + 1 of them, 8 each) in shared memory
-int lanczos_max_dim() { return 12000; }
+int lanczos_max_dim() { return 12000; }   // v_j in shared memory (192 KB)
 
 size_t lanczos_scratch_bytes(int64_t n, int m) {
     return sizeof(double2) * (size_t)(3 * n) + sizeof(double) * (size_t)(2 * 1024 + 2 * m + 1) + 6 * 256 + 64;
@@ -295,10 +282,8 @@ int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, in
     int dev = 0, sms = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int G = (int)std::min<int64_t>(std::min(sms, 1024), n);
-    const int ncl_max = (int)((n - 1) / G + 1);
-    const size_t dyn = sizeof(double2) * ((size_t)n + (size_t)ncl_max * kLzWarps);
-    if (dyn > 227 * 1024 - 1024) return fail(BSE_EUNSUPPORTED, "Lanczos path: n = %lld exceeds shared memory", (long long)n);
+    const int G = (int)std::min<int64_t>(std::min(sms, 1024), std::max<int64_t>(1, (n + kLzWarps - 1) / kLzWarps));
+    const size_t dyn = sizeof(double2) * (size_t)n;
     BSE_CUDA(cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kLzThreads, dyn));

@@ -64,8 +64,9 @@ def test_ritz_pairs_and_spectrum_match_the_oracle(gpu, name, steps):
 
 def test_fraction_alone_equals_the_ritz_pole_sum(gpu):
     """Without Ritz pairs Im eps comes from the continued fraction alone; it
-    equals the Lorentzian sum over the Ritz pairs of T_m and the oracle's
-    fraction."""
+    equals the call with Ritz pairs and the oracle's fraction.  20 steps: two
+    recurrences without reorthogonalisation, summed in different orders,
+    stay within rounding of each other only until a Ritz value converges."""
     from oracle import haydock as hk
     bse, torch, get = gpu
     ctx = get("si4")
@@ -74,11 +75,11 @@ def test_fraction_alone_equals_the_ritz_pole_sum(gpu):
     d, inp, Hm, c = _oracle_block("si4", mu)
     h = torch.tensor(Hm, device="cuda").T.contiguous().T
     omega = torch.tensor(d["omega"], device="cuda")
-    _, _, im_r = bse.lanczos_spectrum(ctx, mu, h, omega, d["eta"], 30)
-    rz, wt, im_f = bse.lanczos_spectrum(ctx, mu, h, omega, d["eta"], 30, ritz=False)
+    _, _, im_r = bse.lanczos_spectrum(ctx, mu, h, omega, d["eta"], 20)
+    rz, wt, im_f = bse.lanczos_spectrum(ctx, mu, h, omega, d["eta"], 20, ritz=False)
     assert rz is None and wt is None
     im_r, im_f = im_r.cpu().numpy(), im_f.cpu().numpy()
-    a, bb, n2 = hk.lanczos(Hm, c, 30)
+    a, bb, n2 = hk.lanczos(Hm, c, 20)
     ref = hk.haydock_spectrum(inp, a, bb, n2, d["omega"], d["eta"])
     assert np.linalg.norm(im_f - ref) <= 1e-9 * np.linalg.norm(ref)
     assert np.linalg.norm(im_f - im_r) <= 1e-9 * np.linalg.norm(ref)
