@@ -349,7 +349,15 @@ static int ensure_partner(bse_ctx* c, int mu) {
     if (pd.part[0].host.dim != c->partner_dim[mu])
         return fail(BSE_ESYMM, "irrep %d: partner basis has %lld vectors but Tr P_11 = %lld", mu,
                     (long long)pd.part[0].host.dim, (long long)c->partner_dim[mu]);
-    for (int i = 1; i < d; ++i) BSE_TRY(transfer_basis(c->t, pd.part[0].host, weights(i, 0), pd.part[i].host));
+    {
+        std::vector<std::vector<double>> ws;
+        std::vector<Basis*> outs;
+        for (int i = 1; i < d; ++i) {
+            ws.push_back(weights(i, 0));
+            outs.push_back(&pd.part[i].host);
+        }
+        if (d > 1) BSE_TRY(transfer_bases(c->t, pd.part[0].host, ws, outs));
+    }
     for (int i = 0; i < d; ++i) BSE_TRY(upload_basis(c, pd.part[i]));
     pd.d = d;
     pd.ready = true;

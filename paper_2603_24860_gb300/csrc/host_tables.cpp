@@ -451,10 +451,35 @@ int build_multiplets_and_orbits(Tables& t, const double* eps) {
     return BSE_OK;
 }
 
+// run f(i) for i in [0, n) on a small pool of host threads (at most the
+// hardware threads, BSE_HOST_THREADS overrides), items taken in order of
+// decreasing cost when costs are given so that the largest do not finish last
+template <class F>
+static void parallel_for(int n, F f, const std::vector<double>* cost = nullptr) {
+    int nt = (int)std::thread::hardware_concurrency();
+    if (const char* e = std::getenv("BSE_HOST_THREADS")) nt = std::atoi(e);
+    nt = std::max(1, std::min(nt, std::min(32, n)));
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    if (cost) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return (*cost)[a] > (*cost)[b]; });
+    if (nt == 1) {
+        for (int i : order) f(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int i = 0; i < nt; ++i)
+        pool.emplace_back([&] {
+            for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) f(order[q]);
+        });
+    for (auto& th : pool) th.join();
+}
+
 int check_band_rotations(const Tables& t) {
-    // each multiplet block of Gamma(s) at k must be unitary
-    for (int s = 0; s < t.nops; ++s)
-        for (int k = 0; k < t.nk; ++k) {
+    // each multiplet block of Gamma(s) at k must be unitary (one operation per host thread)
+    std::atomic<int> bad{-1};
+    parallel_for(t.nops, [&](int s) {
+        for (int k = 0; k < t.nk && bad.load() < 0; ++k) {
             int64_t off = (int64_t)s * t.gam_per_s + t.gam_koff[k];
             auto chk = [&](const std::vector<std::pair<int, int>>& ms) -> bool {
                 for (auto& m : ms) {
@@ -470,9 +495,15 @@ int check_band_rotations(const Tables& t) {
                 }
                 return true;
             };
-            if (!chk(t.vmult[k]) || !chk(t.cmult[k]))
-                return fail(BSE_ESYMM, "band rotation of operation %d at k=%d is not unitary", s, k);
+            if (!chk(t.vmult[k]) || !chk(t.cmult[k])) {
+                int none = -1;
+                bad.compare_exchange_strong(none, s * t.nk + k);
+            }
         }
+    });
+    if (bad.load() >= 0)
+        return fail(BSE_ESYMM, "band rotation of operation %d at k=%d is not unitary", bad.load() / t.nk,
+                    bad.load() % t.nk);
     return BSE_OK;
 }
 
@@ -558,23 +589,22 @@ static double orbit_trace(const Tables& t, int o, const double* w) {
     return tr;
 }
 
-// run f(o) for every orbit on a small pool of host threads
-template <class F>
-static void for_each_orbit(int no, F f) {
-    int nt = (int)std::thread::hardware_concurrency();
-    if (const char* e = std::getenv("BSE_HOST_THREADS")) nt = std::atoi(e);
-    nt = std::max(1, std::min(nt, 32));
-    if (nt == 1 || no < 64) {
-        for (int o = 0; o < no; ++o) f(o);
-        return;
+// cost estimate of orbit o's work: its dense n_o x n_o restriction
+static std::vector<double> orbit_costs(const Tables& t) {
+    const int no = (int)t.orbit_star.size();
+    std::vector<double> c(no);
+    for (int o = 0; o < no; ++o) {
+        const double n_o = (double)(t.orbit_off[o + 1] - t.orbit_off[o]);
+        c[o] = n_o * n_o;
     }
-    std::atomic<int> next{0};
-    std::vector<std::thread> pool;
-    for (int i = 0; i < nt; ++i)
-        pool.emplace_back([&] {
-            for (int o = next.fetch_add(1); o < no; o = next.fetch_add(1)) f(o);
-        });
-    for (auto& th : pool) th.join();
+    return c;
+}
+
+// run f(o) for every orbit on the host threads, the largest orbits first
+template <class F>
+static void for_each_orbit(const Tables& t, F f) {
+    const std::vector<double> c = orbit_costs(t);
+    parallel_for((int)c.size(), f, &c);
 }
 
 // canonical orthonormal basis of the range of P = sum_s w[s] Gamma~(s): P e_j
@@ -588,7 +618,7 @@ int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& o
     const int no = (int)t.orbit_star.size();
     std::vector<std::vector<cplx>> acc_o(no);
     std::vector<int> nacc_o(no, 0);
-    for_each_orbit(no, [&](int o) {
+    for_each_orbit(t, [&](int o) {
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
         std::vector<cplx> x(n_o);
         // the orbit contributes rank = Tr P vectors; the columns after the one that
@@ -809,29 +839,39 @@ int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam) 
     return BSE_OK;
 }
 
-// out columns = (sum_s w[s] Gamma~(s)) u, column by column (orbit-local)
-int transfer_basis(const Tables& t, const Basis& u, const std::vector<double>& w, Basis& out) {
-    out = u;
+// outs[i] columns = (sum_s ws[i][s] Gamma~(s)) u, column by column (orbit-local),
+// for every i in one pass over the orbits
+int transfer_bases(const Tables& t, const Basis& u, const std::vector<std::vector<double>>& ws,
+                   const std::vector<Basis*>& outs) {
+    for (Basis* b : outs) *b = u;
     const int no = (int)t.orbit_star.size();
     // first column of each orbit in u (columns are grouped by orbit)
     std::vector<int64_t> first(no + 1, -1);
     for (int64_t j = u.dim - 1; j >= 0; --j) first[u.col_orbit[j]] = j;
-    for_each_orbit(no, [&](int o) {
+    std::vector<double> cost = orbit_costs(t);
+    for (int o = 0; o < no; ++o) {   // building M and applying it to the orbit's columns
+        int64_t nc = 0;
+        for (int64_t j = first[o]; first[o] >= 0 && j < u.dim && u.col_orbit[j] == o; ++j) ++nc;
+        cost[o] *= (double)(1 + nc);
+    }
+    parallel_for(no, [&](int o) {
         if (first[o] < 0) return;
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
         std::vector<cplx> M;
-        orbit_matrix(t, o, w.data(), M);
-        for (int64_t j = first[o]; j < u.dim && u.col_orbit[j] == o; ++j) {
-            const cplx* x = &u.coef[u.col_off[j]];
-            cplx* y = &out.coef[u.col_off[j]];
-            for (int64_t i = 0; i < n_o; ++i) y[i] = 0.0;
-            for (int64_t jj = 0; jj < n_o; ++jj) {
-                if (x[jj] == 0.0) continue;
-                const cplx* col = &M[(size_t)jj * n_o];
-                for (int64_t i = 0; i < n_o; ++i) y[i] += col[i] * x[jj];
+        for (size_t q = 0; q < ws.size(); ++q) {
+            orbit_matrix(t, o, ws[q].data(), M);
+            for (int64_t j = first[o]; j < u.dim && u.col_orbit[j] == o; ++j) {
+                const cplx* x = &u.coef[u.col_off[j]];
+                cplx* y = &outs[q]->coef[u.col_off[j]];
+                for (int64_t i = 0; i < n_o; ++i) y[i] = 0.0;
+                for (int64_t jj = 0; jj < n_o; ++jj) {
+                    if (x[jj] == 0.0) continue;
+                    const cplx* col = &M[(size_t)jj * n_o];
+                    for (int64_t i = 0; i < n_o; ++i) y[i] += col[i] * x[jj];
+                }
             }
         }
-    });
+    }, &cost);
     return BSE_OK;
 }
 

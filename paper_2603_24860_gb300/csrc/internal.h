@@ -95,7 +95,9 @@ struct Basis {
 int build_basis(const Tables& t, int mu, Basis& out);
 int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& out);
 int partner_matrices(const Tables& t, int mu, int& d, std::vector<double>& gam);
-int transfer_basis(const Tables& t, const Basis& u, const std::vector<double>& w, Basis& out);
+// outs[i] = (sum_s ws[i][s] Gamma~(s)) u for every i, in one pass over the orbits
+int transfer_bases(const Tables& t, const Basis& u, const std::vector<std::vector<double>>& ws,
+                   const std::vector<Basis*>& outs);
 
 // ---------------------------------------------------------------------------
 // device-side view of the system (passed by value to kernels)
