@@ -858,16 +858,23 @@ int transfer_bases(const Tables& t, const Basis& u, const std::vector<std::vecto
         if (first[o] < 0) return;
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
         std::vector<cplx> M;
+        int64_t j1 = first[o];
+        while (j1 < u.dim && u.col_orbit[j1] == o) ++j1;
         for (size_t q = 0; q < ws.size(); ++q) {
             orbit_matrix(t, o, ws[q].data(), M);
-            for (int64_t j = first[o]; j < u.dim && u.col_orbit[j] == o; ++j) {
-                const cplx* x = &u.coef[u.col_off[j]];
+            // y_j = M x_j for all of the orbit's columns at once: each column of M is
+            // read once (M can be megabytes), the vectors y_j stay in cache
+            for (int64_t j = first[o]; j < j1; ++j) {
                 cplx* y = &outs[q]->coef[u.col_off[j]];
                 for (int64_t i = 0; i < n_o; ++i) y[i] = 0.0;
-                for (int64_t jj = 0; jj < n_o; ++jj) {
-                    if (x[jj] == 0.0) continue;
-                    const cplx* col = &M[(size_t)jj * n_o];
-                    for (int64_t i = 0; i < n_o; ++i) y[i] += col[i] * x[jj];
+            }
+            for (int64_t jj = 0; jj < n_o; ++jj) {
+                const cplx* col = &M[(size_t)jj * n_o];
+                for (int64_t j = first[o]; j < j1; ++j) {
+                    const cplx xj = u.coef[u.col_off[j] + jj];
+                    if (xj == 0.0) continue;
+                    cplx* y = &outs[q]->coef[u.col_off[j]];
+                    for (int64_t i = 0; i < n_o; ++i) y[i] += col[i] * xj;
                 }
             }
         }
