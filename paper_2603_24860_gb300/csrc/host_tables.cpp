@@ -2,10 +2,15 @@
 // the point group S/S_T of the space group, the k mesh and its stars, the
 // character table (computed, not typed), multiplets, orbits of the product
 // basis and the canonical orthonormal basis of each irrep subspace.
+#include <unistd.h>
+
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <condition_variable>
 #include <cstdlib>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <cstdarg>
@@ -451,9 +456,79 @@ int build_multiplets_and_orbits(Tables& t, const double* eps) {
     return BSE_OK;
 }
 
-// run f(i) for i in [0, n) on a small pool of host threads (at most the
-// hardware threads, BSE_HOST_THREADS overrides), items taken in order of
-// decreasing cost when costs are given so that the largest do not finish last
+// Host threads for the set-up passes, created on first use and kept for the
+// life of the process: a pass over a few hundred small orbits is shorter
+// than creating and joining a thread per core.  The workers are detached and
+// the pool is never destroyed (no teardown at exit); a forked child builds a
+// pool of its own.  One parallel region runs at a time.
+namespace {
+struct HostPool {
+    std::mutex run_mu, mu;
+    std::condition_variable cv_start, cv_done;
+    const std::function<void(int)>* job = nullptr;
+    unsigned gen = 0;
+    int want = 0, pending = 0, nworkers = 0;
+    pid_t owner = 0;
+};
+
+HostPool* host_pool(int nworkers) {
+    static std::mutex make_mu;
+    static HostPool* pool = nullptr;
+    std::lock_guard<std::mutex> lk(make_mu);
+    if (!pool || pool->owner != getpid()) {   // first use, or a forked child: a new pool (the old one is left)
+        pool = new HostPool();
+        pool->owner = getpid();
+    }
+    while (pool->nworkers < nworkers) {
+        const int id = ++pool->nworkers;   // worker ids 1..; the caller is 0
+        HostPool* P = pool;
+        std::thread([P, id] {
+            unsigned seen = 0;
+            for (;;) {
+                const std::function<void(int)>* job;
+                {
+                    std::unique_lock<std::mutex> l(P->mu);
+                    P->cv_start.wait(l, [&] { return P->gen != seen; });
+                    seen = P->gen;
+                    if (id >= P->want) continue;
+                    job = P->job;
+                }
+                (*job)(id);
+                {
+                    std::lock_guard<std::mutex> l(P->mu);
+                    if (--P->pending == 0) P->cv_done.notify_all();
+                }
+            }
+        }).detach();
+    }
+    return pool;
+}
+
+// body(w) on nt workers (w = 0 is the calling thread); returns when all are done
+void host_run(int nt, const std::function<void(int)>& body) {
+    if (nt <= 1) {
+        body(0);
+        return;
+    }
+    HostPool* P = host_pool(nt - 1);
+    std::lock_guard<std::mutex> run(P->run_mu);
+    {
+        std::lock_guard<std::mutex> l(P->mu);
+        P->job = &body;
+        P->want = nt;
+        P->pending = nt - 1;
+        ++P->gen;
+    }
+    P->cv_start.notify_all();
+    body(0);
+    std::unique_lock<std::mutex> l(P->mu);
+    P->cv_done.wait(l, [&] { return P->pending == 0; });
+}
+}  // namespace
+
+// run f(i) for i in [0, n) on the host threads (at most the hardware threads,
+// BSE_HOST_THREADS overrides), items taken in order of decreasing cost when
+// costs are given so that the largest do not finish last
 template <class F>
 static void parallel_for(int n, F f, const std::vector<double>* cost = nullptr) {
     int nt = (int)std::thread::hardware_concurrency();
@@ -462,17 +537,10 @@ static void parallel_for(int n, F f, const std::vector<double>* cost = nullptr) 
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     if (cost) std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return (*cost)[a] > (*cost)[b]; });
-    if (nt == 1) {
-        for (int i : order) f(i);
-        return;
-    }
     std::atomic<int> next{0};
-    std::vector<std::thread> pool;
-    for (int i = 0; i < nt; ++i)
-        pool.emplace_back([&] {
-            for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) f(order[q]);
-        });
-    for (auto& th : pool) th.join();
+    host_run(nt, [&](int) {
+        for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) f(order[q]);
+    });
 }
 
 int check_band_rotations(const Tables& t) {
@@ -620,7 +688,8 @@ int build_basis_weighted(const Tables& t, const std::vector<double>& w, Basis& o
     std::vector<int> nacc_o(no, 0);
     for_each_orbit(t, [&](int o) {
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
-        std::vector<cplx> x(n_o);
+        thread_local std::vector<cplx> x;   // scratch kept by each host thread
+        x.resize(n_o);
         // the orbit contributes rank = Tr P vectors; the columns after the one that
         // completes them have zero residual, so they are neither formed nor projected
         const long rank = std::lround(orbit_trace(t, o, w.data()));
@@ -857,7 +926,7 @@ int transfer_bases(const Tables& t, const Basis& u, const std::vector<std::vecto
     parallel_for(no, [&](int o) {
         if (first[o] < 0) return;
         const int64_t n_o = t.orbit_off[o + 1] - t.orbit_off[o];
-        std::vector<cplx> M;
+        thread_local std::vector<cplx> M;   // scratch kept by each host thread
         int64_t j1 = first[o];
         while (j1 < u.dim && u.col_orbit[j1] == o) ++j1;
         for (size_t q = 0; q < ws.size(); ++q) {
