@@ -18,12 +18,16 @@
 // reduction (152 x 227 KB hold a 1400 x 1400 complex matrix), otherwise they
 // stay in global memory.  Because the block is Hermitian, (A v)_j is a dot
 // product with column j, so each step needs no cross-CTA reduction except one
-// scalar, and two grid barriers per step order the reflector and x = tau A v.
+// scalar, and one grid barrier per step orders the reflector and x = tau A v.
+// The reduction computes in double-float arithmetic (dfloat.h) on the FP32
+// pipe, 64 times wider than GB300's FP64 pipe; the block is read in FP64 and
+// T is written in FP64.
 #include <cuda_runtime.h>
 
 #include <cfloat>
 #include <cmath>
 
+#include "dfloat.h"
 #include "fp64_fast.h"
 #include "grid_sync.h"
 #include "internal.h"
@@ -34,15 +38,7 @@ namespace {
 
 constexpr int kTriThreads = 256;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kChunk = 8;                 // columns reduced together
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
+constexpr int kChunk = 8;                 // columns updated together
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -50,31 +46,21 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Rank-2 update  A_rc -= v_r conj(w_c) + w_r conj(v_c)  of a chunk, eight FMAs per element
+// Rank-2 update A_rc -= v_r conj(w_c) + w_r conj(v_c) of a chunk of columns,
+// rows r0 + t, r0 + t + nt, ...
 template <int NC>
-__device__ __forceinline__ void chunk_update(double2* cb, size_t cs, const double2* V, const double2* W,
-                                             const int* jcol, int r0, int n) {
-    double2 vj[NC], wj[NC];
+__device__ __forceinline__ void chunk_update(cdf* cb, size_t cs, const cdf* V, const cdf* W, const int* jcol,
+                                             int r0, int n, int t, int nt) {
+    cdf vj[NC], wj[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         vj[c] = V[jcol[c]];
         wj[c] = W[jcol[c]];
     }
-    for (int r = r0 + (int)threadIdx.x; r < n; r += kTriThreads) {
-        const double2 v = V[r], w = W[r];
+    for (int r = r0 + t; r < n; r += nt) {
+        const cdf v = V[r], w = W[r];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            double2 q = cb[c * cs + r];
-            q.x = fma(-v.x, wj[c].x, q.x);
-            q.x = fma(-v.y, wj[c].y, q.x);
-            q.x = fma(-w.x, vj[c].x, q.x);
-            q.x = fma(-w.y, vj[c].y, q.x);
-            q.y = fma(-v.y, wj[c].x, q.y);
-            q.y = fma(v.x, wj[c].y, q.y);
-            q.y = fma(-w.y, vj[c].x, q.y);
-            q.y = fma(w.x, vj[c].y, q.y);
-            cb[c * cs + r] = q;
-        }
+        for (int c = 0; c < NC; ++c) cb[c * cs + r] = cdf_rank2(cb[c * cs + r], v, w, wj[c], vj[c]);
     }
 }
 
@@ -91,224 +77,263 @@ __device__ __forceinline__ void chunk_update(double2* cb, size_t cs, const doubl
     }
 
 struct TriArgs {
-    double2* A;           // n x n column-major, leading dimension n (updated in place in the global variant)
+    double2* A;           // n x n column-major, leading dimension n; the global variant rewrites it in place in
+                          // double-float (same 16 bytes per element) and updates it there
     int64_t n;
     const double2* v0;    // initial reflector
     const double* beta0;  // its (real) scalar
-    double2* ncol;        // [2][n] the next column to be reflected, published by its owner, by parity
-    double2* xbuf;        // [2][n] x = tau A v, by step parity
-    double2* spart;       // [2][G] per-CTA parts of x^H v, by step parity
+    cdf* ncol;            // [2][n] the next column to be reflected, published by its owner, by parity
+    cdf* xbuf;            // [2][n] x = tau A v, by step parity
+    cdf* spart;           // [2][G] per-CTA parts of x^H v, by step parity
     double* d;            // [n] diagonal of T
     double* e;            // [n] off-diagonal of T (e[n-1] unused)
     unsigned* bar;        // barrier counter, zero on entry
     int* err;             // error flag, zero on entry
 };
 
+// Reflector k from alpha = (column k)_{k+1} and sigma = sum_{r>k+1} |(column k)_r|^2
+// in the zlarfg convention (v_{k+1} = 1): beta = -sign(Re alpha) sqrt(|alpha|^2 + sigma),
+// tau = (beta - alpha) / beta, v_r = x_r / (alpha - beta).  FP64 version, for
+// squared norms outside the safe range of the double-float one.
+__device__ void reflector_fp64(double2 al, double sigma, double2& tau, double2& inv, double& beta) {
+    if (sigma == 0.0 && al.y == 0.0) {
+        tau = make_double2(0.0, 0.0);
+        beta = al.x;
+        inv = make_double2(0.0, 0.0);
+        return;
+    }
+    const double nrm2 = fma(al.x, al.x, fma(al.y, al.y, sigma));
+    const double y = copysign(rsqrt_nr(nrm2), al.x);   // -1/beta
+    beta = -nrm2 * y;
+    tau = make_double2(fma(al.x, y, 1.0), al.y * y);
+    const double2 den = make_double2(al.x - beta, al.y);
+    const double rm = rcp_nr(fma(den.x, den.x, den.y * den.y));
+    inv = make_double2(den.x * rm, -den.y * rm);
+}
+
+// The same in double-float: a few hundred FP32 cycles instead of a chain of
+// dependent FP64 instructions
+__device__ void reflector(cdf al, float2 sigma, cdf& tau, cdf& inv, float2& beta) {
+    if (sigma.x == 0.f && al.z == 0.f && al.w == 0.f) {
+        tau = cdf_zero();
+        beta = make_float2(al.x, al.y);
+        inv = cdf_zero();
+        return;
+    }
+    float s = sigma.x, lo = sigma.y;
+    df_acc(s, lo, al.x, al.y, al.x, al.y);
+    df_acc(s, lo, al.z, al.w, al.z, al.w);
+    const float2 nrm2 = df_fin(s, lo);
+    if (!(nrm2.x >= 0x1p-100f && nrm2.x <= 0x1p100f)) {
+        double2 t, iv;
+        double b;
+        reflector_fp64(cdf_to(al), df_to(sigma), t, iv, b);
+        tau = cdf_from(t);
+        inv = cdf_from(iv);
+        beta = df_from(b);
+        return;
+    }
+    const float2 nrm = df_sqrt(nrm2);
+    beta = al.x < 0.f ? nrm : df_neg(nrm);
+    const float2 rb = df_rcp(beta);
+    const float2 ar = df_mul(make_float2(al.x, al.y), rb), ai = df_mul(make_float2(al.z, al.w), rb);
+    const float2 tr = df_add(make_float2(1.f, 0.f), df_neg(ar));
+    tau = make_float4(tr.x, tr.y, -ai.x, -ai.y);
+    const float2 dr = df_add(make_float2(al.x, al.y), df_neg(beta));
+    const float2 di = make_float2(al.z, al.w);
+    float q = 0.f, ql = 0.f;
+    df_acc(q, ql, dr.x, dr.y, dr.x, dr.y);
+    df_acc(q, ql, di.x, di.y, di.x, di.y);
+    const float2 rm = df_rcp(df_fin(q, ql));
+    const float2 ir = df_mul(dr, rm), ii = df_mul(di, rm);
+    inv = make_float4(ir.x, ir.y, -ii.x, -ii.y);
+}
+
 // One grid barrier per reflection step s (H(s) = I - tau v v^H on rows >= s+1,
-// s = -1 being the start reflector H0 on all rows):
-//   P1  x(s) and the parts of x^H v from all CTAs: alpha = -tau (x^H v)/2,
-//       w = x + alpha v (shared memory)
-//   P2  own columns j > s:  A_rj -= v_r conj(w_j) + w_r conj(v_j),  r > s
-//   P3  every CTA applies the same update to the published copy of column
-//       k = s+1 and forms reflector k from it (zlarfg convention, v_{k+1} = 1)
-//   P4  the owner of column k+1 publishes it (its state before step k)
-//   P5  x(k)_j = tau(k) sum_r conj(A_rj) v_r for own columns j > k (Hermitian:
+// s = -1 being the start reflector H0 on all rows), k = s+1:
+//   P1  x(s), the parts of x^H v from all CTAs and the published column k:
+//       alpha = -tau (x^H v)/2
+//   P2  w = x + alpha v; column k updated by this step,
+//       c_r - v_r conj(w_k) - w_r conj(v_k), and its squared norm below row k+1
+//   P3  warp 0: reflector k from it (zlarfg convention, v_{k+1} = 1);
+//       warps 1-7 at the same time: own columns j >= k,
+//       A_rj -= v_r conj(w_j) + w_r conj(v_j), rows r >= k
+//   P4  the new reflector v(k) in place of column k; the owner of column k+1
+//       publishes it (its state before step k)
+//   P5  x(k)_j = tau(k) sum_r conj(A_rj) v(k)_r for own columns j > k (Hermitian:
 //       (A v)_j is a column dot product) and this CTA's part of x^H v
 //   grid barrier
 template <bool kSmem>
 __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
-    extern __shared__ __align__(16) double2 s_dyn[];
-    __shared__ double2 s_s[kTriWarps];
-    __shared__ double2 s_scal[2];   // [0] inv(alpha - beta) of the new reflector, [1] alpha of P1
-    __shared__ double2 s_tau;
-    __shared__ double s_sig[kTriWarps];
+    extern __shared__ __align__(16) cdf s_dyn[];
+    __shared__ cdf s_part[kTriWarps];
+    __shared__ cdf s_alpha, s_tau, s_inv;
     __shared__ int s_flag;
 
     const int n = (int)a.n;
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;
-    double2* V = s_dyn;
-    double2* W = s_dyn + n;
-    double2* C = s_dyn + 2 * (size_t)n;
-    double2* s_cols = s_dyn + 3 * (size_t)n;
-    auto col = [&](int l) -> double2* {
-        return kSmem ? s_cols + (size_t)l * n : a.A + (size_t)(blk + l * G) * n;
+    cdf* V = s_dyn;                       // reflector of the step
+    cdf* W = s_dyn + n;                   // w of the step
+    cdf* C = s_dyn + 2 * (size_t)n;       // next column, then its update, then the next reflector
+    cdf* s_cols = s_dyn + 3 * (size_t)n;
+    cdf* gA = reinterpret_cast<cdf*>(a.A);
+    auto col = [&](int l) -> cdf* {
+        return kSmem ? s_cols + (size_t)l * n : gA + (size_t)(blk + l * G) * n;
     };
     const size_t cstride = kSmem ? (size_t)n : (size_t)G * n;
-    if (kSmem)
-        for (int l = 0; l < ncl; ++l) {
-            const double2* src = a.A + (size_t)(blk + l * G) * n;
-            for (int r = tid; r < n; r += kTriThreads) s_cols[(size_t)l * n + r] = src[r];
+    // own columns in double-float; in the global variant each element is read
+    // and rewritten in place by the same thread
+    for (int l = 0; l < ncl; ++l) {
+        const double2* src = a.A + (size_t)(blk + l * G) * n;
+        cdf* dst = col(l);
+        for (int r = tid; r < n; r += kTriThreads) {
+            const double2 z = src[r];
+            dst[r] = cdf_from(z);
         }
-    for (int r = tid; r < n; r += kTriThreads) V[r] = __ldcg(a.v0 + r);
-    if (tid == 0) s_tau = make_double2(__ldcg(a.beta0), 0.0);
+    }
+    for (int r = tid; r < n; r += kTriThreads) V[r] = cdf_from(__ldcg(a.v0 + r));
+    if (tid == 0) s_tau = cdf_from(make_double2(__ldcg(a.beta0), 0.0));
     __syncthreads();
     // column 0 as it is before the start reflector
     if (blk == 0)
         for (int r = tid; r < n; r += kTriThreads) a.ncol[r] = col(0)[r];
     unsigned nbar = 0;
 
-    // P5 for reflector k (rows > k; k = -1: all rows): one warp per column, so
-    // the only cross-lane FP64 work is one shuffle reduction per column
-    auto dots = [&](int k) {
+    // P5 for reflector k (rows > k; k = -1: all rows) with reflector vector Vk:
+    // one warp per column
+    auto dots = [&](int k, const cdf* Vk) {
         const int r0 = k + 1;
-        const double2 tau = s_tau;
+        const cdf tau = s_tau;
         const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;
-        double2* xb = a.xbuf + (size_t)(k & 1) * n;
-        double2 sw = make_double2(0.0, 0.0);
+        cdf* xb = a.xbuf + (size_t)(k & 1) * n;
+        cdf sw = cdf_zero();
         for (int l = l0 + wid; l < ncl; l += kTriWarps) {
-            const double2* cl = col(l);
-            double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+            const cdf* cl = col(l);
+            cdf acc = cdf_zero(), acc2 = cdf_zero();
             int r = r0 + lane;
             for (; r + 32 < n; r += 64) {
-                const double2 a0 = cl[r], v0 = V[r], a1 = cl[r + 32], v1 = V[r + 32];
-                acc.x = fma(a0.x, v0.x, acc.x);
-                acc.x = fma(a0.y, v0.y, acc.x);
-                acc.y = fma(a0.x, v0.y, acc.y);
-                acc.y = fma(-a0.y, v0.x, acc.y);
-                acc2.x = fma(a1.x, v1.x, acc2.x);
-                acc2.x = fma(a1.y, v1.y, acc2.x);
-                acc2.y = fma(a1.x, v1.y, acc2.y);
-                acc2.y = fma(-a1.y, v1.x, acc2.y);
+                acc = cdf_dot_acc(acc, cl[r], Vk[r]);
+                acc2 = cdf_dot_acc(acc2, cl[r + 32], Vk[r + 32]);
             }
-            if (r < n) {
-                const double2 a0 = cl[r], v0 = V[r];
-                acc.x = fma(a0.x, v0.x, acc.x);
-                acc.x = fma(a0.y, v0.y, acc.x);
-                acc.y = fma(a0.x, v0.y, acc.y);
-                acc.y = fma(-a0.y, v0.x, acc.y);
-            }
-            const double sx = warp_sum(acc.x + acc2.x), sy = warp_sum(acc.y + acc2.y);
+            if (r < n) acc = cdf_dot_acc(acc, cl[r], Vk[r]);
+            acc = cdf_warp_sum(cdf_add(acc, acc2));
             if (lane == 0) {
                 const int j = blk + l * G;
-                const double2 x = cmul(tau, make_double2(sx, sy));
+                const cdf x = cdf_mul(tau, acc);
                 xb[j] = x;
-                const double2 t = cmulc(x, V[j]);
-                sw.x += t.x;
-                sw.y += t.y;
+                sw = cdf_dot_acc(sw, x, Vk[j]);
             }
         }
-        if (lane == 0) s_s[wid] = sw;
+        if (lane == 0) s_part[wid] = sw;
         __syncthreads();
         if (tid == 0) {
-            double2 sp = make_double2(0.0, 0.0);
-            for (int w = 0; w < kTriWarps; ++w) {
-                sp.x += s_s[w].x;
-                sp.y += s_s[w].y;
-            }
+            cdf sp = s_part[0];
+            for (int w = 1; w < kTriWarps; ++w) sp = cdf_add(sp, s_part[w]);
             a.spart[(size_t)(k & 1) * G + blk] = sp;
         }
     };
 
-    dots(-1);
+    dots(-1, V);
     if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
 
     for (int s = -1; s <= n - 2; ++s) {
-        const int r0 = s + 1;
-        const int k = s + 1;   // column reflected next
+        const int k = s + 1;   // first row of this step's reflector, column reflected next
         const bool more = s < n - 2;
-        // P1: gather x(s), the parts of x^H v and the published column k in one round trip
-        const double2* xb = a.xbuf + (size_t)(s & 1) * n;
-        const double2* nc_src = a.ncol + (size_t)(k & 1) * n;
-        for (int r = r0 + tid; r < n; r += kTriThreads) {
+        // P1
+        const cdf* xb = a.xbuf + (size_t)(s & 1) * n;
+        const cdf* nc_src = a.ncol + (size_t)(k & 1) * n;
+        const cdf xk = __ldcg(xb + k);
+        for (int r = k + tid; r < n; r += kTriThreads) {
             W[r] = __ldcg(xb + r);
             if (more) C[r] = __ldcg(nc_src + r);
         }
         if (wid == 0) {
-            double sx = 0.0, sy = 0.0;
-            const double2* sp = a.spart + (size_t)(s & 1) * G;
-#pragma unroll 4
-            for (int b = lane; b < G; b += 32) {
-                const double2 p = __ldcg(sp + b);
-                sx += p.x;
-                sy += p.y;
-            }
-            sx = warp_sum(sx);
-            sy = warp_sum(sy);
+            const cdf* sp = a.spart + (size_t)(s & 1) * G;
+            cdf acc = cdf_zero();
+            for (int b = lane; b < G; b += 32) acc = cdf_add(acc, __ldcg(sp + b));
+            acc = cdf_warp_sum(acc);
             if (lane == 0) {
-                const double2 al = cmul(s_tau, make_double2(sx, sy));
-                s_scal[1] = make_double2(-0.5 * al.x, -0.5 * al.y);
+                const cdf al = cdf_mul(s_tau, acc);
+                s_alpha = make_float4(-0.5f * al.x, -0.5f * al.y, -0.5f * al.z, -0.5f * al.w);
             }
         }
         __syncthreads();
-        const double2 alpha = s_scal[1];
-        for (int r = r0 + tid; r < n; r += kTriThreads) {
-            const double2 v = V[r];
-            double2 x = W[r];
-            x.x = fma(alpha.x, v.x, fma(-alpha.y, v.y, x.x));
-            x.y = fma(alpha.x, v.y, fma(alpha.y, v.x, x.y));
-            W[r] = x;
+        // P2
+        const cdf alpha = s_alpha;
+        const cdf vk = V[k];
+        const cdf wk = cdf_fma(xk, alpha, vk);
+        float sg = 0.f, sgl = 0.f;
+        for (int r = k + tid; r < n; r += kTriThreads) {
+            const cdf v = V[r];
+            const cdf w = cdf_fma(W[r], alpha, v);
+            W[r] = w;
+            if (more) {
+                const cdf cr = cdf_rank2(C[r], v, w, wk, vk);
+                C[r] = cr;
+                if (r >= k + 2) {
+                    df_acc(sg, sgl, cr.x, cr.y, cr.x, cr.y);
+                    df_acc(sg, sgl, cr.z, cr.w, cr.z, cr.w);
+                }
+            }
+        }
+        if (more) {
+            const float2 f = df_fin(sg, sgl);
+            const cdf t = cdf_warp_sum(make_float4(f.x, f.y, 0.f, 0.f));
+            if (lane == 0) s_part[wid] = t;
         }
         __syncthreads();
-        // P2: rank-2 update of own columns j >= r0
-        const int l0 = blk >= r0 ? 0 : (r0 - blk + G - 1) / G;
-        for (int c0 = l0; c0 < ncl; c0 += kChunk) {
-            const int nc = min(kChunk, ncl - c0);
-            int jcol[kChunk];
+        // P3
+        if (wid == 0) {
+            if (more && lane == 0) {
+                float2 sigma = make_float2(s_part[0].x, s_part[0].y);
+                for (int w = 1; w < kTriWarps; ++w) sigma = df_add(sigma, make_float2(s_part[w].x, s_part[w].y));
+                cdf tau, inv;
+                float2 beta;
+                reflector(C[k + 1], sigma, tau, inv, beta);
+                s_tau = tau;
+                s_inv = inv;
+                if (blk == 0) {
+                    a.d[k] = df_to(make_float2(C[k].x, C[k].y));
+                    a.e[k] = df_to(beta);
+                }
+            }
+        } else {
+            const int l0 = blk >= k ? 0 : (k - blk + G - 1) / G;
+            for (int c0 = l0; c0 < ncl; c0 += kChunk) {
+                const int nc = min(kChunk, ncl - c0);
+                int jcol[kChunk];
 #pragma unroll
-            for (int c = 0; c < kChunk; ++c) jcol[c] = blk + (c0 + c) * G;
-            BSE_NC_DISPATCH(nc, chunk_update, col(c0), cstride, V, W, jcol, r0, n)
+                for (int c = 0; c < kChunk; ++c) jcol[c] = blk + (c0 + c) * G;
+                BSE_NC_DISPATCH(nc, chunk_update, col(c0), cstride, V, W, jcol, k, n, tid - 32, kTriThreads - 32)
+            }
         }
         if (!more) break;
-        // P3: column k after this step's update, then its reflector
-        const double2 vk = V[k], wk = W[k];
         __syncthreads();
-        double sg = 0.0;
-        for (int r = k + tid; r < n; r += kTriThreads) {
-            const double2 c = C[r], v = V[r], w = W[r];
-            double2 cr;   // c - v conj(w_k) - w conj(v_k)
-            cr.x = fma(-v.x, wk.x, fma(-v.y, wk.y, fma(-w.x, vk.x, fma(-w.y, vk.y, c.x))));
-            cr.y = fma(-v.y, wk.x, fma(v.x, wk.y, fma(-w.y, vk.x, fma(w.x, vk.y, c.y))));
-            W[r] = cr;
-            if (r >= k + 2) sg = fma(cr.x, cr.x, fma(cr.y, cr.y, sg));
-        }
-        sg = warp_sum(sg);
-        if (lane == 0) s_sig[wid] = sg;
-        __syncthreads();
-        if (tid == 0) {
-            double sigma = 0.0;
-            for (int w = 0; w < kTriWarps; ++w) sigma += s_sig[w];
-            const double2 al = W[k + 1];
-            double2 tau, inv;
-            double beta;
-            if (sigma == 0.0 && al.y == 0.0) {
-                tau = make_double2(0.0, 0.0);
-                beta = al.x;
-                inv = make_double2(0.0, 0.0);
-            } else {
-                const double nrm2 = fma(al.x, al.x, fma(al.y, al.y, sigma));
-                const double y = copysign(rsqrt_nr(nrm2), al.x);   // -1/beta
-                beta = -nrm2 * y;
-                tau = make_double2(fma(al.x, y, 1.0), al.y * y);     // (beta - alpha) / beta
-                const double2 den = make_double2(al.x - beta, al.y);
-                const double rm = rcp_nr(fma(den.x, den.x, den.y * den.y));
-                inv = make_double2(den.x * rm, -den.y * rm);
-            }
-            s_scal[0] = inv;
-            s_tau = tau;
-            if (blk == 0) {
-                a.d[k] = W[k].x;
-                a.e[k] = beta;
-            }
-        }
-        __syncthreads();
+        // P4
         {
-            const double2 inv = s_scal[0];
-            for (int r = k + 1 + tid; r < n; r += kTriThreads) V[r] = r == k + 1 ? make_double2(1.0, 0.0) : cmul(W[r], inv);
+            const cdf inv = s_inv;
+            for (int r = k + 1 + tid; r < n; r += kTriThreads)
+                C[r] = r == k + 1 ? make_float4(1.f, 0.f, 0.f, 0.f) : cdf_mul(C[r], inv);
         }
-        __syncthreads();
-        // P4: publish column k+1 (state before step k)
         if (k + 1 <= n - 2 && (k + 1) % G == blk) {
-            const double2* ck = col((k + 1) / G);
-            double2* dst = a.ncol + (size_t)((k + 1) & 1) * n;
+            const cdf* ck = col((k + 1) / G);
+            cdf* dst = a.ncol + (size_t)((k + 1) & 1) * n;
             for (int r = k + 1 + tid; r < n; r += kTriThreads) dst[r] = ck[r];
         }
+        __syncthreads();
         // P5
-        dots(k);
+        dots(k, C);
+        cdf* t = V;
+        V = C;
+        C = t;
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
     }
     __syncthreads();
-    if ((n - 1) % G == blk && tid == 0) a.d[n - 1] = col((n - 1) / G)[n - 1].x;
+    if ((n - 1) % G == blk && tid == 0) {
+        const cdf z = col((n - 1) / G)[n - 1];
+        a.d[n - 1] = df_to(make_float2(z.x, z.y));
+    }
 }
 
 // Gram matrix of the conjugated projections: G_ij = sum_r b_i[r] conj(b_j[r]) (one block)
@@ -656,7 +681,7 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 }  // namespace
 
 size_t tridiag_scratch_bytes(int64_t n) {
-    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (double2); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
+    // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (16 bytes each); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
     // twisted passes 5 n*n doubles; 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) +
            sizeof(float) * (size_t)(2 * n) + 8192;
@@ -684,9 +709,9 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
         return (void*)q;
     };
     double2* v0 = (double2*)take(sizeof(double2) * n);
-    double2* ncol = (double2*)take(sizeof(double2) * 2 * n);
-    double2* xbuf = (double2*)take(sizeof(double2) * 2 * n);
-    double2* spart = (double2*)take(sizeof(double2) * 2048);
+    cdf* ncol = (cdf*)take(sizeof(cdf) * 2 * n);
+    cdf* xbuf = (cdf*)take(sizeof(cdf) * 2 * n);
+    cdf* spart = (cdf*)take(sizeof(cdf) * 2048);
     double* d = (double*)take(sizeof(double) * n);
     double* e = (double*)take(sizeof(double) * n);
     double* e2 = (double*)take(sizeof(double) * n);
@@ -704,9 +729,9 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     BSE_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 3) / 4));
-    const size_t static_smem = sizeof(double2) * (kTriWarps + 3) + sizeof(double) * kTriWarps + 64;
-    const size_t vec_bytes = sizeof(double2) * 3 * (size_t)n;   // v, w and the next column of a step
-    const size_t cols_bytes = sizeof(double2) * (size_t)((n - 1) / G + 1) * n;
+    const size_t static_smem = sizeof(cdf) * (kTriWarps + 3) + 64;
+    const size_t vec_bytes = sizeof(cdf) * 3 * (size_t)n;   // v, w and the next column of a step
+    const size_t cols_bytes = sizeof(cdf) * (size_t)((n - 1) / G + 1) * n;
     const bool smem = vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
     if (!smem) G = sms;
     if (vec_bytes + static_smem > (size_t)maxsm)
