@@ -35,6 +35,12 @@ METRIC = "H-block build TFLOP/s vs peak; time-to-spectrum, mixed vs FP64 at 0.1 
 # 152 SMs x 2 DFMA/clk (FP64) or 128 FFMA/clk (FP32) x 2 flop
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# The tridiagonal reduction computes in double-float on the FP32 pipe: one real
+# multiply-add (2 flops of the FP64 count) costs about 13 FP32 instructions
+# (12.75 in the rank-2 update, 13.5 in the column dot products, which do a
+# third of the work), so its ALU ceiling is the FP32 instruction rate / 13 x 2
+DF_FMA_INSTR = 13.0
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_FMA_INSTR * 2 / 1e12
 HA_MEV = 27211.386245988
 # DRAM bytes per launch of the direct-term kernel from the committed ncu capture
 # (profiles/), keyed by workload; None until a capture of the current kernel exists.
@@ -43,7 +49,7 @@ DIRECT_TRAFFIC = {("si8", "fp64"): 41.711872e6 + 1210.309e6,    # profiles/direc
 # DRAM bytes per launch of the tridiagonal reduction kernel (profiles/), keyed by
 # (workload, block): the block is read once and the reduction then works from
 # shared memory.
-REDUCE_TRAFFIC = {("si8", "partner"): 10.499584e6 + 0.002048e6}    # profiles/tridiag_kernel_si8_partner.md
+REDUCE_TRAFFIC = {("si8", "partner"): 10.5216e6 + 768.0}    # profiles/tridiag_kernel_si8_partner.md
 WORKLOADS = {
     "si8": "Si-like diamond (Oh, a=10.26 bohr), Gamma-centred 8x8x8 mesh, Nv=4, Nc=6, |G|<=3.2 (2pi/a); "
            "T1u block of the full dim 12288",
@@ -323,10 +329,13 @@ def run_ours(args, rank, world, local):
             "fp16": bse.BSE_FP16_SPLIT}[args.prec]
 
     def step(host_inputs=None, d2h=None, p=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ctx = bse.bse_create(host_inputs if host_inputs is not None else inp, stream=stream,
                              device=None if host_inputs is not None else devin)
+        ev[0].record(stream)
         bse.bse_set_timing(ctx, True)
         bse.bse_build_blocks(ctx, targets, pflags, prec if p is None else p, bse.BSE_TERM_ALL, Hs, dims)
+        ev[1].record(stream)
         s1 = bse.bse_get_stats(ctx)
         eig = 0.0
         red = 0.0
@@ -341,6 +350,7 @@ def run_ours(args, rank, world, local):
         s2["ms_eig"] = eig
         s2["ms_reduce"] = red
         s2["solvers"] = solvers
+        s2["events"] = ev
         if d2h is not None:
             for src, dst in zip([x for t in zip(oms, oscs, ims) for x in t], d2h):
                 dst.copy_(src, non_blocking=True)
@@ -357,6 +367,9 @@ def run_ours(args, rank, world, local):
             e1.record(stream)
             e1.synchronize()
             per.append(e0.elapsed_time(e1))
+            ev = s2.pop("events")
+            s2["phase_ms"] = {"create": e0.elapsed_time(ev[0]), "build": ev[0].elapsed_time(ev[1]),
+                              "spectrum": ev[1].elapsed_time(e1)}
             stats.append((s1, s2))
             bse.bse_destroy(ctx)
         return per, stats
@@ -474,8 +487,12 @@ def run_ours(args, rank, world, local):
         rflops = sum(16.0 / 3.0 * n ** 3 for n, s in zip(dims, stats[-1][1]["solvers"]) if s == bse.BSE_SOLVER_TRIDIAG)
         ra = rflops / (ms_reduce * 1e-3) / 1e12
         roofs.append({"bound": "alu", "kernel": "tridiag_kernel", "ms_per_step": ms_reduce, "achieved": ra,
-                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ra / FP64_PEAK_TFLOPS,
-                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)",
+                      "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ra / DF_PEAK_TFLOPS,
+                      "peak_source": "derived: double-float on the FP32 pipe, 152 SMs x 128 FP32 instr/clk x "
+                                     "2.07 GHz / %g instr per real multiply-add x 2 flop; the FP64 pipe "
+                                     "(1.259 TFLOP/s) is not used; the kernel is bound by the latency of its "
+                                     "n sequential reflection steps (one grid barrier each)" % DF_FMA_INSTR,
+                      "frac_of_fp64_pipe": ra / FP64_PEAK_TFLOPS,
                       "flops_per_launch": rflops / max(1, sum(1 for s in stats[-1][1]["solvers"]
                                                               if s == bse.BSE_SOLVER_TRIDIAG)),
                       "launches_per_step": sum(1 for s in stats[-1][1]["solvers"] if s == bse.BSE_SOLVER_TRIDIAG),
@@ -536,6 +553,7 @@ def run_ours(args, rank, world, local):
         "time_to_spectrum_ms": total_ms / args.steps,
         "eigensolver": sorted({{1: "dense zheevd", 2: "tridiagonal reduction (no eigenvectors)"}[s]
                                for s in stats[-1][1]["solvers"]}),
+        "phase_ms": {k: statistics.mean(x[1]["phase_ms"][k] for x in stats) for k in ("create", "build", "spectrum")},
         "stage_ms": {"direct": ms_direct, "rotate_part_of_direct": ms_rotate, "project": ms_project, "exchange": ms_exchange, "eigensolve": ms_eig,
                      "create": statistics.mean(x[1]["ms_create"] for x in stats),
                      "create_parts": {k: statistics.mean(x[1][k] for x in stats)
