@@ -459,7 +459,7 @@ typedef struct {
     float ms_create_tables;     /* ... host tables (group, mesh, stars, characters, orbits) */
     float ms_create_upload;     /* ... device copies of the inputs and the look-up box */
     float ms_create_gamma;      /* ... band rotations (kernels, copy back, unitarity check) */
-    float ms_create_wdiv;       /* ... head correction */
+    float ms_create_wdiv;       /* ... head correction: host time to launch it (its kernels run behind the host work that follows) */
     float ms_basis;             /* wall time of the last basis construction (host, incl. upload) */
     int32_t solver;             /* eigensolver of the last spectrum: BSE_SOLVER_DENSE or BSE_SOLVER_TRIDIAG */
     float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */

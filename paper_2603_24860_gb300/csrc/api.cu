@@ -108,7 +108,8 @@ struct bse_ctx {
     std::vector<PartnerDev> partner;
     std::vector<int64_t> partner_dim;   // dim_mu / d_mu for partner-capable irreps, else 0
     int ng0 = 0;
-    double w_div = 0.0;
+    mutable double w_div = 0.0;        // host copy of W^div, valid when wdiv_host_ok
+    mutable bool wdiv_host_ok = false;
     double spin = 2.0;
     DevBuf P;            // exchange vectors [N][ng0]
     bool P_ready = false;
@@ -129,7 +130,8 @@ struct bse_ctx {
     bool seeds = true;   // compute one k pair per symmetry orbit and rotate the rest
     DevBuf rots;
     DevBuf lossScratch;
-    DevBuf wsym, wcand;  // orbit sum of W^div: per-column arrays and the flat candidate list
+    DevBuf wsym;         // orbit sum of W^div: per-column arrays
+    DevBuf wdivDev;      // W^div on the device (one double), read by the kernels that need it
     int32_t solver_mode = BSE_SOLVER_AUTO;
     DevBuf triScratch, triSmall;   // tridiagonal path: scratch; gram [9], weight sum, error flag
     // scratch (library-owned, grow-only)
@@ -512,21 +514,26 @@ static int compute_wdiv(bse_ctx* c, const double* L) {
     if (sym) {
         BSE_TRY(ensure(c->wsym, wdiv_sym_bytes(c->t.lattice, c->t.n, qmax, delta)));
         ws.base = c->wsym.p;
-        ws.owner = c;
-        ws.grow = [](WdivScratch* self, size_t bytes) -> int {
-            bse_ctx* cc = (bse_ctx*)self->owner;
-            BSE_TRY(ensure(cc->wcand, bytes));
-            self->cand = cc->wcand.p;
-            return BSE_OK;
-        };
     }
+    BSE_TRY(ensure(c->wdivDev, sizeof(double)));
     BSE_TRY(launch_wdiv(rl, c->t.n, L, b, qmax, delta, (double*)c->wpart.p, np, (double*)c->wsum.p, c->stream,
                         sym ? c->t.nops : 0, sym ? Mx.data() : nullptr, sym ? &ws : nullptr));
-    double sum = 0.0;
-    BSE_CUDA(cudaMemcpyAsync(&sum, c->wsum.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    BSE_CUDA(cudaStreamSynchronize(c->stream));
-    double integral = M_PI * h00(L) / std::sqrt(b) * std::erf(std::sqrt(b) * qmax);
-    c->w_div = integral / (2.0 * M_PI * M_PI) - 4.0 * M_PI / (c->t.nk * c->t.v_uc) * sum;
+    // W^div = integral / (2 pi^2) - 4 pi / (N_k V) sum, left on the device: the
+    // sum runs behind the host work that follows (the basis of the first build)
+    const double integral = M_PI * h00(L) / std::sqrt(b) * std::erf(std::sqrt(b) * qmax);
+    BSE_TRY(launch_wdiv_finalize((const double*)c->wsum.p, integral / (2.0 * M_PI * M_PI),
+                                 4.0 * M_PI / (c->t.nk * c->t.v_uc), (double*)c->wdivDev.p, c->stream));
+    c->wdiv_host_ok = false;
+    return BSE_OK;
+}
+
+// the host copy of W^div (waits for its sum)
+static int wdiv_host(const bse_ctx* c) {
+    if (!c->wdiv_host_ok) {
+        BSE_CUDA(cudaMemcpyAsync(&c->w_div, c->wdivDev.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        BSE_CUDA(cudaStreamSynchronize(c->stream));
+        c->wdiv_host_ok = true;
+    }
     return BSE_OK;
 }
 
@@ -768,11 +775,12 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
     c->irr.resize(t.n_irreps);
     const double t4 = now_ms();
     if (std::isnan(sys->w_div)) {
-        BSE_TRY(compute_wdiv(c, sys->eps_inf));
+        BSE_TRY(compute_wdiv(c, sys->eps_inf));   // asynchronous: no wait here
     } else {
         c->w_div = sys->w_div;
+        c->wdiv_host_ok = true;
+        BSE_TRY(upload(c->wdivDev, &c->w_div, 1, st));
     }
-    BSE_CUDA(cudaStreamSynchronize(st));
     const double t5 = now_ms();
     c->stats.ms_create_tables = (float)(t1 - t0);
     c->stats.ms_create_upload = (float)(t2 - t1);
@@ -789,7 +797,7 @@ static void free_ctx(bse_ctx* c) {
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
                       &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots,
-                      &c->lossScratch, &c->wsym, &c->wcand, &c->lzScratch})
+                      &c->lossScratch, &c->wsym, &c->wdivDev, &c->lzScratch})
         release(*b);
     for (auto& d : c->irr) {
         release(d.col_orbit);
@@ -884,6 +892,7 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
     v->bright = t.bright.data();
     v->block_dim = c->block_dim.data();
     v->orbit_of = t.orbit_of.data();
+    BSE_TRY(wdiv_host(c));
     v->w_div = c->w_div;
     v->partner_dim = c->partner_dim.data();
     return BSE_OK;
@@ -937,7 +946,7 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
         BSE_CUDA(cudaMemset2DAsync(h, sizeof(double2) * ld, 0, sizeof(double2) * t.N, t.N, c->stream));
     }
     if (terms & BSE_TERM_DIAG)
-        BSE_TRY(launch_diag_full((const double*)c->de.p, t.N, c->w_div, (double2*)h, ld, c->stream));
+        BSE_TRY(launch_diag_full((const double*)c->de.p, t.N, (const double*)c->wdivDev.p, (double2*)h, ld, c->stream));
     if (terms & BSE_TERM_EXCHANGE) {
         BSE_TRY(ensure_exchange_vectors(c));
         BSE_TRY(launch_exchange_full((const double2*)c->P.p, (const double*)c->vbar.p, c->ng0, t.N,
@@ -1074,7 +1083,7 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             BSE_TRY(launch_project_left(db[i], tl, n, (const double2*)c->arenaY.p,
                                         (terms & BSE_TERM_EXCHANGE) ? (const double2*)c->Pmu.p + pmu_off[i] : nullptr,
                                         (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
-                                        (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
+                                        (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, (const double*)c->wdivDev.p,
                                         (double2*)h[i], ld[i], bt.max_ca[i], bt.max_cb[i], c->stream));
         }
         if (c->timing) {
@@ -1259,7 +1268,7 @@ static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaE
         BSE_TRY(launch_project_left(db, tl, nt, (const double2*)b->arenaY[j].p,
                                     (terms & BSE_TERM_EXCHANGE) ? (const double2*)b->pmu.p + pmu_off[i] : nullptr,
                                     (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
-                                    (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, c->w_div,
+                                    (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, (const double*)c->wdivDev.p,
                                     (double2*)b->h[i], b->ld[i], bt.max_ca[0], bt.max_cb[0], br[j]));
     }
     for (int j = 0; j < nb; ++j) {

@@ -208,11 +208,14 @@ size_t direct_smem(const DevSys& s, int prec32);
 int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st);
 int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X,
                          double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
-// de: eps_c - eps_v per product index (or null to skip the diagonal)
+// de: eps_c - eps_v per product index (or null to skip the diagonal); w_div:
+// device pointer to W^div, subtracted on the diagonal with it
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y,
                         const double2* Pmu, const double* vbar, int ng0, double xscale, const double* de,
-                        double w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
-int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st);
+                        const double* w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
+int launch_diag_full(const double* de, int64_t N, const double* w_div, double2* H, int64_t ld, cudaStream_t st);
+// w = a - b * (*sum), on the stream
+int launch_wdiv_finalize(const double* sum, double a, double b, double* w, cudaStream_t st);
 void note_launch();
 // split-precision tensor-core direct term (direct_tc.cu)
 // split-precision support for a system: NG padded to 16 (ngp), the shared memory of a CTA and the
@@ -261,13 +264,10 @@ int launch_spectrum(const double* Om, const double* osc, int64_t dim, const doub
 // nops > 0, Mx [nops][9] is the point group acting on the integer coordinates
 // of Q = sum X_j b_j / n_j (row-major) and the sum runs over one point per
 // orbit (the caller has checked that L is invariant); nops = 0: every point.
-// scratch of the orbit sum: base holds the per-column arrays (wdiv_sym_bytes),
-// grow(self, bytes) makes cand hold the flat candidate list
+// scratch of the orbit sum: the per-column arrays (wdiv_sym_bytes).  Nothing
+// of the sum returns to the host: out receives it on the stream.
 struct WdivScratch {
-    void* base = nullptr;
-    void* cand = nullptr;
-    int (*grow)(WdivScratch* self, size_t bytes) = nullptr;
-    void* owner = nullptr;
+    void* base = nullptr;   // wdiv_sym_bytes() of device memory
 };
 size_t wdiv_sym_bytes(const double* lattice, const int* n, double qmax, double delta);
 int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, double b, double qmax,

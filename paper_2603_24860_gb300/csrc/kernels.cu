@@ -283,8 +283,8 @@ __global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ t
 
 __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ Y,
                                     const double2* __restrict__ Pmu, const double* __restrict__ vbar, int ng0,
-                                    double xscale, const double* __restrict__ de, double w_div, double2* H,
-                                    int64_t ld) {
+                                    double xscale, const double* __restrict__ de,
+                                    const double* __restrict__ w_div, double2* H, int64_t ld) {
     const TileTask t = tiles[blockIdx.z];
     const int64_t ii = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t nrow = t.ca1 - t.ca0, ncol = t.cb1 - t.cb0;
@@ -308,7 +308,7 @@ __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ ti
                 d.x = fma(e, z.x, d.x);
                 d.y = fma(e, z.y, d.y);
             }
-            acc.x += d.x - (i == j ? w_div : 0.0);
+            acc.x += d.x - (i == j ? *w_div : 0.0);
             acc.y += d.y;
         }
         if (Pmu) {
@@ -348,7 +348,7 @@ int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, i
 }
 
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y, const double2* Pmu,
-                        const double* vbar, int ng0, double xscale, const double* de, double w_div, double2* H,
+                        const double* vbar, int ng0, double xscale, const double* de, const double* w_div, double2* H,
                         int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st) {
     if (ntiles == 0) return BSE_OK;
     dim3 blk(32, 8);
@@ -413,12 +413,13 @@ int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t 
 }
 
 // H[I, I] += eps_c - eps_v - W^div (column-major H)
-__global__ void diag_full_kernel(const double* __restrict__ de, int64_t N, double w_div, double2* H, int64_t ld) {
+__global__ void diag_full_kernel(const double* __restrict__ de, int64_t N, const double* __restrict__ w_div, double2* H,
+                                 int64_t ld) {
     int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (I < N) H[I * ld + I].x += de[I] - w_div;
+    if (I < N) H[I * ld + I].x += de[I] - *w_div;
 }
 
-int launch_diag_full(const double* de, int64_t N, double w_div, double2* H, int64_t ld, cudaStream_t st) {
+int launch_diag_full(const double* de, int64_t N, const double* w_div, double2* H, int64_t ld, cudaStream_t st) {
     diag_full_kernel<<<ceil_div(N, 256), 256, 0, st>>>(de, N, w_div, H, ld);
     LAUNCH_CHECK();
     return BSE_OK;
@@ -665,17 +666,18 @@ __global__ void wdiv_kernel(WdivGeom g, double* partial) {
 // equal projections, by the lexicographic order of the integer vectors); its
 // orbit has |G| / |stab(X)| points.  The necessary conditions (p - M_g^T p).X
 // >= 0 are linear in X_3, so each column (X_1, X_2) is clipped to the
-// interval of its cone (wdiv_clip_kernel); the candidates of all columns are
-// then laid out flat (wdiv_fill_kernel, after a scan of the counts) and
-// evaluated one per thread (wdiv_point_kernel), which keeps the FP64 work of
-// the ~1/|G| remaining points free of the columns' very uneven lengths.
+// interval of its cone (wdiv_clip_kernel); after a scan of the counts every
+// column knows the index of its first candidate (wdiv_offsets_kernel), and
+// the candidates are evaluated one per thread (wdiv_point_kernel, which finds
+// a candidate's column by binary search over those offsets).  That keeps the
+// FP64 work of the ~1/|G| remaining points free of the columns' very uneven
+// lengths, and the whole sum runs without a host round trip.
 struct WdivCols {
     int* lo;            // [ncol] first X_3 of the column's interval
     int* cnt;           // [ncol] candidates of the column
     int64_t* blocksum;  // [nblk] candidates per block of 256 columns, then their exclusive scan
     int64_t* total;     // [1]
-    int* cand;          // [total] column index of each candidate
-    int* x3;            // [total] its X_3
+    int64_t* off;       // [ncol] index of the column's first candidate (nondecreasing)
 };
 
 __device__ __forceinline__ void wdiv_column(const WdivGeom& g, const WdivSym& sy, int64_t id, int& lo, int& hi) {
@@ -757,7 +759,7 @@ __global__ void wdiv_scan_kernel(WdivCols c, int64_t nblk) {
     if (t == 1023) *c.total = s[1023];
 }
 
-__global__ void wdiv_fill_kernel(WdivGeom g, WdivCols c) {
+__global__ void wdiv_offsets_kernel(WdivGeom g, WdivCols c) {
     __shared__ int s[256];
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t ncol = (int64_t)(2 * g.e1 + 1) * (2 * g.e2 + 1);
@@ -770,25 +772,29 @@ __global__ void wdiv_fill_kernel(WdivGeom g, WdivCols c) {
         s[threadIdx.x] += v;
         __syncthreads();
     }
-    const int64_t base = c.blocksum[blockIdx.x] + s[threadIdx.x] - n;
-    const int lo = id < ncol ? c.lo[id] : 0;
-    for (int i = 0; i < n; ++i) {
-        c.cand[base + i] = (int)id;
-        c.x3[base + i] = lo + i;
-    }
+    if (id < ncol) c.off[id] = c.blocksum[blockIdx.x] + s[threadIdx.x] - n;
 }
 
 // one candidate per thread, grid-stride over the total; partial sums per block
 __global__ void wdiv_point_kernel(WdivGeom g, const __grid_constant__ WdivSym sy, WdivCols c, double* partial) {
     __shared__ double red[256];
     const int64_t total = *c.total;
+    const int64_t ncol = (int64_t)(2 * g.e1 + 1) * (2 * g.e2 + 1);
     const double lim2 = g.lim * g.lim, in2 = (g.qmax - g.delta) * (g.qmax - g.delta);
     double acc = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t id = c.cand[q];
+        // the column holding candidate q: the last one whose first candidate is <= q
+        // (an empty column shares its offset with the next column, so it is never last)
+        int64_t lo = 0, hi = ncol - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(c.off + mid) <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t id = lo;
         const int x1 = (int)(id / (2 * g.e2 + 1)) - g.e1;
         const int x2 = (int)(id % (2 * g.e2 + 1)) - g.e2;
-        const int x3 = c.x3[q];
+        const int x3 = __ldg(c.lo + id) + (int)(q - __ldg(c.off + id));
         if (x1 == 0 && x2 == 0 && x3 == 0) continue;
         double Q[3];
 #pragma unroll
@@ -862,6 +868,16 @@ __global__ void reduce_kernel(const double* __restrict__ partial, int64_t n, dou
     if (threadIdx.x == 0) *out = red[0];
 }
 
+__global__ void wdiv_finalize_kernel(const double* __restrict__ sum, double a, double b, double* w) {
+    *w = a - b * *sum;
+}
+
+int launch_wdiv_finalize(const double* sum, double a, double b, double* w, cudaStream_t st) {
+    wdiv_finalize_kernel<<<1, 1, 0, st>>>(sum, a, b, w);
+    LAUNCH_CHECK();
+    return BSE_OK;
+}
+
 static void wdiv_extent(const double* lattice, const int* n, double lim, int e[3]) {
     for (int j = 0; j < 3; ++j) {
         double len = sqrt(lattice[j] * lattice[j] + lattice[3 + j] * lattice[3 + j] + lattice[6 + j] * lattice[6 + j]);
@@ -874,7 +890,7 @@ size_t wdiv_sym_bytes(const double* lattice, const int* n, double qmax, double d
     wdiv_extent(lattice, n, qmax + delta, e);
     const int64_t ncol = (int64_t)(2 * e[0] + 1) * (2 * e[1] + 1);
     const int64_t nblk = (ncol + 255) / 256;
-    return sizeof(int) * 2 * (size_t)ncol + 16 + sizeof(int64_t) * (size_t)(nblk + 1);
+    return sizeof(int) * 2 * (size_t)ncol + 16 + sizeof(int64_t) * (size_t)(nblk + 1 + ncol);
 }
 
 int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta) {
@@ -929,19 +945,12 @@ int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, 
         c.cnt = c.lo + ncol;
         c.blocksum = (int64_t*)(((uintptr_t)(c.cnt + ncol) + 15) & ~(uintptr_t)15);
         c.total = c.blocksum + nblk;
-        c.cand = nullptr;
-        c.x3 = nullptr;
+        c.off = c.total + 1;
         wdiv_clip_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, sy, c);
         LAUNCH_CHECK();
         wdiv_scan_kernel<<<1, 1024, 0, st>>>(c, nblk);
         LAUNCH_CHECK();
-        int64_t total = 0;
-        BSE_CUDA(cudaMemcpyAsync(&total, c.total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        BSE_CUDA(cudaStreamSynchronize(st));
-        BSE_TRY(sym_scratch->grow(sym_scratch, (size_t)std::max<int64_t>(total, 1) * 2 * sizeof(int)));
-        c.cand = (int*)sym_scratch->cand;
-        c.x3 = c.cand + std::max<int64_t>(total, 1);
-        wdiv_fill_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, c);
+        wdiv_offsets_kernel<<<(unsigned)nblk, 256, 0, st>>>(g, c);
         LAUNCH_CHECK();
         const int64_t pb = std::min<int64_t>(nblk, 152 * 8);
         wdiv_point_kernel<<<(unsigned)pb, 256, 0, st>>>(g, sy, c, partial);
