@@ -403,7 +403,7 @@ struct TriBounds {
 // Gershgorin interval, deflation of negligible off-diagonals, e^2, and FP32
 // copies of d and e^2 for the first rounds of the bisection (one block)
 __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __restrict__ e, int64_t n, double* e2,
-                                  float* d32, float* e2_32, TriBounds* out) {
+                                  float* d32, float* e2_32, float2* d_df, float2* e2_df, TriBounds* out) {
     __shared__ double s_lo[kTriWarps], s_hi[kTriWarps], s_nm[kTriWarps], s_e[kTriWarps];
     __shared__ int s_m[kTriWarps];
     double lo = DBL_MAX, hi = -DBL_MAX, nm = 0.0, emax = 0.0;
@@ -444,9 +444,13 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
         const bool small = fabs(e[i]) <= tol;
         e2[i] = small ? 0.0 : e[i] * e[i];
         e2_32[i] = (float)e2[i];
+        e2_df[i] = df_from(e2[i]);
         if (small && (int)i + 1 < m) m = (int)i + 1;
     }
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) d32[i] = (float)d[i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        d32[i] = (float)d[i];
+        d_df[i] = df_from(d[i]);
+    }
     for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) s_m[wid] = m;
     __syncthreads();
@@ -462,39 +466,6 @@ __global__ void tri_bounds_kernel(const double* __restrict__ d, const double* __
         b.pivmin32 = FLT_MIN * (float)fmin(fmax(1.0, emax), 1e30);
         *out = b;
     }
-}
-
-// Number of eigenvalues below x of the tridiagonal rows [i0, i1): sign
-// changes of the leading principal minors p_i = det(T[i0..i] - x), from the
-// three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm).
-// No division (an FP64 divide costs about a thousand cycles of latency on
-// this GPU); p_{i-1}, p_i are rescaled by an exact power of two every eight
-// rows.  An exact zero p_i is replaced by -2^-200 p_{i-1}, as a zero pivot is
-// replaced by a tiny negative one in the ratio form.
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int i0, int i1,
-                                           double x) {
-    double pm = 1.0, p = __ldg(d + i0) - x;
-    if ((__double_as_longlong(p) << 1) == 0) p = -0x1p-200;
-    bool sp = neg_bit(p);
-    int c = sp;
-    for (int i = i0 + 1; i < i1; ++i) {
-        double pn = fma(__ldg(d + i) - x, p, -__ldg(e2 + i - 1) * pm);
-        if ((__double_as_longlong(pn) << 1) == 0) pn = -p * 0x1p-200;   // zero pivot -> -tiny (ratio p_i / p_{i-1})
-        const bool sn = neg_bit(pn);
-        c += sn != sp;
-        sp = sn;
-        pm = p;
-        p = pn;
-        if (((i - i0) & 7) == 0) {
-            const int ex = (int)((__double_as_longlong(p) >> 52) & 0x7ff) - 1023;
-            if (ex > 256 || ex < -256) {
-                const double s = exp2i(-ex);
-                p *= s;
-                pm *= s;
-            }
-        }
-    }
-    return c;
 }
 
 // Number of eigenvalues below x of rows [i0, i1) in FP32, ratio form
@@ -516,18 +487,44 @@ __device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const 
     return c;
 }
 
+// The same count in double-float (ratio form, FP32 exponent range, pivots
+// kept at least pivmin in magnitude): exact for a matrix within a few units
+// of 2^-47 of T, on the FP32 pipe.  A quotient e^2/q beyond FP32's range
+// stands for the infinite one of IEEE arithmetic (the next pivot takes its
+// sign, and the quotient after it vanishes).
+__device__ __forceinline__ int sturm_count_df(const float2* __restrict__ d, const float2* __restrict__ e2, int i0,
+                                              int i1, float2 x, float pivmin) {
+    const float2 nx = df_neg(x);
+    float2 q = df_add(__ldg(d + i0), nx);
+    if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
+    int c = q.x < 0.f;
+    for (int i = i0 + 1; i < i1; ++i) {
+        const float2 dx = df_add(__ldg(d + i), nx);
+        const float2 t = df_mul(__ldg(e2 + i - 1), df_rcp(q));
+        q = fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f);
+        if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
+        c += q.x < 0.f;
+    }
+    return c;
+}
+
 // Sixteen lanes per level: 17-section of the Gershgorin interval with Sturm
 // counts: 6 rounds in FP32 (from 2 ||T|| to about eps_32 ||T||), the bracket
-// widened by the FP32 counts' backward error, then 9 rounds in FP64 to below
-// eps ||T|| (17^9 > 1e11).  GB300 runs two FP64 lanes
-// per clock per SM, so the cost is the chain of FP64 warp instructions each
-// warp issues: fewer, wider rounds and one warp per SM sub-partition beat
-// narrow bisection.  Every lane runs all rounds (uniform ballots).  Levels
-// k < m belong to rows [0, m), the others to rows [m, n).
+// widened by the FP32 counts' backward error (16 eps_32 (||T|| + |x|)), then
+// 7 rounds in double-float to about 2e-14 ||T|| (17^7 = 4e8), below the
+// backward error of the double-float reduction that made T.  Both kinds of
+// count run on the FP32 pipe; the cost is each warp's chain of dependent
+// instructions, so fewer, wider rounds beat narrow bisection.  Every lane
+// runs all rounds (uniform ballots).  Levels k < m belong to rows [0, m),
+// the others to rows [m, n).  Launched as blocks of four warps, one per SM
+// sub-partition.
 constexpr int kSect = 16;
-__global__ void bisect_kernel(const double* __restrict__ d, const double* __restrict__ e2,
-                              const float* __restrict__ d32, const float* __restrict__ e2_32, int64_t n,
-                              const TriBounds* __restrict__ bnd, double* lam) {
+constexpr int kBisectThreads = 128;
+__global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __restrict__ d_df,
+                                                                const float2* __restrict__ e2_df,
+                                                                const float* __restrict__ d32,
+                                                                const float* __restrict__ e2_32, int64_t n,
+                                                                const TriBounds* __restrict__ bnd, double* lam) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, sub = lane % kSect, base = lane - sub;
     const int64_t k = min(t / kSect, n - 1);
@@ -547,9 +544,9 @@ __global__ void bisect_kernel(const double* __restrict__ d, const double* __rest
     }
     const double del = 16.0 * FLT_EPSILON * (b.tnorm + fmax(fabs((double)lof), fabs((double)hif)));
     double lo = fmax(b.gl, (double)lof - del), hi = fmin(b.gu, (double)hif + del);
-    for (int it = 0; it < 9; ++it) {
+    for (int it = 0; it < 7; ++it) {
         const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (kSect + 1));
-        const int c = sturm_count(d, e2, i0, i1, x);
+        const int c = sturm_count_df(d_df, e2_df, i0, i1, df_from(x), b.pivmin32);
         const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
         const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
         const double xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
@@ -682,9 +679,10 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 
 size_t tridiag_scratch_bytes(int64_t n) {
     // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (16 bytes each); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
+    // d_df, e2_df (n float2);
     // twisted passes 5 n*n doubles; 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) +
-           sizeof(float) * (size_t)(2 * n) + 8192;
+           sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) + 8192;
 }
 
 int tridiag_max_dim() { return 4736; }   // v, w and the next column of a step in 227 KB of shared memory
@@ -717,6 +715,8 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     double* e2 = (double*)take(sizeof(double) * n);
     float* d32 = (float*)take(sizeof(float) * n);
     float* e2_32 = (float*)take(sizeof(float) * n);
+    float2* d_df = (float2*)take(sizeof(float2) * n);
+    float2* e2_df = (float2*)take(sizeof(float2) * n);
     double* lam = (double*)take(sizeof(double) * n);
     double* w = (double*)take(sizeof(double) * n);
     double* beta0 = (double*)take(sizeof(double));
@@ -768,10 +768,11 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     note_launch();
     if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
 
-    tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, d32, e2_32, bnd);
+    tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, d32, e2_32, d_df, e2_df, bnd);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    bisect_kernel<<<(unsigned)((kSect * n + 31) / 32), 32, 0, st>>>(d, e2, d32, e2_32, n, bnd, lam);
+    bisect_kernel<<<(unsigned)((kSect * n + kBisectThreads - 1) / kBisectThreads), kBisectThreads, 0, st>>>(
+        d_df, e2_df, d32, e2_32, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d, e, n, bnd, lam, dp, w);
