@@ -107,6 +107,8 @@ struct bse_ctx {
     };
     std::vector<PartnerDev> partner;
     std::vector<int64_t> partner_dim;   // dim_mu / d_mu for partner-capable irreps, else 0
+    std::vector<std::vector<double>> pgam;   // irrep matrices [s][d][d] of partner-capable irreps
+    std::vector<int> pgam_d;                 // their dimension, 0 where there are none
     int ng0 = 0;
     mutable double w_div = 0.0;        // host copy of W^div, valid when wdiv_host_ok
     mutable bool wdiv_host_ok = false;
@@ -145,13 +147,34 @@ struct bse_ctx {
 
 namespace {
 
+// std::allocator whose resize leaves trivially constructible elements
+// uninitialised: the planner fills the task lists in parallel afterwards
+template <class T>
+struct NoInit : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInit<U>;
+    };
+    NoInit() = default;
+    template <class U>
+    NoInit(const NoInit<U>&) {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... args) {
+        ::new ((void*)p) U(std::forward<A>(args)...);
+    }
+};
+
 // star-pair tiles shared by one or more target bases (irrep blocks or partner
 // blocks), grouped into batches whose X and Y arenas fit a budget.  X (the
 // direct term on the product basis of a star pair) does not depend on the
 // target, so every target of a batch projects the same X tiles.
 struct Batch {
     std::vector<PairTask> tasks;          // k pairs the direct kernel computes (seeds when symmetry is used)
-    std::vector<RotTask> rots;            // k pairs rotated from their seed (Eq. Wtrafo)
+    std::vector<RotTask, NoInit<RotTask>> rots;   // k pairs rotated from their seed (Eq. Wtrafo)
     std::vector<TileTask> tiles;          // all targets' tiles, concatenated
     std::vector<int> tile_off;            // [targets + 1] range of each target in tiles
     size_t xbytes = 0;
@@ -168,16 +191,16 @@ size_t arena_budget() {
 // (s k0, s k'_r)-equivalent to a pair with k0 = star a's representative and
 // k'_r the representative (lowest k) of the orbit of k' under the little
 // group of k0.  rep[j], gop[j] for the members j of star b: that
-// representative and an operation of the little group taking k'_j to it.
-static void little_orbits(const Tables& t, int a, int b, std::vector<int>& rep, std::vector<int>& gop) {
-    const int k0 = t.stars[a][0];
+// representative and the first operation of the little group lg (ascending)
+// taking k'_j to it.
+static void little_orbits(const Tables& t, const std::vector<int>& lg, int b, std::vector<int>& rep,
+                          std::vector<int>& gop) {
     const auto& sb = t.stars[b];
     rep.assign(sb.size(), -1);
     gop.assign(sb.size(), -1);
     for (size_t j = 0; j < sb.size(); ++j) {
         const int kp = sb[j];
-        for (int g = 0; g < t.nops; ++g) {
-            if (t.rotk[(size_t)g * t.nk + k0] != k0) continue;
+        for (int g : lg) {
             const int x = t.rotk[(size_t)g * t.nk + kp];
             if (rep[j] < 0 || x < rep[j]) {
                 rep[j] = x;
@@ -187,6 +210,12 @@ static void little_orbits(const Tables& t, int a, int b, std::vector<int>& rep, 
     }
 }
 
+// Batches of star-pair tiles (a <= b over the stars some target uses) under
+// the arena budget, with every target's tiles and the k pairs of each tile:
+// the seeds the direct kernel computes and the pairs rotated from them.  The
+// tiles are placed in one sequential pass (cheap); the k pairs, about N_k^2/2
+// of them, are counted and then written by the host thread pool, tile by
+// tile, at offsets from a prefix sum, in the same order as a sequential loop.
 int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t budget, std::vector<Batch>& out,
                  bool seeds = false) {
     out.clear();
@@ -194,7 +223,6 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
     for (int a = 0; a < t.nops; ++a)
         for (int b = 0; b < t.nops; ++b)
             if (t.mult[(size_t)a * t.nops + b] == t.identity) inv[a] = b;
-    std::vector<int> rep, gop;
     const size_t nt = bases.size();
     auto ncols = [&](size_t i, int a) { return bases[i]->star_col[a + 1] - bases[i]->star_col[a]; };
     std::vector<int> act;
@@ -205,8 +233,24 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
                 break;
             }
     const int B = t.B;
+    // little group of each used star's representative (ascending operations)
+    std::vector<std::vector<int>> lg(t.stars.size());
+    if (seeds)
+        for (int a : act) {
+            const int k0 = t.stars[a][0];
+            for (int g = 0; g < t.nops; ++g)
+                if (t.rotk[(size_t)g * t.nk + k0] == k0) lg[a].push_back(g);
+        }
+    struct Tile {
+        int a, b, batch;
+        int64_t xoff, rows;
+        int64_t seeds = 0, pairs = 0, task_off = 0, rot_off = 0;
+        std::vector<int> rep, gop;
+    };
+    std::vector<Tile> tiles;
     std::vector<std::vector<TileTask>> per(nt);
     Batch cur;
+    int nb = 0;
     auto reset = [&]() {
         cur = Batch();
         cur.ybytes.assign(nt, 0);
@@ -222,8 +266,10 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
             cur.tile_off.push_back((int)cur.tiles.size());
         }
         out.push_back(std::move(cur));
+        ++nb;
     };
     reset();
+    bool any = false;   // the current batch has a tile
     for (size_t iA = 0; iA < act.size(); ++iA)
         for (size_t iB = iA; iB < act.size(); ++iB) {
             const int a = act[iA], b = act[iB];
@@ -232,9 +278,9 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
             if (!used) continue;
             const int64_t rows = (int64_t)t.stars[a].size() * B, cols = (int64_t)t.stars[b].size() * B;
             const size_t xs = sizeof(double2) * rows * cols;
-            bool full = !cur.tasks.empty() && cur.xbytes + xs > budget;
+            bool full = any && cur.xbytes + xs > budget;
             for (size_t i = 0; i < nt && !full; ++i)
-                full = !cur.tasks.empty() && ncols(i, a) > 0 && cur.ybytes[i] + sizeof(double2) * rows * ncols(i, b) > budget;
+                full = any && ncols(i, a) > 0 && cur.ybytes[i] + sizeof(double2) * rows * ncols(i, b) > budget;
             if (full) {
                 flush();
                 reset();
@@ -260,49 +306,111 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
                 cur.max_ca[i] = std::max(cur.max_ca[i], ma);
                 cur.max_cb[i] = std::max(cur.max_cb[i], mb);
             }
-            const auto& sa = t.stars[a];
-            const auto& sb = t.stars[b];
-            if (seeds) little_orbits(t, a, b, rep, gop);
-            const int k0 = sa[0];
-            for (size_t i = 0; i < sa.size(); ++i)
-                for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
-                    if (seeds) {
-                        const int k = sa[i], kp = sb[j];
-                        const int s1 = inv[t.s_k[k]];   // takes k to k0
-                        const int jpp = t.pos_in_star[t.rotk[(size_t)s1 * t.nk + kp]];
-                        const int r = rep[jpp];
-                        const int s = t.mult[(size_t)gop[jpp] * t.nops + s1];
-                        if (t.rotk[(size_t)s * t.nk + k] != k0 || t.rotk[(size_t)s * t.nk + kp] != r)
-                            return fail(BSE_ESYMM, "seed of the k pair (%d, %d) not found", k, kp);
-                        const int jr = t.pos_in_star[r];
-                        if (!(i == 0 && (int)j == jr)) {
-                            RotTask rt;
-                            rt.src = xoff + (int64_t)jr * B * rows;
-                            rt.dst = xoff + (int64_t)j * B * rows + (int64_t)i * B;
-                            rt.dstm = xoff + (int64_t)i * B * rows + (int64_t)j * B;
-                            rt.k = k;
-                            rt.kp = kp;
-                            rt.s = s;
-                            rt.ld = (int32_t)rows;
-                            rt.flags = (a == b && j > i) ? 1 : 0;
-                            rt.pad = 0;
-                            cur.rots.push_back(rt);
-                            continue;
-                        }
-                    }
-                    PairTask p;
-                    p.k = sa[i];
-                    p.kp = sb[j];
-                    p.row0 = (int32_t)(i * B);
-                    p.col0 = (int32_t)(j * B);
-                    p.xoff = xoff;
-                    p.ld = (int32_t)rows;
-                    p.flags = (a == b && j > i) ? 1 : 0;
-                    cur.tasks.push_back(p);
-                }
+            Tile tl;
+            tl.a = a;
+            tl.b = b;
+            tl.batch = nb;
+            tl.xoff = xoff;
+            tl.rows = rows;
+            const int64_t na = (int64_t)t.stars[a].size(), nbm = (int64_t)t.stars[b].size();
+            tl.pairs = a == b ? na * (na + 1) / 2 : na * nbm;
+            tiles.push_back(std::move(tl));
             cur.xbytes += xs;
+            any = true;
         }
-    if (!cur.tasks.empty()) flush();
+    if (any) flush();
+    // k pairs: seeds per tile (the members of star b that are their own
+    // little-orbit representative, paired with k0), offsets, then the lists
+    const int ntl = (int)tiles.size();
+    std::vector<double> cost(ntl);
+    for (int q = 0; q < ntl; ++q) cost[q] = (double)tiles[q].pairs;
+    host_parallel_for(ntl, [&](int q) {
+        Tile& tl = tiles[q];
+        if (seeds) {
+            little_orbits(t, lg[tl.a], tl.b, tl.rep, tl.gop);
+            const auto& sb = t.stars[tl.b];
+            for (size_t j = 0; j < sb.size(); ++j) tl.seeds += tl.rep[j] == sb[j];
+        } else {
+            tl.seeds = tl.pairs;
+        }
+    }, &cost);
+    {
+        std::vector<int64_t> nt_task(out.size(), 0), nt_rot(out.size(), 0);
+        for (Tile& tl : tiles) {
+            tl.task_off = nt_task[tl.batch];
+            tl.rot_off = nt_rot[tl.batch];
+            nt_task[tl.batch] += tl.seeds;
+            nt_rot[tl.batch] += tl.pairs - tl.seeds;
+        }
+        for (size_t q = 0; q < out.size(); ++q) {
+            out[q].tasks.resize((size_t)nt_task[q]);
+            out[q].rots.resize((size_t)nt_rot[q]);
+        }
+    }
+    std::vector<char> bad(ntl, 0);
+    host_parallel_for(ntl, [&](int q) {
+        const Tile& tl = tiles[q];
+        Batch& bt = out[tl.batch];
+        const int a = tl.a, b = tl.b;
+        const int64_t xoff = tl.xoff, rows = tl.rows;
+        const auto& sa = t.stars[a];
+        const auto& sb = t.stars[b];
+        const int k0 = sa[0];
+        PairTask* pt = bt.tasks.data() + tl.task_off;
+        RotTask* rt = bt.rots.data() + tl.rot_off;
+        int64_t ntask = 0, nrot = 0;
+        for (size_t i = 0; i < sa.size(); ++i)
+            for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
+                if (seeds) {
+                    const int k = sa[i], kp = sb[j];
+                    const int s1 = inv[t.s_k[k]];   // takes k to k0
+                    const int jpp = t.pos_in_star[t.rotk[(size_t)s1 * t.nk + kp]];
+                    const int r = tl.rep[jpp];
+                    const int s = t.mult[(size_t)tl.gop[jpp] * t.nops + s1];
+                    if (t.rotk[(size_t)s * t.nk + k] != k0 || t.rotk[(size_t)s * t.nk + kp] != r) {
+                        bad[q] = 1;
+                        return;
+                    }
+                    const int jr = t.pos_in_star[r];
+                    if (!(i == 0 && (int)j == jr)) {
+                        if (tl.rot_off + nrot >= tl.rot_off + (tl.pairs - tl.seeds)) {
+                            bad[q] = 2;
+                            return;
+                        }
+                        RotTask& o = rt[nrot++];
+                        o.src = xoff + (int64_t)jr * B * rows;
+                        o.dst = xoff + (int64_t)j * B * rows + (int64_t)i * B;
+                        o.dstm = xoff + (int64_t)i * B * rows + (int64_t)j * B;
+                        o.k = k;
+                        o.kp = kp;
+                        o.s = s;
+                        o.ld = (int32_t)rows;
+                        o.flags = (a == b && j > i) ? 1 : 0;
+                        o.pad = 0;
+                        continue;
+                    }
+                }
+                if (ntask >= tl.seeds) {
+                    bad[q] = 2;
+                    return;
+                }
+                PairTask& p = pt[ntask++];
+                p.k = sa[i];
+                p.kp = sb[j];
+                p.row0 = (int32_t)(i * B);
+                p.col0 = (int32_t)(j * B);
+                p.xoff = xoff;
+                p.ld = (int32_t)rows;
+                p.flags = (a == b && j > i) ? 1 : 0;
+            }
+        if (ntask != tl.seeds || nrot != tl.pairs - tl.seeds) bad[q] = 2;
+    }, &cost);
+    for (int q = 0; q < ntl; ++q) {
+        if (bad[q] == 1) return fail(BSE_ESYMM, "seed of a k pair of star pair (%d, %d) not found", tiles[q].a, tiles[q].b);
+        if (bad[q] == 2)
+            return fail(BSE_ESYMM, "star pair (%d, %d): seeds are not the own little-orbit representatives",
+                        tiles[q].a, tiles[q].b);
+    }
     return BSE_OK;
 }
 
@@ -338,9 +446,9 @@ static int ensure_partner(bse_ctx* c, int mu) {
     auto& pd = c->partner[mu];
     if (pd.ready) return BSE_OK;
     const double t0 = now_ms();
-    int d = 0;
-    std::vector<double> gam;
-    BSE_TRY(partner_matrices(c->t, mu, d, gam));
+    const int d = c->pgam_d[mu];
+    if (d == 0) return fail(BSE_EUNSUPPORTED, "irrep %d has no irrep matrices for a partner block", mu);
+    const std::vector<double>& gam = c->pgam[mu];
     const int G = c->t.nops;
     auto weights = [&](int i, int j) {
         std::vector<double> w(G);
@@ -745,14 +853,25 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
         tot += r;
     }
     if (tot != t.N) return fail(BSE_ESYMM, "block dimensions sum to %lld, not N = %lld", (long long)tot, (long long)t.N);
+    // irrep matrices of every irrep that has them (one irrep per host thread),
+    // kept for the partner bases, and the partner dimensions Tr P_11
     c->partner_dim.assign(t.n_irreps, 0);
-    for (int mu = 0; mu < t.n_irreps; ++mu) {
+    c->pgam.assign(t.n_irreps, {});
+    c->pgam_d.assign(t.n_irreps, 0);
+    host_parallel_for(t.n_irreps, [&](int mu) {
         int d = 0;
         std::vector<double> gam;
         if (partner_matrices(t, mu, d, gam) != BSE_OK) {   // no irrep matrices: no partner block
             clear_error();
-            continue;
+            return;
         }
+        c->pgam[mu] = std::move(gam);
+        c->pgam_d[mu] = d;
+    });
+    for (int mu = 0; mu < t.n_irreps; ++mu) {
+        const int d = c->pgam_d[mu];
+        if (d == 0) continue;
+        const std::vector<double>& gam = c->pgam[mu];
         cplx a = 0;
         for (int s = 0; s < t.nops; ++s) a += gam[(size_t)s * d * d] * trace[s];
         double dd = a.real() * d / t.nops;

@@ -543,6 +543,10 @@ static void parallel_for(int n, F f, const std::vector<double>* cost = nullptr) 
     });
 }
 
+void host_parallel_for(int n, const std::function<void(int)>& f, const std::vector<double>* cost) {
+    parallel_for(n, [&](int i) { f(i); }, cost);
+}
+
 int check_band_rotations(const Tables& t) {
     // each multiplet block of Gamma(s) at k must be unitary (one operation per host thread)
     std::atomic<int> bad{-1};

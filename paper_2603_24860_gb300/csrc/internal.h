@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -83,6 +84,9 @@ int build_mesh(Tables& t);
 int build_characters(Tables& t);
 int build_multiplets_and_orbits(Tables& t, const double* eps_host);
 int check_band_rotations(const Tables& t);
+// f(0), ..., f(n-1) on the persistent host thread pool (largest cost first when
+// costs are given); returns when all have run
+void host_parallel_for(int n, const std::function<void(int)>& f, const std::vector<double>* cost = nullptr);
 
 // canonical basis of one irrep (host_tables.cpp)
 struct Basis {
