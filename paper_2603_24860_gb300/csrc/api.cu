@@ -87,6 +87,7 @@ struct IrrepDev {
     bool ready = false;
     Basis host;
     DevBuf col_orbit, col_off, coef;
+    DevBuf coef_df;   // coef in double-float, for the projection of FP32 tiles
 };
 
 }  // namespace
@@ -422,6 +423,7 @@ static DevBasis dev_basis_of(bse_ctx* c, IrrepDev& d) {
     b.col_orbit = (const int*)d.col_orbit.p;
     b.col_off = (const int64_t*)d.col_off.p;
     b.coef = (const double2*)d.coef.p;
+    b.coef_df = (const float4*)d.coef_df.p;
     b.orbit_off = (const int64_t*)c->orbit_off.p;
     b.members = (const int64_t*)c->members.p;
     b.member_loc = (const int*)c->member_loc.p;
@@ -434,6 +436,8 @@ static int upload_basis(bse_ctx* c, IrrepDev& d) {
     BSE_TRY(upload(d.col_orbit, d.host.col_orbit.data(), d.host.col_orbit.size(), c->stream));
     BSE_TRY(upload(d.col_off, d.host.col_off.data(), d.host.col_off.size(), c->stream));
     BSE_TRY(upload(d.coef, reinterpret_cast<const double2*>(d.host.coef.data()), d.host.coef.size(), c->stream));
+    BSE_TRY(ensure(d.coef_df, sizeof(float4) * d.host.coef.size()));
+    BSE_TRY(launch_to_df((const double2*)d.coef.p, (float4*)d.coef_df.p, (int64_t)d.host.coef.size(), c->stream));
     BSE_CUDA(cudaStreamSynchronize(c->stream));
     d.ready = true;
     return BSE_OK;
@@ -922,12 +926,14 @@ static void free_ctx(bse_ctx* c) {
         release(d.col_orbit);
         release(d.col_off);
         release(d.coef);
+        release(d.coef_df);
     }
     for (auto& p : c->partner)
         for (auto& d : p.part) {
             release(d.col_orbit);
             release(d.col_off);
             release(d.coef);
+            release(d.coef_df);
         }
     if (c->solver) cusolverDnDestroy(c->solver);
     for (auto& e : c->ev)

@@ -163,6 +163,7 @@ struct DevBasis {
     const int* col_orbit;       // [dim]
     const int64_t* col_off;     // [dim+1]
     const double2* coef;        // concatenated
+    const float4* coef_df;      // the same in double-float (real hi, lo, imaginary hi, lo)
     const int64_t* orbit_off;   // [n_orbits+1]
     const int64_t* members;     // product indices
     const int* member_loc;      // local row of each member inside its star tile
@@ -210,6 +211,8 @@ int launch_rotate_multi(const RotSys* systems, int bmax, int prec32, const RotTa
 // dynamic shared memory of the direct kernel for a system
 size_t direct_smem(const DevSys& s, int prec32);
 int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st);
+// complex double-float copy (real hi, lo, imaginary hi, lo) of n complex doubles
+int launch_to_df(const double2* in, float4* out, int64_t n, cudaStream_t st);
 int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X,
                          double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
 // de: eps_c - eps_v per product index (or null to skip the diagonal); w_div:

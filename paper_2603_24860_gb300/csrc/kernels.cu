@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "dfloat.h"
 #include "fp64_fast.h"
 #include "internal.h"
 
@@ -259,6 +260,7 @@ int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs
 //   Y = X U_b   (tile rows of star a, columns of star b's basis vectors)
 //   H_mu[cols a, cols b] = U_a^dagger Y (+ exchange, projected)
 // ---------------------------------------------------------------------------
+// FP64 tiles (the FP64 build): FP64 products and sums
 template <typename VX>
 __global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const VX* __restrict__ X,
                                      double2* Y) {
@@ -279,6 +281,53 @@ __global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ t
         }
         Y[t.yoff + jj * t.rows + r] = acc;
     }
+}
+
+// FP32 tiles (the mixed builds): each product of an FP32 element of X with a
+// coefficient of U is formed exactly in double-float (TwoProduct) and summed
+// in double-float on the FP32 pipe, whose rate is 64 times the FP64 pipe's;
+// the sum's error (about 2^-47 relative) is far below that of the FP32 tile
+__global__ void project_right_df_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const float2* __restrict__ X,
+                                        double2* Y) {
+    const TileTask t = tiles[blockIdx.z];
+    const int r = blockIdx.x * 32 + threadIdx.x;
+    const int64_t ncol = t.cb1 - t.cb0;
+    if (r >= t.rows) return;
+    const float2* Xt = X + t.xoff;
+    for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
+        const int64_t j = t.cb0 + jj;
+        const int o = Bs.col_orbit[j];
+        const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+        const float4* u = Bs.coef_df + Bs.col_off[j];
+        float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+        for (int64_t tt = 0; tt < n_o; ++tt) {
+            const float2 x = Xt[(int64_t)Bs.member_loc[m0 + tt] * t.rows + r];
+            const float4 c = u[tt];
+            // (x.x + i x.y)(c.re + i c.im), x exact in FP32
+            df_acc(sr, lr, x.x, 0.f, c.x, c.y);
+            df_acc(sr, lr, -x.y, 0.f, c.z, c.w);
+            df_acc(si, li, x.x, 0.f, c.z, c.w);
+            df_acc(si, li, x.y, 0.f, c.x, c.y);
+            const float2 fr = df_fin(sr, lr), fi = df_fin(si, li);
+            sr = fr.x;
+            lr = fr.y;
+            si = fi.x;
+            li = fi.y;
+        }
+        Y[t.yoff + jj * t.rows + r] = make_double2((double)sr + (double)lr, (double)si + (double)li);
+    }
+}
+
+__global__ void to_df_kernel(const double2* __restrict__ in, float4* out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cdf_from(in[i]);
+}
+
+int launch_to_df(const double2* in, float4* out, int64_t n, cudaStream_t st) {
+    if (n == 0) return BSE_OK;
+    to_df_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(in, out, n);
+    LAUNCH_CHECK();
+    return BSE_OK;
 }
 
 __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const double2* __restrict__ Y,
@@ -339,7 +388,7 @@ int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, i
         int n = ntiles - off < 65535 ? ntiles - off : 65535;
         dim3 grd(ceil_div(max_rows, 32), gy, n);
         if (x32)
-            project_right_kernel<float2><<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, Y);
+            project_right_df_kernel<<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, Y);
         else
             project_right_kernel<double2><<<grd, blk, 0, st>>>(b, tiles + off, (const double2*)X, Y);
         LAUNCH_CHECK();
