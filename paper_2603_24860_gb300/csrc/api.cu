@@ -132,6 +132,10 @@ struct bse_ctx {
     DevBuf gam, gam32, gkoff, gboff, mfirst, msize;
     bool seeds = true;   // compute one k pair per symmetry orbit and rotate the rest
     DevBuf rots;
+    DevBuf rtiles, rmeta;   // device enumeration of the rotated pairs: tile records, per-member arrays
+    DevBuf rtab_buf;        // group and star tables it reads (made on first use)
+    RotTables rtab{};
+    bool rtab_ready = false;
     DevBuf lossScratch;
     DevBuf wsym;         // orbit sum of W^div: per-column arrays
     DevBuf wdivDev;      // W^div on the device (one double), read by the kernels that need it
@@ -175,7 +179,10 @@ struct NoInit : std::allocator<T> {
 // target, so every target of a batch projects the same X tiles.
 struct Batch {
     std::vector<PairTask> tasks;          // k pairs the direct kernel computes (seeds when symmetry is used)
-    std::vector<RotTask, NoInit<RotTask>> rots;   // k pairs rotated from their seed (Eq. Wtrafo)
+    std::vector<RotTask, NoInit<RotTask>> rots;   // k pairs rotated from their seed (Eq. Wtrafo), host list
+    std::vector<RotTile> rtiles;          // or: the tiles whose rotated pairs the device enumerates,
+    std::vector<int> rmeta;               // their per-member arrays (jr, then gop, then seedpre)
+    int64_t npairs = 0, nrots = 0;        // the pairs of those tiles and the rotated ones
     std::vector<TileTask> tiles;          // all targets' tiles, concatenated
     std::vector<int> tile_off;            // [targets + 1] range of each target in tiles
     size_t xbytes = 0;
@@ -194,12 +201,11 @@ size_t arena_budget() {
 // group of k0.  rep[j], gop[j] for the members j of star b: that
 // representative and the first operation of the little group lg (ascending)
 // taking k'_j to it.
-static void little_orbits(const Tables& t, const std::vector<int>& lg, int b, std::vector<int>& rep,
-                          std::vector<int>& gop) {
+static void little_orbits(const Tables& t, const std::vector<int>& lg, int b, int* rep, int* gop) {
     const auto& sb = t.stars[b];
-    rep.assign(sb.size(), -1);
-    gop.assign(sb.size(), -1);
     for (size_t j = 0; j < sb.size(); ++j) {
+        rep[j] = -1;
+        gop[j] = -1;
         const int kp = sb[j];
         for (int g : lg) {
             const int x = t.rotk[(size_t)g * t.nk + kp];
@@ -218,7 +224,7 @@ static void little_orbits(const Tables& t, const std::vector<int>& lg, int b, st
 // of them, are counted and then written by the host thread pool, tile by
 // tile, at offsets from a prefix sum, in the same order as a sequential loop.
 int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t budget, std::vector<Batch>& out,
-                 bool seeds = false) {
+                 bool seeds = false, bool host_rots = true) {
     out.clear();
     std::vector<int> inv(t.nops, -1);
     for (int a = 0; a < t.nops; ++a)
@@ -246,8 +252,9 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
         int a, b, batch;
         int64_t xoff, rows;
         int64_t seeds = 0, pairs = 0, task_off = 0, rot_off = 0;
-        std::vector<int> rep, gop;
+        int64_t rep_off = 0;   // its members' entries in rep / gop
     };
+    std::vector<int> rep, gop;   // little-orbit representative of each member of star b, and the operation
     std::vector<Tile> tiles;
     std::vector<std::vector<TileTask>> per(nt);
     Batch cur;
@@ -315,7 +322,12 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
             tl.rows = rows;
             const int64_t na = (int64_t)t.stars[a].size(), nbm = (int64_t)t.stars[b].size();
             tl.pairs = a == b ? na * (na + 1) / 2 : na * nbm;
-            tiles.push_back(std::move(tl));
+            tl.rep_off = (int64_t)rep.size();
+            if (seeds) {
+                rep.resize(rep.size() + nbm);
+                gop.resize(gop.size() + nbm);
+            }
+            tiles.push_back(tl);
             cur.xbytes += xs;
             any = true;
         }
@@ -323,18 +335,16 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
     // k pairs: seeds per tile (the members of star b that are their own
     // little-orbit representative, paired with k0), offsets, then the lists
     const int ntl = (int)tiles.size();
-    std::vector<double> cost(ntl);
-    for (int q = 0; q < ntl; ++q) cost[q] = (double)tiles[q].pairs;
-    host_parallel_for(ntl, [&](int q) {
-        Tile& tl = tiles[q];
+    for (Tile& tl : tiles) {   // small: |star b| x |little group| per tile
         if (seeds) {
-            little_orbits(t, lg[tl.a], tl.b, tl.rep, tl.gop);
+            int* rp = rep.data() + tl.rep_off;
+            little_orbits(t, lg[tl.a], tl.b, rp, gop.data() + tl.rep_off);
             const auto& sb = t.stars[tl.b];
-            for (size_t j = 0; j < sb.size(); ++j) tl.seeds += tl.rep[j] == sb[j];
+            for (size_t j = 0; j < sb.size(); ++j) tl.seeds += rp[j] == sb[j];
         } else {
             tl.seeds = tl.pairs;
         }
-    }, &cost);
+    }
     {
         std::vector<int64_t> nt_task(out.size(), 0), nt_rot(out.size(), 0);
         for (Tile& tl : tiles) {
@@ -345,11 +355,46 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
         }
         for (size_t q = 0; q < out.size(); ++q) {
             out[q].tasks.resize((size_t)nt_task[q]);
-            out[q].rots.resize((size_t)nt_rot[q]);
+            out[q].nrots = nt_rot[q];
+            if (host_rots || !seeds) out[q].rots.resize((size_t)nt_rot[q]);
         }
     }
+    const bool dev_rots = seeds && !host_rots;
+    if (dev_rots)   // the device enumerates the rotated pairs: tile records and per-member arrays
+        for (size_t q = 0; q < out.size(); ++q) {
+            Batch& bt = out[q];
+            std::vector<int> jr, go, pre;
+            for (const Tile& tl : tiles) {
+                if (tl.batch != (int)q || tl.pairs == tl.seeds) continue;
+                const auto& sb = t.stars[tl.b];
+                const int* rp = rep.data() + tl.rep_off;
+                const int* gp = gop.data() + tl.rep_off;
+                RotTile rt;
+                rt.xoff = tl.xoff;
+                rt.pair_off = bt.npairs;
+                rt.rot_off = tl.rot_off;
+                rt.rows = (int32_t)tl.rows;
+                rt.a = tl.a;
+                rt.b = tl.b;
+                rt.tri = tl.a == tl.b;
+                rt.seeds = (int32_t)tl.seeds;
+                rt.rep_off = (int32_t)jr.size();
+                int before = 0;
+                for (size_t j = 0; j < sb.size(); ++j) {
+                    jr.push_back(t.pos_in_star[rp[j]]);
+                    go.push_back(gp[j]);
+                    pre.push_back(before);
+                    before += rp[j] == sb[j];
+                }
+                bt.rtiles.push_back(rt);
+                bt.npairs += tl.pairs;
+            }
+            bt.rmeta = jr;
+            bt.rmeta.insert(bt.rmeta.end(), go.begin(), go.end());
+            bt.rmeta.insert(bt.rmeta.end(), pre.begin(), pre.end());
+        }
     std::vector<char> bad(ntl, 0);
-    host_parallel_for(ntl, [&](int q) {
+    auto fill = [&](int q) {
         const Tile& tl = tiles[q];
         Batch& bt = out[tl.batch];
         const int a = tl.a, b = tl.b;
@@ -358,16 +403,37 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
         const auto& sb = t.stars[b];
         const int k0 = sa[0];
         PairTask* pt = bt.tasks.data() + tl.task_off;
-        RotTask* rt = bt.rots.data() + tl.rot_off;
         int64_t ntask = 0, nrot = 0;
+        const int* rp = seeds ? rep.data() + tl.rep_off : nullptr;
+        const int* gp = seeds ? gop.data() + tl.rep_off : nullptr;
+        if (dev_rots) {   // seeds only: (k0, k'_j) for j its own little-orbit representative
+            for (size_t j = 0; j < sb.size(); ++j) {
+                if (rp[j] != sb[j]) continue;
+                if (ntask >= tl.seeds) {
+                    bad[q] = 2;
+                    return;
+                }
+                PairTask& p = pt[ntask++];
+                p.k = k0;
+                p.kp = sb[j];
+                p.row0 = 0;
+                p.col0 = (int32_t)(j * B);
+                p.xoff = xoff;
+                p.ld = (int32_t)rows;
+                p.flags = (a == b && j > 0) ? 1 : 0;
+            }
+            if (ntask != tl.seeds) bad[q] = 2;
+            return;
+        }
+        RotTask* rt = bt.rots.data() + tl.rot_off;
         for (size_t i = 0; i < sa.size(); ++i)
             for (size_t j = (a == b ? i : 0); j < sb.size(); ++j) {
                 if (seeds) {
                     const int k = sa[i], kp = sb[j];
                     const int s1 = inv[t.s_k[k]];   // takes k to k0
                     const int jpp = t.pos_in_star[t.rotk[(size_t)s1 * t.nk + kp]];
-                    const int r = tl.rep[jpp];
-                    const int s = t.mult[(size_t)tl.gop[jpp] * t.nops + s1];
+                    const int r = rp[jpp];
+                    const int s = t.mult[(size_t)gp[jpp] * t.nops + s1];
                     if (t.rotk[(size_t)s * t.nk + k] != k0 || t.rotk[(size_t)s * t.nk + kp] != r) {
                         bad[q] = 1;
                         return;
@@ -405,7 +471,14 @@ int plan_batches(const Tables& t, const std::vector<const Basis*>& bases, size_t
                 p.flags = (a == b && j > i) ? 1 : 0;
             }
         if (ntask != tl.seeds || nrot != tl.pairs - tl.seeds) bad[q] = 2;
-    }, &cost);
+    };
+    if (dev_rots) {
+        for (int q = 0; q < ntl; ++q) fill(q);
+    } else {   // every k pair on the host: the host thread pool, largest tiles first
+        std::vector<double> cost(ntl);
+        for (int q = 0; q < ntl; ++q) cost[q] = (double)tiles[q].pairs;
+        host_parallel_for(ntl, fill, &cost);
+    }
     for (int q = 0; q < ntl; ++q) {
         if (bad[q] == 1) return fail(BSE_ESYMM, "seed of a k pair of star pair (%d, %d) not found", tiles[q].a, tiles[q].b);
         if (bad[q] == 2)
@@ -919,7 +992,7 @@ static void free_ctx(bse_ctx* c) {
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
-                      &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots,
+                      &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots, &c->rtiles, &c->rmeta, &c->rtab_buf,
                       &c->lossScratch, &c->wsym, &c->wdivDev, &c->lzScratch})
         release(*b);
     for (auto& d : c->irr) {
@@ -1113,6 +1186,47 @@ static void tc_group_tasks(const Tables& t, const std::vector<PairTask>& in, int
 // One build of several blocks (whole irrep blocks or partner blocks): the
 // direct term of every star pair runs once per batch and each target projects
 // the same X tiles with its own basis (Eqs. transformationU, Hblock).
+// device copies of the tables the enumeration of rotated k pairs reads
+static int ensure_rot_tables(bse_ctx* c) {
+    if (c->rtab_ready) return BSE_OK;
+    const Tables& t = c->t;
+    std::vector<int> inv(t.nops, -1);
+    for (int a = 0; a < t.nops; ++a)
+        for (int b = 0; b < t.nops; ++b)
+            if (t.mult[(size_t)a * t.nops + b] == t.identity) inv[a] = b;
+    std::vector<int> all(t.mult.begin(), t.mult.end());
+    const size_t o_inv = all.size();
+    all.insert(all.end(), inv.begin(), inv.end());
+    const size_t o_sk = all.size();
+    all.insert(all.end(), t.s_k.begin(), t.s_k.end());
+    const size_t o_pos = all.size();
+    all.insert(all.end(), t.pos_in_star.begin(), t.pos_in_star.end());
+    const size_t o_off = all.size();
+    int run = 0;
+    for (const auto& st : t.stars) {
+        all.push_back(run);
+        run += (int)st.size();
+    }
+    all.push_back(run);
+    const size_t o_k = all.size();
+    for (const auto& st : t.stars) all.insert(all.end(), st.begin(), st.end());
+    BSE_TRY(upload(c->rtab_buf, all.data(), all.size(), c->stream));
+    const int* b = (const int*)c->rtab_buf.p;
+    c->rtab.rotk = (const int*)c->rotk.p;
+    c->rtab.mult = b;
+    c->rtab.inv = b + o_inv;
+    c->rtab.s_k = b + o_sk;
+    c->rtab.pos_in_star = b + o_pos;
+    c->rtab.star_off = b + o_off;
+    c->rtab.star_k = b + o_k;
+    c->rtab.nops = t.nops;
+    c->rtab.nk = t.nk;
+    c->rtab.B = t.B;
+    BSE_CUDA(cudaStreamSynchronize(c->stream));   // the host vector goes out of scope
+    c->rtab_ready = true;
+    return BSE_OK;
+}
+
 static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t prec, uint32_t terms,
                        void* const* h, const int64_t* ld) {
     const int tcp = prec == BSE_BF16_SPLIT || prec == BSE_FP16_SPLIT;
@@ -1154,14 +1268,16 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         }
     }
     if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
-    if (tcp && (terms & BSE_TERM_DIRECT)) {
-        BSE_TRY(ensure_wemb(c, ngp, fp16));
+    const bool dev_rots = c->seeds && (terms & BSE_TERM_DIRECT);   // rotated pairs enumerated on the device
+    if (tcp && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_wemb(c, ngp, fp16));
+    if ((tcp && (terms & BSE_TERM_DIRECT)) || dev_rots) {
         BSE_TRY(ensure(c->status, sizeof(int)));
         BSE_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
     }
+    if (dev_rots) BSE_TRY(ensure_rot_tables(c));
     const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
     std::vector<Batch> batches;
-    BSE_TRY(plan_batches(t, bases, arena_budget(), batches, c->seeds && (terms & BSE_TERM_DIRECT)));
+    BSE_TRY(plan_batches(t, bases, arena_budget(), batches, dev_rots, false));
     if (c->timing) {
         c->stats.ms_direct = c->stats.ms_project = c->stats.ms_rotate = 0.f;
         c->stats.direct_launches = 0;
@@ -1181,6 +1297,12 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
         }
         BSE_TRY(upload(c->tiles, bt.tiles.data(), bt.tiles.size(), c->stream));
+        if ((terms & BSE_TERM_DIRECT) && bt.nrots > 0) {
+            // before any launch of the batch: a pageable copy waits for the stream to drain
+            BSE_TRY(upload(c->rtiles, bt.rtiles.data(), bt.rtiles.size(), c->stream));
+            BSE_TRY(upload(c->rmeta, bt.rmeta.data(), bt.rmeta.size(), c->stream));
+            BSE_TRY(ensure(c->rots, sizeof(RotTask) * (size_t)bt.nrots));
+        }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
         if ((terms & BSE_TERM_DIRECT) && tcp) {
             BSE_TRY(launch_direct_tc(c->S, fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ngp,
@@ -1193,10 +1315,13 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             BSE_CUDA(cudaMemsetAsync(c->arenaX.p, 0, bt.xbytes / sizeof(double2) * xel, c->stream));
         }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[8], c->stream));
-        if ((terms & BSE_TERM_DIRECT) && !bt.rots.empty()) {   // the other pairs from their seeds (Eq. Wtrafo)
-            BSE_TRY(upload(c->rots, bt.rots.data(), bt.rots.size(), c->stream));
-            BSE_TRY(launch_rotate(rot_sys(c, p32), p32, (const RotTask*)c->rots.p, (int64_t)bt.rots.size(),
-                                  c->arenaX.p, c->stream));
+        if ((terms & BSE_TERM_DIRECT) && bt.nrots > 0) {   // the other pairs from their seeds (Eq. Wtrafo)
+            const int* jr = (const int*)c->rmeta.p;
+            const size_t nm = bt.rmeta.size() / 3;
+            BSE_TRY(launch_rot_tasks(c->rtab, (const RotTile*)c->rtiles.p, (int)bt.rtiles.size(), bt.npairs, jr,
+                                     jr + nm, jr + 2 * nm, (RotTask*)c->rots.p, (int*)c->status.p, c->stream));
+            BSE_TRY(launch_rotate(rot_sys(c, p32), p32, (const RotTask*)c->rots.p, bt.nrots, c->arenaX.p,
+                                  c->stream));
         }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[1], c->stream));
         for (size_t i = 0; i < nt; ++i) {
@@ -1224,11 +1349,12 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             c->stats.direct_launches += 1;
         }
     }
-    if (tcp && (terms & BSE_TERM_DIRECT)) {
+    if ((tcp && (terms & BSE_TERM_DIRECT)) || dev_rots) {
         int st = 0;
         BSE_CUDA(cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         BSE_CUDA(cudaStreamSynchronize(c->stream));
-        if (st) return fail(BSE_ETIMEOUT, "a bounded wait of the tensor-core direct kernel gave up");
+        if (st & 2) return fail(BSE_ESYMM, "the seed of a rotated k pair was not found");
+        if (st & 1) return fail(BSE_ETIMEOUT, "a bounded wait of the tensor-core direct kernel gave up");
     }
     return BSE_OK;
 }

@@ -206,6 +206,39 @@ struct RotTask {
     int32_t pad;
 };
 int launch_rotate(const RotSys& one, int prec32, const RotTask* tasks, int64_t n, void* X, cudaStream_t st);
+
+// A star-pair tile whose rotated k pairs the device enumerates (Eq. Wtrafo):
+// its pairs (i, j) (members i of star a, j of star b; j >= i when a == b)
+// are numbered row by row from pair_off; the seeds are the pairs (0, j) with
+// j its own little-orbit representative, every other pair is written as a
+// RotTask at rot_off + (its number in the tile - the seeds before it).
+struct RotTile {
+    int64_t xoff;       // tile origin in the arena (elements)
+    int64_t pair_off;   // number of the tile's first pair in the batch
+    int64_t rot_off;    // index of its first rotated pair in the RotTask list
+    int32_t rows;       // tile rows (= leading dimension) = |star a| x B
+    int32_t a, b;       // stars
+    int32_t tri;        // a == b
+    int32_t seeds;      // seeds of the tile
+    int32_t rep_off;    // offset of the tile's per-member arrays of star b
+};
+// device copies of the group and star tables the enumeration reads
+struct RotTables {
+    const int* rotk;          // [nops][nk] index of s k
+    const int* mult;          // [nops][nops] index of s1 s2
+    const int* inv;           // [nops]
+    const int* s_k;           // [nk] operation taking the representative of k's star to k
+    const int* pos_in_star;   // [nk]
+    const int* star_k;        // members of all stars, star by star
+    const int* star_off;      // [nstars + 1]
+    int nops, nk, B;
+};
+// jr[rep_off + j]: position in star b of the little-orbit representative of
+// member j; gop[rep_off + j]: the little-group operation taking j to it;
+// seedpre[rep_off + j]: seeds (0, j') with j' < j.  An inconsistent table
+// sets bit 1 of *status (the tile's tasks are then incomplete).
+int launch_rot_tasks(const RotTables& g, const RotTile* tiles, int ntiles, int64_t npairs, const int* jr,
+                     const int* gop, const int* seedpre, RotTask* out, int* status, cudaStream_t st);
 int launch_rotate_multi(const RotSys* systems, int bmax, int prec32, const RotTask* tasks, int64_t n, void* X,
                         cudaStream_t st);
 // dynamic shared memory of the direct kernel for a system

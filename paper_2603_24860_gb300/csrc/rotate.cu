@@ -133,6 +133,80 @@ int launch_rotate_t(const RotSys* systems, const RotSys& one, int B, const RotTa
 
 }  // namespace
 
+namespace {
+
+__global__ void rot_tasks_kernel(RotTables g, const RotTile* __restrict__ tiles, int ntiles, int64_t npairs,
+                                 const int* __restrict__ jr_of, const int* __restrict__ gop_of,
+                                 const int* __restrict__ seedpre, RotTask* out, int* status) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    int lo = 0, hi = ntiles - 1;   // the tile of pair p: last one starting at or before p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tiles[mid].pair_off <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    const RotTile T = tiles[lo];
+    const int na = g.star_off[T.a + 1] - g.star_off[T.a], nb = g.star_off[T.b + 1] - g.star_off[T.b];
+    const int64_t q = p - T.pair_off;
+    int i, j;
+    if (T.tri) {   // row i holds j = i .. nb-1
+        int64_t r = q;
+        int len = nb;
+        i = 0;
+        while (r >= len && i + 1 < na) {
+            r -= len;
+            ++i;
+            --len;
+        }
+        j = i + (int)r;
+    } else {
+        i = (int)(q / nb);
+        j = (int)(q % nb);
+    }
+    if (i >= na || j >= nb) {
+        atomicOr(status, 2);
+        return;
+    }
+    const int k = g.star_k[g.star_off[T.a] + i], kp = g.star_k[g.star_off[T.b] + j];
+    const int k0 = g.star_k[g.star_off[T.a]];
+    const int s1 = g.inv[g.s_k[k]];   // takes k to k0
+    const int jpp = g.pos_in_star[g.rotk[(int64_t)s1 * g.nk + kp]];
+    const int jr = jr_of[T.rep_off + jpp];
+    const int s = g.mult[gop_of[T.rep_off + jpp] * g.nops + s1];
+    const int r = g.star_k[g.star_off[T.b] + jr];
+    if (g.rotk[(int64_t)s * g.nk + k] != k0 || g.rotk[(int64_t)s * g.nk + kp] != r) {
+        atomicOr(status, 2);
+        return;
+    }
+    if (i == 0 && j == jr) return;   // a seed: computed by the direct kernel
+    const int64_t ridx = i == 0 ? q - seedpre[T.rep_off + j] : q - T.seeds;
+    const int64_t B = g.B, rows = T.rows;
+    RotTask o;
+    o.src = T.xoff + (int64_t)jr * B * rows;
+    o.dst = T.xoff + (int64_t)j * B * rows + (int64_t)i * B;
+    o.dstm = T.xoff + (int64_t)i * B * rows + (int64_t)j * B;
+    o.k = k;
+    o.kp = kp;
+    o.s = s;
+    o.ld = T.rows;
+    o.flags = (T.tri && j > i) ? 1 : 0;
+    o.pad = 0;
+    out[T.rot_off + ridx] = o;
+}
+
+}  // namespace
+
+int launch_rot_tasks(const RotTables& g, const RotTile* tiles, int ntiles, int64_t npairs, const int* jr,
+                     const int* gop, const int* seedpre, RotTask* out, int* status, cudaStream_t st) {
+    if (npairs == 0 || ntiles == 0) return BSE_OK;
+    rot_tasks_kernel<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(g, tiles, ntiles, npairs, jr, gop, seedpre,
+                                                                         out, status);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
 int launch_rotate(const RotSys& one, int prec32, const RotTask* tasks, int64_t n, void* X, cudaStream_t st) {
     return prec32 ? launch_rotate_t<float, false>(nullptr, one, one.nv * one.nc, tasks, n, X, st)
                   : launch_rotate_t<double, false>(nullptr, one, one.nv * one.nc, tasks, n, X, st);
