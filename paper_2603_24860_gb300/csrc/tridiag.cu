@@ -563,70 +563,77 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __
 // zero for levels of rows [m, n).  With z_r = 1, z_i = -L+_i z_{i+1} above r
 // and z_{i+1} = -U-_i z_i below it, so
 //   z_0^2 = prod_{i<r} L+_i^2,  sum_{i<r} z_i^2 = h_r,  sum_{i>r} z_i^2 = t_r
-// with h_{i+1} = L+_i^2 (1 + h_i) and t_i = U-_i^2 (1 + t_{i+1}).
-// A block of two warps takes 32 levels: warp 0 runs the top-down pass, warp
-// 1 the bottom-up pass at the same time (each FP64 instruction of a warp
-// costs the same whatever its active lanes, so the passes are split across
-// warps, not lanes); both then scan half of the twist indices.
-// st: scratch of 5 [m][n] arrays (level index fastest).
-__global__ void __launch_bounds__(64) twisted_weights_kernel(const double* __restrict__ d, const double* __restrict__ e,
-                                                             int64_t n, const TriBounds* __restrict__ bnd,
-                                                             const double* __restrict__ lam, double* st, double* w) {
-    __shared__ unsigned long long s_best[2][32];
+// with L+_i^2 = e_i^2 / (D+_i)^2, h_{i+1} = L+_i^2 (1 + h_i),
+// U-_i^2 = e_i^2 / (D-_{i+1})^2 and t_i = U-_i^2 (1 + t_{i+1}).
+// A block of two warps takes 32 levels (one per lane).  The pivots D+ (warp
+// 0, top-down) and D- (warp 1, bottom-up) follow the ratio recurrences
+// D_next = (d - lam) - e^2 / D in double-float on the FP32 pipe and are
+// stored; both warps then scan half of the twist indices; last, warp 0
+// forms z_0^2 and h_r from the stored D+ above r and warp 1 t_r from the D-
+// below it, in FP64 (these products can leave FP32's range), with the
+// factors e^2 / D^2 formed in double-float unless |D| < 2^-50.
+// st: scratch of 2 [m][n] double-float arrays (level index fastest).
+__device__ __forceinline__ float2 twist_clamp(float2 p, float piv) {
+    return fabsf(p.x) < piv ? make_float2(-piv, 0.f) : p;
+}
+// e^2 / D^2 as a double (D clamped, nonzero)
+__device__ __forceinline__ double twist_factor(float2 e2, float2 D, double e2d) {
+    if (fabsf(D.x) >= 0x1p-50f) {
+        const float2 r = df_rcp(D);
+        return df_to(df_mul(e2, df_mul(r, r)));
+    }
+    const double Dd = df_to(D);
+    return e2d / (Dd * Dd);
+}
+__global__ void __launch_bounds__(64) twisted_weights_kernel(const float2* __restrict__ d_df,
+                                                             const float2* __restrict__ e2_df,
+                                                             const double* __restrict__ e2d, int64_t n,
+                                                             const TriBounds* __restrict__ bnd,
+                                                             const double* __restrict__ lam, float2* st, double* w) {
+    __shared__ float s_best[2][32];
     __shared__ int s_r[2][32];
+    __shared__ double s_t[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t k0 = (int64_t)blockIdx.x * 32 + lane;
     const TriBounds b = *bnd;
     const int m = b.m;
     const bool act = k0 < m;
     const int64_t k = act ? k0 : 0;
-    const double l = lam[k], piv = b.pivmin;
-    double* Dp = st;
-    double* Ph = st + (size_t)n * n;
-    double* Hh = st + 2 * (size_t)n * n;
-    double* Dm = st + 3 * (size_t)n * n;
-    double* Tt = st + 4 * (size_t)n * n;
+    const float2 nl = df_neg(df_from(lam[k]));
+    const float piv = b.pivmin32;
+    float2* Dp = st;
+    float2* Dm = st + (size_t)n * n;
     if (act) {
-        if (wid == 0) {   // top-down: D+_i, and P_i, h_i before row i
-            double p = __ldg(d) - l, P = 1.0, h = 0.0;
+        if (wid == 0) {   // top-down: D+_i (clamped)
+            float2 p = twist_clamp(df_add(__ldg(d_df), nl), piv);
             for (int i = 0; i + 1 < m; ++i) {
-                if (fabs(p) < piv) p = -piv;
                 Dp[(size_t)i * n + k] = p;
-                Ph[(size_t)i * n + k] = P;
-                Hh[(size_t)i * n + k] = h;
-                const double L = __ldg(e + i) * rcp_nr(p);
-                const double L2 = L * L;
-                p = fma(-__ldg(e + i), L, __ldg(d + i + 1) - l);
-                P *= L2;
-                h = fma(L2, h, L2);
+                const float2 t = df_mul(__ldg(e2_df + i), df_rcp(p));
+                const float2 dx = df_add(__ldg(d_df + i + 1), nl);
+                p = twist_clamp(fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f), piv);
             }
-            if (fabs(p) < piv) p = -piv;
             Dp[(size_t)(m - 1) * n + k] = p;
-            Ph[(size_t)(m - 1) * n + k] = P;
-            Hh[(size_t)(m - 1) * n + k] = h;
-        } else {          // bottom-up: D-_i and t_i
-            double q = __ldg(d + m - 1) - l, t = 0.0;
+        } else {          // bottom-up: D-_i (as computed, clamped where used)
+            float2 q = df_add(__ldg(d_df + m - 1), nl);
             Dm[(size_t)(m - 1) * n + k] = q;
-            Tt[(size_t)(m - 1) * n + k] = 0.0;
             for (int i = m - 2; i >= 0; --i) {
-                if (fabs(q) < piv) q = -piv;
-                const double u = __ldg(e + i) * rcp_nr(q);
-                q = fma(-u, __ldg(e + i), __ldg(d + i) - l);
-                t = u * u * (1.0 + t);
+                const float2 t = df_mul(__ldg(e2_df + i), df_rcp(twist_clamp(q, piv)));
+                const float2 dx = df_add(__ldg(d_df + i), nl);
+                q = fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f);
                 Dm[(size_t)i * n + k] = q;
-                Tt[(size_t)i * n + k] = t;
             }
         }
     }
     __syncthreads();
     // twist index: smallest |gamma_i| over this warp's half (ties: lowest i)
-    unsigned long long best = ~0ull;
+    float best = INFINITY;
     int rb = 0;
     if (act) {
         const int h0 = wid == 0 ? 0 : m / 2, h1 = wid == 0 ? m / 2 : m;
         for (int i = h0; i < h1; ++i) {
-            const double g = Dp[(size_t)i * n + k] + Dm[(size_t)i * n + k] - (__ldg(d + i) - l);
-            const unsigned long long ga = (unsigned long long)__double_as_longlong(g) & 0x7fffffffffffffffull;
+            const float2 g = df_add(df_add(Dp[(size_t)i * n + k], Dm[(size_t)i * n + k]),
+                                    df_neg(df_add(__ldg(d_df + i), nl)));
+            const float ga = fabsf(g.x);
             if (ga < best) {
                 best = ga;
                 rb = i;
@@ -636,10 +643,27 @@ __global__ void __launch_bounds__(64) twisted_weights_kernel(const double* __res
     s_best[wid][lane] = best;
     s_r[wid][lane] = rb;
     __syncthreads();
+    const int r = s_best[1][lane] < s_best[0][lane] ? s_r[1][lane] : s_r[0][lane];
+    double P = 1.0, h = 0.0, t = 0.0;
+    if (act) {
+        if (wid == 0) {
+            for (int i = 0; i < r; ++i) {
+                const double L2 = twist_factor(__ldg(e2_df + i), Dp[(size_t)i * n + k], __ldg(e2d + i));
+                P *= L2;
+                h = fma(L2, h, L2);
+            }
+        } else {
+            for (int i = m - 2; i >= r; --i) {
+                const double U2 = twist_factor(__ldg(e2_df + i), twist_clamp(Dm[(size_t)(i + 1) * n + k], piv),
+                                               __ldg(e2d + i));
+                t = U2 * (1.0 + t);
+            }
+            s_t[lane] = t;
+        }
+    }
+    __syncthreads();
     if (wid == 0 && act) {
-        const int r = s_best[1][lane] < s_best[0][lane] ? s_r[1][lane] : s_r[0][lane];
-        const double P = Ph[(size_t)r * n + k], h = Hh[(size_t)r * n + k], t = Tt[(size_t)r * n + k];
-        w[k] = P * rcp_nr(1.0 + h + t);
+        w[k] = P * rcp_nr(1.0 + h + s_t[lane]);
     } else if (wid == 0 && k0 < n) {
         w[k0] = 0.0;
     }
@@ -680,8 +704,9 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 size_t tridiag_scratch_bytes(int64_t n) {
     // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (16 bytes each); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
     // d_df, e2_df (n float2);
-    // twisted passes 5 n*n doubles; 256-byte alignment of each piece
-    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n + 5 * n * n) +
+    // twisted pivots 2 n*n float2; 256-byte alignment of each piece
+    return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n) +
+           sizeof(float2) * (size_t)(2 * n * n) +
            sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) + 8192;
 }
 
@@ -722,7 +747,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     double* beta0 = (double*)take(sizeof(double));
     TriBounds* bnd = (TriBounds*)take(sizeof(TriBounds));
     unsigned* bar = (unsigned*)take(sizeof(unsigned));
-    double* dp = (double*)take(sizeof(double) * 5 * n * n);
+    float2* dp = (float2*)take(sizeof(float2) * 2 * n * n);
 
     int dev = 0, sms = 0, maxsm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
@@ -775,7 +800,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
         d_df, e2_df, d32, e2_32, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d, e, n, bnd, lam, dp, w);
+    twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d_df, e2_df, e2, n, bnd, lam, dp, w);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     rank_levels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lam, w, n, scale, omega_out, osc);
