@@ -155,20 +155,43 @@ int build_mesh(Tables& t) {
     long Nl = std::lcm(std::lcm((long)n1, (long)n2), (long)n3);
     long step[3] = {Nl / n1, Nl / n2, Nl / n3};
     t.rotk.assign((size_t)t.nops * t.nk, -1);
-    for (int s = 0; s < t.nops; ++s)
+    // k = sum_j x_j b_j / n_j goes to s k with mesh coordinates (M x) mod n,
+    // M_ij = rk_ij n_i / n_j: integral exactly when the mesh is invariant (a
+    // column j with n_j = 1 never contributes).  Per operation, tables of
+    // (M_ij x) mod n_i replace the integer divisions of a direct evaluation.
+    const int nmax = std::max(n1, std::max(n2, n3));
+    std::vector<int> tab((size_t)9 * nmax);
+    for (int s = 0; s < t.nops; ++s) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                long Mij = 0;
+                if (t.n[j] > 1) {
+                    const long num = (long)t.rk[9 * s + 3 * i + j] * step[j];
+                    if (num % step[i] != 0) return fail(BSE_EINVAL, "mesh not invariant under operation %d", s);
+                    Mij = num / step[i];
+                }
+                int* tb = &tab[(size_t)(3 * i + j) * nmax];
+                const long mi = ((Mij % t.n[i]) + t.n[i]) % t.n[i];
+                long v = 0;
+                for (int x = 0; x < t.n[j]; ++x) {
+                    tb[x] = (int)v;
+                    v += mi;
+                    if (v >= t.n[i]) v -= t.n[i];
+                }
+            }
+        int32_t* out = &t.rotk[(size_t)s * t.nk];
         for (int k = 0; k < t.nk; ++k) {
-            long X[3], Y[3];
-            for (int i = 0; i < 3; ++i) X[i] = t.kidx[3 * k + i] * step[i];
+            const int* x = &t.kidx[3 * k];
             int id[3];
             for (int i = 0; i < 3; ++i) {
-                Y[i] = 0;
-                for (int j = 0; j < 3; ++j) Y[i] += (long)t.rk[9 * s + 3 * i + j] * X[j];
-                if (Y[i] % step[i] != 0) return fail(BSE_EINVAL, "mesh not invariant under operation %d", s);
-                long v = Y[i] / step[i];
-                id[i] = (int)(((v % t.n[i]) + t.n[i]) % t.n[i]);
+                int v = tab[(size_t)(3 * i) * nmax + x[0]] + tab[(size_t)(3 * i + 1) * nmax + x[1]] +
+                        tab[(size_t)(3 * i + 2) * nmax + x[2]];
+                while (v >= t.n[i]) v -= t.n[i];
+                id[i] = v;
             }
-            t.rotk[(size_t)s * t.nk + k] = (id[0] * n2 + id[1]) * n3 + id[2];
+            out[k] = (id[0] * n2 + id[1]) * n3 + id[2];
         }
+    }
     t.star_of.assign(t.nk, -1);
     t.star_rep.clear();
     t.stars.clear();

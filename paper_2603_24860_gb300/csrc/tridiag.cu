@@ -479,8 +479,15 @@ __device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const 
     float q = __ldg(d + i0) - x;
     if (fabsf(q) < pivmin) q = -pivmin;
     int c = q < 0.f;
+    // the next row's operands are loaded a row ahead, off the recurrence's chain
+    float dn = i0 + 1 < i1 ? __ldg(d + i0 + 1) : 0.f, en = i0 + 1 < i1 ? __ldg(e2 + i0) : 0.f;
     for (int i = i0 + 1; i < i1; ++i) {
-        q = (__ldg(d + i) - x) - __ldg(e2 + i - 1) / q;
+        const float di = dn, ei = en;
+        if (i + 1 < i1) {
+            dn = __ldg(d + i + 1);
+            en = __ldg(e2 + i);
+        }
+        q = (di - x) - ei / q;
         if (fabsf(q) < pivmin) q = -pivmin;
         c += q < 0.f;
     }
@@ -498,9 +505,16 @@ __device__ __forceinline__ int sturm_count_df(const float2* __restrict__ d, cons
     float2 q = df_add(__ldg(d + i0), nx);
     if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
     int c = q.x < 0.f;
+    const float2 z = make_float2(0.f, 0.f);
+    float2 dn = i0 + 1 < i1 ? __ldg(d + i0 + 1) : z, en = i0 + 1 < i1 ? __ldg(e2 + i0) : z;
     for (int i = i0 + 1; i < i1; ++i) {
-        const float2 dx = df_add(__ldg(d + i), nx);
-        const float2 t = df_mul(__ldg(e2 + i - 1), df_rcp(q));
+        const float2 di = dn, ei = en;
+        if (i + 1 < i1) {
+            dn = __ldg(d + i + 1);
+            en = __ldg(e2 + i);
+        }
+        const float2 dx = df_add(di, nx);
+        const float2 t = df_mul(ei, df_rcp(q));
         q = fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f);
         if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
         c += q.x < 0.f;
@@ -606,19 +620,31 @@ __global__ void __launch_bounds__(64) twisted_weights_kernel(const float2* __res
     if (act) {
         if (wid == 0) {   // top-down: D+_i (clamped)
             float2 p = twist_clamp(df_add(__ldg(d_df), nl), piv);
+            float2 en = m > 1 ? __ldg(e2_df) : make_float2(0.f, 0.f), dn = m > 1 ? __ldg(d_df + 1) : en;
             for (int i = 0; i + 1 < m; ++i) {
+                const float2 ei = en, di = dn;   // operands of this row, the next row's loaded ahead
+                if (i + 2 < m) {
+                    en = __ldg(e2_df + i + 1);
+                    dn = __ldg(d_df + i + 2);
+                }
                 Dp[(size_t)i * n + k] = p;
-                const float2 t = df_mul(__ldg(e2_df + i), df_rcp(p));
-                const float2 dx = df_add(__ldg(d_df + i + 1), nl);
+                const float2 t = df_mul(ei, df_rcp(p));
+                const float2 dx = df_add(di, nl);
                 p = twist_clamp(fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f), piv);
             }
             Dp[(size_t)(m - 1) * n + k] = p;
         } else {          // bottom-up: D-_i (as computed, clamped where used)
             float2 q = df_add(__ldg(d_df + m - 1), nl);
             Dm[(size_t)(m - 1) * n + k] = q;
+            float2 en = m > 1 ? __ldg(e2_df + m - 2) : make_float2(0.f, 0.f), dn = m > 1 ? __ldg(d_df + m - 2) : en;
             for (int i = m - 2; i >= 0; --i) {
-                const float2 t = df_mul(__ldg(e2_df + i), df_rcp(twist_clamp(q, piv)));
-                const float2 dx = df_add(__ldg(d_df + i), nl);
+                const float2 ei = en, di = dn;
+                if (i > 0) {
+                    en = __ldg(e2_df + i - 1);
+                    dn = __ldg(d_df + i - 1);
+                }
+                const float2 t = df_mul(ei, df_rcp(twist_clamp(q, piv)));
+                const float2 dx = df_add(di, nl);
                 q = fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f);
                 Dm[(size_t)i * n + k] = q;
             }
