@@ -494,17 +494,20 @@ __device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const 
     return c;
 }
 
-// The same count in double-float (ratio form, FP32 exponent range, pivots
-// kept at least pivmin in magnitude): exact for a matrix within a few units
-// of 2^-47 of T, on the FP32 pipe.  A quotient e^2/q beyond FP32's range
-// stands for the infinite one of IEEE arithmetic (the next pivot takes its
-// sign, and the quotient after it vanishes).
+// The same count in double-float on the FP32 pipe, from the three-term
+// recurrence of the leading principal minors p_i = det(T[i0..i] - x),
+//   p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}   (Sturm: sign changes count),
+// which needs no division: two double-float multiply-adds per row.  p_i and
+// p_{i-1} are rescaled together by an exact power of two whenever the larger
+// leaves [2^-40, 2^40] (FP32's exponent range); an exact zero p_i becomes
+// -2^-60 p_{i-1}, the tiny negative pivot of the ratio form.
 __device__ __forceinline__ int sturm_count_df(const float2* __restrict__ d, const float2* __restrict__ e2, int i0,
-                                              int i1, float2 x, float pivmin) {
+                                              int i1, float2 x) {
     const float2 nx = df_neg(x);
-    float2 q = df_add(__ldg(d + i0), nx);
-    if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
-    int c = q.x < 0.f;
+    float2 pm = make_float2(1.f, 0.f);
+    float2 p = df_add(__ldg(d + i0), nx);
+    if (p.x == 0.f) p = make_float2(-0x1p-60f, 0.f);
+    int c = p.x < 0.f;
     const float2 z = make_float2(0.f, 0.f);
     float2 dn = i0 + 1 < i1 ? __ldg(d + i0 + 1) : z, en = i0 + 1 < i1 ? __ldg(e2 + i0) : z;
     for (int i = i0 + 1; i < i1; ++i) {
@@ -514,25 +517,37 @@ __device__ __forceinline__ int sturm_count_df(const float2* __restrict__ d, cons
             en = __ldg(e2 + i);
         }
         const float2 dx = df_add(di, nx);
-        const float2 t = df_mul(ei, df_rcp(q));
-        q = fabsf(t.x) < 0x1p120f ? df_add(dx, df_neg(t)) : make_float2(-t.x, 0.f);
-        if (fabsf(q.x) < pivmin) q = make_float2(-pivmin, 0.f);
-        c += q.x < 0.f;
+        float sh = 0.f, sl = 0.f;
+        df_acc(sh, sl, dx.x, dx.y, p.x, p.y);
+        df_acc(sh, sl, -ei.x, -ei.y, pm.x, pm.y);
+        float2 pn = df_fin(sh, sl);
+        if (pn.x == 0.f) pn = make_float2(-p.x * 0x1p-60f, 0.f);
+        c += (pn.x < 0.f) != (p.x < 0.f);
+        pm = p;
+        p = pn;
+        const float big = fmaxf(fabsf(p.x), fabsf(pm.x));
+        if (big > 0x1p40f || big < 0x1p-40f) {
+            const int ex = ((__float_as_int(big) >> 23) & 0xff) - 127;   // big = 1.f x 2^ex
+            const float sc = __int_as_float((127 - ex) << 23);            // 2^-ex, exact
+            p = make_float2(p.x * sc, p.y * sc);
+            pm = make_float2(pm.x * sc, pm.y * sc);
+        }
     }
     return c;
 }
 
-// Sixteen lanes per level: 17-section of the Gershgorin interval with Sturm
-// counts: 6 rounds in FP32 (from 2 ||T|| to about eps_32 ||T||), the bracket
-// widened by the FP32 counts' backward error (16 eps_32 (||T|| + |x|)), then
-// 7 rounds in double-float to about 2e-14 ||T|| (17^7 = 4e8), below the
+// One warp per level: 33-section of the Gershgorin interval with Sturm
+// counts: 4 rounds in FP32 (from 2 ||T|| to below the FP32 counts' backward
+// error), the bracket widened by that error (16 eps_32 (||T|| + |x|)), then
+// 6 rounds in double-float to about 1e-14 ||T|| (33^6 = 1.3e9), below the
 // backward error of the double-float reduction that made T.  Both kinds of
 // count run on the FP32 pipe; the cost is each warp's chain of dependent
 // instructions, so fewer, wider rounds beat narrow bisection.  Every lane
 // runs all rounds (uniform ballots).  Levels k < m belong to rows [0, m),
 // the others to rows [m, n).  Launched as blocks of four warps, one per SM
 // sub-partition.
-constexpr int kSect = 16;
+constexpr int kSect = 32;
+constexpr unsigned kSectMask = kSect == 32 ? 0xffffffffu : ((1u << (kSect & 31)) - 1u);
 constexpr int kBisectThreads = 128;
 __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __restrict__ d_df,
                                                                 const float2* __restrict__ e2_df,
@@ -546,10 +561,10 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __
     const int i0 = k < b.m ? 0 : b.m, i1 = k < b.m ? b.m : (int)n;
     const int kk = (int)(k - i0);
     float lof = (float)b.gl, hif = (float)b.gu;
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 4; ++it) {
         const float x = lof + (hif - lof) * (float)(sub + 1) * (1.0f / (kSect + 1));
         const int c = sturm_count32(d32, e2_32, i0, i1, x, b.pivmin32);
-        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & kSectMask;
         const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
         const float xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
         const float xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
@@ -558,10 +573,10 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __
     }
     const double del = 16.0 * FLT_EPSILON * (b.tnorm + fmax(fabs((double)lof), fabs((double)hif)));
     double lo = fmax(b.gl, (double)lof - del), hi = fmin(b.gu, (double)hif + del);
-    for (int it = 0; it < 7; ++it) {
+    for (int it = 0; it < 6; ++it) {
         const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (kSect + 1));
-        const int c = sturm_count_df(d_df, e2_df, i0, i1, df_from(x), b.pivmin32);
-        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & ((1u << kSect) - 1u);
+        const int c = sturm_count_df(d_df, e2_df, i0, i1, df_from(x));
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & kSectMask;
         const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
         const double xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
         const double xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
