@@ -581,19 +581,31 @@ constexpr int kSpecLanes = 8;
 __global__ void spectrum_kernel(const double* __restrict__ Om, const double* __restrict__ osc, int64_t dim,
                                 const double* __restrict__ omega, int64_t n_omega, double eta, double pref,
                                 double* im) {
+    // the Lorentzian terms in double-float on the FP32 pipe (GB300's FP64
+    // pipe is 64 times narrower); the levels and weights are read in FP64
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t w = g / kSpecLanes;
     const int part = (int)(g % kSpecLanes);
-    const double x = w < n_omega ? omega[w] : 0.0, e2 = eta * eta;
-    double acc = 0.0;
+    const float2 x = df_from(w < n_omega ? omega[w] : 0.0);
+    const float2 e2 = df_from(eta * eta);
+    float sh = 0.f, sl = 0.f;
     if (w < n_omega)
         for (int64_t l = part; l < dim; l += kSpecLanes) {
-            const double d1 = x - Om[l], d2 = x + Om[l];
-            acc = fma(osc[l], eta * (rcp_nr(fma(d1, d1, e2)) - rcp_nr(fma(d2, d2, e2))), acc);
+            const float2 om = df_from(__ldg(Om + l)), ow = df_from(__ldg(osc + l));
+            const float2 d1 = df_add(x, df_neg(om)), d2 = df_add(x, om);
+            float a = e2.x, al = e2.y, b = e2.x, bl = e2.y;
+            df_acc(a, al, d1.x, d1.y, d1.x, d1.y);
+            df_acc(b, bl, d2.x, d2.y, d2.x, d2.y);
+            const float2 r = df_add(df_rcp(df_fin(a, al)), df_neg(df_rcp(df_fin(b, bl))));
+            df_acc(sh, sl, ow.x, ow.y, r.x, r.y);
+            const float2 f = df_fin(sh, sl);
+            sh = f.x;
+            sl = f.y;
         }
+    double acc = (double)sh + (double)sl;
 #pragma unroll
     for (int o = kSpecLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (part == 0 && w < n_omega) im[w] = pref * acc;
+    if (part == 0 && w < n_omega) im[w] = pref * eta * acc;
 }
 
 int launch_spectrum(const double* Om, const double* osc, int64_t dim, const double* omega, int64_t n_omega, double eta,

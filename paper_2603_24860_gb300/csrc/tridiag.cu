@@ -716,11 +716,18 @@ __global__ void rank_levels_kernel(const double* __restrict__ lam, const double*
                                    double scale, double* omega_out, double* osc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    // order-preserving integer keys of the (finite) levels: the comparisons
+    // run on the integer pipe instead of GB300's narrow FP64 pipe
+    auto key = [](double v) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    };
     const double x = lam[k];
+    const unsigned long long kx = key(x);
     int64_t pos = 0;
     for (int64_t j = 0; j < n; ++j) {
-        const double y = __ldg(lam + j);
-        pos += (y < x) || (y == x && j < k);
+        const unsigned long long ky = key(__ldg(lam + j));
+        pos += (ky < kx) || (ky == kx && j < k);
     }
     omega_out[pos] = x;
     osc[pos] = scale * w[k];
