@@ -115,6 +115,7 @@ struct bse_ctx {
     mutable bool wdiv_host_ok = false;
     double spin = 2.0;
     DevBuf P;            // exchange vectors [N][ng0]
+    DevBuf Pt;           // projected exchange vectors scaled by v^1/2, double-float (mixed builds)
     bool P_ready = false;
     DevBuf B;            // dipoles [N]
     bool B_ready = false;
@@ -989,7 +990,7 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
 static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
-                      &c->arenaX, &c->arenaY, &c->Pmu, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
+                      &c->arenaX, &c->arenaY, &c->Pmu, &c->Pt, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
                       &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
                       &c->triScratch, &c->triSmall, &c->dinst,
                       &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots, &c->rtiles, &c->rmeta, &c->rtab_buf,
@@ -1261,6 +1262,11 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             if (db[i].dim > 0)
                 BSE_TRY(launch_exchange_project(db[i], (const double2*)c->P.p, c->ng0,
                                                 (double2*)c->Pmu.p + pmu_off[i], c->stream));
+        if (p32) {   // the mixed builds project the exchange in double-float: v^1/2-scaled copies
+            BSE_TRY(ensure(c->Pt, sizeof(float4) * (size_t)pmu_off[nt]));
+            BSE_TRY(launch_exchange_df((const double2*)c->Pmu.p, (const double*)c->vbar.p, pmu_off[nt] / c->ng0,
+                                       c->ng0, (float4*)c->Pt.p, c->stream));
+        }
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
             BSE_CUDA(cudaEventSynchronize(c->ev[4]));
@@ -1328,13 +1334,15 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             const int n = bt.tile_off[i + 1] - bt.tile_off[i];
             if (n == 0) continue;
             const TileTask* tl = (const TileTask*)c->tiles.p + bt.tile_off[i];
+            // the mixed builds keep Y in double-float between the two stages (same 16 bytes per element)
             BSE_TRY(launch_project_right(db[i], tl, n, p32, c->arenaX.p, (double2*)c->arenaY.p, bt.max_rows[i],
-                                         bt.max_cb[i], c->stream));
+                                         bt.max_cb[i], c->stream, p32));
             BSE_TRY(launch_project_left(db[i], tl, n, (const double2*)c->arenaY.p,
                                         (terms & BSE_TERM_EXCHANGE) ? (const double2*)c->Pmu.p + pmu_off[i] : nullptr,
                                         (const double*)c->vbar.p, c->ng0, c->spin * c->S.inv_vol,
                                         (terms & BSE_TERM_DIAG) ? (const double*)c->de.p : nullptr, (const double*)c->wdivDev.p,
-                                        (double2*)h[i], ld[i], bt.max_ca[i], bt.max_cb[i], c->stream));
+                                        (double2*)h[i], ld[i], bt.max_ca[i], bt.max_cb[i], c->stream, p32,
+                                        (terms & BSE_TERM_EXCHANGE) && p32 ? (const float4*)c->Pt.p + pmu_off[i] : nullptr));
         }
         if (c->timing) {
             BSE_CUDA(cudaEventRecord(c->ev[2], c->stream));

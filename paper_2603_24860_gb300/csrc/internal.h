@@ -246,13 +246,18 @@ size_t direct_smem(const DevSys& s, int prec32);
 int launch_narrow(const double2* in, float2* out, int64_t n, cudaStream_t st);
 // complex double-float copy (real hi, lo, imaginary hi, lo) of n complex doubles
 int launch_to_df(const double2* in, float4* out, int64_t n, cudaStream_t st);
+// x32: FP32 tiles (double-float products); ydf: write Y in double-float (float4) for
+// launch_project_left with ydf
 int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X,
-                         double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st);
+                         double2* Y, int64_t max_rows, int64_t max_cols, cudaStream_t st, int ydf = 0);
 // de: eps_c - eps_v per product index (or null to skip the diagonal); w_div:
 // device pointer to W^div, subtracted on the diagonal with it
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y,
                         const double2* Pmu, const double* vbar, int ng0, double xscale, const double* de,
-                        const double* w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st);
+                        const double* w_div, double2* H, int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st,
+                        int ydf = 0, const float4* Pt = nullptr);
+// Pt[i][g] = sqrt(vbar[g]) Pmu[i][g] in double-float, for launch_project_left with ydf
+int launch_exchange_df(const double2* Pmu, const double* vbar, int64_t n, int ng0, float4* out, cudaStream_t st);
 int launch_diag_full(const double* de, int64_t N, const double* w_div, double2* H, int64_t ld, cudaStream_t st);
 // w = a - b * (*sum), on the stream
 int launch_wdiv_finalize(const double* sum, double a, double b, double* w, cudaStream_t st);

@@ -287,8 +287,16 @@ __global__ void project_right_kernel(DevBasis Bs, const TileTask* __restrict__ t
 // coefficient of U is formed exactly in double-float (TwoProduct) and summed
 // in double-float on the FP32 pipe, whose rate is 64 times the FP64 pipe's;
 // the sum's error (about 2^-47 relative) is far below that of the FP32 tile
+// Y in FP64 (double2) or, for a double-float left projection, in double-float (float4)
+__device__ __forceinline__ void store_y(double2* y, float sr, float lr, float si, float li) {
+    *y = make_double2((double)sr + (double)lr, (double)si + (double)li);
+}
+__device__ __forceinline__ void store_y(float4* y, float sr, float lr, float si, float li) {
+    *y = make_float4(sr, lr, si, li);
+}
+template <typename YT>
 __global__ void project_right_df_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const float2* __restrict__ X,
-                                        double2* Y) {
+                                        YT* Y) {
     const TileTask t = tiles[blockIdx.z];
     const int r = blockIdx.x * 32 + threadIdx.x;
     const int64_t ncol = t.cb1 - t.cb0;
@@ -314,8 +322,74 @@ __global__ void project_right_df_kernel(DevBasis Bs, const TileTask* __restrict_
             si = fi.x;
             li = fi.y;
         }
-        Y[t.yoff + jj * t.rows + r] = make_double2((double)sr + (double)lr, (double)si + (double)li);
+        store_y(Y + t.yoff + jj * t.rows + r, sr, lr, si, li);
     }
+}
+
+// H_mu elements from double-float Y (the mixed builds): U_a^dagger Y and the
+// projected exchange sum_g (v^1/2 P_i)_g conj(v^1/2 P_j)_g in double-float on
+// the FP32 pipe; the diagonal term U_i^dagger diag(eps_c - eps_v) U_j on a
+// shared orbit and W^div in FP64.  Pt: v^1/2-scaled projected exchange
+// vectors in double-float (or null).
+__global__ void project_left_df_kernel(DevBasis Bs, const TileTask* __restrict__ tiles, const float4* __restrict__ Y,
+                                       const float4* __restrict__ Pt, int ng0, double xscale,
+                                       const double* __restrict__ de, const double* __restrict__ w_div, double2* H,
+                                       int64_t ld) {
+    const TileTask t = tiles[blockIdx.z];
+    const int64_t ii = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t nrow = t.ca1 - t.ca0, ncol = t.cb1 - t.cb0;
+    if (ii >= nrow) return;
+    const int64_t i = t.ca0 + ii;
+    const int o = Bs.col_orbit[i];
+    const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
+    const float4* u = Bs.coef_df + Bs.col_off[i];
+    for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
+        const int64_t j = t.cb0 + jj;
+        const float4* y = Y + t.yoff + jj * t.rows;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t tt = 0; tt < n_o; ++tt) acc = cdf_dot_acc(acc, u[tt], y[Bs.member_loc[m0 + tt]]);
+        double2 h = cdf_to(acc);
+        if (de && Bs.col_orbit[j] == o) {
+            const double2* ui = Bs.coef + Bs.col_off[i];
+            const double2* uj = Bs.coef + Bs.col_off[j];
+            double2 d = make_double2(0.0, 0.0);
+            for (int64_t tt = 0; tt < n_o; ++tt) {
+                double2 z = cmul(conjd(ui[tt]), uj[tt]);
+                const double e = de[Bs.members[m0 + tt]];
+                d.x = fma(e, z.x, d.x);
+                d.y = fma(e, z.y, d.y);
+            }
+            h.x += d.x - (i == j ? *w_div : 0.0);
+            h.y += d.y;
+        }
+        if (Pt) {
+            const float4* pi = Pt + i * ng0;
+            const float4* pj = Pt + j * ng0;
+            float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int g = 0; g < ng0; ++g) ex = cdf_dot_acc(ex, pj[g], pi[g]);   // P_i conj(P_j)
+            const double2 e = cdf_to(ex);
+            h.x = fma(xscale, e.x, h.x);
+            h.y = fma(xscale, e.y, h.y);
+        }
+        H[j * ld + i] = h;
+        if (t.star_a != t.star_b) H[i * ld + j] = conjd(h);
+    }
+}
+
+__global__ void scale_to_df_kernel(const double2* __restrict__ P, const double* __restrict__ vbar, int64_t n, int ng0,
+                                   float4* out) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n * ng0) return;
+    const double s = sqrt(vbar[id % ng0]);
+    const double2 p = P[id];
+    out[id] = cdf_from(make_double2(s * p.x, s * p.y));
+}
+
+int launch_exchange_df(const double2* Pmu, const double* vbar, int64_t n, int ng0, float4* out, cudaStream_t st) {
+    if (n == 0 || ng0 == 0) return BSE_OK;
+    scale_to_df_kernel<<<(unsigned)ceil_div(n * ng0, 256), 256, 0, st>>>(Pmu, vbar, n, ng0, out);
+    LAUNCH_CHECK();
+    return BSE_OK;
 }
 
 __global__ void to_df_kernel(const double2* __restrict__ in, float4* out, int64_t n) {
@@ -378,7 +452,7 @@ __global__ void project_left_kernel(DevBasis Bs, const TileTask* __restrict__ ti
 }
 
 int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, int x32, const void* X, double2* Y,
-                         int64_t max_rows, int64_t max_cols, cudaStream_t st) {
+                         int64_t max_rows, int64_t max_cols, cudaStream_t st, int ydf) {
     if (ntiles == 0) return BSE_OK;
     dim3 blk(32, 8);
     int gy = ceil_div(max_cols, 8);
@@ -387,8 +461,10 @@ int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, i
     for (int off = 0; off < ntiles; off += 65535) {
         int n = ntiles - off < 65535 ? ntiles - off : 65535;
         dim3 grd(ceil_div(max_rows, 32), gy, n);
-        if (x32)
-            project_right_df_kernel<<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, Y);
+        if (x32 && ydf)
+            project_right_df_kernel<float4><<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, (float4*)Y);
+        else if (x32)
+            project_right_df_kernel<double2><<<grd, blk, 0, st>>>(b, tiles + off, (const float2*)X, Y);
         else
             project_right_kernel<double2><<<grd, blk, 0, st>>>(b, tiles + off, (const double2*)X, Y);
         LAUNCH_CHECK();
@@ -398,7 +474,7 @@ int launch_project_right(const DevBasis& b, const TileTask* tiles, int ntiles, i
 
 int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, const double2* Y, const double2* Pmu,
                         const double* vbar, int ng0, double xscale, const double* de, const double* w_div, double2* H,
-                        int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st) {
+                        int64_t ld, int64_t max_ca, int64_t max_cb, cudaStream_t st, int ydf, const float4* Pt) {
     if (ntiles == 0) return BSE_OK;
     dim3 blk(32, 8);
     int gy = ceil_div(max_cb, 8);
@@ -407,7 +483,11 @@ int launch_project_left(const DevBasis& b, const TileTask* tiles, int ntiles, co
     for (int off = 0; off < ntiles; off += 65535) {
         int n = ntiles - off < 65535 ? ntiles - off : 65535;
         dim3 grd(ceil_div(max_ca, 32) > 0 ? ceil_div(max_ca, 32) : 1, gy, n);
-        project_left_kernel<<<grd, blk, 0, st>>>(b, tiles + off, Y, Pmu, vbar, ng0, xscale, de, w_div, H, ld);
+        if (ydf)
+            project_left_df_kernel<<<grd, blk, 0, st>>>(b, tiles + off, (const float4*)Y, Pmu ? Pt : nullptr, ng0,
+                                                        xscale, de, w_div, H, ld);
+        else
+            project_left_kernel<<<grd, blk, 0, st>>>(b, tiles + off, Y, Pmu, vbar, ng0, xscale, de, w_div, H, ld);
         LAUNCH_CHECK();
     }
     return BSE_OK;
