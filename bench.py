@@ -42,6 +42,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DF_FMA_INSTR = 13.0
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / DF_FMA_INSTR * 2 / 1e12
 HA_MEV = 27211.386245988
+# arithmetic of the stages after the direct term (reported in config.precision)
+EIG_PREC = ("eigenvector-free eigensolver: Householder reduction, bisection refinement and twisted pivots in "
+            "double-float (48-bit significand) on the FP32 pipe, T and the results FP64")
+MIXED_REST = ("projection of the FP32 tiles and the exchange in double-float (products exact), diagonal and "
+              "W^div FP64; " + EIG_PREC)
 # DRAM bytes per launch of the direct-term kernel from the committed ncu capture
 # (profiles/), keyed by workload; None until a capture of the current kernel exists.
 DIRECT_TRAFFIC = {("si8", "fp64"): 41.711872e6 + 1210.309e6,    # profiles/direct_kernel_si8.md
@@ -536,17 +541,15 @@ def run_ours(args, rank, world, local):
                                              if args.block == "all" else "whole irrep block"),
                    "block_dims": dims,
                    "block_dim": int(tab["block_dim"][mu]), "solved_dim": dim, "full_dim": int(tab["n_product"]),
-                   "precision": {bse.BSE_FP32: "direct term FP32 on CUDA cores; diagonal, projection, exchange "
-                                               "and eigensolver FP64",
-                                 bse.BSE_FP64: "FP64 throughout",
+                   "precision": {bse.BSE_FP32: "direct term FP32 on CUDA cores; " + MIXED_REST,
+                                 bse.BSE_FP64: "direct term, projection and exchange FP64; " + EIG_PREC,
                                  bse.BSE_BF16_SPLIT: "pair densities FP32 on CUDA cores, dense contractions on "
                                                      "tcgen05 tensor cores with bf16 hi+lo operands (3 products) "
-                                                     "and FP32 accumulation; diagonal, projection, exchange and "
-                                                     "eigensolver FP64",
+                                                     "and FP32 accumulation; " + MIXED_REST,
                                  bse.BSE_FP16_SPLIT: "pair densities FP32 on CUDA cores, dense contractions on "
                                                      "tcgen05 tensor cores with fp16 hi+lo operands scaled by "
-                                                     "powers of two (3 products) and FP32 accumulation; diagonal, "
-                                                     "projection, exchange and eigensolver FP64"}[prec],
+                                                     "powers of two (3 products) and FP32 accumulation; "
+                                                     + MIXED_REST}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "k_pairs": work["k_pairs"], "star_pair_tiles": work["tiles"]},
