@@ -62,7 +62,10 @@ enum {
    with every operand split into a 16-bit hi + lo pair (bf16: 2 x 8
    significant bits; fp16: 2 x 11 bits, each operand scaled by an exact power
    of two into fp16's range) and three products accumulated in FP32.  The
-   diagonal, the projection and the exchange stay FP64. */
+   diagonal and W^div stay FP64; the projection and the exchange are FP64
+   in the FP64 build and, for the FP32 tiles of the other modes, formed in
+   double-float (a pair of floats, 48-bit significand: products exact, sums
+   far below the tiles' own error). */
 enum { BSE_FP64 = 0, BSE_BF16_SPLIT = 1, BSE_FP16_SPLIT = 2, BSE_FP32 = 3 };
 
 /* terms of H to include (bit mask) */
@@ -294,8 +297,9 @@ int bse_block_basis(bse_ctx* ctx, int32_t irrep, void* u_dev, int64_t ld);
 int bse_dipoles(bse_ctx* ctx, void* b_dev);
 
 /*
- * bse_block_spectrum - eigensolution of H_mu (dense Hermitian FP64 solver)
- * and the spectrum of the block:
+ * bse_block_spectrum - eigensolution of H_mu (dense Hermitian FP64 solver,
+ * or the eigenvector-free path of bse_set_solver) and the spectrum of the
+ * block:
  *   B_lambda = a_lambda^T (U_mu^T B)                (Eq. oscillatorA)
  *   Im eps_M(w) = 4 pi spin / Nk sum_lambda |B_lambda|^2
  *                 [eta/((w - Omega)^2 + eta^2) - eta/((w + Omega)^2 + eta^2)]
@@ -358,9 +362,12 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      are ||c||^2 times the squared first components of T's
  *                      eigenvectors (bisection for the levels, a twisted
  *                      factorisation per level for the components); no
- *                      eigenvector matrix is formed.  Needs the partners'
+ *                      eigenvector matrix is formed.  The reduction, the
+ *                      bisection's refinement and the twisted pivots compute
+ *                      in double-float (48-bit significand) on the FP32
+ *                      pipe: levels within about n 2^-47 ||H_mu||.  Needs the partners'
  *                      projections b_i to be parallel (true for the partner
- *                      blocks of bse_partner_spectrum) and n <= 8192; the
+ *                      blocks of bse_partner_spectrum) and n <= 4736; the
  *                      sum of the weights must come out as 1 within 1e-8.
  *                      Otherwise the spectrum call fails (EUNSUPPORTED or
  *                      ESOLVER).  Exactly degenerate levels (the d_mu
