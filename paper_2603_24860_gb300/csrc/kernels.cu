@@ -94,7 +94,9 @@ __global__ void rotmap_kernel(DevSys S, const int* __restrict__ rk, const double
     }
     const int* R = rk + 9 * s;
     const int k2 = rotk[(int64_t)s * S.nk + k];
-    const double n[3] = {(double)S.n1, (double)S.n2, (double)S.n3};
+    // 1/n by a Newton reciprocal (an FP64 divide costs hundreds of cycles of
+    // GB300's FP64 pipe); fr - f2 is an integer up to rounding, f2 enters the phase
+    const double rn[3] = {rcp_nr((double)S.n1), rcp_nr((double)S.n2), rcp_nr((double)S.n3)};
     const int* m = S.gk + ((int64_t)k * S.npw_max + i) * 3;
     int mr[3];
     double th = 0.0;
@@ -104,10 +106,10 @@ __global__ void rotmap_kernel(DevSys S, const int* __restrict__ rk, const double
         int mm = 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            fr += R[3 * a + b] * (S.kidx[3 * k + b] / n[b]);
+            fr += R[3 * a + b] * (S.kidx[3 * k + b] * rn[b]);
             mm += R[3 * a + b] * m[b];
         }
-        double f2 = S.kidx[3 * k2 + a] / n[a];
+        double f2 = S.kidx[3 * k2 + a] * rn[a];
         int fold = (int)rint(fr - f2);
         mr[a] = mm + fold;
         th += (f2 + mr[a]) * tau[3 * s + a];
