@@ -48,7 +48,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Rank-2 update A_rc -= v_r conj(w_c) + w_r conj(v_c) of a chunk of columns,
 // rows r0 + t, r0 + t + nt, ...
-template <int NC>
+// kTwo (columns in global memory): two rows per iteration, all their loads
+// issued before the arithmetic, so that more bytes are in flight per thread
+template <int NC, bool kTwo>
 __device__ __forceinline__ void chunk_update(cdf* cb, size_t cs, const cdf* V, const cdf* W, const int* jcol,
                                              int r0, int n, int t, int nt) {
     cdf vj[NC], wj[NC];
@@ -57,23 +59,39 @@ __device__ __forceinline__ void chunk_update(cdf* cb, size_t cs, const cdf* V, c
         vj[c] = V[jcol[c]];
         wj[c] = W[jcol[c]];
     }
-    for (int r = r0 + t; r < n; r += nt) {
+    int r = r0 + t;
+    if (kTwo)
+        for (; r + nt < n; r += 2 * nt) {
+            cdf q0[NC], q1[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                q0[c] = cb[c * cs + r];
+                q1[c] = cb[c * cs + r + nt];
+            }
+            const cdf v0 = V[r], w0 = W[r], v1 = V[r + nt], w1 = W[r + nt];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                cb[c * cs + r] = cdf_rank2(q0[c], v0, w0, wj[c], vj[c]);
+                cb[c * cs + r + nt] = cdf_rank2(q1[c], v1, w1, wj[c], vj[c]);
+            }
+        }
+    for (; r < n; r += nt) {
         const cdf v = V[r], w = W[r];
 #pragma unroll
         for (int c = 0; c < NC; ++c) cb[c * cs + r] = cdf_rank2(cb[c * cs + r], v, w, wj[c], vj[c]);
     }
 }
 
-#define BSE_NC_DISPATCH(nc, F, ...)         \
-    switch (nc) {                            \
-        case 1: F<1>(__VA_ARGS__); break;    \
-        case 2: F<2>(__VA_ARGS__); break;    \
-        case 3: F<3>(__VA_ARGS__); break;    \
-        case 4: F<4>(__VA_ARGS__); break;    \
-        case 5: F<5>(__VA_ARGS__); break;    \
-        case 6: F<6>(__VA_ARGS__); break;    \
-        case 7: F<7>(__VA_ARGS__); break;    \
-        default: F<8>(__VA_ARGS__); break;   \
+#define BSE_NC_DISPATCH(nc, two, F, ...)          \
+    switch (nc) {                                  \
+        case 1: F<1, two>(__VA_ARGS__); break;     \
+        case 2: F<2, two>(__VA_ARGS__); break;     \
+        case 3: F<3, two>(__VA_ARGS__); break;     \
+        case 4: F<4, two>(__VA_ARGS__); break;     \
+        case 5: F<5, two>(__VA_ARGS__); break;     \
+        case 6: F<6, two>(__VA_ARGS__); break;     \
+        case 7: F<7, two>(__VA_ARGS__); break;     \
+        default: F<8, two>(__VA_ARGS__); break;    \
     }
 
 struct TriArgs {
@@ -212,6 +230,14 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
             const cdf* cl = col(l);
             cdf acc = cdf_zero(), acc2 = cdf_zero();
             int r = r0 + lane;
+            if (!kSmem)   // columns in global memory: four rows' loads in flight per lane
+                for (; r + 96 < n; r += 128) {
+                    const cdf a0 = cl[r], a1 = cl[r + 32], a2 = cl[r + 64], a3 = cl[r + 96];
+                    acc = cdf_dot_acc(acc, a0, Vk[r]);
+                    acc2 = cdf_dot_acc(acc2, a1, Vk[r + 32]);
+                    acc = cdf_dot_acc(acc, a2, Vk[r + 64]);
+                    acc2 = cdf_dot_acc(acc2, a3, Vk[r + 96]);
+                }
             for (; r + 32 < n; r += 64) {
                 acc = cdf_dot_acc(acc, cl[r], Vk[r]);
                 acc2 = cdf_dot_acc(acc2, cl[r + 32], Vk[r + 32]);
@@ -305,7 +331,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
                 int jcol[kChunk];
 #pragma unroll
                 for (int c = 0; c < kChunk; ++c) jcol[c] = blk + (c0 + c) * G;
-                BSE_NC_DISPATCH(nc, chunk_update, col(c0), cstride, V, W, jcol, k, n, tid - 32, kTriThreads - 32)
+                BSE_NC_DISPATCH(nc, !kSmem, chunk_update, col(c0), cstride, V, W, jcol, k, n, tid - 32,
+                                kTriThreads - 32)
             }
         }
         if (!more) break;
