@@ -208,7 +208,8 @@ def test_empty_block(gpu):
     pytest.skip("no empty irrep block among the small cases")
 
 
-# --- FP32 direct term (CUDA cores); diagonal, projection, exchange stay FP64 ---
+# --- FP32 direct term (CUDA cores); diagonal FP64, projection and exchange in
+#     double-float (48-bit significand) ---
 HA_MEV = 27211.386245988
 TOL32 = 2e-6          # H_mu elements relative to the largest element
 
@@ -232,7 +233,8 @@ def test_blocks_fp32(gpu, name):
 
 @pytest.mark.parametrize("terms", [2, 4])
 def test_block_terms_fp32(gpu, terms):
-    """The FP32 mode only changes the direct term; the exchange is FP64."""
+    """The FP32 mode changes the direct term; the exchange, projected in
+    double-float (products exact, 48-bit sums), keeps the FP64 tolerance."""
     from oracle.projection import project
     bse, torch, get = gpu
     d, inp, grp, mt, b = oracle_case("si4")
