@@ -365,7 +365,10 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      eigenvector matrix is formed.  The reduction, the
  *                      bisection's refinement and the twisted pivots compute
  *                      in double-float (48-bit significand) on the FP32
- *                      pipe: levels within about n 2^-47 ||H_mu||.  Needs the partners'
+ *                      pipe: levels within about n 2^-47 ||H_mu||, for
+ *                      blocks whose entries lie below 2^50 in magnitude
+ *                      (FP32's exponent range; Hartree-unit blocks are far
+ *                      inside it).  Needs the partners'
  *                      projections b_i to be parallel (true for the partner
  *                      blocks of bse_partner_spectrum) and n <= 4736; the
  *                      sum of the weights must come out as 1 within 1e-8.
