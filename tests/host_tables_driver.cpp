@@ -9,6 +9,15 @@
 //                  rotk i32[n_ops nk], star_of i32[nk], star_rep i32[n_stars],
 //                  s_k i32[nk], class_of i32[n_ops], chi i32[n_irreps n_ops],
 //                  irrep_dim i32[n_irreps], bright i32[n_irreps], orbit_of i32[N]
+// With a third and fourth argument (band rotations in, bases out), the
+// driver also builds the bases from given band rotations Gamma(s): complex
+// f64 [n_ops][gam_per_s] in the library's layout (per k the multiplet blocks,
+// valence then conduction, [target][source] row-major), and writes
+//   gam_per_s i64, n_orbits i64, orbit_off i64[n_orbits + 1],
+//   orbit_members i64[orbit_off[n_orbits]], then per irrep the basis of
+//   Eq. projection and the partner bases (d = 0 when there are none):
+//   basis, d i32, d bases, each basis as dim i64, col_orbit i32[dim],
+//   col_off i64[dim + 1], coef c128[col_off[dim]].
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -26,9 +35,73 @@ static void put(FILE* f, const T* p, size_t n) {
     fwrite(p, sizeof(T), n, f);
 }
 
+static void put_basis(FILE* o, const Basis& b) {
+    put(o, &b.dim, 1);
+    put(o, b.col_orbit.data(), b.col_orbit.size());
+    put(o, b.col_off.data(), b.col_off.size());
+    put(o, b.coef.data(), b.coef.size());
+}
+
+// the bases of every irrep and its partner bases, as the library builds them
+// (the partner weights are those of the partner-block path)
+static int write_bases(Tables& t, const char* gin, const char* bout) {
+    FILE* f = fopen(gin, "rb");
+    if (!f) return 2;
+    t.gamma.resize((size_t)t.nops * t.gam_per_s);
+    const bool ok = get(f, t.gamma.data(), t.gamma.size());
+    fclose(f);
+    if (!ok) {
+        fprintf(stderr, "short band rotations\n");
+        return 2;
+    }
+    if (check_band_rotations(t) != BSE_OK) {
+        fprintf(stderr, "band rotations not unitary\n");
+        return 1;
+    }
+    FILE* o = fopen(bout, "wb");
+    if (!o) return 2;
+    const int64_t norb = (int64_t)t.orbit_off.size() - 1;
+    put(o, &t.gam_per_s, 1);
+    put(o, &norb, 1);
+    put(o, t.orbit_off.data(), t.orbit_off.size());
+    put(o, t.orbit_members.data(), t.orbit_members.size());
+    for (int mu = 0; mu < t.n_irreps; ++mu) {
+        Basis b;
+        if (build_basis(t, mu, b) != BSE_OK) return 1;
+        put_basis(o, b);
+        int d = 0;
+        std::vector<double> gam;
+        if (partner_matrices(t, mu, d, gam) != BSE_OK) {
+            const int32_t zero = 0;
+            put(o, &zero, 1);
+            continue;
+        }
+        const int G = t.nops;
+        auto weights = [&](int i, int j) {
+            std::vector<double> w(G);
+            for (int s = 0; s < G; ++s) w[s] = (double)d / G * gam[((size_t)s * d + i) * d + j];
+            return w;
+        };
+        std::vector<Basis> part(d);
+        if (build_basis_weighted(t, weights(0, 0), part[0]) != BSE_OK) return 1;
+        std::vector<std::vector<double>> ws;
+        std::vector<Basis*> outs;
+        for (int i = 1; i < d; ++i) {
+            ws.push_back(weights(i, 0));
+            outs.push_back(&part[i]);
+        }
+        if (d > 1 && transfer_bases(t, part[0], ws, outs) != BSE_OK) return 1;
+        const int32_t d32 = d;
+        put(o, &d32, 1);
+        for (const Basis& pb : part) put_basis(o, pb);
+    }
+    fclose(o);
+    return 0;
+}
+
 int main(int argc, char** argv) {
-    if (argc != 3) {
-        fprintf(stderr, "usage: %s input output\n", argv[0]);
+    if (argc != 3 && argc != 5) {
+        fprintf(stderr, "usage: %s input output [band_rotations bases]\n", argv[0]);
         return 2;
     }
     FILE* f = fopen(argv[1], "rb");
@@ -82,5 +155,5 @@ int main(int argc, char** argv) {
     put(o, t.bright.data(), t.bright.size());
     put(o, t.orbit_of.data(), t.orbit_of.size());
     fclose(o);
-    return 0;
+    return argc == 5 ? write_bases(t, argv[3], argv[4]) : 0;
 }
