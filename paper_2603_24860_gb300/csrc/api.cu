@@ -107,9 +107,13 @@ struct bse_ctx {
         IrrepDev part[3];   // partner 1 basis and its transfers P_i1 U_1
     };
     std::vector<PartnerDev> partner;
-    std::vector<int64_t> partner_dim;   // dim_mu / d_mu for partner-capable irreps, else 0
-    std::vector<std::vector<double>> pgam;   // irrep matrices [s][d][d] of partner-capable irreps
-    std::vector<int> pgam_d;                 // their dimension, 0 where there are none
+    // partner data of each irrep, made on first use (ensure_pmat): dim_mu / d_mu
+    // for partner-capable irreps (else 0), the irrep matrices [s][d][d] and d
+    mutable std::vector<int64_t> partner_dim;
+    mutable std::vector<std::vector<double>> pgam;
+    mutable std::vector<int> pgam_d;
+    mutable std::vector<char> pready;
+    std::vector<cplx> ptrace;   // Tr Gamma~(s) of the product space, for Tr P_11
     int ng0 = 0;
     mutable double w_div = 0.0;        // host copy of W^div, valid when wdiv_host_ok
     mutable bool wdiv_host_ok = false;
@@ -517,12 +521,38 @@ static int upload_basis(bse_ctx* c, IrrepDev& d) {
     return BSE_OK;
 }
 
+// irrep matrices of irrep mu (when it has them) and its partner dimension
+// Tr P_11 = d/|S| sum_s Gamma_mu(s)_11 Tr Gamma~(s), made once
+static int ensure_pmat(const bse_ctx* c, int mu) {
+    if (c->pready[mu]) return BSE_OK;
+    const Tables& t = c->t;
+    int d = 0;
+    std::vector<double> gam;
+    if (partner_matrices(t, mu, d, gam) != BSE_OK) {   // no irrep matrices: no partner block
+        clear_error();
+        c->pready[mu] = 1;
+        return BSE_OK;
+    }
+    cplx a = 0;
+    for (int s = 0; s < t.nops; ++s) a += gam[(size_t)s * d * d] * c->ptrace[s];
+    const double dd = a.real() * d / t.nops;
+    const long r = std::lround(dd);
+    if (std::fabs(dd - r) > 1e-6 || r * d != c->block_dim[mu])
+        return fail(BSE_ESYMM, "Tr P_11 of irrep %d = %.9f is not dim/d", mu, dd);
+    c->pgam[mu] = std::move(gam);
+    c->pgam_d[mu] = d;
+    c->partner_dim[mu] = r;
+    c->pready[mu] = 1;
+    return BSE_OK;
+}
+
 // partner 1 of an irrep: canonical basis of the range of P_11 and its
 // transfers U_i = P_i1 U_1
 static int ensure_partner(bse_ctx* c, int mu) {
     if (mu < 0 || mu >= c->t.n_irreps) return fail(BSE_EINVAL, "irrep %d out of range [0, %d)", mu, c->t.n_irreps);
     auto& pd = c->partner[mu];
     if (pd.ready) return BSE_OK;
+    BSE_TRY(ensure_pmat(c, mu));
     const double t0 = now_ms();
     const int d = c->pgam_d[mu];
     if (d == 0) return fail(BSE_EUNSUPPORTED, "irrep %d has no irrep matrices for a partner block", mu);
@@ -931,33 +961,12 @@ static int create_impl(bse_ctx* c, const bse_system* sys) {
         tot += r;
     }
     if (tot != t.N) return fail(BSE_ESYMM, "block dimensions sum to %lld, not N = %lld", (long long)tot, (long long)t.N);
-    // irrep matrices of every irrep that has them (one irrep per host thread),
-    // kept for the partner bases, and the partner dimensions Tr P_11
+    // irrep matrices and partner dimensions are made per irrep on first use
+    c->ptrace = trace;
     c->partner_dim.assign(t.n_irreps, 0);
     c->pgam.assign(t.n_irreps, {});
     c->pgam_d.assign(t.n_irreps, 0);
-    host_parallel_for(t.n_irreps, [&](int mu) {
-        int d = 0;
-        std::vector<double> gam;
-        if (partner_matrices(t, mu, d, gam) != BSE_OK) {   // no irrep matrices: no partner block
-            clear_error();
-            return;
-        }
-        c->pgam[mu] = std::move(gam);
-        c->pgam_d[mu] = d;
-    });
-    for (int mu = 0; mu < t.n_irreps; ++mu) {
-        const int d = c->pgam_d[mu];
-        if (d == 0) continue;
-        const std::vector<double>& gam = c->pgam[mu];
-        cplx a = 0;
-        for (int s = 0; s < t.nops; ++s) a += gam[(size_t)s * d * d] * trace[s];
-        double dd = a.real() * d / t.nops;
-        long r = std::lround(dd);
-        if (std::fabs(dd - r) > 1e-6 || r * d != c->block_dim[mu])
-            return fail(BSE_ESYMM, "Tr P_11 of irrep %d = %.9f is not dim/d", mu, dd);
-        c->partner_dim[mu] = r;
-    }
+    c->pready.assign(t.n_irreps, 0);
     c->partner.resize(t.n_irreps);
     // orbit tables on the device
     std::vector<int> loc(t.orbit_members.size());
@@ -1093,6 +1102,7 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
     v->orbit_of = t.orbit_of.data();
     BSE_TRY(wdiv_host(c));
     v->w_div = c->w_div;
+    for (int mu = 0; mu < t.n_irreps; ++mu) BSE_TRY(ensure_pmat(c, mu));
     v->partner_dim = c->partner_dim.data();
     return BSE_OK;
 }
