@@ -93,3 +93,41 @@ def test_head_only_on_diagonal():
     h1 = hm.full_hamiltonian(inp, mt, w_div=0.3, terms="d")
     h0 = hm.full_hamiltonian(inp, mt, w_div=0.0, terms="d")
     assert np.allclose(h1 - h0, -0.3 * np.eye(inp.N), atol=1e-15)
+
+
+def _sub_index(inp, ks):
+    b = inp.nv * inp.nc
+    return np.concatenate([np.arange(k * b, (k + 1) * b) for k in ks])
+
+
+def _block_cases(mt):
+    """Star-pair row/column sets: a diagonal star pair (rows = cols), an
+    off-diagonal pair, and one with rows != cols in order and length."""
+    st = [list(map(int, s)) for s in mt.stars]
+    big = max(range(len(st)), key=lambda a: len(st[a]))
+    other = next(a for a in range(len(st)) if a != big and len(st[a]) > 1)
+    return [(st[big], st[big]),
+            (st[big], st[other]),
+            (st[other][::-1] + st[0], st[big][:3])]
+
+
+@pytest.mark.parametrize("name", ["si4", "mos2_331"])
+def test_hamiltonian_block_is_the_full_h_restricted(name):
+    """hamiltonian_block (the star-pair sub-block every full-size parity check
+    compares against) equals full_hamiltonian's rows and columns of the same
+    product indices (Eq. BSE-eigval with the head correction of Eq. Wdiv on
+    the diagonal), element by element."""
+    d, inp, grp, mt, b = oracle_case(name)
+    H = oracle_h(name)
+    wd = _wdiv_of(name)
+    for rows, cols in _block_cases(mt):
+        got = hm.hamiltonian_block(inp, mt, rows, cols, wd)
+        ref = H[np.ix_(_sub_index(inp, rows), _sub_index(inp, cols))]
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(H).max()
+
+
+def _wdiv_of(name):
+    from conftest import _H
+    oracle_h(name)
+    return _H[(name, "wdiv")]

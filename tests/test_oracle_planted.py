@@ -85,3 +85,34 @@ def test_head_and_wings_ignored_at_q0():
     finally:
         inp.w = saved
     assert np.abs(K1 - K0).max() == 0.0
+
+
+def test_dropped_head_correction_in_sub_block_is_caught():
+    """A sub-block builder that forgets -W^div on the diagonal (or takes the
+    exchange vectors of the rows for the columns) fails the restriction pin of
+    test_oracle_hamiltonian."""
+    from conftest import oracle_h
+    from test_oracle_hamiltonian import _block_cases, _sub_index, _wdiv_of
+    d, inp, grp, mt, b = oracle_case("si4")
+    H = oracle_h("si4")
+    wd = _wdiv_of("si4")
+    scale = np.abs(H).max()
+
+    def no_head(rows, cols):
+        same = _sub_index(inp, rows)[:, None] == _sub_index(inp, cols)[None, :]
+        return hm.hamiltonian_block(inp, mt, rows, cols, wd) + wd * same
+
+    def rows_for_cols(rows, cols):
+        P, vbar = hm.exchange_vectors_for(inp, mt, rows)
+        Pr, _ = hm.exchange_vectors_for(inp, mt, rows[:1] * len(cols))
+        return (hm.hamiltonian_block(inp, mt, rows, cols, wd)
+                - inp.spin * (P * vbar) @ hm.exchange_vectors_for(inp, mt, cols)[0].conj().T / inp.volume
+                + inp.spin * (P * vbar) @ Pr.conj().T / inp.volume)
+
+    rows, cols = _block_cases(mt)[0]
+    ref = H[np.ix_(_sub_index(inp, rows), _sub_index(inp, cols))]
+    assert np.abs(hm.hamiltonian_block(inp, mt, rows, cols, wd) - ref).max() <= 1e-14 * scale
+    assert np.abs(no_head(rows, cols) - ref).max() > 1e-3 * abs(wd)
+    rows, cols = _block_cases(mt)[1]
+    ref = H[np.ix_(_sub_index(inp, rows), _sub_index(inp, cols))]
+    assert np.abs(rows_for_cols(rows, cols) - ref).max() > 1e-8 * scale
