@@ -153,8 +153,29 @@ typedef struct {
     const int32_t* orbit_of;      /* [N] orbit of each product index; orbits ordered by lowest member */
     double w_div;                 /* head correction used on the diagonal (Ha) */
     const int64_t* partner_dim;   /* [n_irreps] dim_mu / d_mu where a partner block exists, else 0 */
+    const int32_t* fold;          /* [n_ops][nk][3] integer G-bar with R^{-T} f_k = f_{sk} + G-bar (Eq. sk) */
+    int32_t npw_max, ng_max;      /* capacities of the sphere arrays below */
+    const int32_t* npw;           /* [nk] |S_k|: plane waves of the coset sphere of k */
+    const int32_t* gk;            /* [nk][npw_max][3] integer m of p = f_k + m in S_k, in the order of bse_system */
+    const int32_t* ng;            /* [nk] |S_q|: points Q = f_q + G of the sphere of W(q) */
+    const int32_t* gq;            /* [nk][ng_max][3] integer G of S_q, in the order of bse_system */
 } bse_tables_view;
 
+/*
+ * bse_tables - the symmetry tables the construction works from (Sec. III.C):
+ * the rotated mesh points s k and their folds (Eq. sk), the stars with their
+ * representatives and the operations s_k reaching each member, the
+ * conjugacy classes and characters (computed, Burnside-Dixon; Eq. LOT
+ * holds), the irreps' multiplicities in the polar-vector representation
+ * (Sec. III.D: the optically active irreps), the block dimensions
+ * dim_mu = Tr P_mu (Eq. projection: d_mu/|S| sum_s chi_mu(s)^* Tr Gamma~(s)),
+ * the orbits of the product basis, the coset spheres S_k and S_q, W^div, and
+ * the partner dimensions.  The first call also forms the irrep matrices of
+ * every irrep that has them (for the partner dimensions); it returns ESYMM
+ * when their row projector's trace Tr P_11 is not dim_mu / d_mu (inputs that
+ * break the symmetry in a way bse_create's checks do not see), EINVAL for a
+ * null argument.  Views stay valid until bse_destroy.
+ */
 int bse_tables(const bse_ctx* ctx, bse_tables_view* out);
 
 /*
@@ -164,11 +185,17 @@ int bse_tables(const bse_ctx* ctx, bse_tables_view* out);
  * bands: BSE_BANDS_CC (n, n' conduction), BSE_BANDS_VV, or BSE_BANDS_CV
  * (n conduction, n' valence; with k = k' these are the exchange vectors
  * m^k_cv(G) of Eq. v_scalar).
+ * prec: BSE_FP64 (FP64 arithmetic, out complex128) or the precision of a
+ * mixed build, BSE_FP32, BSE_BF16_SPLIT or BSE_FP16_SPLIT: the densities
+ * those builds use, FP32 arithmetic on the FP32 copy of the coefficients
+ * (out complex64; the split modes split them into 16-bit pairs only inside
+ * the tensor-core kernel).
  * k, kp: host arrays [npairs]; out_dev: device [npairs][n][n'][ng_max]
- * complex128, entries with G index >= ng(q) set to zero; caller-owned.
+ * of that type, entries with G index >= ng(q) set to zero; caller-owned.
+ * Errors: EINVAL (bands, prec, a k index out of range, null pointers).
  */
 int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npairs,
-                 int32_t bands, void* out_dev);
+                 int32_t bands, int32_t prec, void* out_dev);
 
 /*
  * bse_build_block - H_mu = U_mu^dagger H U_mu for irrep mu, never forming
@@ -190,7 +217,10 @@ int bse_pairdens(bse_ctx* ctx, const int32_t* k, const int32_t* kp, int64_t npai
  */
 enum { BSE_IRREP_ALL = -1 };
 
-/* bse_block_dim - dim_mu = Tr P_mu of an irrep (N for BSE_IRREP_ALL). */
+/* bse_block_dim - dim_mu = Tr P_mu of an irrep (N for BSE_IRREP_ALL): the
+ * trace of the projector of Eq. projection, d_mu/|S| sum_s chi_mu(s)^*
+ * Tr Gamma~(s), from the band rotations of the k points each operation fixes
+ * (Sec. III.C.4); integer-exact.  Errors: EINVAL (irrep out of range). */
 int bse_block_dim(const bse_ctx* ctx, int32_t irrep, int64_t* dim);
 
 int bse_build_block(bse_ctx* ctx, int32_t irrep, int32_t prec, uint32_t terms,
@@ -397,6 +427,22 @@ enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2 };
  */
 int bse_set_seeds(bse_ctx* ctx, int32_t on);
 int bse_set_solver(bse_ctx* ctx, int32_t solver);
+
+/*
+ * bse_set_wait_limit - how long the context's kernels wait at a bounded
+ * device wait (no counterpart in the paper: failure handling).  Every wait of
+ * a device-wide step is bounded: the grid barriers of the tridiagonal
+ * reduction and of the Lanczos recurrence, and the mbarrier waits of the
+ * tensor-core direct kernel on its bulk copy and its MMAs.  A wait that gives
+ * up raises an error flag, lets the copy or MMAs it waited for finish (the
+ * default limit), frees its tensor memory and returns; the call then reports
+ * ETIMEOUT and the context stays usable.  polls >= 0: a wait gives up after
+ * that many polls (0: at once, which makes every such call report ETIMEOUT;
+ * meant for tests of the failure path); polls < 0 (the default): seconds of
+ * polling.  A batch (bse_batch_create) keeps the limits its contexts had when
+ * it was created.
+ */
+int bse_set_wait_limit(bse_ctx* ctx, int64_t polls);
 
 /*
  * bse_loss_spectrum - longitudinal excitons and the loss spectrum of a block

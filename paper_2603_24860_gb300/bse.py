@@ -50,6 +50,8 @@ class BseTablesView(C.Structure):
         ("rotk", _P32), ("star_of_k", _P32), ("star_rep", _P32), ("s_k", _P32),
         ("class_of_op", _P32), ("chi", _P32), ("irrep_dim", _P32), ("bright", _P32),
         ("block_dim", _P64), ("orbit_of", _P32), ("w_div", C.c_double), ("partner_dim", _P64),
+        ("fold", _P32), ("npw_max", C.c_int32), ("ng_max", C.c_int32), ("npw", _P32), ("gk", _P32),
+        ("ng", _P32), ("gq", _P32),
     ]
 
 
@@ -73,7 +75,7 @@ EXPORTS = {
     "bse_destroy": (C.c_int, [C.c_void_p]),
     "bse_last_error": (C.c_char_p, []),
     "bse_tables": (C.c_int, [C.c_void_p, C.POINTER(BseTablesView)]),
-    "bse_pairdens": (C.c_int, [C.c_void_p, _P32, _P32, C.c_int64, C.c_int32, C.c_void_p]),
+    "bse_pairdens": (C.c_int, [C.c_void_p, _P32, _P32, C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),
     "bse_build_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_uint32, C.c_void_p, C.c_int64]),
     "bse_build_full": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_int64]),
     "bse_block_basis": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
@@ -91,6 +93,7 @@ EXPORTS = {
     "bse_block_star_columns": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _P64]),
     "bse_set_solver": (C.c_int, [C.c_void_p, C.c_int32]),
     "bse_set_seeds": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bse_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "bse_loss_spectrum": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "bse_block_dim": (C.c_int, [C.c_void_p, C.c_int32, _P64]),
@@ -242,16 +245,19 @@ def bse_tables(ctx: Context) -> dict:
         rotk=get(v.rotk, no * nk, (no, nk)), star_of_k=get(v.star_of_k, nk), star_rep=get(v.star_rep, v.n_stars),
         s_k=get(v.s_k, nk), class_of_op=get(v.class_of_op, no), chi=get(v.chi, ni * no, (ni, no)),
         irrep_dim=get(v.irrep_dim, ni), bright=get(v.bright, ni), block_dim=get(v.block_dim, ni),
-        orbit_of=get(v.orbit_of, v.n_product), w_div=v.w_div, partner_dim=get(v.partner_dim, ni))
+        orbit_of=get(v.orbit_of, v.n_product), w_div=v.w_div, partner_dim=get(v.partner_dim, ni),
+        fold=get(v.fold, no * nk * 3, (no, nk, 3)), npw=get(v.npw, nk), gk=get(v.gk, nk * v.npw_max * 3,
+                                                                               (nk, v.npw_max, 3)),
+        ng=get(v.ng, nk), gq=get(v.gq, nk * v.ng_max * 3, (nk, v.ng_max, 3)))
 
 
-def bse_pairdens(ctx: Context, k, kp, bands: int, out):
-    """rho for pairs (k[i], kp[i]) into the complex128 CUDA tensor out
-    [npairs, n, n', ng_max]."""
+def bse_pairdens(ctx: Context, k, kp, bands: int, out, prec: int = BSE_FP64):
+    """rho for pairs (k[i], kp[i]) into the CUDA tensor out [npairs, n, n',
+    ng_max]: complex128 for BSE_FP64, complex64 for the mixed precisions."""
     k = np.ascontiguousarray(k, dtype=np.int32)
     kp = np.ascontiguousarray(kp, dtype=np.int32)
     assert len(k) == len(kp)
-    _check(lib().bse_pairdens(ctx.handle, k.ctypes.data_as(_P32), kp.ctypes.data_as(_P32), len(k), bands,
+    _check(lib().bse_pairdens(ctx.handle, k.ctypes.data_as(_P32), kp.ctypes.data_as(_P32), len(k), bands, prec,
                               _ptr(out)))
     return out
 
@@ -421,6 +427,10 @@ def loss_spectrum(ctx: Context, omega_levels, osc, omega, eta: float):
 
 def bse_set_seeds(ctx: Context, on: bool):
     _check(lib().bse_set_seeds(ctx.handle, 1 if on else 0))
+
+
+def bse_set_wait_limit(ctx: Context, polls: int):
+    _check(lib().bse_set_wait_limit(ctx.handle, polls))
 
 
 def bse_set_solver(ctx: Context, solver: int):

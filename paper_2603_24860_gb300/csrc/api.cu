@@ -145,6 +145,7 @@ struct bse_ctx {
     DevBuf wsym;         // orbit sum of W^div: per-column arrays
     DevBuf wdivDev;      // W^div on the device (one double), read by the kernels that need it
     int32_t solver_mode = BSE_SOLVER_AUTO;
+    long wait_polls = -1;   // polls of every bounded device wait (negative: the kernels' defaults)
     DevBuf triScratch, triSmall;   // tridiagonal path: scratch; gram [9], weight sum, error flag
     // scratch (library-owned, grow-only)
     DevBuf arenaX, arenaY, Pmu, tasks, tiles, pairs, eigA, eigWork, info, Bmu, wpart, wsum, counter;
@@ -1100,6 +1101,13 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
     v->bright = t.bright.data();
     v->block_dim = c->block_dim.data();
     v->orbit_of = t.orbit_of.data();
+    v->fold = t.fold.data();
+    v->npw_max = (int32_t)(c->gk.size() / (3 * (size_t)t.nk));
+    v->ng_max = (int32_t)(c->gq.size() / (3 * (size_t)t.nk));
+    v->npw = c->npw.data();
+    v->gk = c->gk.data();
+    v->ng = c->ng.data();
+    v->gq = c->gq.data();
     BSE_TRY(wdiv_host(c));
     v->w_div = c->w_div;
     for (int mu = 0; mu < t.n_irreps; ++mu) BSE_TRY(ensure_pmat(c, mu));
@@ -1107,12 +1115,15 @@ int bse_tables(const bse_ctx* c, bse_tables_view* v) {
     return BSE_OK;
 }
 
-int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs, int32_t bands, void* out) {
+int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs, int32_t bands, int32_t prec,
+                 void* out) {
     clear_error();
     if (!c) return fail(BSE_EINVAL, "null context");
     AllocStream alloc_on_(c->stream);
     if (!c || (npairs > 0 && (!k || !kp || !out))) return fail(BSE_EINVAL, "null argument");
     if (bands < 0 || bands > 2) return fail(BSE_EINVAL, "bands must be CC, VV or CV");
+    if (prec != BSE_FP64 && prec != BSE_FP32 && prec != BSE_BF16_SPLIT && prec != BSE_FP16_SPLIT)
+        return fail(BSE_EINVAL, "unknown precision %d", prec);
     if (npairs < 0 || npairs > (1ll << 31) - 1) return fail(BSE_EINVAL, "npairs out of range");
     if (npairs == 0) return BSE_OK;
     std::vector<int32_t> both((size_t)2 * npairs);
@@ -1124,7 +1135,10 @@ int bse_pairdens(bse_ctx* c, const int32_t* k, const int32_t* kp, int64_t npairs
     }
     BSE_TRY(upload(c->pairs, both.data(), both.size(), c->stream));
     const int* d = (const int*)c->pairs.p;
-    return launch_pairdens(c->S, d, d + npairs, npairs, bands, 0, (double2*)out, c->stream);
+    if (prec == BSE_FP64) return launch_pairdens(c->S, d, d + npairs, npairs, bands, 0, (double2*)out, c->stream);
+    BSE_TRY(ensure_narrow(c));
+    return launch_pairdens32(c->S, (const float2*)c->coef32.p, d, d + npairs, npairs, bands, (float2*)out,
+                             c->stream);
 }
 
 int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
@@ -1324,7 +1338,7 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
             BSE_TRY(launch_direct_tc(c->S, fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ngp,
                                      (const PairTask*)c->tasks.p,
                                      (const TcGroup*)c->groups.p, (int64_t)groups.size(), c->arenaX.p,
-                                     (int*)c->status.p, c->stream));
+                                     (int*)c->status.p, c->stream, c->wait_polls));
         } else if (terms & BSE_TERM_DIRECT) {
             BSE_TRY(direct_single(c, p32, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(), c->arenaX.p));
         } else {
@@ -1504,7 +1518,7 @@ static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaE
             BSE_TRY(launch_direct_tc(c->S, b->fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ti.ngp,
                                      (const PairTask*)b->tctasks.p + ti.task_off,
                                      (const TcGroup*)b->tcgroups.p + ti.group_off, ti.ngroups, b->arenaX.p,
-                                     (int*)b->status.p, st));
+                                     (int*)b->status.p, st, c->wait_polls));
         }
     }
     if (terms & BSE_TERM_DIRECT) {
@@ -1887,7 +1901,7 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
     BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
                                     c->triScratch.p, omega_out, osc, wsum, err, c->stream,
-                                    c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr));
+                                    c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     struct {
         double s;
@@ -2053,7 +2067,7 @@ int bse_block_spectrum_lanczos(bse_ctx* c, int32_t mu, int32_t partner, const vo
     double *alpha = nullptr, *beta = nullptr;
     int done = 0;
     BSE_TRY(launch_lanczos((const double2*)h, ld, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, steps,
-                           c->lzScratch.p, &alpha, &beta, &done, c->stream));
+                           c->lzScratch.p, &alpha, &beta, &done, c->stream, c->wait_polls));
     const double pref = 4.0 * M_PI * c->spin / c->t.nk;
     BSE_TRY(launch_cf_spectrum(alpha, beta + 1, done, scale, omega, n_omega, eta, pref, im_eps, c->stream));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
@@ -2114,6 +2128,13 @@ int bse_set_solver(bse_ctx* c, int32_t solver) {
     if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG)
         return fail(BSE_EINVAL, "unknown solver %d", solver);
     c->solver_mode = solver;
+    return BSE_OK;
+}
+
+int bse_set_wait_limit(bse_ctx* c, int64_t polls) {
+    clear_error();
+    if (!c) return fail(BSE_EINVAL, "null argument");
+    c->wait_polls = polls < 0 ? -1 : (long)std::min<int64_t>(polls, (int64_t)1 << 40);
     return BSE_OK;
 }
 

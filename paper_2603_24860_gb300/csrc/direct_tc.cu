@@ -25,6 +25,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "grid_sync.h"
 #include "internal.h"
 #include "tc_ptx.h"
 
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
                                                            const E* __restrict__ wemb, const int* __restrict__ wexp,
                                                            const PairTask* __restrict__ tasks,
                                                            const TcGroup* __restrict__ groups, int ngp, int kg,
-                                                           float2* X, int* status) {
+                                                           float2* X, int* status, long spin) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nv = S.nv, nc = S.nc, nb = S.nb, P = nc * nc + nv * nv, ncc = nc * nc, nvv = nv * nv;
@@ -147,7 +148,6 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
     __shared__ int s_erho[kMaxG];   // scale exponent of each pair's densities
     // TMEM: T_r in columns [0, NB), T_i in [NB, 2 NB), K^d of pair p in [2 NB + NR p, 2 NB + NR (p + 1))
     constexpr uint32_t kCols = kTmemCols;
-    constexpr long kSpin = 1l << 24;
 
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
@@ -263,7 +263,11 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         s_max = 0u;   // read only after the barriers below
     }
     // ---- MMA1: T_r and T_i for all pairs (M = 128, N = NR kg, K = ngp) ----
-    bool ok = __syncthreads_and(tc::mbar_wait(&mbar[0], 0, kSpin)) != 0;
+    // a wait that gives up still lets the operation it waited for finish (the
+    // default limit) before the region is reused, TMEM is freed or the CTA exits
+    const bool got_w = tc::mbar_wait(&mbar[0], 0, spin);
+    if (!got_w) tc::mbar_wait(&mbar[0], 0, kMbarSpinLimit);
+    bool ok = __syncthreads_and(got_w) != 0;
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -290,7 +294,11 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
         chain(tmem + (uint32_t)NB, Wr, Rn, false);
         tc::mma_commit(&mbar[1]);
     }
-    ok = __syncthreads_and(ok && tc::mbar_wait(&mbar[1], 0, kSpin)) != 0;
+    {
+        const bool got = ok && tc::mbar_wait(&mbar[1], 0, spin);
+        if (ok && !got) tc::mbar_wait(&mbar[1], 0, kMbarSpinLimit);
+        ok = __syncthreads_and(got) != 0;
+    }
     tc::fence_after();
     // ---- T: TMEM -> scale -> split -> B2 (rows p*NR + vv'; K index Q for T_r, ngp + Q for T_i) ----
     int eT = 0;
@@ -365,7 +373,9 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float
             }
             tc::mma_commit(&mbar[2]);
         }
-        ok = __syncthreads_and(tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), kSpin)) != 0;
+        const bool got = tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), spin);
+        if (!got) tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), kMbarSpinLimit);
+        ok = __syncthreads_and(got) != 0;
         tc::fence_after();
     }
     // ---- epilogue: TMEM -> staging (A region) -> -K^d / V into the tile ----
@@ -483,7 +493,7 @@ int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaSt
 template <typename E>
 static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* wemb, const int* wexp, int ngp,
                               const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                              cudaStream_t st) {
+                              cudaStream_t st, long wait_polls) {
     int ngp2, kg = 1;
     size_t sm;
     BSE_TRY(tc_supported(s, ngp2, sm, &kg));
@@ -493,7 +503,8 @@ static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* w
     for (int64_t off = 0; off < ngroups; off += 1 << 30) {
         int64_t n = ngroups - off < (1 << 30) ? ngroups - off : (1 << 30);
         direct_tc_kernel<E><<<(unsigned)n, 256, sm, st>>>(s, (const float2*)coef32, (const E*)wemb, wexp, tasks,
-                                                          groups + off, ngp, kg, (float2*)X, status);
+                                                          groups + off, ngp, kg, (float2*)X, status,
+                                                          wait_limit(wait_polls, kMbarSpinLimit));
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc launch: %s", cudaGetErrorString(e));
@@ -503,10 +514,12 @@ static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* w
 
 int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
                      const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                     cudaStream_t st) {
+                     cudaStream_t st, long wait_polls) {
     if (ngroups == 0) return BSE_OK;
-    return fp16 ? launch_direct_tc_t<__half>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st)
-                : launch_direct_tc_t<__nv_bfloat16>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st);
+    return fp16 ? launch_direct_tc_t<__half>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st,
+                                             wait_polls)
+                : launch_direct_tc_t<__nv_bfloat16>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st,
+                                                    wait_polls);
 }
 
 }  // namespace bse

@@ -192,6 +192,16 @@ int build_mesh(Tables& t) {
             out[k] = (id[0] * n2 + id[1]) * n3 + id[2];
         }
     }
+    // folds G-bar_i = floor((R^{-T} f_k)_i), exactly: (R^{-T} f_k)_i = sum_j rk_ij x_j step_j / Nl
+    t.fold.assign((size_t)t.nops * t.nk * 3, 0);
+    for (int s = 0; s < t.nops; ++s)
+        for (int k = 0; k < t.nk; ++k)
+            for (int i = 0; i < 3; ++i) {
+                long num = 0;
+                for (int j = 0; j < 3; ++j) num += (long)t.rk[9 * s + 3 * i + j] * t.kidx[3 * k + j] * step[j];
+                const long fl = num >= 0 ? num / Nl : -((-num + Nl - 1) / Nl);
+                t.fold[((size_t)s * t.nk + k) * 3 + i] = (int32_t)fl;
+            }
     t.star_of.assign(t.nk, -1);
     t.star_rep.clear();
     t.stars.clear();

@@ -52,6 +52,7 @@ struct Tables {
     int identity = -1;
     std::vector<int32_t> kidx;        // [nk*3] mesh indices i, j, l
     std::vector<int32_t> rotk;        // [nops*nk]
+    std::vector<int32_t> fold;        // [nops*nk*3] G-bar = R^{-T} f_k - f_{sk}, integer
     std::vector<int32_t> star_of, star_rep, s_k, pos_in_star;
     std::vector<std::vector<int32_t>> stars;
     std::vector<int32_t> class_of;
@@ -176,6 +177,9 @@ int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, co
                  const int* ent, int64_t n_ent, double2* out, cudaStream_t st);
 int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands,
                     int exchange_layout, double2* out, cudaStream_t st);
+// the same in FP32 from the FP32 copy of the coefficients (pair layout only)
+int launch_pairdens32(const DevSys& s, const float2* coef32, const int* k, const int* kp, int64_t npairs, int bands,
+                      float2* out, cudaStream_t st);
 // direct term (direct.cu): prec32 = 0 -> FP64 (coef/w double2, X double2), 1 -> FP32 (float2)
 // direct term of the tasks of one or more systems: insts (device) holds the
 // systems, task.flags >> 1 indexes them; smax: any system's (nb, nv, nc,
@@ -268,9 +272,10 @@ void note_launch();
 int tc_supported(const DevSys& s, int& ngp, size_t& smem, int* kg = nullptr);
 // split-precision W(q) embeddings (fp16 != 0: fp16 hi + lo, else bf16) and their per-q scale exponents
 int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st);
+// wait_polls: polls of an mbarrier wait before it gives up (negative: the default)
 int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
                      const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                     cudaStream_t st);
+                     cudaStream_t st, long wait_polls = -1);
 int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
 int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
                          double2* H, int64_t ld, cudaStream_t st);
@@ -284,14 +289,17 @@ size_t tridiag_scratch_bytes(int64_t n);
 int tridiag_max_dim();
 int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st);
 // ev0 / ev1 (may be null) are recorded around the reduction kernel
+// wait_polls: polls of a grid barrier before it gives up (negative: the default)
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
-                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                            long wait_polls = -1);
 // lanczos.cu: the Lanczos recurrence on a Hermitian block from conj(b) (Lanczos-Haydock, Sec. IV)
 size_t lanczos_scratch_bytes(int64_t n, int m);
 int lanczos_max_dim();
 // steps: requested; on return *done (host) = steps performed, alpha [done], beta [done] (beta[j] couples j-1, j)
+// wait_polls: polls of a grid barrier before it gives up (negative: the default)
 int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, int steps, void* scratch,
-                   double** alpha, double** beta, int* done, cudaStream_t st);
+                   double** alpha, double** beta, int* done, cudaStream_t st, long wait_polls = -1);
 // T_m dense (k x k column-major) from alpha and beta1 (beta1[j] couples j, j + 1); Gauss weights
 // scale V[0][j]^2 from its eigenvector matrix V
 int launch_tm_dense(const double* alpha, const double* beta1, int k, double* T, cudaStream_t st);
@@ -319,6 +327,8 @@ int launch_wdiv(const double* recip_and_lattice, const int* n, const double* L, 
                 double delta, double* partial, int64_t npartial_max, double* out, cudaStream_t st, int nops = 0,
                 const int* Mx = nullptr, WdivScratch* sym_scratch = nullptr);
 int64_t wdiv_partials(const double* lattice, const int* n, double qmax, double delta);
+// points of one lattice column of that sum (the loop length of one thread)
+int64_t wdiv_column_length(const double* lattice, const int* n, double qmax, double delta);
 int launch_count_overlap(const DevSys& s, const PairTask* tasks, int64_t ntasks, unsigned long long* out,
                          cudaStream_t st);
 int64_t launches_total();

@@ -164,23 +164,27 @@ int launch_gamma(const DevSys& s, int nops, const int* rotk, const int* perm, co
 // pair densities (Eq. w_interaction in plane waves)
 // ---------------------------------------------------------------------------
 // shared-memory staging of one k pair: coefficients of both k and the
-// index table idx[g][j] = position of p'_j + Q_g in S_k (or -1).
+// index table idx[g][j] = position of p'_j + Q_g in S_k (or -1).  V is the
+// complex type of the coefficients (double2, or float2 for the FP32 copy the
+// mixed builds compute their pair densities from).
+template <typename V>
 struct PairStage {
-    double2* ck;    // [nb][npw_max]
-    double2* ckp;   // [nb][npw_max]
+    V* ck;          // [nb][npw_max]
+    V* ckp;         // [nb][npw_max]
     short* idx;     // [ng][npkp]
     int q, ng, npkp;
 };
 
-__device__ void stage_pair(const DevSys& S, int k, int kp, PairStage& P) {
+template <typename V>
+__device__ void stage_pair(const DevSys& S, const V* __restrict__ coef, int k, int kp, PairStage<V>& P) {
     int fold[3];
     P.q = mesh_minus(S, k, kp, fold);
     P.ng = S.ng[P.q];
     P.npkp = S.npw[kp];
     const int tot = S.nb * S.npw_max;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        P.ck[e] = S.coef[(int64_t)k * tot + e];
-        P.ckp[e] = S.coef[(int64_t)kp * tot + e];
+        P.ck[e] = coef[(int64_t)k * tot + e];
+        P.ckp[e] = coef[(int64_t)kp * tot + e];
     }
     const int* gq = S.gq + (int64_t)P.q * S.ng_max * 3;
     const int* gk = S.gk + (int64_t)kp * S.npw_max * 3;
@@ -191,35 +195,46 @@ __device__ void stage_pair(const DevSys& S, int k, int kp, PairStage& P) {
     }
 }
 
-// rho[a][b][g] for bands n = n_lo + a (a < nn), n' = np_lo + b (b < nnp)
-__device__ __forceinline__ double2 rho_elem(const DevSys& S, const PairStage& P, int n, int np_, int g) {
-    const double2* cn = P.ck + n * S.npw_max;
-    const double2* cp = P.ckp + np_ * S.npw_max;
+__device__ __forceinline__ void cfma_conj_any(double2& acc, double2 a, double2 b) { cfma_conj(acc, a, b); }
+__device__ __forceinline__ void cfma_conj_any(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+
+// rho[a][b][g] for bands n = n_lo + a (a < nn), n' = np_lo + b (b < nnp), in the precision of V
+template <typename V>
+__device__ __forceinline__ V rho_elem(const DevSys& S, const PairStage<V>& P, int n, int np_, int g) {
+    const V* cn = P.ck + n * S.npw_max;
+    const V* cp = P.ckp + np_ * S.npw_max;
     const short* row = P.idx + g * P.npkp;
-    double2 acc = make_double2(0.0, 0.0);
+    V acc;
+    acc.x = 0;
+    acc.y = 0;
     for (int j = 0; j < P.npkp; ++j) {
         int i = row[j];
-        if (i >= 0) cfma_conj(acc, cn[i], cp[j]);
+        if (i >= 0) cfma_conj_any(acc, cn[i], cp[j]);
     }
     return acc;
 }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t stage_bytes(int nb, int npw_max, int ng_max) {
-    return align16(sizeof(double2) * (size_t)nb * npw_max) * 2 + align16(sizeof(short) * (size_t)ng_max * npw_max);
+__host__ __device__ inline size_t stage_bytes(int cplx_bytes, int nb, int npw_max, int ng_max) {
+    return align16((size_t)cplx_bytes * nb * npw_max) * 2 + align16(sizeof(short) * (size_t)ng_max * npw_max);
 }
 
-__global__ void pairdens_kernel(DevSys S, const int* __restrict__ kk, const int* __restrict__ kpp, int bands,
-                                int exchange_layout, double2* out) {
+template <typename V>
+__global__ void pairdens_kernel(DevSys S, const V* __restrict__ coef, const int* __restrict__ kk,
+                                const int* __restrict__ kpp, int bands, int exchange_layout, V* out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PairStage P;
-    P.ck = (double2*)smem;
-    P.ckp = (double2*)(smem + align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
-    P.idx = (short*)(smem + 2 * align16(sizeof(double2) * (size_t)S.nb * S.npw_max));
+    PairStage<V> P;
+    const size_t cb = align16(sizeof(V) * (size_t)S.nb * S.npw_max);
+    P.ck = (V*)smem;
+    P.ckp = (V*)(smem + cb);
+    P.idx = (short*)(smem + 2 * cb);
     const int64_t pr = blockIdx.x;
     const int k = kk[pr], kp = kpp[pr];
-    stage_pair(S, k, kp, P);
+    stage_pair(S, coef, k, kp, P);
     __syncthreads();
     int n_lo, nn, np_lo, nnp;
     if (bands == BSE_BANDS_CC) { n_lo = S.nv; nn = S.nc; np_lo = S.nv; nnp = S.nc; }
@@ -227,10 +242,13 @@ __global__ void pairdens_kernel(DevSys S, const int* __restrict__ kk, const int*
     else { n_lo = S.nv; nn = S.nc; np_lo = 0; nnp = S.nv; }
     if (!exchange_layout) {
         const int tot = nn * nnp * S.ng_max;
-        double2* o = out + pr * (int64_t)tot;
+        V* o = out + pr * (int64_t)tot;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             int g = e % S.ng_max, ab = e / S.ng_max;
-            o[e] = g < P.ng ? rho_elem(S, P, n_lo + ab / nnp, np_lo + ab % nnp, g) : make_double2(0.0, 0.0);
+            V z;
+            z.x = 0;
+            z.y = 0;
+            o[e] = g < P.ng ? rho_elem(S, P, n_lo + ab / nnp, np_lo + ab % nnp, g) : z;
         }
     } else {
         // exchange vectors P[(k*nv + v)*nc + c][g] = m^k_cv(G_g), q = 0
@@ -244,17 +262,28 @@ __global__ void pairdens_kernel(DevSys S, const int* __restrict__ kk, const int*
     }
 }
 
-int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands, int exchange_layout,
-                    double2* out, cudaStream_t st) {
+template <typename V>
+static int launch_pairdens_t(const DevSys& s, const V* coef, const int* k, const int* kp, int64_t npairs, int bands,
+                             int exchange_layout, V* out, cudaStream_t st) {
     if (npairs == 0) return BSE_OK;
-    size_t sm = stage_bytes(s.nb, s.npw_max, s.ng_max);
+    size_t sm = stage_bytes((int)sizeof(V), s.nb, s.npw_max, s.ng_max);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(pairdens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(pairdens_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return fail(BSE_ECUDA, "pairdens smem %zu: %s", sm, cudaGetErrorString(e));
     }
-    pairdens_kernel<<<(unsigned)npairs, 256, sm, st>>>(s, k, kp, bands, exchange_layout, out);
+    pairdens_kernel<V><<<(unsigned)npairs, 256, sm, st>>>(s, coef, k, kp, bands, exchange_layout, out);
     LAUNCH_CHECK();
     return BSE_OK;
+}
+
+int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs, int bands, int exchange_layout,
+                    double2* out, cudaStream_t st) {
+    return launch_pairdens_t(s, s.coef, k, kp, npairs, bands, exchange_layout, out, st);
+}
+
+int launch_pairdens32(const DevSys& s, const float2* coef32, const int* k, const int* kp, int64_t npairs, int bands,
+                      float2* out, cudaStream_t st) {
+    return launch_pairdens_t(s, coef32, k, kp, npairs, bands, 0, out, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1021,11 +1050,21 @@ int launch_wdiv_finalize(const double* sum, double a, double b, double* w, cudaS
     return BSE_OK;
 }
 
+// extent of the integer coordinates X_j of the points Q = sum_j X_j b_j / n_j
+// with |Q| <= lim (clamped far above any mesh that is accepted, so that the
+// conversion cannot overflow)
 static void wdiv_extent(const double* lattice, const int* n, double lim, int e[3]) {
     for (int j = 0; j < 3; ++j) {
         double len = sqrt(lattice[j] * lattice[j] + lattice[3 + j] * lattice[3 + j] + lattice[6 + j] * lattice[6 + j]);
-        e[j] = (int)ceil(n[j] * lim * len / (2.0 * M_PI)) + 1;
+        const double x = ceil((double)n[j] * lim * len / (2.0 * M_PI)) + 1.0;
+        e[j] = x < (double)(1 << 28) ? (int)x : (1 << 28);
     }
+}
+
+int64_t wdiv_column_length(const double* lattice, const int* n, double qmax, double delta) {
+    int e[3];
+    wdiv_extent(lattice, n, qmax + delta, e);
+    return 2 * (int64_t)e[2] + 1;
 }
 
 size_t wdiv_sym_bytes(const double* lattice, const int* n, double qmax, double delta) {

@@ -78,6 +78,7 @@ struct LzArgs {
     int* done;          // steps performed
     unsigned* bar;      // barrier counter, zero on entry
     int* err;           // error flag, zero on entry
+    long spin;          // polls of a grid barrier before it gives up
 };
 
 __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
             }
         }
         block_part(p1, a.part1);
-        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
         const double al = grid_total(a.part1);
         // u_{j+1} = y - alpha_j v_j on own columns (the thread that wrote y)
         double p2 = 0.0;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) lanczos_kernel(LzArgs a) {
                 p2 = fma(y.x, y.x, fma(y.y, y.y, p2));
             }
         block_part(p2, a.part2);
-        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
         const double bn = sqrt(grid_total(a.part2));
         if (blk == 0 && tid == 0) {
             a.alpha[j] = al;
@@ -260,7 +261,7 @@ size_t lanczos_scratch_bytes(int64_t n, int m) {
 }
 
 int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, int steps, void* scratch,
-                   double** alpha, double** beta, int* done, cudaStream_t st) {
+                   double** alpha, double** beta, int* done, cudaStream_t st, long wait_polls) {
     if (n < 1 || n > lanczos_max_dim())
         return fail(BSE_EUNSUPPORTED, "Lanczos path: block dimension %lld (at most %d)", (long long)n, lanczos_max_dim());
     if (steps < 1) return fail(BSE_EINVAL, "Lanczos path: %d steps", steps);
@@ -307,6 +308,7 @@ int launch_lanczos(const double2* h, int64_t ld, int64_t n, const double2* b, in
     a.done = dn;
     a.bar = bar;
     a.err = err;
+    a.spin = wait_limit(wait_polls, kGridSpinLimit);
     void* args[] = {&a};
     BSE_CUDA(cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(G), dim3(kLzThreads), args, dyn, st));
     note_launch();

@@ -26,6 +26,9 @@ using namespace bse;
 // block).  65536 doubles = 512 KiB, resident on every device that loads the
 // library until the process exits.
 #define BSE_NOALLOC_MAX_PARTIALS 65536
+// Longest lattice column one thread sums (points along the third axis); far
+// above what any mesh within the partial-sum limit needs
+#define BSE_NOALLOC_MAX_COLUMN 65536
 
 static __device__ __align__(256) double g_noalloc_partials[BSE_NOALLOC_MAX_PARTIALS];
 
@@ -50,7 +53,10 @@ static int noalloc_scratch(double** out) {
     return BSE_OK;
 }
 
-// w = c0 - c1 * w, rounded like the host expression (no contraction)
+// w = c0 - c1 * w with both operations rounded separately.  The result agrees
+// with the W^div of bse_create to about 1e-10 relative, not bit for bit:
+// bse_create sums one point per orbit of the point group (weighted by the
+// orbit size) and may round its last step differently.
 __global__ void noalloc_finalize_kernel(double* w, double c0, double c1) { w[0] = __dsub_rn(c0, __dmul_rn(c1, w[0])); }
 
 extern "C" int bse_head_correction_noalloc(const double* lattice, const int32_t* mesh, const double* eps_inf,
@@ -74,14 +80,19 @@ extern "C" int bse_head_correction_noalloc(const double* lattice, const int32_t*
     for (int i = 0; i < 9; ++i) rl[9 + i] = L[i];
     const int n[3] = {mesh[0], mesh[1], mesh[2]};
     const double v_uc = std::fabs(det);
-    const int nk = n[0] * n[1] * n[2];
+    const int64_t nk = (int64_t)n[0] * n[1] * n[2];
+    if (nk > INT32_MAX) return fail(BSE_EINVAL, "mesh has %lld points, more than 2^31 - 1", (long long)nk);
     const double b = 0.005;
     const double qmax = std::sqrt(-std::log(b) / b);
-    const double delta = std::cbrt(8.0 * M_PI * M_PI * M_PI / v_uc / nk);
+    const double delta = std::cbrt(8.0 * M_PI * M_PI * M_PI / v_uc / (double)nk);
     const int64_t need = wdiv_partials(L, n, qmax, delta);
     if (need > BSE_NOALLOC_MAX_PARTIALS)
         return fail(BSE_EINVAL, "mesh too fine for the fixed scratch: the lattice sum needs %lld partial sums, "
                     "at most %d are available", (long long)need, BSE_NOALLOC_MAX_PARTIALS);
+    const int64_t col = wdiv_column_length(L, n, qmax, delta);
+    if (col > BSE_NOALLOC_MAX_COLUMN)
+        return fail(BSE_EINVAL, "mesh too fine along its third axis: a lattice column has %lld points, at most %d",
+                    (long long)col, BSE_NOALLOC_MAX_COLUMN);
     double* scratch = nullptr;
     BSE_TRY(noalloc_scratch(&scratch));
     cudaStream_t st = (cudaStream_t)stream;
@@ -89,7 +100,8 @@ extern "C" int bse_head_correction_noalloc(const double* lattice, const int32_t*
     // kernel of this call, so no part of the scratch has to start at zero
     BSE_TRY(launch_wdiv(rl, n, eps_inf, b, qmax, delta, scratch, BSE_NOALLOC_MAX_PARTIALS, w_div_dev, st));
     const double integral = M_PI * head_h00(eps_inf) / std::sqrt(b) * std::erf(std::sqrt(b) * qmax);
-    noalloc_finalize_kernel<<<1, 1, 0, st>>>(w_div_dev, integral / (2.0 * M_PI * M_PI), 4.0 * M_PI / (nk * v_uc));
+    noalloc_finalize_kernel<<<1, 1, 0, st>>>(w_div_dev, integral / (2.0 * M_PI * M_PI),
+                                             4.0 * M_PI / ((double)nk * v_uc));
     BSE_CUDA(cudaGetLastError());
     return BSE_OK;
 }

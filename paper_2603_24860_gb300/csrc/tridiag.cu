@@ -107,6 +107,7 @@ struct TriArgs {
     double* e;            // [n] off-diagonal of T (e[n-1] unused)
     unsigned* bar;        // barrier counter, zero on entry
     int* err;             // error flag, zero on entry
+    long spin;            // polls of a grid barrier before it gives up
 };
 
 // Reflector k from alpha = (column k)_{k+1} and sigma = sum_{r>k+1} |(column k)_r|^2
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
     };
 
     dots(-1, V);
-    if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+    if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
 
     for (int s = -1; s <= n - 2; ++s) {
         const int k = s + 1;   // first row of this step's reflector, column reflected next
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
         cdf* t = V;
         V = C;
         C = t;
-        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag)) return;
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
     }
     __syncthreads();
     if ((n - 1) % G == blk && tid == 0) {
@@ -798,7 +799,8 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // Reduce the block h (n x n, ld n, device; overwritten in the global-memory
 // variant) to T after the start reflector of b, then levels and weights.
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
-                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+                            double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                            long wait_polls) {
     if (n < 1 || n > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld", (long long)n);
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) {
@@ -856,6 +858,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     a.e = e;
     a.bar = bar;
     a.err = err;
+    a.spin = wait_limit(wait_polls, kGridSpinLimit);
     void* args[] = {&a};
     const size_t dyn = vec_bytes + (smem ? cols_bytes : 0);
     const void* fn = smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;

@@ -54,6 +54,7 @@ class Config:
     gamma: float = 0.1       # strength of local-field terms
     n_omega: int = 4001
     a: float | None = None   # lattice constant override (bohr)
+    eps_inf_z: float | None = None   # zz element of the dielectric tensor of the head correction, if uniaxial
 
 
 CONFIGS = {
@@ -73,6 +74,9 @@ CONFIGS = {
                    eta_ev=0.18),
     "mos2_331": Config("mos2_331", "MoS2", (3, 3, 1), 2, 2, Fr(93, 50), 1.9, 15.0,
                        SEED_BASE + 14, eta_ev=0.05),
+    # the same cell with a uniaxial dielectric tensor diag(15, 15, 6) in the head correction
+    "mos2_331_uni": Config("mos2_331_uni", "MoS2", (3, 3, 1), 2, 2, Fr(93, 50), 1.9, 15.0,
+                           SEED_BASE + 14, eta_ev=0.05, eps_inf_z=6.0),
 }
 
 
@@ -316,7 +320,7 @@ def _generate(cfg: Config) -> dict:
         ng_count=ng.astype(np.int32),
         gq=gk.copy(),
         w=w,
-        eps_inf=np.eye(3) * cfg.eps_inf,
+        eps_inf=np.diag([cfg.eps_inf, cfg.eps_inf, cfg.eps_inf if cfg.eps_inf_z is None else cfg.eps_inf_z]),
         qhat=np.array(cfg.qhat, dtype=np.float64),
         scissor=0.0,
         spin_factor=2,

@@ -2,7 +2,7 @@
 configuration as computed by the CPU oracle (oracle.hamiltonian.head_correction,
 Eqs. Wdiv, divergence_int, divergence_sum).  Calls only the oracle and the
 input generator.  Run from the repository root:
-    python tests/golden/make_wdiv.py si2 si4 lif4 mos2_331 si8 si12 lif10
+    python tests/golden/make_wdiv.py si2 si4 lif4 mos2_331 mos2_331_uni si8 si12 lif10
 """
 import json
 import os

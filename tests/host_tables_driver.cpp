@@ -8,7 +8,8 @@
 // output (binary): nk, n_ops, n_stars, n_irreps i32; N, n_orbits i64;
 //                  rotk i32[n_ops nk], star_of i32[nk], star_rep i32[n_stars],
 //                  s_k i32[nk], class_of i32[n_ops], chi i32[n_irreps n_ops],
-//                  irrep_dim i32[n_irreps], bright i32[n_irreps], orbit_of i32[N]
+//                  irrep_dim i32[n_irreps], bright i32[n_irreps], orbit_of i32[N],
+//                  fold i32[n_ops nk 3]
 // With a third and fourth argument (band rotations in, bases out), the
 // driver also builds the bases from given band rotations Gamma(s): complex
 // f64 [n_ops][gam_per_s] in the library's layout (per k the multiplet blocks,
@@ -154,6 +155,7 @@ int main(int argc, char** argv) {
     put(o, t.irrep_dim.data(), t.irrep_dim.size());
     put(o, t.bright.data(), t.bright.size());
     put(o, t.orbit_of.data(), t.orbit_of.size());
+    put(o, t.fold.data(), t.fold.size());
     fclose(o);
     return argc == 5 ? write_bases(t, argv[3], argv[4]) : 0;
 }

@@ -60,9 +60,15 @@ def test_tables_bit_exact(gpu, name):
         orb[mem] = o
     assert np.array_equal(t["orbit_of"], orb)
     assert t["n_orbits"] == len(b.orbits)
+    # folds of the rotated mesh points (Eq. sk) and the coset spheres S_k, S_q
+    assert np.array_equal(t["fold"], mt.fold)
+    assert np.array_equal(t["npw"], d["nk_count"]) and np.array_equal(t["ng"], d["ng_count"])
+    for k in range(inp.nk):
+        assert np.array_equal(t["gk"][k, :t["npw"][k]], np.asarray(d["gk"])[k, :d["nk_count"][k]])
+        assert np.array_equal(t["gq"][k, :t["ng"][k]], np.asarray(d["gq"])[k, :d["ng_count"][k]])
 
 
-@pytest.mark.parametrize("name", ["si2", "si4", "lif4", "mos2_331", "si8", "lif10"])
+@pytest.mark.parametrize("name", ["si2", "si4", "lif4", "mos2_331", "mos2_331_uni", "si8", "lif10"])
 def test_head_correction(gpu, name):
     bse, torch, get = gpu
     w = bse.bse_tables(get(name))["w_div"]
@@ -90,6 +96,16 @@ def test_pair_densities(gpu, name, bands):
         ng = ref.shape[2]
         assert np.abs(got[i, :, :, :ng] - ref).max() < 1e-13
         assert np.all(got[i, :, :, ng:] == 0)
+    # the FP32 densities of the mixed builds (FP32 coefficients, FP32 sums of about 50 terms)
+    for prec in (bse.BSE_FP32, bse.BSE_FP16_SPLIT):
+        out32 = torch.zeros((len(k), n, npr, ngmax), dtype=torch.complex64, device="cuda")
+        bse.bse_pairdens(get(name), k, kp, bands, out32, prec=prec)
+        got32 = out32.cpu().numpy()
+        for i in range(len(k)):
+            ref, q = pair_density(inp, mt, int(k[i]), int(kp[i]), *sets[bands])
+            ng = ref.shape[2]
+            assert np.abs(got32[i, :, :, :ng] - ref).max() < 2e-6
+            assert np.all(got32[i, :, :, ng:] == 0)
 
 
 @pytest.mark.parametrize("name", SMALL)
@@ -646,3 +662,20 @@ def test_loss_spectrum(gpu, name):
         assert abs(gw.sum() - os_.cpu().numpy().sum()) <= 1e-9 * scale
         checked += 1
     assert checked >= 1
+
+
+def test_blocks_uniaxial_head_correction(gpu):
+    """The MoS2-like cell with a uniaxial dielectric tensor diag(15, 15, 6):
+    the library's H00 (Gauss-Legendre quadrature of Eq. hinv0) and orbit sum
+    enter the diagonal of every block exactly as the oracle's W^div does."""
+    from oracle.projection import project
+    bse, torch, get = gpu
+    d, inp, grp, mt, b = oracle_case("mos2_331_uni")
+    assert abs(bse.bse_tables(get("mos2_331_uni"))["w_div"] - GOLD["mos2_331_uni"]) <= TOL * GOLD["mos2_331_uni"]
+    H = oracle_h("mos2_331_uni")
+    for mu in range(len(b.dims)):
+        U, _ = b.basis(mu)
+        if U.shape[1] == 0:
+            continue
+        got = bse.block(get("mos2_331_uni"), mu).cpu().numpy()
+        assert _rel(got, project(U, H)) <= TOL, mu

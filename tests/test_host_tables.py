@@ -67,6 +67,7 @@ def _run(driver, d, tmp):
          "star_rep": take(np.int32, nstars), "s_k": take(np.int32, nk), "class_of": take(np.int32, nops),
          "chi": take(np.int32, nirr * nops).reshape(nirr, nops), "irrep_dim": take(np.int32, nirr),
          "bright": take(np.int32, nirr), "orbit_of": take(np.int32, N), "n_orbits": int(norb)}
+    t["fold"] = take(np.int32, nops * nk * 3).reshape(nops, nk, 3)
     assert pos == len(raw)
     return t
 
@@ -79,6 +80,7 @@ def test_host_tables_match_the_oracle(driver, tmp_path, name):
     mt = MeshTables(grp, d["mesh"])
     chi, dims, cls = grp.characters()
     assert np.array_equal(t["rotk"], mt.rotk)
+    assert np.array_equal(t["fold"], mt.fold)
     assert np.array_equal(t["star_of"], mt.star_of)
     assert np.array_equal(t["star_rep"], mt.star_rep)
     assert np.array_equal(t["s_k"], mt.s_k)

@@ -74,3 +74,27 @@ def test_head_correction_limit():
     w4 = hm.head_correction(inp4)
     assert 0 < w4 < w2
     assert abs(w2 / w4 - 2.0) < 0.2
+
+
+def test_sum_brute_force_uniaxial():
+    """The lattice sum with a uniaxial dielectric tensor (Q^T L Q in the
+    denominator, Eq. divergence_sum) equals a plain loop over mesh points."""
+    d, inp, grp, mt, b = oracle_case("mos2_331_uni")
+    L = inp.eps_inf
+    assert L[0, 0] != L[2, 2]
+    bb = 0.5
+    qm = hm.q_max(bb)
+    delta = (8 * math.pi ** 3 / inp.v_uc / inp.nk) ** (1 / 3)
+    n = np.array(inp.mesh)
+    tot = 0.0
+    r = 12
+    for x in itertools.product(range(-r, r + 1), repeat=3):
+        if x == (0, 0, 0):
+            continue
+        Q = inp.recip @ (np.array(x) / n)
+        q = math.sqrt(Q @ Q)
+        if q > qm + delta:
+            continue
+        w = 1.0 if q < qm - delta else hm.smooth((q - qm) / delta)
+        tot += math.exp(-bb * q * q) / (Q @ L @ Q) * w
+    assert abs(hm.divergence_sum(inp, bb) - tot) < 1e-13 * tot

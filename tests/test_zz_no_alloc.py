@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-@pytest.mark.parametrize("name", ["si4", "mos2_331", "si8"])
+@pytest.mark.parametrize("name", ["si4", "mos2_331", "mos2_331_uni", "si8"])
 def test_noalloc_matches_create_twice(name):
     import torch
     from paper_2603_24860_gb300 import bse
@@ -43,3 +43,9 @@ def test_noalloc_rejects_meshes_beyond_the_fixed_scratch():
         bse.bse_head_correction_noalloc(d["lattice"], [64, 64, 64], d["eps_inf"], out)
     assert e.value.code == bse.BSE_EINVAL
     assert "fixed scratch" in str(e.value)
+    # a mesh whose point count overflows 32 bits, and one whose lattice columns
+    # (third axis) are too long for one thread, are rejected before any launch
+    for mesh in ([2, 1, 1 << 30], [1, 1, 1 << 20]):
+        with pytest.raises(bse.BseError) as e:
+            bse.bse_head_correction_noalloc(d["lattice"], mesh, d["eps_inf"], out)
+        assert e.value.code == bse.BSE_EINVAL
