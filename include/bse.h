@@ -398,14 +398,21 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      pipe: levels within about n 2^-47 ||H_mu||, for
  *                      blocks whose entries lie below 2^50 in magnitude
  *                      (FP32's exponent range; Hartree-unit blocks are far
- *                      inside it).  Needs the partners'
+ *                      inside it).  Blocks of up to about 1200 rows are
+ *                      reduced in shared memory (a column per CTA); larger
+ *                      ones, with their columns in device memory, by a
+ *                      blocked form of the same reduction (panels of 32
+ *                      reflectors: one pass of column dot products per step,
+ *                      the panel's rank-64 update at its end).  Needs the partners'
  *                      projections b_i to be parallel (true for the partner
- *                      blocks of bse_partner_spectrum) and n <= 4736; the
+ *                      blocks of bse_partner_spectrum) and n <= 8192; the
  *                      sum of the weights must come out as 1 within 1e-8.
  *                      Otherwise the spectrum call fails (EUNSUPPORTED or
  *                      ESOLVER).  Exactly degenerate levels (the d_mu
  *                      copies in a whole block of a d_mu-dimensional irrep)
  *                      break the last condition.
+ *   BSE_SOLVER_TRIDIAG_BLOCKED  as TRIDIAG with the blocked reduction at
+ *                      every size (for checks and measurements).
  *   BSE_SOLVER_AUTO    (default) TRIDIAG for partner blocks, for blocks
  *                      of one-dimensional irreps and for blocks of irreps
  *                      outside the polar-vector representation (B_mu = 0
@@ -413,7 +420,7 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      otherwise and whenever a TRIDIAG condition fails.
  * bse_stats.solver reports the solver the last spectrum used.
  */
-enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2 };
+enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2, BSE_SOLVER_TRIDIAG_BLOCKED = 3 };
 
 /*
  * bse_set_seeds - direct term by seeds (on, the default) or pair by pair.

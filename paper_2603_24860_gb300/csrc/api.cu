@@ -1901,7 +1901,8 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[3], c->stream));
     BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
                                     c->triScratch.p, omega_out, osc, wsum, err, c->stream,
-                                    c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls));
+                                    c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls,
+                                    c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ? 1 : 0));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     struct {
         double s;
@@ -1933,7 +1934,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
         BSE_TRY(launch_bmu(dev_basis_of(c, parts[p]), (const double2*)c->B.p, (double2*)c->Bmu.p + (size_t)p * dim,
                            c->stream));
     const double pref = 4.0 * M_PI * c->spin / c->t.nk;
-    const bool try_tri = c->solver_mode == BSE_SOLVER_TRIDIAG ||
+    const bool try_tri = c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
                          (c->solver_mode == BSE_SOLVER_AUTO && (nparts > 1 || irrep_dim == 1 || dark) &&
                           dim <= tridiag_max_dim());
     if (try_tri) {
@@ -1951,7 +1952,9 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
             c->stats.solver = BSE_SOLVER_TRIDIAG;
             return BSE_OK;
         }
-        if (c->solver_mode == BSE_SOLVER_TRIDIAG || rc == BSE_ETIMEOUT || rc == BSE_ECUDA) return rc;
+        if (c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
+            rc == BSE_ETIMEOUT || rc == BSE_ECUDA)
+            return rc;
         clear_error();
     }
     BSE_TRY(ensure(c->eigA, sizeof(double2) * (size_t)dim * dim));
@@ -2125,7 +2128,8 @@ int bse_loss_spectrum(bse_ctx* c, int64_t n, const double* omega_levels, const d
 int bse_set_solver(bse_ctx* c, int32_t solver) {
     clear_error();
     if (!c) return fail(BSE_EINVAL, "null argument");
-    if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG)
+    if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG &&
+        solver != BSE_SOLVER_TRIDIAG_BLOCKED)
         return fail(BSE_EINVAL, "unknown solver %d", solver);
     c->solver_mode = solver;
     return BSE_OK;

@@ -364,6 +364,374 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked reduction for blocks whose columns live in global memory.
+//
+// The same reflectors as tridiag_kernel, applied in panels of kNb: within a
+// panel the trailing matrix A is left as it was at the panel's start, and the
+// reflectors' two-sided updates A_cur = A - sum_l (v_l w_l^H + w_l v_l^H) are
+// carried as corrections.  Step s (reflector s acts on rows > s; s = -1 is the
+// start reflector on all rows), with l reflectors of the panel before it:
+//   phase 1  reflector s from the current column s (published in phase 2 of
+//            step s - 1); z_i = sum_r conj(A[r,i]) v_r for own columns i > s
+//            (A Hermitian: (A v)_i is a column dot product), started on the
+//            unscaled column while one warp forms the reflector's scalars;
+//            s1_b = W_b^H v, s2_b = V_b^H v by CTAs b < 2 l
+//   grid barrier
+//   phase 2  y = tau (z - V s1 - W s2), alpha = -tau/2 y^H v with
+//            y^H v = conj(tau) (z^H v - 2 Re s1^H s2); w = y + alpha v for own
+//            indices, stored as column l of W (v as column l of V); the
+//            current column k = s + 1 on own rows, A[:,k] - sum_{l' <= l}
+//            (V_l' conj(W[k,l']) + W_l' conj(V[k,l'])), published with its
+//            squared norm below row k + 1
+//   grid barrier
+//   panel end: A -= V W^H + W V^H on own columns and the trailing rows
+//            (rank 2 kNb, register-blocked, double-float on the FP32 pipe)
+// Per step the trailing matrix is read once (the dot products) instead of
+// being read, written and read again by a rank-2 update and the dot products.
+// ---------------------------------------------------------------------------
+constexpr int kNb = 32;           // reflectors per panel
+constexpr int kHerCols = 8;       // own columns updated together in the panel-end update
+
+struct TriBArgs {
+    cdf* A;               // n x n column-major; the FP64 block on entry, rewritten in place in double-float
+    int64_t n;
+    const double2* v0;    // start reflector (all rows) and its scalar
+    const double* beta0;
+    cdf* V;               // [kNb][n] the panel's reflectors: row i of reflector l at l * n + i
+    cdf* W;               // [kNb][n] their w vectors
+    cdf* ncol;            // [n] the current column of the next reflector (rows >= its index)
+    float2* npart;        // [G] per-CTA parts of its squared norm below the subdiagonal
+    cdf* zbuf;            // [n] z_i of the step
+    cdf* zpart;           // [G] per-CTA parts of z^H v
+    cdf* sdot;            // [2 kNb] s1 (first kNb entries) and s2
+    double* d;            // [n] diagonal of T
+    double* e;            // [n] off-diagonal of T
+    unsigned* bar;        // barrier counter, zero on entry
+    int* err;             // error flag, zero on entry
+    long spin;            // polls of a grid barrier before it gives up
+};
+
+// dynamic shared memory of the blocked kernel (cdf units): the staged column
+// (n), the panel-end coefficients of own columns (ncl x 2 kNb), own z, v, w
+// (3 ncl), s1, s2 and the current column's coefficients (4 (kNb + 1))
+__host__ __device__ inline size_t tri_blocked_smem(int64_t n, int G) {
+    const int64_t ncl = (n + G - 1) / G;
+    return sizeof(cdf) * (size_t)(n + ncl * 2 * kNb + 3 * ncl + 4 * (kNb + 1)) + 64;
+}
+
+// sum_{r >= r0} conj(x[r]) c[r] over a column x in global memory (lanes over rows,
+// four rows' loads in flight per lane), reduced over the warp
+__device__ __forceinline__ cdf warp_coldot(const cdf* __restrict__ x, const cdf* c, int r0, int n, int lane) {
+    cdf acc = cdf_zero(), acc2 = cdf_zero();
+    int r = r0 + lane;
+    for (; r + 96 < n; r += 128) {
+        const cdf a0 = x[r], a1 = x[r + 32], a2 = x[r + 64], a3 = x[r + 96];
+        acc = cdf_dot_acc(acc, a0, c[r]);
+        acc2 = cdf_dot_acc(acc2, a1, c[r + 32]);
+        acc = cdf_dot_acc(acc, a2, c[r + 64]);
+        acc2 = cdf_dot_acc(acc2, a3, c[r + 96]);
+    }
+    for (; r < n; r += 32) acc = cdf_dot_acc(acc, x[r], c[r]);
+    return cdf_warp_sum(cdf_add(acc, acc2));
+}
+
+__device__ __forceinline__ cdf cdf_conj(cdf a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+
+__global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArgs a) {
+    extern __shared__ __align__(16) cdf s_dyn[];
+    __shared__ cdf s_tau, s_inv, s_alpha, s_red[kTriWarps];
+    __shared__ cdf s_raw[2 * kNb];   // unscaled s dots of this CTA
+    __shared__ float2 s_nrm[kTriWarps];
+    __shared__ int s_next, s_flag;
+
+    const int n = (int)a.n;
+    const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;
+    cdf* Cs = s_dyn;                                   // [n] the staged column (or v0)
+    cdf* coef = Cs + n;                                // [ncl][2 kNb] W[i,l], V[i,l] of own columns (panel end)
+    cdf* zown = coef + (size_t)ncl * 2 * kNb;          // [ncl]
+    cdf* vown = zown + ncl;                            // [ncl]
+    cdf* wown = vown + ncl;                            // [ncl]
+    cdf* s12 = wown + ncl;                             // [2 (kNb + 1)]: s1 then s2
+    cdf* cwv = s12 + 2 * (kNb + 1);                    // [2 (kNb + 1)]: W[k,l'] then V[k,l']
+    cdf* gA = a.A;
+    auto col = [&](int i) -> cdf* { return gA + (size_t)i * n; };
+
+    // own columns in double-float, in place (same 16 bytes per element)
+    for (int m = 0; m < ncl; ++m) {
+        const double2* src = reinterpret_cast<const double2*>(col(blk + m * G));
+        cdf* dst = col(blk + m * G);
+        for (int r = tid; r < n; r += kTriThreads) {
+            const double2 z = src[r];
+            dst[r] = cdf_from(z);
+        }
+    }
+    unsigned nbar = 0;
+
+    for (int s = -1; s <= n - 2; ++s) {
+        const int k = s + 1;
+        const int l = (s + 1) % kNb;     // reflectors of the panel before this one
+        // ---------------- phase 1 ----------------
+        // stage the current column (rows >= s) or the start reflector
+        if (s < 0) {
+            for (int r = tid; r < n; r += kTriThreads) Cs[r] = cdf_from(__ldcg(a.v0 + r));
+        } else {
+            for (int r = s + tid; r < n; r += kTriThreads) Cs[r] = __ldcg(a.ncol + r);
+        }
+        if (tid == 0) s_next = 0;
+        __syncthreads();
+        // own columns i > s, then the dots s_q, q = blk, blk + G, ... < 2 l
+        const int m0 = blk > s ? 0 : (s - blk) / G + 1;
+        const int nown = ncl - m0;
+        const int nsq = blk < 2 * l ? (2 * l - 1 - blk) / G + 1 : 0;
+        const int ntask = nown + nsq;
+        const int r0 = s < 0 ? 0 : s + 2;
+        if (wid == 0 && s >= 0) {   // the reflector's scalars (zlarfg convention, v_{s+1} = 1)
+            float2 sg = make_float2(0.f, 0.f);
+            for (int b = lane; b < G; b += 32) sg = df_add(sg, __ldcg(a.npart + b));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                sg = df_add(sg, make_float2(__shfl_xor_sync(0xffffffffu, sg.x, o), __shfl_xor_sync(0xffffffffu, sg.y, o)));
+            if (lane == 0) {
+                cdf tau, inv;
+                float2 beta;
+                reflector(Cs[s + 1], sg, tau, inv, beta);
+                s_tau = tau;
+                s_inv = inv;
+                if (blk == 0) {
+                    a.d[s] = df_to(make_float2(Cs[s].x, Cs[s].y));
+                    a.e[s] = df_to(beta);
+                }
+            }
+            __syncwarp();
+        } else if (tid == 0 && s < 0) {
+            s_tau = cdf_from(make_double2(__ldcg(a.beta0), 0.0));
+            s_inv = make_float4(1.f, 0.f, 0.f, 0.f);
+        }
+        // dot tasks, taken dynamically (warp 0 joins once the reflector is done)
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_next, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= ntask) break;
+            if (t < nown) {
+                const int m = m0 + t;
+                const cdf* x = col(blk + m * G);
+                cdf zr = warp_coldot(x, Cs, r0, n, lane);
+                // completed below once the reflector's scalars are known:
+                // z = conj(A[s+1, i]) + inv zr (s >= 0); z = zr for the start reflector
+                if (lane == 0) zown[m] = zr;
+            } else {
+                const int q = blk + (t - nown) * G;   // s1_q (q < l) or s2_{q - l}
+                const cdf* x = q < l ? a.W + (size_t)q * n : a.V + (size_t)(q - l) * n;
+                cdf sr = warp_coldot(x, Cs, r0, n, lane);
+                if (lane == 0) s_raw[q] = sr;
+            }
+        }
+        __syncthreads();
+        {
+            const cdf tau = s_tau, inv = s_inv;
+            float sr_ = 0.f, lr_ = 0.f, si_ = 0.f, li_ = 0.f;   // this thread's part of z^H v
+            for (int m = m0 + tid; m < ncl; m += kTriThreads) {
+                const int i = blk + m * G;
+                cdf z = zown[m];
+                cdf v;
+                if (s >= 0) {
+                    z = cdf_fma(cdf_conj(col(i)[s + 1]), inv, z);   // conj(A[s+1,i]) + inv zr
+                    v = i == s + 1 ? make_float4(1.f, 0.f, 0.f, 0.f) : cdf_mul(Cs[i], inv);
+                } else {
+                    v = Cs[i];
+                }
+                zown[m] = z;
+                vown[m] = v;
+                a.zbuf[i] = z;
+                // conj(z) v
+                df_acc(sr_, lr_, z.x, z.y, v.x, v.y);
+                df_acc(sr_, lr_, z.z, z.w, v.z, v.w);
+                df_acc(si_, li_, z.x, z.y, v.z, v.w);
+                df_acc(si_, li_, -z.z, -z.w, v.x, v.y);
+            }
+            float2 pr = df_fin(sr_, lr_), pi = df_fin(si_, li_);
+            cdf part = cdf_warp_sum(make_float4(pr.x, pr.y, pi.x, pi.y));
+            if (lane == 0) s_red[wid] = part;
+            if (tid < nsq) {
+                const int q = blk + tid * G;
+                const cdf sr = s_raw[q];
+                const cdf* x = q < l ? a.W + (size_t)q * n : a.V + (size_t)(q - l) * n;
+                // s_q = conj(X[s+1]) + inv sr (s >= 0)
+                a.sdot[q < l ? q : kNb + q - l] = s >= 0 ? cdf_fma(cdf_conj(x[s + 1]), inv, sr) : sr;
+            }
+            (void)tau;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            cdf sp = s_red[0];
+            for (int w = 1; w < kTriWarps; ++w) sp = cdf_add(sp, s_red[w]);
+            a.zpart[blk] = sp;
+        }
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
+
+        // ---------------- phase 2 ----------------
+        const cdf tau = s_tau;
+        if (wid == 0) {
+            cdf zv = cdf_zero();
+            for (int b = lane; b < G; b += 32) zv = cdf_add(zv, __ldcg(a.zpart + b));
+            zv = cdf_warp_sum(zv);
+            // s1, s2 of the panel's earlier reflectors and Re s1^H s2
+            cdf s1 = cdf_zero(), s2 = cdf_zero();
+            if (lane < l) {
+                s1 = __ldcg(a.sdot + lane);
+                s2 = __ldcg(a.sdot + kNb + lane);
+                s12[lane] = s1;
+                s12[kNb + 1 + lane] = s2;
+            }
+            cdf cr = cdf_dot_acc(cdf_zero(), s1, s2);   // conj(s1) s2
+            cr = cdf_warp_sum(cr);
+            if (lane == 0) {
+                // y^H v = conj(tau) (z^H v - 2 Re s1^H s2); alpha = -tau/2 y^H v
+                const cdf zc = make_float4(zv.x, zv.y, zv.z, zv.w);
+                const float2 two_re = df_add(make_float2(cr.x, cr.y), make_float2(cr.x, cr.y));
+                const cdf d0 = cdf_add(zc, make_float4(-two_re.x, -two_re.y, 0.f, 0.f));
+                const cdf yv = cdf_mul(cdf_conj(tau), d0);
+                const cdf al = cdf_mul(tau, yv);
+                s_alpha = make_float4(-0.5f * al.x, -0.5f * al.y, -0.5f * al.z, -0.5f * al.w);
+            }
+        }
+        __syncthreads();
+        const cdf alpha = s_alpha;
+        // own indices i > s: corr_i = sum_{l' < l} V[i,l'] s1_l' + W[i,l'] s2_l' (lanes over l'),
+        // y_i = tau (z_i - corr_i), w_i = y_i + alpha v_i; column l of V and W
+        for (int m = m0 + wid; m < ncl; m += kTriWarps) {
+            const int i = blk + m * G;
+            cdf c = cdf_zero();
+            if (lane < l) {
+                c = cdf_mul(__ldcg(a.V + (size_t)lane * n + i), s12[lane]);
+                c = cdf_fma(c, __ldcg(a.W + (size_t)lane * n + i), s12[kNb + 1 + lane]);
+            }
+            c = cdf_warp_sum(c);
+            if (lane == 0) {
+                const cdf zc = zown[m];
+                const cdf y = cdf_mul(tau, cdf_add(zc, make_float4(-c.x, -c.y, -c.z, -c.w)));
+                const cdf w = cdf_fma(y, alpha, vown[m]);
+                wown[m] = w;
+                a.W[(size_t)l * n + i] = w;
+                a.V[(size_t)l * n + i] = vown[m];
+            }
+        }
+        // W[k,l] and V[k,l] of the current column's index k, redundantly in every CTA (last warp)
+        if (k <= n - 1 && wid == kTriWarps - 1) {
+            cdf c = cdf_zero(), wl = cdf_zero(), vl = cdf_zero();
+            if (lane < l) {
+                vl = __ldcg(a.V + (size_t)lane * n + k);
+                wl = __ldcg(a.W + (size_t)lane * n + k);
+                c = cdf_mul(vl, s12[lane]);
+                c = cdf_fma(c, wl, s12[kNb + 1 + lane]);
+                cwv[lane] = wl;
+                cwv[kNb + 1 + lane] = vl;
+            }
+            c = cdf_warp_sum(c);
+            if (lane == 0) {
+                const cdf zk = __ldcg(a.zbuf + k);
+                const cdf y = cdf_mul(tau, cdf_add(zk, make_float4(-c.x, -c.y, -c.z, -c.w)));
+                const cdf vk = s >= 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : Cs[0];
+                cwv[l] = cdf_fma(y, alpha, vk);
+                cwv[kNb + 1 + l] = vk;
+            }
+        }
+        __syncthreads();
+        // the current column k on own rows i >= k (lanes over l' <= l), and its squared norm below row k + 1
+        float nh = 0.f, nl = 0.f;
+        if (k <= n - 1) {
+            const int mk = blk >= k ? 0 : (k - blk + G - 1) / G;
+            for (int m = mk + wid; m < ncl; m += kTriWarps) {
+                const int i = blk + m * G;
+                cdf t = cdf_zero();
+                if (lane < l) {
+                    const cdf vi = __ldcg(a.V + (size_t)lane * n + i), wi = __ldcg(a.W + (size_t)lane * n + i);
+                    t = cdf_fma(cdf_mul(vi, cdf_conj(cwv[lane])), wi, cdf_conj(cwv[kNb + 1 + lane]));
+                } else if (lane == l) {
+                    t = cdf_fma(cdf_mul(vown[m], cdf_conj(cwv[l])), wown[m], cdf_conj(cwv[kNb + 1 + l]));
+                }
+                t = cdf_warp_sum(t);
+                if (lane == 0) {
+                    const cdf q = col(k)[i];
+                    const cdf ai = cdf_add(q, make_float4(-t.x, -t.y, -t.z, -t.w));
+                    a.ncol[i] = ai;
+                    if (i >= k + 2) {
+                        df_acc(nh, nl, ai.x, ai.y, ai.x, ai.y);
+                        df_acc(nh, nl, ai.z, ai.w, ai.z, ai.w);
+                    }
+                }
+            }
+        }
+        if (lane == 0) s_nrm[wid] = df_fin(nh, nl);
+        __syncthreads();
+        if (tid == 0) {
+            float2 t = s_nrm[0];
+            for (int w = 1; w < kTriWarps; ++w) t = df_add(t, s_nrm[w]);
+            a.npart[blk] = t;
+        }
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
+
+        // ---------------- panel end: A -= V W^H + W V^H on own columns >= k, rows >= k ----------------
+        if (l == kNb - 1 && s < n - 2) {
+            const int mk = blk >= k ? 0 : (k - blk + G - 1) / G;
+            const int nc = ncl - mk;
+            for (int e2 = tid; e2 < nc * kNb; e2 += kTriThreads) {
+                const int mm = e2 / kNb, ll = e2 % kNb;
+                const int i = blk + (mk + mm) * G;
+                coef[(size_t)mm * 2 * kNb + ll] = __ldcg(a.W + (size_t)ll * n + i);
+                coef[(size_t)mm * 2 * kNb + kNb + ll] = __ldcg(a.V + (size_t)ll * n + i);
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < nc; c0 += kHerCols) {
+                const int cn = min(kHerCols, nc - c0);
+                for (int r = k + tid; r < n; r += kTriThreads) {
+                    float acc[kHerCols][4];
+#pragma unroll
+                    for (int c = 0; c < kHerCols; ++c) {
+                        const cdf q = c < cn ? col(blk + (mk + c0 + c) * G)[r] : cdf_zero();
+                        acc[c][0] = q.x;
+                        acc[c][1] = q.y;
+                        acc[c][2] = q.z;
+                        acc[c][3] = q.w;
+                    }
+                    for (int ll = 0; ll < kNb; ++ll) {
+                        const cdf vr = __ldcg(a.V + (size_t)ll * n + r), wr = __ldcg(a.W + (size_t)ll * n + r);
+#pragma unroll
+                        for (int c = 0; c < kHerCols; ++c) {
+                            if (c >= cn) break;
+                            const cdf wc = coef[(size_t)(c0 + c) * 2 * kNb + ll];
+                            const cdf vc = coef[(size_t)(c0 + c) * 2 * kNb + kNb + ll];
+                            // acc -= vr conj(wc) + wr conj(vc)
+                            df_acc(acc[c][0], acc[c][1], -vr.x, -vr.y, wc.x, wc.y);
+                            df_acc(acc[c][0], acc[c][1], -vr.z, -vr.w, wc.z, wc.w);
+                            df_acc(acc[c][0], acc[c][1], -wr.x, -wr.y, vc.x, vc.y);
+                            df_acc(acc[c][0], acc[c][1], -wr.z, -wr.w, vc.z, vc.w);
+                            df_acc(acc[c][2], acc[c][3], -vr.z, -vr.w, wc.x, wc.y);
+                            df_acc(acc[c][2], acc[c][3], vr.x, vr.y, wc.z, wc.w);
+                            df_acc(acc[c][2], acc[c][3], -wr.z, -wr.w, vc.x, vc.y);
+                            df_acc(acc[c][2], acc[c][3], wr.x, wr.y, vc.z, vc.w);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < kHerCols; ++c) {
+                        if (c >= cn) break;
+                        const float2 re = df_fin(acc[c][0], acc[c][1]), im = df_fin(acc[c][2], acc[c][3]);
+                        col(blk + (mk + c0 + c) * G)[r] = make_float4(re.x, re.y, im.x, im.y);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (blk == 0 && tid == 0) {
+        const cdf z = __ldcg(a.ncol + (n - 1));
+        a.d[n - 1] = df_to(make_float2(z.x, z.y));
+    }
+}
+
 // Gram matrix of the conjugated projections: G_ij = sum_r b_i[r] conj(b_j[r]) (one block)
 __global__ void gram_kernel(const double2* __restrict__ b, int64_t n, int np, double2* G) {
     __shared__ double s[kTriWarps][18];
@@ -779,14 +1147,16 @@ __global__ void sum_kernel(const double* __restrict__ w, int64_t n, double* out)
 
 size_t tridiag_scratch_bytes(int64_t n) {
     // v0 n, ncol 2n, xbuf 2n, spart 2 x 1024 (16 bytes each); d, e, e2, lam, w (n doubles); d32, e2_32 (n floats);
-    // d_df, e2_df (n float2);
-    // twisted pivots 2 n*n float2; 256-byte alignment of each piece
+    // d_df, e2_df (n float2); twisted pivots 2 n*n float2; the blocked reduction's V and W (2 kNb n,
+    // 16 bytes each), its norm parts (1024 float2) and s dots (2 kNb); 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n) +
-           sizeof(float2) * (size_t)(2 * n * n) +
-           sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) + 8192;
+           sizeof(float2) * (size_t)(2 * n * n) + sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) +
+           sizeof(cdf) * (size_t)(2 * kNb * n + 2 * kNb) + sizeof(float2) * 1024 + 16384;
 }
 
-int tridiag_max_dim() { return 4736; }   // v, w and the next column of a step in 227 KB of shared memory
+// the blocked reduction keeps a column (16 n bytes) and the panel coefficients
+// of its own columns in 227 KB of shared memory: n up to about 10 000
+int tridiag_max_dim() { return 8192; }
 
 int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st) {
     if (np < 1 || np > 3) return fail(BSE_EINVAL, "gram of %d vectors", np);
@@ -800,7 +1170,7 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // variant) to T after the start reflector of b, then levels and weights.
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
-                            long wait_polls) {
+                            long wait_polls, int variant) {
     if (n < 1 || n > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld", (long long)n);
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) {
@@ -825,6 +1195,10 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     TriBounds* bnd = (TriBounds*)take(sizeof(TriBounds));
     unsigned* bar = (unsigned*)take(sizeof(unsigned));
     float2* dp = (float2*)take(sizeof(float2) * 2 * n * n);
+    cdf* Vp = (cdf*)take(sizeof(cdf) * kNb * n);
+    cdf* Wp = (cdf*)take(sizeof(cdf) * kNb * n);
+    cdf* sdot = (cdf*)take(sizeof(cdf) * 2 * kNb);
+    float2* npart = (float2*)take(sizeof(float2) * 1024);
 
     int dev = 0, sms = 0, maxsm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
@@ -834,9 +1208,9 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     const size_t static_smem = sizeof(cdf) * (kTriWarps + 3) + 64;
     const size_t vec_bytes = sizeof(cdf) * 3 * (size_t)n;   // v, w and the next column of a step
     const size_t cols_bytes = sizeof(cdf) * (size_t)((n - 1) / G + 1) * n;
-    const bool smem = vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
-    if (!smem) G = sms;
-    if (vec_bytes + static_smem > (size_t)maxsm)
+    const bool smem = variant != 1 && vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
+    if (!smem) G = (int)std::min<int64_t>(sms, n);
+    if (!smem && tri_blocked_smem(n, G) > (size_t)maxsm)
         return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld exceeds shared memory", (long long)n);
 
     BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
@@ -846,30 +1220,61 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     note_launch();
     BSE_CUDA(cudaGetLastError());
 
-    TriArgs a;
-    a.A = h;
-    a.n = n;
-    a.v0 = v0;
-    a.beta0 = beta0;
-    a.ncol = ncol;
-    a.xbuf = xbuf;
-    a.spart = spart;
-    a.d = d;
-    a.e = e;
-    a.bar = bar;
-    a.err = err;
-    a.spin = wait_limit(wait_polls, kGridSpinLimit);
-    void* args[] = {&a};
-    const size_t dyn = vec_bytes + (smem ? cols_bytes : 0);
-    const void* fn = smem ? (const void*)tridiag_kernel<true> : (const void*)tridiag_kernel<false>;
-    BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    int per_sm = 0;
-    BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
-    if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
-    if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
-    BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
-    note_launch();
-    if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
+    if (smem) {
+        TriArgs a;
+        a.A = h;
+        a.n = n;
+        a.v0 = v0;
+        a.beta0 = beta0;
+        a.ncol = ncol;
+        a.xbuf = xbuf;
+        a.spart = spart;
+        a.d = d;
+        a.e = e;
+        a.bar = bar;
+        a.err = err;
+        a.spin = wait_limit(wait_polls, kGridSpinLimit);
+        void* args[] = {&a};
+        const size_t dyn = vec_bytes + cols_bytes;
+        const void* fn = (const void*)tridiag_kernel<true>;
+        BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int per_sm = 0;
+        BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
+        if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
+        if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
+        BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
+        note_launch();
+        if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
+    } else {
+        TriBArgs a;
+        a.A = reinterpret_cast<cdf*>(h);
+        a.n = n;
+        a.v0 = v0;
+        a.beta0 = beta0;
+        a.V = Vp;
+        a.W = Wp;
+        a.ncol = ncol;
+        a.npart = npart;
+        a.zbuf = xbuf;
+        a.zpart = spart;
+        a.sdot = sdot;
+        a.d = d;
+        a.e = e;
+        a.bar = bar;
+        a.err = err;
+        a.spin = wait_limit(wait_polls, kGridSpinLimit);
+        void* args[] = {&a};
+        const size_t dyn = tri_blocked_smem(n, G);
+        const void* fn = (const void*)tridiag_blocked_kernel;
+        BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int per_sm = 0;
+        BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
+        if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
+        if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
+        BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
+        note_launch();
+        if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
+    }
 
     tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, d32, e2_32, d_df, e2_df, bnd);
     note_launch();

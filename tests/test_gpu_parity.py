@@ -477,17 +477,20 @@ def test_solver_choice_and_agreement(gpu, name):
             continue
         h1 = bse.partner_block(ctx, mu)
         out = {}
-        for solver in (bse.BSE_SOLVER_AUTO, bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG):
+        for solver in (bse.BSE_SOLVER_AUTO, bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG,
+                       bse.BSE_SOLVER_TRIDIAG_BLOCKED):
             bse.bse_set_solver(ctx, solver)
             out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
             used = bse.bse_get_stats(ctx)["solver"]
             assert used == (bse.BSE_SOLVER_DENSE if solver == bse.BSE_SOLVER_DENSE else bse.BSE_SOLVER_TRIDIAG)
         bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
-        (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[bse.BSE_SOLVER_TRIDIAG]
-        assert np.abs(om - om2).max() <= TOL
-        for cl in _clusters(om):
-            assert abs(osc[cl].sum() - osc2[cl].sum()) <= 1e-10 * max(osc.sum(), 1e-300)
-        assert np.linalg.norm(im - im2) <= 1e-9 * max(np.linalg.norm(im), 1e-300)
+        # the reduction in shared memory and the blocked (panel) reduction, both against zheevd
+        for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED):
+            (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[other]
+            assert np.abs(om - om2).max() <= TOL
+            for cl in _clusters(om):
+                assert abs(osc[cl].sum() - osc2[cl].sum()) <= 1e-10 * max(osc.sum(), 1e-300)
+            assert np.linalg.norm(im - im2) <= 1e-9 * max(np.linalg.norm(im), 1e-300)
         if t["irrep_dim"][mu] > 1:
             hb = bse.block(ctx, mu)
             bse.spectrum(ctx, mu, hb, omega, d["eta"])

@@ -109,9 +109,9 @@ def test_fp32_levels_within_0p1_mev(si12):
 
 
 def test_partner_solvers_agree(si12):
-    """The 3470-dim partner block exceeds the shared-memory capacity, so the
-    tridiagonal reduction keeps it in global memory; levels and strengths
-    against the dense eigensolver."""
+    """The 3582-dim partner block exceeds the shared-memory capacity, so the
+    tridiagonal reduction keeps its columns in global memory (the blocked,
+    panel form); levels and strengths against the dense eigensolver."""
     bse, torch, ctx, t, mu, h64, h32, cols, d, *_ = si12
     omega = torch.tensor(d["omega"], device="cuda")
     out = {}

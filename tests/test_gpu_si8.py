@@ -136,17 +136,19 @@ def test_partner_solvers_agree(built):
     h1 = bse.partner_block(ctx, mu)
     omega = torch.tensor(d["omega"], device="cuda")
     out = {}
-    for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG):
+    for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED):
         bse.bse_set_solver(ctx, solver)
         out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
     bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
-    (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[bse.BSE_SOLVER_TRIDIAG]
-    assert np.abs(om - om2).max() <= TOL * np.abs(om).max()
-    assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()
-    assert np.linalg.norm(im - im2) <= 1e-9 * np.linalg.norm(im)
-    # the reduction and the bisection compute in double-float (48-bit
-    # significand): backward error of order n 2^-47, far inside the tolerance
-    assert np.abs(om - om2).max() <= 1e-12 * np.abs(om).max()
+    # the reduction in shared memory, and the blocked one (26 panels of 32 reflectors)
+    for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED):
+        (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[other]
+        assert np.abs(om - om2).max() <= TOL * np.abs(om).max()
+        assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()
+        assert np.linalg.norm(im - im2) <= 1e-9 * np.linalg.norm(im)
+        # the reduction and the bisection compute in double-float (48-bit
+        # significand): backward error of order n 2^-47, far inside the tolerance
+        assert np.abs(om - om2).max() <= 1e-12 * np.abs(om).max()
 
 
 def test_loss_levels_against_dense(built):
