@@ -148,7 +148,7 @@ def test_partner_solvers_agree(built):
         assert np.linalg.norm(im - im2) <= 1e-9 * np.linalg.norm(im)
         # the reduction and the bisection compute in double-float (48-bit
         # significand): backward error of order n 2^-47, far inside the tolerance
-        assert np.abs(om - om2).max() <= 1e-12 * np.abs(om).max()
+        assert np.abs(om - om2).max() <= len(om) * 2.0 ** -47 * np.abs(om).max()
 
 
 def test_loss_levels_against_dense(built):
