@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_kernel(TriArgs a) {
 // being read, written and read again by a rank-2 update and the dot products.
 // ---------------------------------------------------------------------------
 constexpr int kNb = 32;           // reflectors per panel
-constexpr int kHerCols = 8;       // own columns updated together in the panel-end update
+constexpr int kHerCols = 12;      // own columns updated together in the panel-end update
 
 struct TriBArgs {
     cdf* A;               // n x n column-major; the FP64 block on entry, rewritten in place in double-float
@@ -402,9 +402,10 @@ struct TriBArgs {
     cdf* W;               // [kNb][n] their w vectors
     cdf* ncol;            // [n] the current column of the next reflector (rows >= its index)
     float2* npart;        // [G] per-CTA parts of its squared norm below the subdiagonal
-    cdf* zbuf;            // [n] z_i of the step
-    cdf* zpart;           // [G] per-CTA parts of z^H v
-    cdf* sdot;            // [2 kNb] s1 (first kNb entries) and s2
+    cdf* zbuf;            // [2][n] the unscaled dot zr_i and the row s+1 term t_i of z_i = t_i + inv zr_i
+    cdf* zpart;           // [G][4] per-CTA sums for z^H v: sum conj(t_i) c_i, sum conj(zr_i) c_i over own
+                          // i >= s+2 (c the current column), and conj(t_i), conj(zr_i) of i = s+1
+    cdf* sdot;            // [2][2 kNb] s1 (first kNb entries) and s2: unscaled sums and row s+1 terms
     double* d;            // [n] diagonal of T
     double* e;            // [n] off-diagonal of T
     unsigned* bar;        // barrier counter, zero on entry
@@ -413,35 +414,60 @@ struct TriBArgs {
 };
 
 // dynamic shared memory of the blocked kernel (cdf units): the staged column
-// (n), the panel-end coefficients of own columns (ncl x 2 kNb), own z, v, w
-// (3 ncl), s1, s2 and the current column's coefficients (4 (kNb + 1))
+// (n); per own column m the panel's W[i,l] and V[i,l] (2 kNb), its z, the row
+// s+1 term of its dot, its v and w, and its entry of the next current column
+// (5); s1, s2 and the current column's coefficients (4 (kNb + 1))
 __host__ __device__ inline size_t tri_blocked_smem(int64_t n, int G) {
     const int64_t ncl = (n + G - 1) / G;
-    return sizeof(cdf) * (size_t)(n + ncl * 2 * kNb + 3 * ncl + 4 * (kNb + 1)) + 64;
-}
-
-// sum_{r >= r0} conj(x[r]) c[r] over a column x in global memory (lanes over rows,
-// four rows' loads in flight per lane), reduced over the warp
-__device__ __forceinline__ cdf warp_coldot(const cdf* __restrict__ x, const cdf* c, int r0, int n, int lane) {
-    cdf acc = cdf_zero(), acc2 = cdf_zero();
-    int r = r0 + lane;
-    for (; r + 96 < n; r += 128) {
-        const cdf a0 = x[r], a1 = x[r + 32], a2 = x[r + 64], a3 = x[r + 96];
-        acc = cdf_dot_acc(acc, a0, c[r]);
-        acc2 = cdf_dot_acc(acc2, a1, c[r + 32]);
-        acc = cdf_dot_acc(acc, a2, c[r + 64]);
-        acc2 = cdf_dot_acc(acc2, a3, c[r + 96]);
-    }
-    for (; r < n; r += 32) acc = cdf_dot_acc(acc, x[r], c[r]);
-    return cdf_warp_sum(cdf_add(acc, acc2));
+    return sizeof(cdf) * (size_t)(n + ncl * (2 * kNb + 5) + 4 * (kNb + 1)) + 64;
 }
 
 __device__ __forceinline__ cdf cdf_conj(cdf a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ cdf cdf_neg(cdf a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+
+// a load of the streamed trailing matrix: marked evict-first in L2, so that the
+// hundreds of MB read per step do not push the kernel's instructions and the
+// panel's small vectors out of L2 (a refetch from saturated HBM costs tens of
+// microseconds on the step's critical path)
+template <bool kStream>
+__device__ __forceinline__ cdf ld_col(const cdf* p) { return kStream ? __ldcs(p) : __ldcg(p); }
+
+// sum_{r >= r0} conj(x[r]) c[r] over a column x in global memory, lanes over
+// rows, eight rows' loads in flight per lane; reduced over the warp
+template <bool kStream>
+__device__ __forceinline__ cdf warp_coldot(const cdf* __restrict__ x, const cdf* c, int r0, int n, int lane) {
+    cdf acc0 = cdf_zero(), acc1 = cdf_zero(), acc2 = cdf_zero(), acc3 = cdf_zero();
+    int r = r0 + lane;
+    // sixteen rows' loads in flight per lane (8 KB per warp) while the column streams from HBM
+    for (; r + 480 < n; r += 512) {
+        cdf q[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) q[u] = ld_col<kStream>(x + r + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+            acc0 = cdf_dot_acc(acc0, q[u], c[r + 32 * u]);
+            acc1 = cdf_dot_acc(acc1, q[u + 1], c[r + 32 * u + 32]);
+            acc2 = cdf_dot_acc(acc2, q[u + 2], c[r + 32 * u + 64]);
+            acc3 = cdf_dot_acc(acc3, q[u + 3], c[r + 32 * u + 96]);
+        }
+    }
+    for (; r + 96 < n; r += 128) {
+        const cdf q0 = ld_col<kStream>(x + r), q1 = ld_col<kStream>(x + r + 32), q2 = ld_col<kStream>(x + r + 64),
+                  q3 = ld_col<kStream>(x + r + 96);
+        acc0 = cdf_dot_acc(acc0, q0, c[r]);
+        acc1 = cdf_dot_acc(acc1, q1, c[r + 32]);
+        acc2 = cdf_dot_acc(acc2, q2, c[r + 64]);
+        acc3 = cdf_dot_acc(acc3, q3, c[r + 96]);
+    }
+    for (; r < n; r += 32) acc0 = cdf_dot_acc(acc0, ld_col<kStream>(x + r), c[r]);
+    return cdf_warp_sum(cdf_add(cdf_add(acc0, acc1), cdf_add(acc2, acc3)));
+}
 
 __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArgs a) {
     extern __shared__ __align__(16) cdf s_dyn[];
-    __shared__ cdf s_tau, s_inv, s_alpha, s_red[kTriWarps];
-    __shared__ cdf s_raw[2 * kNb];   // unscaled s dots of this CTA
+    __shared__ cdf s_tau, s_inv, s_alpha;
+    __shared__ cdf s_zk;                     // z_k of the current column's index
+    __shared__ cdf s_zp[kTriWarps][4];       // per-warp parts of the z^H v sums
     __shared__ float2 s_nrm[kTriWarps];
     __shared__ int s_next, s_flag;
 
@@ -449,14 +475,17 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
     const int G = gridDim.x, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ncl = blk < n ? (n - 1 - blk) / G + 1 : 0;
     cdf* Cs = s_dyn;                                   // [n] the staged column (or v0)
-    cdf* coef = Cs + n;                                // [ncl][2 kNb] W[i,l], V[i,l] of own columns (panel end)
-    cdf* zown = coef + (size_t)ncl * 2 * kNb;          // [ncl]
-    cdf* vown = zown + ncl;                            // [ncl]
+    cdf* WV = Cs + n;                                  // [ncl][2 kNb]: W[i,l] then V[i,l] of own index i
+    cdf* zown = WV + (size_t)ncl * 2 * kNb;            // [ncl] z_i (unscaled sum, then z)
+    cdf* ztop = zown + ncl;                            // [ncl] conj(A[s+1, i])
+    cdf* vown = ztop + ncl;                            // [ncl]
     cdf* wown = vown + ncl;                            // [ncl]
-    cdf* s12 = wown + ncl;                             // [2 (kNb + 1)]: s1 then s2
+    cdf* colk = wown + ncl;                            // [ncl] A[i, k] of the next current column, own rows
+    cdf* s12 = colk + ncl;                             // [2 (kNb + 1)]: s1 then s2
     cdf* cwv = s12 + 2 * (kNb + 1);                    // [2 (kNb + 1)]: W[k,l'] then V[k,l']
     cdf* gA = a.A;
     auto col = [&](int i) -> cdf* { return gA + (size_t)i * n; };
+    auto WVo = [&](int m, int l2) -> cdf& { return WV[(size_t)m * 2 * kNb + l2]; };
 
     // own columns in double-float, in place (same 16 bytes per element)
     for (int m = 0; m < ncl; ++m) {
@@ -472,6 +501,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
     for (int s = -1; s <= n - 2; ++s) {
         const int k = s + 1;
         const int l = (s + 1) % kNb;     // reflectors of the panel before this one
+        const int m0 = blk > s ? 0 : (s - blk) / G + 1;   // own indices i > s (= own rows i >= k)
+        const int nown = ncl - m0;
         // ---------------- phase 1 ----------------
         // stage the current column (rows >= s) or the start reflector
         if (s < 0) {
@@ -482,8 +513,6 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
         if (tid == 0) s_next = 0;
         __syncthreads();
         // own columns i > s, then the dots s_q, q = blk, blk + G, ... < 2 l
-        const int m0 = blk > s ? 0 : (s - blk) / G + 1;
-        const int nown = ncl - m0;
         const int nsq = blk < 2 * l ? (2 * l - 1 - blk) / G + 1 : 0;
         const int ntask = nown + nsq;
         const int r0 = s < 0 ? 0 : s + 2;
@@ -509,7 +538,13 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
             s_tau = cdf_from(make_double2(__ldcg(a.beta0), 0.0));
             s_inv = make_float4(1.f, 0.f, 0.f, 0.f);
         }
-        // dot tasks, taken dynamically (warp 0 joins once the reflector is done)
+        // dot tasks, taken dynamically (warp 0 joins once the reflector is done).  A column task
+        // publishes the unscaled sum zr_i and the row s+1 term t_i = conj(A[s+1,i]) (z_i = t_i +
+        // inv zr_i once the reflector is known), fetches the entry A[i,k] of the next current
+        // column and adds to this warp's parts of z^H v = sum_i conj(z_i) v_i, which with
+        // v_i = inv c_i (i >= s+2), v_{s+1} = 1 is inv sum conj(t_i) c_i + |inv|^2 sum conj(zr_i) c_i
+        // + conj(t_{s+1}) + conj(inv) conj(zr_{s+1}).  An s task publishes the same pair for s_q.
+        cdf p0 = cdf_zero(), p1 = cdf_zero(), p2 = cdf_zero(), p3 = cdf_zero();
         for (;;) {
             int t = 0;
             if (lane == 0) t = atomicAdd(&s_next, 1);
@@ -517,151 +552,171 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
             if (t >= ntask) break;
             if (t < nown) {
                 const int m = m0 + t;
-                const cdf* x = col(blk + m * G);
-                cdf zr = warp_coldot(x, Cs, r0, n, lane);
-                // completed below once the reflector's scalars are known:
-                // z = conj(A[s+1, i]) + inv zr (s >= 0); z = zr for the start reflector
-                if (lane == 0) zown[m] = zr;
+                const int i = blk + m * G;
+                const cdf* x = col(i);
+                cdf top = cdf_zero(), ck = cdf_zero();
+                if (lane == 0) {
+                    if (s >= 0) top = cdf_conj(__ldcg(x + s + 1));
+                    if (l > 0) ck = __ldcg(col(k) + i);   // column k is not written during a panel
+                }
+                const cdf zr = warp_coldot<true>(x, Cs, r0, n, lane);
+                if (lane == 0) {
+                    zown[m] = zr;
+                    ztop[m] = top;
+                    colk[m] = ck;
+                    a.zbuf[i] = zr;
+                    a.zbuf[n + i] = top;
+                    if (s < 0) {                       // start reflector: v = v0, z = zr
+                        p1 = cdf_dot_acc(p1, zr, Cs[i]);
+                    } else if (i >= s + 2) {
+                        p0 = cdf_dot_acc(p0, top, Cs[i]);
+                        p1 = cdf_dot_acc(p1, zr, Cs[i]);
+                    } else {                           // i = s + 1: conj(z) = conj(t) + conj(inv) conj(zr)
+                        p2 = cdf_conj(top);
+                        p3 = cdf_conj(zr);
+                    }
+                }
             } else {
                 const int q = blk + (t - nown) * G;   // s1_q (q < l) or s2_{q - l}
                 const cdf* x = q < l ? a.W + (size_t)q * n : a.V + (size_t)(q - l) * n;
-                cdf sr = warp_coldot(x, Cs, r0, n, lane);
-                if (lane == 0) s_raw[q] = sr;
-            }
-        }
-        __syncthreads();
-        {
-            const cdf tau = s_tau, inv = s_inv;
-            float sr_ = 0.f, lr_ = 0.f, si_ = 0.f, li_ = 0.f;   // this thread's part of z^H v
-            for (int m = m0 + tid; m < ncl; m += kTriThreads) {
-                const int i = blk + m * G;
-                cdf z = zown[m];
-                cdf v;
-                if (s >= 0) {
-                    z = cdf_fma(cdf_conj(col(i)[s + 1]), inv, z);   // conj(A[s+1,i]) + inv zr
-                    v = i == s + 1 ? make_float4(1.f, 0.f, 0.f, 0.f) : cdf_mul(Cs[i], inv);
-                } else {
-                    v = Cs[i];
+                cdf top = cdf_zero();
+                if (lane == 0 && s >= 0) top = cdf_conj(__ldcg(x + s + 1));
+                const cdf sr = warp_coldot<false>(x, Cs, r0, n, lane);
+                if (lane == 0) {
+                    const int o = q < l ? q : kNb + q - l;
+                    a.sdot[o] = sr;
+                    a.sdot[2 * kNb + o] = top;
                 }
-                zown[m] = z;
-                vown[m] = v;
-                a.zbuf[i] = z;
-                // conj(z) v
-                df_acc(sr_, lr_, z.x, z.y, v.x, v.y);
-                df_acc(sr_, lr_, z.z, z.w, v.z, v.w);
-                df_acc(si_, li_, z.x, z.y, v.z, v.w);
-                df_acc(si_, li_, -z.z, -z.w, v.x, v.y);
             }
-            float2 pr = df_fin(sr_, lr_), pi = df_fin(si_, li_);
-            cdf part = cdf_warp_sum(make_float4(pr.x, pr.y, pi.x, pi.y));
-            if (lane == 0) s_red[wid] = part;
-            if (tid < nsq) {
-                const int q = blk + tid * G;
-                const cdf sr = s_raw[q];
-                const cdf* x = q < l ? a.W + (size_t)q * n : a.V + (size_t)(q - l) * n;
-                // s_q = conj(X[s+1]) + inv sr (s >= 0)
-                a.sdot[q < l ? q : kNb + q - l] = s >= 0 ? cdf_fma(cdf_conj(x[s + 1]), inv, sr) : sr;
-            }
-            (void)tau;
+        }
+        if (lane == 0) {
+            s_zp[wid][0] = p0;
+            s_zp[wid][1] = p1;
+            s_zp[wid][2] = p2;
+            s_zp[wid][3] = p3;
         }
         __syncthreads();
-        if (tid == 0) {
-            cdf sp = s_red[0];
-            for (int w = 1; w < kTriWarps; ++w) sp = cdf_add(sp, s_red[w]);
-            a.zpart[blk] = sp;
+        if (wid == 0 && lane < 4) {
+            cdf sum = s_zp[0][lane];
+            for (int w = 1; w < kTriWarps; ++w) sum = cdf_add(sum, s_zp[w][lane]);
+            a.zpart[(size_t)blk * 4 + lane] = sum;
         }
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
 
         // ---------------- phase 2 ----------------
-        const cdf tau = s_tau;
-        if (wid == 0) {
-            cdf zv = cdf_zero();
-            for (int b = lane; b < G; b += 32) zv = cdf_add(zv, __ldcg(a.zpart + b));
-            zv = cdf_warp_sum(zv);
-            // s1, s2 of the panel's earlier reflectors and Re s1^H s2
+        const cdf tau = s_tau, inv = s_inv;
+        if (wid == 0) {   // z^H v, s1, s2, Re s1^H s2 and alpha
+            cdf q0 = cdf_zero(), q1 = cdf_zero(), q2 = cdf_zero(), q3 = cdf_zero();
+            for (int b = lane; b < G; b += 32) {
+                const cdf* zp = a.zpart + (size_t)b * 4;
+                q0 = cdf_add(q0, __ldcg(zp));
+                q1 = cdf_add(q1, __ldcg(zp + 1));
+                q2 = cdf_add(q2, __ldcg(zp + 2));
+                q3 = cdf_add(q3, __ldcg(zp + 3));
+            }
             cdf s1 = cdf_zero(), s2 = cdf_zero();
             if (lane < l) {
-                s1 = __ldcg(a.sdot + lane);
-                s2 = __ldcg(a.sdot + kNb + lane);
+                const cdf r1 = __ldcg(a.sdot + lane), t1 = __ldcg(a.sdot + 2 * kNb + lane);
+                const cdf r2 = __ldcg(a.sdot + kNb + lane), t2 = __ldcg(a.sdot + 3 * kNb + lane);
+                s1 = s >= 0 ? cdf_fma(t1, inv, r1) : r1;
+                s2 = s >= 0 ? cdf_fma(t2, inv, r2) : r2;
                 s12[lane] = s1;
                 s12[kNb + 1 + lane] = s2;
             }
-            cdf cr = cdf_dot_acc(cdf_zero(), s1, s2);   // conj(s1) s2
-            cr = cdf_warp_sum(cr);
+            q0 = cdf_warp_sum(q0);
+            q1 = cdf_warp_sum(q1);
+            q2 = cdf_warp_sum(q2);
+            q3 = cdf_warp_sum(q3);
+            const cdf cr = cdf_warp_sum(cdf_dot_acc(cdf_zero(), s1, s2));   // s1^H s2
             if (lane == 0) {
+                // z^H v = inv q0 + |inv|^2 q1 + q2 + conj(inv) q3 (start reflector: q1)
+                cdf zv;
+                if (s >= 0) {
+                    const cdf ii = cdf_dot_acc(cdf_zero(), inv, inv);   // |inv|^2
+                    zv = cdf_fma(cdf_fma(cdf_fma(q2, inv, q0), ii, q1), cdf_conj(inv), q3);
+                } else {
+                    zv = q1;
+                }
                 // y^H v = conj(tau) (z^H v - 2 Re s1^H s2); alpha = -tau/2 y^H v
-                const cdf zc = make_float4(zv.x, zv.y, zv.z, zv.w);
                 const float2 two_re = df_add(make_float2(cr.x, cr.y), make_float2(cr.x, cr.y));
-                const cdf d0 = cdf_add(zc, make_float4(-two_re.x, -two_re.y, 0.f, 0.f));
-                const cdf yv = cdf_mul(cdf_conj(tau), d0);
-                const cdf al = cdf_mul(tau, yv);
+                const cdf d0 = cdf_add(zv, make_float4(-two_re.x, -two_re.y, 0.f, 0.f));
+                const cdf al = cdf_mul(tau, cdf_mul(cdf_conj(tau), d0));
                 s_alpha = make_float4(-0.5f * al.x, -0.5f * al.y, -0.5f * al.z, -0.5f * al.w);
             }
+        } else if (wid == 1) {   // W[k,l'], V[k,l'] (l' < l) and z_k of the current column's index k
+            if (lane < l) {
+                cwv[lane] = __ldcg(a.W + (size_t)lane * n + k);
+                cwv[kNb + 1 + lane] = __ldcg(a.V + (size_t)lane * n + k);
+            }
+            if (lane == 0) {
+                const cdf zr = __ldcg(a.zbuf + k), tk = __ldcg(a.zbuf + n + k);
+                s_zk = s >= 0 ? cdf_fma(tk, inv, zr) : zr;
+            }
+        } else if (wid == 2) {   // z and v of own indices
+            for (int m = m0 + lane; m < ncl; m += 32) {
+                const int i = blk + m * G;
+                if (s >= 0) {
+                    zown[m] = cdf_fma(ztop[m], inv, zown[m]);
+                    vown[m] = i == s + 1 ? make_float4(1.f, 0.f, 0.f, 0.f) : cdf_mul(Cs[i], inv);
+                } else {
+                    vown[m] = Cs[i];
+                }
+            }
+        } else if (l == 0) {
+            // first step of a panel: column k may have been updated by its owner's panel-end
+            // update after phase 1 read it, so its entries are read again here
+            for (int m = m0 + tid - 96; m < ncl; m += kTriThreads - 96) colk[m] = __ldcg(col(k) + blk + m * G);
         }
         __syncthreads();
         const cdf alpha = s_alpha;
         // own indices i > s: corr_i = sum_{l' < l} V[i,l'] s1_l' + W[i,l'] s2_l' (lanes over l'),
-        // y_i = tau (z_i - corr_i), w_i = y_i + alpha v_i; column l of V and W
-        for (int m = m0 + wid; m < ncl; m += kTriWarps) {
-            const int i = blk + m * G;
+        // y_i = tau (z_i - corr_i), w_i = y_i + alpha v_i; column l of V and W.  The last warp
+        // also forms W[k,l] = w_k of the current column's index (every CTA, redundantly).
+        for (int t = wid; t < nown + 1; t += kTriWarps) {
+            const bool own = t < nown;
+            const int m = m0 + t;
             cdf c = cdf_zero();
             if (lane < l) {
-                c = cdf_mul(__ldcg(a.V + (size_t)lane * n + i), s12[lane]);
-                c = cdf_fma(c, __ldcg(a.W + (size_t)lane * n + i), s12[kNb + 1 + lane]);
+                const cdf vi = own ? WVo(m, kNb + lane) : cwv[kNb + 1 + lane];
+                const cdf wi = own ? WVo(m, lane) : cwv[lane];
+                c = cdf_fma(cdf_mul(vi, s12[lane]), wi, s12[kNb + 1 + lane]);
             }
             c = cdf_warp_sum(c);
             if (lane == 0) {
-                const cdf zc = zown[m];
-                const cdf y = cdf_mul(tau, cdf_add(zc, make_float4(-c.x, -c.y, -c.z, -c.w)));
-                const cdf w = cdf_fma(y, alpha, vown[m]);
-                wown[m] = w;
-                a.W[(size_t)l * n + i] = w;
-                a.V[(size_t)l * n + i] = vown[m];
-            }
-        }
-        // W[k,l] and V[k,l] of the current column's index k, redundantly in every CTA (last warp)
-        if (k <= n - 1 && wid == kTriWarps - 1) {
-            cdf c = cdf_zero(), wl = cdf_zero(), vl = cdf_zero();
-            if (lane < l) {
-                vl = __ldcg(a.V + (size_t)lane * n + k);
-                wl = __ldcg(a.W + (size_t)lane * n + k);
-                c = cdf_mul(vl, s12[lane]);
-                c = cdf_fma(c, wl, s12[kNb + 1 + lane]);
-                cwv[lane] = wl;
-                cwv[kNb + 1 + lane] = vl;
-            }
-            c = cdf_warp_sum(c);
-            if (lane == 0) {
-                const cdf zk = __ldcg(a.zbuf + k);
-                const cdf y = cdf_mul(tau, cdf_add(zk, make_float4(-c.x, -c.y, -c.z, -c.w)));
-                const cdf vk = s >= 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : Cs[0];
-                cwv[l] = cdf_fma(y, alpha, vk);
-                cwv[kNb + 1 + l] = vk;
+                if (own) {
+                    const cdf y = cdf_mul(tau, cdf_add(zown[m], cdf_neg(c)));
+                    const cdf w = cdf_fma(y, alpha, vown[m]);
+                    const int i = blk + m * G;
+                    wown[m] = w;
+                    WVo(m, l) = w;
+                    WVo(m, kNb + l) = vown[m];
+                    a.W[(size_t)l * n + i] = w;
+                    a.V[(size_t)l * n + i] = vown[m];
+                } else if (k <= n - 1) {
+                    const cdf y = cdf_mul(tau, cdf_add(s_zk, cdf_neg(c)));
+                    const cdf vk = s >= 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : Cs[0];
+                    cwv[l] = cdf_fma(y, alpha, vk);
+                    cwv[kNb + 1 + l] = vk;
+                }
             }
         }
         __syncthreads();
-        // the current column k on own rows i >= k (lanes over l' <= l), and its squared norm below row k + 1
+        // the current column k on own rows i >= k: A[i,k] - sum_{l' <= l} (V[i,l'] conj(W[k,l'])
+        // + W[i,l'] conj(V[k,l'])) (lanes over l'), and its squared norm below row k + 1
         float nh = 0.f, nl = 0.f;
-        if (k <= n - 1) {
-            const int mk = blk >= k ? 0 : (k - blk + G - 1) / G;
-            for (int m = mk + wid; m < ncl; m += kTriWarps) {
-                const int i = blk + m * G;
-                cdf t = cdf_zero();
-                if (lane < l) {
-                    const cdf vi = __ldcg(a.V + (size_t)lane * n + i), wi = __ldcg(a.W + (size_t)lane * n + i);
-                    t = cdf_fma(cdf_mul(vi, cdf_conj(cwv[lane])), wi, cdf_conj(cwv[kNb + 1 + lane]));
-                } else if (lane == l) {
-                    t = cdf_fma(cdf_mul(vown[m], cdf_conj(cwv[l])), wown[m], cdf_conj(cwv[kNb + 1 + l]));
-                }
-                t = cdf_warp_sum(t);
-                if (lane == 0) {
-                    const cdf q = col(k)[i];
-                    const cdf ai = cdf_add(q, make_float4(-t.x, -t.y, -t.z, -t.w));
-                    a.ncol[i] = ai;
-                    if (i >= k + 2) {
-                        df_acc(nh, nl, ai.x, ai.y, ai.x, ai.y);
-                        df_acc(nh, nl, ai.z, ai.w, ai.z, ai.w);
-                    }
+        for (int m = m0 + wid; m < ncl; m += kTriWarps) {
+            const int i = blk + m * G;
+            cdf t = cdf_zero();
+            if (lane <= l)
+                t = cdf_fma(cdf_mul(WVo(m, kNb + lane), cdf_conj(cwv[lane])), WVo(m, lane),
+                            cdf_conj(cwv[kNb + 1 + lane]));
+            t = cdf_warp_sum(t);
+            if (lane == 0) {
+                const cdf ai = cdf_add(colk[m], cdf_neg(t));
+                a.ncol[i] = ai;
+                if (i >= k + 2) {
+                    df_acc(nh, nl, ai.x, ai.y, ai.x, ai.y);
+                    df_acc(nh, nl, ai.z, ai.w, ai.z, ai.w);
                 }
             }
         }
@@ -676,34 +731,30 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
 
         // ---------------- panel end: A -= V W^H + W V^H on own columns >= k, rows >= k ----------------
         if (l == kNb - 1 && s < n - 2) {
-            const int mk = blk >= k ? 0 : (k - blk + G - 1) / G;
-            const int nc = ncl - mk;
-            for (int e2 = tid; e2 < nc * kNb; e2 += kTriThreads) {
-                const int mm = e2 / kNb, ll = e2 % kNb;
-                const int i = blk + (mk + mm) * G;
-                coef[(size_t)mm * 2 * kNb + ll] = __ldcg(a.W + (size_t)ll * n + i);
-                coef[(size_t)mm * 2 * kNb + kNb + ll] = __ldcg(a.V + (size_t)ll * n + i);
-            }
-            __syncthreads();
+            const int nc = ncl - m0;
             for (int c0 = 0; c0 < nc; c0 += kHerCols) {
                 const int cn = min(kHerCols, nc - c0);
                 for (int r = k + tid; r < n; r += kTriThreads) {
                     float acc[kHerCols][4];
 #pragma unroll
                     for (int c = 0; c < kHerCols; ++c) {
-                        const cdf q = c < cn ? col(blk + (mk + c0 + c) * G)[r] : cdf_zero();
+                        const cdf q = c < cn ? __ldcs(col(blk + (m0 + c0 + c) * G) + r) : cdf_zero();
                         acc[c][0] = q.x;
                         acc[c][1] = q.y;
                         acc[c][2] = q.z;
                         acc[c][3] = q.w;
                     }
+                    cdf vn = __ldcg(a.V + r), wn = __ldcg(a.W + r);   // the next reflector's row, loaded ahead
                     for (int ll = 0; ll < kNb; ++ll) {
-                        const cdf vr = __ldcg(a.V + (size_t)ll * n + r), wr = __ldcg(a.W + (size_t)ll * n + r);
+                        const cdf vr = vn, wr = wn;
+                        if (ll + 1 < kNb) {
+                            vn = __ldcg(a.V + (size_t)(ll + 1) * n + r);
+                            wn = __ldcg(a.W + (size_t)(ll + 1) * n + r);
+                        }
 #pragma unroll
                         for (int c = 0; c < kHerCols; ++c) {
                             if (c >= cn) break;
-                            const cdf wc = coef[(size_t)(c0 + c) * 2 * kNb + ll];
-                            const cdf vc = coef[(size_t)(c0 + c) * 2 * kNb + kNb + ll];
+                            const cdf wc = WVo(m0 + c0 + c, ll), vc = WVo(m0 + c0 + c, kNb + ll);
                             // acc -= vr conj(wc) + wr conj(vc)
                             df_acc(acc[c][0], acc[c][1], -vr.x, -vr.y, wc.x, wc.y);
                             df_acc(acc[c][0], acc[c][1], -vr.z, -vr.w, wc.z, wc.w);
@@ -719,7 +770,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
                     for (int c = 0; c < kHerCols; ++c) {
                         if (c >= cn) break;
                         const float2 re = df_fin(acc[c][0], acc[c][1]), im = df_fin(acc[c][2], acc[c][3]);
-                        col(blk + (mk + c0 + c) * G)[r] = make_float4(re.x, re.y, im.x, im.y);
+                        __stcs(col(blk + (m0 + c0 + c) * G) + r, make_float4(re.x, re.y, im.x, im.y));
                     }
                 }
             }
@@ -1151,7 +1202,7 @@ size_t tridiag_scratch_bytes(int64_t n) {
     // 16 bytes each), its norm parts (1024 float2) and s dots (2 kNb); 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n) +
            sizeof(float2) * (size_t)(2 * n * n) + sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) +
-           sizeof(cdf) * (size_t)(2 * kNb * n + 2 * kNb) + sizeof(float2) * 1024 + 16384;
+           sizeof(cdf) * (size_t)(2 * kNb * n + 4 * kNb) + sizeof(float2) * 1024 + 16384;
 }
 
 // the blocked reduction keeps a column (16 n bytes) and the panel coefficients
@@ -1197,7 +1248,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     float2* dp = (float2*)take(sizeof(float2) * 2 * n * n);
     cdf* Vp = (cdf*)take(sizeof(cdf) * kNb * n);
     cdf* Wp = (cdf*)take(sizeof(cdf) * kNb * n);
-    cdf* sdot = (cdf*)take(sizeof(cdf) * 2 * kNb);
+    cdf* sdot = (cdf*)take(sizeof(cdf) * 4 * kNb);
     float2* npart = (float2*)take(sizeof(float2) * 1024);
 
     int dev = 0, sms = 0, maxsm = 0;
