@@ -527,7 +527,7 @@ typedef struct {
     int32_t solver;             /* eigensolver of the last spectrum: BSE_SOLVER_DENSE or BSE_SOLVER_TRIDIAG */
     float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */
     float ms_rotate;            /* rotated direct-term blocks of the last build (part of ms_direct) */
-    int32_t reserved;
+    int32_t reduce_kind;        /* reduction of the last TRIDIAG spectrum: 0 block in shared memory, 1 blocked (panels) */
 } bse_stats;
 
 int bse_set_timing(bse_ctx* ctx, int32_t on);

@@ -67,7 +67,7 @@ class BseStats(C.Structure):
                 ("ms_spectrum", C.c_float), ("ms_create", C.c_float), ("ms_create_tables", C.c_float),
                 ("ms_create_upload", C.c_float), ("ms_create_gamma", C.c_float), ("ms_create_wdiv", C.c_float),
                 ("ms_basis", C.c_float), ("solver", C.c_int32), ("ms_reduce", C.c_float),
-                ("ms_rotate", C.c_float), ("reserved", C.c_int32)]
+                ("ms_rotate", C.c_float), ("reduce_kind", C.c_int32)]
 
 
 EXPORTS = {

@@ -1902,7 +1902,7 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
                                     c->triScratch.p, omega_out, osc, wsum, err, c->stream,
                                     c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls,
-                                    c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ? 1 : 0));
+                                    c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ? 1 : 0, &c->stats.reduce_kind));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     struct {
         double s;

@@ -292,9 +292,10 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // wait_polls: polls of a grid barrier before it gives up (negative: the default)
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
-                            long wait_polls = -1, int variant = 0);
+                            long wait_polls = -1, int variant = 0, int* used = nullptr);
 // variant: 0 the reduction with the block in shared memory when it fits, else the blocked
-// (panel) reduction with the columns in global memory; 1 the blocked reduction always
+// (panel) reduction with the columns in global memory; 1 the blocked reduction always.
+// *used (optional): 0 the shared-memory reduction ran, 1 the blocked one
 // lanczos.cu: the Lanczos recurrence on a Hermitian block from conj(b) (Lanczos-Haydock, Sec. IV)
 size_t lanczos_scratch_bytes(int64_t n, int m);
 int lanczos_max_dim();

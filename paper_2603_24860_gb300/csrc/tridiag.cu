@@ -1221,7 +1221,7 @@ int launch_gram(const double2* b, int64_t n, int np, double2* G, cudaStream_t st
 // variant) to T after the start reflector of b, then levels and weights.
 int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scale, void* scratch, double* omega_out,
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
-                            long wait_polls, int variant) {
+                            long wait_polls, int variant, int* used) {
     if (n < 1 || n > tridiag_max_dim()) return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld", (long long)n);
     char* p = (char*)scratch;
     auto take = [&](size_t bytes) {
@@ -1263,6 +1263,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     if (!smem) G = (int)std::min<int64_t>(sms, n);
     if (!smem && tri_blocked_smem(n, G) > (size_t)maxsm)
         return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld exceeds shared memory", (long long)n);
+    if (used) *used = smem ? 0 : 1;
 
     BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     BSE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
