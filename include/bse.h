@@ -266,18 +266,21 @@ int bse_build_blocks(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_
 /*
  * Batched builds (no counterpart in the paper, which treats one crystal at a
  * time): one block for each of n independent contexts on the same device
- * and stream.  The direct terms of all contexts run in one launch of the
- * direct kernel (every k-pair task carries the index of its context's
- * system); the exchange and projections follow per context.  The sequence
- * is captured once into a CUDA graph, so a build of the whole batch is one
- * graph launch.
+ * and stream.  The direct terms of all contexts run in one launch of a
+ * persistent kernel (a grid sized to the GPU taking the k-pair tasks of all
+ * contexts, or for the split modes their groups of k pairs sharing one q,
+ * from a device work queue, longest first; every task carries the index of
+ * its context's system); the exchange and projections follow per context.
+ * An autotuner times the candidate tile shapes on the batch's own tasks at
+ * bse_batch_create (pairs per CTA per class of instances for the split modes,
+ * threads per CTA otherwise; the choices of a class are kept for the
+ * process).  The sequence is captured once into a CUDA graph, so a build of
+ * the whole batch is one graph launch.
  *
  * bse_batch_create - plan the batch: target i is the block of irrep[i] of
  *   ctxs[i] (partner == NULL or partner[i] == 0) or its partner block
  *   (partner[i] != 0), written to h_dev[i] with leading dimension ld[i];
- *   prec any of the precision enum (the split modes launch the tensor-core
- *   kernel once per instance inside the graph, each over its own q-sorted
- *   k pairs).  All arrays are host arrays of n entries,
+ *   prec any of the precision enum.  All arrays are host arrays of n entries,
  *   borrowed for the call; the contexts and the output buffers must outlive
  *   the batch.  Builds the bases, uploads the plan, allocates one X arena
  *   for all contexts (the sum of their direct-term tiles) and captures the
@@ -287,6 +290,11 @@ int bse_build_blocks(bse_ctx* ctx, int32_t n, const int32_t* irrep, const int32_
  * bse_batch_run - launch the graph on the contexts' stream (asynchronous).
  *   The result of target i equals that of bse_build_blocks on ctxs[i] alone.
  * bse_batch_kernels - number of kernel launches one run performs.
+ * bse_batch_tuning - the autotuner's choices for the batch, as a JSON object
+ *   (NUL-terminated, truncated to len - 1 characters): for the split modes the
+ *   k pairs per CTA of each class of instances (same nv, nc, NG and sphere
+ *   capacities) with the measured time of each candidate, for FP32 / FP64 the
+ *   threads per CTA of the persistent direct kernel, and the X arena size.
  * bse_batch_destroy - wait for the stream and free the batch (NULL allowed);
  *   ETIMEOUT if a bounded wait of the tensor-core kernel gave up in any run.
  * bse_build_blocks_batched - create, run once, destroy.
@@ -295,6 +303,7 @@ int bse_batch_create(bse_batch** out, bse_ctx* const* ctxs, int32_t n, const int
                      int32_t prec, uint32_t terms, void* const* h_dev, const int64_t* ld);
 int bse_batch_run(bse_batch* batch);
 int bse_batch_kernels(const bse_batch* batch, int64_t* out);
+int bse_batch_tuning(const bse_batch* batch, char* buf, int64_t len);
 int bse_batch_destroy(bse_batch* batch);
 int bse_build_blocks_batched(bse_ctx* const* ctxs, int32_t n, const int32_t* irrep, const int32_t* partner,
                              int32_t prec, uint32_t terms, void* const* h_dev, const int64_t* ld);
@@ -528,6 +537,8 @@ typedef struct {
     float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */
     float ms_rotate;            /* rotated direct-term blocks of the last build (part of ms_direct) */
     int32_t reduce_kind;        /* reduction of the last TRIDIAG spectrum: 0 block in shared memory, 1 blocked (panels) */
+    int32_t tc_pairs_per_cta;   /* k pairs per CTA (sharing one W(q)) of the last split-precision build, as tuned */
+    int32_t pad_;
 } bse_stats;
 
 int bse_set_timing(bse_ctx* ctx, int32_t on);

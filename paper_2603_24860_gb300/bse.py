@@ -67,7 +67,8 @@ class BseStats(C.Structure):
                 ("ms_spectrum", C.c_float), ("ms_create", C.c_float), ("ms_create_tables", C.c_float),
                 ("ms_create_upload", C.c_float), ("ms_create_gamma", C.c_float), ("ms_create_wdiv", C.c_float),
                 ("ms_basis", C.c_float), ("solver", C.c_int32), ("ms_reduce", C.c_float),
-                ("ms_rotate", C.c_float), ("reduce_kind", C.c_int32)]
+                ("ms_rotate", C.c_float), ("reduce_kind", C.c_int32),
+                ("tc_pairs_per_cta", C.c_int32), ("pad_", C.c_int32)]
 
 
 EXPORTS = {
@@ -104,6 +105,7 @@ EXPORTS = {
                                    C.c_uint32, C.POINTER(C.c_void_p), _P64]),
     "bse_batch_run": (C.c_int, [C.c_void_p]),
     "bse_batch_kernels": (C.c_int, [C.c_void_p, _P64]),
+    "bse_batch_tuning": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "bse_batch_destroy": (C.c_int, [C.c_void_p]),
     "bse_build_blocks_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _P32, _P32, C.c_int32, C.c_uint32,
                                            C.POINTER(C.c_void_p), _P64]),
@@ -324,6 +326,14 @@ def bse_batch_kernels(batch: Batch) -> int:
     v = C.c_int64()
     _check(lib().bse_batch_kernels(batch.handle, C.byref(v)))
     return v.value
+
+
+def bse_batch_tuning(batch: Batch) -> dict:
+    """The autotuner's choices for the batch (JSON from the library)."""
+    import json as _json
+    buf = C.create_string_buffer(8192)
+    _check(lib().bse_batch_tuning(batch.handle, buf, len(buf)))
+    return _json.loads(buf.value.decode())
 
 
 def bse_batch_destroy(batch: Batch):

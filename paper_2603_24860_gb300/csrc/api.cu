@@ -8,6 +8,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -132,6 +135,7 @@ struct bse_ctx {
     int wemb_ngp = 0;
     int wemb_fp16 = -1;  // element type of wemb (1 fp16, 0 bf16)
     DevBuf groups, status;
+    DevBuf tcinst, tcq;  // the tensor-core launch's system and its work-queue counter
     DevBuf dinst;        // the context's system as a direct-kernel instance
     // band rotations kept on the device for the rotated direct-term blocks (Eq. Wtrafo)
     DevBuf gam, gam32, gkoff, gboff, mfirst, msize;
@@ -1001,7 +1005,7 @@ static void free_ctx(bse_ctx* c) {
     for (DevBuf* b : {&c->coef, &c->eps, &c->w, &c->dgk, &c->dgq, &c->dnpw, &c->dng, &c->kidx, &c->box, &c->rk,
                       &c->tau, &c->rotk, &c->vbar, &c->orbit_off, &c->members, &c->member_loc, &c->P, &c->B,
                       &c->arenaX, &c->arenaY, &c->Pmu, &c->Pt, &c->tasks, &c->tiles, &c->pairs, &c->eigA, &c->eigWork,
-                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status,
+                      &c->info, &c->Bmu, &c->wpart, &c->wsum, &c->de, &c->coef32, &c->w32, &c->wemb, &c->wexp, &c->groups, &c->status, &c->tcinst, &c->tcq,
                       &c->triScratch, &c->triSmall, &c->dinst,
                       &c->gam, &c->gam32, &c->gkoff, &c->gboff, &c->mfirst, &c->msize, &c->rots, &c->rtiles, &c->rmeta, &c->rtab_buf,
                       &c->lossScratch, &c->wsym, &c->wdivDev, &c->lzScratch})
@@ -1181,7 +1185,7 @@ int bse_build_full(bse_ctx* c, uint32_t terms, void* h, int64_t ld) {
 // The tensor-core kernel takes groups of up to kg pairs with the same
 // q = k - k' (they share W(q)): the tasks sorted by q (stable) and their groups.
 static void tc_group_tasks(const Tables& t, const std::vector<PairTask>& in, int kg, std::vector<PairTask>& sorted,
-                           std::vector<TcGroup>& groups) {
+                           std::vector<TcGroup>& groups, int inst = 0, int32_t task_base = 0) {
     std::vector<int> qof(in.size());
     for (size_t i = 0; i < in.size(); ++i) {
         int iq[3];
@@ -1196,9 +1200,10 @@ static void tc_group_tasks(const Tables& t, const std::vector<PairTask>& in, int
     groups.clear();
     for (size_t i = 0; i < order.size();) {
         TcGroup gp;
-        gp.first = (int32_t)i;
+        gp.first = task_base + (int32_t)i;
         gp.q = qof[order[i]];
         gp.count = 0;
+        gp.inst = inst;
         while (i < order.size() && qof[order[i]] == gp.q && gp.count < kg) {
             ++gp.count;
             ++i;
@@ -1249,6 +1254,125 @@ static int ensure_rot_tables(bse_ctx* c) {
     c->rtab.B = t.B;
     BSE_CUDA(cudaStreamSynchronize(c->stream));   // the host vector goes out of scope
     c->rtab_ready = true;
+    return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the tensor-core direct term: the pairs per CTA (kg, the k pairs
+// sharing one W(q) in MMA1) of a class of systems with the same shapes.  Each
+// candidate the shared memory and the 256 TMEM columns allow is timed once on
+// the class's own tasks (a persistent launch, CUDA events on the stream) and the
+// fastest is kept for the process.
+// ---------------------------------------------------------------------------
+namespace {
+struct TcClassKey {
+    int fp16, nv, nc, ngp, npw, ng;
+    bool operator<(const TcClassKey& o) const {
+        return std::tie(fp16, nv, nc, ngp, npw, ng) < std::tie(o.fp16, o.nv, o.nc, o.ngp, o.npw, o.ng);
+    }
+};
+struct TcChoice {
+    int kg = 1;
+    float ms[3] = {-1.f, -1.f, -1.f};   // measured launch times for kg = 1, 2, 4 (-1: not a candidate)
+};
+std::mutex g_tune_mu;
+std::map<TcClassKey, TcChoice> g_tc_tuned;
+
+TcClassKey tc_key(const DevSys& s, int fp16, int ngp) { return {fp16, s.nv, s.nc, ngp, s.npw_max, s.ng_max}; }
+
+std::string tc_choice_json(const TcClassKey& k, const TcChoice& c, int instances) {
+    char buf[320];
+    std::snprintf(buf, sizeof buf,
+                  "{\"class\": \"nv=%d nc=%d NGp=%d npw_max=%d ng_max=%d %s\", \"instances\": %d, "
+                  "\"pairs_per_cta\": %d, \"threads_per_cta\": 256, \"ms\": {\"1\": %.4g, \"2\": %.4g, \"4\": %.4g}}",
+                  k.nv, k.nc, k.ngp, k.npw, k.ng, k.fp16 ? "fp16" : "bf16", instances, c.kg, c.ms[0], c.ms[1],
+                  c.ms[2]);
+    return buf;
+}
+}  // namespace
+
+// time the persistent tensor-core kernel on one system's tasks (xoff inside X) for each admissible kg
+static int tune_tc(bse_ctx* c, int fp16, int ngp, const std::vector<PairTask>& tasks, void* X, int* status,
+                   TcChoice& out) {
+    out = TcChoice();
+    if (tasks.empty()) return BSE_OK;
+    DevBuf dt, dg, di, dq;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = BSE_OK;
+    float best = -1.f;
+    const int kgs[3] = {1, 2, 4};
+    do {
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            rc = fail(BSE_ECUDA, "autotuner events");
+            break;
+        }
+        if ((rc = ensure(dq, sizeof(unsigned long long))) != BSE_OK) break;
+        for (int j = 0; j < 3 && rc == BSE_OK; ++j) {
+            const int kg = kgs[j];
+            const size_t sm = tc_smem(c->S, ngp, kg);
+            if (sm == 0) continue;
+            TcInst ti{};
+            ti.S = c->S;
+            ti.coef = (const float2*)c->coef32.p;
+            ti.wemb = c->wemb.p;
+            ti.wexp = (const int*)c->wexp.p;
+            ti.ngp = ngp;
+            ti.kg = kg;
+            std::vector<PairTask> sorted;
+            std::vector<TcGroup> groups;
+            tc_group_tasks(c->t, tasks, kg, sorted, groups);
+            if ((rc = upload(dt, sorted.data(), sorted.size(), c->stream)) != BSE_OK) break;
+            if ((rc = upload(dg, groups.data(), groups.size(), c->stream)) != BSE_OK) break;
+            if ((rc = upload(di, &ti, 1, c->stream)) != BSE_OK) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == BSE_OK; ++rep) {   // the first run warms up
+                if (cudaMemsetAsync(dq.p, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
+                    cudaEventRecord(e0, c->stream) != cudaSuccess) {
+                    rc = fail(BSE_ECUDA, "autotuner launch");
+                    break;
+                }
+                rc = launch_direct_tc((const TcInst*)di.p, fp16, sm, (const PairTask*)dt.p, (const TcGroup*)dg.p,
+                                      (int64_t)groups.size(), (unsigned long long*)dq.p, X, status, c->stream,
+                                      c->wait_polls);
+                if (rc == BSE_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+                                     cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = fail(BSE_ECUDA, "autotuner timing");
+            }
+            if (rc != BSE_OK) break;
+            out.ms[j] = ms;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                out.kg = kg;
+            }
+        }
+    } while (0);
+    release(dt);
+    release(dg);
+    release(di);
+    release(dq);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+// the tuned kg of a system's class (tuned on these tasks on first use)
+static int tc_pairs_per_cta(bse_ctx* c, int fp16, int ngp, const std::vector<PairTask>& tasks, void* X, int* status,
+                            int* kg) {
+    const TcClassKey key = tc_key(c->S, fp16, ngp);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tc_tuned.find(key);
+        if (it != g_tc_tuned.end()) {
+            *kg = it->second.kg;
+            return BSE_OK;
+        }
+    }
+    TcChoice ch;
+    BSE_TRY(tune_tc(c, fp16, ngp, tasks, X, status, ch));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tc_tuned[key] = ch;
+    *kg = ch.kg;
     return BSE_OK;
 }
 
@@ -1318,11 +1442,25 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         BSE_TRY(ensure(c->arenaX, bt.xbytes / sizeof(double2) * xel));
         BSE_TRY(ensure(c->arenaY, ymax));
         std::vector<TcGroup> groups;
+        size_t tc_sm = 0;
         if (tcp && (terms & BSE_TERM_DIRECT)) {
+            // pairs per CTA tuned for this class of systems (on this batch's tasks, first use only)
+            BSE_TRY(tc_pairs_per_cta(c, fp16, ngp, bt.tasks, c->arenaX.p, (int*)c->status.p, &tc_group));
+            tc_sm = tc_smem(c->S, ngp, tc_group);
             std::vector<PairTask> sorted;
             tc_group_tasks(t, bt.tasks, tc_group, sorted, groups);
             BSE_TRY(upload(c->tasks, sorted.data(), sorted.size(), c->stream));
             BSE_TRY(upload(c->groups, groups.data(), groups.size(), c->stream));
+            TcInst ti{};
+            ti.S = c->S;
+            ti.coef = (const float2*)c->coef32.p;
+            ti.wemb = c->wemb.p;
+            ti.wexp = (const int*)c->wexp.p;
+            ti.ngp = ngp;
+            ti.kg = tc_group;
+            BSE_TRY(upload(c->tcinst, &ti, 1, c->stream));
+            BSE_TRY(ensure(c->tcq, sizeof(unsigned long long)));
+            c->stats.tc_pairs_per_cta = tc_group;
         } else {
             BSE_TRY(upload(c->tasks, bt.tasks.data(), bt.tasks.size(), c->stream));
         }
@@ -1335,10 +1473,11 @@ static int build_multi(bse_ctx* c, const std::vector<IrrepDev*>& tg, int32_t pre
         }
         if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[0], c->stream));
         if ((terms & BSE_TERM_DIRECT) && tcp) {
-            BSE_TRY(launch_direct_tc(c->S, fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ngp,
-                                     (const PairTask*)c->tasks.p,
-                                     (const TcGroup*)c->groups.p, (int64_t)groups.size(), c->arenaX.p,
-                                     (int*)c->status.p, c->stream, c->wait_polls));
+            BSE_CUDA(cudaMemsetAsync(c->tcq.p, 0, sizeof(unsigned long long), c->stream));
+            BSE_TRY(launch_direct_tc((const TcInst*)c->tcinst.p, fp16, tc_sm, (const PairTask*)c->tasks.p,
+                                     (const TcGroup*)c->groups.p, (int64_t)groups.size(),
+                                     (unsigned long long*)c->tcq.p, c->arenaX.p, (int*)c->status.p, c->stream,
+                                     c->wait_polls));
         } else if (terms & BSE_TERM_DIRECT) {
             BSE_TRY(direct_single(c, p32, (const PairTask*)c->tasks.p, (int64_t)bt.tasks.size(), c->arenaX.p));
         } else {
@@ -1468,14 +1607,17 @@ struct bse_batch {
     DevBuf insts, tasks, tiles, arenaX, pmu, rsys, rots;
     int64_t nrots = 0;
     int bmax = 0;
-    // split precisions: one tensor-core launch per instance over its q-sorted tasks
-    struct TcInst {
-        int64_t task_off = 0, group_off = 0, ngroups = 0;
-        int ngp = 0;
-    };
-    std::vector<TcInst> tci;
+    // split precisions: one persistent tensor-core launch over the q-sorted groups of all instances
+    std::vector<int> tc_ngp;       // per instance
     int tcp = 0, fp16 = 0;
-    DevBuf tctasks, tcgroups, status;
+    int64_t tc_ngroups = 0;
+    size_t tc_smem_max = 0;
+    DevBuf tctasks, tcgroups, status, tcinsts, queue;
+    // FP32 / FP64: one persistent launch of the direct kernel over the tasks of all instances
+    int64_t ntasks = 0;
+    DevSys smax{};
+    int direct_threads = 256;
+    std::string tuning;           // the autotuner's choices (JSON)
     static constexpr int kBranches = 4;   // concurrent projection branches of the graph
     DevBuf arenaY[kBranches];
     cudaGraph_t graph = nullptr;
@@ -1487,45 +1629,35 @@ static void free_batch(bse_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (DevBuf* d : {&b->insts, &b->tasks, &b->tiles, &b->arenaX, &b->pmu, &b->rsys, &b->rots, &b->tctasks,
-                      &b->tcgroups, &b->status})
+                      &b->tcgroups, &b->status, &b->tcinsts, &b->queue})
         release(*d);
     for (auto& y : b->arenaY) release(y);
     delete b;
 }
 
-// a group of instances whose direct-term tasks share one launch (and its
-// dynamic shared memory, the maximum of the group)
-struct DirectClass {
-    int64_t first = 0, count = 0;
-    DevSys smax{};
-};
-
 // the launches of one batched build, captured into the graph on stream st:
-// the direct term per shared-memory class, then the exchange and the
+// the direct term (one persistent launch), then the exchange and the
 // projections of the instances on kBranches concurrent branches (fork/join
 // through events), each branch with its own Y arena
 static int batch_launches(bse_batch* b, cudaStream_t st, cudaStream_t* br, cudaEvent_t* ev, int p32, uint32_t terms,
                           const std::vector<Batch>& plans, const std::vector<int64_t>& pmu_off,
-                          const std::vector<int>& tile_off, const std::vector<DirectClass>& classes,
+                          const std::vector<int>& tile_off,
                           const std::vector<int>& order) {
     const int nb = bse_batch::kBranches;
-    if ((terms & BSE_TERM_DIRECT) && b->tcp) {
+    if ((terms & BSE_TERM_DIRECT) && b->tcp) {   // one persistent launch over every instance's groups
         BSE_CUDA(cudaMemsetAsync(b->status.p, 0, sizeof(int), st));
-        for (size_t i = 0; i < b->tci.size(); ++i) {
-            const bse_batch::TcInst& ti = b->tci[i];
-            if (ti.ngroups == 0) continue;
-            bse_ctx* c = b->ctx[i];
-            BSE_TRY(launch_direct_tc(c->S, b->fp16, c->coef32.p, c->wemb.p, (const int*)c->wexp.p, ti.ngp,
-                                     (const PairTask*)b->tctasks.p + ti.task_off,
-                                     (const TcGroup*)b->tcgroups.p + ti.group_off, ti.ngroups, b->arenaX.p,
-                                     (int*)b->status.p, st, c->wait_polls));
-        }
+        BSE_CUDA(cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned long long), st));
+        BSE_TRY(launch_direct_tc((const TcInst*)b->tcinsts.p, b->fp16, b->tc_smem_max, (const PairTask*)b->tctasks.p,
+                                 (const TcGroup*)b->tcgroups.p, b->tc_ngroups, (unsigned long long*)b->queue.p,
+                                 b->arenaX.p, (int*)b->status.p, st, b->ctx[0]->wait_polls));
     }
     if (terms & BSE_TERM_DIRECT) {
-        for (const DirectClass& dc : classes)
-            if (!b->tcp)
-                BSE_TRY(launch_direct_multi((const DirectInst*)b->insts.p, dc.smax, p32,
-                                            (const PairTask*)b->tasks.p + dc.first, dc.count, b->arenaX.p, st));
+        if (!b->tcp && b->ntasks > 0) {   // one persistent launch over every instance's tasks
+            BSE_CUDA(cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned long long), st));
+            BSE_TRY(launch_direct_persistent((const DirectInst*)b->insts.p, b->smax, p32, (const PairTask*)b->tasks.p,
+                                             b->ntasks, (unsigned long long*)b->queue.p, b->direct_threads, 0,
+                                             b->arenaX.p, st));
+        }
         if (b->nrots > 0)   // pairs rotated from their seeds (Eq. Wtrafo)
             BSE_TRY(launch_rotate_multi((const RotSys*)b->rsys.p, b->bmax, p32, (const RotTask*)b->rots.p, b->nrots,
                                         b->arenaX.p, st));
@@ -1580,11 +1712,11 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
         if (terms & BSE_TERM_EXCHANGE) BSE_TRY(ensure_exchange_vectors(c));
         if (p32 && (terms & BSE_TERM_DIRECT)) BSE_TRY(ensure_narrow(c));
         if (b->tcp) {
-            bse_batch::TcInst ti;
+            int ngp = 0;
             size_t sm = 0;
-            BSE_TRY(tc_supported(c->S, ti.ngp, sm));
-            BSE_TRY(ensure_wemb(c, ti.ngp, b->fp16));
-            b->tci.push_back(ti);
+            BSE_TRY(tc_supported(c->S, ngp, sm));
+            BSE_TRY(ensure_wemb(c, ngp, b->fp16));
+            b->tc_ngp.push_back(ngp);
         }
         b->h.push_back(h[i]);
         b->ld.push_back(ld[i]);
@@ -1593,7 +1725,6 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
     std::vector<Batch> plans(n);
     std::vector<int64_t> xbase(n + 1, 0), pmu_off(n + 1, 0);
     std::vector<int> tile_off(n + 1, 0);
-    std::vector<PairTask> tasks;
     std::vector<TileTask> tiles;
     std::vector<DirectInst> insts(n);
     std::vector<RotSys> rsys(n);
@@ -1636,53 +1767,123 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
         }
     }
     b->nrots = (int64_t)rots.size();
-    std::vector<PairTask> tctasks;
-    std::vector<TcGroup> tcgroups;
-    if (b->tcp)
-        for (int32_t i = 0; i < n; ++i) {
+    const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
+    BSE_TRY(ensure(b->arenaX, (size_t)xbase[n] * xel));
+    BSE_TRY(ensure(b->queue, sizeof(unsigned long long)));
+    BSE_TRY(ensure(b->status, sizeof(int)));
+    // instances in decreasing order of their direct-term work per k pair, so that the work queue
+    // of the persistent launch hands out the longest tasks first
+    std::vector<int> bycost(n);
+    for (int32_t i = 0; i < n; ++i) bycost[i] = i;
+    auto pair_cost = [&](int i) {
+        const DevSys& sy = b->ctx[i]->S;
+        return (double)sy.ng_max * ((double)sy.nv * sy.nv * sy.ng_max + (double)sy.nc * sy.nc * sy.nv * sy.nv) +
+               (double)sy.npw_max * sy.ng_max * (sy.nc * sy.nc + sy.nv * sy.nv);
+    };
+    std::stable_sort(bycost.begin(), bycost.end(), [&](int x, int y) { return pair_cost(x) > pair_cost(y); });
+    std::string tune = "{";
+    if (b->tcp && (terms & BSE_TERM_DIRECT)) {
+        // pairs per CTA of each class of instances (tuned on the class's first instance), then one
+        // group list over all instances for the persistent tensor-core launch
+        std::vector<TcInst> tinst(n);
+        std::vector<PairTask> tctasks;
+        std::vector<TcGroup> tcgroups;
+        std::map<TcClassKey, int> class_count;
+        for (int q = 0; q < n; ++q) {
+            const int i = bycost[q];
             bse_ctx* c = b->ctx[i];
-            int ngp = 0, kg = 1;
-            size_t sm = 0;
-            BSE_TRY(tc_supported(c->S, ngp, sm, &kg));
-            std::vector<PairTask> in(plans[i].tasks), sorted;
-            std::vector<TcGroup> gr;
+            std::vector<PairTask> in(plans[i].tasks);
             for (PairTask& t : in) t.xoff += xbase[i];
-            tc_group_tasks(c->t, in, kg, sorted, gr);
-            b->tci[i].task_off = (int64_t)tctasks.size();
-            b->tci[i].group_off = (int64_t)tcgroups.size();
-            b->tci[i].ngroups = (int64_t)gr.size();
+            int kg = 1;
+            BSE_TRY(tc_pairs_per_cta(c, b->fp16, b->tc_ngp[i], in, b->arenaX.p, (int*)b->status.p, &kg));
+            class_count[tc_key(c->S, b->fp16, b->tc_ngp[i])] += 1;
+            TcInst& ti = tinst[i];
+            ti.S = c->S;
+            ti.coef = (const float2*)c->coef32.p;
+            ti.wemb = c->wemb.p;
+            ti.wexp = (const int*)c->wexp.p;
+            ti.ngp = b->tc_ngp[i];
+            ti.kg = kg;
+            b->tc_smem_max = std::max(b->tc_smem_max, tc_smem(c->S, ti.ngp, kg));
+            std::vector<PairTask> sorted;
+            std::vector<TcGroup> gr;
+            tc_group_tasks(c->t, in, kg, sorted, gr, i, (int32_t)tctasks.size());
             tctasks.insert(tctasks.end(), sorted.begin(), sorted.end());
             tcgroups.insert(tcgroups.end(), gr.begin(), gr.end());
         }
-    // direct-term tasks grouped by shared-memory class (rounded to 8 KB), so a
-    // small system does not run at the occupancy of the largest one
-    std::vector<int> byclass(n);
-    for (int32_t i = 0; i < n; ++i) byclass[i] = i;
-    auto cls = [&](int i) { return (direct_smem(b->ctx[i]->S, p32) + 8191) / 8192; };
-    std::stable_sort(byclass.begin(), byclass.end(), [&](int x, int y) { return cls(x) < cls(y); });
-    std::vector<DirectClass> classes;
-    for (int q = 0; q < n; ++q) {
-        const int i = byclass[q];
-        if (classes.empty() || cls(byclass[q - 1]) != cls(i)) {
-            DirectClass dc;
-            dc.first = (int64_t)tasks.size();
-            dc.smax = b->ctx[i]->S;
-            classes.push_back(dc);
+        b->tc_ngroups = (int64_t)tcgroups.size();
+        BSE_TRY(upload(b->tctasks, tctasks.data(), tctasks.size(), b->stream));
+        BSE_TRY(upload(b->tcgroups, tcgroups.data(), tcgroups.size(), b->stream));
+        BSE_TRY(upload(b->tcinsts, tinst.data(), tinst.size(), b->stream));
+        tune += "\"direct_kernel\": \"direct_tc_kernel (persistent, one launch)\", \"classes\": [";
+        bool first = true;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto& kv : class_count) {
+            tune += (first ? "" : ", ") + tc_choice_json(kv.first, g_tc_tuned[kv.first], kv.second);
+            first = false;
         }
-        DirectClass& dc = classes.back();
-        const DevSys& s = b->ctx[i]->S;
-        dc.smax.nb = std::max(dc.smax.nb, s.nb);
-        dc.smax.nv = std::max(dc.smax.nv, s.nv);
-        dc.smax.nc = std::max(dc.smax.nc, s.nc);
-        dc.smax.npw_max = std::max(dc.smax.npw_max, s.npw_max);
-        dc.smax.ng_max = std::max(dc.smax.ng_max, s.ng_max);
-        for (PairTask t : plans[i].tasks) {
-            t.xoff += xbase[i];
-            t.flags |= i << 1;
-            tasks.push_back(t);
+        tune += "]";
+    } else if (terms & BSE_TERM_DIRECT) {
+        // FP32 / FP64: every instance's tasks in one list for the persistent direct kernel
+        std::vector<PairTask> tasks_all;
+        for (int q = 0; q < n; ++q) {
+            const int i = bycost[q];
+            const DevSys& sy = b->ctx[i]->S;
+            if (q == 0) b->smax = sy;
+            b->smax.nb = std::max(b->smax.nb, sy.nb);
+            b->smax.nv = std::max(b->smax.nv, sy.nv);
+            b->smax.nc = std::max(b->smax.nc, sy.nc);
+            b->smax.npw_max = std::max(b->smax.npw_max, sy.npw_max);
+            b->smax.ng_max = std::max(b->smax.ng_max, sy.ng_max);
+            for (PairTask t : plans[i].tasks) {
+                t.xoff += xbase[i];
+                t.flags |= i << 1;
+                tasks_all.push_back(t);
+            }
         }
-        dc.count = (int64_t)tasks.size() - dc.first;
+        b->ntasks = (int64_t)tasks_all.size();
+        BSE_TRY(upload(b->tasks, tasks_all.data(), tasks_all.size(), b->stream));
+        BSE_TRY(upload(b->insts, insts.data(), insts.size(), b->stream));
+        // threads per CTA of the persistent launch, timed on the batch's own tasks
+        float ms[2] = {-1.f, -1.f};
+        const int thr[2] = {128, 256};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        BSE_CUDA(cudaEventCreate(&e0));
+        BSE_CUDA(cudaEventCreate(&e1));
+        int rc = BSE_OK;
+        for (int j = 0; j < 2 && rc == BSE_OK && b->ntasks > 0; ++j)
+            for (int rep = 0; rep < 2 && rc == BSE_OK; ++rep) {
+                if (cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned long long), b->stream) != cudaSuccess ||
+                    cudaEventRecord(e0, b->stream) != cudaSuccess) {
+                    rc = fail(BSE_ECUDA, "autotuner launch");
+                    break;
+                }
+                rc = launch_direct_persistent((const DirectInst*)b->insts.p, b->smax, p32, (const PairTask*)b->tasks.p,
+                                              b->ntasks, (unsigned long long*)b->queue.p, thr[j], 0, b->arenaX.p,
+                                              b->stream);
+                if (rc == BSE_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                                     cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms[j], e0, e1) != cudaSuccess))
+                    rc = fail(BSE_ECUDA, "autotuner timing");
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        BSE_TRY(rc);
+        b->direct_threads = (ms[0] >= 0.f && ms[0] < ms[1]) ? 128 : 256;
+        char buf[256];
+        std::snprintf(buf, sizeof buf,
+                      "\"direct_kernel\": \"direct_persistent_kernel (one launch)\", \"threads_per_cta\": %d, "
+                      "\"ms\": {\"128\": %.4g, \"256\": %.4g}", b->direct_threads, ms[0], ms[1]);
+        tune += buf;
     }
+    // the arena: one X arena holds every instance's tiles (its size in MB)
+    {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "%s\"x_arena_mb\": %.1f}", tune.size() > 1 ? ", " : "",
+                      (double)xbase[n] * xel / (1 << 20));
+        tune += buf;
+    }
+    b->tuning = tune;
     // projection order: largest first, dealt round-robin to the branches
     std::vector<int> order(n);
     for (int32_t i = 0; i < n; ++i) order[i] = i;
@@ -1690,18 +1891,9 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
     size_t ybr[bse_batch::kBranches] = {0, 0, 0, 0};
     for (size_t q = 0; q < order.size(); ++q)
         ybr[q % bse_batch::kBranches] = std::max(ybr[q % bse_batch::kBranches], ysz[order[q]]);
-    const size_t xel = p32 ? sizeof(float2) : sizeof(double2);
-    BSE_TRY(upload(b->insts, insts.data(), insts.size(), b->stream));
-    BSE_TRY(upload(b->tasks, tasks.data(), tasks.size(), b->stream));
     BSE_TRY(upload(b->tiles, tiles.data(), tiles.size(), b->stream));
     BSE_TRY(upload(b->rsys, rsys.data(), rsys.size(), b->stream));
     BSE_TRY(upload(b->rots, rots.data(), rots.size(), b->stream));
-    if (b->tcp) {
-        BSE_TRY(upload(b->tctasks, tctasks.data(), tctasks.size(), b->stream));
-        BSE_TRY(upload(b->tcgroups, tcgroups.data(), tcgroups.size(), b->stream));
-        BSE_TRY(ensure(b->status, sizeof(int)));
-    }
-    BSE_TRY(ensure(b->arenaX, (size_t)xbase[n] * xel));
     for (int j = 0; j < bse_batch::kBranches; ++j) BSE_TRY(ensure(b->arenaY[j], ybr[j]));
     BSE_TRY(ensure(b->pmu, sizeof(double2) * (size_t)std::max<int64_t>(pmu_off[n], 1)));
     BSE_CUDA(cudaStreamSynchronize(b->stream));
@@ -1727,7 +1919,7 @@ static int batch_create_impl(bse_batch* b, int32_t n, const int32_t* irrep, cons
         cleanup();
         return fail(BSE_ECUDA, "graph capture: %s", cudaGetErrorString(be));
     }
-    const int rc = batch_launches(b, cs, br, ev, p32, terms, plans, pmu_off, tile_off, classes, order);
+    const int rc = batch_launches(b, cs, br, ev, p32, terms, plans, pmu_off, tile_off, order);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &g);
     cleanup();
@@ -1780,6 +1972,15 @@ int bse_batch_kernels(const bse_batch* b, int64_t* out) {
     clear_error();
     if (!b || !out) return fail(BSE_EINVAL, "null argument");
     *out = b->kernels;
+    return BSE_OK;
+}
+
+int bse_batch_tuning(const bse_batch* b, char* buf, int64_t len) {
+    clear_error();
+    if (!b || !buf || len < 1) return fail(BSE_EINVAL, "null argument");
+    const size_t m = std::min<size_t>(b->tuning.size(), (size_t)len - 1);
+    std::memcpy(buf, b->tuning.data(), m);
+    buf[m] = 0;
     return BSE_OK;
 }
 

@@ -14,6 +14,8 @@
 // list with its lanes spread over band pairs, so every issued FMA is useful.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bse {
@@ -62,23 +64,12 @@ __host__ __device__ inline DirectPlan direct_plan(int cplx_bytes, int nb, int nv
 
 constexpr int kMaxSlots = 4;   // band pairs per lane: nc^2 + nv^2 <= 128
 
-// kBatch: the task's system comes from insts[flags >> 1] (copied into shared
-// memory); otherwise every task uses the kernel parameter `one`.
-template <typename R, bool kBatch>
-__global__ void __launch_bounds__(256) direct_kernel(const DirectInst* __restrict__ insts,
-                                                     const __grid_constant__ DirectInst one,
-                                                     const PairTask* __restrict__ tasks, typename C2<R>::T* X) {
+// One k pair (task t) of system I with the whole CTA; smem: the dynamic shared
+// memory of the CTA (direct_plan of the system).
+template <typename R>
+__device__ __forceinline__ void direct_task(const DirectInst& I, const PairTask t, typename C2<R>::T* X,
+                                            unsigned char* smem) {
     using V = typename C2<R>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ DirectInst sI;
-    const PairTask t = tasks[blockIdx.x];
-    if (kBatch) {   // the task's system, copied cooperatively (one round trip)
-        const unsigned long long* src = (const unsigned long long*)(insts + (t.flags >> 1));
-        unsigned long long* dst = (unsigned long long*)&sI;
-        for (int i = threadIdx.x; i < (int)(sizeof(DirectInst) / 8); i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
-    }
-    const DirectInst& I = kBatch ? sI : one;
     const DevSys& S = I.S;
     const V* __restrict__ coef = (const V*)I.coef;
     const V* __restrict__ wq = (const V*)I.w;
@@ -210,6 +201,55 @@ __global__ void __launch_bounds__(256) direct_kernel(const DirectInst* __restric
     }
 }
 
+// one CTA per task; kBatch: the task's system comes from insts[flags >> 1]
+// (copied into shared memory), otherwise every task uses the parameter `one`
+template <typename R, bool kBatch>
+__global__ void __launch_bounds__(256) direct_kernel(const DirectInst* __restrict__ insts,
+                                                     const __grid_constant__ DirectInst one,
+                                                     const PairTask* __restrict__ tasks, typename C2<R>::T* X) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DirectInst sI;
+    const PairTask t = tasks[blockIdx.x];
+    if (kBatch) {   // the task's system, copied cooperatively (one round trip)
+        const unsigned long long* src = (const unsigned long long*)(insts + (t.flags >> 1));
+        unsigned long long* dst = (unsigned long long*)&sI;
+        for (int i = threadIdx.x; i < (int)(sizeof(DirectInst) / 8); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    direct_task<R>(kBatch ? sI : one, t, X, smem);
+}
+
+// Persistent form for batches: a grid sized to the GPU takes the tasks of all
+// systems from one work queue (a device counter, zero on entry), each CTA a
+// task at a time, in the order of the list (largest systems first).
+template <typename R>
+__global__ void __launch_bounds__(256) direct_persistent_kernel(const DirectInst* __restrict__ insts,
+                                                                const PairTask* __restrict__ tasks, int64_t ntasks,
+                                                                unsigned long long* counter, typename C2<R>::T* X) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DirectInst sI;
+    __shared__ long long s_t;
+    __shared__ int s_inst;
+    if (threadIdx.x == 0) s_inst = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long ti = s_t;
+        if (ti >= ntasks) break;
+        const PairTask t = tasks[ti];
+        const int inst = t.flags >> 1;
+        if (inst != s_inst) {   // uniform: every thread reads the same s_inst
+            const unsigned long long* src = (const unsigned long long*)(insts + inst);
+            unsigned long long* dst = (unsigned long long*)&sI;
+            for (int i = threadIdx.x; i < (int)(sizeof(DirectInst) / 8); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            if (threadIdx.x == 0) s_inst = inst;
+        }
+        direct_task<R>(sI, t, X, smem);
+        __syncthreads();   // shared memory and s_t are reused by the next task
+    }
+}
+
 template <typename R, bool kBatch>
 static int launch_direct_t(const DirectInst* insts, const DirectInst& one, const DevSys& s, const PairTask* tasks,
                            int64_t ntasks, void* X, cudaStream_t st) {
@@ -234,11 +274,43 @@ static int launch_direct_t(const DirectInst* insts, const DirectInst& one, const
     return BSE_OK;
 }
 
-int launch_direct_multi(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks, int64_t ntasks,
-                        void* X, cudaStream_t st) {
-    DirectInst none{};
-    return prec32 ? launch_direct_t<float, true>(insts, none, smax, tasks, ntasks, X, st)
-                  : launch_direct_t<double, true>(insts, none, smax, tasks, ntasks, X, st);
+
+template <typename R>
+static int launch_direct_persistent_t(const DirectInst* insts, const DevSys& s, const PairTask* tasks, int64_t ntasks,
+                                      unsigned long long* counter, int threads, int ctas_per_sm, void* X,
+                                      cudaStream_t st) {
+    using V = typename C2<R>::T;
+    if (ntasks == 0) return BSE_OK;
+    if (s.nc * s.nc + s.nv * s.nv > 32 * kMaxSlots)
+        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", 32 * kMaxSlots);
+    if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
+    if (threads != 128 && threads != 256) return fail(BSE_EINVAL, "threads per CTA must be 128 or 256");
+    DirectPlan pl = direct_plan((int)sizeof(V), s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
+    if (pl.total + sizeof(DirectInst) > 227 * 1024)
+        return fail(BSE_EUNSUPPORTED, "direct kernel needs %zu bytes of shared memory", pl.total);
+    cudaError_t e = cudaFuncSetAttribute(direct_persistent_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pl.total);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", pl.total, cudaGetErrorString(e));
+    int dev = 0, sms = 0, per_sm = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_persistent_kernel<R>, threads, pl.total));
+    if (per_sm < 1) return fail(BSE_EUNSUPPORTED, "direct kernel: no CTA fits an SM");
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, ntasks);
+    direct_persistent_kernel<R><<<(unsigned)grid, threads, pl.total, st>>>(insts, tasks, ntasks, counter, (V*)X);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct launch: %s", cudaGetErrorString(e));
+    return BSE_OK;
+}
+
+int launch_direct_persistent(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks,
+                             int64_t ntasks, unsigned long long* counter, int threads, int ctas_per_sm, void* X,
+                             cudaStream_t st) {
+    return prec32 ? launch_direct_persistent_t<float>(insts, smax, tasks, ntasks, counter, threads, ctas_per_sm, X, st)
+                  : launch_direct_persistent_t<double>(insts, smax, tasks, ntasks, counter, threads, ctas_per_sm, X,
+                                                       st);
 }
 
 int launch_direct(const DirectInst& one, int prec32, const PairTask* tasks, int64_t ntasks, void* X, cudaStream_t st) {

@@ -25,6 +25,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "grid_sync.h"
 #include "internal.h"
 #include "tc_ptx.h"
@@ -114,299 +116,337 @@ __device__ __forceinline__ void cmacc32(float2& acc, float2 a, float2 b) {   // 
     acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
 }
 
+// Persistent kernel: a grid sized to the GPU takes groups from a work queue (a
+// device counter, zero before the launch) over the systems of the launch (one,
+// or the instances of a batch: group.inst indexes insts).  Each CTA allocates
+// its tensor memory once and processes one group at a time; the mbarriers are
+// reused, their phases counted across groups.  A wait that gives up stops the
+// CTA: it lets the copy or the MMAs it waited for finish (the default limit),
+// raises *status, frees its tensor memory and returns.
 template <typename E>
-__global__ void __launch_bounds__(256, 1) direct_tc_kernel(DevSys S, const float2* __restrict__ coef,
-                                                           const E* __restrict__ wemb, const int* __restrict__ wexp,
+__global__ void __launch_bounds__(256, 1) direct_tc_kernel(const TcInst* __restrict__ insts,
                                                            const PairTask* __restrict__ tasks,
-                                                           const TcGroup* __restrict__ groups, int ngp, int kg,
-                                                           float2* X, int* status, long spin) {
+                                                           const TcGroup* __restrict__ groups, int64_t ngroups,
+                                                           unsigned long long* counter, float2* X, int* status,
+                                                           long spin) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int nv = S.nv, nc = S.nc, nb = S.nb, P = nc * nc + nv * nv, ncc = nc * nc, nvv = nv * nv;
-    const TcPlan pl = tc_plan(kg, ngp, nb, nv, nc, S.npw_max, S.ng_max);
-    const int K2 = 2 * ngp;                             // K of MMA2
-    const int NR = tc_rows(nv);                         // rows per pair (N of MMA2)
-    const int NB = NR * kg;                             // N of MMA1 (rows of B1 and B2)
-    unsigned char* Am = smem;   // the pair-density staging, then W planes, A2 (hi | lo) and the epilogue staging
-    unsigned char* Bm = Am + pl.a;                      // B1 planes, then B2 (hi | lo)
-    float2* RC = (float2*)(Bm + pl.b);                  // [kg][ncc][ngp] rho_cc'
-    float2* ckT = (float2*)Am;
-    float2* ckpT = (float2*)((unsigned char*)ckT + pl.st_coef);
-    int* cnt = (int*)((unsigned char*)ckpT + pl.st_coef);
-    int* list = (int*)((unsigned char*)cnt + pl.st_cnt);
-    float2* rho = (float2*)((unsigned char*)list + pl.st_list);   // [ng][P]
-    uint64_t* mbar = (uint64_t*)((unsigned char*)RC + pl.rc);
-    uint32_t* slot = (uint32_t*)(mbar + 4);
-    const size_t wpl = (size_t)128 * ngp * 2;           // one W plane (bytes)
-    const size_t bpl = (size_t)NB * ngp * 2;            // one B1 plane
-    const size_t a2h = (size_t)128 * K2 * 2;            // A2 hi (lo follows)
-    const size_t b2h = (size_t)NB * K2 * 2;             // B2 hi (lo follows)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
-    const TcGroup grp = groups[blockIdx.x];
-    const int q = grp.q, ng = S.ng[q];
+    __shared__ __align__(8) uint64_t mbar[3];
+    __shared__ uint32_t slot;
+    __shared__ long long s_g;
+    __shared__ __align__(16) TcInst sI;
     __shared__ unsigned s_max;      // block maximum of an operand (float bits)
     __shared__ int s_erho[kMaxG];   // scale exponent of each pair's densities
     // TMEM: T_r in columns [0, NB), T_i in [NB, 2 NB), K^d of pair p in [2 NB + NR p, 2 NB + NR (p + 1))
     constexpr uint32_t kCols = kTmemCols;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
 
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
         tc::mbar_init(&mbar[1], 1);
         tc::mbar_init(&mbar[2], 1);
     }
-    if (warp == 0) tc::tmem_alloc(slot, kCols);
-    // zero the B1 planes (rows of absent pairs and of vv' >= nv^2 must be finite: they feed the scale of T)
-    for (size_t e = tid * 16; e < pl.b; e += blockDim.x * 16) *(uint4*)(Bm + e) = make_uint4(0, 0, 0, 0);
+    if (warp == 0) tc::tmem_alloc(&slot, kCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = *slot;
+    const uint32_t tmem = slot;
+    uint32_t ph01 = 0;   // completed phases of mbar[0] and mbar[1] (one per group)
+    uint32_t ph2 = 0;    // completed phases of mbar[2] (one per pair)
+    bool ok = true;
 
-    // ---- pair densities (CUDA cores, FP32) for every pair of the group ----
-    for (int p = 0; p < grp.count; ++p) {
-        const PairTask t = tasks[grp.first + p];
-        if (tid == 0) s_max = 0u;
-        int fold[3];
-        const int n3[3] = {S.n1, S.n2, S.n3};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int ik = S.kidx[3 * t.k + a], ikp = S.kidx[3 * t.kp + a];
-            int iq = (ik - ikp + n3[a]) % n3[a];
-            fold[a] = (ikp + iq - ik) / n3[a];
-        }
-        const int npkp = S.npw[t.kp];
-        for (int e = tid; e < nb * S.npw_max; e += blockDim.x) {
-            int b = e / S.npw_max, i = e % S.npw_max;
-            ckT[i * nb + b] = coef[((int64_t)t.k * nb + b) * S.npw_max + i];
-            ckpT[i * nb + b] = coef[((int64_t)t.kp * nb + b) * S.npw_max + i];
-        }
-        const int* gq = S.gq + (int64_t)q * S.ng_max * 3;
-        const int* gk = S.gk + (int64_t)t.kp * S.npw_max * 3;
-        for (int g = warp; g < ng; g += nwarp) {
-            int c = 0;
-            for (int j0 = 0; j0 < npkp; j0 += 32) {
-                int j = j0 + lane, idx = -1;
-                if (j < npkp) {
-                    int x0 = gk[3 * j] + gq[3 * g] + fold[0] - S.blo[0];
-                    int x1 = gk[3 * j + 1] + gq[3 * g + 1] + fold[1] - S.blo[1];
-                    int x2 = gk[3 * j + 2] + gq[3 * g + 2] + fold[2] - S.blo[2];
-                    if ((unsigned)x0 < (unsigned)S.bdim[0] && (unsigned)x1 < (unsigned)S.bdim[1] &&
-                        (unsigned)x2 < (unsigned)S.bdim[2])
-                        idx = S.box[(int64_t)t.k * S.bvol + ((int64_t)x0 * S.bdim[1] + x1) * S.bdim[2] + x2];
-                }
-                unsigned m = __ballot_sync(0xffffffffu, idx >= 0);
-                if (idx >= 0) list[g * S.npw_max + c + __popc(m & ((1u << lane) - 1u))] = idx | (j << 16);
-                c += __popc(m);
-            }
-            if (lane == 0) cnt[g] = c;
+    for (;;) {
+        if (tid == 0) s_g = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long gi = s_g;
+        if (gi >= ngroups) break;
+        const TcGroup grp = groups[gi];
+        {   // the group's system
+            const unsigned long long* src = (const unsigned long long*)(insts + grp.inst);
+            unsigned long long* dst = (unsigned long long*)&sI;
+            for (int i = tid; i < (int)(sizeof(TcInst) / 8); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
-        for (int g = warp; g < ng; g += nwarp) {
-            const int* L = list + g * S.npw_max;
-            const int len = cnt[g];
-            for (int p0 = 0; p0 < P; p0 += 32) {
-                const int pp = p0 + lane;
-                if (pp >= P) break;
-                int na, nbp;
-                if (pp < ncc) {
-                    na = nv + pp / nc;
-                    nbp = nv + pp % nc;
-                } else {
-                    na = (pp - ncc) / nv;
-                    nbp = (pp - ncc) % nv;
-                }
-                float2 acc = make_float2(0.f, 0.f);
-                for (int e = 0; e < len; ++e) {
-                    const int ij = L[e];
-                    cmacc32(acc, ckT[(ij & 0xffff) * nb + na], ckpT[(ij >> 16) * nb + nbp]);
-                }
-                rho[g * P + pp] = acc;
-            }
-        }
-        __syncthreads();
-        // one scale for all densities of the pair
-        float mx = 0.f;
-        for (int e = tid; e < ng * P; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(rho[e].x), fabsf(rho[e].y)));
-        const int erho = scale_exp(block_max(mx, &s_max));
-        const float srho = pow2f(erho);
-        if (tid == 0) s_erho[p] = erho;
-        // B1 rows p*NR + vv': planes rho_r, rho_i, -rho_i of rho_vv' (hi, lo), K index Q; rho_cc' kept for MMA2
-        for (int e = tid; e < nvv * ngp; e += blockDim.x) {
-            const int vv = e / ngp, Q = e % ngp;
-            const float2 r = Q < ng ? rho[Q * P + ncc + vv] : make_float2(0.f, 0.f);
-            const uint32_t o = core_off(p * NR + vv, Q, ngp);
-            E h, l;
-            split16(r.x * srho, h, l);
-            *(E*)(Bm + o) = h;
-            *(E*)(Bm + bpl + o) = l;
-            split16(r.y * srho, h, l);
-            *(E*)(Bm + 2 * bpl + o) = h;
-            *(E*)(Bm + 3 * bpl + o) = l;
-            split16(-r.y * srho, h, l);
-            *(E*)(Bm + 4 * bpl + o) = h;
-            *(E*)(Bm + 5 * bpl + o) = l;
-        }
-        for (int e = tid; e < ncc * ngp; e += blockDim.x) {
-            const int cc = e / ngp, Q = e % ngp;
-            RC[((size_t)p * ncc + cc) * ngp + Q] = Q < ng ? rho[Q * P + cc] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-    }
+        const DevSys& S = sI.S;
+        const float2* __restrict__ coef = sI.coef;
+        const E* __restrict__ wemb = (const E*)sI.wemb;
+        const int* __restrict__ wexp = sI.wexp;
+        const int ngp = sI.ngp, kg = sI.kg;
+        const int nv = S.nv, nc = S.nc, nb = S.nb, P = nc * nc + nv * nv, ncc = nc * nc, nvv = nv * nv;
+        const TcPlan pl = tc_plan(kg, ngp, nb, nv, nc, S.npw_max, S.ng_max);
+        const int K2 = 2 * ngp;                             // K of MMA2
+        const int NR = tc_rows(nv);                         // rows per pair (N of MMA2)
+        const int NB = NR * kg;                             // N of MMA1 (rows of B1 and B2)
+        unsigned char* Am = smem;   // the pair-density staging, then W planes, A2 (hi | lo) and the epilogue staging
+        unsigned char* Bm = Am + pl.a;                      // B1 planes, then B2 (hi | lo)
+        float2* RC = (float2*)(Bm + pl.b);                  // [kg][ncc][ngp] rho_cc'
+        float2* ckT = (float2*)Am;
+        float2* ckpT = (float2*)((unsigned char*)ckT + pl.st_coef);
+        int* cnt = (int*)((unsigned char*)ckpT + pl.st_coef);
+        int* list = (int*)((unsigned char*)cnt + pl.st_cnt);
+        float2* rho = (float2*)((unsigned char*)list + pl.st_list);   // [ng][P]
+        const size_t wpl = (size_t)128 * ngp * 2;           // one W plane (bytes)
+        const size_t bpl = (size_t)NB * ngp * 2;            // one B1 plane
+        const size_t a2h = (size_t)128 * K2 * 2;            // A2 hi (lo follows)
+        const size_t b2h = (size_t)NB * K2 * 2;             // B2 hi (lo follows)
+        const int q = grp.q, ng = S.ng[q];
 
-    // ---- W(q) into the region of the staging, now dead (generic-proxy accesses ordered before the bulk copy) ----
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-        const uint32_t bytes = (uint32_t)(4 * wpl);
-        tc::mbar_expect_tx(&mbar[0], bytes);
-        tc::bulk_g2s(Am, wemb + (size_t)q * 4 * 128 * ngp, bytes, &mbar[0]);
-        s_max = 0u;   // read only after the barriers below
-    }
-    // ---- MMA1: T_r and T_i for all pairs (M = 128, N = NR kg, K = ngp) ----
-    // a wait that gives up still lets the operation it waited for finish (the
-    // default limit) before the region is reused, TMEM is freed or the CTA exits
-    const bool got_w = tc::mbar_wait(&mbar[0], 0, spin);
-    if (!got_w) tc::mbar_wait(&mbar[0], 0, kMbarSpinLimit);
-    bool ok = __syncthreads_and(got_w) != 0;
-    tc::fence_proxy_async();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t idesc1 = tc::idesc_f16(128, NB, Elem<E>::kBf16);
-    if (tid == 0 && ok) {
-        const uint32_t lbo = 128, sbo = (uint32_t)(ngp / 8) * 128;
-        const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm);
-        const uint32_t Wr = a0, Wi = a0 + 2 * (uint32_t)wpl;
-        const uint32_t Rr = b0, Ri = b0 + 2 * (uint32_t)bpl, Rn = b0 + 4 * (uint32_t)bpl;
-        // d += A B over the three split products (A_hi B_hi, A_hi B_lo, A_lo B_hi)
-        auto chain = [&](uint32_t d, uint32_t A, uint32_t B, bool first) {
-            for (int prod = 0; prod < 3; ++prod) {
-                const uint32_t ab = A + (prod == 2 ? (uint32_t)wpl : 0u);
-                const uint32_t bb = B + (prod == 1 ? (uint32_t)bpl : 0u);
-                for (int ks = 0; ks < ngp / 16; ++ks)
-                    tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
-                                idesc1, !(first && prod == 0 && ks == 0));
+        // zero the B1 planes (rows of absent pairs and of vv' >= nv^2 must be finite: they feed the scale of T)
+        for (size_t e = tid * 16; e < pl.b; e += blockDim.x * 16) *(uint4*)(Bm + e) = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+
+        // ---- pair densities (CUDA cores, FP32) for every pair of the group ----
+        for (int p = 0; p < grp.count; ++p) {
+            const PairTask t = tasks[grp.first + p];
+            if (tid == 0) s_max = 0u;
+            int fold[3];
+            const int n3[3] = {S.n1, S.n2, S.n3};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int ik = S.kidx[3 * t.k + a], ikp = S.kidx[3 * t.kp + a];
+                int iq = (ik - ikp + n3[a]) % n3[a];
+                fold[a] = (ikp + iq - ik) / n3[a];
             }
-        };
-        chain(tmem, Wr, Rr, true);                    // T_r = Wr rho_r + Wi rho_i
-        chain(tmem, Wi, Ri, false);
-        chain(tmem + (uint32_t)NB, Wi, Rr, true);     // T_i = Wi rho_r - Wr rho_i
-        chain(tmem + (uint32_t)NB, Wr, Rn, false);
-        tc::mma_commit(&mbar[1]);
-    }
-    {
-        const bool got = ok && tc::mbar_wait(&mbar[1], 0, spin);
-        if (ok && !got) tc::mbar_wait(&mbar[1], 0, kMbarSpinLimit);
-        ok = __syncthreads_and(got) != 0;
-    }
-    tc::fence_after();
-    // ---- T: TMEM -> scale -> split -> B2 (rows p*NR + vv'; K index Q for T_r, ngp + Q for T_i) ----
-    int eT = 0;
-    if (ok) {
-        const int row = 32 * (warp & 3) + lane;                 // lane of TMEM = Q
-        const int half = warp >> 2;                             // warps 0..3: T_r, 4..7: T_i
-        const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * NB);
-        float mx = 0.f;
-        for (int cb = 0; cb < NB; cb += 8) {
-            float v[8];
-            tc::tmem_ld8(tbase + (uint32_t)cb, v);
-            if (row < ngp)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fabsf(v[j]));
-        }
-        eT = scale_exp(block_max(mx, &s_max));
-        const float sT = pow2f(eT);
-        for (int cb = 0; cb < NB; cb += 8) {
-            float v[8];
-            tc::tmem_ld8(tbase + (uint32_t)cb, v);
-            if (row < ngp) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t o = core_off(cb + j, half * ngp + row, K2);
-                    E h, l;
-                    split16(v[j] * sT, h, l);
-                    *(E*)(Bm + o) = h;
-                    *(E*)(Bm + b2h + o) = l;
+            const int npkp = S.npw[t.kp];
+            for (int e = tid; e < nb * S.npw_max; e += blockDim.x) {
+                int b = e / S.npw_max, i = e % S.npw_max;
+                ckT[i * nb + b] = coef[((int64_t)t.k * nb + b) * S.npw_max + i];
+                ckpT[i * nb + b] = coef[((int64_t)t.kp * nb + b) * S.npw_max + i];
+            }
+            const int* gq = S.gq + (int64_t)q * S.ng_max * 3;
+            const int* gk = S.gk + (int64_t)t.kp * S.npw_max * 3;
+            for (int g = warp; g < ng; g += nwarp) {
+                int c = 0;
+                for (int j0 = 0; j0 < npkp; j0 += 32) {
+                    int j = j0 + lane, idx = -1;
+                    if (j < npkp) {
+                        int x0 = gk[3 * j] + gq[3 * g] + fold[0] - S.blo[0];
+                        int x1 = gk[3 * j + 1] + gq[3 * g + 1] + fold[1] - S.blo[1];
+                        int x2 = gk[3 * j + 2] + gq[3 * g + 2] + fold[2] - S.blo[2];
+                        if ((unsigned)x0 < (unsigned)S.bdim[0] && (unsigned)x1 < (unsigned)S.bdim[1] &&
+                            (unsigned)x2 < (unsigned)S.bdim[2])
+                            idx = S.box[(int64_t)t.k * S.bvol + ((int64_t)x0 * S.bdim[1] + x1) * S.bdim[2] + x2];
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, idx >= 0);
+                    if (idx >= 0) list[g * S.npw_max + c + __popc(m & ((1u << lane) - 1u))] = idx | (j << 16);
+                    c += __popc(m);
+                }
+                if (lane == 0) cnt[g] = c;
+            }
+            __syncthreads();
+            for (int g = warp; g < ng; g += nwarp) {
+                const int* L = list + g * S.npw_max;
+                const int len = cnt[g];
+                for (int p0 = 0; p0 < P; p0 += 32) {
+                    const int pp = p0 + lane;
+                    if (pp >= P) break;
+                    int na, nbp;
+                    if (pp < ncc) {
+                        na = nv + pp / nc;
+                        nbp = nv + pp % nc;
+                    } else {
+                        na = (pp - ncc) / nv;
+                        nbp = (pp - ncc) % nv;
+                    }
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int e = 0; e < len; ++e) {
+                        const int ij = L[e];
+                        cmacc32(acc, ckT[(ij & 0xffff) * nb + na], ckpT[(ij >> 16) * nb + nbp]);
+                    }
+                    rho[g * P + pp] = acc;
                 }
             }
-        }
-    }
-    // ---- MMA2 per pair: K^d = rho_cc'^T T (M = 128, N = NR, K = 2 ngp) ----
-    const uint32_t idesc2 = tc::idesc_f16(128, NR, Elem<E>::kBf16);
-    for (int p = 0; p < grp.count && ok; ++p) {
-        const float2* rc = RC + (size_t)p * ncc * ngp;
-        const float srho = pow2f(s_erho[p]);
-        for (int e = tid; e < 128 * ngp; e += blockDim.x) {
-            const int m = e / ngp, Q = e % ngp;
-            float re = 0.f, re2 = 0.f;   // values at k = Q and k = ngp + Q
-            if (m < ncc) {
-                float2 r = rc[m * ngp + Q];
-                re = r.x;
-                re2 = -r.y;
-            } else if (m < 2 * ncc) {
-                float2 r = rc[(m - ncc) * ngp + Q];
-                re = r.y;
-                re2 = r.x;
+            __syncthreads();
+            // one scale for all densities of the pair
+            float mx = 0.f;
+            for (int e = tid; e < ng * P; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(rho[e].x), fabsf(rho[e].y)));
+            const int erho = scale_exp(block_max(mx, &s_max));
+            const float srho = pow2f(erho);
+            if (tid == 0) s_erho[p] = erho;
+            // B1 rows p*NR + vv': planes rho_r, rho_i, -rho_i of rho_vv' (hi, lo), K index Q; rho_cc' kept for MMA2
+            for (int e = tid; e < nvv * ngp; e += blockDim.x) {
+                const int vv = e / ngp, Q = e % ngp;
+                const float2 r = Q < ng ? rho[Q * P + ncc + vv] : make_float2(0.f, 0.f);
+                const uint32_t o = core_off(p * NR + vv, Q, ngp);
+                E h, l;
+                split16(r.x * srho, h, l);
+                *(E*)(Bm + o) = h;
+                *(E*)(Bm + bpl + o) = l;
+                split16(r.y * srho, h, l);
+                *(E*)(Bm + 2 * bpl + o) = h;
+                *(E*)(Bm + 3 * bpl + o) = l;
+                split16(-r.y * srho, h, l);
+                *(E*)(Bm + 4 * bpl + o) = h;
+                *(E*)(Bm + 5 * bpl + o) = l;
             }
-            E h, l;
-            split16(re * srho, h, l);
-            *(E*)(Am + core_off(m, Q, K2)) = h;
-            *(E*)(Am + a2h + core_off(m, Q, K2)) = l;
-            split16(re2 * srho, h, l);
-            *(E*)(Am + core_off(m, ngp + Q, K2)) = h;
-            *(E*)(Am + a2h + core_off(m, ngp + Q, K2)) = l;
+            for (int e = tid; e < ncc * ngp; e += blockDim.x) {
+                const int cc = e / ngp, Q = e % ngp;
+                RC[((size_t)p * ncc + cc) * ngp + Q] = Q < ng ? rho[Q * P + cc] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
         }
+
+        // ---- W(q) into the region of the staging, now dead (generic-proxy accesses ordered before the bulk copy) ----
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(4 * wpl);
+            tc::mbar_expect_tx(&mbar[0], bytes);
+            tc::bulk_g2s(Am, wemb + (size_t)q * 4 * 128 * ngp, bytes, &mbar[0]);
+            s_max = 0u;   // read only after the barriers below
+        }
+        // ---- MMA1: T_r and T_i for all pairs (M = 128, N = NR kg, K = ngp) ----
+        // a wait that gives up still lets the operation it waited for finish (the
+        // default limit) before the region is reused, TMEM is freed or the CTA exits
+        const bool got_w = tc::mbar_wait(&mbar[0], ph01 & 1u, spin);
+        if (!got_w) tc::mbar_wait(&mbar[0], ph01 & 1u, kMbarSpinLimit);
+        ok = __syncthreads_and(got_w) != 0;
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (tid == 0) {
-            const uint32_t lbo = 128, sbo = (uint32_t)(K2 / 8) * 128;
-            const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm) + (uint32_t)core_off(p * NR, 0, K2);
-            const uint32_t d = tmem + 2 * (uint32_t)NB + (uint32_t)(NR * p);
-            for (int prod = 0; prod < 3; ++prod) {
-                const uint32_t ab = a0 + (prod == 2 ? (uint32_t)a2h : 0u);
-                const uint32_t bb = b0 + (prod == 1 ? (uint32_t)b2h : 0u);
-                for (int ks = 0; ks < K2 / 16; ++ks)
-                    tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
-                                idesc2, (prod | ks) != 0);
-            }
-            tc::mma_commit(&mbar[2]);
+        const uint32_t idesc1 = tc::idesc_f16(128, NB, Elem<E>::kBf16);
+        if (tid == 0 && ok) {
+            const uint32_t lbo = 128, sbo = (uint32_t)(ngp / 8) * 128;
+            const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm);
+            const uint32_t Wr = a0, Wi = a0 + 2 * (uint32_t)wpl;
+            const uint32_t Rr = b0, Ri = b0 + 2 * (uint32_t)bpl, Rn = b0 + 4 * (uint32_t)bpl;
+            // d += A B over the three split products (A_hi B_hi, A_hi B_lo, A_lo B_hi)
+            auto chain = [&](uint32_t d, uint32_t A, uint32_t B, bool first) {
+                for (int prod = 0; prod < 3; ++prod) {
+                    const uint32_t ab = A + (prod == 2 ? (uint32_t)wpl : 0u);
+                    const uint32_t bb = B + (prod == 1 ? (uint32_t)bpl : 0u);
+                    for (int ks = 0; ks < ngp / 16; ++ks)
+                        tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
+                                    idesc1, !(first && prod == 0 && ks == 0));
+                }
+            };
+            chain(tmem, Wr, Rr, true);                    // T_r = Wr rho_r + Wi rho_i
+            chain(tmem, Wi, Ri, false);
+            chain(tmem + (uint32_t)NB, Wi, Rr, true);     // T_i = Wi rho_r - Wr rho_i
+            chain(tmem + (uint32_t)NB, Wr, Rn, false);
+            tc::mma_commit(&mbar[1]);
         }
-        const bool got = tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), spin);
-        if (!got) tc::mbar_wait(&mbar[2], (uint32_t)(p & 1), kMbarSpinLimit);
-        ok = __syncthreads_and(got) != 0;
+        if (ok) {
+            const bool got = tc::mbar_wait(&mbar[1], ph01 & 1u, spin);
+            if (!got) tc::mbar_wait(&mbar[1], ph01 & 1u, kMbarSpinLimit);
+            ok = __syncthreads_and(got) != 0;
+        }
+        ++ph01;
         tc::fence_after();
-    }
-    // ---- epilogue: TMEM -> staging (A region) -> -K^d / V into the tile ----
-    float* EPI = (float*)Am;   // [kg][NR][128]
-    if (ok && warp < 4) {
-        const int row = 32 * warp + lane;
-        for (int p = 0; p < grp.count; ++p)
-            for (int cb = 0; cb < NR; cb += 8) {
+        // ---- T: TMEM -> scale -> split -> B2 (rows p*NR + vv'; K index Q for T_r, ngp + Q for T_i) ----
+        int eT = 0;
+        if (ok) {
+            const int row = 32 * (warp & 3) + lane;                 // lane of TMEM = Q
+            const int half = warp >> 2;                             // warps 0..3: T_r, 4..7: T_i
+            const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * NB);
+            float mx = 0.f;
+            for (int cb = 0; cb < NB; cb += 8) {
                 float v[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(2 * NB + NR * p + cb), v);
+                tc::tmem_ld8(tbase + (uint32_t)cb, v);
+                if (row < ngp)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) EPI[((size_t)p * NR + cb + j) * 128 + row] = v[j];
+                    for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fabsf(v[j]));
             }
-    }
-    __syncthreads();
-    if (ok) {
-        const int B = nv * nc;
-        for (int p = 0; p < grp.count; ++p) {
-            const PairTask t = tasks[grp.first + p];
-            // K^d = acc / (2^eW 2^(2 erho) 2^eT) and the factor -1/V
-            const float scale = ldexpf((float)(-S.inv_vol), -(wexp[q] + 2 * s_erho[p] + eT));
-            float2* Xt = X + t.xoff;
-            for (int e = tid; e < B * B; e += blockDim.x) {
-                const int r = e % B, col = e / B;
-                const int v = r / nc, c = r % nc, vp = col / nc, cp = col % nc;
-                const float* ep = EPI + ((size_t)p * NR + v * nv + vp) * 128;
-                float2 val = make_float2(scale * ep[c * nc + cp], scale * ep[ncc + c * nc + cp]);
-                Xt[(int64_t)(t.col0 + col) * t.ld + t.row0 + r] = val;
-                if (t.flags & 1) Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + col] = make_float2(val.x, -val.y);
+            eT = scale_exp(block_max(mx, &s_max));
+            const float sT = pow2f(eT);
+            for (int cb = 0; cb < NB; cb += 8) {
+                float v[8];
+                tc::tmem_ld8(tbase + (uint32_t)cb, v);
+                if (row < ngp) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t o = core_off(cb + j, half * ngp + row, K2);
+                        E h, l;
+                        split16(v[j] * sT, h, l);
+                        *(E*)(Bm + o) = h;
+                        *(E*)(Bm + b2h + o) = l;
+                    }
+                }
             }
         }
+        // ---- MMA2 per pair: K^d = rho_cc'^T T (M = 128, N = NR, K = 2 ngp) ----
+        const uint32_t idesc2 = tc::idesc_f16(128, NR, Elem<E>::kBf16);
+        for (int p = 0; p < grp.count && ok; ++p) {
+            const float2* rc = RC + (size_t)p * ncc * ngp;
+            const float srho = pow2f(s_erho[p]);
+            for (int e = tid; e < 128 * ngp; e += blockDim.x) {
+                const int m = e / ngp, Q = e % ngp;
+                float re = 0.f, re2 = 0.f;   // values at k = Q and k = ngp + Q
+                if (m < ncc) {
+                    float2 r = rc[m * ngp + Q];
+                    re = r.x;
+                    re2 = -r.y;
+                } else if (m < 2 * ncc) {
+                    float2 r = rc[(m - ncc) * ngp + Q];
+                    re = r.y;
+                    re2 = r.x;
+                }
+                E h, l;
+                split16(re * srho, h, l);
+                *(E*)(Am + core_off(m, Q, K2)) = h;
+                *(E*)(Am + a2h + core_off(m, Q, K2)) = l;
+                split16(re2 * srho, h, l);
+                *(E*)(Am + core_off(m, ngp + Q, K2)) = h;
+                *(E*)(Am + a2h + core_off(m, ngp + Q, K2)) = l;
+            }
+            tc::fence_proxy_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            if (tid == 0) {
+                const uint32_t lbo = 128, sbo = (uint32_t)(K2 / 8) * 128;
+                const uint32_t a0 = tc::smem_u32(Am), b0 = tc::smem_u32(Bm) + (uint32_t)core_off(p * NR, 0, K2);
+                const uint32_t d = tmem + 2 * (uint32_t)NB + (uint32_t)(NR * p);
+                for (int prod = 0; prod < 3; ++prod) {
+                    const uint32_t ab = a0 + (prod == 2 ? (uint32_t)a2h : 0u);
+                    const uint32_t bb = b0 + (prod == 1 ? (uint32_t)b2h : 0u);
+                    for (int ks = 0; ks < K2 / 16; ++ks)
+                        tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
+                                    idesc2, (prod | ks) != 0);
+                }
+                tc::mma_commit(&mbar[2]);
+            }
+            const bool got = tc::mbar_wait(&mbar[2], ph2 & 1u, spin);
+            if (!got) tc::mbar_wait(&mbar[2], ph2 & 1u, kMbarSpinLimit);
+            ++ph2;
+            ok = __syncthreads_and(got) != 0;
+            tc::fence_after();
+        }
+        // ---- epilogue: TMEM -> staging (A region) -> -K^d / V into the tile ----
+        float* EPI = (float*)Am;   // [kg][NR][128]
+        if (ok && warp < 4) {
+            const int row = 32 * warp + lane;
+            for (int p = 0; p < grp.count; ++p)
+                for (int cb = 0; cb < NR; cb += 8) {
+                    float v[8];
+                    tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(2 * NB + NR * p + cb), v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) EPI[((size_t)p * NR + cb + j) * 128 + row] = v[j];
+                }
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (ok) {
+            const int B = nv * nc;
+            for (int p = 0; p < grp.count; ++p) {
+                const PairTask t = tasks[grp.first + p];
+                // K^d = acc / (2^eW 2^(2 erho) 2^eT) and the factor -1/V
+                const float scale = ldexpf((float)(-S.inv_vol), -(wexp[q] + 2 * s_erho[p] + eT));
+                float2* Xt = X + t.xoff;
+                for (int e = tid; e < B * B; e += blockDim.x) {
+                    const int r = e % B, col = e / B;
+                    const int v = r / nc, c = r % nc, vp = col / nc, cp = col % nc;
+                    const float* ep = EPI + ((size_t)p * NR + v * nv + vp) * 128;
+                    float2 val = make_float2(scale * ep[c * nc + cp], scale * ep[ncc + c * nc + cp]);
+                    Xt[(int64_t)(t.col0 + col) * t.ld + t.row0 + r] = val;
+                    if (t.flags & 1) Xt[(int64_t)(t.row0 + r) * t.ld + t.col0 + col] = make_float2(val.x, -val.y);
+                }
+            }
+        }
+        if (!ok) break;      // uniform: ok comes from __syncthreads_and
+        __syncthreads();     // shared memory, s_g and sI are reused by the next group
     }
     if (!ok && tid == 0) atomicExch(status, 1);
     tc::fence_before();
@@ -490,35 +530,40 @@ int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaSt
     return BSE_OK;
 }
 
+// dynamic shared memory of a system's plan with kg pairs per group (0 if it does not fit)
+size_t tc_smem(const DevSys& s, int ngp, int kg) {
+    if (3 * tc_rows(s.nv) * kg > kTmemCols) return 0;
+    const size_t sm = tc_plan(kg, ngp, s.nb, s.nv, s.nc, s.npw_max, s.ng_max).total;
+    return sm <= kSmemBudget ? zmax(sm, kSmemFloor) : 0;
+}
+
 template <typename E>
-static int launch_direct_tc_t(const DevSys& s, const void* coef32, const void* wemb, const int* wexp, int ngp,
-                              const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                              cudaStream_t st, long wait_polls) {
-    int ngp2, kg = 1;
-    size_t sm;
-    BSE_TRY(tc_supported(s, ngp2, sm, &kg));
-    if (ngp2 != ngp) return fail(BSE_EINVAL, "split precision: W embedding for NGp %d, system needs %d", ngp, ngp2);
-    cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc smem %zu: %s", sm, cudaGetErrorString(e));
-    for (int64_t off = 0; off < ngroups; off += 1 << 30) {
-        int64_t n = ngroups - off < (1 << 30) ? ngroups - off : (1 << 30);
-        direct_tc_kernel<E><<<(unsigned)n, 256, sm, st>>>(s, (const float2*)coef32, (const E*)wemb, wexp, tasks,
-                                                          groups + off, ngp, kg, (float2*)X, status,
-                                                          wait_limit(wait_polls, kMbarSpinLimit));
-        note_launch();
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc launch: %s", cudaGetErrorString(e));
-    }
+static int launch_direct_tc_t(const TcInst* insts, size_t smem, const PairTask* tasks, const TcGroup* groups,
+                              int64_t ngroups, unsigned long long* counter, void* X, int* status, cudaStream_t st,
+                              long wait_polls) {
+    cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc smem %zu: %s", smem, cudaGetErrorString(e));
+    int dev = 0, sms = 0, per_sm = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_tc_kernel<E>, 256, smem));
+    if (per_sm < 1) return fail(BSE_EUNSUPPORTED, "tensor-core kernel: no CTA fits an SM");
+    per_sm = per_sm > 2 ? 2 : per_sm;   // 2 x 256 TMEM columns per SM
+    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, ngroups);
+    direct_tc_kernel<E><<<(unsigned)grid, 256, smem, st>>>(insts, tasks, groups, ngroups, counter, (float2*)X, status,
+                                                           wait_limit(wait_polls, kMbarSpinLimit));
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc launch: %s", cudaGetErrorString(e));
     return BSE_OK;
 }
 
-int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
-                     const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                     cudaStream_t st, long wait_polls) {
+int launch_direct_tc(const TcInst* insts, int fp16, size_t smem, const PairTask* tasks, const TcGroup* groups,
+                     int64_t ngroups, unsigned long long* counter, void* X, int* status, cudaStream_t st,
+                     long wait_polls) {
     if (ngroups == 0) return BSE_OK;
-    return fp16 ? launch_direct_tc_t<__half>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st,
-                                             wait_polls)
-                : launch_direct_tc_t<__nv_bfloat16>(s, coef32, wemb, wexp, ngp, tasks, groups, ngroups, X, status, st,
+    return fp16 ? launch_direct_tc_t<__half>(insts, smem, tasks, groups, ngroups, counter, X, status, st, wait_polls)
+                : launch_direct_tc_t<__nv_bfloat16>(insts, smem, tasks, groups, ngroups, counter, X, status, st,
                                                     wait_polls);
 }
 

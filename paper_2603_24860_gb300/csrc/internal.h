@@ -146,6 +146,17 @@ struct __align__(16) DirectInst {
 // a group of k pairs with the same q = k - k' (tensor-core direct term)
 struct TcGroup {
     int32_t first, count, q;   // range in the q-sorted task list
+    int32_t inst;              // system of the launch (index into its TcInst array)
+};
+
+// one system of a tensor-core launch
+struct __align__(16) TcInst {
+    DevSys S;
+    const float2* coef;     // FP32 coefficients
+    const void* wemb;       // W(q) embeddings (bf16 or fp16 hi and lo planes)
+    const int* wexp;        // their per-q scale exponents
+    int32_t ngp, kg;        // NG padded to 16; pairs per group
+    int32_t pad[2];
 };
 
 // a star-pair tile for the projection kernels
@@ -180,14 +191,16 @@ int launch_pairdens(const DevSys& s, const int* k, const int* kp, int64_t npairs
 // the same in FP32 from the FP32 copy of the coefficients (pair layout only)
 int launch_pairdens32(const DevSys& s, const float2* coef32, const int* k, const int* kp, int64_t npairs, int bands,
                       float2* out, cudaStream_t st);
-// direct term (direct.cu): prec32 = 0 -> FP64 (coef/w double2, X double2), 1 -> FP32 (float2)
-// direct term of the tasks of one or more systems: insts (device) holds the
-// systems, task.flags >> 1 indexes them; smax: any system's (nb, nv, nc,
-// npw_max, ng_max) maxima, for the shared-memory size
-int launch_direct_multi(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks, int64_t ntasks,
-                        void* X, cudaStream_t st);
-// one system, passed as a kernel parameter
+// direct term (direct.cu): prec32 = 0 -> FP64 (coef/w double2, X double2), 1 -> FP32 (float2).
+// One system, passed as a kernel parameter:
 int launch_direct(const DirectInst& one, int prec32, const PairTask* tasks, int64_t ntasks, void* X, cudaStream_t st);
+// Persistent form for batches: one launch of sms x (CTAs per SM, capped by ctas_per_sm when > 0)
+// CTAs taking the tasks of all systems from a work queue (counter: device, zero before the launch);
+// insts (device) holds the systems, task.flags >> 1 indexes them; smax: any system's (nb, nv, nc,
+// npw_max, ng_max) maxima, for the shared-memory size; threads 128 or 256
+int launch_direct_persistent(const DirectInst* insts, const DevSys& smax, int prec32, const PairTask* tasks,
+                             int64_t ntasks, unsigned long long* counter, int threads, int ctas_per_sm, void* X,
+                             cudaStream_t st);
 
 // rotated direct-term blocks (rotate.cu, Eq. Wtrafo)
 struct RotSys {
@@ -272,10 +285,14 @@ void note_launch();
 int tc_supported(const DevSys& s, int& ngp, size_t& smem, int* kg = nullptr);
 // split-precision W(q) embeddings (fp16 != 0: fp16 hi + lo, else bf16) and their per-q scale exponents
 int launch_wemb(const DevSys& s, int ngp, int fp16, void* out, int* wexp, cudaStream_t st);
+// dynamic shared memory of a system's plan with kg pairs per group (0 if it does not fit)
+size_t tc_smem(const DevSys& s, int ngp, int kg);
+// one persistent launch over groups of one or more systems (insts: device; group.inst indexes it);
+// smem: the largest plan of the systems; counter: device, zero before the launch;
 // wait_polls: polls of an mbarrier wait before it gives up (negative: the default)
-int launch_direct_tc(const DevSys& s, int fp16, const void* coef32, const void* wemb, const int* wexp, int ngp,
-                     const PairTask* tasks, const TcGroup* groups, int64_t ngroups, void* X, int* status,
-                     cudaStream_t st, long wait_polls = -1);
+int launch_direct_tc(const TcInst* insts, int fp16, size_t smem, const PairTask* tasks, const TcGroup* groups,
+                     int64_t ngroups, unsigned long long* counter, void* X, int* status, cudaStream_t st,
+                     long wait_polls = -1);
 int launch_exchange_project(const DevBasis& b, const double2* P, int ng0, double2* Pmu, cudaStream_t st);
 int launch_exchange_full(const double2* P, const double* vbar, int ng0, int64_t N, double xscale,
                          double2* H, int64_t ld, cudaStream_t st);

@@ -2,8 +2,10 @@
 9x9x1 to 18x18x3 meshes and Si-like Oh cells on 4^3 to 7^3 meshes, N_v and
 N_c from 2 to 6, seeded): the partner block of each instance's optically
 active irrep (E1u for q along x in D6h, T1u in Oh) from one graph launch in
-FP32, FP64 and both split precisions (tensor-core direct term, one launch per
-instance in the graph).  Every block equals the single-context build; the
+FP32, FP64 and both split precisions.  The direct term of all 32 instances is
+one launch of a persistent kernel (the tensor-core kernel for the split
+modes) taking tasks from a device work queue, with tile shapes chosen by the
+autotuner.  Every block equals the single-context build; the
 FP32 and split levels agree with the FP64 ones within 0.1 meV for every
 instance; sampled star-pair sub-blocks of the smallest MoS2-like instance
 match the oracle."""
@@ -28,15 +30,17 @@ def batch():
         mu = int(np.nonzero(t["bright"] & (t["partner_dim"] > 0))[0][0])
         mus.append(mu)
         dims.append(int(t["partner_dim"][mu]))
-    out = {}
+    out, info = {}, {}
     for name, prec in (("fp32", bse.BSE_FP32), ("fp64", bse.BSE_FP64), ("bf16", bse.BSE_BF16_SPLIT),
                        ("fp16", bse.BSE_FP16_SPLIT)):
         bufs = [torch.empty(max(n * n, 1), dtype=torch.complex128, device="cuda") for n in dims]
         b = bse.bse_batch_create(ctxs, mus, [1] * len(ctxs), prec, bse.BSE_TERM_ALL, bufs, [max(n, 1) for n in dims])
+        info[name] = (bse.bse_batch_kernels(b), bse.bse_batch_tuning(b))
         bse.bse_batch_run(b)
         torch.cuda.synchronize()
         bse.bse_batch_destroy(b)
         out[name] = [bse.colmajor(x, n, n, max(n, 1)) for x, n in zip(bufs, dims)]
+    out["info"] = info
     yield bse, torch, cfgs, ctxs, mus, dims, out
     for c in ctxs:
         bse.bse_destroy(c)
@@ -49,6 +53,28 @@ def test_batch_shape(batch):
     meshes = {c.mesh for c in cfgs if c.material == "MoS2"}
     assert (18, 18, 3) in meshes and (9, 9, 1) in meshes
     assert all(2 <= c.nv <= 6 and 2 <= c.nc <= 6 for c in cfgs)
+
+
+@pytest.mark.parametrize("name", ["fp32", "fp64", "bf16", "fp16"])
+def test_batch_direct_term_is_one_launch(batch, name):
+    """The graph holds one direct-term launch for all instances: besides it
+    only the rotation kernel and, per non-empty instance, the exchange and the
+    two projection stages; the autotuner reports its choice for every class
+    of instances."""
+    bse, torch, cfgs, ctxs, mus, dims, out = batch
+    kernels, tune = out["info"][name]
+    nonempty = sum(1 for n in dims if n > 0)
+    assert kernels <= 2 + 3 * nonempty
+    if name in ("bf16", "fp16"):
+        assert tune["direct_kernel"].startswith("direct_tc_kernel")
+        assert sum(c["instances"] for c in tune["classes"]) == len(ctxs)
+        for c in tune["classes"]:
+            assert c["pairs_per_cta"] in (1, 2, 4)
+            assert c["ms"][str(c["pairs_per_cta"])] > 0
+    else:
+        assert tune["direct_kernel"].startswith("direct_persistent_kernel")
+        assert tune["threads_per_cta"] in (128, 256)
+    assert tune["x_arena_mb"] > 0
 
 
 @pytest.mark.parametrize("i", list(range(0, 32, 3)))
