@@ -663,6 +663,9 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches,
+        "direct_launches_per_step": stats[-1][0]["direct_launches"],
+        "tc_pairs_per_cta": (stats[-1][0]["tc_pairs_per_cta"]
+                             if prec in (bse.BSE_BF16_SPLIT, bse.BSE_FP16_SPLIT) else None),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
@@ -738,6 +741,7 @@ def run_batch(args, rank, world, local):
     flops = sum(w["rho"] + w["contract"] + w["project"] + w["exchange"] for w in work)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     kernels = bse.bse_batch_kernels(b)
+    tuning = bse.bse_batch_tuning(b)
     l_before = bse.bse_get_stats(ctxs[0])["launches"]
 
     def timed(fn, n):
@@ -791,6 +795,7 @@ def run_batch(args, rank, world, local):
         "build_flops": flops,
         "setup_ms": setup_ms,
         "graph_kernels": kernels,
+        "autotuner": tuning,
         "one_context_at_a_time_ms": statistics.mean(seq),
         "gpu_launches": launches,
         "clocks": clocks,
