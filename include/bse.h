@@ -116,9 +116,11 @@ typedef struct {
  * On success *out owns device memory until bse_destroy.  Blocks until the
  * set-up work has finished.  Device memory of contexts comes from the
  * device's stream-ordered memory pool (cudaMallocAsync on the context's
- * stream); bse_create raises that pool's release threshold to 16 GiB, so
+ * stream); bse_create raises that pool's release threshold to 64 GiB, so
  * memory freed by one context is reused by the next without a driver
- * allocation.
+ * allocation.  The builds' tile arenas take up to a sixth of the free device
+ * memory (at most 32 GiB each; environment variable BSE_ARENA_MB fixes the
+ * budget), so that a workload's tiles fit one batch when there is room.
  * Errors: EINVAL (sizes, non-unimodular R, mesh not invariant, G = 0 missing),
  * ESYMM (operations not a group, sphere not closed under an operation,
  * non-unitary Gamma, block dimensions not summing to N), EUNSUPPORTED

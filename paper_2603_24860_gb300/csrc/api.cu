@@ -31,7 +31,7 @@ namespace {
 // (cudaMallocAsync / cudaFreeAsync on the context's stream).  The pool keeps
 // up to kPoolKeep bytes that contexts free for the next one, so creating a
 // context per workload costs no driver allocation once the pool is warm.
-constexpr uint64_t kPoolKeep = 16ull << 30;
+constexpr uint64_t kPoolKeep = 64ull << 30;
 thread_local cudaStream_t t_alloc_stream = nullptr;
 
 struct AllocStream {   // stream the allocations of one API call are ordered on
@@ -200,9 +200,20 @@ struct Batch {
     std::vector<int64_t> max_rows, max_ca, max_cb;   // per target
 };
 
+// Budget of each tile arena (bytes of FP64 tiles; the FP32 builds use half).
+// BSE_ARENA_MB fixes it; otherwise it is a sixth of the device's free memory,
+// between 2 and 32 GiB, so that the tiles of a workload such as the 12x12x12
+// mesh's T1u block fit one batch (one launch of each kernel of the build)
+// whenever the device has room.
 size_t arena_budget() {
     const char* env = std::getenv("BSE_ARENA_MB");
-    return (size_t)(env ? std::atoll(env) : 2048) << 20;
+    if (env) return (size_t)std::atoll(env) << 20;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return (size_t)2048 << 20;
+    }
+    return std::min<size_t>(std::max<size_t>(fr / 6, (size_t)2 << 30), (size_t)32 << 30);
 }
 
 // Seeds of a star-pair tile (a, b) (Eq. Wtrafo): every k pair (k, k') is
