@@ -264,6 +264,9 @@ static int launch_direct_t(const DirectInst* insts, const DirectInst& one, const
     cudaError_t e = cudaFuncSetAttribute(direct_kernel<R, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pl.total);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", pl.total, cudaGetErrorString(e));
+    // the whole carveout as shared memory: as many CTAs per SM as their plans allow
+    e = cudaFuncSetAttribute(direct_kernel<R, kBatch>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct carveout: %s", cudaGetErrorString(e));
     for (int64_t off = 0; off < ntasks; off += 1 << 30) {
         int64_t nt = ntasks - off < (1 << 30) ? ntasks - off : (1 << 30);
         direct_kernel<R, kBatch><<<(unsigned)nt, 256, pl.total, st>>>(insts, one, tasks + off, (V*)X);
@@ -291,6 +294,8 @@ static int launch_direct_persistent_t(const DirectInst* insts, const DevSys& s, 
     cudaError_t e = cudaFuncSetAttribute(direct_persistent_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pl.total);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct smem %zu: %s", pl.total, cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(direct_persistent_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct carveout: %s", cudaGetErrorString(e));
     int dev = 0, sms = 0, per_sm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

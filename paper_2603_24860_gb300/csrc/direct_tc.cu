@@ -36,6 +36,7 @@ namespace bse {
 using tc::core_off;
 
 constexpr int kMaxG = 4;                            // pairs per group at most
+constexpr int kSlots = 4;                           // band pairs per lane in the pair densities (nc^2 + nv^2 <= 128)
 constexpr int kTmemCols = 256;                      // T_r, T_i and K^d of every pair: 3 nr kg columns
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic shared memory per CTA
 constexpr size_t kSmemFloor = 82 * 1024;            // at most two CTAs (2 x 256 TMEM columns) per SM
@@ -234,27 +235,39 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(const TcInst* __restr
                 if (lane == 0) cnt[g] = c;
             }
             __syncthreads();
+            // lanes over band pairs, up to kSlots per lane in one pass over the overlap list
+            // (independent accumulators: cc' first, then vv')
+            int na[kSlots], nbp[kSlots];
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                const int pp = lane + 32 * sl;
+                if (pp < ncc) {
+                    na[sl] = nv + pp / nc;
+                    nbp[sl] = nv + pp % nc;
+                } else if (pp < P) {
+                    na[sl] = (pp - ncc) / nv;
+                    nbp[sl] = (pp - ncc) % nv;
+                } else {
+                    na[sl] = nbp[sl] = -1;
+                }
+            }
             for (int g = warp; g < ng; g += nwarp) {
                 const int* L = list + g * S.npw_max;
                 const int len = cnt[g];
-                for (int p0 = 0; p0 < P; p0 += 32) {
-                    const int pp = p0 + lane;
-                    if (pp >= P) break;
-                    int na, nbp;
-                    if (pp < ncc) {
-                        na = nv + pp / nc;
-                        nbp = nv + pp % nc;
-                    } else {
-                        na = (pp - ncc) / nv;
-                        nbp = (pp - ncc) % nv;
-                    }
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int e = 0; e < len; ++e) {
-                        const int ij = L[e];
-                        cmacc32(acc, ckT[(ij & 0xffff) * nb + na], ckpT[(ij >> 16) * nb + nbp]);
-                    }
-                    rho[g * P + pp] = acc;
+                float2 acc[kSlots];
+#pragma unroll
+                for (int sl = 0; sl < kSlots; ++sl) acc[sl] = make_float2(0.f, 0.f);
+                for (int e = 0; e < len; ++e) {
+                    const int ij = L[e];
+                    const float2* a = ckT + (ij & 0xffff) * nb;
+                    const float2* b = ckpT + (ij >> 16) * nb;
+#pragma unroll
+                    for (int sl = 0; sl < kSlots; ++sl)
+                        if (na[sl] >= 0) cmacc32(acc[sl], a[na[sl]], b[nbp[sl]]);
                 }
+#pragma unroll
+                for (int sl = 0; sl < kSlots; ++sl)
+                    if (na[sl] >= 0) rho[g * P + lane + 32 * sl] = acc[sl];
             }
             __syncthreads();
             // one scale for all densities of the pair
@@ -543,6 +556,9 @@ static int launch_direct_tc_t(const TcInst* insts, size_t smem, const PairTask* 
                               long wait_polls) {
     cudaError_t e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc smem %zu: %s", smem, cudaGetErrorString(e));
+    // the whole carveout as shared memory, so that two CTAs share an SM when their plans fit
+    e = cudaFuncSetAttribute(direct_tc_kernel<E>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return fail(BSE_ECUDA, "direct_tc carveout: %s", cudaGetErrorString(e));
     int dev = 0, sms = 0, per_sm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
