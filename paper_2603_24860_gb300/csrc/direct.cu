@@ -147,7 +147,30 @@ __device__ __forceinline__ void direct_task(const DirectInst& I, const PairTask 
         for (int s = 0; s < kMaxSlots; ++s) acc[s].x = acc[s].y = R(0);
         const int* L = list + g * S.npw_max;
         const int len = cnt[g];
-        for (int e = 0; e < len; ++e) {
+        // four list entries per iteration, their loads issued before the arithmetic
+        int e = 0;
+        for (; e + 3 < len; e += 4) {
+            const int ij0 = L[e], ij1 = L[e + 1], ij2 = L[e + 2], ij3 = L[e + 3];
+            const V* a0 = ckT + (ij0 & 0xffff) * nb;
+            const V* b0 = ckpT + (ij0 >> 16) * nb;
+            const V* a1 = ckT + (ij1 & 0xffff) * nb;
+            const V* b1 = ckpT + (ij1 >> 16) * nb;
+            const V* a2 = ckT + (ij2 & 0xffff) * nb;
+            const V* b2 = ckpT + (ij2 >> 16) * nb;
+            const V* a3 = ckT + (ij3 & 0xffff) * nb;
+            const V* b3 = ckpT + (ij3 >> 16) * nb;
+#pragma unroll
+            for (int s = 0; s < kMaxSlots; ++s)
+                if (na[s] >= 0) {
+                    const V x0 = a0[na[s]], y0 = b0[nbp[s]], x1 = a1[na[s]], y1 = b1[nbp[s]];
+                    const V x2 = a2[na[s]], y2 = b2[nbp[s]], x3 = a3[na[s]], y3 = b3[nbp[s]];
+                    cmacc(acc[s], x0, y0);
+                    cmacc(acc[s], x1, y1);
+                    cmacc(acc[s], x2, y2);
+                    cmacc(acc[s], x3, y3);
+                }
+        }
+        for (; e < len; ++e) {
             const int ij = L[e];
             const V* a = ckT + (ij & 0xffff) * nb;
             const V* b = ckpT + (ij >> 16) * nb;

@@ -257,7 +257,30 @@ __global__ void __launch_bounds__(256, 1) direct_tc_kernel(const TcInst* __restr
                 float2 acc[kSlots];
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) acc[sl] = make_float2(0.f, 0.f);
-                for (int e = 0; e < len; ++e) {
+                // four list entries per iteration, their loads issued before the arithmetic
+                int e = 0;
+                for (; e + 3 < len; e += 4) {
+                    const int4 ij = make_int4(L[e], L[e + 1], L[e + 2], L[e + 3]);   // L is 4-byte aligned only
+                    const float2* a0 = ckT + (ij.x & 0xffff) * nb;
+                    const float2* b0 = ckpT + (ij.x >> 16) * nb;
+                    const float2* a1 = ckT + (ij.y & 0xffff) * nb;
+                    const float2* b1 = ckpT + (ij.y >> 16) * nb;
+                    const float2* a2 = ckT + (ij.z & 0xffff) * nb;
+                    const float2* b2 = ckpT + (ij.z >> 16) * nb;
+                    const float2* a3 = ckT + (ij.w & 0xffff) * nb;
+                    const float2* b3 = ckpT + (ij.w >> 16) * nb;
+#pragma unroll
+                    for (int sl = 0; sl < kSlots; ++sl)
+                        if (na[sl] >= 0) {
+                            const float2 x0 = a0[na[sl]], y0 = b0[nbp[sl]], x1 = a1[na[sl]], y1 = b1[nbp[sl]];
+                            const float2 x2 = a2[na[sl]], y2 = b2[nbp[sl]], x3 = a3[na[sl]], y3 = b3[nbp[sl]];
+                            cmacc32(acc[sl], x0, y0);
+                            cmacc32(acc[sl], x1, y1);
+                            cmacc32(acc[sl], x2, y2);
+                            cmacc32(acc[sl], x3, y3);
+                        }
+                }
+                for (; e < len; ++e) {
                     const int ij = L[e];
                     const float2* a = ckT + (ij & 0xffff) * nb;
                     const float2* b = ckpT + (ij >> 16) * nb;
