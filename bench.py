@@ -566,7 +566,9 @@ def run_ours(args, rank, world, local):
         rflops = sum(16.0 / 3.0 * n ** 3 for n, s in zip(dims, stats[-1][1]["solvers"]) if s == bse.BSE_SOLVER_TRIDIAG)
         ra = rflops / (ms_reduce * 1e-3) / 1e12
         kinds = {k for k in stats[-1][1]["reduce_kinds"] if k >= 0}
-        rname = "tridiag_blocked_kernel" if kinds == {1} else ("tridiag_kernel" if kinds == {0} else "tridiag kernels")
+        rname = {frozenset({0}): "tridiag_kernel",
+                 frozenset({1}): "tridiag_blocked_kernel + panel_update_tc_kernel",
+                 frozenset({2}): "tridiag_blocked_kernel"}.get(frozenset(kinds), "tridiag kernels")
         roofs.append({"bound": "alu", "kernel": rname, "ms_per_step": ms_reduce, "achieved": ra,
                       "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ra / DF_PEAK_TFLOPS,
                       "peak_source": "derived: double-float on the FP32 pipe, 152 SMs x 128 FP32 instr/clk x "

@@ -413,8 +413,13 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      reduced in shared memory (a column per CTA); larger
  *                      ones, with their columns in device memory, by a
  *                      blocked form of the same reduction (panels of 32
- *                      reflectors: one pass of column dot products per step,
- *                      the panel's rank-64 update at its end).  Needs the partners'
+ *                      reflectors: one pass of column dot products per step;
+ *                      at the panel's end its rank-64 update of the trailing
+ *                      block, on the tensor cores from an exact split of V
+ *                      and W into 8 bf16 integer digits of 7 bits, each
+ *                      digit-pair product summed exactly in FP32, the groups
+ *                      combined in double-float: the operands' 56-bit
+ *                      rounding is the update's only error).  Needs the partners'
  *                      projections b_i to be parallel (true for the partner
  *                      blocks of bse_partner_spectrum) and n <= 8192; the
  *                      sum of the weights must come out as 1 within 1e-8.
@@ -424,6 +429,9 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      break the last condition.
  *   BSE_SOLVER_TRIDIAG_BLOCKED  as TRIDIAG with the blocked reduction at
  *                      every size (for checks and measurements).
+ *   BSE_SOLVER_TRIDIAG_BLOCKED_DF  as TRIDIAG_BLOCKED with the panel-end
+ *                      update on the CUDA cores in double-float (for checks
+ *                      and measurements).
  *   BSE_SOLVER_AUTO    (default) TRIDIAG for partner blocks, for blocks
  *                      of one-dimensional irreps and for blocks of irreps
  *                      outside the polar-vector representation (B_mu = 0
@@ -431,7 +439,13 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      otherwise and whenever a TRIDIAG condition fails.
  * bse_stats.solver reports the solver the last spectrum used.
  */
-enum { BSE_SOLVER_AUTO = 0, BSE_SOLVER_DENSE = 1, BSE_SOLVER_TRIDIAG = 2, BSE_SOLVER_TRIDIAG_BLOCKED = 3 };
+enum {
+    BSE_SOLVER_AUTO = 0,
+    BSE_SOLVER_DENSE = 1,
+    BSE_SOLVER_TRIDIAG = 2,
+    BSE_SOLVER_TRIDIAG_BLOCKED = 3,
+    BSE_SOLVER_TRIDIAG_BLOCKED_DF = 4
+};
 
 /*
  * bse_set_seeds - direct term by seeds (on, the default) or pair by pair.
@@ -538,7 +552,8 @@ typedef struct {
     int32_t solver;             /* eigensolver of the last spectrum: BSE_SOLVER_DENSE or BSE_SOLVER_TRIDIAG */
     float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */
     float ms_rotate;            /* rotated direct-term blocks of the last build (part of ms_direct) */
-    int32_t reduce_kind;        /* reduction of the last TRIDIAG spectrum: 0 block in shared memory, 1 blocked (panels) */
+    int32_t reduce_kind;        /* reduction of the last TRIDIAG spectrum: 0 block in shared memory, 1 blocked
+                                   (panels) with the tensor-core panel update, 2 blocked with the double-float one */
     int32_t tc_pairs_per_cta;   /* k pairs per CTA (sharing one W(q)) of the last split-precision build, as tuned */
     int32_t pad_;
 } bse_stats;

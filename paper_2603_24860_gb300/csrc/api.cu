@@ -2114,7 +2114,10 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
     BSE_TRY(launch_tridiag_spectrum((double2*)c->eigA.p, dim, (const double2*)c->Bmu.p + (size_t)pmax * dim, scale,
                                     c->triScratch.p, omega_out, osc, wsum, err, c->stream,
                                     c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls,
-                                    c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ? 1 : 0, &c->stats.reduce_kind));
+                                    c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED      ? 1
+                                    : c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED_DF ? 2
+                                                                                      : 0,
+                                    &c->stats.reduce_kind));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
     struct {
         double s;
@@ -2146,7 +2149,9 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
         BSE_TRY(launch_bmu(dev_basis_of(c, parts[p]), (const double2*)c->B.p, (double2*)c->Bmu.p + (size_t)p * dim,
                            c->stream));
     const double pref = 4.0 * M_PI * c->spin / c->t.nk;
-    const bool try_tri = c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
+    const bool forced_tri = c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
+                            c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED_DF;
+    const bool try_tri = forced_tri ||
                          (c->solver_mode == BSE_SOLVER_AUTO && (nparts > 1 || irrep_dim == 1 || dark) &&
                           dim <= tridiag_max_dim());
     if (try_tri) {
@@ -2164,8 +2169,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
             c->stats.solver = BSE_SOLVER_TRIDIAG;
             return BSE_OK;
         }
-        if (c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
-            rc == BSE_ETIMEOUT || rc == BSE_ECUDA)
+        if (forced_tri || rc == BSE_ETIMEOUT || rc == BSE_ECUDA)
             return rc;
         clear_error();
     }
@@ -2341,7 +2345,7 @@ int bse_set_solver(bse_ctx* c, int32_t solver) {
     clear_error();
     if (!c) return fail(BSE_EINVAL, "null argument");
     if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG &&
-        solver != BSE_SOLVER_TRIDIAG_BLOCKED)
+        solver != BSE_SOLVER_TRIDIAG_BLOCKED && solver != BSE_SOLVER_TRIDIAG_BLOCKED_DF)
         return fail(BSE_EINVAL, "unknown solver %d", solver);
     c->solver_mode = solver;
     return BSE_OK;

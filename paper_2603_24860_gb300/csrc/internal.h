@@ -311,8 +311,17 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
                             double* osc, double* wsum, int* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
                             long wait_polls = -1, int variant = 0, int* used = nullptr);
 // variant: 0 the reduction with the block in shared memory when it fits, else the blocked
-// (panel) reduction with the columns in global memory; 1 the blocked reduction always.
-// *used (optional): 0 the shared-memory reduction ran, 1 the blocked one
+// (panel) reduction with the columns in global memory and its panel-end update on the tensor
+// cores; 1 the blocked reduction always (tensor-core update); 2 the blocked reduction always,
+// with the panel-end update on the CUDA cores (double-float) inside its single launch.
+// *used (optional): 0 the shared-memory reduction ran, 1 the blocked one with the tensor-core
+// update, 2 the blocked one with the CUDA-core update
+// her2k_tc.cu: the panel-end update A -= V W^H + W V^H (rows and columns >= k0 of the n x n
+// double-float block; V, W [32][n]) from exact bf16 digit GEMMs on the tensor cores; status
+// is raised when a bounded wait gives up
+size_t panel_update_tc_bytes(int64_t n);
+int launch_panel_update_tc(float4* A, int64_t n, int k0, const float4* V, const float4* W, void* scratch, int* status,
+                           cudaStream_t st, long wait_polls);
 // lanczos.cu: the Lanczos recurrence on a Hermitian block from conj(b) (Lanczos-Haydock, Sec. IV)
 size_t lanczos_scratch_bytes(int64_t n, int m);
 int lanczos_max_dim();

@@ -411,6 +411,8 @@ struct TriBArgs {
     unsigned* bar;        // barrier counter, zero on entry
     int* err;             // error flag, zero on entry
     long spin;            // polls of a grid barrier before it gives up
+    int s_begin, s_end;   // the steps of this launch: s_begin <= s < s_end (s = -1: the start reflector)
+    int tc_update;        // 1: the panel-end update is left to the tensor-core kernels between launches
 };
 
 // dynamic shared memory of the blocked kernel (cdf units): the staged column
@@ -487,18 +489,19 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
     auto col = [&](int i) -> cdf* { return gA + (size_t)i * n; };
     auto WVo = [&](int m, int l2) -> cdf& { return WV[(size_t)m * 2 * kNb + l2]; };
 
-    // own columns in double-float, in place (same 16 bytes per element)
-    for (int m = 0; m < ncl; ++m) {
-        const double2* src = reinterpret_cast<const double2*>(col(blk + m * G));
-        cdf* dst = col(blk + m * G);
-        for (int r = tid; r < n; r += kTriThreads) {
-            const double2 z = src[r];
-            dst[r] = cdf_from(z);
+    // own columns in double-float, in place (same 16 bytes per element), at the first launch
+    if (a.s_begin < 0)
+        for (int m = 0; m < ncl; ++m) {
+            const double2* src = reinterpret_cast<const double2*>(col(blk + m * G));
+            cdf* dst = col(blk + m * G);
+            for (int r = tid; r < n; r += kTriThreads) {
+                const double2 z = src[r];
+                dst[r] = cdf_from(z);
+            }
         }
-    }
     unsigned nbar = 0;
 
-    for (int s = -1; s <= n - 2; ++s) {
+    for (int s = a.s_begin; s < a.s_end; ++s) {
         const int k = s + 1;
         const int l = (s + 1) % kNb;     // reflectors of the panel before this one
         const int m0 = blk > s ? 0 : (s - blk) / G + 1;   // own indices i > s (= own rows i >= k)
@@ -730,7 +733,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
         if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
 
         // ---------------- panel end: A -= V W^H + W V^H on own columns >= k, rows >= k ----------------
-        if (l == kNb - 1 && s < n - 2) {
+        if (!a.tc_update && l == kNb - 1 && s < n - 2) {
             const int nc = ncl - m0;
             for (int c0 = 0; c0 < nc; c0 += kHerCols) {
                 const int cn = min(kHerCols, nc - c0);
@@ -777,7 +780,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
             __syncthreads();
         }
     }
-    if (blk == 0 && tid == 0) {
+    if (a.s_end == n - 1 && blk == 0 && tid == 0) {
         const cdf z = __ldcg(a.ncol + (n - 1));
         a.d[n - 1] = df_to(make_float2(z.x, z.y));
     }
@@ -1202,7 +1205,7 @@ size_t tridiag_scratch_bytes(int64_t n) {
     // 16 bytes each), its norm parts (1024 float2) and s dots (2 kNb); 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n) +
            sizeof(float2) * (size_t)(2 * n * n) + sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) +
-           sizeof(cdf) * (size_t)(2 * kNb * n + 4 * kNb) + sizeof(float2) * 1024 + 16384;
+           sizeof(cdf) * (size_t)(2 * kNb * n + 4 * kNb) + sizeof(float2) * 1024 + panel_update_tc_bytes(n) + 16384;
 }
 
 // the blocked reduction keeps a column (16 n bytes) and the panel coefficients
@@ -1250,6 +1253,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     cdf* Wp = (cdf*)take(sizeof(cdf) * kNb * n);
     cdf* sdot = (cdf*)take(sizeof(cdf) * 4 * kNb);
     float2* npart = (float2*)take(sizeof(float2) * 1024);
+    void* tcs = take(panel_update_tc_bytes(n));
 
     int dev = 0, sms = 0, maxsm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
@@ -1259,11 +1263,12 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     const size_t static_smem = sizeof(cdf) * (kTriWarps + 3) + 64;
     const size_t vec_bytes = sizeof(cdf) * 3 * (size_t)n;   // v, w and the next column of a step
     const size_t cols_bytes = sizeof(cdf) * (size_t)((n - 1) / G + 1) * n;
-    const bool smem = variant != 1 && vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
+    const bool smem = variant == 0 && vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
+    const bool tcu = variant != 2;   // blocked: panel-end update on the tensor cores between launches
     if (!smem) G = (int)std::min<int64_t>(sms, n);
     if (!smem && tri_blocked_smem(n, G) > (size_t)maxsm)
         return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld exceeds shared memory", (long long)n);
-    if (used) *used = smem ? 0 : 1;
+    if (used) *used = smem ? 0 : (tcu ? 1 : 2);
 
     BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     BSE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -1323,8 +1328,19 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
         BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTriThreads, dyn));
         if (per_sm < 1 || G > per_sm * sms) return fail(BSE_EUNSUPPORTED, "tridiagonal kernel cannot be co-resident");
         if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
-        BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
-        note_launch();
+        // with the tensor-core update one launch per panel (steps s0 .. s0 + kNb - 1), each
+        // followed by the panel-end update of the trailing block from k = s0 + kNb on
+        const int64_t span = tcu ? kNb : n;
+        for (int64_t s0 = -1; s0 < n - 1; s0 += span) {
+            const int64_t s1 = std::min<int64_t>(s0 + span, n - 1);
+            if (s0 > -1) BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+            a.s_begin = (int)s0;
+            a.s_end = (int)s1;
+            a.tc_update = tcu ? 1 : 0;
+            BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
+            note_launch();
+            if (tcu && s1 <= n - 2) BSE_TRY(launch_panel_update_tc(a.A, n, (int)s1, Vp, Wp, tcs, err, st, wait_polls));
+        }
         if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
     }
 

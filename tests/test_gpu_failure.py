@@ -3,7 +3,8 @@ that runs out; nothing here faults, traps or hangs the GPU.
 
 * Bounded device waits: bse_set_wait_limit(ctx, 0) makes every bounded wait
   give up at once (the grid barriers of the tridiagonal reduction and of the
-  Lanczos recurrence, the mbarrier waits of the tensor-core direct kernel).
+  Lanczos recurrence, the mbarrier waits of the tensor-core direct kernel and
+  of the tensor-core panel update).
   The call reports ETIMEOUT, and once the default limit is back the same
   context gives the oracle's results.
 * Inputs that break the symmetry the method relies on (Sec. III.C): a cut
@@ -36,14 +37,19 @@ def _code(bse, fn, *args):
     return bse.BSE_OK
 
 
-def test_tridiagonal_wait_gives_up_and_context_recovers(lib):
+@pytest.mark.parametrize("solver", ["BSE_SOLVER_TRIDIAG", "BSE_SOLVER_TRIDIAG_BLOCKED"])
+def test_tridiagonal_wait_gives_up_and_context_recovers(lib, solver):
+    """The 69-dim partner block of si4: the reduction in shared memory, and
+    the blocked one, whose tensor-core panel updates (after steps 30 and 62)
+    give up at their first mbarrier wait, let their bulk copies land, free
+    their tensor memory and return."""
     from oracle.projection import PartnerBasis
     bse, torch = lib
     from synth import generate
     d, inp, grp, mt, b = oracle_case("si4")
     ctx = bse.bse_create(generate("si4"), stream=torch.cuda.current_stream())
     mu = b.bright()[0]
-    bse.bse_set_solver(ctx, bse.BSE_SOLVER_TRIDIAG)
+    bse.bse_set_solver(ctx, getattr(bse, solver))
     h = bse.partner_block(ctx, mu)
     omega = torch.tensor(d["omega"], device="cuda")
     bse.bse_set_wait_limit(ctx, 0)
@@ -53,6 +59,7 @@ def test_tridiagonal_wait_gives_up_and_context_recovers(lib):
     pb = PartnerBasis(b, mu)
     ref = pb.U[0].conj().T @ oracle_h("si4") @ pb.U[0]
     assert np.abs(om - np.linalg.eigvalsh(ref)).max() <= TOL
+    assert bse.bse_get_stats(ctx)["reduce_kind"] == (0 if solver == "BSE_SOLVER_TRIDIAG" else 1)
     bse.bse_destroy(ctx)
 
 
