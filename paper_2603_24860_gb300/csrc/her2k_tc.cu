@@ -8,8 +8,14 @@
 //
 // a dense complex contraction with K = 64.  In real form, with K' = 128,
 //   Re(X Y^H) = [Xr Xi] [Yr Yi]^T,   Im(X Y^H) = [Xi -Xr] [Yr Yi]^T.
-// The double-float operands are split exactly into integer digits: a row x of
-// X (or Y) is scaled by 2^-e with 2^e above its largest element, rounded to 56
+// Before the split, V_l is scaled by 2^g_l and W_l by 2^-g_l, with g_l half the
+// difference of the exponents of their largest entries: the products V_l W_l^H
+// and W_l V_l^H are unchanged (powers of two), and the 64 columns of a row come
+// to comparable magnitudes.  (A reflector from a start vector of rounding-level
+// size, e.g. the projection of a dark block, has |V_0| ~ 1e-17 and |W_0| ~ 1e17;
+// unbalanced, such a column would set the scale of every row.)
+// The double-float operands are then split exactly into integer digits: a row x
+// of X (or Y) is scaled by 2^-e with 2^e above its largest element, rounded to 56
 // bits, q = rint(x 2^(56-e)), and written in balanced base 128,
 //   q = sum_{k=0..7} d_k 2^(49-7k),   |d_0| <= 128, |d_k| <= 64,
 // each digit an integer that bf16 holds exactly.  A product of two digits is
@@ -78,12 +84,41 @@ __device__ __forceinline__ void digits8(long long q, float* d) {
 // 2^p as a double (p within the normal range)
 __device__ __forceinline__ double pow2d(int p) { return __longlong_as_double((long long)(1023 + p) << 52); }
 
+// Exponents of the largest entries of V_l (block l) and W_l (block 32 + l) on rows
+// [k0, n); kNoExp for a column of zeros
+constexpr int kNoExp = -100000;
+__global__ void panel_colexp_kernel(const cdf* __restrict__ V, const cdf* __restrict__ W, int n, int k0, int* cx) {
+    __shared__ double s_m[kHThreads / 32];
+    const int l = blockIdx.x & 31;
+    const cdf* x = (blockIdx.x >= 32 ? W : V) + (size_t)l * n;
+    double m = 0.0;
+    for (int r = k0 + (int)threadIdx.x; r < n; r += blockDim.x) {
+        const cdf z = __ldcg(x + r);
+        m = fmax(m, fmax(fabs(cdf_re(z)), fabs(cdf_im(z))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_m[w]);
+        cx[blockIdx.x] = m > 0.0 ? ilogb(m) : kNoExp;
+    }
+}
+
+// balance exponent g_l of reflector pair l: V_l is scaled by 2^g_l, W_l by 2^-g_l
+__device__ __forceinline__ int balance_exp(const int* cx, int l) {
+    const int ev = cx[l], ew = cx[32 + l];
+    if (ev == kNoExp || ew == kNoExp) return 0;
+    return max(-500, min(500, (ew - ev) >> 1));
+}
+
 // One warp per row of X (rows rt0*128 <= r < nrt*128) or of Y (rows ct0*32 <= i < nct*32,
 // after the X rows): the rows of the tiles the update reads.  Rows outside [k0, n) get zero digits.  X row r: X[r,c] = V_c[r] (c < 32), W_{c-32}[r];
 // Y row i: Y[i,c] = W_c[i] (c < 32), V_{c-32}[i].  Lane c holds columns c and c + 32.
 __global__ void panel_digits_kernel(const cdf* __restrict__ V, const cdf* __restrict__ W, int n, int k0, int rt0,
-                                    int nrt, int ct0, int nct, __nv_bfloat16* Adig, __nv_bfloat16* Bdig, int* ex,
-                                    int* fy) {
+                                    int nrt, int ct0, int nct, const int* __restrict__ cx, __nv_bfloat16* Adig,
+                                    __nv_bfloat16* Bdig, int* ex, int* fy) {
     const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     const int nx = (nrt - rt0) * kHM, ny = (nct - ct0) * kHN;
     if (gw >= nx + ny) return;
@@ -94,10 +129,13 @@ __global__ void panel_digits_kernel(const cdf* __restrict__ V, const cdf* __rest
     if (live) {
         const cdf a = isx ? __ldcg(V + (size_t)lane * n + r) : __ldcg(W + (size_t)lane * n + r);
         const cdf b = isx ? __ldcg(W + (size_t)lane * n + r) : __ldcg(V + (size_t)lane * n + r);
-        v[0] = cdf_re(a);
-        v[1] = cdf_im(a);
-        v[2] = cdf_re(b);
-        v[3] = cdf_im(b);
+        const int g = balance_exp(cx, lane);
+        const double sv = pow2d(g), sw = pow2d(-g);   // V_l and W_l balanced (exact)
+        const double sa = isx ? sv : sw, sb = isx ? sw : sv;
+        v[0] = cdf_re(a) * sa;
+        v[1] = cdf_im(a) * sa;
+        v[2] = cdf_re(b) * sb;
+        v[3] = cdf_im(b) * sb;
     }
     double m = fmax(fmax(fabs(v[0]), fabs(v[1])), fmax(fabs(v[2]), fabs(v[3])));
 #pragma unroll
@@ -335,7 +373,7 @@ __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a
 size_t panel_update_tc_bytes(int64_t n) {
     const int64_t nrt = (n + kHM - 1) / kHM, nct = (n + kHN - 1) / kHN;
     return (size_t)nrt * kDig * kADigBytes + (size_t)nct * kBTileBytes + sizeof(int) * (size_t)(nrt * kHM + nct * kHN) +
-           4096;
+           sizeof(int) * 64 + 4096;
 }
 
 int launch_panel_update_tc(cdf* A, int64_t n, int k0, const cdf* V, const cdf* W, void* scratch, int* status,
@@ -350,11 +388,16 @@ int launch_panel_update_tc(cdf* A, int64_t n, int k0, const cdf* V, const cdf* W
     p += (size_t)nct * kBTileBytes;
     int* ex = (int*)p;
     int* fy = ex + (size_t)nrt * kHM;
-    // digits of the rows the tiles read (from the first tile row / column on)
+    int* cx = fy + (size_t)nct * kHN;
+    // balance exponents of the reflector pairs, then the digits of the rows the tiles read
+    // (from the first tile row / column on)
+    panel_colexp_kernel<<<64, kHThreads, 0, st>>>(V, W, (int)n, k0, cx);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
     {
         const int64_t warps = (int64_t)(nrt - rt0) * kHM + (int64_t)(nct - ct0) * kHN;
         panel_digits_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(V, W, (int)n, k0, rt0, nrt, ct0, nct,
-                                                                                Adig, Bdig, ex, fy);
+                                                                                cx, Adig, Bdig, ex, fy);
         note_launch();
         BSE_CUDA(cudaGetLastError());
     }
