@@ -1,5 +1,5 @@
 // Panel-end update of the blocked tridiagonal reduction on the tcgen05 tensor
-// cores, exact to about 2^-50 of its terms (sm_103a).
+// cores, accurate to about 2^-48 of its largest term (sm_103a).
 //
 // At the end of a panel of reflectors (V_l, W_l, l < 32) the trailing matrix
 // (rows and columns >= k0, both triangles, double-float) receives
@@ -7,36 +7,41 @@
 //   A -= sum_l (V_l W_l^H + W_l V_l^H) = X Y^H,   X = [V W], Y = [W V]   (n x 64 complex)
 //
 // a dense complex contraction with K = 64.  In real form, with K' = 128,
-//   Re(X Y^H) = [Xr Xi] [Yr Yi]^T,   Im(X Y^H) = [Xi -Xr] [Yr Yi]^T.
+//   Re(X Y^H) = [Xr Xi] [Yr Yi]^T,   Im(X Y^H) = [Xr Xi] [-Yi Yr]^T,
+// so X is stored once and each 32-column tile of Y in both forms, stacked as
+// the 64 rows (N) of one MMA operand: one MMA gives the real and imaginary parts.
 // Before the split, V_l is scaled by 2^g_l and W_l by 2^-g_l, with g_l half the
 // difference of the exponents of their largest entries: the products V_l W_l^H
 // and W_l V_l^H are unchanged (powers of two), and the 64 columns of a row come
 // to comparable magnitudes.  (A reflector from a start vector of rounding-level
 // size, e.g. the projection of a dark block, has |V_0| ~ 1e-17 and |W_0| ~ 1e17;
 // unbalanced, such a column would set the scale of every row.)
-// The double-float operands are then split exactly into integer digits: a row x
-// of X (or Y) is scaled by 2^-e with 2^e above its largest element, rounded to 56
-// bits, q = rint(x 2^(56-e)), and written in balanced base 128,
+// The double-float operands are then split exactly into digits: a row x of X (or
+// Y) is scaled by 2^-e with 2^e above its largest element, rounded to 56 bits,
+// q = rint(x 2^(56-e)), and written in balanced base 128,
 //   q = sum_{k=0..7} d_k 2^(49-7k),   |d_0| <= 128, |d_k| <= 64,
-// each digit an integer that bf16 holds exactly.  A product of two digits is
-// an integer below 2^14, a sum of 128 of them below 2^21, and the sum of the
-// up to 8 digit pairs (k, m) with the same k + m below 2^24: every partial GEMM
-// is exact in the FP32 accumulators of TMEM.  Pairs with k + m <= 7 are kept
-// (the others weigh below 2^-112 of the largest term), so that
-//   (X Y^H)_ri = 2^(e_r + f_i) sum_{g=0..7} 2^(-7g - 14) G_g[r,i],
-//   G_g = sum_{k+m=g} D^X_k (D^Y_m)^T,
-// and the result carries the 56-bit rounding of the operands only, below the
-// reduction's double-float roundoff.  The epilogue sums the eight exact FP32
-// groups in double-float, scales by the two powers of two and subtracts the
-// result from A in double-float.
+// and the digits are stored pre-scaled, x_k = d_k 2^-7k, which bf16 holds exactly.
+// A product x_k y_m is an integer below 2^14 times 2^-7(k+m), so for each
+// g = k + m the sum over K' and over the pairs with that g is an integer below
+// 2^24 times 2^-7g: exact in an FP32 accumulator of TMEM.  The groups g = 0..3
+// accumulate exactly, one accumulator each; the pairs with 4 <= g <= 7 (weights
+// below 2^-28 of the largest term) share a fifth accumulator, whose FP32
+// rounding stays below 2^-48 of that term; pairs with g > 7 (below 2^-56) are
+// left out.  Then
+//   (X Y^H)_ri = 2^(e_r + f_i - 14) (G_0 + G_1 + G_2 + G_3 + G_rest),
+// summed in double-float by the epilogue, scaled by the powers of two and
+// subtracted from A in double-float.
 //
-// Layout: the digits of X (both real operands of a 128-row tile) and of Y (a
-// 32-row tile) are written by panel_digits_kernel in the tcgen05 core-matrix
-// layout, tile after tile, so that one bulk copy brings a tile's operand.  A
-// persistent kernel (one CTA of 4 warps per SM) takes 128 x 32 output tiles of
-// the trailing block; per tile its 512 TMEM columns hold the 8 groups x
-// (real, imaginary) x 32 columns, the 8 digits of Y stay in shared memory
-// (64 KB), the digits of X stream through two 64 KB buffers.
+// Layout: the digits of X (a 128-row tile) and of Y (a 32-row tile in both forms)
+// are written by panel_digits_kernel in the tcgen05 core-matrix layout, tile
+// after tile, so that one bulk copy brings a tile's operand.  A persistent kernel
+// (one CTA of 4 warps per SM) takes a contiguous range of the 128 x 32 output
+// tiles in column-tile-major order: the 8 digits of the Y tile (128 KB) stay in
+// shared memory while its row tiles pass, the digits of X stream through a ring
+// of three 32 KB slots, and one thread keeps the tensor pipe fed (the MMAs of
+// digit k are queued before it waits for those of digit k - 1, whose slot then
+// takes digit k + 2).  A tile's 5 x 64 accumulator columns are read back by all
+// four warps (a warp per 32 TMEM lanes = rows) while the next digits land.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -52,15 +57,19 @@ namespace bse {
 namespace {
 
 constexpr int kHM = 128;           // rows of an output tile (TMEM lanes, M of the MMA)
-constexpr int kHN = 32;            // columns of an output tile (N of the MMA)
+constexpr int kHN = 32;            // complex output columns of a tile
+constexpr int kBN = 64;            // N of the MMA: the tile's rows of [Yr Yi], then of [-Yi Yr]
 constexpr int kHK = 128;           // K of the real GEMM (64 complex terms: 32 reflectors, V and W)
 constexpr int kDig = 8;            // digits per operand
+constexpr int kExact = 4;          // digit-pair groups g < kExact accumulate exactly, one accumulator each
+constexpr int kAcc = kExact + 1;   // accumulators per tile (the last one holds the groups g >= kExact)
+constexpr int kSlots = 3;          // ring of X digit buffers
 constexpr int kHThreads = 128;
-constexpr uint32_t kHTmemCols = 512;
-constexpr size_t kADigBytes = (size_t)2 * kHM * kHK * 2;   // one digit of an X tile: real and imaginary operands
-constexpr size_t kBDigBytes = (size_t)kHN * kHK * 2;       // one digit of a Y tile
-constexpr size_t kBTileBytes = kDig * kBDigBytes;          // the 8 digits of a Y tile (64 KB)
-constexpr size_t kHerSmem = kBTileBytes + 2 * kADigBytes + 1024;
+constexpr uint32_t kHTmemCols = 512;                       // kAcc x kBN = 320 used
+constexpr size_t kADigBytes = (size_t)kHM * kHK * 2;       // one digit of an X tile (32 KB)
+constexpr size_t kBDigBytes = (size_t)kBN * kHK * 2;       // one digit of a Y tile, both forms (16 KB)
+constexpr size_t kBTileBytes = kDig * kBDigBytes;          // the 8 digits of a Y tile (128 KB)
+constexpr size_t kHerSmem = kBTileBytes + kSlots * kADigBytes + 1024;
 
 __device__ __forceinline__ double cdf_re(cdf z) { return (double)z.x + (double)z.y; }
 __device__ __forceinline__ double cdf_im(cdf z) { return (double)z.z + (double)z.w; }
@@ -146,41 +155,44 @@ __global__ void panel_digits_kernel(const cdf* __restrict__ V, const cdf* __rest
     float d[4][kDig];
 #pragma unroll
     for (int j = 0; j < 4; ++j) digits8(__double2ll_rn(v[j] * sc), d[j]);
-    // K index: real parts of columns 0..63 at 0..63, imaginary parts at 64..127
+    // K index: real parts of columns 0..63 at 0..63, imaginary parts at 64..127; digit k
+    // stored as d_k 2^-7k (exact in bf16)
     const int kr0 = lane, kr1 = lane + 32, ki0 = 64 + lane, ki1 = 96 + lane;
+    auto bf = [](float x) { return __float2bfloat16_rn(x); };
     if (isx) {
         const int rt = r / kHM, rr = r % kHM;
 #pragma unroll
         for (int k = 0; k < kDig; ++k) {
-            unsigned char* base = (unsigned char*)Adig + ((size_t)rt * kDig + k) * kADigBytes;
-            unsigned char* re = base;                                 // [Xr Xi]
-            unsigned char* im = base + (size_t)kHM * kHK * 2;         // [Xi -Xr]
-            *(__nv_bfloat16*)(re + tc::core_off(rr, kr0, kHK)) = __float2bfloat16_rn(d[0][k]);
-            *(__nv_bfloat16*)(re + tc::core_off(rr, kr1, kHK)) = __float2bfloat16_rn(d[2][k]);
-            *(__nv_bfloat16*)(re + tc::core_off(rr, ki0, kHK)) = __float2bfloat16_rn(d[1][k]);
-            *(__nv_bfloat16*)(re + tc::core_off(rr, ki1, kHK)) = __float2bfloat16_rn(d[3][k]);
-            *(__nv_bfloat16*)(im + tc::core_off(rr, kr0, kHK)) = __float2bfloat16_rn(d[1][k]);
-            *(__nv_bfloat16*)(im + tc::core_off(rr, kr1, kHK)) = __float2bfloat16_rn(d[3][k]);
-            *(__nv_bfloat16*)(im + tc::core_off(rr, ki0, kHK)) = __float2bfloat16_rn(-d[0][k]);
-            *(__nv_bfloat16*)(im + tc::core_off(rr, ki1, kHK)) = __float2bfloat16_rn(-d[2][k]);
+            const float w = __int_as_float((127 - 7 * k) << 23);   // 2^-7k
+            unsigned char* base = (unsigned char*)Adig + ((size_t)rt * kDig + k) * kADigBytes;   // [Xr Xi]
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k] * w);
         }
     } else {
         const int ct = r / kHN, rr = r % kHN;
 #pragma unroll
         for (int k = 0; k < kDig; ++k) {
-            unsigned char* base = (unsigned char*)Bdig + ((size_t)ct * kDig + k) * kBDigBytes;   // [Yr Yi]
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = __float2bfloat16_rn(d[0][k]);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = __float2bfloat16_rn(d[2][k]);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = __float2bfloat16_rn(d[1][k]);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = __float2bfloat16_rn(d[3][k]);
+            const float w = __int_as_float((127 - 7 * k) << 23);
+            unsigned char* base = (unsigned char*)Bdig + ((size_t)ct * kDig + k) * kBDigBytes;
+            // row rr: [Yr Yi]; row rr + 32: [-Yi Yr]
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr0, kHK)) = bf(-d[1][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr1, kHK)) = bf(-d[3][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki0, kHK)) = bf(d[0][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki1, kHK)) = bf(d[2][k] * w);
         }
     }
 }
 
 struct HerArgs {
     cdf* A;                            // n x n column-major, double-float
-    const __nv_bfloat16* Adig;         // [nrt][8][2][128 x 128] core-matrix layout
-    const __nv_bfloat16* Bdig;         // [nct][8][32 x 128]
+    const __nv_bfloat16* Adig;         // [nrt][8][128 x 128] core-matrix layout
+    const __nv_bfloat16* Bdig;         // [nct][8][64 x 128]
     const int* ex;                     // [nrt*128] row exponents of X
     const int* fy;                     // [nct*32] row exponents of Y
     int n, k0, rt0, ct0, ntr, ntc;     // trailing block from k0; tiles rt0.., ct0.. (ntr x ntc of them)
@@ -188,61 +200,72 @@ struct HerArgs {
     long spin;                         // polls of an mbarrier wait before it gives up
 };
 
-// Persistent: output tiles (rt, ct) in row-tile-major order, blockIdx.x + j gridDim.x.
-// TMEM column of group g, part p (0 real, 1 imaginary), output column c: (p * 8 + g) * 32 + c.
+// DF sum of the five accumulators of one output (exact FP32 values)
+__device__ __forceinline__ float2 her_sum(const uint32_t (&v)[kAcc][8], int j) {
+    float h, l, h2, l2;
+    two_sum(__uint_as_float(v[0][j]), __uint_as_float(v[1][j]), h, l);
+    two_sum(__uint_as_float(v[2][j]), __uint_as_float(v[3][j]), h2, l2);
+    const float2 s = df_add(make_float2(h, l), make_float2(h2, l2));
+    return df_add(s, make_float2(__uint_as_float(v[4][j]), 0.f));
+}
+
+// Persistent: CTA b takes the tiles [T b / G, T (b + 1) / G) of the column-tile-major
+// order (t = ctl * ntr + rtl).  The X digit stream of a CTA: item j = digit j % 8 of its
+// tile j / 8, in slot j % 3; its copy is the (j / 3)-th completion of mb_full[slot], its
+// MMAs the (j / 3)-th commit to mb_empty[slot].  TMEM column of accumulator c, output
+// column i of the tile: c * 64 + i (real part), c * 64 + 32 + i (imaginary part).
 __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* Bs = smem;                                  // 8 digits of the Y tile
-    unsigned char* As = smem + kBTileBytes;                    // two digit buffers of the X tile
-    __shared__ __align__(8) uint64_t mb_b, mb_a[2], mb_m[2];
+    unsigned char* Bs = smem;                                  // 8 digits of the Y tile (both forms)
+    unsigned char* As = smem + kBTileBytes;                    // kSlots digit buffers of X tiles
+    __shared__ __align__(8) uint64_t mb_y, mb_full[kSlots], mb_empty[kSlots], mb_acc;
     __shared__ uint32_t slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        tc::mbar_init(&mb_b, 1);
-        tc::mbar_init(&mb_a[0], 1);
-        tc::mbar_init(&mb_a[1], 1);
-        tc::mbar_init(&mb_m[0], 1);
-        tc::mbar_init(&mb_m[1], 1);
+        tc::mbar_init(&mb_y, 1);
+        tc::mbar_init(&mb_acc, 1);
+        for (int i = 0; i < kSlots; ++i) {
+            tc::mbar_init(&mb_full[i], 1);
+            tc::mbar_init(&mb_empty[i], 1);
+        }
     }
     if (warp == 0) tc::tmem_alloc(&slot, kHTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = slot;
-    // phases issued (copies started, MMAs committed) and waited for, per mbarrier
-    uint32_t ib = 0, pb = 0, ia[2] = {0, 0}, pa[2] = {0, 0}, im[2] = {0, 0}, pm[2] = {0, 0};
-    const uint32_t idesc = tc::idesc_f16(kHM, kHN, 1);
+    const int64_t T = (int64_t)a.ntr * a.ntc;
+    const int t_begin = (int)(T * blockIdx.x / gridDim.x), t_end = (int)(T * (blockIdx.x + 1) / gridDim.x);
+    const int nitems = (t_end - t_begin) * kDig;
+    const uint32_t idesc = tc::idesc_f16(kHM, kBN, 1);
     const uint32_t lbo = 128, sbo = (uint32_t)(kHK / 8) * 128;
-    bool ok = true;
     // a bounded wait; on giving up the awaited operation is still let finish (default limit)
-    auto wait = [&](uint64_t* mb, uint32_t& ph) {
-        const bool got = tc::mbar_wait(mb, ph & 1u, a.spin);
-        if (!got) tc::mbar_wait(mb, ph & 1u, kMbarSpinLimit);
-        ++ph;
+    auto wait = [&](uint64_t* mb, uint32_t parity) {
+        const bool got = tc::mbar_wait(mb, parity, a.spin);
+        if (!got) tc::mbar_wait(mb, parity, kMbarSpinLimit);
         return got;
     };
-    const int ntiles = a.ntr * a.ntc;
-    // bulk copies of a tile's Y digits and of its first two X digits (tid 0 issues, all count)
-    auto issue_tile = [&](int t) {
-        const int rt = a.rt0 + t / a.ntc, ct = a.ct0 + t % a.ntc;
-        const unsigned char* ag = (const unsigned char*)a.Adig + (size_t)rt * kDig * kADigBytes;
-        if (tid == 0) {
-            tc::mbar_expect_tx(&mb_b, (uint32_t)kBTileBytes);
-            tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)ct * kBTileBytes, (uint32_t)kBTileBytes, &mb_b);
-            for (int b = 0; b < 2; ++b) {
-                tc::mbar_expect_tx(&mb_a[b], (uint32_t)kADigBytes);
-                tc::bulk_g2s(As + b * kADigBytes, ag + b * kADigBytes, (uint32_t)kADigBytes, &mb_a[b]);
-            }
-        }
-        ++ib;
-        ++ia[0];
-        ++ia[1];
+    auto item_src = [&](int j) {
+        const int t = t_begin + j / kDig;
+        const int rt = a.rt0 + t % a.ntr;
+        return (const unsigned char*)a.Adig + ((size_t)rt * kDig + j % kDig) * kADigBytes;
     };
-    if ((int)blockIdx.x < ntiles) issue_tile(blockIdx.x);
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int rt = a.rt0 + t / a.ntc, ct = a.ct0 + t % a.ntc;
-        const unsigned char* ag = (const unsigned char*)a.Adig + (size_t)rt * kDig * kADigBytes;
+    // state of thread 0 (the issuing thread): stream items copied, landed, committed, retired
+    int issued = 0, landed = 0, committed = 0, retired = 0, ys = 0, accs = 0;
+    auto issue_item = [&](int j) {
+        const int sl = j % kSlots;
+        tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kADigBytes);
+        tc::bulk_g2s(As + sl * kADigBytes, item_src(j), (uint32_t)kADigBytes, &mb_full[sl]);
+        issued = j + 1;
+    };
+    if (tid == 0)
+        for (int j = 0; j < kSlots && j < nitems; ++j) issue_item(j);
+    bool ok = true;
+    int cur_ct = -1;
+    for (int tl = 0; t_begin + tl < t_end && ok; ++tl) {
+        const int t = t_begin + tl;
+        const int rt = a.rt0 + t % a.ntr, ct = a.ct0 + t / a.ntr;
         // this thread's row of the output tile; its first 8 entries of A load while the MMAs run
         const int r = rt * kHM + warp * 32 + lane;
         const bool rlive = r >= a.k0 && r < a.n;
@@ -255,81 +278,74 @@ __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a
         };
         cdf qa[8], qb[8];
         load_chunk(0, qa);
-        ok = __syncthreads_and(wait(&mb_b, pb)) != 0;
-        for (int k = 0; k < kDig && ok; ++k) {
-            const int b = k & 1;
-            ok = __syncthreads_and(wait(&mb_a[b], pa[b])) != 0;
-            if (!ok) break;
-            tc::fence_after();
-            if (tid == 0) {
-                const uint32_t a0 = tc::smem_u32(As + b * kADigBytes), b0 = tc::smem_u32(Bs);
+        bool ok0 = true;
+        if (tid == 0) {
+            if (ct != cur_ct) {   // every MMA of the earlier tiles is complete: the Y buffer is free
+                tc::mbar_expect_tx(&mb_y, (uint32_t)kBTileBytes);
+                tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)ct * kBTileBytes, (uint32_t)kBTileBytes, &mb_y);
+                ok0 = wait(&mb_y, (uint32_t)(ys & 1));
+                ++ys;
+            }
+            for (int k = 0; k < kDig && ok0; ++k) {
+                const int j = tl * kDig + k, sl = j % kSlots;
+                ok0 = wait(&mb_full[sl], (uint32_t)((j / kSlots) & 1));
+                landed = j + 1;
+                if (!ok0) break;
+                tc::fence_after();
+                const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kADigBytes), lbo, sbo);
                 for (int m = 0; m + k < kDig; ++m) {
-                    const int g = k + m;
-                    for (int part = 0; part < 2; ++part) {
-                        const uint32_t d = tmem + (uint32_t)((part * kDig + g) * kHN);
-                        const uint32_t ab = a0 + (uint32_t)(part * kHM * kHK * 2);
-                        const uint32_t bb = b0 + (uint32_t)(m * kBDigBytes);
-                        for (int ks = 0; ks < kHK / 16; ++ks)
-                            tc::mma_f16(d, tc::smem_desc(ab + ks * 256, lbo, sbo), tc::smem_desc(bb + ks * 256, lbo, sbo),
-                                        idesc, (k | ks) != 0);
-                    }
+                    const int g = k + m, acc = g < kExact ? g : kExact;
+                    const bool first = k == 0 && (g < kExact || m == kExact);
+                    const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + m * kBDigBytes), lbo, sbo);
+                    const uint32_t d = tmem + (uint32_t)(acc * kBN);
+#pragma unroll
+                    for (int ks = 0; ks < kHK / 16; ++ks)   // 16 K per MMA: 256 bytes, 16 descriptor units
+                        tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, (first && ks == 0) ? 0u : 1u);
                 }
-                tc::mma_commit(&mb_m[b]);
-            }
-            ++im[b];
-            if (k + 2 < kDig) {   // the buffer takes digit k + 2 once digit k's MMAs are done
-                ok = __syncthreads_and(wait(&mb_m[b], pm[b])) != 0;
-                if (ok) {
-                    if (tid == 0) {
-                        tc::mbar_expect_tx(&mb_a[b], (uint32_t)kADigBytes);
-                        tc::bulk_g2s(As + b * kADigBytes, ag + (size_t)(k + 2) * kADigBytes, (uint32_t)kADigBytes,
-                                     &mb_a[b]);
-                    }
-                    ++ia[b];
+                tc::mma_commit(&mb_empty[sl]);
+                committed = j + 1;
+                if (j >= 1) {   // the MMAs of item j - 1 done: its slot takes item j + 2
+                    ok0 = wait(&mb_empty[(j - 1) % kSlots], (uint32_t)(((j - 1) / kSlots) & 1));
+                    retired = j;
+                    if (ok0 && j + 2 < nitems) issue_item(j + 2);
                 }
             }
+            if (ok0) {
+                tc::mma_commit(&mb_acc);
+                ++accs;
+            }
+            cur_ct = ct;
         }
+        ok = __syncthreads_and(tid != 0 || ok0) != 0;
         if (!ok) break;
-        // the MMAs of digits 6 and 7
-        {
-            const bool w0 = wait(&mb_m[0], pm[0]);
-            const bool w1 = wait(&mb_m[1], pm[1]);
-            ok = __syncthreads_and(w0 && w1) != 0;
-        }
+        // the tile's accumulators are complete
+        ok = __syncthreads_and(wait(&mb_acc, (uint32_t)(tl & 1))) != 0;
         if (!ok) break;
         tc::fence_after();
-        // shared memory is free: the next tile's copies land during the epilogue
-        if (t + (int)gridDim.x < ntiles) issue_tile(t + gridDim.x);
-        // epilogue, 8 columns at a time (the next 8 entries of A loading meanwhile): the eight
-        // exact groups read together, summed in double-float, scaled by 2^(e_r + f_i), subtracted
+        // epilogue, 8 columns at a time (the next 8 entries of A loading meanwhile)
         const int er = rlive ? __ldg(a.ex + r) : 0;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
         auto finish_chunk = [&](int c0, const cdf* q) {
-            float2 acc[2][8];
+            uint32_t vr[kAcc][8], vi[kAcc][8];
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                uint32_t v[kDig][8];
+            for (int c = 0; c < kAcc; ++c) {
+                tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + c0), vr[c]);
+                tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + kHN + c0), vi[c]);
+            }
 #pragma unroll
-                for (int g = 0; g < kDig; ++g)
-                    tc::tmem_ld8_async(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((p * kDig + g) * kHN + c0), v[g]);
-#pragma unroll
-                for (int g = 0; g < kDig; ++g) tc::tmem_ld_wait(v[g]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[p][j] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int g = 0; g < kDig; ++g) {
-                    const float w = __int_as_float((127 - 7 * g - 14) << 23);   // 2^(-7g - 14), exact
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[p][j] = df_add(acc[p][j], make_float2(__uint_as_float(v[g][j]) * w, 0.f));
-                }
+            for (int c = 0; c < kAcc; ++c) {
+                tc::tmem_ld_wait(vr[c]);
+                tc::tmem_ld_wait(vi[c]);
             }
             if (rlive)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int i = ct * kHN + c0 + j;
                     if (i < a.k0 || i >= a.n) continue;
-                    const float sc = ldexpf(1.f, er + __ldg(a.fy + i));
-                    const float2 re = df_add(make_float2(q[j].x, q[j].y), make_float2(-acc[0][j].x * sc, -acc[0][j].y * sc));
-                    const float2 im = df_add(make_float2(q[j].z, q[j].w), make_float2(-acc[1][j].x * sc, -acc[1][j].y * sc));
+                    const float sc = ldexpf(1.f, er + __ldg(a.fy + i) - 14);
+                    const float2 sr = her_sum(vr, j), si = her_sum(vi, j);
+                    const float2 re = df_add(make_float2(q[j].x, q[j].y), make_float2(-sr.x * sc, -sr.y * sc));
+                    const float2 im = df_add(make_float2(q[j].z, q[j].w), make_float2(-si.x * sc, -si.y * sc));
                     a.A[(size_t)i * a.n + r] = make_float4(re.x, re.y, im.x, im.y);
                 }
         };
@@ -344,24 +360,13 @@ __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a
         __syncthreads();   // TMEM is reused by the next tile
         tc::fence_after();
     }
-    if (!ok) {
+    if (!ok && tid == 0) {
         // a wait gave up: let every copy and MMA still in flight finish (the default limit)
         // before the CTA frees its tensor memory and exits
-        while (pb < ib) {
-            tc::mbar_wait(&mb_b, pb & 1u, kMbarSpinLimit);
-            ++pb;
-        }
-        for (int b = 0; b < 2; ++b) {
-            while (pa[b] < ia[b]) {
-                tc::mbar_wait(&mb_a[b], pa[b] & 1u, kMbarSpinLimit);
-                ++pa[b];
-            }
-            while (pm[b] < im[b]) {
-                tc::mbar_wait(&mb_m[b], pm[b] & 1u, kMbarSpinLimit);
-                ++pm[b];
-            }
-        }
-        if (tid == 0) atomicExch(a.status, 1);
+        for (int j = landed; j < issued; ++j) tc::mbar_wait(&mb_full[j % kSlots], (uint32_t)((j / kSlots) & 1), kMbarSpinLimit);
+        for (int j = retired; j < committed; ++j)
+            tc::mbar_wait(&mb_empty[j % kSlots], (uint32_t)((j / kSlots) & 1), kMbarSpinLimit);
+        atomicExch(a.status, 1);
     }
     tc::fence_before();
     __syncthreads();
