@@ -432,6 +432,12 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *   BSE_SOLVER_TRIDIAG_BLOCKED_DF  as TRIDIAG_BLOCKED with the panel-end
  *                      update on the CUDA cores in double-float (for checks
  *                      and measurements).
+ *   BSE_SOLVER_TRIDIAG_TWOSTAGE  as TRIDIAG with a two-stage reduction at
+ *                      every size: dense -> band of half-bandwidth 32 by
+ *                      panels of 32 Householder reflectors (one pass of the
+ *                      trailing block through a GEMM and the tensor-core
+ *                      rank-64 update per panel), then band -> tridiagonal by
+ *                      bulge chasing; every reflector keeps e_0 fixed.
  *   BSE_SOLVER_AUTO    (default) TRIDIAG for partner blocks, for blocks
  *                      of one-dimensional irreps and for blocks of irreps
  *                      outside the polar-vector representation (B_mu = 0
@@ -444,7 +450,8 @@ enum {
     BSE_SOLVER_DENSE = 1,
     BSE_SOLVER_TRIDIAG = 2,
     BSE_SOLVER_TRIDIAG_BLOCKED = 3,
-    BSE_SOLVER_TRIDIAG_BLOCKED_DF = 4
+    BSE_SOLVER_TRIDIAG_BLOCKED_DF = 4,
+    BSE_SOLVER_TRIDIAG_TWOSTAGE = 5
 };
 
 /*
@@ -553,7 +560,8 @@ typedef struct {
     float ms_reduce;            /* tridiagonal reduction kernel of the last spectrum (TRIDIAG), else 0 */
     float ms_rotate;            /* rotated direct-term blocks of the last build (part of ms_direct) */
     int32_t reduce_kind;        /* reduction of the last TRIDIAG spectrum: 0 block in shared memory, 1 blocked
-                                   (panels) with the tensor-core panel update, 2 blocked with the double-float one */
+                                   (panels) with the tensor-core panel update, 2 blocked with the double-float one,
+                                   3 two-stage (band, then bulge chasing) */
     int32_t tc_pairs_per_cta;   /* k pairs per CTA (sharing one W(q)) of the last split-precision build, as tuned */
     int32_t pad_;
 } bse_stats;

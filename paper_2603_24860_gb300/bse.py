@@ -26,6 +26,7 @@ BSE_TERM_DIAG, BSE_TERM_EXCHANGE, BSE_TERM_DIRECT, BSE_TERM_ALL = 1, 2, 4, 7
 BSE_BANDS_CC, BSE_BANDS_VV, BSE_BANDS_CV = 0, 1, 2
 BSE_SOLVER_AUTO, BSE_SOLVER_DENSE, BSE_SOLVER_TRIDIAG, BSE_SOLVER_TRIDIAG_BLOCKED = 0, 1, 2, 3
 BSE_SOLVER_TRIDIAG_BLOCKED_DF = 4
+BSE_SOLVER_TRIDIAG_TWOSTAGE = 5
 BSE_IRREP_ALL = -1
 
 _P32 = C.POINTER(C.c_int32)

@@ -2116,6 +2116,7 @@ static int spectrum_tridiag(bse_ctx* c, int nparts, bool dark, int64_t dim, cons
                                     c->timing ? c->ev[6] : nullptr, c->timing ? c->ev[7] : nullptr, c->wait_polls,
                                     c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED      ? 1
                                     : c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED_DF ? 2
+                                    : c->solver_mode == BSE_SOLVER_TRIDIAG_TWOSTAGE   ? 3
                                                                                       : 0,
                                     &c->stats.reduce_kind));
     if (c->timing) BSE_CUDA(cudaEventRecord(c->ev[4], c->stream));
@@ -2150,7 +2151,7 @@ static int spectrum_generic(bse_ctx* c, IrrepDev* parts, int nparts, int irrep_d
                            c->stream));
     const double pref = 4.0 * M_PI * c->spin / c->t.nk;
     const bool forced_tri = c->solver_mode == BSE_SOLVER_TRIDIAG || c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED ||
-                            c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED_DF;
+                            c->solver_mode == BSE_SOLVER_TRIDIAG_BLOCKED_DF || c->solver_mode == BSE_SOLVER_TRIDIAG_TWOSTAGE;
     const bool try_tri = forced_tri ||
                          (c->solver_mode == BSE_SOLVER_AUTO && (nparts > 1 || irrep_dim == 1 || dark) &&
                           dim <= tridiag_max_dim());
@@ -2345,7 +2346,8 @@ int bse_set_solver(bse_ctx* c, int32_t solver) {
     clear_error();
     if (!c) return fail(BSE_EINVAL, "null argument");
     if (solver != BSE_SOLVER_AUTO && solver != BSE_SOLVER_DENSE && solver != BSE_SOLVER_TRIDIAG &&
-        solver != BSE_SOLVER_TRIDIAG_BLOCKED && solver != BSE_SOLVER_TRIDIAG_BLOCKED_DF)
+        solver != BSE_SOLVER_TRIDIAG_BLOCKED && solver != BSE_SOLVER_TRIDIAG_BLOCKED_DF &&
+        solver != BSE_SOLVER_TRIDIAG_TWOSTAGE)
         return fail(BSE_EINVAL, "unknown solver %d", solver);
     c->solver_mode = solver;
     return BSE_OK;

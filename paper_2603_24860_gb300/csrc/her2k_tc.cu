@@ -196,6 +196,7 @@ struct HerArgs {
     const int* ex;                     // [nrt*128] row exponents of X
     const int* fy;                     // [nct*32] row exponents of Y
     int n, k0, rt0, ct0, ntr, ntc;     // trailing block from k0; tiles rt0.., ct0.. (ntr x ntc of them)
+    int resident_from;                 // columns below it are streamed (evict-first loads and stores)
     int* status;                       // raised when a bounded wait gives up
     long spin;                         // polls of an mbarrier wait before it gives up
 };
@@ -273,7 +274,9 @@ __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int i = ct * kHN + c0 + j;
-                q[j] = rlive && i >= a.k0 && i < a.n ? __ldcg(a.A + (size_t)i * a.n + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const cdf* src = a.A + (size_t)i * a.n + r;
+                q[j] = rlive && i >= a.k0 && i < a.n ? (i < a.resident_from ? __ldcs(src) : __ldcg(src))
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         };
         cdf qa[8], qb[8];
@@ -346,7 +349,11 @@ __global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a
                     const float2 sr = her_sum(vr, j), si = her_sum(vi, j);
                     const float2 re = df_add(make_float2(q[j].x, q[j].y), make_float2(-sr.x * sc, -sr.y * sc));
                     const float2 im = df_add(make_float2(q[j].z, q[j].w), make_float2(-si.x * sc, -si.y * sc));
-                    a.A[(size_t)i * a.n + r] = make_float4(re.x, re.y, im.x, im.y);
+                    const cdf out = make_float4(re.x, re.y, im.x, im.y);
+                    if (i < a.resident_from)
+                        __stcs(a.A + (size_t)i * a.n + r, out);
+                    else
+                        a.A[(size_t)i * a.n + r] = out;
                 }
         };
         load_chunk(8, qb);
@@ -381,8 +388,8 @@ size_t panel_update_tc_bytes(int64_t n) {
            sizeof(int) * 64 + 4096;
 }
 
-int launch_panel_update_tc(cdf* A, int64_t n, int k0, const cdf* V, const cdf* W, void* scratch, int* status,
-                           cudaStream_t st, long wait_polls) {
+int launch_panel_update_tc(cdf* A, int64_t n, int k0, int resident_from, const cdf* V, const cdf* W, void* scratch,
+                           int* status, cudaStream_t st, long wait_polls) {
     if (k0 >= n) return BSE_OK;
     const int nrt = (int)((n + kHM - 1) / kHM), nct = (int)((n + kHN - 1) / kHN);
     const int rt0 = k0 / kHM, ct0 = k0 / kHN;
@@ -418,6 +425,7 @@ int launch_panel_update_tc(cdf* A, int64_t n, int k0, const cdf* V, const cdf* W
     h.ct0 = ct0;
     h.ntr = nrt - rt0;
     h.ntc = nct - ct0;
+    h.resident_from = resident_from;
     h.status = status;
     h.spin = wait_limit(wait_polls, kMbarSpinLimit);
     BSE_CUDA(cudaFuncSetAttribute(panel_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHerSmem));

@@ -317,11 +317,19 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
 // *used (optional): 0 the shared-memory reduction ran, 1 the blocked one with the tensor-core
 // update, 2 the blocked one with the CUDA-core update
 // her2k_tc.cu: the panel-end update A -= V W^H + W V^H (rows and columns >= k0 of the n x n
-// double-float block; V, W [32][n]) from exact bf16 digit GEMMs on the tensor cores; status
-// is raised when a bounded wait gives up
+// double-float block; V, W [32][n]) from exact bf16 digit GEMMs on the tensor cores; columns
+// below resident_from are read and written with evict-first hints; status is raised when a
+// bounded wait gives up
 size_t panel_update_tc_bytes(int64_t n);
-int launch_panel_update_tc(float4* A, int64_t n, int k0, const float4* V, const float4* W, void* scratch, int* status,
-                           cudaStream_t st, long wait_polls);
+// tridiag2.cu: the two-stage reduction (start reflector, dense -> band 32 by panels with the
+// tensor-core rank-64 update, band -> tridiagonal by bulge chasing) of the FP64 block A (n x n,
+// rewritten in double-float in place) to d, e; V, W [32][n] and tc_scratch as for the panel
+// update, scratch of tridiag2_bytes(n)
+size_t tridiag2_bytes(int64_t n);
+int launch_tridiag2(float4* A, int64_t n, const double2* v0, const double* beta0, double* d, double* e, float4* V,
+                    float4* W, void* tc_scratch, void* scratch, int* err, cudaStream_t st, long wait_polls);
+int launch_panel_update_tc(float4* A, int64_t n, int k0, int resident_from, const float4* V, const float4* W,
+                           void* scratch, int* status, cudaStream_t st, long wait_polls);
 // lanczos.cu: the Lanczos recurrence on a Hermitian block from conj(b) (Lanczos-Haydock, Sec. IV)
 size_t lanczos_scratch_bytes(int64_t n, int m);
 int lanczos_max_dim();

@@ -31,6 +31,7 @@
 #include "fp64_fast.h"
 #include "grid_sync.h"
 #include "internal.h"
+#include "reflector.h"
 
 namespace bse {
 
@@ -110,63 +111,6 @@ struct TriArgs {
     long spin;            // polls of a grid barrier before it gives up
 };
 
-// Reflector k from alpha = (column k)_{k+1} and sigma = sum_{r>k+1} |(column k)_r|^2
-// in the zlarfg convention (v_{k+1} = 1): beta = -sign(Re alpha) sqrt(|alpha|^2 + sigma),
-// tau = (beta - alpha) / beta, v_r = x_r / (alpha - beta).  FP64 version, for
-// squared norms outside the safe range of the double-float one.
-__device__ void reflector_fp64(double2 al, double sigma, double2& tau, double2& inv, double& beta) {
-    if (sigma == 0.0 && al.y == 0.0) {
-        tau = make_double2(0.0, 0.0);
-        beta = al.x;
-        inv = make_double2(0.0, 0.0);
-        return;
-    }
-    const double nrm2 = fma(al.x, al.x, fma(al.y, al.y, sigma));
-    const double y = copysign(rsqrt_nr(nrm2), al.x);   // -1/beta
-    beta = -nrm2 * y;
-    tau = make_double2(fma(al.x, y, 1.0), al.y * y);
-    const double2 den = make_double2(al.x - beta, al.y);
-    const double rm = rcp_nr(fma(den.x, den.x, den.y * den.y));
-    inv = make_double2(den.x * rm, -den.y * rm);
-}
-
-// The same in double-float: a few hundred FP32 cycles instead of a chain of
-// dependent FP64 instructions
-__device__ void reflector(cdf al, float2 sigma, cdf& tau, cdf& inv, float2& beta) {
-    if (sigma.x == 0.f && al.z == 0.f && al.w == 0.f) {
-        tau = cdf_zero();
-        beta = make_float2(al.x, al.y);
-        inv = cdf_zero();
-        return;
-    }
-    float s = sigma.x, lo = sigma.y;
-    df_acc(s, lo, al.x, al.y, al.x, al.y);
-    df_acc(s, lo, al.z, al.w, al.z, al.w);
-    const float2 nrm2 = df_fin(s, lo);
-    if (!(nrm2.x >= 0x1p-100f && nrm2.x <= 0x1p100f)) {
-        double2 t, iv;
-        double b;
-        reflector_fp64(cdf_to(al), df_to(sigma), t, iv, b);
-        tau = cdf_from(t);
-        inv = cdf_from(iv);
-        beta = df_from(b);
-        return;
-    }
-    const float2 nrm = df_sqrt(nrm2);
-    beta = al.x < 0.f ? nrm : df_neg(nrm);
-    const float2 rb = df_rcp(beta);
-    const float2 ar = df_mul(make_float2(al.x, al.y), rb), ai = df_mul(make_float2(al.z, al.w), rb);
-    const float2 tr = df_add(make_float2(1.f, 0.f), df_neg(ar));
-    tau = make_float4(tr.x, tr.y, -ai.x, -ai.y);
-    const float2 dr = df_add(make_float2(al.x, al.y), df_neg(beta));
-    const float2 di = make_float2(al.z, al.w);
-    float q = 0.f, ql = 0.f;
-    df_acc(q, ql, dr.x, dr.y, dr.x, dr.y);
-    df_acc(q, ql, di.x, di.y, di.x, di.y);
-    const float2 rm = df_rcp(df_fin(q, ql));
-    const float2 ir = df_mul(dr, rm), ii = df_mul(di, rm);
-    inv = make_float4(ir.x, ir.y, -ii.x, -ii.y);
-}
 
 // One grid barrier per reflection step s (H(s) = I - tau v v^H on rows >= s+1,
 // s = -1 being the start reflector H0 on all rows), k = s+1:
@@ -413,6 +357,9 @@ struct TriBArgs {
     long spin;            // polls of a grid barrier before it gives up
     int s_begin, s_end;   // the steps of this launch: s_begin <= s < s_end (s = -1: the start reflector)
     int tc_update;        // 1: the panel-end update is left to the tensor-core kernels between launches
+    int resident_from;    // columns i >= resident_from are read with normal L2 priority (they stay in
+                          // L2 from step to step), the others streamed with evict-first loads
+    int stage_rows;       // rows per shared-memory stage of the column dot products (0: loads to registers)
 };
 
 // dynamic shared memory of the blocked kernel (cdf units): the staged column
@@ -435,7 +382,8 @@ template <bool kStream>
 __device__ __forceinline__ cdf ld_col(const cdf* p) { return kStream ? __ldcs(p) : __ldcg(p); }
 
 // sum_{r >= r0} conj(x[r]) c[r] over a column x in global memory, lanes over
-// rows, eight rows' loads in flight per lane; reduced over the warp
+// rows, sixteen rows' loads in flight per lane; reduced over the warp (used when
+// shared memory has no room for the staged form below)
 template <bool kStream>
 __device__ __forceinline__ cdf warp_coldot(const cdf* __restrict__ x, const cdf* c, int r0, int n, int lane) {
     cdf acc0 = cdf_zero(), acc1 = cdf_zero(), acc2 = cdf_zero(), acc3 = cdf_zero();
@@ -465,6 +413,69 @@ __device__ __forceinline__ cdf warp_coldot(const cdf* __restrict__ x, const cdf*
     return cdf_warp_sum(cdf_add(cdf_add(acc0, acc1), cdf_add(acc2, acc3)));
 }
 
+// 16-byte asynchronous copies global -> shared (L2 only), optionally with an evict-first L2 policy
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_ef(void* dst, const void* src, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// The same dot product with the column streamed through three shared-memory
+// stages of R rows per warp (R a multiple of 32): while a stage is multiplied
+// the next two are in flight, without holding registers, so that the warp's
+// HBM or L2 latency overlaps its double-float arithmetic.  Each lane copies and
+// reads only its own rows (r = base + lane + 32 u), so no warp synchronisation
+// is needed; every stage commits a copy group, empty or not.
+__device__ __forceinline__ cdf warp_coldot_staged(const cdf* __restrict__ x, const cdf* c, int r0, int n, int lane,
+                                               cdf* stg, int R, bool stream, uint64_t pol) {
+    cdf acc0 = cdf_zero(), acc1 = cdf_zero(), acc2 = cdf_zero(), acc3 = cdf_zero();
+    const int nst = (n - r0 + R - 1) / R;
+    auto issue = [&](int st) {
+        if (st < nst) {
+            cdf* b = stg + (st % 3) * R;
+            const int base = r0 + st * R;
+            const int lim = min(R, n - base);
+            if (stream)
+                for (int u = lane; u < lim; u += 32) cp_async16_ef(b + u, x + base + u, pol);
+            else
+                for (int u = lane; u < lim; u += 32) cp_async16(b + u, x + base + u);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + 2);
+        cp_async_wait<2>();   // this lane's copies of stage st have landed
+        const cdf* b = stg + (st % 3) * R;
+        const int base = r0 + st * R;
+        const int lim = min(R, n - base);
+        int u = lane;
+        for (; u + 96 < lim; u += 128) {
+            acc0 = cdf_dot_acc(acc0, b[u], c[base + u]);
+            acc1 = cdf_dot_acc(acc1, b[u + 32], c[base + u + 32]);
+            acc2 = cdf_dot_acc(acc2, b[u + 64], c[base + u + 64]);
+            acc3 = cdf_dot_acc(acc3, b[u + 96], c[base + u + 96]);
+        }
+        for (; u < lim; u += 32) acc0 = cdf_dot_acc(acc0, b[u], c[base + u]);
+    }
+    cp_async_wait<0>();
+    return cdf_warp_sum(cdf_add(cdf_add(acc0, acc1), cdf_add(acc2, acc3)));
+}
+
 __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArgs a) {
     extern __shared__ __align__(16) cdf s_dyn[];
     __shared__ cdf s_tau, s_inv, s_alpha;
@@ -485,6 +496,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
     cdf* colk = wown + ncl;                            // [ncl] A[i, k] of the next current column, own rows
     cdf* s12 = colk + ncl;                             // [2 (kNb + 1)]: s1 then s2
     cdf* cwv = s12 + 2 * (kNb + 1);                    // [2 (kNb + 1)]: W[k,l'] then V[k,l']
+    cdf* stg = s_dyn + tri_blocked_smem(n, G) / sizeof(cdf) + (size_t)wid * 3 * a.stage_rows;   // this warp's stages
+    const uint64_t pol = evict_first_policy();
     cdf* gA = a.A;
     auto col = [&](int i) -> cdf* { return gA + (size_t)i * n; };
     auto WVo = [&](int m, int l2) -> cdf& { return WV[(size_t)m * 2 * kNb + l2]; };
@@ -562,7 +575,10 @@ __global__ void __launch_bounds__(kTriThreads, 1) tridiag_blocked_kernel(TriBArg
                     if (s >= 0) top = cdf_conj(__ldcg(x + s + 1));
                     if (l > 0) ck = __ldcg(col(k) + i);   // column k is not written during a panel
                 }
-                const cdf zr = warp_coldot<true>(x, Cs, r0, n, lane);
+                const bool stream = i < a.resident_from;
+                const cdf zr = a.stage_rows > 0 ? warp_coldot_staged(x, Cs, r0, n, lane, stg, a.stage_rows, stream, pol)
+                               : stream         ? warp_coldot<true>(x, Cs, r0, n, lane)
+                                                : warp_coldot<false>(x, Cs, r0, n, lane);
                 if (lane == 0) {
                     zown[m] = zr;
                     ztop[m] = top;
@@ -1205,7 +1221,8 @@ size_t tridiag_scratch_bytes(int64_t n) {
     // 16 bytes each), its norm parts (1024 float2) and s dots (2 kNb); 256-byte alignment of each piece
     return sizeof(double2) * (size_t)(5 * n + 2048) + sizeof(double) * (size_t)(5 * n) +
            sizeof(float2) * (size_t)(2 * n * n) + sizeof(float) * (size_t)(2 * n) + sizeof(float2) * (size_t)(2 * n) +
-           sizeof(cdf) * (size_t)(2 * kNb * n + 4 * kNb) + sizeof(float2) * 1024 + panel_update_tc_bytes(n) + 16384;
+           sizeof(cdf) * (size_t)(2 * kNb * n + 4 * kNb) + sizeof(float2) * 1024 + panel_update_tc_bytes(n) +
+           tridiag2_bytes(n) + 16384;
 }
 
 // the blocked reduction keeps a column (16 n bytes) and the panel coefficients
@@ -1254,6 +1271,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     cdf* sdot = (cdf*)take(sizeof(cdf) * 4 * kNb);
     float2* npart = (float2*)take(sizeof(float2) * 1024);
     void* tcs = take(panel_update_tc_bytes(n));
+    void* two = take(tridiag2_bytes(n));
 
     int dev = 0, sms = 0, maxsm = 0;
     BSE_CUDA(cudaGetDevice(&dev));
@@ -1268,7 +1286,7 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     if (!smem) G = (int)std::min<int64_t>(sms, n);
     if (!smem && tri_blocked_smem(n, G) > (size_t)maxsm)
         return fail(BSE_EUNSUPPORTED, "tridiagonal path: n = %lld exceeds shared memory", (long long)n);
-    if (used) *used = smem ? 0 : (tcu ? 1 : 2);
+    if (used) *used = variant == 3 ? 3 : (smem ? 0 : (tcu ? 1 : 2));
 
     BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     BSE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -1277,7 +1295,11 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     note_launch();
     BSE_CUDA(cudaGetLastError());
 
-    if (smem) {
+    if (variant == 3) {   // two-stage: dense -> band -> tridiagonal
+        if (ev0) BSE_CUDA(cudaEventRecord(ev0, st));
+        BSE_TRY(launch_tridiag2(reinterpret_cast<cdf*>(h), n, v0, beta0, d, e, Vp, Wp, tcs, two, err, st, wait_polls));
+        if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
+    } else if (smem) {
         TriArgs a;
         a.A = h;
         a.n = n;
@@ -1320,8 +1342,16 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
         a.bar = bar;
         a.err = err;
         a.spin = wait_limit(wait_polls, kGridSpinLimit);
+        // the last columns, about 80 MB of them, stay in L2 between steps (the other columns and
+        // the panel's vectors share the rest); a block that fits keeps all its columns there
+        const int64_t keep = std::min<int64_t>(n, (int64_t)80000000 / (16 * n));
+        a.resident_from = (int)(n - keep);
+        // three stages of up to 256 rows per warp in the shared memory left over
+        const size_t base_smem = tri_blocked_smem(n, G);
+        const int64_t room = ((int64_t)maxsm - (int64_t)base_smem - 1024) / (kTriWarps * 3 * (int64_t)sizeof(cdf));
+        a.stage_rows = room >= 64 ? (int)std::min<int64_t>(256, room / 32 * 32) : 0;
         void* args[] = {&a};
-        const size_t dyn = tri_blocked_smem(n, G);
+        const size_t dyn = base_smem + (size_t)kTriWarps * 3 * a.stage_rows * sizeof(cdf);
         const void* fn = (const void*)tridiag_blocked_kernel;
         BSE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
         int per_sm = 0;
@@ -1339,7 +1369,8 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
             a.tc_update = tcu ? 1 : 0;
             BSE_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kTriThreads), args, dyn, st));
             note_launch();
-            if (tcu && s1 <= n - 2) BSE_TRY(launch_panel_update_tc(a.A, n, (int)s1, Vp, Wp, tcs, err, st, wait_polls));
+            if (tcu && s1 <= n - 2)
+                BSE_TRY(launch_panel_update_tc(a.A, n, (int)s1, a.resident_from, Vp, Wp, tcs, err, st, wait_polls));
         }
         if (ev1) BSE_CUDA(cudaEventRecord(ev1, st));
     }

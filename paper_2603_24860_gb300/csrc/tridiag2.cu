@@ -1,0 +1,789 @@
+// Two-stage reduction of a Hermitian block to a real tridiagonal T that keeps
+// e_0 fixed (sm_103a): the stage that feeds the eigenvector-free spectrum
+// (Eqs. oscillator, oscillatorA; levels from T, weights from the first
+// components of its eigenvectors).
+//
+// The start reflector H0 (which maps conj(U^T B) onto e_0) is applied to the
+// whole block first.  Then
+//
+//   stage 1  dense -> band of half-bandwidth 32.  Panel j holds the columns
+//            c0 = 32 j .. c0 + 31 and the rows r1 = c0 + 32 .. n - 1 below the
+//            band.  Its Householder QR (zlarfg reflectors on rows >= r1, so
+//            that e_0 stays fixed) gives Q = I - V T V^H (compact WY form, T by
+//            the forward column-wise recurrence) and leaves [R; 0] in the
+//            panel.  The trailing block A22 = A[r1:, r1:] becomes Q^H A22 Q =
+//            A22 - V W^H - W V^H with Y = A22 V T and W = Y - 1/2 V (T^H V^H Y):
+//            one pass of A22 through a GEMM for A22 V (double-float on the
+//            CUDA cores, split over K) and the rank-64 update on the tensor
+//            cores (her2k_tc.cu).  The trailing block is read twice per panel
+//            instead of once per reflection step.
+//   stage 2  band -> tridiagonal by bulge chasing.  Sweep i annihilates column
+//            i below the subdiagonal with a reflector on rows i+1 .. i+32 and
+//            chases the bulge down the band in windows of 32 rows: task t of
+//            sweep i reflects the first column of the block left by task t-1,
+//            applies the reflector to the rest of that block (left), to the
+//            32 x 32 diagonal block (both sides) and to the block below
+//            (right), which becomes the next bulge.  One CTA runs a sweep at a
+//            time; sweep i may run task t once sweep i - 1 has finished task
+//            t + 2 (their blocks no longer overlap).  Only the lower triangle
+//            of the band is read and written.
+//
+// Every reflector acts on rows >= 1, so Q e_0 = e_0.  The tridiagonal matrix
+// left in the band is complex Hermitian; a diagonal unitary scaling makes its
+// off-diagonal real and non-negative without changing the levels or the
+// magnitudes of the first eigenvector components: d_i = Re A[i,i],
+// e_i = |A[i+1,i]|.  All arithmetic is double-float (dfloat.h) on the FP32
+// pipe, the rank-64 update excepted (exact bf16 digit products).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "dfloat.h"
+#include "fp64_fast.h"
+#include "grid_sync.h"
+#include "internal.h"
+#include "reflector.h"
+
+namespace bse {
+
+namespace {
+
+constexpr int kB = 32;              // half-bandwidth of stage 1 = reflectors per panel
+constexpr int kT2 = 256;            // threads of most kernels here
+constexpr int kW2 = kT2 / 32;
+constexpr int kMaxKs = 8;           // K splits of the A22 V product
+constexpr int kQrMaxCta = 32;       // CTAs of the panel QR
+constexpr int kGramRows = 128;      // rows per CTA of the 32 x 32 Gram products
+constexpr int kSweepDone = 1 << 30;
+
+__device__ __forceinline__ cdf conjc(cdf a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ cdf negc(cdf a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ cdf onec() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+
+// raw double-float complex accumulator (s, lo per part), normalised at the end
+struct CAcc {
+    float sr, lr, si, li;
+    __device__ __forceinline__ void zero() { sr = lr = si = li = 0.f; }
+    // += a b
+    __device__ __forceinline__ void mac(cdf a, cdf b) {
+        df_acc(sr, lr, a.x, a.y, b.x, b.y);
+        df_acc(sr, lr, -a.z, -a.w, b.z, b.w);
+        df_acc(si, li, a.x, a.y, b.z, b.w);
+        df_acc(si, li, a.z, a.w, b.x, b.y);
+    }
+    // += conj(a) b
+    __device__ __forceinline__ void dot(cdf a, cdf b) {
+        df_acc(sr, lr, a.x, a.y, b.x, b.y);
+        df_acc(sr, lr, a.z, a.w, b.z, b.w);
+        df_acc(si, li, a.x, a.y, b.z, b.w);
+        df_acc(si, li, -a.z, -a.w, b.x, b.y);
+    }
+    __device__ __forceinline__ cdf get() const {
+        const float2 r = df_fin(sr, lr), i = df_fin(si, li);
+        return make_float4(r.x, r.y, i.x, i.y);
+    }
+};
+
+__device__ __forceinline__ float2 warp_sum_df(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    return v;
+}
+
+// the block in place from FP64 to double-float (16 bytes per element either way)
+__global__ void to_cdf_kernel(cdf* A, int64_t nn) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
+        const double2 z = reinterpret_cast<const double2*>(A)[k];
+        A[k] = cdf_from(z);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Start reflector H0 = I - beta v v^H (beta real): A <- H0 A H0 = A - v w^H - w v^H
+// with y = A v, mu = v^H y (real) and w = beta y - beta^2 mu / 2 v.
+// ---------------------------------------------------------------------------
+
+// y_i = (A v)_i = sum_r conj(A[r,i]) v_r (A Hermitian): one warp per column
+__global__ void h0_matvec_kernel(const cdf* __restrict__ A, int n, const double2* __restrict__ v0, cdf* y) {
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const cdf* col = A + (size_t)i * n;
+    CAcc acc;
+    acc.zero();
+    for (int r = lane; r < n; r += 32) acc.dot(__ldcg(col + r), cdf_from(v0[r]));
+    cdf s = cdf_warp_sum(acc.get());
+    if (lane == 0) y[i] = s;
+}
+
+// mu = v^H y, then v and w as double-float vectors (one block)
+__global__ void h0_vectors_kernel(const double2* __restrict__ v0, const double* __restrict__ beta0, const cdf* y,
+                                  int n, cdf* v, cdf* w) {
+    __shared__ float2 s_part[kW2];
+    __shared__ float2 s_c;
+    const int tid = threadIdx.x;
+    float s = 0.f, lo = 0.f;
+    for (int r = tid; r < n; r += blockDim.x) {
+        const cdf a = cdf_from(v0[r]), b = y[r];
+        df_acc(s, lo, a.x, a.y, b.x, b.y);   // Re(conj(a) b)
+        df_acc(s, lo, a.z, a.w, b.z, b.w);
+    }
+    float2 t = warp_sum_df(df_fin(s, lo));
+    if ((tid & 31) == 0) s_part[tid >> 5] = t;
+    __syncthreads();
+    if (tid == 0) {
+        float2 mu = s_part[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mu = df_add(mu, s_part[k]);
+        const float2 b = df_from(*beta0);
+        s_c = df_mul(df_mul(df_mul(b, b), mu), make_float2(0.5f, 0.f));   // beta^2 mu / 2
+    }
+    __syncthreads();
+    const float2 b = df_from(*beta0), c = s_c;
+    for (int r = tid; r < n; r += blockDim.x) {
+        const cdf a = cdf_from(v0[r]), yy = y[r];
+        v[r] = a;
+        const float2 wr = df_add(df_mul(b, make_float2(yy.x, yy.y)), df_neg(df_mul(c, make_float2(a.x, a.y))));
+        const float2 wi = df_add(df_mul(b, make_float2(yy.z, yy.w)), df_neg(df_mul(c, make_float2(a.z, a.w))));
+        w[r] = make_float4(wr.x, wr.y, wi.x, wi.y);
+    }
+}
+
+// A[r,i] -= v_r conj(w_i) + w_r conj(v_i) on the whole block
+__global__ void rank2_all_kernel(cdf* A, int n, const cdf* __restrict__ v, const cdf* __restrict__ w) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / n), r = (int)(k - (int64_t)i * n);
+        A[k] = cdf_rank2(A[k], v[r], w[r], w[i], v[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Panel QR (cooperative; CTA b holds the panel rows rho in [b ch, (b+1) ch),
+// one thread per row, in shared memory).  Per reflector l: the partial squared
+// norms of column l below row l and its pivot; grid barrier; every CTA forms
+// the reflector (zlarfg, v_l = 1) from the sums, scales its rows of v and adds
+// its part of w = v^H P for the columns right of l; grid barrier; every CTA
+// sums w and applies P <- P - conj(tau) v w to its rows.
+// ---------------------------------------------------------------------------
+struct PanelArgs {
+    cdf* A;            // n x n, column-major, double-float
+    int n, c0, r1, m;  // panel columns c0 .. c0 + 31, rows r1 .. r1 + m - 1 (r1 = c0 + 32)
+    int nref;          // reflectors (min(32, m - 1))
+    cdf* V;            // [32][n] reflector l at V[l n + r], zero above its row r1 + l
+    cdf* tau;          // [32]
+    float2* part;      // [G] partial squared norms
+    cdf* piv;          // [32] pivots (entry l of column l after reflectors < l)
+    cdf* wpart;        // [G][64] partial w (columns > l) and partial V^H v_l (entries 32 + k, k < l)
+    cdf* T;            // [32][32] the T factor of Q = I - V T V^H (written by CTA 0)
+    unsigned* bar;     // zero on entry
+    int* err;
+    long spin;
+};
+
+__global__ void __launch_bounds__(kT2, 1) panel_qr_kernel(PanelArgs a) {
+    extern __shared__ __align__(16) cdf s_qr[];   // P rows: [32][ch], then V rows: [32][ch]
+    __shared__ float2 s_red[kW2];
+    __shared__ cdf s_w[2 * kB];
+    __shared__ cdf s_T[kB][kB + 1];   // CTA 0: the T factor, column by column
+    __shared__ cdf s_tau, s_inv;
+    __shared__ float2 s_beta;
+    __shared__ int s_flag;
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ch = (a.m + G - 1) / G;
+    const int rho0 = b * ch, nown = max(0, min(a.m, rho0 + ch) - rho0);
+    cdf* P = s_qr;                       // P[l * ch + t]
+    cdf* Vs = s_qr + (size_t)kB * ch;    // Vs[l * ch + t]
+    const int n = a.n;
+    const int rho = rho0 + tid;          // this thread's panel row (tid < nown)
+    const bool mine = tid < nown;
+    for (int l = 0; l < kB; ++l) {
+        const cdf x = mine ? __ldcg(a.A + (size_t)(a.c0 + l) * n + a.r1 + rho) : cdf_zero();
+        if (tid < ch) {
+            P[l * ch + tid] = x;
+            Vs[l * ch + tid] = cdf_zero();
+        }
+    }
+    __syncthreads();
+    unsigned nbar = 0;
+    for (int l = 0; l < a.nref; ++l) {
+        // squared norm of column l below row l, and its pivot
+        float s = 0.f, lo = 0.f;
+        if (mine && rho > l) {
+            const cdf x = P[l * ch + tid];
+            df_acc(s, lo, x.x, x.y, x.x, x.y);
+            df_acc(s, lo, x.z, x.w, x.z, x.w);
+        }
+        if (mine && rho == l) a.piv[l] = P[l * ch + tid];
+        float2 t = warp_sum_df(df_fin(s, lo));
+        if (lane == 0) s_red[wid] = t;
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < kW2; ++k) t = df_add(t, s_red[k]);
+            a.part[b] = t;
+        }
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
+        // the reflector from the sums (warp 0), v on own rows, partial w = v^H P
+        if (wid == 0) {
+            float2 sg = make_float2(0.f, 0.f);
+            for (int k = lane; k < G; k += 32) sg = df_add(sg, __ldcg(a.part + k));
+            sg = warp_sum_df(sg);
+            if (lane == 0) {
+                cdf tau, inv;
+                float2 beta;
+                reflector(__ldcg(a.piv + l), sg, tau, inv, beta);
+                s_tau = tau;
+                s_inv = inv;
+                s_beta = beta;
+                if (b == 0) a.tau[l] = tau;
+            }
+        }
+        __syncthreads();
+        const cdf inv = s_inv;
+        if (mine && rho >= l) {
+            const cdf x = P[l * ch + tid];
+            const cdf v = rho == l ? onec() : cdf_mul(x, inv);
+            Vs[l * ch + tid] = v;
+            P[l * ch + tid] = rho == l ? make_float4(s_beta.x, s_beta.y, 0.f, 0.f) : cdf_zero();
+        }
+        __syncthreads();
+        // a warp per task, lanes over own rows: w_c = v^H P[:, c] (c > l) and
+        // g_k = v_k^H v (k < l, for the T factor)
+        for (int c = wid; c < kB - 1; c += kW2) {
+            const int col = c < l ? c : c + 1;   // tasks: g_0 .. g_{l-1}, then w_{l+1} .. w_31
+            const bool isg = c < l;
+            CAcc acc;
+            acc.zero();
+            for (int u = lane; u < nown; u += 32)
+                if (rho0 + u >= l) {
+                    if (isg)
+                        acc.dot(Vs[col * ch + u], Vs[l * ch + u]);
+                    else
+                        acc.dot(Vs[l * ch + u], P[col * ch + u]);
+                }
+            const cdf sum = cdf_warp_sum(acc.get());
+            if (lane == 0) a.wpart[(size_t)b * 2 * kB + (isg ? kB + col : col)] = sum;
+        }
+        if (!grid_barrier(a.bar, (++nbar) * G, a.err, &s_flag, a.spin)) return;
+        // sums over the CTAs (four threads per entry); P <- P - conj(tau) v w on own rows >= l,
+        // columns > l; CTA 0: column l of T, T[0:l, l] = -tau_l T[0:l, 0:l] g
+        {
+            const int ent = tid >> 2, k0 = tid & 3;
+            const bool need = ent < kB ? ent > l : ent - kB < l;
+            cdf sum = cdf_zero();
+            if (need)
+#pragma unroll 4
+                for (int k = k0; k < G; k += 4) sum = cdf_add(sum, __ldcg(a.wpart + (size_t)k * 2 * kB + ent));
+            sum = cdf_add(sum, cdf_shfl_xor(sum, 1));
+            sum = cdf_add(sum, cdf_shfl_xor(sum, 2));
+            if (k0 == 0 && need) s_w[ent] = sum;
+        }
+        __syncthreads();
+        if (b == 0 && tid <= l) {
+            if (tid == l) {
+                s_T[l][l] = s_tau;
+            } else {
+                CAcc acc;
+                acc.zero();
+                for (int k = tid; k < l; ++k) acc.mac(s_T[tid][k], s_w[kB + k]);
+                s_T[tid][l] = cdf_mul(negc(s_tau), acc.get());
+            }
+        }
+        if (mine && rho >= l) {
+            const cdf f = cdf_mul(conjc(s_tau), Vs[l * ch + tid]);   // conj(tau) v_rho
+            for (int c = l + 1; c < kB; ++c) P[c * ch + tid] = cdf_fma(P[c * ch + tid], negc(f), s_w[c]);
+        }
+        __syncthreads();
+    }
+    // the panel ([R; 0]), the reflectors and T back to global memory
+    if (b == 0)
+        for (int e = tid; e < kB * kB; e += kT2) {
+            const int r = e >> 5, c = e & 31;
+            a.T[e] = r <= c && c < a.nref ? s_T[r][c] : cdf_zero();
+        }
+    if (mine)
+        for (int l = 0; l < kB; ++l) {
+            a.A[(size_t)(a.c0 + l) * n + a.r1 + rho] = P[l * ch + tid];
+            a.V[(size_t)l * n + a.r1 + rho] = Vs[l * ch + tid];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// 32 x 32 Gram products X^H Y over rows r1 .. r1 + m - 1 of two [32][n] arrays:
+// part[blk][i][j] = sum over the CTA's rows of conj(X[i][r]) Y[j][r]
+// (1024 threads, thread (i, j); rows staged in shared memory 32 at a time).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024, 1) gram32_kernel(const cdf* __restrict__ X, const cdf* __restrict__ Y, int n,
+                                                         int r1, int m, cdf* part) {
+    __shared__ cdf xs[kB][33], ys[kB][33];
+    const int tid = threadIdx.x, i = tid >> 5, j = tid & 31;
+    const int q0 = blockIdx.x * kGramRows, q1 = min(m, q0 + kGramRows);
+    CAcc acc;
+    acc.zero();
+    for (int q = q0; q < q1; q += 32) {
+        const int cnt = min(32, q1 - q);
+        // thread (i, j): row q + j of column i
+        xs[i][j] = j < cnt ? __ldcg(X + (size_t)i * n + r1 + q + j) : cdf_zero();
+        ys[i][j] = j < cnt ? __ldcg(Y + (size_t)i * n + r1 + q + j) : cdf_zero();
+        __syncthreads();
+        for (int u = 0; u < cnt; ++u) acc.dot(xs[i][u], ys[j][u]);
+        __syncthreads();
+    }
+    part[(size_t)blockIdx.x * kB * kB + i * kB + j] = acc.get();
+}
+
+// ---------------------------------------------------------------------------
+// Z = A22 V over rows and columns r1 .. n-1 of A (V: [32][n]), split over K:
+// CTA (row tile rt, split ks) sums columns [k_lo, k_hi) of its 64 rows into
+// zpart[ks][rho][l].  A tile 64 x 32 and V tile 32 x 32 staged in shared
+// memory per step of 32 columns; thread (ty = tid & 31, tx = tid >> 5) holds
+// rows 2 ty, 2 ty + 1 and columns 4 tx .. 4 tx + 3 (eight accumulators).
+// ---------------------------------------------------------------------------
+constexpr int kZR = 64;   // rows per CTA
+__global__ void __launch_bounds__(kT2, 2) zgemm_kernel(const cdf* __restrict__ A, int n, int r1, int m,
+                                                       const cdf* __restrict__ V, int kchunk, cdf* zpart) {
+    __shared__ cdf As[32][kZR];       // [k][row]
+    __shared__ cdf Vsm[32][kB];       // [k][l]
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    const int row0 = blockIdx.x * kZR, ks = blockIdx.y;
+    const int k_lo = ks * kchunk, k_hi = min(m, k_lo + kchunk);
+    CAcc acc[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v].zero();
+    for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
+        const int kc = min(32, k_hi - k0);
+        // A tile: 32 columns x 64 rows (thread: row tid & 63, columns tid >> 6 + 4 j)
+        for (int e = tid; e < 32 * kZR; e += kT2) {
+            const int rr = e & (kZR - 1), kk = e >> 6;
+            As[kk][rr] = kk < kc && row0 + rr < m ? __ldcg(A + (size_t)(r1 + k0 + kk) * n + r1 + row0 + rr) : cdf_zero();
+        }
+        for (int e = tid; e < 32 * kB; e += kT2) {
+            const int kk = e & 31, l = e >> 5;
+            Vsm[kk][l] = kk < kc ? __ldcg(V + (size_t)l * n + r1 + k0 + kk) : cdf_zero();
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kc; ++kk) {
+            const cdf a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const cdf bv = Vsm[kk][4 * tx + v];
+                acc[0][v].mac(a0, bv);
+                acc[1][v].mac(a1, bv);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int rho = row0 + 2 * ty + u;
+        if (rho < m)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) zpart[((size_t)ks * m + rho) * kB + 4 * tx + v] = acc[u][v].get();
+    }
+}
+
+// Y = Z T (Z summed over the K splits), rows r1 .. n-1, into Y[32][n] (a warp per row,
+// lane = column of Y)
+__global__ void ysum_kernel(const cdf* __restrict__ zpart, int nks, int m, const cdf* __restrict__ T, int n, int r1,
+                            cdf* Y) {
+    __shared__ cdf Ts[kB][kB + 1];
+    for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) Ts[e >> 5][e & 31] = T[e];
+    __syncthreads();
+    const int rho = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (rho >= m) return;
+    cdf z = cdf_zero();
+    for (int k = 0; k < nks; ++k) z = cdf_add(z, zpart[((size_t)k * m + rho) * kB + lane]);
+    CAcc acc;
+    acc.zero();
+    for (int l = 0; l < kB; ++l) {
+        const cdf zl = make_float4(__shfl_sync(0xffffffffu, z.x, l), __shfl_sync(0xffffffffu, z.y, l),
+                                   __shfl_sync(0xffffffffu, z.z, l), __shfl_sync(0xffffffffu, z.w, l));
+        if (l <= lane) acc.mac(zl, Ts[l][lane]);
+    }
+    Y[(size_t)lane * n + r1 + rho] = acc.get();
+}
+
+// M = T^H S with S = V^H Y summed from the parts (1024 threads, thread (i, j))
+__global__ void __launch_bounds__(1024, 1) mfactor_kernel(const cdf* __restrict__ spart, int ng,
+                                                          const cdf* __restrict__ T, cdf* M) {
+    __shared__ cdf S[kB][kB + 1], Ts[kB][kB + 1];
+    const int tid = threadIdx.x, i = tid >> 5, j = tid & 31;
+    cdf s = cdf_zero();
+    for (int k = 0; k < ng; ++k) s = cdf_add(s, spart[(size_t)k * kB * kB + i * kB + j]);
+    S[i][j] = s;
+    Ts[i][j] = T[i * kB + j];
+    __syncthreads();
+    CAcc acc;
+    acc.zero();
+    for (int k = 0; k <= i; ++k) acc.dot(Ts[k][i], S[k][j]);   // conj(T[k][i]) S[k][j]
+    M[i * kB + j] = acc.get();
+}
+
+// W = Y - 1/2 V M, in place over Y (a warp per row, lane = column)
+__global__ void wfinal_kernel(const cdf* __restrict__ V, const cdf* __restrict__ M, int n, int r1, int m, cdf* W) {
+    __shared__ cdf Ms[kB][kB + 1];
+    for (int e = threadIdx.x; e < kB * kB; e += blockDim.x) Ms[e >> 5][e & 31] = M[e];
+    __syncthreads();
+    const int rho = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (rho >= m) return;
+    const cdf v = __ldcg(V + (size_t)lane * n + r1 + rho);
+    CAcc acc;
+    acc.zero();
+    for (int k = 0; k < kB; ++k) {
+        const cdf vk = make_float4(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k),
+                                   __shfl_sync(0xffffffffu, v.z, k), __shfl_sync(0xffffffffu, v.w, k));
+        acc.mac(vk, Ms[k][lane]);
+    }
+    cdf* w = W + (size_t)lane * n + r1 + rho;
+    *w = cdf_fma(*w, make_float4(-0.5f, 0.f, 0.f, 0.f), acc.get());
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: bulge chasing (cooperative; sweeps i = blockIdx.x, blockIdx.x + G, ...).
+// Task t of sweep i has the window rows and columns [p, q), p = i + 1 + 32 t,
+// q = min(p + 32, n); it reflects column cc = (t == 0 ? i : p - 32) on rows
+// [p, q) (rows below p zeroed), applies the reflector to the block left of the
+// window ([p, q) x [p - 32, p), t >= 1, kept in shared memory from task t - 1),
+// to the window's diagonal block (both sides) and to the block below
+// ([q, q + 32) x [p, q), right), which becomes the next task's left block.
+// Shared memory: three 32 x 33 blocks (D, and the left and below blocks, whose
+// roles swap from task to task) and four vectors.
+// ---------------------------------------------------------------------------
+struct BulgeArgs {
+    cdf* A;
+    int n;
+    int* prog;   // [n] tasks finished by each sweep (kSweepDone once it has ended), zero on entry
+    int* err;
+    long spin;
+};
+
+constexpr int kBlk = kB * (kB + 1);
+constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 4 * kB);
+
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+// sum over the 8 lanes of a group (lanes 8 g .. 8 g + 7)
+__device__ __forceinline__ cdf group8_sum(cdf v) {
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) v = cdf_add(v, cdf_shfl_xor(v, o));
+    return v;
+}
+
+// A task is split in two parts.  R_t: the reflector of the task's column (for t >= 1
+// the first column of the block below of task t - 1, final once that task's right
+// update is done), its entry beta written to A, and the sweep's count raised to t + 1:
+// this is all that sweep i + 1 needs from task t (their regions share only that entry).
+// L_t: once sweep i - 1 has raised its count to t + 3 (its R_{t+2} done, hence its L_{t+1}),
+// the lower triangle of the window's block and the block below are loaded; thread
+// (r, k) = (tid / 8, tid % 8) forms its part over columns 4k .. 4k + 3 of y_r = (D v)_r,
+// z_r = (B v)_r and s_r = (v^H L)_r, summed over the 8 threads of a row; warp 0 forms
+// mu = v^H y and w = tau y - |tau|^2 mu / 2 v; then D -= v w^H + w v^H (lower triangle),
+// B -= tau z v^H, L -= conj(tau) v s^H (columns >= 1), and the blocks are written back.
+// Order within the sweep: R_0, L_0, R_1, L_1, ...  Every warp forms the reflector
+// (lane l holds v_l), so no synchronisation separates it from the products.
+__global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
+    extern __shared__ __align__(16) cdf s_bg[];
+    __shared__ int s_ok;
+    cdf* D = s_bg;                     // D[r * 33 + c], lower triangle (r >= c)
+    cdf* Lb = s_bg + kBlk;             // left block: Lb[r * 33 + c], rows p + r, columns p - 32 + c
+    cdf* Bb = s_bg + 2 * kBlk;         // block below: Bb[r * 33 + c], rows q + r, columns p + c
+    cdf* vs = s_bg + 3 * kBlk;         // v
+    cdf* ys = vs + kB;                 // y, then w
+    cdf* zs = ys + kB;                 // tau z
+    cdf* ss = zs + kB;                 // s; the first reflected column before
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int pr = tid >> 3, pk = tid & 7;   // product thread: row pr, columns 4 pk .. 4 pk + 3
+    const int n = a.n;
+    cdf* A = a.A;
+    auto at = [&](int r, int c) -> cdf* { return A + (size_t)c * n + r; };
+    constexpr int S = kB + 1;
+    // tid 0 waits until sweep i - 1 has raised its count to `need`; false if the wait gave up
+    auto wait_prev = [&](int i, int need) {
+        if (tid == 0) {
+            bool ok = true;
+            if (i > 0) {
+                ok = false;
+                for (long it = 0; it < a.spin; ++it) {
+                    if (ld_acquire_gpu((const unsigned*)(a.prog + i - 1)) >= (unsigned)need) {
+                        ok = true;
+                        break;
+                    }
+                    if ((it & 63) == 63 && *(volatile int*)a.err) break;
+                    if (it > 4096) __nanosleep(32);
+                }
+                if (!ok) atomicExch(a.err, 1);
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    };
+    // the reflector of column x (lane l holds x_l, l < len), in every warp
+    auto form = [&](cdf xl, int len, cdf& vl, cdf& tau, float2& beta) {
+        float sg = 0.f, lo = 0.f;
+        if (lane >= 1 && lane < len) {
+            df_acc(sg, lo, xl.x, xl.y, xl.x, xl.y);
+            df_acc(sg, lo, xl.z, xl.w, xl.z, xl.w);
+        }
+        const float2 sigma = warp_sum_df(df_fin(sg, lo));
+        cdf inv;
+        reflector(shfl_cdf(xl, 0), sigma, tau, inv, beta);
+        vl = lane == 0 ? onec() : (lane < len ? cdf_mul(xl, inv) : cdf_zero());
+    };
+    for (int i = blockIdx.x; i < n - 2; i += gridDim.x) {
+        cdf vl, tau;
+        float2 beta;
+        // R_0: column i on rows i+1 .. i+32, final once sweep i - 1 has done R_1
+        {
+            const int p = i + 1, len = min(p + kB, n) - p;
+            if (!wait_prev(i, 2)) return;
+            const cdf xl = lane < len ? __ldcg(at(p + lane, i)) : cdf_zero();
+            form(xl, len, vl, tau, beta);
+            if (wid == 0) {
+                vs[lane] = vl;
+                if (lane < len) *at(p + lane, i) = lane == 0 ? make_float4(beta.x, beta.y, 0.f, 0.f) : cdf_zero();
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicExch(a.prog + i, 1);
+        }
+        for (int t = 0;; ++t) {
+            const int p = i + 1 + kB * t;
+            const int q = min(p + kB, n), len = q - p;
+            const int qb = min(q + kB, n), lenb = qb - q;
+            const bool next = q <= n - 2;
+            // L_t
+            if (!wait_prev(i, t + 3)) return;
+            for (int e = tid; e < kB * kB; e += kT2) {
+                const int r = e & 31, c = e >> 5;
+                if (r >= c && r < len) D[r * S + c] = __ldcg(at(p + r, p + c));
+                if (r < lenb && c < len) Bb[r * S + c] = __ldcg(at(q + r, p + c));
+            }
+            __syncthreads();
+            CAcc ay, az, as;
+            ay.zero();
+            az.zero();
+            as.zero();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * pk + u;
+                const cdf vc = shfl_cdf(vl, c);
+                if (pr < len && c < len) ay.mac(pr >= c ? D[pr * S + c] : conjc(D[c * S + pr]), vc);
+                if (pr < lenb && c < len) az.mac(Bb[pr * S + c], vc);
+                if (t > 0 && c < len) as.dot(vc, Lb[c * S + pr]);   // column pr of L, rows c
+            }
+            const cdf yr = group8_sum(ay.get()), zr = group8_sum(az.get()), sr = group8_sum(as.get());
+            if (pk == 0) {
+                ys[pr] = yr;
+                zs[pr] = cdf_mul(tau, zr);
+                ss[pr] = sr;
+            }
+            __syncthreads();
+            if (wid == 0) {   // mu = Re v^H y, w = tau y - |tau|^2 mu / 2 v
+                float m0 = 0.f, m1 = 0.f;
+                const cdf yy = ys[lane];
+                if (lane < len) {
+                    df_acc(m0, m1, vl.x, vl.y, yy.x, yy.y);
+                    df_acc(m0, m1, vl.z, vl.w, yy.z, yy.w);
+                }
+                const float2 mu = warp_sum_df(df_fin(m0, m1));
+                float t0 = 0.f, t1 = 0.f;
+                df_acc(t0, t1, tau.x, tau.y, tau.x, tau.y);
+                df_acc(t0, t1, tau.z, tau.w, tau.z, tau.w);
+                const float2 cf = df_mul(df_mul(df_fin(t0, t1), mu), make_float2(-0.5f, 0.f));
+                __syncwarp();
+                ys[lane] = lane < len ? cdf_fma(cdf_mul(tau, yy), make_float4(cf.x, cf.y, 0.f, 0.f), vl) : cdf_zero();
+            }
+            __syncthreads();
+            const cdf mct = negc(conjc(tau));
+            for (int e = tid; e < kB * kB; e += kT2) {
+                const int r = e & 31, c = e >> 5;
+                if (c <= r && r < len) D[r * S + c] = cdf_rank2(D[r * S + c], vs[r], ys[r], ys[c], vs[c]);
+                if (r < lenb && c < len) Bb[r * S + c] = cdf_fma(Bb[r * S + c], negc(zs[r]), conjc(vs[c]));
+                if (t > 0 && r < len && c >= 1) Lb[r * S + c] = cdf_fma(Lb[r * S + c], cdf_mul(mct, vs[r]), ss[c]);
+            }
+            __syncthreads();
+            // write back: D (lower), the left block (its column 0 went out with R_t), the block
+            // below when no task follows
+            for (int e = tid; e < kB * kB; e += kT2) {
+                const int r = e & 31, c = e >> 5;
+                if (c <= r && r < len) *at(p + r, p + c) = D[r * S + c];
+                if (t > 0 && r < len && c >= 1) *at(p + r, p - kB + c) = Lb[r * S + c];
+                if (!next && r < lenb && c < len) *at(q + r, p + c) = Bb[r * S + c];
+            }
+            if (!next) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) atomicExch(a.prog + i, kSweepDone);
+                break;
+            }
+            // R_{t+1}: the first column of the block below (rows q .. qb - 1)
+            form(Bb[lane * S], lenb, vl, tau, beta);
+            __syncthreads();   // every warp has read column 0 of the block below
+            if (wid == 0) {
+                vs[lane] = vl;
+                const cdf xo = lane == 0 ? make_float4(beta.x, beta.y, 0.f, 0.f) : cdf_zero();
+                Bb[lane * S] = xo;
+                if (lane < lenb) *at(q + lane, p) = xo;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicExch(a.prog + i, t + 2);
+            cdf* tmp = Lb;   // the block below becomes the next task's left block
+            Lb = Bb;
+            Bb = tmp;
+        }
+        __syncthreads();
+    }
+}
+
+// d_i = Re A[i,i], e_i = |A[i+1,i]| (FP64)
+__global__ void band_extract_kernel(const cdf* __restrict__ A, int n, double* d, double* e) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const cdf a = __ldcg(A + (size_t)i * n + i);
+    d[i] = (double)a.x + (double)a.y;
+    if (i + 1 < n) {
+        const cdf b = __ldcg(A + (size_t)i * n + i + 1);
+        const double re = (double)b.x + (double)b.y, im = (double)b.z + (double)b.w;
+        e[i] = sqrt(re * re + im * im);
+    } else {
+        e[i] = 0.0;
+    }
+}
+
+}  // namespace
+
+size_t tridiag2_bytes(int64_t n) {
+    const int64_t ng = (n + kGramRows - 1) / kGramRows;
+    // H0 vectors (3 n); A22 V parts (kMaxKs n 32); Gram parts (ng 1024); T, M (2 x 1024); tau, pivots
+    // (64); partial norms (256 float2); partial w and g (256 x 64); progress (n ints); barrier; alignment
+    return sizeof(cdf) * (size_t)(3 * n + kMaxKs * n * kB + ng * kB * kB + 2 * kB * kB + 2 * kB + 512 * kB) +
+           sizeof(float2) * 256 + sizeof(int) * (size_t)n + 64 + 16 * 256;
+}
+
+int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0, double* d, double* e, cdf* V, cdf* W,
+                    void* tc_scratch, void* scratch, int* err, cudaStream_t st, long wait_polls) {
+    const int n = (int)n64;
+    char* p = (char*)scratch;
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return (void*)q;
+    };
+    const int64_t ngmax = (n + kGramRows - 1) / kGramRows;
+    cdf* hy = (cdf*)take(sizeof(cdf) * n);
+    cdf* hv = (cdf*)take(sizeof(cdf) * n);
+    cdf* hw = (cdf*)take(sizeof(cdf) * n);
+    cdf* zpart = (cdf*)take(sizeof(cdf) * (size_t)kMaxKs * n * kB);
+    cdf* spart = (cdf*)take(sizeof(cdf) * (size_t)ngmax * kB * kB);
+    cdf* T = (cdf*)take(sizeof(cdf) * kB * kB);
+    cdf* M = (cdf*)take(sizeof(cdf) * kB * kB);
+    cdf* tau = (cdf*)take(sizeof(cdf) * kB);
+    cdf* piv = (cdf*)take(sizeof(cdf) * kB);
+    float2* part = (float2*)take(sizeof(float2) * 256);
+    cdf* wpart = (cdf*)take(sizeof(cdf) * 256 * 2 * kB);
+    int* prog = (int*)take(sizeof(int) * n);
+    unsigned* bar = (unsigned*)take(sizeof(unsigned));
+    const long spin = wait_limit(wait_polls, kGridSpinLimit);
+
+    int dev = 0, sms = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nn = (int64_t)n * n;
+    to_cdf_kernel<<<sms * 4, kT2, 0, st>>>(A, nn);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    // start reflector
+    h0_matvec_kernel<<<(unsigned)((n + kW2 - 1) / kW2), kT2, 0, st>>>(A, n, v0, hy);
+    note_launch();
+    h0_vectors_kernel<<<1, kT2, 0, st>>>(v0, beta0, hy, n, hv, hw);
+    note_launch();
+    rank2_all_kernel<<<sms * 4, kT2, 0, st>>>(A, n, hv, hw);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+
+    // stage 1: panels of 32 columns
+    for (int c0 = 0;; c0 += kB) {
+        const int r1 = c0 + kB, m = n - r1;
+        if (m < 2) break;
+        const int nref = std::min(kB, m - 1);
+        // panel QR on Gq co-resident CTAs of one row each per thread
+        int Gq = std::max((m + 159) / 160, std::min(kQrMaxCta, (m + 31) / 32));
+        Gq = std::min(Gq, sms);
+        const int ch = (m + Gq - 1) / Gq;
+        const size_t qsm = sizeof(cdf) * 2 * kB * (size_t)ch;
+        if (ch > kT2) return fail(BSE_EUNSUPPORTED, "two-stage reduction: n = %d too large for the panel QR", n);
+        BSE_CUDA(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+        BSE_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+        PanelArgs pa;
+        pa.A = A;
+        pa.n = n;
+        pa.c0 = c0;
+        pa.r1 = r1;
+        pa.m = m;
+        pa.nref = nref;
+        pa.V = V;
+        pa.tau = tau;
+        pa.part = part;
+        pa.piv = piv;
+        pa.wpart = wpart;
+        pa.T = T;
+        pa.bar = bar;
+        pa.err = err;
+        pa.spin = spin;
+        void* qargs[] = {&pa};
+        BSE_CUDA(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(Gq), dim3(kT2), qargs, qsm, st));
+        note_launch();
+        const int ng = (m + kGramRows - 1) / kGramRows;
+        // Z = A22 V split over K, Y = Z T
+        const int rt = (m + kZR - 1) / kZR;
+        int ks = std::max(1, std::min(kMaxKs, (2 * sms + rt - 1) / rt));
+        ks = std::min(ks, (m + 31) / 32);
+        const int kchunk = (m + ks - 1) / ks;
+        zgemm_kernel<<<dim3(rt, ks), kT2, 0, st>>>(A, n, r1, m, V, kchunk, zpart);
+        note_launch();
+        ysum_kernel<<<(unsigned)((m + kW2 - 1) / kW2), kT2, 0, st>>>(zpart, ks, m, T, n, r1, W);
+        note_launch();
+        // W = Y - 1/2 V T^H V^H Y
+        gram32_kernel<<<ng, 1024, 0, st>>>(V, W, n, r1, m, spart);
+        note_launch();
+        mfactor_kernel<<<1, 1024, 0, st>>>(spart, ng, T, M);
+        note_launch();
+        wfinal_kernel<<<(unsigned)((m + kW2 - 1) / kW2), kT2, 0, st>>>(V, M, n, r1, m, W);
+        note_launch();
+        BSE_CUDA(cudaGetLastError());
+        // A22 -= V W^H + W V^H on the tensor cores
+        BSE_TRY(launch_panel_update_tc(A, n, r1, 0, V, W, tc_scratch, err, st, wait_polls));
+    }
+
+    // stage 2: bulge chasing
+    if (n > 2) {
+        BSE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * n, st));
+        BSE_CUDA(cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBulgeSmem));
+        int per_sm = 0;
+        BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulge_kernel, kT2, kBulgeSmem));
+        if (per_sm < 1) return fail(BSE_EUNSUPPORTED, "bulge-chasing kernel cannot be resident");
+        const int G = std::min(sms, n - 2);
+        BulgeArgs ba;
+        ba.A = A;
+        ba.n = n;
+        ba.prog = prog;
+        ba.err = err;
+        ba.spin = spin;
+        void* bargs[] = {&ba};
+        BSE_CUDA(cudaLaunchCooperativeKernel((const void*)bulge_kernel, dim3(G), dim3(kT2), bargs, kBulgeSmem, st));
+        note_launch();
+    }
+    band_extract_kernel<<<(unsigned)((n + kT2 - 1) / kT2), kT2, 0, st>>>(A, n, d, e);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
+}  // namespace bse

@@ -478,7 +478,8 @@ def test_solver_choice_and_agreement(gpu, name):
         h1 = bse.partner_block(ctx, mu)
         out = {}
         for solver in (bse.BSE_SOLVER_AUTO, bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG,
-                       bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+                       bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF,
+                       bse.BSE_SOLVER_TRIDIAG_TWOSTAGE):
             bse.bse_set_solver(ctx, solver)
             out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
             used = bse.bse_get_stats(ctx)["solver"]
@@ -486,7 +487,8 @@ def test_solver_choice_and_agreement(gpu, name):
         bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
         # the reduction in shared memory and the blocked (panel) reduction with its tensor-core
         # and its double-float panel update, all against zheevd
-        for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+        for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF,
+                      bse.BSE_SOLVER_TRIDIAG_TWOSTAGE):
             (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[other]
             assert np.abs(om - om2).max() <= TOL
             for cl in _clusters(om):

@@ -115,13 +115,16 @@ def test_partner_solvers_agree(si12):
     bse, torch, ctx, t, mu, h64, h32, cols, d, *_ = si12
     omega = torch.tensor(d["omega"], device="cuda")
     out = {}
-    for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+    kind = {bse.BSE_SOLVER_TRIDIAG_BLOCKED: 1, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF: 2,
+            bse.BSE_SOLVER_TRIDIAG_TWOSTAGE: 3}
+    others = tuple(kind)
+    for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG) + others:
         bse.bse_set_solver(ctx, solver)
         out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h64, omega, d["eta"])]
-        if solver != bse.BSE_SOLVER_DENSE:   # the panel-end update on the tensor cores by default
-            assert bse.bse_get_stats(ctx)["reduce_kind"] == (1 if solver == bse.BSE_SOLVER_TRIDIAG else 2)
+        if solver in kind:
+            assert bse.bse_get_stats(ctx)["reduce_kind"] == kind[solver]
     bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
-    for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+    for other in (bse.BSE_SOLVER_TRIDIAG,) + others:
         (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[other]
         assert np.abs(om - om2).max() <= 1e-10 * np.abs(om).max()
         assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()

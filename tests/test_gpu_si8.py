@@ -138,15 +138,18 @@ def test_partner_solvers_agree(built):
     out = {}
     kinds = {}
     for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED,
-                   bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+                   bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF, bse.BSE_SOLVER_TRIDIAG_TWOSTAGE):
         bse.bse_set_solver(ctx, solver)
         out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h1, omega, d["eta"])]
         kinds[solver] = bse.bse_get_stats(ctx)["reduce_kind"]
     bse.bse_set_solver(ctx, bse.BSE_SOLVER_AUTO)
     assert kinds[bse.BSE_SOLVER_TRIDIAG_BLOCKED] == 1 and kinds[bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF] == 2
-    # the reduction in shared memory, and the blocked one (26 panels of 32 reflectors) with the
-    # panel-end update from exact digit GEMMs on the tensor cores and in double-float
-    for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF):
+    assert kinds[bse.BSE_SOLVER_TRIDIAG_TWOSTAGE] == 3
+    # the reduction in shared memory, the blocked one (26 panels of 32 reflectors) with the
+    # panel-end update from exact digit GEMMs on the tensor cores and in double-float, and the
+    # two-stage one (band of half-bandwidth 32, then bulge chasing)
+    for other in (bse.BSE_SOLVER_TRIDIAG, bse.BSE_SOLVER_TRIDIAG_BLOCKED, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF,
+                  bse.BSE_SOLVER_TRIDIAG_TWOSTAGE):
         (om, osc, im), (om2, osc2, im2) = out[bse.BSE_SOLVER_DENSE], out[other]
         assert np.abs(om - om2).max() <= TOL * np.abs(om).max()
         assert np.abs(osc - osc2).max() <= 1e-9 * osc.sum()
