@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbse_gb300.so")
-SOURCES = ["host_tables.cpp", "kernels.cu", "direct.cu", "direct_tc.cu", "tridiag.cu", "tridiag2.cu", "her2k_tc.cu", "rotate.cu", "loss.cu", "lanczos.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["host_tables.cpp", "kernels.cu", "direct.cu", "direct_tc.cu", "tridiag.cu", "tridiag2.cu", "zgemm_tc.cu", "her2k_tc.cu", "rotate.cu", "loss.cu", "lanczos.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

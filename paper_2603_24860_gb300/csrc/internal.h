@@ -326,6 +326,12 @@ size_t panel_update_tc_bytes(int64_t n);
 // rewritten in double-float in place) to d, e; V, W [32][n] and tc_scratch as for the panel
 // update, scratch of tridiag2_bytes(n)
 size_t tridiag2_bytes(int64_t n);
+// zgemm_tc.cu: Z = A22 V (rows and columns r1.. of the n x n double-float block, V [32][n]) from
+// exact bf16 digit GEMMs on the tensor cores, K split nsplit ways into zpart[nsplit][m][32]
+size_t zgemm_tc_bytes(int64_t n);
+int zgemm_tc_splits(int64_t m, int sms);
+int launch_zgemm_tc(const float4* A, int64_t n, int r1, int m, const float4* V, void* scratch, float4* zpart,
+                    int nsplit, int* status, cudaStream_t st, long wait_polls);
 int launch_tridiag2(float4* A, int64_t n, const double2* v0, const double* beta0, double* d, double* e, float4* V,
                     float4* W, void* tc_scratch, void* scratch, int* err, cudaStream_t st, long wait_polls);
 int launch_panel_update_tc(float4* A, int64_t n, int k0, int resident_from, const float4* V, const float4* W,

@@ -310,6 +310,175 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_kernel(PanelArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The same panel QR on one thread-block cluster: the panel rows are spread over
+// the cluster's CTAs (in shared memory, v_l stored in place of the entries it
+// annihilates, beta_l on the diagonal), and the per-reflector sums travel through
+// distributed shared memory with two cluster barriers per reflector instead of
+// two grid barriers and global-memory round trips.  A CTA reads another CTA's
+// part only between the barrier after which it was written and the next one,
+// and a final barrier keeps every CTA resident until the last remote read.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// the address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(const void* p, uint32_t rank) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(ra)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return ra;
+}
+__device__ __forceinline__ cdf ld_cluster_cdf(uint32_t ra) {
+    cdf v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(ra)
+                 : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
+    extern __shared__ __align__(16) cdf s_qc[];   // P[l * ch + u], rows rho0 + u
+    __shared__ cdf s_part, s_piv;                 // this CTA's squared-norm part; the pivot (its owner)
+    __shared__ cdf s_wp[2 * kB];                  // this CTA's parts of w (columns > l) and g (kB + k, k < l)
+    __shared__ cdf s_w[2 * kB];                   // their sums over the cluster
+    __shared__ cdf s_T[kB][kB + 1];               // rank 0: the T factor
+    __shared__ float2 s_red[kW2];
+    __shared__ cdf s_tau, s_inv;
+    __shared__ float2 s_beta;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t rank = cluster_rank();
+    const int CQ = gridDim.x;   // the grid is one cluster
+    const int ch = (a.m + CQ - 1) / CQ;
+    const int rho0 = (int)rank * ch, nown = max(0, min(a.m, rho0 + ch) - rho0);
+    const int n = a.n;
+    cdf* P = s_qc;
+    for (int e = tid; e < kB * ch; e += kT2) {
+        const int l = e / ch, u = e - l * ch;
+        P[e] = u < nown ? __ldcg(a.A + (size_t)(a.c0 + l) * n + a.r1 + rho0 + u) : cdf_zero();
+    }
+    __syncthreads();
+    for (int l = 0; l < a.nref; ++l) {
+        // part of the squared norm of column l below row l; the pivot in its owner
+        float sq = 0.f, lo = 0.f;
+        for (int u = tid; u < nown; u += kT2)
+            if (rho0 + u > l) {
+                const cdf x = P[l * ch + u];
+                df_acc(sq, lo, x.x, x.y, x.x, x.y);
+                df_acc(sq, lo, x.z, x.w, x.z, x.w);
+            }
+        if (tid == 0 && l >= rho0 && l < rho0 + nown) s_piv = P[l * ch + (l - rho0)];
+        float2 t = warp_sum_df(df_fin(sq, lo));
+        if (lane == 0) s_red[wid] = t;
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < kW2; ++k) t = df_add(t, s_red[k]);
+            s_part = make_float4(t.x, t.y, 0.f, 0.f);
+        }
+        cluster_sync_all();
+        // the reflector from every CTA's part (warp 0, in each CTA)
+        if (wid == 0) {
+            float2 sg = make_float2(0.f, 0.f);
+            if (lane < CQ) {
+                const cdf pp = ld_cluster_cdf(map_rank(&s_part, (uint32_t)lane));
+                sg = make_float2(pp.x, pp.y);
+            }
+            sg = warp_sum_df(sg);
+            const cdf piv = ld_cluster_cdf(map_rank(&s_piv, (uint32_t)(l / ch)));
+            if (lane == 0) {
+                cdf tau, inv;
+                float2 beta;
+                reflector(piv, sg, tau, inv, beta);
+                s_tau = tau;
+                s_inv = inv;
+                s_beta = beta;
+                if (rank == 0) a.tau[l] = tau;
+            }
+        }
+        __syncthreads();
+        // v below the diagonal in place, beta on it
+        for (int u = tid; u < nown; u += kT2) {
+            const int rho = rho0 + u;
+            if (rho > l) P[l * ch + u] = cdf_mul(P[l * ch + u], s_inv);
+            if (rho == l) P[l * ch + u] = make_float4(s_beta.x, s_beta.y, 0.f, 0.f);
+        }
+        __syncthreads();
+        // parts of w_c = v^H P[:, c] (c > l) and g_k = v_k^H v (k < l), a warp per task
+        for (int c = wid; c < kB - 1; c += kW2) {
+            const bool isg = c < l;
+            const int col = isg ? c : c + 1;
+            CAcc acc;
+            acc.zero();
+            for (int u = lane; u < nown; u += 32) {
+                const int rho = rho0 + u;
+                if (rho < l) continue;
+                const cdf vr = rho == l ? onec() : P[l * ch + u];
+                if (isg)
+                    acc.dot(P[col * ch + u], vr);   // v_col below its diagonal (rho >= l > col)
+                else
+                    acc.dot(vr, P[col * ch + u]);
+            }
+            const cdf sum = cdf_warp_sum(acc.get());
+            if (lane == 0) s_wp[isg ? kB + col : col] = sum;
+        }
+        cluster_sync_all();
+        // sums over the cluster (four threads per entry)
+        {
+            const int ent = tid >> 2, k0 = tid & 3;
+            const bool need = ent < kB ? ent > l : ent - kB < l;
+            cdf sum = cdf_zero();
+            if (need)
+                for (int k = k0; k < CQ; k += 4) sum = cdf_add(sum, ld_cluster_cdf(map_rank(&s_wp[ent], (uint32_t)k)));
+            sum = cdf_add(sum, cdf_shfl_xor(sum, 1));
+            sum = cdf_add(sum, cdf_shfl_xor(sum, 2));
+            if (k0 == 0 && need) s_w[ent] = sum;
+        }
+        __syncthreads();
+        if (rank == 0 && tid <= l) {   // column l of T: T[0:l, l] = -tau_l T[0:l, 0:l] g
+            if (tid == l) {
+                s_T[l][l] = s_tau;
+            } else {
+                CAcc acc;
+                acc.zero();
+                for (int k = tid; k < l; ++k) acc.mac(s_T[tid][k], s_w[kB + k]);
+                s_T[tid][l] = cdf_mul(negc(s_tau), acc.get());
+            }
+        }
+        // P <- P - conj(tau) v w on own rows >= l, columns > l
+        const cdf mct = negc(conjc(s_tau));
+        for (int u = tid; u < nown; u += kT2) {
+            const int rho = rho0 + u;
+            if (rho < l) continue;
+            const cdf f = cdf_mul(mct, rho == l ? onec() : P[l * ch + u]);
+            for (int c = l + 1; c < kB; ++c) P[c * ch + u] = cdf_fma(P[c * ch + u], f, s_w[c]);
+        }
+        __syncthreads();
+    }
+    // the panel ([R; 0]), the reflectors and T back to global memory
+    if (rank == 0)
+        for (int e = tid; e < kB * kB; e += kT2) {
+            const int r = e >> 5, c = e & 31;
+            a.T[e] = r <= c && c < a.nref ? s_T[r][c] : cdf_zero();
+        }
+    for (int e = tid; e < kB * ch; e += kT2) {
+        const int l = e / ch, u = e - l * ch;
+        if (u >= nown) continue;
+        const int rho = rho0 + u;
+        const cdf x = P[e];
+        const bool below = l < a.nref && rho > l;   // v_l stored in place
+        a.A[(size_t)(a.c0 + l) * n + a.r1 + rho] = below ? cdf_zero() : x;
+        a.V[(size_t)l * n + a.r1 + rho] = l >= a.nref || rho < l ? cdf_zero() : (rho == l ? onec() : x);
+    }
+    cluster_sync_all();   // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // 32 x 32 Gram products X^H Y over rows r1 .. r1 + m - 1 of two [32][n] arrays:
 // part[blk][i][j] = sum over the CTA's rows of conj(X[i][r]) Y[j][r]
 // (1024 threads, thread (i, j); rows staged in shared memory 32 at a time).
@@ -664,7 +833,7 @@ size_t tridiag2_bytes(int64_t n) {
     // H0 vectors (3 n); A22 V parts (kMaxKs n 32); Gram parts (ng 1024); T, M (2 x 1024); tau, pivots
     // (64); partial norms (256 float2); partial w and g (256 x 64); progress (n ints); barrier; alignment
     return sizeof(cdf) * (size_t)(3 * n + kMaxKs * n * kB + ng * kB * kB + 2 * kB * kB + 2 * kB + 512 * kB) +
-           sizeof(float2) * 256 + sizeof(int) * (size_t)n + 64 + 16 * 256;
+           sizeof(float2) * 256 + sizeof(int) * (size_t)n + zgemm_tc_bytes(n) + 64 + 16 * 256;
 }
 
 int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0, double* d, double* e, cdf* V, cdf* W,
@@ -690,6 +859,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
     cdf* wpart = (cdf*)take(sizeof(cdf) * 256 * 2 * kB);
     int* prog = (int*)take(sizeof(int) * n);
     unsigned* bar = (unsigned*)take(sizeof(unsigned));
+    void* zscratch = take(zgemm_tc_bytes(n));
     const long spin = wait_limit(wait_polls, kGridSpinLimit);
 
     int dev = 0, sms = 0;
@@ -707,6 +877,50 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
     rank2_all_kernel<<<sms * 4, kT2, 0, st>>>(A, n, hv, hw);
     note_launch();
     BSE_CUDA(cudaGetLastError());
+
+    // the panel QR on one cluster of CQ CTAs (16, else 8) when the rows of the largest panel
+    // fit its shared memory, else on co-resident CTAs with grid barriers
+    int CQ = 0;
+    {
+        const int m0 = n - kB;
+        for (int cq : {16, 8}) {
+            if (m0 < 2) break;
+            const int ch = (m0 + cq - 1) / cq;
+            const size_t smem = sizeof(cdf) * kB * (size_t)ch;
+            if (ch > 4 * kT2 || smem > 200 * 1024) continue;
+            if (cq > 8 &&
+                cudaFuncSetAttribute(panel_qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (cudaFuncSetAttribute(panel_qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cq;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cq);
+            cfg.blockDim = dim3(kT2);
+            cfg.dynamicSmemBytes = smem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, (void*)panel_qr_cluster_kernel, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (nc >= 1) {
+                CQ = cq;
+                break;
+            }
+        }
+    }
 
     // stage 1: panels of 32 columns
     for (int c0 = 0;; c0 += kB) {
@@ -737,17 +951,30 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
         pa.bar = bar;
         pa.err = err;
         pa.spin = spin;
-        void* qargs[] = {&pa};
-        BSE_CUDA(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(Gq), dim3(kT2), qargs, qsm, st));
+        if (CQ > 0) {
+            const int chq = (m + CQ - 1) / CQ;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CQ;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(CQ);
+            cfg.blockDim = dim3(kT2);
+            cfg.dynamicSmemBytes = sizeof(cdf) * kB * (size_t)chq;
+            cfg.stream = st;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            BSE_CUDA(cudaLaunchKernelEx(&cfg, panel_qr_cluster_kernel, pa));
+        } else {
+            void* qargs[] = {&pa};
+            BSE_CUDA(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(Gq), dim3(kT2), qargs, qsm, st));
+        }
         note_launch();
         const int ng = (m + kGramRows - 1) / kGramRows;
         // Z = A22 V split over K, Y = Z T
-        const int rt = (m + kZR - 1) / kZR;
-        int ks = std::max(1, std::min(kMaxKs, (2 * sms + rt - 1) / rt));
-        ks = std::min(ks, (m + 31) / 32);
-        const int kchunk = (m + ks - 1) / ks;
-        zgemm_kernel<<<dim3(rt, ks), kT2, 0, st>>>(A, n, r1, m, V, kchunk, zpart);
-        note_launch();
+        const int ks = zgemm_tc_splits(m, sms);
+        BSE_TRY(launch_zgemm_tc(A, n, r1, m, V, zscratch, zpart, ks, err, st, wait_polls));
         ysum_kernel<<<(unsigned)((m + kW2 - 1) / kW2), kT2, 0, st>>>(zpart, ks, m, T, n, r1, W);
         note_launch();
         // W = Y - 1/2 V T^H V^H Y

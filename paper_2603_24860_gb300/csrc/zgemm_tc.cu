@@ -1,0 +1,416 @@
+// Z = A22 V of the two-stage reduction on the tcgen05 tensor cores (sm_103a):
+// A22 = A[r1:, r1:] (m x m, double-float, Hermitian), V = [32][n] reflectors.
+//
+// The contraction runs over K in chunks of 64 complex columns.  In real form,
+// with K' = 128 per chunk,
+//   Re Z[r,l] = [Ar Ai] [Vr -Vi]^T,   Im Z[r,l] = [Ar Ai] [Vi Vr]^T,
+// so the A22 chunk is one MMA operand (M = 128 rows) and the two forms of the V
+// chunk are stacked as the 64 rows (N) of the other.  Within a chunk the
+// operands are split exactly as in the panel update (her2k_tc.cu): a row of the
+// A22 chunk and a column of the V chunk each get a power-of-two scale from their
+// largest entry, are rounded to 56 bits and written as 8 balanced base-128
+// digits stored pre-scaled (d_k 2^-7k, exact in bf16); the digit-pair groups
+// g = k + m < 4 accumulate exactly in FP32 in TMEM, the groups 4..7 share a fifth
+// accumulator.  Per chunk the five accumulators are summed in double-float,
+// scaled by 2^(e_r + f_l - 14) and added to double-float accumulators held in
+// registers, so the chunks combine in double-float.  CTA (row tile, split) takes
+// a contiguous range of chunks; its partial Z goes to zpart[split][row][l].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dfloat.h"
+#include "grid_sync.h"
+#include "internal.h"
+#include "tc_ptx.h"
+
+namespace bse {
+
+namespace {
+
+constexpr int kZM = 128;                                   // rows of a tile (M, TMEM lanes)
+constexpr int kZL = 32;                                    // columns of Z (reflectors)
+constexpr int kZN = 64;                                    // N of the MMA: [Vr -Vi] rows, then [Vi Vr] rows
+constexpr int kZK = 128;                                   // K' of a chunk (64 complex columns)
+constexpr int kZC = 64;                                    // complex columns per chunk
+constexpr int kZDig = 8;
+constexpr int kZExact = 4;
+constexpr int kZAcc = kZExact + 1;
+constexpr int kZSlots = 3;
+constexpr int kZThreads = 128;
+constexpr uint32_t kZTmemCols = 512;                       // kZAcc x kZN = 320 used
+constexpr size_t kZADig = (size_t)kZM * kZK * 2;           // one digit of an A22 tile chunk (32 KB)
+constexpr size_t kZBDig = (size_t)kZN * kZK * 2;           // one digit of a V chunk, both forms (16 KB)
+constexpr size_t kZBChunk = kZDig * kZBDig;                // 128 KB
+constexpr size_t kZSmem = kZBChunk + kZSlots * kZADig + 1024;
+constexpr int kZMaxSplit = 8;
+
+// Balanced base-128 digits d_0 .. d_7 (weights 2^49 .. 2^0, stored pre-scaled by 2^-7k) of
+// rint(x 2^(56-e)) for a double-float x = h + l, |x| < 2^e, without FP64 or 64-bit integer
+// arithmetic: (h, l) scaled by 2^(56-e) (two exact power-of-two factors), then per digit
+// q = rint(h / w) for w = 2^(49-7k), h <- h - q w (exact: a multiple of ulp(h) below w/2), and
+// (h, l) renormalised by TwoSum; the last digit is rint(h + l).
+__device__ __forceinline__ void df_digits8(float h, float l, int e, float* d) {
+    const int s = 56 - e, s1 = s / 2, s2 = s - s1;
+    const float f1 = __int_as_float((127 + s1) << 23), f2 = __int_as_float((127 + s2) << 23);
+    float hs = (h * f1) * f2, ls = (l * f1) * f2;
+#pragma unroll
+    for (int k = 0; k < kZDig - 1; ++k) {
+        const float w = __int_as_float((127 + 49 - 7 * k) << 23), wi = __int_as_float((127 - 49 + 7 * k) << 23);
+        const float q = rintf(hs * wi);
+        hs = fmaf(-q, w, hs);
+        two_sum(hs, ls, hs, ls);
+        d[k] = q * __int_as_float((127 - 7 * k) << 23);
+    }
+    d[kZDig - 1] = rintf(hs + ls) * __int_as_float((127 - 7 * (kZDig - 1)) << 23);
+}
+
+// 2^e above every |h| of the given maximum (|h + l| < 2^e as well)
+__device__ __forceinline__ int exp_above_f(float m) { return m > 0.f ? ilogbf(m) + 1 : 0; }
+
+// eight bf16 values (exact: pre-scaled digits) packed as one 16-byte store
+__device__ __forceinline__ uint4 pack8(const float* x) {
+    uint4 u;
+    __nv_bfloat162 t;
+    t = __floats2bfloat162_rn(x[0], x[1]);
+    u.x = *reinterpret_cast<uint32_t*>(&t);
+    t = __floats2bfloat162_rn(x[2], x[3]);
+    u.y = *reinterpret_cast<uint32_t*>(&t);
+    t = __floats2bfloat162_rn(x[4], x[5]);
+    u.z = *reinterpret_cast<uint32_t*>(&t);
+    t = __floats2bfloat162_rn(x[6], x[7]);
+    u.w = *reinterpret_cast<uint32_t*>(&t);
+    return u;
+}
+
+// row exponents of A22 per chunk: thread per (row r, chunk c), consecutive threads on
+// consecutive rows; 2^ex is above the row's largest entry in the chunk
+__global__ void a22_exp_kernel(const cdf* __restrict__ A, int n, int r1, int m, int nrt, int nch, int* ex) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t rows = (int64_t)nrt * kZM;
+    if (gid >= rows * nch) return;
+    const int r = (int)(gid % rows), c = (int)(gid / rows);
+    const int c0 = c * kZC, cn = min(kZC, m - c0);
+    float mx = 0.f;
+    if (r < m) {
+        const cdf* row = A + (size_t)(r1 + c0) * n + r1 + r;
+#pragma unroll 8
+        for (int j = 0; j < cn; ++j) {
+            const cdf z = __ldcg(row + (size_t)j * n);
+            mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.z)));
+        }
+    }
+    ex[gid] = exp_above_f(mx);
+}
+
+// A22 digits: thread per (row r of a 128-row tile, chunk c, group of 8 columns g): the 16-byte
+// pieces of each digit for the group's Re parts (K 8g .. 8g+7) and Im parts (K 64 + 8g ..).
+// Tiles [rt][c][k] of 128 x 128 in the core-matrix layout; consecutive threads take
+// consecutive rows (coalesced loads).
+__global__ void a22_digits_kernel(const cdf* __restrict__ A, int n, int r1, int m, int nrt, int nch,
+                                  __nv_bfloat16* Adig, const int* __restrict__ ex) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t rows = (int64_t)nrt * kZM;
+    if (gid >= rows * nch * (kZC / 8)) return;
+    const int r = (int)(gid % rows);
+    const int64_t cg = gid / rows;
+    const int g = (int)(cg % (kZC / 8)), c = (int)(cg / (kZC / 8));
+    const int rt = r / kZM, rr = r % kZM;
+    const bool live = r < m;
+    const int c0 = c * kZC, cn = min(kZC, m - c0);
+    const cdf* row = A + (size_t)(r1 + c0) * n + r1 + r;   // entry j of the chunk at row[j n]
+    const int e = ex[(size_t)c * rows + r];
+    cdf z[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int j = 8 * g + u;
+        z[u] = live && j < cn ? __ldcg(row + (size_t)j * n) : cdf_zero();
+    }
+    float dr[8][kZDig], di[8][kZDig];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        df_digits8(z[u].x, z[u].y, e, dr[u]);
+        df_digits8(z[u].z, z[u].w, e, di[u]);
+    }
+    unsigned char* tile = (unsigned char*)Adig + ((size_t)rt * nch + c) * kZDig * kZADig;
+#pragma unroll
+    for (int k = 0; k < kZDig; ++k) {
+        float pr[8], pi[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            pr[u] = dr[u][k];
+            pi[u] = di[u][k];
+        }
+        unsigned char* base = tile + (size_t)k * kZADig;
+        *(uint4*)(base + tc::core_off(rr, 8 * g, kZK)) = pack8(pr);
+        *(uint4*)(base + tc::core_off(rr, kZC + 8 * g, kZK)) = pack8(pi);
+    }
+}
+
+// V digits: thread per (chunk c, group of 8 columns g, reflector l); the column exponent over the
+// chunk; rows l of [Vr -Vi] and 32 + l of [Vi Vr] of each digit (tiles [c][k] of 64 x 128)
+__global__ void v_digits_kernel(const cdf* __restrict__ V, int n, int r1, int m, int nch, __nv_bfloat16* Bdig,
+                                int* fy) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nch * (kZC / 8) * kZL) return;
+    const int l = gid % kZL, g = (gid / kZL) % (kZC / 8), c = gid / (kZL * (kZC / 8));
+    const int c0 = c * kZC, cn = min(kZC, m - c0);
+    const cdf* col = V + (size_t)l * n + r1 + c0;
+    float mx = 0.f;
+    for (int j = 0; j < cn; ++j) {
+        const cdf z = __ldcg(col + j);
+        mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.z)));
+    }
+    const int e = exp_above_f(mx);
+    if (g == 0) fy[c * kZL + l] = e;
+    float dr[8][kZDig], di[8][kZDig];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int j = 8 * g + u;
+        const cdf z = j < cn ? __ldcg(col + j) : cdf_zero();
+        df_digits8(z.x, z.y, e, dr[u]);
+        df_digits8(z.z, z.w, e, di[u]);
+    }
+    unsigned char* tile = (unsigned char*)Bdig + (size_t)c * kZBChunk;
+#pragma unroll
+    for (int k = 0; k < kZDig; ++k) {
+        float pr[8], pi[8], ni[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            pr[u] = dr[u][k];
+            pi[u] = di[u][k];
+            ni[u] = -di[u][k];
+        }
+        unsigned char* base = tile + (size_t)k * kZBDig;
+        *(uint4*)(base + tc::core_off(l, 8 * g, kZK)) = pack8(pr);   // [Vr -Vi]
+        *(uint4*)(base + tc::core_off(l, kZC + 8 * g, kZK)) = pack8(ni);
+        *(uint4*)(base + tc::core_off(kZL + l, 8 * g, kZK)) = pack8(pi);   // [Vi Vr]
+        *(uint4*)(base + tc::core_off(kZL + l, kZC + 8 * g, kZK)) = pack8(pr);
+    }
+}
+
+struct ZArgs {
+    const __nv_bfloat16* Adig;   // [nrt][nch][8][128 x 128]
+    const __nv_bfloat16* Bdig;   // [nch][8][64 x 128]
+    const int* ex;               // [nch][nrt * 128] row exponents
+    const int* fy;               // [nch][32] column exponents
+    cdf* zpart;                  // [split][m][32]
+    int m, nrt, nch, nsplit;
+    int* status;
+    long spin;
+};
+
+// five accumulators of one output (exact FP32 values) summed in double-float
+__device__ __forceinline__ float2 zsum5(const uint32_t (&v)[kZAcc][8], int j) {
+    float h, l, h2, l2;
+    two_sum(__uint_as_float(v[0][j]), __uint_as_float(v[1][j]), h, l);
+    two_sum(__uint_as_float(v[2][j]), __uint_as_float(v[3][j]), h2, l2);
+    const float2 s = df_add(make_float2(h, l), make_float2(h2, l2));
+    return df_add(s, make_float2(__uint_as_float(v[4][j]), 0.f));
+}
+
+// CTA (rt = blockIdx.x, split = blockIdx.y) takes chunks [nch s / S, nch (s + 1) / S).  The
+// X stream: item j = digit j % 8 of chunk c_lo + j / 8, in slot j % 3 (copy = the (j / 3)-th
+// completion of mb_full[slot], MMAs = the (j / 3)-th commit to mb_empty[slot]); the V chunk
+// of the next chunk is fetched once the MMAs of the current one are done, during its drain.
+__global__ void __launch_bounds__(kZThreads, 1) zgemm_tc_kernel(ZArgs a) {
+    extern __shared__ __align__(1024) unsigned char zsm_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)zsm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* Bs = smem;
+    unsigned char* As = smem + kZBChunk;
+    __shared__ __align__(8) uint64_t mb_y, mb_full[kZSlots], mb_empty[kZSlots], mb_acc;
+    __shared__ uint32_t slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        tc::mbar_init(&mb_y, 1);
+        tc::mbar_init(&mb_acc, 1);
+        for (int i = 0; i < kZSlots; ++i) {
+            tc::mbar_init(&mb_full[i], 1);
+            tc::mbar_init(&mb_empty[i], 1);
+        }
+    }
+    if (warp == 0) tc::tmem_alloc(&slot, kZTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = slot;
+    const int rt = blockIdx.x, sp = blockIdx.y;
+    const int c_lo = (int)((int64_t)a.nch * sp / a.nsplit), c_hi = (int)((int64_t)a.nch * (sp + 1) / a.nsplit);
+    const int nitems = (c_hi - c_lo) * kZDig;
+    const uint32_t idesc = tc::idesc_f16(kZM, kZN, 1);
+    const uint32_t lbo = 128, sbo = (uint32_t)(kZK / 8) * 128;
+    auto wait = [&](uint64_t* mb, uint32_t parity) {
+        const bool got = tc::mbar_wait(mb, parity, a.spin);
+        if (!got) tc::mbar_wait(mb, parity, kMbarSpinLimit);
+        return got;
+    };
+    auto item_src = [&](int j) {
+        const int c = c_lo + j / kZDig;
+        return (const unsigned char*)a.Adig + (((size_t)rt * a.nch + c) * kZDig + j % kZDig) * kZADig;
+    };
+    int issued = 0, landed = 0, committed = 0, retired = 0, ys = 0, yw = 0;
+    auto issue_item = [&](int j) {
+        const int sl = j % kZSlots;
+        tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kZADig);
+        tc::bulk_g2s(As + sl * kZADig, item_src(j), (uint32_t)kZADig, &mb_full[sl]);
+        issued = j + 1;
+    };
+    auto issue_y = [&](int c) {
+        tc::mbar_expect_tx(&mb_y, (uint32_t)kZBChunk);
+        tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)c * kZBChunk, (uint32_t)kZBChunk, &mb_y);
+        ++ys;
+    };
+    if (tid == 0 && nitems > 0) {
+        issue_y(c_lo);
+        for (int j = 0; j < kZSlots && j < nitems; ++j) issue_item(j);
+    }
+    const int r = rt * kZM + warp * 32 + lane;   // this thread's row (TMEM lane)
+    const bool rlive = r < a.m;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    float zr[kZL][2], zi[kZL][2];   // double-float accumulators of Z[r][l]
+#pragma unroll
+    for (int l = 0; l < kZL; ++l) zr[l][0] = zr[l][1] = zi[l][0] = zi[l][1] = 0.f;
+    bool ok = true;
+    for (int cl = 0; c_lo + cl < c_hi && ok; ++cl) {
+        const int c = c_lo + cl;
+        bool ok0 = true;
+        if (tid == 0) {
+            ok0 = wait(&mb_y, (uint32_t)(yw & 1));
+            ++yw;
+            for (int k = 0; k < kZDig && ok0; ++k) {
+                const int j = cl * kZDig + k, sl = j % kZSlots;
+                ok0 = wait(&mb_full[sl], (uint32_t)((j / kZSlots) & 1));
+                landed = j + 1;
+                if (!ok0) break;
+                tc::fence_after();
+                const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kZADig), lbo, sbo);
+                for (int mm = 0; mm + k < kZDig; ++mm) {
+                    const int g = k + mm, acc = g < kZExact ? g : kZExact;
+                    const bool first = k == 0 && (g < kZExact || mm == kZExact);
+                    const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + mm * kZBDig), lbo, sbo);
+                    const uint32_t d = tmem + (uint32_t)(acc * kZN);
+#pragma unroll
+                    for (int ks = 0; ks < kZK / 16; ++ks)
+                        tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc,
+                                    (first && ks == 0) ? 0u : 1u);
+                }
+                tc::mma_commit(&mb_empty[sl]);
+                committed = j + 1;
+                if (j >= 1) {
+                    ok0 = wait(&mb_empty[(j - 1) % kZSlots], (uint32_t)(((j - 1) / kZSlots) & 1));
+                    retired = j;
+                    if (ok0 && j + 2 < nitems) issue_item(j + 2);
+                }
+            }
+            if (ok0) tc::mma_commit(&mb_acc);
+        }
+        ok = __syncthreads_and(tid != 0 || ok0) != 0;
+        if (!ok) break;
+        ok = __syncthreads_and(wait(&mb_acc, (uint32_t)(cl & 1))) != 0;
+        if (!ok) break;
+        tc::fence_after();
+        // the V chunk buffer is free: fetch the next chunk's during the drain
+        if (tid == 0 && c + 1 < c_hi) issue_y(c + 1);
+        // drain: Z[r][l] += 2^(e_r + f_l - 14) (G_0 + .. + G_3 + G_rest), eight columns at a time
+        const int er = rlive ? __ldg(a.ex + (size_t)c * a.nrt * kZM + r) : 0;
+#pragma unroll
+        for (int c0 = 0; c0 < kZL; c0 += 8) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {   // real parts (columns c0..), then imaginary (32 + c0..)
+                uint32_t v[kZAcc][8];
+#pragma unroll
+                for (int q = 0; q < kZAcc; ++q)
+                    tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(q * kZN + part * kZL + c0), v[q]);
+#pragma unroll
+                for (int q = 0; q < kZAcc; ++q) tc::tmem_ld_wait(v[q]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float sc = ldexpf(1.f, er + __ldg(a.fy + c * kZL + c0 + j) - 14);
+                    const float2 sv = zsum5(v, j);
+                    float(&acc)[2] = part == 0 ? zr[c0 + j] : zi[c0 + j];
+                    const float2 nv = df_add(make_float2(acc[0], acc[1]), make_float2(sv.x * sc, sv.y * sc));
+                    acc[0] = nv.x;
+                    acc[1] = nv.y;
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();   // TMEM is reused by the next chunk
+        tc::fence_after();
+    }
+    if (ok && rlive) {
+        cdf* out = a.zpart + ((size_t)sp * a.m + r) * kZL;
+#pragma unroll
+        for (int l = 0; l < kZL; ++l) out[l] = make_float4(zr[l][0], zr[l][1], zi[l][0], zi[l][1]);
+    }
+    if (!ok && tid == 0) {
+        for (int j = landed; j < issued; ++j)
+            tc::mbar_wait(&mb_full[j % kZSlots], (uint32_t)((j / kZSlots) & 1), kMbarSpinLimit);
+        for (int j = retired; j < committed; ++j)
+            tc::mbar_wait(&mb_empty[j % kZSlots], (uint32_t)((j / kZSlots) & 1), kMbarSpinLimit);
+        while (yw < ys) {
+            tc::mbar_wait(&mb_y, (uint32_t)(yw & 1), kMbarSpinLimit);
+            ++yw;
+        }
+        atomicExch(a.status, 1);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kZTmemCols);
+}
+
+}  // namespace
+
+size_t zgemm_tc_bytes(int64_t n) {
+    const int64_t nrt = (n + kZM - 1) / kZM, nch = (n + kZC - 1) / kZC;
+    return (size_t)nrt * nch * kZDig * kZADig + (size_t)nch * kZBChunk + sizeof(int) * (size_t)(nch * (nrt * kZM + kZL)) +
+           4096;
+}
+
+int zgemm_tc_splits(int64_t m, int sms) {
+    const int nrt = (int)((m + kZM - 1) / kZM), nch = (int)((m + kZC - 1) / kZC);
+    return std::max(1, std::min({kZMaxSplit, nch, (sms + nrt - 1) / nrt}));
+}
+
+int launch_zgemm_tc(const cdf* A, int64_t n64, int r1, int m, const cdf* V, void* scratch, cdf* zpart, int nsplit,
+                    int* status, cudaStream_t st, long wait_polls) {
+    const int n = (int)n64;
+    const int nrt = (m + kZM - 1) / kZM, nch = (m + kZC - 1) / kZC;
+    char* p = (char*)scratch;
+    __nv_bfloat16* Adig = (__nv_bfloat16*)p;
+    p += (size_t)nrt * nch * kZDig * kZADig;
+    __nv_bfloat16* Bdig = (__nv_bfloat16*)p;
+    p += (size_t)nch * kZBChunk;
+    int* ex = (int*)p;
+    int* fy = ex + (size_t)nch * nrt * kZM;
+    {
+        a22_exp_kernel<<<(unsigned)(((int64_t)nrt * kZM * nch + 255) / 256), 256, 0, st>>>(A, n, r1, m, nrt, nch, ex);
+        note_launch();
+        const int64_t threads = (int64_t)nrt * kZM * nch * (kZC / 8);
+        a22_digits_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, n, r1, m, nrt, nch, Adig, ex);
+        note_launch();
+        v_digits_kernel<<<(nch * (kZC / 8) * kZL + 127) / 128, 128, 0, st>>>(V, n, r1, m, nch, Bdig, fy);
+        note_launch();
+        BSE_CUDA(cudaGetLastError());
+    }
+    ZArgs z;
+    z.Adig = Adig;
+    z.Bdig = Bdig;
+    z.ex = ex;
+    z.fy = fy;
+    z.zpart = zpart;
+    z.m = m;
+    z.nrt = nrt;
+    z.nch = nch;
+    z.nsplit = nsplit;
+    z.status = status;
+    z.spin = wait_limit(wait_polls, kMbarSpinLimit);
+    BSE_CUDA(cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZSmem));
+    zgemm_tc_kernel<<<dim3(nrt, nsplit), kZThreads, kZSmem, st>>>(z);
+    note_launch();
+    BSE_CUDA(cudaGetLastError());
+    return BSE_OK;
+}
+
+}  // namespace bse
