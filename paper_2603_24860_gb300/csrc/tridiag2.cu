@@ -53,7 +53,7 @@ namespace {
 constexpr int kB = 32;              // half-bandwidth of stage 1 = reflectors per panel
 constexpr int kT2 = 256;            // threads of most kernels here
 constexpr int kW2 = kT2 / 32;
-constexpr int kMaxKs = 8;           // K splits of the A22 V product
+constexpr int kMaxKs = 8;           // K splits of the A22 V product (at least those of zgemm_tc.cu)
 constexpr int kQrMaxCta = 32;       // CTAs of the panel QR
 constexpr int kGramRows = 128;      // rows per CTA of the 32 x 32 Gram products
 constexpr int kSweepDone = 1 << 30;
@@ -343,13 +343,20 @@ __device__ __forceinline__ cdf ld_cluster_cdf(uint32_t ra) {
     return v;
 }
 
+// One cluster barrier per reflector.  Before reflector l is known, every CTA sums over
+// its rows rho > l: sigma = |P[rho][l]|^2, d_c = conj(P[rho][l]) P[rho][c] (c > l) and
+// h_k = conj(v_k[rho]) P[rho][l] (k < l); the owner of row l adds the pivot row P[l][c]
+// (c >= l) and v_k[l] (k < l).  After the barrier every CTA sums the parts (through
+// distributed shared memory) and forms the reflector, w_c = v^H P[:, c] = P[l][c] +
+// conj(inv) d_c and g_k = v_k^H v = conj(v_k[l]) + inv h_k.  The parts are double-buffered
+// by the parity of l: a CTA rewrites a buffer only after the next barrier, which every
+// other CTA passes after its reads.
+constexpr int kQp = 1 + 2 * kB;   // parts per CTA: sigma, d_c or h_k (entries 1..32), pivot row / v_k[l] (33..64)
 __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
     extern __shared__ __align__(16) cdf s_qc[];   // P[l * ch + u], rows rho0 + u
-    __shared__ cdf s_part, s_piv;                 // this CTA's squared-norm part; the pivot (its owner)
-    __shared__ cdf s_wp[2 * kB];                  // this CTA's parts of w (columns > l) and g (kB + k, k < l)
-    __shared__ cdf s_w[2 * kB];                   // their sums over the cluster
+    __shared__ cdf s_wp[2][kQp];                  // this CTA's parts, by parity of l
+    __shared__ cdf s_w[kQp];                      // their sums over the cluster (pivot entries from the owner)
     __shared__ cdf s_T[kB][kB + 1];               // rank 0: the T factor
-    __shared__ float2 s_red[kW2];
     __shared__ cdf s_tau, s_inv;
     __shared__ float2 s_beta;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -365,98 +372,101 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
     }
     __syncthreads();
     for (int l = 0; l < a.nref; ++l) {
-        // part of the squared norm of column l below row l; the pivot in its owner
-        float sq = 0.f, lo = 0.f;
-        for (int u = tid; u < nown; u += kT2)
-            if (rho0 + u > l) {
-                const cdf x = P[l * ch + u];
-                df_acc(sq, lo, x.x, x.y, x.x, x.y);
-                df_acc(sq, lo, x.z, x.w, x.z, x.w);
-            }
-        if (tid == 0 && l >= rho0 && l < rho0 + nown) s_piv = P[l * ch + (l - rho0)];
-        float2 t = warp_sum_df(df_fin(sq, lo));
-        if (lane == 0) s_red[wid] = t;
-        __syncthreads();
-        if (tid == 0) {
-            for (int k = 1; k < kW2; ++k) t = df_add(t, s_red[k]);
-            s_part = make_float4(t.x, t.y, 0.f, 0.f);
-        }
-        cluster_sync_all();
-        // the reflector from every CTA's part (warp 0, in each CTA)
-        if (wid == 0) {
-            float2 sg = make_float2(0.f, 0.f);
-            if (lane < CQ) {
-                const cdf pp = ld_cluster_cdf(map_rank(&s_part, (uint32_t)lane));
-                sg = make_float2(pp.x, pp.y);
-            }
-            sg = warp_sum_df(sg);
-            const cdf piv = ld_cluster_cdf(map_rank(&s_piv, (uint32_t)(l / ch)));
-            if (lane == 0) {
-                cdf tau, inv;
-                float2 beta;
-                reflector(piv, sg, tau, inv, beta);
-                s_tau = tau;
-                s_inv = inv;
-                s_beta = beta;
-                if (rank == 0) a.tau[l] = tau;
-            }
-        }
-        __syncthreads();
-        // v below the diagonal in place, beta on it
-        for (int u = tid; u < nown; u += kT2) {
-            const int rho = rho0 + u;
-            if (rho > l) P[l * ch + u] = cdf_mul(P[l * ch + u], s_inv);
-            if (rho == l) P[l * ch + u] = make_float4(s_beta.x, s_beta.y, 0.f, 0.f);
-        }
-        __syncthreads();
-        // parts of w_c = v^H P[:, c] (c > l) and g_k = v_k^H v (k < l), a warp per task
-        for (int c = wid; c < kB - 1; c += kW2) {
-            const bool isg = c < l;
-            const int col = isg ? c : c + 1;
+        cdf* wp = s_wp[l & 1];
+        const bool owner = l >= rho0 && l < rho0 + nown;
+        // parts over own rows rho > l: task 0 sigma, tasks 1..31 d_c (c = l + task) or h_k (k = task - ...)
+        for (int task = wid; task < kB; task += kW2) {
+            // task 0: sigma; task q in 1..31: d_{l+q} if l + q < 32, else h_{l+q-32}
+            const int q = task, cc = l + q;
+            const bool isd = q >= 1 && cc < kB, ish = q >= 1 && cc >= kB && cc - kB < l;
             CAcc acc;
             acc.zero();
             for (int u = lane; u < nown; u += 32) {
-                const int rho = rho0 + u;
-                if (rho < l) continue;
-                const cdf vr = rho == l ? onec() : P[l * ch + u];
-                if (isg)
-                    acc.dot(P[col * ch + u], vr);   // v_col below its diagonal (rho >= l > col)
-                else
-                    acc.dot(vr, P[col * ch + u]);
+                if (rho0 + u <= l) continue;
+                const cdf x = P[l * ch + u];
+                if (q == 0)
+                    acc.dot(x, x);
+                else if (isd)
+                    acc.dot(x, P[cc * ch + u]);
+                else if (ish)
+                    acc.dot(P[(cc - kB) * ch + u], x);
             }
             const cdf sum = cdf_warp_sum(acc.get());
-            if (lane == 0) s_wp[isg ? kB + col : col] = sum;
+            if (lane == 0) wp[q == 0 ? 0 : (isd ? cc - l : (ish ? kB - l + (cc - kB) : 0))] = sum;
+        }
+        if (owner) {   // the pivot row P[l][c] (c >= l) at 1 + kB + (c - l); v_k[l] (k < l) at 1 + kB + (32 - l) + k
+            const int u = l - rho0;
+            if (tid < kB) {
+                const int c = tid;
+                if (c >= l)
+                    wp[1 + kB + (c - l)] = P[c * ch + u];
+                else
+                    wp[1 + kB + (kB - l) + c] = P[c * ch + u];
+            }
         }
         cluster_sync_all();
-        // sums over the cluster (four threads per entry)
+        // sums of the parts over the cluster (four threads per entry), pivot data from the owner
         {
-            const int ent = tid >> 2, k0 = tid & 3;
-            const bool need = ent < kB ? ent > l : ent - kB < l;
+            const int ent = tid >> 2, k0 = tid & 3;   // sigma, d, h (entries 0..31): summed
             cdf sum = cdf_zero();
-            if (need)
-                for (int k = k0; k < CQ; k += 4) sum = cdf_add(sum, ld_cluster_cdf(map_rank(&s_wp[ent], (uint32_t)k)));
+            if (ent < kB)
+                for (int k = k0; k < CQ; k += 4) sum = cdf_add(sum, ld_cluster_cdf(map_rank(&wp[ent], (uint32_t)k)));
             sum = cdf_add(sum, cdf_shfl_xor(sum, 1));
             sum = cdf_add(sum, cdf_shfl_xor(sum, 2));
-            if (k0 == 0 && need) s_w[ent] = sum;
+            if (ent < kB && k0 == 0) s_w[ent] = sum;
+            if (tid < kB)   // the pivot row and v_k[l] (entries 33..64), from the owner of row l
+                s_w[1 + kB + tid] = ld_cluster_cdf(map_rank(&wp[1 + kB + tid], (uint32_t)(l / ch)));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            cdf tau, inv;
+            float2 beta;
+            reflector(s_w[1 + kB], make_float2(s_w[0].x, s_w[0].y), tau, inv, beta);
+            s_tau = tau;
+            s_inv = inv;
+            s_beta = beta;
+            if (rank == 0) a.tau[l] = tau;
+        }
+        __syncthreads();
+        const cdf tau = s_tau, inv = s_inv, cinv = conjc(inv);
+        // w_c and g_k from the sums (kept in the d / h entries: w_c at 1 + (c - l), g_k at 1 + (32 - l) + k)
+        __syncthreads();
+        if (tid < kB) {
+            const int c = tid;
+            if (c > l) {
+                const cdf d = s_w[c - l];
+                s_w[c - l] = cdf_fma(s_w[1 + kB + (c - l)], cinv, d);   // P[l][c] + conj(inv) d_c
+            } else if (c < l) {
+                const cdf h = s_w[kB - l + c];
+                s_w[kB - l + c] = cdf_fma(conjc(s_w[1 + kB + (kB - l) + c]), inv, h);   // conj(v_k[l]) + inv h_k
+            }
         }
         __syncthreads();
         if (rank == 0 && tid <= l) {   // column l of T: T[0:l, l] = -tau_l T[0:l, 0:l] g
             if (tid == l) {
-                s_T[l][l] = s_tau;
+                s_T[l][l] = tau;
             } else {
                 CAcc acc;
                 acc.zero();
-                for (int k = tid; k < l; ++k) acc.mac(s_T[tid][k], s_w[kB + k]);
-                s_T[tid][l] = cdf_mul(negc(s_tau), acc.get());
+                for (int k = tid; k < l; ++k) acc.mac(s_T[tid][k], s_w[kB - l + k]);
+                s_T[tid][l] = cdf_mul(negc(tau), acc.get());
             }
         }
-        // P <- P - conj(tau) v w on own rows >= l, columns > l
-        const cdf mct = negc(conjc(s_tau));
+        // own rows: v in place (beta on the diagonal), then P <- P - conj(tau) v w for columns > l
+        const cdf mct = negc(conjc(tau));
         for (int u = tid; u < nown; u += kT2) {
             const int rho = rho0 + u;
             if (rho < l) continue;
-            const cdf f = cdf_mul(mct, rho == l ? onec() : P[l * ch + u]);
-            for (int c = l + 1; c < kB; ++c) P[c * ch + u] = cdf_fma(P[c * ch + u], f, s_w[c]);
+            cdf v;
+            if (rho == l) {
+                v = onec();
+                P[l * ch + u] = make_float4(s_beta.x, s_beta.y, 0.f, 0.f);
+            } else {
+                v = cdf_mul(P[l * ch + u], inv);
+                P[l * ch + u] = v;
+            }
+            const cdf f = cdf_mul(mct, v);
+            for (int c = l + 1; c < kB; ++c) P[c * ch + u] = cdf_fma(P[c * ch + u], f, s_w[c - l]);
         }
         __syncthreads();
     }
@@ -500,58 +510,6 @@ __global__ void __launch_bounds__(1024, 1) gram32_kernel(const cdf* __restrict__
         __syncthreads();
     }
     part[(size_t)blockIdx.x * kB * kB + i * kB + j] = acc.get();
-}
-
-// ---------------------------------------------------------------------------
-// Z = A22 V over rows and columns r1 .. n-1 of A (V: [32][n]), split over K:
-// CTA (row tile rt, split ks) sums columns [k_lo, k_hi) of its 64 rows into
-// zpart[ks][rho][l].  A tile 64 x 32 and V tile 32 x 32 staged in shared
-// memory per step of 32 columns; thread (ty = tid & 31, tx = tid >> 5) holds
-// rows 2 ty, 2 ty + 1 and columns 4 tx .. 4 tx + 3 (eight accumulators).
-// ---------------------------------------------------------------------------
-constexpr int kZR = 64;   // rows per CTA
-__global__ void __launch_bounds__(kT2, 2) zgemm_kernel(const cdf* __restrict__ A, int n, int r1, int m,
-                                                       const cdf* __restrict__ V, int kchunk, cdf* zpart) {
-    __shared__ cdf As[32][kZR];       // [k][row]
-    __shared__ cdf Vsm[32][kB];       // [k][l]
-    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
-    const int row0 = blockIdx.x * kZR, ks = blockIdx.y;
-    const int k_lo = ks * kchunk, k_hi = min(m, k_lo + kchunk);
-    CAcc acc[2][4];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v].zero();
-    for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
-        const int kc = min(32, k_hi - k0);
-        // A tile: 32 columns x 64 rows (thread: row tid & 63, columns tid >> 6 + 4 j)
-        for (int e = tid; e < 32 * kZR; e += kT2) {
-            const int rr = e & (kZR - 1), kk = e >> 6;
-            As[kk][rr] = kk < kc && row0 + rr < m ? __ldcg(A + (size_t)(r1 + k0 + kk) * n + r1 + row0 + rr) : cdf_zero();
-        }
-        for (int e = tid; e < 32 * kB; e += kT2) {
-            const int kk = e & 31, l = e >> 5;
-            Vsm[kk][l] = kk < kc ? __ldcg(V + (size_t)l * n + r1 + k0 + kk) : cdf_zero();
-        }
-        __syncthreads();
-        for (int kk = 0; kk < kc; ++kk) {
-            const cdf a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const cdf bv = Vsm[kk][4 * tx + v];
-                acc[0][v].mac(a0, bv);
-                acc[1][v].mac(a1, bv);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int rho = row0 + 2 * ty + u;
-        if (rho < m)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) zpart[((size_t)ks * m + rho) * kB + 4 * tx + v] = acc[u][v].get();
-    }
 }
 
 // Y = Z T (Z summed over the K splits), rows r1 .. n-1, into Y[32][n] (a warp per row,
@@ -632,16 +590,26 @@ struct BulgeArgs {
 constexpr int kBlk = kB * (kB + 1);
 constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 4 * kB);
 
+// publish a count: every thread's earlier writes were ordered before this by __syncthreads,
+// and the release makes them visible before the count (as in the grid barrier)
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
     return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
                        __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
-// sum over the 8 lanes of a group (lanes 8 g .. 8 g + 7)
-__device__ __forceinline__ cdf group8_sum(cdf v) {
+// sum over the G lanes of a group (lanes G g .. G g + G - 1)
+template <int G>
+__device__ __forceinline__ cdf group_sum(cdf v) {
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) v = cdf_add(v, cdf_shfl_xor(v, o));
+    for (int o = 1; o < G; o <<= 1) v = cdf_add(v, cdf_shfl_xor(v, o));
     return v;
 }
+constexpr int kBT = 512;                // threads of the bulge-chasing kernel
+constexpr int kBRow = kBT / kB;         // product threads per row
+constexpr int kBCol = kB / kBRow;       // columns per product thread
 
 // A task is split in two parts.  R_t: the reflector of the task's column (for t >= 1
 // the first column of the block below of task t - 1, final once that task's right
@@ -655,7 +623,7 @@ __device__ __forceinline__ cdf group8_sum(cdf v) {
 // B -= tau z v^H, L -= conj(tau) v s^H (columns >= 1), and the blocks are written back.
 // Order within the sweep: R_0, L_0, R_1, L_1, ...  Every warp forms the reflector
 // (lane l holds v_l), so no synchronisation separates it from the products.
-__global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
+__global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
     extern __shared__ __align__(16) cdf s_bg[];
     __shared__ int s_ok;
     cdf* D = s_bg;                     // D[r * 33 + c], lower triangle (r >= c)
@@ -666,7 +634,7 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
     cdf* zs = ys + kB;                 // tau z
     cdf* ss = zs + kB;                 // s; the first reflected column before
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int pr = tid >> 3, pk = tid & 7;   // product thread: row pr, columns 4 pk .. 4 pk + 3
+    const int pr = tid / kBRow, pk = tid % kBRow;   // product thread: row pr, columns kBCol pk ..
     const int n = a.n;
     cdf* A = a.A;
     auto at = [&](int r, int c) -> cdf* { return A + (size_t)c * n + r; };
@@ -682,8 +650,7 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
                         ok = true;
                         break;
                     }
-                    if ((it & 63) == 63 && *(volatile int*)a.err) break;
-                    if (it > 4096) __nanosleep(32);
+                    if ((it & 255) == 255 && *(volatile int*)a.err) break;
                 }
                 if (!ok) atomicExch(a.err, 1);
             }
@@ -717,9 +684,8 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
                 vs[lane] = vl;
                 if (lane < len) *at(p + lane, i) = lane == 0 ? make_float4(beta.x, beta.y, 0.f, 0.f) : cdf_zero();
             }
-            __threadfence();
             __syncthreads();
-            if (tid == 0) atomicExch(a.prog + i, 1);
+            if (tid == 0) st_release_gpu(a.prog + i, 1);
         }
         for (int t = 0;; ++t) {
             const int p = i + 1 + kB * t;
@@ -728,7 +694,7 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
             const bool next = q <= n - 2;
             // L_t
             if (!wait_prev(i, t + 3)) return;
-            for (int e = tid; e < kB * kB; e += kT2) {
+            for (int e = tid; e < kB * kB; e += kBT) {
                 const int r = e & 31, c = e >> 5;
                 if (r >= c && r < len) D[r * S + c] = __ldcg(at(p + r, p + c));
                 if (r < lenb && c < len) Bb[r * S + c] = __ldcg(at(q + r, p + c));
@@ -739,20 +705,22 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
             az.zero();
             as.zero();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = 4 * pk + u;
+            for (int u = 0; u < kBCol; ++u) {
+                const int c = kBCol * pk + u;
                 const cdf vc = shfl_cdf(vl, c);
                 if (pr < len && c < len) ay.mac(pr >= c ? D[pr * S + c] : conjc(D[c * S + pr]), vc);
                 if (pr < lenb && c < len) az.mac(Bb[pr * S + c], vc);
                 if (t > 0 && c < len) as.dot(vc, Lb[c * S + pr]);   // column pr of L, rows c
             }
-            const cdf yr = group8_sum(ay.get()), zr = group8_sum(az.get()), sr = group8_sum(as.get());
+            const cdf yr = group_sum<kBRow>(ay.get()), zr = group_sum<kBRow>(az.get()),
+                      sr = group_sum<kBRow>(as.get());
             if (pk == 0) {
                 ys[pr] = yr;
                 zs[pr] = cdf_mul(tau, zr);
                 ss[pr] = sr;
             }
             __syncthreads();
+            const cdf mct = negc(conjc(tau));
             if (wid == 0) {   // mu = Re v^H y, w = tau y - |tau|^2 mu / 2 v
                 float m0 = 0.f, m1 = 0.f;
                 const cdf yy = ys[lane];
@@ -768,27 +736,29 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
                 __syncwarp();
                 ys[lane] = lane < len ? cdf_fma(cdf_mul(tau, yy), make_float4(cf.x, cf.y, 0.f, 0.f), vl) : cdf_zero();
             }
-            __syncthreads();
-            const cdf mct = negc(conjc(tau));
-            for (int e = tid; e < kB * kB; e += kT2) {
+            // the block below and the left block need only z, s and v: updated while warp 0 forms w
+            for (int e = tid; e < kB * kB; e += kBT) {
                 const int r = e & 31, c = e >> 5;
-                if (c <= r && r < len) D[r * S + c] = cdf_rank2(D[r * S + c], vs[r], ys[r], ys[c], vs[c]);
                 if (r < lenb && c < len) Bb[r * S + c] = cdf_fma(Bb[r * S + c], negc(zs[r]), conjc(vs[c]));
                 if (t > 0 && r < len && c >= 1) Lb[r * S + c] = cdf_fma(Lb[r * S + c], cdf_mul(mct, vs[r]), ss[c]);
             }
             __syncthreads();
+            for (int e = tid; e < kB * kB; e += kBT) {
+                const int r = e & 31, c = e >> 5;
+                if (c <= r && r < len) D[r * S + c] = cdf_rank2(D[r * S + c], vs[r], ys[r], ys[c], vs[c]);
+            }
+            __syncthreads();
             // write back: D (lower), the left block (its column 0 went out with R_t), the block
             // below when no task follows
-            for (int e = tid; e < kB * kB; e += kT2) {
+            for (int e = tid; e < kB * kB; e += kBT) {
                 const int r = e & 31, c = e >> 5;
                 if (c <= r && r < len) *at(p + r, p + c) = D[r * S + c];
                 if (t > 0 && r < len && c >= 1) *at(p + r, p - kB + c) = Lb[r * S + c];
                 if (!next && r < lenb && c < len) *at(q + r, p + c) = Bb[r * S + c];
             }
             if (!next) {
-                __threadfence();
                 __syncthreads();
-                if (tid == 0) atomicExch(a.prog + i, kSweepDone);
+                if (tid == 0) st_release_gpu(a.prog + i, kSweepDone);
                 break;
             }
             // R_{t+1}: the first column of the block below (rows q .. qb - 1)
@@ -800,9 +770,8 @@ __global__ void __launch_bounds__(kT2, 1) bulge_kernel(BulgeArgs a) {
                 Bb[lane * S] = xo;
                 if (lane < lenb) *at(q + lane, p) = xo;
             }
-            __threadfence();
             __syncthreads();
-            if (tid == 0) atomicExch(a.prog + i, t + 2);
+            if (tid == 0) st_release_gpu(a.prog + i, t + 2);
             cdf* tmp = Lb;   // the block below becomes the next task's left block
             Lb = Bb;
             Bb = tmp;
@@ -994,7 +963,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
         BSE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * n, st));
         BSE_CUDA(cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBulgeSmem));
         int per_sm = 0;
-        BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulge_kernel, kT2, kBulgeSmem));
+        BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulge_kernel, kBT, kBulgeSmem));
         if (per_sm < 1) return fail(BSE_EUNSUPPORTED, "bulge-chasing kernel cannot be resident");
         const int G = std::min(sms, n - 2);
         BulgeArgs ba;
@@ -1004,7 +973,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
         ba.err = err;
         ba.spin = spin;
         void* bargs[] = {&ba};
-        BSE_CUDA(cudaLaunchCooperativeKernel((const void*)bulge_kernel, dim3(G), dim3(kT2), bargs, kBulgeSmem, st));
+        BSE_CUDA(cudaLaunchCooperativeKernel((const void*)bulge_kernel, dim3(G), dim3(kBT), bargs, kBulgeSmem, st));
         note_launch();
     }
     band_extract_kernel<<<(unsigned)((n + kT2 - 1) / kT2), kT2, 0, st>>>(A, n, d, e);
