@@ -118,17 +118,37 @@ __global__ void h0_matvec_kernel(const cdf* __restrict__ A, int n, const double2
     if (lane == 0) y[i] = s;
 }
 
-// mu = v^H y, then v and w as double-float vectors (one block)
+// v and w as double-float vectors (one block).  H0 is unchanged by v -> v / |v|,
+// beta -> beta |v|^2, which keeps every product in range whatever the size of the start
+// vector (a nearly dark block has |v| of rounding size and beta ~ 1 / |v|^2); then
+// mu = v^H y and w = beta y - beta^2 mu / 2 v with y = A v scaled the same way.
 __global__ void h0_vectors_kernel(const double2* __restrict__ v0, const double* __restrict__ beta0, const cdf* y,
                                   int n, cdf* v, cdf* w) {
+    __shared__ double s_d[kW2];
     __shared__ float2 s_part[kW2];
-    __shared__ float2 s_c;
+    __shared__ float2 s_c, s_b;
+    __shared__ double s_sv;
     const int tid = threadIdx.x;
+    double nv = 0.0;
+    for (int r = tid; r < n; r += blockDim.x) nv += v0[r].x * v0[r].x + v0[r].y * v0[r].y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    if ((tid & 31) == 0) s_d[tid >> 5] = nv;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_d[k];
+        s_sv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        s_b = df_from(*beta0 * t);   // beta |v|^2
+    }
+    __syncthreads();
+    const double sv = s_sv;
     float s = 0.f, lo = 0.f;
     for (int r = tid; r < n; r += blockDim.x) {
-        const cdf a = cdf_from(v0[r]), b = y[r];
-        df_acc(s, lo, a.x, a.y, b.x, b.y);   // Re(conj(a) b)
-        df_acc(s, lo, a.z, a.w, b.z, b.w);
+        const cdf a = cdf_from(make_double2(v0[r].x * sv, v0[r].y * sv)), b = y[r];
+        const float2 br = df_mul(make_float2(b.x, b.y), df_from(sv)), bi = df_mul(make_float2(b.z, b.w), df_from(sv));
+        df_acc(s, lo, a.x, a.y, br.x, br.y);   // Re(conj(a) b)
+        df_acc(s, lo, a.z, a.w, bi.x, bi.y);
     }
     float2 t = warp_sum_df(df_fin(s, lo));
     if ((tid & 31) == 0) s_part[tid >> 5] = t;
@@ -136,16 +156,17 @@ __global__ void h0_vectors_kernel(const double2* __restrict__ v0, const double* 
     if (tid == 0) {
         float2 mu = s_part[0];
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mu = df_add(mu, s_part[k]);
-        const float2 b = df_from(*beta0);
+        const float2 b = s_b;
         s_c = df_mul(df_mul(df_mul(b, b), mu), make_float2(0.5f, 0.f));   // beta^2 mu / 2
     }
     __syncthreads();
-    const float2 b = df_from(*beta0), c = s_c;
+    const float2 b = s_b, c = s_c, svf = df_from(sv);
     for (int r = tid; r < n; r += blockDim.x) {
-        const cdf a = cdf_from(v0[r]), yy = y[r];
+        const cdf a = cdf_from(make_double2(v0[r].x * sv, v0[r].y * sv)), yy = y[r];
         v[r] = a;
-        const float2 wr = df_add(df_mul(b, make_float2(yy.x, yy.y)), df_neg(df_mul(c, make_float2(a.x, a.y))));
-        const float2 wi = df_add(df_mul(b, make_float2(yy.z, yy.w)), df_neg(df_mul(c, make_float2(a.z, a.w))));
+        const float2 yr = df_mul(make_float2(yy.x, yy.y), svf), yi = df_mul(make_float2(yy.z, yy.w), svf);
+        const float2 wr = df_add(df_mul(b, yr), df_neg(df_mul(c, make_float2(a.x, a.y))));
+        const float2 wi = df_add(df_mul(b, yi), df_neg(df_mul(c, make_float2(a.z, a.w))));
         w[r] = make_float4(wr.x, wr.y, wi.x, wi.y);
     }
 }
