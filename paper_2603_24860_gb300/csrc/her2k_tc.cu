@@ -210,170 +210,193 @@ __device__ __forceinline__ float2 her_sum(const uint32_t (&v)[kAcc][8], int j) {
     return df_add(s, make_float2(__uint_as_float(v[4][j]), 0.f));
 }
 
-// Persistent: CTA b takes the tiles [T b / G, T (b + 1) / G) of the column-tile-major
-// order (t = ctl * ntr + rtl).  The X digit stream of a CTA: item j = digit j % 8 of its
-// tile j / 8, in slot j % 3; its copy is the (j / 3)-th completion of mb_full[slot], its
-// MMAs the (j / 3)-th commit to mb_empty[slot].  TMEM column of accumulator c, output
-// column i of the tile: c * 64 + i (real part), c * 64 + 32 + i (imaginary part).
-__global__ void __launch_bounds__(kHThreads, 1) panel_update_tc_kernel(HerArgs a) {
+// mbarrier wait that gives up after `limit` polls or once another role has raised the
+// CTA's abort flag
+__device__ __forceinline__ bool ws_wait(uint64_t* mb, uint32_t parity, long limit, volatile int* abort) {
+    for (long it = 0; it < limit; ++it) {
+        if (tc::mbar_wait(mb, parity, 1)) return true;
+        if ((it & 15) == 15 && *abort) return false;
+    }
+    return false;
+}
+
+// Persistent: CTA b takes the tiles [T b / G, T (b + 1) / G) of the column-tile-major order
+// (t = ctl * ntr + rtl), with warp-specialised roles: warp 4 (one lane) copies a tile's Y
+// digits when its column tile changes (once the MMAs of the previous tile are done) and streams
+// the 8 X digits of each tile through three slots as they free up; warp 5 (one lane) issues the
+// MMAs as operands land, once the epilogue of the previous tile has released TMEM; warps 0-3
+// (a warp per 32 TMEM lanes = rows) read the accumulators back and update A.  X item j = digit
+// j % 8 of tile j / 8 uses slot j % 3 (its copy the (j / 3)-th completion of mb_full[slot], its
+// MMAs the (j / 3)-th commit to mb_empty[slot]); mb_acc and mb_free complete once per tile,
+// mb_y once per Y copy.  TMEM column of accumulator c, output column i of the tile: c * 64 + i
+// (real part), c * 64 + 32 + i (imaginary part).
+constexpr int kHWThreads = 192;
+__global__ void __launch_bounds__(kHWThreads, 1) panel_update_tc_kernel(HerArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* Bs = smem;                                  // 8 digits of the Y tile (both forms)
     unsigned char* As = smem + kBTileBytes;                    // kSlots digit buffers of X tiles
-    __shared__ __align__(8) uint64_t mb_y, mb_full[kSlots], mb_empty[kSlots], mb_acc;
+    __shared__ __align__(8) uint64_t mb_y, mb_full[kSlots], mb_empty[kSlots], mb_acc, mb_free, mb_fin;
     __shared__ uint32_t slot;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         tc::mbar_init(&mb_y, 1);
         tc::mbar_init(&mb_acc, 1);
+        tc::mbar_init(&mb_free, 4);
+        tc::mbar_init(&mb_fin, 1);
         for (int i = 0; i < kSlots; ++i) {
             tc::mbar_init(&mb_full[i], 1);
             tc::mbar_init(&mb_empty[i], 1);
         }
+        s_abort = 0;
     }
     if (warp == 0) tc::tmem_alloc(&slot, kHTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = slot;
+    volatile int* abort = &s_abort;
     const int64_t T = (int64_t)a.ntr * a.ntc;
     const int t_begin = (int)(T * blockIdx.x / gridDim.x), t_end = (int)(T * (blockIdx.x + 1) / gridDim.x);
-    const int nitems = (t_end - t_begin) * kDig;
-    const uint32_t idesc = tc::idesc_f16(kHM, kBN, 1);
-    const uint32_t lbo = 128, sbo = (uint32_t)(kHK / 8) * 128;
-    // a bounded wait; on giving up the awaited operation is still let finish (default limit)
-    auto wait = [&](uint64_t* mb, uint32_t parity) {
-        const bool got = tc::mbar_wait(mb, parity, a.spin);
-        if (!got) tc::mbar_wait(mb, parity, kMbarSpinLimit);
-        return got;
+    const int ntl = t_end - t_begin;
+    auto tile_ct = [&](int tl) { return a.ct0 + (t_begin + tl) / a.ntr; };
+    auto tile_rt = [&](int tl) { return a.rt0 + (t_begin + tl) % a.ntr; };
+    auto fail_now = [&]() {
+        *abort = 1;
+        atomicExch(a.status, 1);
     };
-    auto item_src = [&](int j) {
-        const int t = t_begin + j / kDig;
-        const int rt = a.rt0 + t % a.ntr;
-        return (const unsigned char*)a.Adig + ((size_t)rt * kDig + j % kDig) * kADigBytes;
-    };
-    // state of thread 0 (the issuing thread): stream items copied, landed, committed, retired
-    int issued = 0, landed = 0, committed = 0, retired = 0, ys = 0, accs = 0;
-    auto issue_item = [&](int j) {
-        const int sl = j % kSlots;
-        tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kADigBytes);
-        tc::bulk_g2s(As + sl * kADigBytes, item_src(j), (uint32_t)kADigBytes, &mb_full[sl]);
-        issued = j + 1;
-    };
-    if (tid == 0)
-        for (int j = 0; j < kSlots && j < nitems; ++j) issue_item(j);
-    bool ok = true;
-    int cur_ct = -1;
-    for (int tl = 0; t_begin + tl < t_end && ok; ++tl) {
-        const int t = t_begin + tl;
-        const int rt = a.rt0 + t % a.ntr, ct = a.ct0 + t / a.ntr;
-        // this thread's row of the output tile; its first 8 entries of A load while the MMAs run
-        const int r = rt * kHM + warp * 32 + lane;
-        const bool rlive = r >= a.k0 && r < a.n;
-        auto load_chunk = [&](int c0, cdf* q) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int i = ct * kHN + c0 + j;
-                const cdf* src = a.A + (size_t)i * a.n + r;
-                q[j] = rlive && i >= a.k0 && i < a.n ? (i < a.resident_from ? __ldcs(src) : __ldcg(src))
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        };
-        cdf qa[8], qb[8];
-        load_chunk(0, qa);
-        bool ok0 = true;
-        if (tid == 0) {
-            if (ct != cur_ct) {   // every MMA of the earlier tiles is complete: the Y buffer is free
-                tc::mbar_expect_tx(&mb_y, (uint32_t)kBTileBytes);
-                tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)ct * kBTileBytes, (uint32_t)kBTileBytes, &mb_y);
-                ok0 = wait(&mb_y, (uint32_t)(ys & 1));
-                ++ys;
-            }
-            for (int k = 0; k < kDig && ok0; ++k) {
-                const int j = tl * kDig + k, sl = j % kSlots;
-                ok0 = wait(&mb_full[sl], (uint32_t)((j / kSlots) & 1));
-                landed = j + 1;
-                if (!ok0) break;
-                tc::fence_after();
-                const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kADigBytes), lbo, sbo);
-                for (int m = 0; m + k < kDig; ++m) {
-                    const int g = k + m, acc = g < kExact ? g : kExact;
-                    const bool first = k == 0 && (g < kExact || m == kExact);
-                    const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + m * kBDigBytes), lbo, sbo);
-                    const uint32_t d = tmem + (uint32_t)(acc * kBN);
-#pragma unroll
-                    for (int ks = 0; ks < kHK / 16; ++ks)   // 16 K per MMA: 256 bytes, 16 descriptor units
-                        tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc, (first && ks == 0) ? 0u : 1u);
+    if (warp == 4) {
+        if (lane == 0) {   // producer
+            int last[kSlots] = {-1, -1, -1}, ys = 0, cur_ct = -1;
+            bool ok = true;
+            for (int tl = 0; tl < ntl && ok; ++tl) {
+                const int ct = tile_ct(tl), rt = tile_rt(tl);
+                if (ct != cur_ct) {   // the MMAs of the previous tile are done: the Y buffer is free
+                    if (tl > 0 && !(ok = ws_wait(&mb_acc, (uint32_t)((tl - 1) & 1), a.spin, abort))) break;
+                    tc::mbar_expect_tx(&mb_y, (uint32_t)kBTileBytes);
+                    tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)ct * kBTileBytes, (uint32_t)kBTileBytes,
+                                 &mb_y);
+                    ++ys;
+                    cur_ct = ct;
                 }
-                tc::mma_commit(&mb_empty[sl]);
-                committed = j + 1;
-                if (j >= 1) {   // the MMAs of item j - 1 done: its slot takes item j + 2
-                    ok0 = wait(&mb_empty[(j - 1) % kSlots], (uint32_t)(((j - 1) / kSlots) & 1));
-                    retired = j;
-                    if (ok0 && j + 2 < nitems) issue_item(j + 2);
+                for (int k = 0; k < kDig; ++k) {
+                    const int j = tl * kDig + k, sl = j % kSlots;
+                    if (j >= kSlots &&
+                        !(ok = ws_wait(&mb_empty[sl], (uint32_t)(((j - kSlots) / kSlots) & 1), a.spin, abort)))
+                        break;
+                    tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kADigBytes);
+                    tc::bulk_g2s(As + sl * kADigBytes,
+                                 (const unsigned char*)a.Adig + ((size_t)rt * kDig + k) * kADigBytes,
+                                 (uint32_t)kADigBytes, &mb_full[sl]);
+                    last[sl] = j;
                 }
             }
-            if (ok0) {
-                tc::mma_commit(&mb_acc);
-                ++accs;
-            }
-            cur_ct = ct;
+            if (!ok) fail_now();
+            for (int sl = 0; sl < kSlots; ++sl)
+                if (last[sl] >= 0) tc::mbar_wait(&mb_full[sl], (uint32_t)((last[sl] / kSlots) & 1), kMbarSpinLimit);
+            if (ys > 0) tc::mbar_wait(&mb_y, (uint32_t)((ys - 1) & 1), kMbarSpinLimit);
         }
-        ok = __syncthreads_and(tid != 0 || ok0) != 0;
-        if (!ok) break;
-        // the tile's accumulators are complete
-        ok = __syncthreads_and(wait(&mb_acc, (uint32_t)(tl & 1))) != 0;
-        if (!ok) break;
-        tc::fence_after();
-        // epilogue, 8 columns at a time (the next 8 entries of A loading meanwhile)
-        const int er = rlive ? __ldg(a.ex + r) : 0;
+    } else if (warp == 5) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = tc::idesc_f16(kHM, kBN, 1);
+            const uint32_t lbo = 128, sbo = (uint32_t)(kHK / 8) * 128;
+            int yw = 0, cur_ct = -1;
+            bool ok = true;
+            for (int tl = 0; tl < ntl && ok; ++tl) {
+                const int ct = tile_ct(tl);
+                if (ct != cur_ct) {
+                    if (!(ok = ws_wait(&mb_y, (uint32_t)(yw & 1), a.spin, abort))) break;
+                    ++yw;
+                    cur_ct = ct;
+                }
+                if (tl > 0 && !(ok = ws_wait(&mb_free, (uint32_t)((tl - 1) & 1), a.spin, abort))) break;
+                tc::fence_after();
+                for (int k = 0; k < kDig; ++k) {
+                    const int j = tl * kDig + k, sl = j % kSlots;
+                    if (!(ok = ws_wait(&mb_full[sl], (uint32_t)((j / kSlots) & 1), a.spin, abort))) break;
+                    tc::fence_after();
+                    const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kADigBytes), lbo, sbo);
+                    for (int m = 0; m + k < kDig; ++m) {
+                        const int g = k + m, acc = g < kExact ? g : kExact;
+                        const bool first = k == 0 && (g < kExact || m == kExact);
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + m * kBDigBytes), lbo, sbo);
+                        const uint32_t d = tmem + (uint32_t)(acc * kBN);
+#pragma unroll
+                        for (int ks = 0; ks < kHK / 16; ++ks)   // 16 K per MMA: 256 bytes, 16 descriptor units
+                            tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc,
+                                        (first && ks == 0) ? 0u : 1u);
+                    }
+                    tc::mma_commit(&mb_empty[sl]);
+                }
+                if (ok) tc::mma_commit(&mb_acc);
+            }
+            if (!ok) fail_now();
+            tc::mma_commit(&mb_fin);   // every MMA issued has completed before TMEM is released
+            tc::mbar_wait(&mb_fin, 0u, kMbarSpinLimit);
+        }
+    } else {   // epilogue warps 0-3
         const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-        auto finish_chunk = [&](int c0, const cdf* q) {
-            uint32_t vr[kAcc][8], vi[kAcc][8];
-#pragma unroll
-            for (int c = 0; c < kAcc; ++c) {
-                tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + c0), vr[c]);
-                tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + kHN + c0), vi[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < kAcc; ++c) {
-                tc::tmem_ld_wait(vr[c]);
-                tc::tmem_ld_wait(vi[c]);
-            }
-            if (rlive)
+        for (int tl = 0; tl < ntl; ++tl) {
+            const int ct = tile_ct(tl), rt = tile_rt(tl);
+            const int r = rt * kHM + warp * 32 + lane;
+            const bool rlive = r >= a.k0 && r < a.n;
+            auto load_chunk = [&](int c0, cdf* q) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int i = ct * kHN + c0 + j;
-                    if (i < a.k0 || i >= a.n) continue;
-                    const float sc = ldexpf(1.f, er + __ldg(a.fy + i) - 14);
-                    const float2 sr = her_sum(vr, j), si = her_sum(vi, j);
-                    const float2 re = df_add(make_float2(q[j].x, q[j].y), make_float2(-sr.x * sc, -sr.y * sc));
-                    const float2 im = df_add(make_float2(q[j].z, q[j].w), make_float2(-si.x * sc, -si.y * sc));
-                    const cdf out = make_float4(re.x, re.y, im.x, im.y);
-                    if (i < a.resident_from)
-                        __stcs(a.A + (size_t)i * a.n + r, out);
-                    else
-                        a.A[(size_t)i * a.n + r] = out;
+                    const cdf* src = a.A + (size_t)i * a.n + r;
+                    q[j] = rlive && i >= a.k0 && i < a.n ? (i < a.resident_from ? __ldcs(src) : __ldcg(src))
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-        };
-        load_chunk(8, qb);
-        finish_chunk(0, qa);
-        load_chunk(16, qa);
-        finish_chunk(8, qb);
-        load_chunk(24, qb);
-        finish_chunk(16, qa);
-        finish_chunk(24, qb);
-        tc::fence_before();
-        __syncthreads();   // TMEM is reused by the next tile
-        tc::fence_after();
-    }
-    if (!ok && tid == 0) {
-        // a wait gave up: let every copy and MMA still in flight finish (the default limit)
-        // before the CTA frees its tensor memory and exits
-        for (int j = landed; j < issued; ++j) tc::mbar_wait(&mb_full[j % kSlots], (uint32_t)((j / kSlots) & 1), kMbarSpinLimit);
-        for (int j = retired; j < committed; ++j)
-            tc::mbar_wait(&mb_empty[j % kSlots], (uint32_t)((j / kSlots) & 1), kMbarSpinLimit);
-        atomicExch(a.status, 1);
+            };
+            cdf qa[8], qb[8];
+            load_chunk(0, qa);   // loads while the MMAs run
+            if (!ws_wait(&mb_acc, (uint32_t)(tl & 1), a.spin, abort)) {
+                fail_now();
+                break;
+            }
+            tc::fence_after();
+            const int er = rlive ? __ldg(a.ex + r) : 0;
+            auto finish_chunk = [&](int c0, const cdf* q) {
+                uint32_t vr[kAcc][8], vi[kAcc][8];
+#pragma unroll
+                for (int c = 0; c < kAcc; ++c) {
+                    tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + c0), vr[c]);
+                    tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(c * kBN + kHN + c0), vi[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < kAcc; ++c) {
+                    tc::tmem_ld_wait(vr[c]);
+                    tc::tmem_ld_wait(vi[c]);
+                }
+                if (rlive)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int i = ct * kHN + c0 + j;
+                        if (i < a.k0 || i >= a.n) continue;
+                        const float sc = ldexpf(1.f, er + __ldg(a.fy + i) - 14);
+                        const float2 sr = her_sum(vr, j), si = her_sum(vi, j);
+                        const float2 re = df_add(make_float2(q[j].x, q[j].y), make_float2(-sr.x * sc, -sr.y * sc));
+                        const float2 im = df_add(make_float2(q[j].z, q[j].w), make_float2(-si.x * sc, -si.y * sc));
+                        const cdf out = make_float4(re.x, re.y, im.x, im.y);
+                        if (i < a.resident_from)
+                            __stcs(a.A + (size_t)i * a.n + r, out);
+                        else
+                            a.A[(size_t)i * a.n + r] = out;
+                    }
+            };
+            load_chunk(8, qb);
+            finish_chunk(0, qa);
+            load_chunk(16, qa);
+            finish_chunk(8, qb);
+            load_chunk(24, qb);
+            finish_chunk(16, qa);
+            finish_chunk(24, qb);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&mb_free)) : "memory");
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -434,7 +457,7 @@ int launch_panel_update_tc(cdf* A, int64_t n, int k0, int resident_from, const c
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t ntiles = (int64_t)h.ntr * h.ntc;
     const int grid = (int)std::min<int64_t>(sms, ntiles);
-    panel_update_tc_kernel<<<grid, kHThreads, kHerSmem, st>>>(h);
+    panel_update_tc_kernel<<<grid, kHWThreads, kHerSmem, st>>>(h);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     return BSE_OK;

@@ -38,7 +38,6 @@ constexpr int kZDig = 8;
 constexpr int kZExact = 4;
 constexpr int kZAcc = kZExact + 1;
 constexpr int kZSlots = 3;
-constexpr int kZThreads = 128;
 constexpr uint32_t kZTmemCols = 512;                       // kZAcc x kZN = 320 used
 constexpr size_t kZADig = (size_t)kZM * kZK * 2;           // one digit of an A22 tile chunk (32 KB)
 constexpr size_t kZBDig = (size_t)kZN * kZK * 2;           // one digit of a V chunk, both forms (16 KB)
@@ -210,150 +209,166 @@ __device__ __forceinline__ float2 zsum5(const uint32_t (&v)[kZAcc][8], int j) {
     return df_add(s, make_float2(__uint_as_float(v[4][j]), 0.f));
 }
 
-// CTA (rt = blockIdx.x, split = blockIdx.y) takes chunks [nch s / S, nch (s + 1) / S).  The
-// X stream: item j = digit j % 8 of chunk c_lo + j / 8, in slot j % 3 (copy = the (j / 3)-th
-// completion of mb_full[slot], MMAs = the (j / 3)-th commit to mb_empty[slot]); the V chunk
-// of the next chunk is fetched once the MMAs of the current one are done, during its drain.
-__global__ void __launch_bounds__(kZThreads, 1) zgemm_tc_kernel(ZArgs a) {
+// mbarrier wait that gives up after `limit` polls or once another role has raised the
+// CTA's abort flag
+__device__ __forceinline__ bool ws_wait(uint64_t* mb, uint32_t parity, long limit, volatile int* abort) {
+    for (long it = 0; it < limit; ++it) {
+        if (tc::mbar_wait(mb, parity, 1)) return true;
+        if ((it & 15) == 15 && *abort) return false;
+    }
+    return false;
+}
+
+// CTA (rt = blockIdx.x, split = blockIdx.y) takes chunks [nch s / S, nch (s + 1) / S), with
+// warp-specialised roles: warp 4 (one lane) copies the V chunk into its buffer once the MMAs of
+// the previous chunk are done and streams the 8 digits of the A22 chunk through three slots as
+// they free up; warp 5 (one lane) issues the MMAs as operands land, once the drain of the previous
+// chunk has released TMEM; warps 0-3 drain each chunk's accumulators (a warp per 32 TMEM lanes =
+// rows) into double-float registers.  X item j = digit j % 8 of chunk c_lo + j / 8 uses slot
+// j % 3 (its copy the (j / 3)-th completion of mb_full[slot], its MMAs the (j / 3)-th commit to
+// mb_empty[slot]); one completion of mb_y, mb_acc and mb_free per chunk.
+constexpr int kZWThreads = 192;
+__global__ void __launch_bounds__(kZWThreads, 1) zgemm_tc_kernel(ZArgs a) {
     extern __shared__ __align__(1024) unsigned char zsm_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)zsm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* Bs = smem;
     unsigned char* As = smem + kZBChunk;
-    __shared__ __align__(8) uint64_t mb_y, mb_full[kZSlots], mb_empty[kZSlots], mb_acc;
+    __shared__ __align__(8) uint64_t mb_y, mb_full[kZSlots], mb_empty[kZSlots], mb_acc, mb_free, mb_fin;
     __shared__ uint32_t slot;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         tc::mbar_init(&mb_y, 1);
         tc::mbar_init(&mb_acc, 1);
+        tc::mbar_init(&mb_free, 4);
+        tc::mbar_init(&mb_fin, 1);
         for (int i = 0; i < kZSlots; ++i) {
             tc::mbar_init(&mb_full[i], 1);
             tc::mbar_init(&mb_empty[i], 1);
         }
+        s_abort = 0;
     }
     if (warp == 0) tc::tmem_alloc(&slot, kZTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = slot;
+    volatile int* abort = &s_abort;
     const int rt = blockIdx.x, sp = blockIdx.y;
     const int c_lo = (int)((int64_t)a.nch * sp / a.nsplit), c_hi = (int)((int64_t)a.nch * (sp + 1) / a.nsplit);
-    const int nitems = (c_hi - c_lo) * kZDig;
-    const uint32_t idesc = tc::idesc_f16(kZM, kZN, 1);
-    const uint32_t lbo = 128, sbo = (uint32_t)(kZK / 8) * 128;
-    auto wait = [&](uint64_t* mb, uint32_t parity) {
-        const bool got = tc::mbar_wait(mb, parity, a.spin);
-        if (!got) tc::mbar_wait(mb, parity, kMbarSpinLimit);
-        return got;
-    };
-    auto item_src = [&](int j) {
-        const int c = c_lo + j / kZDig;
-        return (const unsigned char*)a.Adig + (((size_t)rt * a.nch + c) * kZDig + j % kZDig) * kZADig;
-    };
-    int issued = 0, landed = 0, committed = 0, retired = 0, ys = 0, yw = 0;
-    auto issue_item = [&](int j) {
-        const int sl = j % kZSlots;
-        tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kZADig);
-        tc::bulk_g2s(As + sl * kZADig, item_src(j), (uint32_t)kZADig, &mb_full[sl]);
-        issued = j + 1;
-    };
-    auto issue_y = [&](int c) {
-        tc::mbar_expect_tx(&mb_y, (uint32_t)kZBChunk);
-        tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)c * kZBChunk, (uint32_t)kZBChunk, &mb_y);
-        ++ys;
-    };
-    if (tid == 0 && nitems > 0) {
-        issue_y(c_lo);
-        for (int j = 0; j < kZSlots && j < nitems; ++j) issue_item(j);
-    }
-    const int r = rt * kZM + warp * 32 + lane;   // this thread's row (TMEM lane)
-    const bool rlive = r < a.m;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    float zr[kZL][2], zi[kZL][2];   // double-float accumulators of Z[r][l]
-#pragma unroll
-    for (int l = 0; l < kZL; ++l) zr[l][0] = zr[l][1] = zi[l][0] = zi[l][1] = 0.f;
-    bool ok = true;
-    for (int cl = 0; c_lo + cl < c_hi && ok; ++cl) {
-        const int c = c_lo + cl;
-        bool ok0 = true;
-        if (tid == 0) {
-            ok0 = wait(&mb_y, (uint32_t)(yw & 1));
-            ++yw;
-            for (int k = 0; k < kZDig && ok0; ++k) {
-                const int j = cl * kZDig + k, sl = j % kZSlots;
-                ok0 = wait(&mb_full[sl], (uint32_t)((j / kZSlots) & 1));
-                landed = j + 1;
-                if (!ok0) break;
-                tc::fence_after();
-                const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kZADig), lbo, sbo);
-                for (int mm = 0; mm + k < kZDig; ++mm) {
-                    const int g = k + mm, acc = g < kZExact ? g : kZExact;
-                    const bool first = k == 0 && (g < kZExact || mm == kZExact);
-                    const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + mm * kZBDig), lbo, sbo);
-                    const uint32_t d = tmem + (uint32_t)(acc * kZN);
-#pragma unroll
-                    for (int ks = 0; ks < kZK / 16; ++ks)
-                        tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc,
-                                    (first && ks == 0) ? 0u : 1u);
-                }
-                tc::mma_commit(&mb_empty[sl]);
-                committed = j + 1;
-                if (j >= 1) {
-                    ok0 = wait(&mb_empty[(j - 1) % kZSlots], (uint32_t)(((j - 1) / kZSlots) & 1));
-                    retired = j;
-                    if (ok0 && j + 2 < nitems) issue_item(j + 2);
-                }
-            }
-            if (ok0) tc::mma_commit(&mb_acc);
-        }
-        ok = __syncthreads_and(tid != 0 || ok0) != 0;
-        if (!ok) break;
-        ok = __syncthreads_and(wait(&mb_acc, (uint32_t)(cl & 1))) != 0;
-        if (!ok) break;
-        tc::fence_after();
-        // the V chunk buffer is free: fetch the next chunk's during the drain
-        if (tid == 0 && c + 1 < c_hi) issue_y(c + 1);
-        // drain: Z[r][l] += 2^(e_r + f_l - 14) (G_0 + .. + G_3 + G_rest), eight columns at a time
-        const int er = rlive ? __ldg(a.ex + (size_t)c * a.nrt * kZM + r) : 0;
-#pragma unroll
-        for (int c0 = 0; c0 < kZL; c0 += 8) {
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {   // real parts (columns c0..), then imaginary (32 + c0..)
-                uint32_t v[kZAcc][8];
-#pragma unroll
-                for (int q = 0; q < kZAcc; ++q)
-                    tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(q * kZN + part * kZL + c0), v[q]);
-#pragma unroll
-                for (int q = 0; q < kZAcc; ++q) tc::tmem_ld_wait(v[q]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float sc = ldexpf(1.f, er + __ldg(a.fy + c * kZL + c0 + j) - 14);
-                    const float2 sv = zsum5(v, j);
-                    float(&acc)[2] = part == 0 ? zr[c0 + j] : zi[c0 + j];
-                    const float2 nv = df_add(make_float2(acc[0], acc[1]), make_float2(sv.x * sc, sv.y * sc));
-                    acc[0] = nv.x;
-                    acc[1] = nv.y;
-                }
-            }
-        }
-        tc::fence_before();
-        __syncthreads();   // TMEM is reused by the next chunk
-        tc::fence_after();
-    }
-    if (ok && rlive) {
-        cdf* out = a.zpart + ((size_t)sp * a.m + r) * kZL;
-#pragma unroll
-        for (int l = 0; l < kZL; ++l) out[l] = make_float4(zr[l][0], zr[l][1], zi[l][0], zi[l][1]);
-    }
-    if (!ok && tid == 0) {
-        for (int j = landed; j < issued; ++j)
-            tc::mbar_wait(&mb_full[j % kZSlots], (uint32_t)((j / kZSlots) & 1), kMbarSpinLimit);
-        for (int j = retired; j < committed; ++j)
-            tc::mbar_wait(&mb_empty[j % kZSlots], (uint32_t)((j / kZSlots) & 1), kMbarSpinLimit);
-        while (yw < ys) {
-            tc::mbar_wait(&mb_y, (uint32_t)(yw & 1), kMbarSpinLimit);
-            ++yw;
-        }
+    const int nchunk = c_hi - c_lo;
+    auto fail_now = [&]() {
+        *abort = 1;
         atomicExch(a.status, 1);
+    };
+    if (warp == 4) {
+        if (lane == 0) {   // producer
+            int last[kZSlots] = {-1, -1, -1}, ys = 0;
+            bool ok = true;
+            for (int cl = 0; cl < nchunk && ok; ++cl) {
+                if (cl > 0 && !(ok = ws_wait(&mb_acc, (uint32_t)((cl - 1) & 1), a.spin, abort))) break;
+                tc::mbar_expect_tx(&mb_y, (uint32_t)kZBChunk);
+                tc::bulk_g2s(Bs, (const unsigned char*)a.Bdig + (size_t)(c_lo + cl) * kZBChunk, (uint32_t)kZBChunk,
+                             &mb_y);
+                ++ys;
+                for (int k = 0; k < kZDig; ++k) {
+                    const int j = cl * kZDig + k, sl = j % kZSlots;
+                    if (j >= kZSlots && !(ok = ws_wait(&mb_empty[sl], (uint32_t)(((j - kZSlots) / kZSlots) & 1),
+                                                       a.spin, abort)))
+                        break;
+                    tc::mbar_expect_tx(&mb_full[sl], (uint32_t)kZADig);
+                    tc::bulk_g2s(As + sl * kZADig,
+                                 (const unsigned char*)a.Adig + (((size_t)rt * a.nch + c_lo + cl) * kZDig + k) * kZADig,
+                                 (uint32_t)kZADig, &mb_full[sl]);
+                    last[sl] = j;
+                }
+            }
+            if (!ok) fail_now();
+            // every copy issued has landed before the CTA may leave
+            for (int sl = 0; sl < kZSlots; ++sl)
+                if (last[sl] >= 0) tc::mbar_wait(&mb_full[sl], (uint32_t)((last[sl] / kZSlots) & 1), kMbarSpinLimit);
+            if (ys > 0) tc::mbar_wait(&mb_y, (uint32_t)((ys - 1) & 1), kMbarSpinLimit);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = tc::idesc_f16(kZM, kZN, 1);
+            const uint32_t lbo = 128, sbo = (uint32_t)(kZK / 8) * 128;
+            bool ok = true;
+            for (int cl = 0; cl < nchunk && ok; ++cl) {
+                if (!(ok = ws_wait(&mb_y, (uint32_t)(cl & 1), a.spin, abort))) break;
+                if (cl > 0 && !(ok = ws_wait(&mb_free, (uint32_t)((cl - 1) & 1), a.spin, abort))) break;
+                tc::fence_after();
+                for (int k = 0; k < kZDig; ++k) {
+                    const int j = cl * kZDig + k, sl = j % kZSlots;
+                    if (!(ok = ws_wait(&mb_full[sl], (uint32_t)((j / kZSlots) & 1), a.spin, abort))) break;
+                    tc::fence_after();
+                    const uint64_t ad = tc::smem_desc(tc::smem_u32(As + sl * kZADig), lbo, sbo);
+                    for (int mm = 0; mm + k < kZDig; ++mm) {
+                        const int g = k + mm, acc = g < kZExact ? g : kZExact;
+                        const bool first = k == 0 && (g < kZExact || mm == kZExact);
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + mm * kZBDig), lbo, sbo);
+                        const uint32_t d = tmem + (uint32_t)(acc * kZN);
+#pragma unroll
+                        for (int ks = 0; ks < kZK / 16; ++ks)
+                            tc::mma_f16(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc,
+                                        (first && ks == 0) ? 0u : 1u);
+                    }
+                    tc::mma_commit(&mb_empty[sl]);
+                }
+                if (ok) tc::mma_commit(&mb_acc);
+            }
+            if (!ok) fail_now();
+            // every MMA issued has completed before TMEM is released
+            tc::mma_commit(&mb_fin);
+            tc::mbar_wait(&mb_fin, 0u, kMbarSpinLimit);
+        }
+    } else {   // drain warps 0-3
+        const int r = rt * kZM + warp * 32 + lane;
+        const bool rlive = r < a.m;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        float zr[kZL][2], zi[kZL][2];   // double-float accumulators of Z[r][l]
+#pragma unroll
+        for (int l = 0; l < kZL; ++l) zr[l][0] = zr[l][1] = zi[l][0] = zi[l][1] = 0.f;
+        bool ok = true;
+        for (int cl = 0; cl < nchunk; ++cl) {
+            const int c = c_lo + cl;
+            if (!ws_wait(&mb_acc, (uint32_t)(cl & 1), a.spin, abort)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after();
+            const int er = rlive ? __ldg(a.ex + (size_t)c * a.nrt * kZM + r) : 0;
+#pragma unroll
+            for (int c0 = 0; c0 < kZL; c0 += 8) {
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {   // real parts (columns c0..), then imaginary (32 + c0..)
+                    uint32_t v[kZAcc][8];
+#pragma unroll
+                    for (int q = 0; q < kZAcc; ++q)
+                        tc::tmem_ld8_async(tmem + lane_off + (uint32_t)(q * kZN + part * kZL + c0), v[q]);
+#pragma unroll
+                    for (int q = 0; q < kZAcc; ++q) tc::tmem_ld_wait(v[q]);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float sc = ldexpf(1.f, er + __ldg(a.fy + c * kZL + c0 + j) - 14);
+                        const float2 sv = zsum5(v, j);
+                        float(&acc)[2] = part == 0 ? zr[c0 + j] : zi[c0 + j];
+                        const float2 nv = df_add(make_float2(acc[0], acc[1]), make_float2(sv.x * sc, sv.y * sc));
+                        acc[0] = nv.x;
+                        acc[1] = nv.y;
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&mb_free)) : "memory");
+        }
+        if (!ok) fail_now();
+        if (ok && rlive) {
+            cdf* out = a.zpart + ((size_t)sp * a.m + r) * kZL;
+#pragma unroll
+            for (int l = 0; l < kZL; ++l) out[l] = make_float4(zr[l][0], zr[l][1], zi[l][0], zi[l][1]);
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -407,7 +422,7 @@ int launch_zgemm_tc(const cdf* A, int64_t n64, int r1, int m, const cdf* V, void
     z.status = status;
     z.spin = wait_limit(wait_polls, kMbarSpinLimit);
     BSE_CUDA(cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kZSmem));
-    zgemm_tc_kernel<<<dim3(nrt, nsplit), kZThreads, kZSmem, st>>>(z);
+    zgemm_tc_kernel<<<dim3(nrt, nsplit), kZWThreads, kZSmem, st>>>(z);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     return BSE_OK;
