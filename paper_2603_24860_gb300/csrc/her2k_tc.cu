@@ -48,6 +48,7 @@
 #include <algorithm>
 
 #include "dfloat.h"
+#include "digits.h"
 #include "grid_sync.h"
 #include "internal.h"
 #include "tc_ptx.h"
@@ -60,7 +61,7 @@ constexpr int kHM = 128;           // rows of an output tile (TMEM lanes, M of t
 constexpr int kHN = 32;            // complex output columns of a tile
 constexpr int kBN = 64;            // N of the MMA: the tile's rows of [Yr Yi], then of [-Yi Yr]
 constexpr int kHK = 128;           // K of the real GEMM (64 complex terms: 32 reflectors, V and W)
-constexpr int kDig = 8;            // digits per operand
+constexpr int kDig = kDigits;      // digits per operand
 constexpr int kExact = 4;          // digit-pair groups g < kExact accumulate exactly, one accumulator each
 constexpr int kAcc = kExact + 1;   // accumulators per tile (the last one holds the groups g >= kExact)
 constexpr int kSlots = 3;          // ring of X digit buffers
@@ -71,47 +72,25 @@ constexpr size_t kBDigBytes = (size_t)kBN * kHK * 2;       // one digit of a Y t
 constexpr size_t kBTileBytes = kDig * kBDigBytes;          // the 8 digits of a Y tile (128 KB)
 constexpr size_t kHerSmem = kBTileBytes + kSlots * kADigBytes + 1024;
 
-__device__ __forceinline__ double cdf_re(cdf z) { return (double)z.x + (double)z.y; }
-__device__ __forceinline__ double cdf_im(cdf z) { return (double)z.z + (double)z.w; }
-
-// balanced base-128 digits of q (|q| <= 2^56): d_0 .. d_7, weights 2^49 .. 2^0
-__device__ __forceinline__ void digits8(long long q, float* d) {
-#pragma unroll
-    for (int k = 0; k < kDig; ++k) {
-        const int sh = 49 - 7 * k;
-        long long dk;
-        if (sh > 0) {
-            dk = (q + (1ll << (sh - 1))) >> sh;   // nearest integer (arithmetic shift floors)
-            q -= dk << sh;
-        } else {
-            dk = q;
-        }
-        d[k] = (float)dk;
-    }
-}
-
-// 2^p as a double (p within the normal range)
-__device__ __forceinline__ double pow2d(int p) { return __longlong_as_double((long long)(1023 + p) << 52); }
-
 // Exponents of the largest entries of V_l (block l) and W_l (block 32 + l) on rows
 // [k0, n); kNoExp for a column of zeros
 constexpr int kNoExp = -100000;
 __global__ void panel_colexp_kernel(const cdf* __restrict__ V, const cdf* __restrict__ W, int n, int k0, int* cx) {
-    __shared__ double s_m[kHThreads / 32];
+    __shared__ float s_m[kHThreads / 32];
     const int l = blockIdx.x & 31;
     const cdf* x = (blockIdx.x >= 32 ? W : V) + (size_t)l * n;
-    double m = 0.0;
+    float m = 0.f;
     for (int r = k0 + (int)threadIdx.x; r < n; r += blockDim.x) {
         const cdf z = __ldcg(x + r);
-        m = fmax(m, fmax(fabs(cdf_re(z)), fabs(cdf_im(z))));
+        m = fmaxf(m, fmaxf(fabsf(z.x), fabsf(z.z)));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_m[w]);
-        cx[blockIdx.x] = m > 0.0 ? ilogb(m) : kNoExp;
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_m[w]);
+        cx[blockIdx.x] = m > 0.f ? ilogbf(m) : kNoExp;
     }
 }
 
@@ -119,7 +98,7 @@ __global__ void panel_colexp_kernel(const cdf* __restrict__ V, const cdf* __rest
 __device__ __forceinline__ int balance_exp(const int* cx, int l) {
     const int ev = cx[l], ew = cx[32 + l];
     if (ev == kNoExp || ew == kNoExp) return 0;
-    return max(-500, min(500, (ew - ev) >> 1));
+    return max(-120, min(120, (ew - ev) >> 1));
 }
 
 // One warp per row of X (rows rt0*128 <= r < nrt*128) or of Y (rows ct0*32 <= i < nct*32,
@@ -134,27 +113,25 @@ __global__ void panel_digits_kernel(const cdf* __restrict__ V, const cdf* __rest
     const bool isx = gw < nx;
     const int r = isx ? rt0 * kHM + gw : ct0 * kHN + (gw - nx);
     const bool live = r >= k0 && r < n;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};   // Re, Im of column lane, then of column lane + 32
+    float v[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // Re, Im of column lane, then lane + 32
     if (live) {
         const cdf a = isx ? __ldcg(V + (size_t)lane * n + r) : __ldcg(W + (size_t)lane * n + r);
         const cdf b = isx ? __ldcg(W + (size_t)lane * n + r) : __ldcg(V + (size_t)lane * n + r);
-        const int g = balance_exp(cx, lane);
-        const double sv = pow2d(g), sw = pow2d(-g);   // V_l and W_l balanced (exact)
-        const double sa = isx ? sv : sw, sb = isx ? sw : sv;
-        v[0] = cdf_re(a) * sa;
-        v[1] = cdf_im(a) * sa;
-        v[2] = cdf_re(b) * sb;
-        v[3] = cdf_im(b) * sb;
+        const int g = balance_exp(cx, lane);   // V_l scaled by 2^g, W_l by 2^-g (exact)
+        const int ga = isx ? g : -g, gb = -ga;
+        v[0][0] = scale_pow2(a.x, ga), v[0][1] = scale_pow2(a.y, ga);
+        v[1][0] = scale_pow2(a.z, ga), v[1][1] = scale_pow2(a.w, ga);
+        v[2][0] = scale_pow2(b.x, gb), v[2][1] = scale_pow2(b.y, gb);
+        v[3][0] = scale_pow2(b.z, gb), v[3][1] = scale_pow2(b.w, gb);
     }
-    double m = fmax(fmax(fabs(v[0]), fabs(v[1])), fmax(fabs(v[2]), fabs(v[3])));
+    float m = fmaxf(fmaxf(fabsf(v[0][0]), fabsf(v[1][0])), fmaxf(fabsf(v[2][0]), fabsf(v[3][0])));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const int e = m > 0.0 ? ilogb(m) + 1 : 0;   // |x| < 2^e for every element of the row
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int e = exp_above_f(m);   // |x| < 2^e for every element of the row
     if (lane == 0) (isx ? ex : fy)[r] = e;
-    const double sc = pow2d(56 - e);
     float d[4][kDig];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) digits8(__double2ll_rn(v[j] * sc), d[j]);
+    for (int j = 0; j < 4; ++j) df_digits8(v[j][0], v[j][1], e, d[j]);
     // K index: real parts of columns 0..63 at 0..63, imaginary parts at 64..127; digit k
     // stored as d_k 2^-7k (exact in bf16)
     const int kr0 = lane, kr1 = lane + 32, ki0 = 64 + lane, ki1 = 96 + lane;
@@ -163,28 +140,26 @@ __global__ void panel_digits_kernel(const cdf* __restrict__ V, const cdf* __rest
         const int rt = r / kHM, rr = r % kHM;
 #pragma unroll
         for (int k = 0; k < kDig; ++k) {
-            const float w = __int_as_float((127 - 7 * k) << 23);   // 2^-7k
             unsigned char* base = (unsigned char*)Adig + ((size_t)rt * kDig + k) * kADigBytes;   // [Xr Xi]
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k]);
         }
     } else {
         const int ct = r / kHN, rr = r % kHN;
 #pragma unroll
         for (int k = 0; k < kDig; ++k) {
-            const float w = __int_as_float((127 - 7 * k) << 23);
             unsigned char* base = (unsigned char*)Bdig + ((size_t)ct * kDig + k) * kBDigBytes;
             // row rr: [Yr Yi]; row rr + 32: [-Yi Yr]
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr0, kHK)) = bf(-d[1][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr1, kHK)) = bf(-d[3][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki0, kHK)) = bf(d[0][k] * w);
-            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki1, kHK)) = bf(d[2][k] * w);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr0, kHK)) = bf(d[0][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, kr1, kHK)) = bf(d[2][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki0, kHK)) = bf(d[1][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr, ki1, kHK)) = bf(d[3][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr0, kHK)) = bf(-d[1][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, kr1, kHK)) = bf(-d[3][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki0, kHK)) = bf(d[0][k]);
+            *(__nv_bfloat16*)(base + tc::core_off(rr + kHN, ki1, kHK)) = bf(d[2][k]);
         }
     }
 }

@@ -55,7 +55,7 @@ constexpr int kT2 = 256;            // threads of most kernels here
 constexpr int kW2 = kT2 / 32;
 constexpr int kMaxKs = 8;           // K splits of the A22 V product (at least those of zgemm_tc.cu)
 constexpr int kQrMaxCta = 32;       // CTAs of the panel QR
-constexpr int kGramRows = 128;      // rows per CTA of the 32 x 32 Gram products
+constexpr int kGramRows = 32;       // rows per CTA of the 32 x 32 Gram products
 constexpr int kSweepDone = 1 << 30;
 
 __device__ __forceinline__ cdf conjc(cdf a) { return make_float4(a.x, a.y, -a.z, -a.w); }
@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(1024, 1) mfactor_kernel(const cdf* __restrict_
     __shared__ cdf S[kB][kB + 1], Ts[kB][kB + 1];
     const int tid = threadIdx.x, i = tid >> 5, j = tid & 31;
     cdf s = cdf_zero();
-    for (int k = 0; k < ng; ++k) s = cdf_add(s, spart[(size_t)k * kB * kB + i * kB + j]);
+#pragma unroll 8
+    for (int k = 0; k < ng; ++k) s = cdf_add(s, __ldcg(spart + (size_t)k * kB * kB + i * kB + j));
     S[i][j] = s;
     Ts[i][j] = T[i * kB + j];
     __syncthreads();

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "dfloat.h"
+#include "digits.h"
 #include "grid_sync.h"
 #include "internal.h"
 #include "tc_ptx.h"
@@ -34,7 +35,7 @@ constexpr int kZL = 32;                                    // columns of Z (refl
 constexpr int kZN = 64;                                    // N of the MMA: [Vr -Vi] rows, then [Vi Vr] rows
 constexpr int kZK = 128;                                   // K' of a chunk (64 complex columns)
 constexpr int kZC = 64;                                    // complex columns per chunk
-constexpr int kZDig = 8;
+constexpr int kZDig = kDigits;
 constexpr int kZExact = 4;
 constexpr int kZAcc = kZExact + 1;
 constexpr int kZSlots = 3;
@@ -45,28 +46,7 @@ constexpr size_t kZBChunk = kZDig * kZBDig;                // 128 KB
 constexpr size_t kZSmem = kZBChunk + kZSlots * kZADig + 1024;
 constexpr int kZMaxSplit = 8;
 
-// Balanced base-128 digits d_0 .. d_7 (weights 2^49 .. 2^0, stored pre-scaled by 2^-7k) of
-// rint(x 2^(56-e)) for a double-float x = h + l, |x| < 2^e, without FP64 or 64-bit integer
-// arithmetic: (h, l) scaled by 2^(56-e) (two exact power-of-two factors), then per digit
-// q = rint(h / w) for w = 2^(49-7k), h <- h - q w (exact: a multiple of ulp(h) below w/2), and
-// (h, l) renormalised by TwoSum; the last digit is rint(h + l).
-__device__ __forceinline__ void df_digits8(float h, float l, int e, float* d) {
-    const int s = 56 - e, s1 = s / 2, s2 = s - s1;
-    const float f1 = __int_as_float((127 + s1) << 23), f2 = __int_as_float((127 + s2) << 23);
-    float hs = (h * f1) * f2, ls = (l * f1) * f2;
-#pragma unroll
-    for (int k = 0; k < kZDig - 1; ++k) {
-        const float w = __int_as_float((127 + 49 - 7 * k) << 23), wi = __int_as_float((127 - 49 + 7 * k) << 23);
-        const float q = rintf(hs * wi);
-        hs = fmaf(-q, w, hs);
-        two_sum(hs, ls, hs, ls);
-        d[k] = q * __int_as_float((127 - 7 * k) << 23);
-    }
-    d[kZDig - 1] = rintf(hs + ls) * __int_as_float((127 - 7 * (kZDig - 1)) << 23);
-}
 
-// 2^e above every |h| of the given maximum (|h + l| < 2^e as well)
-__device__ __forceinline__ int exp_above_f(float m) { return m > 0.f ? ilogbf(m) + 1 : 0; }
 
 // eight bf16 values (exact: pre-scaled digits) packed as one 16-byte store
 __device__ __forceinline__ uint4 pack8(const float* x) {
