@@ -568,14 +568,21 @@ def run_ours(args, rank, world, local):
         kinds = {k for k in stats[-1][1]["reduce_kinds"] if k >= 0}
         rname = {frozenset({0}): "tridiag_kernel",
                  frozenset({1}): "tridiag_blocked_kernel + panel_update_tc_kernel",
-                 frozenset({2}): "tridiag_blocked_kernel"}.get(frozenset(kinds), "tridiag kernels")
+                 frozenset({2}): "tridiag_blocked_kernel",
+                 frozenset({3}): "two-stage reduction (panel_qr_cluster_kernel, zgemm_tc_kernel, "
+                                 "panel_update_tc_kernel, bulge_kernel)"}.get(frozenset(kinds), "tridiag kernels")
         roofs.append({"bound": "alu", "kernel": rname, "ms_per_step": ms_reduce, "achieved": ra,
                       "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ra / DF_PEAK_TFLOPS,
-                      "peak_source": "derived: double-float on the FP32 pipe, 152 SMs x 128 FP32 instr/clk x "
-                                     "2.07 GHz / %g instr per real multiply-add x 2 flop; the FP64 pipe "
-                                     "(1.259 TFLOP/s) is not used; per reflection step a pass of column dot "
-                                     "products over the trailing matrix and one or two grid barriers, and in the "
-                                     "blocked form a rank-64 update per panel of 32 steps" % DF_FMA_INSTR,
+                      "peak_source": ("derived: double-float on the FP32 pipe, 152 SMs x 128 FP32 instr/clk x "
+                                      "2.07 GHz / %g instr per real multiply-add x 2 flop; the FP64 pipe "
+                                      "(1.259 TFLOP/s) is not used; " % DF_FMA_INSTR) +
+                                     ("two-stage: per panel of 32 columns a panel QR on one 16-CTA cluster, A22 V and "
+                                      "the rank-64 update as exact bf16 digit GEMMs on the tensor cores, then "
+                                      "band-to-tridiagonal bulge chasing (one sweep per row, latency-bound)"
+                                      if kinds == {3} else
+                                      "per reflection step a pass of column dot products over the trailing matrix "
+                                      "and one or two grid barriers, and in the blocked form a rank-64 update per "
+                                      "panel of 32 steps"),
                       "frac_of_fp64_pipe": ra / FP64_PEAK_TFLOPS,
                       "flops_per_launch": rflops / max(1, sum(1 for s in stats[-1][1]["solvers"]
                                                               if s == bse.BSE_SOLVER_TRIDIAG)),

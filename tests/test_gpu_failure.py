@@ -37,12 +37,15 @@ def _code(bse, fn, *args):
     return bse.BSE_OK
 
 
-@pytest.mark.parametrize("solver", ["BSE_SOLVER_TRIDIAG", "BSE_SOLVER_TRIDIAG_BLOCKED"])
-def test_tridiagonal_wait_gives_up_and_context_recovers(lib, solver):
-    """The 69-dim partner block of si4: the reduction in shared memory, and
-    the blocked one, whose tensor-core panel updates (after steps 30 and 62)
+@pytest.mark.parametrize("solver,kind", [("BSE_SOLVER_TRIDIAG", 0), ("BSE_SOLVER_TRIDIAG_BLOCKED", 1),
+                                         ("BSE_SOLVER_TRIDIAG_TWOSTAGE", 3)])
+def test_tridiagonal_wait_gives_up_and_context_recovers(lib, solver, kind):
+    """The 69-dim partner block of si4: the reduction in shared memory; the
+    blocked one, whose tensor-core panel updates (after steps 30 and 62)
     give up at their first mbarrier wait, let their bulk copies land, free
-    their tensor memory and return."""
+    their tensor memory and return; and the two-stage one, whose tensor-core
+    kernels do the same and whose bulge-chasing sweeps give up at their first
+    wait for the sweep before."""
     from oracle.projection import PartnerBasis
     bse, torch = lib
     from synth import generate
@@ -59,7 +62,7 @@ def test_tridiagonal_wait_gives_up_and_context_recovers(lib, solver):
     pb = PartnerBasis(b, mu)
     ref = pb.U[0].conj().T @ oracle_h("si4") @ pb.U[0]
     assert np.abs(om - np.linalg.eigvalsh(ref)).max() <= TOL
-    assert bse.bse_get_stats(ctx)["reduce_kind"] == (0 if solver == "BSE_SOLVER_TRIDIAG" else 1)
+    assert bse.bse_get_stats(ctx)["reduce_kind"] == kind
     bse.bse_destroy(ctx)
 
 

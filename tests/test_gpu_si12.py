@@ -115,9 +115,10 @@ def test_partner_solvers_agree(si12):
     bse, torch, ctx, t, mu, h64, h32, cols, d, *_ = si12
     omega = torch.tensor(d["omega"], device="cuda")
     out = {}
-    kind = {bse.BSE_SOLVER_TRIDIAG_BLOCKED: 1, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF: 2,
+    # n = 3582: the automatic choice (TRIDIAG) takes the two-stage reduction
+    kind = {bse.BSE_SOLVER_TRIDIAG: 3, bse.BSE_SOLVER_TRIDIAG_BLOCKED: 1, bse.BSE_SOLVER_TRIDIAG_BLOCKED_DF: 2,
             bse.BSE_SOLVER_TRIDIAG_TWOSTAGE: 3}
-    others = tuple(kind)
+    others = tuple(k for k in kind if k != bse.BSE_SOLVER_TRIDIAG)
     for solver in (bse.BSE_SOLVER_DENSE, bse.BSE_SOLVER_TRIDIAG) + others:
         bse.bse_set_solver(ctx, solver)
         out[solver] = [x.cpu().numpy() for x in bse.partner_spectrum(ctx, mu, h64, omega, d["eta"])]
