@@ -53,12 +53,17 @@ TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic.md")
 
 
 def _source_hash(rel):
+    """sha256 prefix of a source file, or of several files joined by '+' (their contents
+    concatenated in that order)"""
     import hashlib
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            return hashlib.sha256(f.read()).hexdigest()[:16]
+        for part in rel.split("+"):
+            with open(os.path.join(ROOT, part.strip()), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
+    return h.hexdigest()[:16]
 
 
 def dram_traffic(kernel, config, prec, block):
