@@ -24,9 +24,11 @@
 //            applies the reflector to the rest of that block (left), to the
 //            32 x 32 diagonal block (both sides) and to the block below
 //            (right), which becomes the next bulge.  One CTA runs a sweep at a
-//            time; sweep i may run task t once sweep i - 1 has finished task
-//            t + 2 (their blocks no longer overlap).  Only the lower triangle
-//            of the band is read and written.
+//            time; sweep i may load the window of task t but its last column
+//            once sweep i - 1 is done with those entries, and the last column
+//            (33 entries) once sweep i - 1 has published the critical part of
+//            its task t + 1; the left block needs no wait.  Only the lower
+//            triangle of the band is read and written.
 //
 // Every reflector acts on rows >= 1, so Q e_0 = e_0.  The tridiagonal matrix
 // left in the band is complex Hermitian; a diagonal unitary scaling makes its
@@ -371,10 +373,14 @@ __device__ __forceinline__ cdf ld_cluster_cdf(uint32_t ra) {
 // distributed shared memory) and forms the reflector, w_c = v^H P[:, c] = P[l][c] +
 // conj(inv) d_c and g_k = v_k^H v = conj(v_k[l]) + inv h_k.  The parts are double-buffered
 // by the parity of l: a CTA rewrites a buffer only after the next barrier, which every
-// other CTA passes after its reads.
-constexpr int kQp = 1 + 2 * kB;   // parts per CTA: sigma, d_c or h_k (entries 1..32), pivot row / v_k[l] (33..64)
-__global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
-    extern __shared__ __align__(16) cdf s_qc[];   // P[l * ch + u], rows rho0 + u
+// other CTA passes after its reads.  Task q (0..31) of reflector l is sigma (q = 0), d_{l+q}
+// (l + q < 32) or h_{l+q-32}, and its part goes to entry q; warp w forms tasks w and w + 16
+// in one pass over the rows.
+constexpr int kQp = 1 + 2 * kB;   // parts per CTA: sigma, d_c or h_k (entries 1..31), pivot row / v_k[l] (33..64)
+constexpr int kTQ = 512;          // threads of the cluster panel QR
+constexpr int kWQ = kTQ / 32;
+__global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
+    extern __shared__ __align__(16) cdf s_qc[];   // P[l * ch + u], rows rho0 + u; then F[u]
     __shared__ cdf s_wp[2][kQp];                  // this CTA's parts, by parity of l
     __shared__ cdf s_w[kQp];                      // their sums over the cluster (pivot entries from the owner)
     __shared__ cdf s_T[kB][kB + 1];               // rank 0: the T factor
@@ -387,56 +393,64 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
     const int rho0 = (int)rank * ch, nown = max(0, min(a.m, rho0 + ch) - rho0);
     const int n = a.n;
     cdf* P = s_qc;
-    for (int e = tid; e < kB * ch; e += kT2) {
+    cdf* F = s_qc + (size_t)kB * ch;   // -conj(tau) v of the own rows
+    for (int e = tid; e < kB * ch; e += kTQ) {
         const int l = e / ch, u = e - l * ch;
         P[e] = u < nown ? __ldcg(a.A + (size_t)(a.c0 + l) * n + a.r1 + rho0 + u) : cdf_zero();
     }
     __syncthreads();
+    // the two columns of task q's products conj(P[ca]) P[cb]
+    auto task_cols = [&](int q, int l, int& ca, int& cb) {
+        const int cc = l + q;
+        if (q == 0) {
+            ca = l;
+            cb = l;
+        } else if (cc < kB) {
+            ca = l;
+            cb = cc;
+        } else {
+            ca = cc - kB;
+            cb = l;
+        }
+    };
     for (int l = 0; l < a.nref; ++l) {
         cdf* wp = s_wp[l & 1];
-        const bool owner = l >= rho0 && l < rho0 + nown;
-        // parts over own rows rho > l: task 0 sigma, tasks 1..31 d_c (c = l + task) or h_k (k = task - ...)
-        for (int task = wid; task < kB; task += kW2) {
-            // task 0: sigma; task q in 1..31: d_{l+q} if l + q < 32, else h_{l+q-32}
-            const int q = task, cc = l + q;
-            const bool isd = q >= 1 && cc < kB, ish = q >= 1 && cc >= kB && cc - kB < l;
-            CAcc acc;
-            acc.zero();
-            for (int u = lane; u < nown; u += 32) {
-                if (rho0 + u <= l) continue;
-                const cdf x = P[l * ch + u];
-                if (q == 0)
-                    acc.dot(x, x);
-                else if (isd)
-                    acc.dot(x, P[cc * ch + u]);
-                else if (ish)
-                    acc.dot(P[(cc - kB) * ch + u], x);
+        {
+            int ca0, cb0, ca1, cb1;
+            task_cols(wid, l, ca0, cb0);
+            task_cols(wid + kWQ, l, ca1, cb1);
+            CAcc acc0, acc1;
+            acc0.zero();
+            acc1.zero();
+            for (int u = max(0, l + 1 - rho0) + lane; u < nown; u += 32) {
+                acc0.dot(P[ca0 * ch + u], P[cb0 * ch + u]);
+                acc1.dot(P[ca1 * ch + u], P[cb1 * ch + u]);
             }
-            const cdf sum = cdf_warp_sum(acc.get());
-            if (lane == 0) wp[q == 0 ? 0 : (isd ? cc - l : (ish ? kB - l + (cc - kB) : 0))] = sum;
+            const cdf s0 = cdf_warp_sum(acc0.get()), s1 = cdf_warp_sum(acc1.get());
+            if (lane == 0) {
+                wp[wid] = s0;
+                wp[wid + kWQ] = s1;
+            }
         }
-        if (owner) {   // the pivot row P[l][c] (c >= l) at 1 + kB + (c - l); v_k[l] (k < l) at 1 + kB + (32 - l) + k
-            const int u = l - rho0;
-            if (tid < kB) {
-                const int c = tid;
-                if (c >= l)
-                    wp[1 + kB + (c - l)] = P[c * ch + u];
-                else
-                    wp[1 + kB + (kB - l) + c] = P[c * ch + u];
-            }
+        if (l >= rho0 && l < rho0 + nown && tid < kB) {
+            // the pivot row P[l][c] (c >= l) at 1 + kB + (c - l); v_k[l] (k < l) at 1 + kB + (32 - l) + k
+            const int u = l - rho0, c = tid;
+            if (c >= l)
+                wp[1 + kB + (c - l)] = P[c * ch + u];
+            else
+                wp[1 + kB + (kB - l) + c] = P[c * ch + u];
         }
         cluster_sync_all();
-        // sums of the parts over the cluster (four threads per entry), pivot data from the owner
+        // sums of the parts over the cluster (16 threads per entry, one remote load each),
+        // pivot data from the owner
         {
-            const int ent = tid >> 2, k0 = tid & 3;   // sigma, d, h (entries 0..31): summed
-            cdf sum = cdf_zero();
-            if (ent < kB)
-                for (int k = k0; k < CQ; k += 4) sum = cdf_add(sum, ld_cluster_cdf(map_rank(&wp[ent], (uint32_t)k)));
-            sum = cdf_add(sum, cdf_shfl_xor(sum, 1));
-            sum = cdf_add(sum, cdf_shfl_xor(sum, 2));
-            if (ent < kB && k0 == 0) s_w[ent] = sum;
-            if (tid < kB)   // the pivot row and v_k[l] (entries 33..64), from the owner of row l
-                s_w[1 + kB + tid] = ld_cluster_cdf(map_rank(&wp[1 + kB + tid], (uint32_t)(l / ch)));
+            const int ent = tid >> 4, k = tid & 15;
+            cdf x = k < CQ ? ld_cluster_cdf(map_rank(&wp[ent], (uint32_t)k)) : cdf_zero();
+            const cdf pv = tid < kB ? ld_cluster_cdf(map_rank(&wp[1 + kB + tid], (uint32_t)(l / ch))) : cdf_zero();
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) x = cdf_add(x, cdf_shfl_xor(x, o));
+            if (k == 0) s_w[ent] = x;
+            if (tid < kB) s_w[1 + kB + tid] = pv;
         }
         __syncthreads();
         if (tid == 0) {
@@ -451,7 +465,6 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
         __syncthreads();
         const cdf tau = s_tau, inv = s_inv, cinv = conjc(inv);
         // w_c and g_k from the sums (kept in the d / h entries: w_c at 1 + (c - l), g_k at 1 + (32 - l) + k)
-        __syncthreads();
         if (tid < kB) {
             const int c = tid;
             if (c > l) {
@@ -462,20 +475,9 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
                 s_w[kB - l + c] = cdf_fma(conjc(s_w[1 + kB + (kB - l) + c]), inv, h);   // conj(v_k[l]) + inv h_k
             }
         }
-        __syncthreads();
-        if (rank == 0 && tid <= l) {   // column l of T: T[0:l, l] = -tau_l T[0:l, 0:l] g
-            if (tid == l) {
-                s_T[l][l] = tau;
-            } else {
-                CAcc acc;
-                acc.zero();
-                for (int k = tid; k < l; ++k) acc.mac(s_T[tid][k], s_w[kB - l + k]);
-                s_T[tid][l] = cdf_mul(negc(tau), acc.get());
-            }
-        }
-        // own rows: v in place (beta on the diagonal), then P <- P - conj(tau) v w for columns > l
+        // own rows: v in place (beta on the diagonal), F = -conj(tau) v
         const cdf mct = negc(conjc(tau));
-        for (int u = tid; u < nown; u += kT2) {
+        for (int u = tid; u < nown; u += kTQ) {
             const int rho = rho0 + u;
             if (rho < l) continue;
             cdf v;
@@ -486,18 +488,38 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_cluster_kernel(PanelArgs a) {
                 v = cdf_mul(P[l * ch + u], inv);
                 P[l * ch + u] = v;
             }
-            const cdf f = cdf_mul(mct, v);
-            for (int c = l + 1; c < kB; ++c) P[c * ch + u] = cdf_fma(P[c * ch + u], f, s_w[c - l]);
+            F[u] = cdf_mul(mct, v);
+        }
+        __syncthreads();
+        if (rank == 0)   // column l of T: T[0:l, l] = -tau_l T[0:l, 0:l] g (warp i: row i)
+            for (int i = wid; i <= l; i += kWQ) {
+                if (i == l) {
+                    if (lane == 0) s_T[l][l] = tau;
+                } else {
+                    CAcc acc;
+                    acc.zero();
+                    if (lane >= i && lane < l) acc.mac(s_T[i][lane], s_w[kB - l + lane]);
+                    const cdf sum = cdf_warp_sum(acc.get());
+                    if (lane == 0) s_T[i][l] = cdf_mul(negc(tau), sum);
+                }
+            }
+        // P <- P - conj(tau) v w on the own rows >= l, columns > l
+        {
+            const int u0 = max(0, l - rho0), nr = nown - u0, nc = kB - 1 - l;
+            for (int e = tid; e < nc * nr; e += kTQ) {
+                const int j = e / nr, u = u0 + e - j * nr, c = l + 1 + j;
+                P[c * ch + u] = cdf_fma(P[c * ch + u], F[u], s_w[c - l]);
+            }
         }
         __syncthreads();
     }
     // the panel ([R; 0]), the reflectors and T back to global memory
     if (rank == 0)
-        for (int e = tid; e < kB * kB; e += kT2) {
+        for (int e = tid; e < kB * kB; e += kTQ) {
             const int r = e >> 5, c = e & 31;
             a.T[e] = r <= c && c < a.nref ? s_T[r][c] : cdf_zero();
         }
-    for (int e = tid; e < kB * ch; e += kT2) {
+    for (int e = tid; e < kB * ch; e += kTQ) {
         const int l = e / ch, u = e - l * ch;
         if (u >= nown) continue;
         const int rho = rho0 + u;
@@ -599,18 +621,19 @@ __global__ void wfinal_kernel(const cdf* __restrict__ V, const cdf* __restrict__
 // to the window's diagonal block (both sides) and to the block below
 // ([q, q + 32) x [p, q), right), which becomes the next task's left block.
 // Shared memory: three 32 x 33 blocks (D, and the left and below blocks, whose
-// roles swap from task to task) and four vectors.
+// roles swap from task to task) and six vectors.
 // ---------------------------------------------------------------------------
 struct BulgeArgs {
     cdf* A;
     int n;
-    int* prog;   // [n] tasks finished by each sweep (kSweepDone once it has ended), zero on entry
+    int* prog;   // [n] crit count of each sweep (kSweepDone once it has ended), zero on entry
+    int* pre;    // [n] pre count of each sweep (kSweepDone once it has ended), zero on entry
     int* err;
     long spin;
 };
 
 constexpr int kBlk = kB * (kB + 1);
-constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 4 * kB);
+constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 6 * kB);
 
 // publish a count: every thread's earlier writes were ordered before this by __syncthreads,
 // and the release makes them visible before the count (as in the grid barrier)
@@ -630,45 +653,57 @@ __device__ __forceinline__ cdf group_sum(cdf v) {
     return v;
 }
 constexpr int kBT = 512;                // threads of the bulge-chasing kernel
-constexpr int kBRow = kBT / kB;         // product threads per row
-constexpr int kBCol = kB / kBRow;       // columns per product thread
+constexpr int kBRow = kBT / kB;         // left-block threads per column of the block
+constexpr int kBCol = kB / kBRow;       // rows per left-block thread
 
-// A task is split in two parts.  R_t: the reflector of the task's column (for t >= 1
-// the first column of the block below of task t - 1, final once that task's right
-// update is done), its entry beta written to A, and the sweep's count raised to t + 1:
-// this is all that sweep i + 1 needs from task t (their regions share only that entry).
-// L_t: once sweep i - 1 has raised its count to t + 3 (its R_{t+2} done, hence its L_{t+1}),
-// the lower triangle of the window's block and the block below are loaded; thread
-// (r, k) = (tid / 8, tid % 8) forms its part over columns 4k .. 4k + 3 of y_r = (D v)_r,
-// z_r = (B v)_r and s_r = (v^H L)_r, summed over the 8 threads of a row; warp 0 forms
-// mu = v^H y and w = tau y - |tau|^2 mu / 2 v; then D -= v w^H + w v^H (lower triangle),
-// B -= tau z v^H, L -= conj(tau) v s^H (columns >= 1), and the blocks are written back.
-// Order within the sweep: R_0, L_0, R_1, L_1, ...  Every warp forms the reflector
-// (lane l holds v_l), so no synchronisation separates it from the products.
+// Each sweep publishes two counts.  crit[i] = t + 2 once the critical part of task t is
+// out: column 0 of its window's block after the two-sided update (whose entries, with the
+// reflected column's beta, are the only ones the next sweep's task t - 1 still waits for)
+// and the reflector of task t + 1.  pre[i] = t once the rest of task t - 1 (the other
+// columns of its diagonal block, its block below) and the left-block part of task t are
+// out.  Task t of sweep i:
+//   deferred part of task t - 1: D -= v w^H + w v^H on columns >= 1 written back, the block
+//     below (now the left block, in shared memory) -= tau z v^H on columns >= 1;
+//   left block (t >= 1; no other sweep touches it meanwhile): thread (c, k) = (tid / 16,
+//     tid % 16) forms its part over rows 2k, 2k + 1 of s_c = (v^H L)_c, summed over the 16
+//     threads; L -= conj(tau) v s^H (columns >= 1) is written back; pre[i] = t;
+//   once pre[i-1] >= t + 1 (sweep i - 1 is done with all of the window but its column 31):
+//     the window's block (lower triangle) and the block below are loaded but for column
+//     31; threads 0..255 form y = D v, threads 256..511 z = B v without those entries (8
+//     threads per row, 4 columns each);
+//   once crit[i-1] >= t + 3: warp 0 loads D(31,31), completes y, forms mu = v^H y,
+//     w = tau y - |tau|^2 mu / 2 v and column 0 of the updated block; warp 1 loads column
+//     31 of the block below, completes z and forms R_{t+1} from column 0 of the updated
+//     block below, B[:,0] - tau z (v_0 = 1); crit[i] = t + 2.
+// The last task of a sweep does all of its work after crit[i-1] >= t + 3.
 __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
     extern __shared__ __align__(16) cdf s_bg[];
     __shared__ int s_ok;
+    __shared__ cdf s_tau;
     cdf* D = s_bg;                     // D[r * 33 + c], lower triangle (r >= c)
     cdf* Lb = s_bg + kBlk;             // left block: Lb[r * 33 + c], rows p + r, columns p - 32 + c
     cdf* Bb = s_bg + 2 * kBlk;         // block below: Bb[r * 33 + c], rows q + r, columns p + c
-    cdf* vs = s_bg + 3 * kBlk;         // v
-    cdf* ys = vs + kB;                 // y, then w
-    cdf* zs = ys + kB;                 // tau z
-    cdf* ss = zs + kB;                 // s; the first reflected column before
+    cdf* vo = s_bg + 3 * kBlk;         // v of the previous task (its deferred part)
+    cdf* vs = vo + kB;                 // v of the task
+    cdf* vn = vs + kB;                 // v of the next task
+    cdf* ys = vn + kB;                 // y, then w
+    cdf* zs = ys + kB;                 // z, then tau z
+    cdf* ss = zs + kB;                 // s
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int pr = tid / kBRow, pk = tid % kBRow;   // product thread: row pr, columns kBCol pk ..
+    const int pr = tid / kBRow, pk = tid % kBRow;   // left-block thread: column pr, rows kBCol pk ..
+    const int half = tid >> 8, r2 = (tid & 255) >> 3, k2 = tid & 7;   // product thread: y or z, row r2
     const int n = a.n;
     cdf* A = a.A;
     auto at = [&](int r, int c) -> cdf* { return A + (size_t)c * n + r; };
     constexpr int S = kB + 1;
-    // tid 0 waits until sweep i - 1 has raised its count to `need`; false if the wait gave up
-    auto wait_prev = [&](int i, int need) {
+    // tid 0 waits until sweep i - 1 has raised count cnt to `need`; false if the wait gave up
+    auto wait_prev = [&](const int* cnt, int i, int need) {
         if (tid == 0) {
             bool ok = true;
             if (i > 0) {
                 ok = false;
                 for (long it = 0; it < a.spin; ++it) {
-                    if (ld_acquire_gpu((const unsigned*)(a.prog + i - 1)) >= (unsigned)need) {
+                    if (ld_acquire_gpu((const unsigned*)(cnt + i - 1)) >= (unsigned)need) {
                         ok = true;
                         break;
                     }
@@ -681,7 +716,7 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
         __syncthreads();
         return s_ok != 0;
     };
-    // the reflector of column x (lane l holds x_l, l < len), in every warp
+    // the reflector of column x (lane l holds x_l, l < len), in the calling warp
     auto form = [&](cdf xl, int len, cdf& vl, cdf& tau, float2& beta) {
         float sg = 0.f, lo = 0.f;
         if (lane >= 1 && lane < len) {
@@ -693,13 +728,27 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
         reflector(shfl_cdf(xl, 0), sigma, tau, inv, beta);
         vl = lane == 0 ? onec() : (lane < len ? cdf_mul(xl, inv) : cdf_zero());
     };
+    // w = tau y - |tau|^2 mu / 2 v with mu = Re v^H y, in warp 0 (lane l holds y_l, v_l)
+    auto form_w = [&](cdf yy, cdf vl, cdf tau, int len) {
+        float m0 = 0.f, m1 = 0.f;
+        if (lane < len) {
+            df_acc(m0, m1, vl.x, vl.y, yy.x, yy.y);
+            df_acc(m0, m1, vl.z, vl.w, yy.z, yy.w);
+        }
+        const float2 mu = warp_sum_df(df_fin(m0, m1));
+        float t0 = 0.f, t1 = 0.f;
+        df_acc(t0, t1, tau.x, tau.y, tau.x, tau.y);
+        df_acc(t0, t1, tau.z, tau.w, tau.z, tau.w);
+        const float2 cf = df_mul(df_mul(df_fin(t0, t1), mu), make_float2(-0.5f, 0.f));
+        return lane < len ? cdf_fma(cdf_mul(tau, yy), make_float4(cf.x, cf.y, 0.f, 0.f), vl) : cdf_zero();
+    };
     for (int i = blockIdx.x; i < n - 2; i += gridDim.x) {
-        cdf vl, tau;
+        cdf vl, tau;   // lane l of every warp holds v_l
         float2 beta;
-        // R_0: column i on rows i+1 .. i+32, final once sweep i - 1 has done R_1
+        // R_0: column i on rows i+1 .. i+32, final once sweep i - 1 has done the critical part of task 0
         {
             const int p = i + 1, len = min(p + kB, n) - p;
-            if (!wait_prev(i, 2)) return;
+            if (!wait_prev(a.prog, i, 2)) return;
             const cdf xl = lane < len ? __ldcg(at(p + lane, i)) : cdf_zero();
             form(xl, len, vl, tau, beta);
             if (wid == 0) {
@@ -713,90 +762,129 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
             const int p = i + 1 + kB * t;
             const int q = min(p + kB, n), len = q - p;
             const int qb = min(q + kB, n), lenb = qb - q;
-            const bool next = q <= n - 2;
-            // L_t
-            if (!wait_prev(i, t + 3)) return;
-            for (int e = tid; e < kB * kB; e += kBT) {
-                const int r = e & 31, c = e >> 5;
-                if (r >= c && r < len) D[r * S + c] = __ldcg(at(p + r, p + c));
-                if (r < lenb && c < len) Bb[r * S + c] = __ldcg(at(q + r, p + c));
-            }
-            __syncthreads();
-            CAcc ay, az, as;
-            ay.zero();
-            az.zero();
-            as.zero();
-#pragma unroll
-            for (int u = 0; u < kBCol; ++u) {
-                const int c = kBCol * pk + u;
-                const cdf vc = shfl_cdf(vl, c);
-                if (pr < len && c < len) ay.mac(pr >= c ? D[pr * S + c] : conjc(D[c * S + pr]), vc);
-                if (pr < lenb && c < len) az.mac(Bb[pr * S + c], vc);
-                if (t > 0 && c < len) as.dot(vc, Lb[c * S + pr]);   // column pr of L, rows c
-            }
-            const cdf yr = group_sum<kBRow>(ay.get()), zr = group_sum<kBRow>(az.get()),
-                      sr = group_sum<kBRow>(as.get());
-            if (pk == 0) {
-                ys[pr] = yr;
-                zs[pr] = cdf_mul(tau, zr);
-                ss[pr] = sr;
-            }
-            __syncthreads();
-            const cdf mct = negc(conjc(tau));
-            if (wid == 0) {   // mu = Re v^H y, w = tau y - |tau|^2 mu / 2 v
-                float m0 = 0.f, m1 = 0.f;
-                const cdf yy = ys[lane];
-                if (lane < len) {
-                    df_acc(m0, m1, vl.x, vl.y, yy.x, yy.y);
-                    df_acc(m0, m1, vl.z, vl.w, yy.z, yy.w);
+            const bool next = q <= n - 2;   // a task follows; then len == 32
+            if (t > 0) {
+                // deferred part of task t - 1 (whose window [p - 32, p) is full)
+                const int pp = p - kB;
+                for (int e = tid; e < kB * kB; e += kBT) {
+                    const int r = e & 31, c = e >> 5;
+                    if (c >= 1 && c <= r) *at(pp + r, pp + c) = cdf_rank2(D[r * S + c], vo[r], ys[r], ys[c], vo[c]);
+                    if (r < len && c >= 1) Lb[r * S + c] = cdf_fma(Lb[r * S + c], negc(zs[r]), conjc(vo[c]));
                 }
-                const float2 mu = warp_sum_df(df_fin(m0, m1));
-                float t0 = 0.f, t1 = 0.f;
-                df_acc(t0, t1, tau.x, tau.y, tau.x, tau.y);
-                df_acc(t0, t1, tau.z, tau.w, tau.z, tau.w);
-                const float2 cf = df_mul(df_mul(df_fin(t0, t1), mu), make_float2(-0.5f, 0.f));
-                __syncwarp();
-                ys[lane] = lane < len ? cdf_fma(cdf_mul(tau, yy), make_float4(cf.x, cf.y, 0.f, 0.f), vl) : cdf_zero();
-            }
-            // the block below and the left block need only z, s and v: updated while warp 0 forms w
-            for (int e = tid; e < kB * kB; e += kBT) {
-                const int r = e & 31, c = e >> 5;
-                if (r < lenb && c < len) Bb[r * S + c] = cdf_fma(Bb[r * S + c], negc(zs[r]), conjc(vs[c]));
-                if (t > 0 && r < len && c >= 1) Lb[r * S + c] = cdf_fma(Lb[r * S + c], cdf_mul(mct, vs[r]), ss[c]);
-            }
-            __syncthreads();
-            for (int e = tid; e < kB * kB; e += kBT) {
-                const int r = e & 31, c = e >> 5;
-                if (c <= r && r < len) D[r * S + c] = cdf_rank2(D[r * S + c], vs[r], ys[r], ys[c], vs[c]);
-            }
-            __syncthreads();
-            // write back: D (lower), the left block (its column 0 went out with R_t), the block
-            // below when no task follows
-            for (int e = tid; e < kB * kB; e += kBT) {
-                const int r = e & 31, c = e >> 5;
-                if (c <= r && r < len) *at(p + r, p + c) = D[r * S + c];
-                if (t > 0 && r < len && c >= 1) *at(p + r, p - kB + c) = Lb[r * S + c];
-                if (!next && r < lenb && c < len) *at(q + r, p + c) = Bb[r * S + c];
-            }
-            if (!next) {
                 __syncthreads();
-                if (tid == 0) st_release_gpu(a.prog + i, kSweepDone);
+                // left block: s = v^H L, L -= conj(tau) v s^H on columns >= 1, written back
+                const cdf mct = negc(conjc(tau));
+                CAcc as;
+                as.zero();
+#pragma unroll
+                for (int u = 0; u < kBCol; ++u) {
+                    const int c = kBCol * pk + u;
+                    const cdf vc = shfl_cdf(vl, c);
+                    if (c < len) as.dot(vc, Lb[c * S + pr]);   // column pr of L, rows c
+                }
+                const cdf sr = group_sum<kBRow>(as.get());
+                if (pk == 0) ss[pr] = sr;
+                __syncthreads();
+                for (int e = tid; e < kB * kB; e += kBT) {
+                    const int r = e & 31, c = e >> 5;
+                    if (r < len && c >= 1) *at(p + r, p - kB + c) = cdf_fma(Lb[r * S + c], cdf_mul(mct, vs[r]), ss[c]);
+                }
+                __syncthreads();
+                if (tid == 0) st_release_gpu(a.pre + i, t);
+            }
+            if (!(next ? wait_prev(a.pre, i, t + 1) : wait_prev(a.prog, i, t + 3))) return;
+            for (int e = tid; e < kB * kB; e += kBT) {
+                const int r = e & 31, c = e >> 5;
+                const bool late = next && c == kB - 1;   // column 31: after crit[i-1] >= t + 3
+                if (r >= c && r < len && !late) D[r * S + c] = __ldcg(at(p + r, p + c));
+                if (r < lenb && c < len && !late) Bb[r * S + c] = __ldcg(at(q + r, p + c));
+            }
+            __syncthreads();
+            {   // y = D v (threads 0..255), z = B v (threads 256..511), without column 31 when a task follows
+                CAcc acc;
+                acc.zero();
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = 4 * k2 + u;
+                    const cdf vc = shfl_cdf(vl, c);
+                    if (half == 0) {
+                        if (r2 < len && c < len && !(next && r2 == kB - 1 && c == kB - 1))
+                            acc.mac(r2 >= c ? D[r2 * S + c] : conjc(D[c * S + r2]), vc);
+                    } else {
+                        if (r2 < lenb && c < len && !(next && c == kB - 1)) acc.mac(Bb[r2 * S + c], vc);
+                    }
+                }
+                const cdf rs = group_sum<8>(acc.get());
+                if (k2 == 0) {
+                    if (half == 0)
+                        ys[r2] = rs;
+                    else
+                        zs[r2] = rs;
+                }
+            }
+            if (!next) {   // the last task: w, tau z, then every update
+                __syncthreads();
+                if (wid == 0)
+                    ys[lane] = form_w(ys[lane], vl, tau, len);
+                else if (wid == 1)
+                    zs[lane] = cdf_mul(tau, zs[lane]);
+                __syncthreads();
+                for (int e = tid; e < kB * kB; e += kBT) {
+                    const int r = e & 31, c = e >> 5;
+                    if (c <= r && r < len) *at(p + r, p + c) = cdf_rank2(D[r * S + c], vs[r], ys[r], ys[c], vs[c]);
+                    if (r < lenb && c < len) *at(q + r, p + c) = cdf_fma(Bb[r * S + c], negc(zs[r]), conjc(vs[c]));
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    st_release_gpu(a.pre + i, kSweepDone);
+                    st_release_gpu(a.prog + i, kSweepDone);
+                }
                 break;
             }
-            // R_{t+1}: the first column of the block below (rows q .. qb - 1)
-            form(Bb[lane * S], lenb, vl, tau, beta);
-            __syncthreads();   // every warp has read column 0 of the block below
-            if (wid == 0) {
-                vs[lane] = vl;
-                const cdf xo = lane == 0 ? make_float4(beta.x, beta.y, 0.f, 0.f) : cdf_zero();
+            if (!wait_prev(a.prog, i, t + 3)) return;   // its barrier also orders the partial sums
+            if (wid == 0) {   // D(31,31), y, w, column 0 of the updated block
+                cdf yy = ys[lane];
+                const cdf v31 = shfl_cdf(vl, kB - 1);
+                if (lane == kB - 1) {
+                    const cdf d = __ldcg(at(p + kB - 1, p + kB - 1));
+                    D[(kB - 1) * S + kB - 1] = d;
+                    yy = cdf_fma(yy, d, v31);
+                }
+                const cdf w = form_w(yy, vl, tau, kB);
+                ys[lane] = w;
+                *at(p + lane, p) = cdf_rank2(D[lane * S], vl, w, shfl_cdf(w, 0), shfl_cdf(vl, 0));
+            } else if (wid == 1) {   // column 31 of the block below, tau z, R_{t+1}
+                const cdf v31 = shfl_cdf(vl, kB - 1);
+                cdf zz = zs[lane], b0 = cdf_zero();
+                if (lane < lenb) {
+                    const cdf b = __ldcg(at(q + lane, p + kB - 1));
+                    Bb[lane * S + kB - 1] = b;
+                    zz = cdf_fma(zz, b, v31);
+                    b0 = Bb[lane * S];
+                }
+                const cdf tz = cdf_mul(tau, zz);
+                zs[lane] = tz;
+                const cdf xl = lane < lenb ? cdf_fma(b0, negc(tz), onec()) : cdf_zero();
+                cdf vln, taun;
+                float2 betan;
+                form(xl, lenb, vln, taun, betan);
+                vn[lane] = vln;
+                if (lane == 0) s_tau = taun;
+                const cdf xo = lane == 0 ? make_float4(betan.x, betan.y, 0.f, 0.f) : cdf_zero();
                 Bb[lane * S] = xo;
                 if (lane < lenb) *at(q + lane, p) = xo;
             }
             __syncthreads();
             if (tid == 0) st_release_gpu(a.prog + i, t + 2);
-            cdf* tmp = Lb;   // the block below becomes the next task's left block
+            vl = vn[lane];
+            tau = s_tau;
+            cdf* tv = vo;   // v of this task stays for its deferred part
+            vo = vs;
+            vs = vn;
+            vn = tv;
+            cdf* tb = Lb;   // the block below becomes the next task's left block
             Lb = Bb;
-            Bb = tmp;
+            Bb = tb;
         }
         __syncthreads();
     }
@@ -822,9 +910,9 @@ __global__ void band_extract_kernel(const cdf* __restrict__ A, int n, double* d,
 size_t tridiag2_bytes(int64_t n) {
     const int64_t ng = (n + kGramRows - 1) / kGramRows;
     // H0 vectors (3 n); A22 V parts (kMaxKs n 32); Gram parts (ng 1024); T, M (2 x 1024); tau, pivots
-    // (64); partial norms (256 float2); partial w and g (256 x 64); progress (n ints); barrier; alignment
+    // (64); partial norms (256 float2); partial w and g (256 x 64); progress (2 n ints); barrier; alignment
     return sizeof(cdf) * (size_t)(3 * n + kMaxKs * n * kB + ng * kB * kB + 2 * kB * kB + 2 * kB + 512 * kB) +
-           sizeof(float2) * 256 + sizeof(int) * (size_t)n + zgemm_tc_bytes(n) + 64 + 16 * 256;
+           sizeof(float2) * 256 + 2 * sizeof(int) * (size_t)n + zgemm_tc_bytes(n) + 64 + 16 * 256;
 }
 
 int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0, double* d, double* e, cdf* V, cdf* W,
@@ -849,6 +937,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
     float2* part = (float2*)take(sizeof(float2) * 256);
     cdf* wpart = (cdf*)take(sizeof(cdf) * 256 * 2 * kB);
     int* prog = (int*)take(sizeof(int) * n);
+    int* pre = (int*)take(sizeof(int) * n);
     unsigned* bar = (unsigned*)take(sizeof(unsigned));
     void* zscratch = take(zgemm_tc_bytes(n));
     const long spin = wait_limit(wait_polls, kGridSpinLimit);
@@ -877,8 +966,8 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
         for (int cq : {16, 8}) {
             if (m0 < 2) break;
             const int ch = (m0 + cq - 1) / cq;
-            const size_t smem = sizeof(cdf) * kB * (size_t)ch;
-            if (ch > 4 * kT2 || smem > 200 * 1024) continue;
+            const size_t smem = sizeof(cdf) * (kB + 1) * (size_t)ch;
+            if (smem > 200 * 1024) continue;
             if (cq > 8 &&
                 cudaFuncSetAttribute(panel_qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                     cudaSuccess) {
@@ -897,7 +986,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
             attr[0].val.clusterDim.y = 1;
             attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(cq);
-            cfg.blockDim = dim3(kT2);
+            cfg.blockDim = dim3(kTQ);
             cfg.dynamicSmemBytes = smem;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
@@ -951,8 +1040,8 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
             attr[0].val.clusterDim.y = 1;
             attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(CQ);
-            cfg.blockDim = dim3(kT2);
-            cfg.dynamicSmemBytes = sizeof(cdf) * kB * (size_t)chq;
+            cfg.blockDim = dim3(kTQ);
+            cfg.dynamicSmemBytes = sizeof(cdf) * (kB + 1) * (size_t)chq;
             cfg.stream = st;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
@@ -983,6 +1072,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
     // stage 2: bulge chasing
     if (n > 2) {
         BSE_CUDA(cudaMemsetAsync(prog, 0, sizeof(int) * n, st));
+        BSE_CUDA(cudaMemsetAsync(pre, 0, sizeof(int) * n, st));
         BSE_CUDA(cudaFuncSetAttribute(bulge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBulgeSmem));
         int per_sm = 0;
         BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulge_kernel, kBT, kBulgeSmem));
@@ -992,6 +1082,7 @@ int launch_tridiag2(cdf* A, int64_t n64, const double2* v0, const double* beta0,
         ba.A = A;
         ba.n = n;
         ba.prog = prog;
+        ba.pre = pre;
         ba.err = err;
         ba.spin = spin;
         void* bargs[] = {&ba};
