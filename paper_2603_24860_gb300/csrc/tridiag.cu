@@ -1003,54 +1003,63 @@ __device__ __forceinline__ int sturm_count_df(const float2* __restrict__ d, cons
     return c;
 }
 
-// One warp per level: 33-section of the Gershgorin interval with Sturm
-// counts: 4 rounds in FP32 (from 2 ||T|| to below the FP32 counts' backward
-// error), the bracket widened by that error (16 eps_32 (||T|| + |x|)), then
-// 6 rounds in double-float to about 1e-14 ||T|| (33^6 = 1.3e9), below the
-// backward error of the double-float reduction that made T.  Both kinds of
-// count run on the FP32 pipe; the cost is each warp's chain of dependent
-// instructions, so fewer, wider rounds beat narrow bisection.  Every lane
-// runs all rounds (uniform ballots).  Levels k < m belong to rows [0, m),
-// the others to rows [m, n).  Launched as blocks of four warps, one per SM
-// sub-partition.
-constexpr int kSect = 32;
-constexpr unsigned kSectMask = kSect == 32 ? 0xffffffffu : ((1u << (kSect & 31)) - 1u);
+// S lanes per level: (S + 1)-section of the Gershgorin interval with Sturm
+// counts: rounds in FP32 until the bracket is below 2 ||T|| / 1.2e6 (under the
+// FP32 counts' backward error), the bracket widened by that error
+// (16 eps_32 (||T|| + |x|)), then rounds in double-float until it has shrunk
+// by 1.3e9 more, to about 1e-14 ||T||, below the backward error of the
+// double-float reduction that made T.  Both kinds of count run on the FP32
+// pipe.  With few levels the cost is each warp's chain of dependent
+// instructions, so wide rounds (S = 32: 4 + 6 rounds) beat narrow ones; with
+// thousands of levels the kernel is issue-bound and S = 8 (7 + 10 rounds, 136
+// counts per level instead of 320) wins.  Every lane runs all rounds (uniform
+// ballots).  Levels k < m belong to rows [0, m), the others to rows [m, n).
+// Launched as blocks of four warps, one per SM sub-partition.
+template <int S>
+struct Sect {
+    static constexpr unsigned mask = S == 32 ? 0xffffffffu : ((1u << (S & 31)) - 1u);
+    static constexpr int rounds32 = S == 32 ? 4 : (S == 16 ? 5 : 7);   // (S + 1)^rounds32 >= 1.2e6
+    static constexpr int rounds_df = S == 32 ? 6 : (S == 16 ? 8 : 10);  // (S + 1)^rounds_df >= 1.3e9
+    static_assert(S == 8 || S == 16 || S == 32, "8-, 16- or 32-lane sections");
+};
 constexpr int kBisectThreads = 128;
+constexpr int64_t kBisectNarrowFrom = 2048;   // levels from which the 9-section beats the 33-section
+template <int S>
 __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const float2* __restrict__ d_df,
                                                                 const float2* __restrict__ e2_df,
                                                                 const float* __restrict__ d32,
                                                                 const float* __restrict__ e2_32, int64_t n,
                                                                 const TriBounds* __restrict__ bnd, double* lam) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, sub = lane % kSect, base = lane - sub;
-    const int64_t k = min(t / kSect, n - 1);
+    const int lane = threadIdx.x & 31, sub = lane % S, base = lane - sub;
+    const int64_t k = min(t / S, n - 1);
     const TriBounds b = *bnd;
     const int i0 = k < b.m ? 0 : b.m, i1 = k < b.m ? b.m : (int)n;
     const int kk = (int)(k - i0);
     float lof = (float)b.gl, hif = (float)b.gu;
-    for (int it = 0; it < 4; ++it) {
-        const float x = lof + (hif - lof) * (float)(sub + 1) * (1.0f / (kSect + 1));
+    for (int it = 0; it < Sect<S>::rounds32; ++it) {
+        const float x = lof + (hif - lof) * (float)(sub + 1) * (1.0f / (S + 1));
         const int c = sturm_count32(d32, e2_32, i0, i1, x, b.pivmin32);
-        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & kSectMask;
-        const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & Sect<S>::mask;
+        const int ls = q ? __ffs(q) - 1 : S;   // first point above level kk
         const float xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
-        const float xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
+        const float xh = __shfl_sync(0xffffffffu, x, base + (ls < S ? ls : S - 1));
         if (ls > 0) lof = xl;
-        if (ls < kSect) hif = xh;
+        if (ls < S) hif = xh;
     }
     const double del = 16.0 * FLT_EPSILON * (b.tnorm + fmax(fabs((double)lof), fabs((double)hif)));
     double lo = fmax(b.gl, (double)lof - del), hi = fmin(b.gu, (double)hif + del);
-    for (int it = 0; it < 6; ++it) {
-        const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (kSect + 1));
+    for (int it = 0; it < Sect<S>::rounds_df; ++it) {
+        const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / (S + 1));
         const int c = sturm_count_df(d_df, e2_df, i0, i1, df_from(x));
-        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & kSectMask;
-        const int ls = q ? __ffs(q) - 1 : kSect;   // first point above level kk
+        const unsigned q = (__ballot_sync(0xffffffffu, c > kk) >> base) & Sect<S>::mask;
+        const int ls = q ? __ffs(q) - 1 : S;   // first point above level kk
         const double xl = __shfl_sync(0xffffffffu, x, base + (ls > 0 ? ls - 1 : 0));
-        const double xh = __shfl_sync(0xffffffffu, x, base + (ls < kSect ? ls : kSect - 1));
+        const double xh = __shfl_sync(0xffffffffu, x, base + (ls < S ? ls : S - 1));
         if (ls > 0) lo = xl;
-        if (ls < kSect) hi = xh;
+        if (ls < S) hi = xh;
     }
-    if (sub == 0 && t / kSect < n) lam[k] = 0.5 * (lo + hi);
+    if (sub == 0 && t / S < n) lam[k] = 0.5 * (lo + hi);
 }
 
 // Squared first component of the eigenvector of rows [0, m) for level k < m,
@@ -1138,6 +1147,9 @@ __global__ void __launch_bounds__(64) twisted_weights_kernel(const float2* __res
     int rb = 0;
     if (act) {
         const int h0 = wid == 0 ? 0 : m / 2, h1 = wid == 0 ? m / 2 : m;
+        // unrolled so that the loads of several rows are in flight at once (the stored
+        // factors come from DRAM and one warp per SM sub-partition cannot hide that latency)
+#pragma unroll 8
         for (int i = h0; i < h1; ++i) {
             const float2 g = df_add(df_add(Dp[(size_t)i * n + k], Dm[(size_t)i * n + k]),
                                     df_neg(df_add(__ldg(d_df + i), nl)));
@@ -1155,12 +1167,14 @@ __global__ void __launch_bounds__(64) twisted_weights_kernel(const float2* __res
     double P = 1.0, h = 0.0, t = 0.0;
     if (act) {
         if (wid == 0) {
+#pragma unroll 8
             for (int i = 0; i < r; ++i) {
                 const double L2 = twist_factor(__ldg(e2_df + i), Dp[(size_t)i * n + k], __ldg(e2d + i));
                 P *= L2;
                 h = fma(L2, h, L2);
             }
         } else {
+#pragma unroll 8
             for (int i = m - 2; i >= r; --i) {
                 const double U2 = twist_factor(__ldg(e2_df + i), twist_clamp(Dm[(size_t)(i + 1) * n + k], piv),
                                                __ldg(e2d + i));
@@ -1382,8 +1396,12 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     tri_bounds_kernel<<<1, kTriThreads, 0, st>>>(d, e, n, e2, d32, e2_32, d_df, e2_df, bnd);
     note_launch();
     BSE_CUDA(cudaGetLastError());
-    bisect_kernel<<<(unsigned)((kSect * n + kBisectThreads - 1) / kBisectThreads), kBisectThreads, 0, st>>>(
-        d_df, e2_df, d32, e2_32, n, bnd, lam);
+    if (n >= kBisectNarrowFrom)
+        bisect_kernel<8><<<(unsigned)((8 * n + kBisectThreads - 1) / kBisectThreads), kBisectThreads, 0, st>>>(
+            d_df, e2_df, d32, e2_32, n, bnd, lam);
+    else
+        bisect_kernel<32><<<(unsigned)((32 * n + kBisectThreads - 1) / kBisectThreads), kBisectThreads, 0, st>>>(
+            d_df, e2_df, d32, e2_32, n, bnd, lam);
     note_launch();
     BSE_CUDA(cudaGetLastError());
     twisted_weights_kernel<<<(unsigned)((n + 31) / 32), 64, 0, st>>>(d_df, e2_df, e2, n, bnd, lam, dp, w);
