@@ -63,6 +63,17 @@ __device__ __forceinline__ void df_acc(float& s, float& lo, float ah, float al, 
     lo = __fmaf_rn(al, bh, lo);
 }
 
+// (s, lo) += a b for a float a and a double-float b = (bh, bl): a product with
+// an exact FP32 factor needs one cross term (11 FP32 instructions)
+__device__ __forceinline__ void df_acc1(float& s, float& lo, float a, float bh, float bl) {
+    const float p = __fmul_rn(a, bh);
+    const float pe = __fmaf_rn(a, bh, -p);
+    float t;
+    two_sum(s, p, s, t);
+    lo = __fadd_rn(lo, __fadd_rn(t, pe));
+    lo = __fmaf_rn(a, bl, lo);
+}
+
 // s + lo as a normalised double-float
 __device__ __forceinline__ float2 df_fin(float s, float lo) {
     float h, l;

@@ -338,22 +338,21 @@ __global__ void project_right_df_kernel(DevBasis Bs, const TileTask* __restrict_
         const int o = Bs.col_orbit[j];
         const int64_t m0 = Bs.orbit_off[o], n_o = Bs.orbit_off[o + 1] - m0;
         const float4* u = Bs.coef_df + Bs.col_off[j];
+        // raw double-float sums (leading words by TwoSum, every error and low part in the
+        // low words), normalised once at the end
         float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+#pragma unroll 4
         for (int64_t tt = 0; tt < n_o; ++tt) {
             const float2 x = Xt[(int64_t)Bs.member_loc[m0 + tt] * t.rows + r];
             const float4 c = u[tt];
             // (x.x + i x.y)(c.re + i c.im), x exact in FP32
-            df_acc(sr, lr, x.x, 0.f, c.x, c.y);
-            df_acc(sr, lr, -x.y, 0.f, c.z, c.w);
-            df_acc(si, li, x.x, 0.f, c.z, c.w);
-            df_acc(si, li, x.y, 0.f, c.x, c.y);
-            const float2 fr = df_fin(sr, lr), fi = df_fin(si, li);
-            sr = fr.x;
-            lr = fr.y;
-            si = fi.x;
-            li = fi.y;
+            df_acc1(sr, lr, x.x, c.x, c.y);
+            df_acc1(sr, lr, -x.y, c.z, c.w);
+            df_acc1(si, li, x.x, c.z, c.w);
+            df_acc1(si, li, x.y, c.x, c.y);
         }
-        store_y(Y + t.yoff + jj * t.rows + r, sr, lr, si, li);
+        const float2 fr = df_fin(sr, lr), fi = df_fin(si, li);
+        store_y(Y + t.yoff + jj * t.rows + r, fr.x, fr.y, fi.x, fi.y);
     }
 }
 
@@ -377,9 +376,18 @@ __global__ void project_left_df_kernel(DevBasis Bs, const TileTask* __restrict__
     for (int64_t jj = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; jj < ncol; jj += (int64_t)gridDim.y * blockDim.y) {
         const int64_t j = t.cb0 + jj;
         const float4* y = Y + t.yoff + jj * t.rows;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t tt = 0; tt < n_o; ++tt) acc = cdf_dot_acc(acc, u[tt], y[Bs.member_loc[m0 + tt]]);
-        double2 h = cdf_to(acc);
+        // raw double-float sums, normalised once at the end
+        float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+#pragma unroll 4
+        for (int64_t tt = 0; tt < n_o; ++tt) {
+            const float4 a = u[tt], b = y[Bs.member_loc[m0 + tt]];   // conj(a) b
+            df_acc(sr, lr, a.x, a.y, b.x, b.y);
+            df_acc(sr, lr, a.z, a.w, b.z, b.w);
+            df_acc(si, li, a.x, a.y, b.z, b.w);
+            df_acc(si, li, -a.z, -a.w, b.x, b.y);
+        }
+        const float2 hr = df_fin(sr, lr), hi = df_fin(si, li);
+        double2 h = make_double2((double)hr.x + (double)hr.y, (double)hi.x + (double)hi.y);
         if (de && Bs.col_orbit[j] == o) {
             const double2* ui = Bs.coef + Bs.col_off[i];
             const double2* uj = Bs.coef + Bs.col_off[j];

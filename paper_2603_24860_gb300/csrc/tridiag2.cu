@@ -95,6 +95,25 @@ __device__ __forceinline__ float2 warp_sum_df(float2 v) {
     return v;
 }
 
+// sum of a raw accumulator over the G lanes of a group (lanes G g .. G g + G - 1): per
+// level TwoSum of the leading words, the low words and TwoSum's error added (the error
+// model of cdf_add), normalised once at the end
+template <int G>
+__device__ __forceinline__ cdf cacc_group_sum(CAcc a) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const float sr = __shfl_xor_sync(0xffffffffu, a.sr, o), lr = __shfl_xor_sync(0xffffffffu, a.lr, o);
+        const float si = __shfl_xor_sync(0xffffffffu, a.si, o), li = __shfl_xor_sync(0xffffffffu, a.li, o);
+        float er, ei;
+        two_sum(a.sr, sr, a.sr, er);
+        two_sum(a.si, si, a.si, ei);
+        a.lr = __fadd_rn(a.lr, __fadd_rn(lr, er));
+        a.li = __fadd_rn(a.li, __fadd_rn(li, ei));
+    }
+    return a.get();
+}
+__device__ __forceinline__ cdf cacc_warp_sum(CAcc a) { return cacc_group_sum<32>(a); }
+
 // the block in place from FP64 to double-float (16 bytes per element either way)
 __global__ void to_cdf_kernel(cdf* A, int64_t nn) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
@@ -344,6 +363,12 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_kernel(PanelArgs a) {
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -384,6 +409,7 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
     __shared__ cdf s_wp[2][kQp];                  // this CTA's parts, by parity of l
     __shared__ cdf s_w[kQp];                      // their sums over the cluster (pivot entries from the owner)
     __shared__ cdf s_T[kB][kB + 1];               // rank 0: the T factor
+    __shared__ cdf s_G[kB][kB + 1];               // rank 0: g of reflector l (row l), tau_l on its diagonal
     __shared__ cdf s_tau, s_inv;
     __shared__ float2 s_beta;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -394,6 +420,21 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
     const int n = a.n;
     cdf* P = s_qc;
     cdf* F = s_qc + (size_t)kB * ch;   // -conj(tau) v of the own rows
+    // rank 0: column j of T, T[0:j, j] = -tau_j T[0:j, 0:j] g_j (warp i: row i)
+    auto t_column = [&](int j) {
+        const cdf tj = s_G[j][j];
+        for (int i = wid; i <= j; i += kWQ) {
+            if (i == j) {
+                if (lane == 0) s_T[j][j] = tj;
+            } else {
+                CAcc acc;
+                acc.zero();
+                if (lane >= i && lane < j) acc.mac(s_T[i][lane], s_G[j][lane]);
+                const cdf sum = cacc_warp_sum(acc);
+                if (lane == 0) s_T[i][j] = cdf_mul(negc(tj), sum);
+            }
+        }
+    };
     for (int e = tid; e < kB * ch; e += kTQ) {
         const int l = e / ch, u = e - l * ch;
         P[e] = u < nown ? __ldcg(a.A + (size_t)(a.c0 + l) * n + a.r1 + rho0 + u) : cdf_zero();
@@ -426,7 +467,7 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
                 acc0.dot(P[ca0 * ch + u], P[cb0 * ch + u]);
                 acc1.dot(P[ca1 * ch + u], P[cb1 * ch + u]);
             }
-            const cdf s0 = cdf_warp_sum(acc0.get()), s1 = cdf_warp_sum(acc1.get());
+            const cdf s0 = cacc_warp_sum(acc0), s1 = cacc_warp_sum(acc1);
             if (lane == 0) {
                 wp[wid] = s0;
                 wp[wid + kWQ] = s1;
@@ -440,7 +481,9 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
             else
                 wp[1 + kB + (kB - l) + c] = P[c * ch + u];
         }
-        cluster_sync_all();
+        cluster_arrive();
+        if (rank == 0 && l > 0) t_column(l - 1);   // while the other CTAs finish their parts
+        cluster_wait();
         // sums of the parts over the cluster (16 threads per entry, one remote load each),
         // pivot data from the owner
         {
@@ -491,18 +534,7 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
             F[u] = cdf_mul(mct, v);
         }
         __syncthreads();
-        if (rank == 0)   // column l of T: T[0:l, l] = -tau_l T[0:l, 0:l] g (warp i: row i)
-            for (int i = wid; i <= l; i += kWQ) {
-                if (i == l) {
-                    if (lane == 0) s_T[l][l] = tau;
-                } else {
-                    CAcc acc;
-                    acc.zero();
-                    if (lane >= i && lane < l) acc.mac(s_T[i][lane], s_w[kB - l + lane]);
-                    const cdf sum = cdf_warp_sum(acc.get());
-                    if (lane == 0) s_T[i][l] = cdf_mul(negc(tau), sum);
-                }
-            }
+        if (rank == 0 && tid <= l) s_G[l][tid] = tid == l ? tau : s_w[kB - l + tid];   // T column l in the next step
         // P <- P - conj(tau) v w on the own rows >= l, columns > l
         {
             const int u0 = max(0, l - rho0), nr = nown - u0, nc = kB - 1 - l;
@@ -513,12 +545,15 @@ __global__ void __launch_bounds__(kTQ, 1) panel_qr_cluster_kernel(PanelArgs a) {
         }
         __syncthreads();
     }
-    // the panel ([R; 0]), the reflectors and T back to global memory
-    if (rank == 0)
+    // the panel ([R; 0]), the reflectors and T back to global memory (the last column of T first)
+    if (rank == 0) {
+        if (a.nref > 0) t_column(a.nref - 1);
+        __syncthreads();
         for (int e = tid; e < kB * kB; e += kTQ) {
             const int r = e >> 5, c = e & 31;
             a.T[e] = r <= c && c < a.nref ? s_T[r][c] : cdf_zero();
         }
+    }
     for (int e = tid; e < kB * ch; e += kTQ) {
         const int l = e / ch, u = e - l * ch;
         if (u >= nown) continue;
@@ -621,7 +656,7 @@ __global__ void wfinal_kernel(const cdf* __restrict__ V, const cdf* __restrict__
 // to the window's diagonal block (both sides) and to the block below
 // ([q, q + 32) x [p, q), right), which becomes the next task's left block.
 // Shared memory: three 32 x 33 blocks (D, and the left and below blocks, whose
-// roles swap from task to task) and six vectors.
+// roles swap from task to task) and five vectors.
 // ---------------------------------------------------------------------------
 struct BulgeArgs {
     cdf* A;
@@ -633,7 +668,7 @@ struct BulgeArgs {
 };
 
 constexpr int kBlk = kB * (kB + 1);
-constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 6 * kB);
+constexpr size_t kBulgeSmem = sizeof(cdf) * (3 * kBlk + 5 * kB);
 
 // publish a count: every thread's earlier writes were ordered before this by __syncthreads,
 // and the release makes them visible before the count (as in the grid barrier)
@@ -653,8 +688,7 @@ __device__ __forceinline__ cdf group_sum(cdf v) {
     return v;
 }
 constexpr int kBT = 512;                // threads of the bulge-chasing kernel
-constexpr int kBRow = kBT / kB;         // left-block threads per column of the block
-constexpr int kBCol = kB / kBRow;       // rows per left-block thread
+constexpr int kBW = kBT / 32;           // its warps
 
 // Each sweep publishes two counts.  crit[i] = t + 2 once the critical part of task t is
 // out: column 0 of its window's block after the two-sided update (whose entries, with the
@@ -662,11 +696,11 @@ constexpr int kBCol = kB / kBRow;       // rows per left-block thread
 // and the reflector of task t + 1.  pre[i] = t once the rest of task t - 1 (the other
 // columns of its diagonal block, its block below) and the left-block part of task t are
 // out.  Task t of sweep i:
-//   deferred part of task t - 1: D -= v w^H + w v^H on columns >= 1 written back, the block
-//     below (now the left block, in shared memory) -= tau z v^H on columns >= 1;
-//   left block (t >= 1; no other sweep touches it meanwhile): thread (c, k) = (tid / 16,
-//     tid % 16) forms its part over rows 2k, 2k + 1 of s_c = (v^H L)_c, summed over the 16
-//     threads; L -= conj(tau) v s^H (columns >= 1) is written back; pre[i] = t;
+//   deferred part of task t - 1 and left block of task t (no other sweep touches either
+//     meanwhile), one column c >= 1 per warp at a time, lane r = row r: D -= v w^H + w v^H
+//     written back; the block below of task t - 1 (in shared memory), now the left block L,
+//     -= tau z v^H in registers; s_c = (v^H L)_c by one warp sum; L -= conj(tau) v s^H
+//     written back; then pre[i] = t;
 //   once pre[i-1] >= t + 1 (sweep i - 1 is done with all of the window but its column 31):
 //     the window's block (lower triangle) and the block below are loaded but for column
 //     31; threads 0..255 form y = D v, threads 256..511 z = B v without those entries (8
@@ -688,9 +722,7 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
     cdf* vn = vs + kB;                 // v of the next task
     cdf* ys = vn + kB;                 // y, then w
     cdf* zs = ys + kB;                 // z, then tau z
-    cdf* ss = zs + kB;                 // s
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int pr = tid / kBRow, pk = tid % kBRow;   // left-block thread: column pr, rows kBCol pk ..
     const int half = tid >> 8, r2 = (tid & 255) >> 3, k2 = tid & 7;   // product thread: y or z, row r2
     const int n = a.n;
     cdf* A = a.A;
@@ -764,30 +796,21 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
             const int qb = min(q + kB, n), lenb = qb - q;
             const bool next = q <= n - 2;   // a task follows; then len == 32
             if (t > 0) {
-                // deferred part of task t - 1 (whose window [p - 32, p) is full)
+                // deferred part of task t - 1 (whose window [p - 32, p) is full) and the left
+                // block of task t, column by column: warp w takes columns w and w + 16, lane r
+                // row r; the block below of task t - 1 is updated in registers, s_c formed by
+                // one warp sum and the left block's update written back
                 const int pp = p - kB;
-                for (int e = tid; e < kB * kB; e += kBT) {
-                    const int r = e & 31, c = e >> 5;
-                    if (c >= 1 && c <= r) *at(pp + r, pp + c) = cdf_rank2(D[r * S + c], vo[r], ys[r], ys[c], vo[c]);
-                    if (r < len && c >= 1) Lb[r * S + c] = cdf_fma(Lb[r * S + c], negc(zs[r]), conjc(vo[c]));
-                }
-                __syncthreads();
-                // left block: s = v^H L, L -= conj(tau) v s^H on columns >= 1, written back
-                const cdf mct = negc(conjc(tau));
-                CAcc as;
-                as.zero();
-#pragma unroll
-                for (int u = 0; u < kBCol; ++u) {
-                    const int c = kBCol * pk + u;
-                    const cdf vc = shfl_cdf(vl, c);
-                    if (c < len) as.dot(vc, Lb[c * S + pr]);   // column pr of L, rows c
-                }
-                const cdf sr = group_sum<kBRow>(as.get());
-                if (pk == 0) ss[pr] = sr;
-                __syncthreads();
-                for (int e = tid; e < kB * kB; e += kBT) {
-                    const int r = e & 31, c = e >> 5;
-                    if (r < len && c >= 1) *at(p + r, p - kB + c) = cdf_fma(Lb[r * S + c], cdf_mul(mct, vs[r]), ss[c]);
+                const cdf f = cdf_mul(negc(conjc(tau)), vl);   // -conj(tau) v_r of this task
+                const cdf zr = zs[lane], vor = vo[lane], wr = ys[lane];   // task t - 1: tau z_r, v_r, w_r
+                for (int c = wid + (wid == 0 ? kBW : 0); c < kB; c += kBW) {   // column 0 needs neither
+                    if (lane >= c) *at(pp + lane, pp + c) = cdf_rank2(D[lane * S + c], vor, wr, ys[c], vo[c]);
+                    const cdf x = lane < len ? cdf_fma(Lb[lane * S + c], negc(zr), conjc(vo[c])) : cdf_zero();
+                    CAcc as;
+                    as.zero();
+                    as.dot(vl, x);
+                    const cdf sc = cacc_warp_sum(as);
+                    if (lane < len) *at(p + lane, p - kB + c) = cdf_fma(x, f, sc);
                 }
                 __syncthreads();
                 if (tid == 0) st_release_gpu(a.pre + i, t);
@@ -814,7 +837,7 @@ __global__ void __launch_bounds__(kBT, 1) bulge_kernel(BulgeArgs a) {
                         if (r2 < lenb && c < len && !(next && c == kB - 1)) acc.mac(Bb[r2 * S + c], vc);
                     }
                 }
-                const cdf rs = group_sum<8>(acc.get());
+                const cdf rs = cacc_group_sum<8>(acc);
                 if (k2 == 0) {
                     if (half == 0)
                         ys[r2] = rs;

@@ -63,49 +63,36 @@ __device__ __forceinline__ uint4 pack8(const float* x) {
     return u;
 }
 
-// row exponents of A22 per chunk: thread per (row r, chunk c), consecutive threads on
-// consecutive rows; 2^ex is above the row's largest entry in the chunk
-__global__ void a22_exp_kernel(const cdf* __restrict__ A, int n, int r1, int m, int nrt, int nch, int* ex) {
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// A22 digits per chunk in one pass: a CTA takes 32 rows of one chunk, warp g the columns
+// 8 g .. 8 g + 7 (lane = row, so the loads are coalesced over rows); the row's exponent
+// per chunk (2^ex above its largest entry there) from the eight warps' maxima in shared
+// memory, written for the GEMM's epilogue, then the exact digit split of the eight entries:
+// the 16-byte pieces of each digit for the group's Re parts (K 8g .. 8g+7) and Im parts
+// (K 64 + 8g ..), in tiles [rt][c][k] of 128 x 128 in the core-matrix layout
+__global__ void __launch_bounds__(256) a22_digits_kernel(const cdf* __restrict__ A, int n, int r1, int m, int nrt,
+                                                         int nch, __nv_bfloat16* Adig, int* __restrict__ ex) {
+    __shared__ float s_mx[kZC / 8][32];
     const int64_t rows = (int64_t)nrt * kZM;
-    if (gid >= rows * nch) return;
-    const int r = (int)(gid % rows), c = (int)(gid / rows);
-    const int c0 = c * kZC, cn = min(kZC, m - c0);
-    float mx = 0.f;
-    if (r < m) {
-        const cdf* row = A + (size_t)(r1 + c0) * n + r1 + r;
-#pragma unroll 8
-        for (int j = 0; j < cn; ++j) {
-            const cdf z = __ldcg(row + (size_t)j * n);
-            mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.z)));
-        }
-    }
-    ex[gid] = exp_above_f(mx);
-}
-
-// A22 digits: thread per (row r of a 128-row tile, chunk c, group of 8 columns g): the 16-byte
-// pieces of each digit for the group's Re parts (K 8g .. 8g+7) and Im parts (K 64 + 8g ..).
-// Tiles [rt][c][k] of 128 x 128 in the core-matrix layout; consecutive threads take
-// consecutive rows (coalesced loads).
-__global__ void a22_digits_kernel(const cdf* __restrict__ A, int n, int r1, int m, int nrt, int nch,
-                                  __nv_bfloat16* Adig, const int* __restrict__ ex) {
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t rows = (int64_t)nrt * kZM;
-    if (gid >= rows * nch * (kZC / 8)) return;
-    const int r = (int)(gid % rows);
-    const int64_t cg = gid / rows;
-    const int g = (int)(cg % (kZC / 8)), c = (int)(cg / (kZC / 8));
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, c = blockIdx.y;
+    const int r = blockIdx.x * 32 + lane;
     const int rt = r / kZM, rr = r % kZM;
     const bool live = r < m;
     const int c0 = c * kZC, cn = min(kZC, m - c0);
     const cdf* row = A + (size_t)(r1 + c0) * n + r1 + r;   // entry j of the chunk at row[j n]
-    const int e = ex[(size_t)c * rows + r];
     cdf z[8];
+    float mx = 0.f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int j = 8 * g + u;
         z[u] = live && j < cn ? __ldcg(row + (size_t)j * n) : cdf_zero();
+        mx = fmaxf(mx, fmaxf(fabsf(z[u].x), fabsf(z[u].z)));
     }
+    s_mx[g][lane] = mx;
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < kZC / 8; ++h) mx = fmaxf(mx, s_mx[h][lane]);
+    const int e = exp_above_f(mx);
+    if (g == 0) ex[(size_t)c * rows + r] = e;
     float dr[8][kZDig], di[8][kZDig];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -380,10 +367,7 @@ int launch_zgemm_tc(const cdf* A, int64_t n64, int r1, int m, const cdf* V, void
     int* ex = (int*)p;
     int* fy = ex + (size_t)nch * nrt * kZM;
     {
-        a22_exp_kernel<<<(unsigned)(((int64_t)nrt * kZM * nch + 255) / 256), 256, 0, st>>>(A, n, r1, m, nrt, nch, ex);
-        note_launch();
-        const int64_t threads = (int64_t)nrt * kZM * nch * (kZC / 8);
-        a22_digits_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, n, r1, m, nrt, nch, Adig, ex);
+        a22_digits_kernel<<<dim3((unsigned)(nrt * kZM / 32), (unsigned)nch), 256, 0, st>>>(A, n, r1, m, nrt, nch, Adig, ex);
         note_launch();
         v_digits_kernel<<<(nch * (kZC / 8) * kZL + 127) / 128, 128, 0, st>>>(V, n, r1, m, nch, Bdig, fy);
         note_launch();
