@@ -45,31 +45,46 @@ __device__ __forceinline__ V cmc(V a, V b) {  // a conj(b)
     return r;
 }
 
-// One CTA per rotated pair.  Phase 1: for every row (v c) at k the factors
-// L = Gamma_v(k)[v1][v] conj(Gamma_c(k)[c1][c]) with the seed rows (v1 c1)
-// of its multiplets, and for every column (v' c') at k' the factors
-// R = Gamma_c(k')[c2][c'] conj(Gamma_v(k')[v2][v']) with the seed columns,
-// into shared memory (at most 9 terms each; one at a general k).  Phase 2:
-// out[(v c), (v' c')] = sum L S[(v1 c1), (v2 c2)] R, the seed element read
-// from the tile arena, written to the block and to its mirror.
+// One warp per rotated pair, kRotWarps pairs per CTA (warp-level synchronisation
+// only, so a pair's latency chain overlaps the other pairs').  Phase 1: for every
+// row (v c) at k the factors L = Gamma_v(k)[v1][v] conj(Gamma_c(k)[c1][c]) with the
+// seed rows (v1 c1) of its multiplets, and for every column (v' c') at k' the
+// factors R = Gamma_c(k')[c2][c'] conj(Gamma_v(k')[v2][v']) with the seed columns,
+// into the warp's part of shared memory (at most 9 terms each; one at a general k).
+// Phase 2: out[(v c), (v' c')] = sum L S[(v1 c1), (v2 c2)] R, the seed element read
+// from the tile arena, written to the block and to its mirror; where every
+// multiplet of both sides is a single band (most k) the one-term form runs with
+// several elements' loads in flight per lane.
 constexpr int kMaxTerms = 9;
-constexpr int kRotThreads = 128;
+constexpr int kRotWarps = 8;
+
+// shared memory of one warp: factors [2][B][kMaxTerms], seed indices [2][B][kMaxTerms], counts [2][B]
+__host__ __device__ constexpr size_t rot_warp_bytes(int B, size_t vsize) {
+    return (size_t)2 * B * kMaxTerms * (vsize + sizeof(int)) + sizeof(int) * 2 * (size_t)B;
+}
 
 template <typename R, bool kBatch>
-__global__ void __launch_bounds__(kRotThreads) rotate_kernel(const RotSys* __restrict__ systems,
-                                                             const __grid_constant__ RotSys one,
-                                                             const RotTask* __restrict__ tasks,
-                                                             typename C2r<R>::T* X) {
+__global__ void __launch_bounds__(kRotWarps * 32) rotate_kernel(const RotSys* __restrict__ systems,
+                                                                const __grid_constant__ RotSys one,
+                                                                const RotTask* __restrict__ tasks, int64_t ntasks,
+                                                                int bstride, typename C2r<R>::T* X) {
     using V = typename C2r<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RotTask t = tasks[blockIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ti = (int64_t)blockIdx.x * kRotWarps + wid;
+    if (ti >= ntasks) return;   // warp-uniform: no CTA-wide barrier follows
+    const RotTask t = tasks[ti];
     const RotSys& Y = kBatch ? systems[t.flags >> 1] : one;
     const int nv = Y.nv, nc = Y.nc, nb = Y.nb, B = nv * nc;
-    V* fac = (V*)smem_raw;                               // [2][B][kMaxTerms]
+    // the warps' parts are laid out for the launch's largest block (bstride >= B): the
+    // instances of a batch may differ in B
+    unsigned char* wbase = smem_raw + (size_t)wid * rot_warp_bytes(bstride, sizeof(V));
+    V* fac = (V*)wbase;                                  // [2][B][kMaxTerms]
     int* idx = (int*)(fac + 2 * B * kMaxTerms);          // [2][B][kMaxTerms]
     int* cnt = idx + 2 * B * kMaxTerms;                  // [2][B]
     const V* gam = (const V*)Y.gam + (size_t)t.s * Y.gps;
-    for (int q = threadIdx.x; q < 2 * B; q += blockDim.x) {
+    bool single = true;
+    for (int q = lane; q < 2 * B; q += 32) {
         const int side = q / B, rc = q % B;              // side 0: rows at k, side 1: columns at k'
         const int kk = side == 0 ? t.k : t.kp;
         const int v = rc / nc, c = rc % nc, ik = kk * nb;
@@ -87,9 +102,26 @@ __global__ void __launch_bounds__(kRotThreads) rotate_kernel(const RotSys* __res
                 ++n;
             }
         cnt[side * B + rc] = n;
+        single = single && n == 1;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    single = __all_sync(0xffffffffu, single);
+    __syncwarp();
+    const V* S = X + t.src;
+    if (single) {
+#pragma unroll 8
+        for (int e = lane; e < B * B; e += 32) {
+            const int r = e % B, col = e / B;
+            const V x = S[(int64_t)idx[(B + col) * kMaxTerms] * t.ld + idx[r * kMaxTerms]];
+            V acc = cm(cm(fac[r * kMaxTerms], x), fac[(B + col) * kMaxTerms]);
+            X[t.dst + (int64_t)col * t.ld + r] = acc;
+            if (t.flags & 1) {
+                acc.y = -acc.y;
+                X[t.dstm + (int64_t)r * t.ld + col] = acc;
+            }
+        }
+        return;
+    }
+    for (int e = lane; e < B * B; e += 32) {
         const int r = e % B, col = e / B;
         const int nr = cnt[r], ncl = cnt[B + col];
         V acc;
@@ -99,7 +131,7 @@ __global__ void __launch_bounds__(kRotThreads) rotate_kernel(const RotSys* __res
             const int srow = idx[r * kMaxTerms + i];
             for (int j = 0; j < ncl; ++j) {
                 const int scol = idx[(B + col) * kMaxTerms + j];
-                const V p = cm(cm(Lf, X[t.src + (int64_t)scol * t.ld + srow]), fac[(B + col) * kMaxTerms + j]);
+                const V p = cm(cm(Lf, S[(int64_t)scol * t.ld + srow]), fac[(B + col) * kMaxTerms + j]);
                 acc.x += p.x;
                 acc.y += p.y;
             }
@@ -117,13 +149,15 @@ int launch_rotate_t(const RotSys* systems, const RotSys& one, int B, const RotTa
                     cudaStream_t st) {
     using V = typename C2r<R>::T;
     if (n == 0) return BSE_OK;
-    const size_t sm = (size_t)2 * B * kMaxTerms * (sizeof(V) + sizeof(int)) + sizeof(int) * 2 * B;
+    const size_t sm = kRotWarps * rot_warp_bytes(B, sizeof(V));
     if (sm > 227 * 1024) return fail(BSE_EUNSUPPORTED, "rotation of %d x %d blocks exceeds shared memory", B, B);
     cudaError_t e = cudaFuncSetAttribute(rotate_kernel<R, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return fail(BSE_ECUDA, "rotate smem: %s", cudaGetErrorString(e));
-    for (int64_t off = 0; off < n; off += 1 << 30) {
-        const int64_t nt = n - off < (1 << 30) ? n - off : (1 << 30);
-        rotate_kernel<R, kBatch><<<(unsigned)nt, kRotThreads, sm, st>>>(systems, one, tasks + off, (V*)X);
+    const int64_t per_launch = (int64_t)kRotWarps << 30;
+    for (int64_t off = 0; off < n; off += per_launch) {
+        const int64_t nt = n - off < per_launch ? n - off : per_launch;
+        rotate_kernel<R, kBatch><<<(unsigned)((nt + kRotWarps - 1) / kRotWarps), kRotWarps * 32, sm, st>>>(
+            systems, one, tasks + off, nt, B, (V*)X);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(BSE_ECUDA, "rotate launch: %s", cudaGetErrorString(e));
