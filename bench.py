@@ -594,17 +594,18 @@ def run_ours(args, rank, world, local):
                       "launches_per_step": sum(1 for s in stats[-1][1]["solvers"] if s == bse.BSE_SOLVER_TRIDIAG),
                       "traffic": dram_traffic(rname, args.config, args.prec, args.block)})
     if ms_rotate > 0 and work["rotated"] > 0:
-        # the rotation kernel moves data: the seed block in, the block (and, for diagonal star pairs, its
-        # mirror) out; B^2 elements of the arena precision each
+        # the rotation kernel moves data: the seed block in, the block out, B^2 elements of the arena
+        # precision each (the mirrors of diagonal star-pair tiles, about 1 % of the blocks at si12, are
+        # not counted)
         el = 16 if prec == bse.BSE_FP64 else 8
         bsz = int(inp["nv"]) * int(inp["nc"])
-        rbytes = work["rotated"] * bsz * bsz * el * 2.5
+        rbytes = work["rotated"] * bsz * bsz * el * 2.0
         hbm = measured_peak("hbm_gbs")
         rach = rbytes / (ms_rotate * 1e-3) / 1e9
         roofs.append({"bound": "hbm", "kernel": "rotate_kernel", "ms_per_step": ms_rotate, "achieved": rach,
                       "peak": hbm, "unit": "GB/s", "frac": rach / hbm if hbm else None,
-                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); bytes: seed block read, block "
-                                     "written, half the blocks also mirrored",
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); bytes: seed block read and "
+                                     "block written per rotated block",
                       "launches_per_step": direct_launches,
                       "traffic": dram_traffic("rotate_kernel", args.config, args.prec, args.block)})
     roof_main = max(roofs, key=lambda r: r["ms_per_step"])   # the kernel with the largest share of the step
