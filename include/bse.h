@@ -411,7 +411,7 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      (FP32's exponent range; Hartree-unit blocks are far
  *                      inside it).  Blocks of up to about 1200 rows are
  *                      reduced in shared memory (a column per CTA); larger
- *                      ones, up to n = 3200, with their columns in device
+ *                      ones, up to n = 1800, with their columns in device
  *                      memory, by a blocked form of the same reduction
  *                      (panels of 32 reflectors: one pass of column dot
  *                      products per step; at the panel's end its rank-64
@@ -419,7 +419,7 @@ int bse_block_spectrum_lanczos(bse_ctx* ctx, int32_t irrep, int32_t partner, con
  *                      from an exact split of V and W into 8 bf16 digits,
  *                      digit-pair products summed in FP32 (exactly for the
  *                      leading groups), the groups combined in double-float);
- *                      from n = 3200 by the two-stage reduction of
+ *                      from n = 1800 by the two-stage reduction of
  *                      BSE_SOLVER_TRIDIAG_TWOSTAGE.  Needs the partners'
  *                      projections b_i to be parallel (true for the partner
  *                      blocks of bse_partner_spectrum) and n <= 8192; the

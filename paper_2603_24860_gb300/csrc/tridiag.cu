@@ -38,7 +38,7 @@ namespace bse {
 namespace {
 
 constexpr int kTriThreads = 256;
-constexpr int64_t kTwoStageFrom = 3200;   // the automatic choice takes the two-stage reduction from this size
+constexpr int64_t kTwoStageFrom = 1800;   // the automatic choice takes the two-stage reduction from this size
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kChunk = 8;                 // columns updated together
 
@@ -1297,8 +1297,8 @@ int launch_tridiag_spectrum(double2* h, int64_t n, const double2* b, double scal
     const size_t vec_bytes = sizeof(cdf) * 3 * (size_t)n;   // v, w and the next column of a step
     const size_t cols_bytes = sizeof(cdf) * (size_t)((n - 1) / G + 1) * n;
     const bool smem = variant == 0 && vec_bytes + cols_bytes + static_smem <= (size_t)maxsm;
-    // above the shared-memory size: the blocked reduction up to n = 3200, where the two-stage
-    // one (whose band-to-tridiagonal stage takes about 14 us per row) overtakes it
+    // above the shared-memory size: the blocked reduction up to n = 1800, where the two-stage
+    // one (whose band-to-tridiagonal stage takes about 9 us per row) overtakes it
     if (variant == 0 && !smem && n >= kTwoStageFrom) variant = 3;
     const bool tcu = variant != 2;   // blocked: panel-end update on the tensor cores between launches
     if (!smem) G = (int)std::min<int64_t>(sms, n);
