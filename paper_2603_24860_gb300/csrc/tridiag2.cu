@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(kT2, 1) panel_qr_kernel(PanelArgs a) {
 // The same panel QR on one thread-block cluster: the panel rows are spread over
 // the cluster's CTAs (in shared memory, v_l stored in place of the entries it
 // annihilates, beta_l on the diagonal), and the per-reflector sums travel through
-// distributed shared memory with two cluster barriers per reflector instead of
-// two grid barriers and global-memory round trips.  A CTA reads another CTA's
-// part only between the barrier after which it was written and the next one,
-// and a final barrier keeps every CTA resident until the last remote read.
+// distributed shared memory with one cluster barrier per reflector instead of
+// grid barriers and global-memory round trips.  A CTA reads another CTA's part
+// only between the barrier after which it was written and the next one, and a
+// final barrier keeps every CTA resident until the last remote read.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
