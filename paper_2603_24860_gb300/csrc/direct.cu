@@ -11,7 +11,10 @@
 //
 // The pair densities use compacted overlap lists: for each Q the plane waves
 // p' with p' + Q in S_k are gathered once (warp ballot), and a warp sweeps a
-// list with its lanes spread over band pairs, so every issued FMA is useful.
+// list.  In FP32 a lane takes a 4 x 4 tile of band pairs and a group of list
+// entries (8 coefficients from shared memory per 16 complex multiply-adds; the
+// groups summed by shuffles); in FP64, where the FP64 pipe bounds the loop, a
+// lane takes up to four band pairs and every entry.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,7 +65,9 @@ __host__ __device__ inline DirectPlan direct_plan(int cplx_bytes, int nb, int nv
     return p;
 }
 
-constexpr int kMaxSlots = 4;   // band pairs per lane: nc^2 + nv^2 <= 128
+
+constexpr int kMaxPairs = 128;   // band pairs nc^2 + nv^2 per k pair (their 4 x 4 tiles fit one warp)
+constexpr int kRhoSlots = kMaxPairs / 32;   // band pairs per lane in the FP64 pair-density loop
 
 // One k pair (task t) of system I with the whole CTA; smem: the dynamic shared
 // memory of the CTA (direct_plan of the system).
@@ -126,61 +131,135 @@ __device__ __forceinline__ void direct_task(const DirectInst& I, const PairTask 
     (void)npk;
     __syncthreads();
 
-    // rho: one warp per Q, lanes over band pairs (cc' first, then vv')
-    int na[kMaxSlots], nbp[kMaxSlots];
-#pragma unroll
-    for (int s = 0; s < kMaxSlots; ++s) {
-        int p = lane + 32 * s;
-        if (p < nc * nc) {
-            na[s] = nv + p / nc;
-            nbp[s] = nv + p % nc;
-        } else if (p < P) {
-            na[s] = (p - nc * nc) / nv;
-            nbp[s] = (p - nc * nc) % nv;
+    if constexpr (sizeof(R) == 4) {
+        // rho: one warp per Q.  The band pairs form an nc x nc (cc') and an nv x nv (vv') matrix,
+        // cut into tiles of up to 4 x 4; lane = (entry group gid, tile tau): the lane sums its
+        // tile over the list entries gid, gid + G, ... (4 + 4 coefficients loaded per entry for
+        // 16 complex multiply-adds), and the G groups are summed by shuffles at the end.
+        const int ntc = (nc + 3) >> 2, ntv = (nv + 3) >> 2, NT = ntc * ntc + ntv * ntv;
+        const int G = 32 / NT, tau = lane % NT, gid = lane / NT;
+        int ra, cb, nrow, ncol, pbase, pstride;   // tile rows / columns (band indices), output p = pbase + u pstride + w
+        if (tau < ntc * ntc) {
+            const int tr = tau / ntc, tc = tau % ntc;
+            ra = nv + 4 * tr;
+            cb = nv + 4 * tc;
+            nrow = min(4, nc - 4 * tr);
+            ncol = min(4, nc - 4 * tc);
+            pbase = (4 * tr) * nc + 4 * tc;
+            pstride = nc;
         } else {
-            na[s] = nbp[s] = -1;
+            const int tv = tau - ntc * ntc, tr = tv / ntv, tc = tv % ntv;
+            ra = 4 * tr;
+            cb = 4 * tc;
+            nrow = min(4, nv - 4 * tr);
+            ncol = min(4, nv - 4 * tc);
+            pbase = nc * nc + (4 * tr) * nv + 4 * tc;
+            pstride = nv;
         }
-    }
-    for (int g = warp; g < ng; g += nwarp) {
-        V acc[kMaxSlots];
+        for (int g = warp; g < ng; g += nwarp) {
+            V acc[4][4];
 #pragma unroll
-        for (int s = 0; s < kMaxSlots; ++s) acc[s].x = acc[s].y = R(0);
-        const int* L = list + g * S.npw_max;
-        const int len = cnt[g];
-        // four list entries per iteration, their loads issued before the arithmetic
-        int e = 0;
-        for (; e + 3 < len; e += 4) {
-            const int ij0 = L[e], ij1 = L[e + 1], ij2 = L[e + 2], ij3 = L[e + 3];
-            const V* a0 = ckT + (ij0 & 0xffff) * nb;
-            const V* b0 = ckpT + (ij0 >> 16) * nb;
-            const V* a1 = ckT + (ij1 & 0xffff) * nb;
-            const V* b1 = ckpT + (ij1 >> 16) * nb;
-            const V* a2 = ckT + (ij2 & 0xffff) * nb;
-            const V* b2 = ckpT + (ij2 >> 16) * nb;
-            const V* a3 = ckT + (ij3 & 0xffff) * nb;
-            const V* b3 = ckpT + (ij3 >> 16) * nb;
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int s = 0; s < kMaxSlots; ++s)
-                if (na[s] >= 0) {
-                    const V x0 = a0[na[s]], y0 = b0[nbp[s]], x1 = a1[na[s]], y1 = b1[nbp[s]];
-                    const V x2 = a2[na[s]], y2 = b2[nbp[s]], x3 = a3[na[s]], y3 = b3[nbp[s]];
-                    cmacc(acc[s], x0, y0);
-                    cmacc(acc[s], x1, y1);
-                    cmacc(acc[s], x2, y2);
-                    cmacc(acc[s], x3, y3);
+                for (int w = 0; w < 4; ++w) acc[u][w].x = acc[u][w].y = R(0);
+            const int* L = list + g * S.npw_max;
+            const int len = gid < G ? cnt[g] : 0;
+#pragma unroll 2
+            for (int e = gid; e < len; e += G) {
+                const int ij = L[e];
+                const V* a = ckT + (ij & 0xffff) * nb + ra;
+                const V* b = ckpT + (ij >> 16) * nb + cb;
+                V x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    x[u] = u < nrow ? a[u] : V{R(0), R(0)};
+                    y[u] = u < ncol ? b[u] : V{R(0), R(0)};
                 }
-        }
-        for (; e < len; ++e) {
-            const int ij = L[e];
-            const V* a = ckT + (ij & 0xffff) * nb;
-            const V* b = ckpT + (ij >> 16) * nb;
 #pragma unroll
-            for (int s = 0; s < kMaxSlots; ++s)
-                if (na[s] >= 0) cmacc(acc[s], a[na[s]], b[nbp[s]]);
-        }
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int s = 0; s < kMaxSlots; ++s)
-            if (na[s] >= 0) rho[g * P + lane + 32 * s] = acc[s];
+                    for (int w = 0; w < 4; ++w) cmacc(acc[u][w], x[u], y[w]);
+            }
+            // sum over the entry groups: lane tau + NT k holds group k's part
+            for (int off = 1; off < G; off <<= 1) {
+                const bool take = gid % (2 * off) == 0 && gid + off < G;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const R ox = __shfl_down_sync(0xffffffffu, acc[u][w].x, off * NT);
+                        const R oy = __shfl_down_sync(0xffffffffu, acc[u][w].y, off * NT);
+                        if (take) {
+                            acc[u][w].x += ox;
+                            acc[u][w].y += oy;
+                        }
+                    }
+            }
+            if (gid == 0)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        if (u < nrow && w < ncol) rho[g * P + pbase + u * pstride + w] = acc[u][w];
+        }
+    } else {
+        // FP64: the FP64 pipe bounds the loop, so the lanes keep one band pair per slot
+        // rho: one warp per Q, lanes over band pairs (cc' first, then vv')
+        int na[kRhoSlots], nbp[kRhoSlots];
+#pragma unroll
+        for (int s = 0; s < kRhoSlots; ++s) {
+            int p = lane + 32 * s;
+            if (p < nc * nc) {
+                na[s] = nv + p / nc;
+                nbp[s] = nv + p % nc;
+            } else if (p < P) {
+                na[s] = (p - nc * nc) / nv;
+                nbp[s] = (p - nc * nc) % nv;
+            } else {
+                na[s] = nbp[s] = -1;
+            }
+        }
+        for (int g = warp; g < ng; g += nwarp) {
+            V acc[kRhoSlots];
+#pragma unroll
+            for (int s = 0; s < kRhoSlots; ++s) acc[s].x = acc[s].y = R(0);
+            const int* L = list + g * S.npw_max;
+            const int len = cnt[g];
+            // four list entries per iteration, their loads issued before the arithmetic
+            int e = 0;
+            for (; e + 3 < len; e += 4) {
+                const int ij0 = L[e], ij1 = L[e + 1], ij2 = L[e + 2], ij3 = L[e + 3];
+                const V* a0 = ckT + (ij0 & 0xffff) * nb;
+                const V* b0 = ckpT + (ij0 >> 16) * nb;
+                const V* a1 = ckT + (ij1 & 0xffff) * nb;
+                const V* b1 = ckpT + (ij1 >> 16) * nb;
+                const V* a2 = ckT + (ij2 & 0xffff) * nb;
+                const V* b2 = ckpT + (ij2 >> 16) * nb;
+                const V* a3 = ckT + (ij3 & 0xffff) * nb;
+                const V* b3 = ckpT + (ij3 >> 16) * nb;
+#pragma unroll
+                for (int s = 0; s < kRhoSlots; ++s)
+                    if (na[s] >= 0) {
+                        const V x0 = a0[na[s]], y0 = b0[nbp[s]], x1 = a1[na[s]], y1 = b1[nbp[s]];
+                        const V x2 = a2[na[s]], y2 = b2[nbp[s]], x3 = a3[na[s]], y3 = b3[nbp[s]];
+                        cmacc(acc[s], x0, y0);
+                        cmacc(acc[s], x1, y1);
+                        cmacc(acc[s], x2, y2);
+                        cmacc(acc[s], x3, y3);
+                    }
+            }
+            for (; e < len; ++e) {
+                const int ij = L[e];
+                const V* a = ckT + (ij & 0xffff) * nb;
+                const V* b = ckpT + (ij >> 16) * nb;
+#pragma unroll
+                for (int s = 0; s < kRhoSlots; ++s)
+                    if (na[s] >= 0) cmacc(acc[s], a[na[s]], b[nbp[s]]);
+            }
+#pragma unroll
+            for (int s = 0; s < kRhoSlots; ++s)
+                if (na[s] >= 0) rho[g * P + lane + 32 * s] = acc[s];
+        }
     }
     __syncthreads();
 
@@ -278,8 +357,8 @@ static int launch_direct_t(const DirectInst* insts, const DirectInst& one, const
                            int64_t ntasks, void* X, cudaStream_t st) {
     using V = typename C2<R>::T;
     if (ntasks == 0) return BSE_OK;
-    if (s.nc * s.nc + s.nv * s.nv > 32 * kMaxSlots)
-        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", 32 * kMaxSlots);
+    if (s.nc * s.nc + s.nv * s.nv > kMaxPairs)
+        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", kMaxPairs);
     if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
     DirectPlan pl = direct_plan((int)sizeof(V), s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
     if (pl.total + sizeof(DirectInst) > 227 * 1024)
@@ -307,8 +386,8 @@ static int launch_direct_persistent_t(const DirectInst* insts, const DevSys& s, 
                                       cudaStream_t st) {
     using V = typename C2<R>::T;
     if (ntasks == 0) return BSE_OK;
-    if (s.nc * s.nc + s.nv * s.nv > 32 * kMaxSlots)
-        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", 32 * kMaxSlots);
+    if (s.nc * s.nc + s.nv * s.nv > kMaxPairs)
+        return fail(BSE_EUNSUPPORTED, "nc^2 + nv^2 > %d is not supported", kMaxPairs);
     if (s.npw_max > 65535) return fail(BSE_EUNSUPPORTED, "npw_max > 65535");
     if (threads != 128 && threads != 256) return fail(BSE_EINVAL, "threads per CTA must be 128 or 256");
     DirectPlan pl = direct_plan((int)sizeof(V), s.nb, s.nv, s.nc, s.npw_max, s.ng_max);
