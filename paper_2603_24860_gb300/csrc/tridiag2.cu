@@ -680,13 +680,6 @@ __device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
     return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
                        __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
-// sum over the G lanes of a group (lanes G g .. G g + G - 1)
-template <int G>
-__device__ __forceinline__ cdf group_sum(cdf v) {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v = cdf_add(v, cdf_shfl_xor(v, o));
-    return v;
-}
 constexpr int kBT = 512;                // threads of the bulge-chasing kernel
 constexpr int kBW = kBT / 32;           // its warps
 
